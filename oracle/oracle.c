@@ -1,0 +1,511 @@
+/*
+ * FP64 CPU oracle for Noise2Fast (arXiv 2108.10209) -- TEST INFRASTRUCTURE ONLY.
+ *
+ * Written from the paper's Methods section ("Noise2Fast Implementation Details") and the
+ * Theoretical Background (Eq. 6-7). Each function states the passage it follows; the readings
+ * taken where the paper is silent or garbled are listed in oracle.h and in the design notes.
+ * No blocking, fusion or reordering beyond the definitions: every output element is a plain
+ * sum accumulated in the order the loop nest shows.
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------------------------ */
+/* SplitMix64 (Steele, Lea & Flood, OOPSLA 2014), counter form.                                */
+uint64_t orc_splitmix64_at(uint64_t seed, uint64_t k) {
+  uint64_t z = seed + (k + 1u) * 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+/* Methods, first paragraph: two 32-channel 3x3 conv+ReLU, repeated three more times with the
+ * width doubled each time, then 1x1 conv + sigmoid. Widths are a parameter (see oracle.h). */
+size_t orc_param_count(const int widths[ORC_LAYERS]) {
+  size_t n = 0;
+  int cin = 1;
+  for (int l = 0; l < ORC_LAYERS; ++l) {
+    n += (size_t)widths[l] * cin * 9 + widths[l];
+    cin = widths[l];
+  }
+  return n + (size_t)cin + 1;
+}
+
+/* Offsets of W_l and b_l (l = 0..7) and of the head (index 8) in the flat vector. */
+static void param_offsets(const int widths[ORC_LAYERS], size_t ow[ORC_LAYERS + 1],
+                          size_t ob[ORC_LAYERS + 1]) {
+  size_t n = 0;
+  int cin = 1;
+  for (int l = 0; l < ORC_LAYERS; ++l) {
+    ow[l] = n;
+    n += (size_t)widths[l] * cin * 9;
+    ob[l] = n;
+    n += widths[l];
+    cin = widths[l];
+  }
+  ow[ORC_LAYERS] = n;
+  ob[ORC_LAYERS] = n + cin;
+}
+
+void orc_init_params(const int widths[ORC_LAYERS], uint64_t seed, double* theta) {
+  size_t k = 0;
+  int cin = 1;
+  for (int l = 0; l <= ORC_LAYERS; ++l) {
+    const int head = (l == ORC_LAYERS);
+    const int cout = head ? 1 : widths[l];
+    const int fan_in = head ? cin : cin * 9;
+    const size_t nw = head ? (size_t)cin : (size_t)cout * cin * 9;
+    const double bound = 1.0 / sqrt((double)fan_in);
+    for (size_t i = 0; i < nw + (size_t)cout; ++i, ++k) {
+      const double u = (double)(orc_splitmix64_at(seed, k) >> 11) * 0x1.0p-53;
+      theta[k] = (double)(float)((2.0 * u - 1.0) * bound);
+    }
+    if (!head) cin = widths[l];
+  }
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Checkerboard downsampling, Eq. 6-7 ("up") and the Methods' primed equations ("left").       */
+void orc_checker(const double* x, int H, int W, double* up_e, double* up_o, double* lf_e,
+                 double* lf_o) {
+  const int hw = W / 2, hh = H / 2;
+  for (int i = 0; i < H; ++i)
+    for (int j = 0; j < hw; ++j) {
+      up_e[i * hw + j] = x[i * W + 2 * j + (i % 2)];
+      up_o[i * hw + j] = x[i * W + 2 * j + 1 - (i % 2)];
+    }
+  for (int i = 0; i < hh; ++i)
+    for (int j = 0; j < W; ++j) {
+      lf_e[i * W + j] = x[(2 * i + (j % 2)) * W + j];
+      lf_o[i * W + j] = x[(2 * i + 1 - (j % 2)) * W + j];
+    }
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* 3x3 convolution with zero "same" padding, forward.                                         */
+void orc_conv3x3_fwd(const double* in, int cin, int h, int w, const double* wt, const double* b,
+                     int cout, int relu, double* out) {
+  const size_t hw = (size_t)h * w;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int o = 0; o < cout; ++o) {
+    double* op = out + (size_t)o * hw;
+    for (size_t i = 0; i < hw; ++i) op[i] = b[o];
+    for (int c = 0; c < cin; ++c) {
+      const double* ip = in + (size_t)c * hw;
+      for (int ky = 0; ky < 3; ++ky)
+        for (int kx = 0; kx < 3; ++kx) {
+          const double wv = wt[((size_t)o * cin + c) * 9 + ky * 3 + kx];
+          const int dy = ky - 1, dx = kx - 1;
+          const int x0 = dx < 0 ? 1 : 0, x1 = dx > 0 ? w - 1 : w;
+          for (int y = 0; y < h; ++y) {
+            const int yy = y + dy;
+            if (yy < 0 || yy >= h) continue;
+            double* orow = op + (size_t)y * w;
+            const double* irow = ip + (size_t)yy * w + dx;
+            for (int x = x0; x < x1; ++x) orow[x] += wv * irow[x];
+          }
+        }
+    }
+    if (relu)
+      for (size_t i = 0; i < hw; ++i) op[i] = op[i] > 0.0 ? op[i] : 0.0;
+  }
+}
+
+/* Gradient w.r.t. the input: correlation with the 180-degree-rotated, transposed kernel.     */
+void orc_conv3x3_dgrad(const double* dout, int cout, int h, int w, const double* wt, int cin,
+                       double* din) {
+  const size_t hw = (size_t)h * w;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int c = 0; c < cin; ++c) {
+    double* dp = din + (size_t)c * hw;
+    for (size_t i = 0; i < hw; ++i) dp[i] = 0.0;
+    for (int o = 0; o < cout; ++o) {
+      const double* gp = dout + (size_t)o * hw;
+      for (int ky = 0; ky < 3; ++ky)
+        for (int kx = 0; kx < 3; ++kx) {
+          const double wv = wt[((size_t)o * cin + c) * 9 + ky * 3 + kx];
+          const int dy = ky - 1, dx = kx - 1;
+          /* din(y,x) += w * dout(y-dy, x-dx) */
+          const int x0 = dx > 0 ? 1 : 0, x1 = dx < 0 ? w - 1 : w;
+          for (int y = 0; y < h; ++y) {
+            const int yy = y - dy;
+            if (yy < 0 || yy >= h) continue;
+            double* drow = dp + (size_t)y * w;
+            const double* grow = gp + (size_t)yy * w - dx;
+            for (int x = x0; x < x1; ++x) drow[x] += wv * grow[x];
+          }
+        }
+    }
+  }
+}
+
+/* Gradient w.r.t. the weights and biases; each sum runs over pixels in raster order.       */
+void orc_conv3x3_wgrad(const double* dout, int cout, int h, int w, const double* in, int cin,
+                       double* dw, double* db) {
+  const size_t hw = (size_t)h * w;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int oc = 0; oc < cout * cin; ++oc) {
+    const int o = oc / cin, c = oc % cin;
+    const double* gp = dout + (size_t)o * hw;
+    const double* ip = in + (size_t)c * hw;
+    for (int ky = 0; ky < 3; ++ky)
+      for (int kx = 0; kx < 3; ++kx) {
+        const int dy = ky - 1, dx = kx - 1;
+        double s = 0.0;
+        for (int y = 0; y < h; ++y) {
+          const int yy = y + dy;
+          if (yy < 0 || yy >= h) continue;
+          for (int x = 0; x < w; ++x) {
+            const int xx = x + dx;
+            if (xx < 0 || xx >= w) continue;
+            s += gp[(size_t)y * w + x] * ip[(size_t)yy * w + xx];
+          }
+        }
+        dw[((size_t)o * cin + c) * 9 + ky * 3 + kx] = s;
+      }
+  }
+  for (int o = 0; o < cout; ++o) {
+    double s = 0.0;
+    for (size_t i = 0; i < hw; ++i) s += dout[(size_t)o * hw + i];
+    db[o] = s;
+  }
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Head: 1x1 convolution to one channel (sigmoid applied by the callers).                     */
+void orc_head_fwd(const double* a, int c, int npx, const double* w, double b, double* z) {
+#pragma omp parallel for schedule(static)
+  for (int p = 0; p < npx; ++p) {
+    double s = b;
+    for (int k = 0; k < c; ++k) s += w[k] * a[(size_t)k * npx + p];
+    z[p] = s;
+  }
+}
+
+double orc_sigmoid(double z) {
+  if (z >= 0.0) return 1.0 / (1.0 + exp(-z));
+  const double e = exp(z);
+  return e / (1.0 + e);
+}
+
+static double softplus(double z) { return (z > 0.0 ? z : 0.0) + log1p(exp(-fabs(z))); }
+
+/* Methods: BCE loss between the target and the network output (batch size 1, mean over pixels).
+ * The noisy targets are not clipped, so the logit form softplus(z) - y z is used: it equals
+ * -[y log s + (1-y) log(1-s)] with s = sigmoid(z) for every real y. */
+double orc_loss(const double* z, const double* y, int npx, int loss_kind, double* dz) {
+  double L = 0.0;
+  for (int p = 0; p < npx; ++p) {
+    const double s = orc_sigmoid(z[p]);
+    if (loss_kind == 0) {
+      L += softplus(z[p]) - y[p] * z[p];
+      if (dz) dz[p] = (s - y[p]) / npx;
+    } else {
+      L += (s - y[p]) * (s - y[p]);
+      if (dz) dz[p] = 2.0 * (s - y[p]) * s * (1.0 - s) / npx;
+    }
+  }
+  return L / npx;
+}
+
+/* Kingma & Ba, Algorithm 1 (bias-corrected moments), as cited by the Methods for Adam.        */
+void orc_adam(double* theta, const double* g, double* m, double* v, size_t n, long t, double lr,
+              double beta1, double beta2, double eps) {
+  const double bc1 = 1.0 - pow(beta1, (double)t), bc2 = 1.0 - pow(beta2, (double)t);
+  for (size_t i = 0; i < n; ++i) {
+    m[i] = beta1 * m[i] + (1.0 - beta1) * g[i];
+    v[i] = beta2 * v[i] + (1.0 - beta2) * g[i] * g[i];
+    const double mh = m[i] / bc1, vh = v[i] / bc2;
+    theta[i] -= lr * mh / (sqrt(vh) + eps);
+  }
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Methods, validation paragraph: stop once one hundred epochs pass without improving the best
+ * validation score; the output is the average of the last one hundred validation outputs,
+ * which are exactly the outputs of the epochs after the best one.                             */
+void orc_stop_init(orc_stop_state* s) {
+  s->best = INFINITY;
+  s->since = 0;
+  s->epoch = 0;
+  s->stopped = 0;
+}
+
+int orc_stop_update(orc_stop_state* s, double score, int patience, int incl_best) {
+  int improved = 0;
+  s->epoch += 1;
+  if (score < s->best) {
+    s->best = score;
+    s->since = 0;
+    improved = 1;
+  } else {
+    s->since += 1;
+  }
+  if (s->since >= (incl_best ? patience - 1 : patience)) s->stopped = 1;
+  return improved;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+struct orc_job {
+  orc_params p;
+  int H, W;
+  double* x;
+  int ph[4], pw[4];
+  double* pin[4]; /* pair inputs */
+  double* ptg[4]; /* pair targets (aliases of the inputs, table order) */
+  double* sub[4]; /* up_e, up_o, lf_e, lf_o */
+  size_t np;
+  double *theta, *grad, *m, *v;
+  long t;
+  size_t ow[ORC_LAYERS + 1], ob[ORC_LAYERS + 1];
+  int cin[ORC_LAYERS];
+  /* last training step */
+  int lh, lw;
+  double* act[ORC_LAYERS];
+  double* delta[ORC_LAYERS];
+  double *z, *dz;
+  double last_loss;
+  /* stop rule and output averaging */
+  orc_stop_state st;
+  int capped;
+  double *S, *Vbest, *V;
+};
+
+static double* dalloc(size_t n) { return (double*)calloc(n ? n : 1, sizeof(double)); }
+
+orc_job* orc_job_new(const double* x, int H, int W, const orc_params* p) {
+  orc_job* j = (orc_job*)calloc(1, sizeof(orc_job));
+  j->p = *p;
+  j->H = H;
+  j->W = W;
+  j->x = dalloc((size_t)H * W);
+  memcpy(j->x, x, sizeof(double) * H * W);
+  j->ph[0] = j->ph[1] = H;
+  j->pw[0] = j->pw[1] = W / 2;
+  j->ph[2] = j->ph[3] = H / 2;
+  j->pw[2] = j->pw[3] = W;
+  for (int k = 0; k < 4; ++k) j->sub[k] = dalloc((size_t)j->ph[k] * j->pw[k]);
+  orc_checker(j->x, H, W, j->sub[0], j->sub[1], j->sub[2], j->sub[3]);
+  /* Methods table: (x_even -> x_odd), (x_odd -> x_even), (x'_even -> x'_odd), (x'_odd -> x'_even) */
+  j->pin[0] = j->sub[0]; j->ptg[0] = j->sub[1];
+  j->pin[1] = j->sub[1]; j->ptg[1] = j->sub[0];
+  j->pin[2] = j->sub[2]; j->ptg[2] = j->sub[3];
+  j->pin[3] = j->sub[3]; j->ptg[3] = j->sub[2];
+  j->np = orc_param_count(p->widths);
+  j->theta = dalloc(j->np);
+  j->grad = dalloc(j->np);
+  j->m = dalloc(j->np);
+  j->v = dalloc(j->np);
+  orc_init_params(p->widths, p->seed, j->theta);
+  param_offsets(p->widths, j->ow, j->ob);
+  int cin = 1;
+  size_t maxpx = 0;
+  for (int k = 0; k < 4; ++k)
+    if ((size_t)j->ph[k] * j->pw[k] > maxpx) maxpx = (size_t)j->ph[k] * j->pw[k];
+  for (int l = 0; l < ORC_LAYERS; ++l) {
+    j->cin[l] = cin;
+    j->act[l] = dalloc((size_t)p->widths[l] * maxpx);
+    j->delta[l] = dalloc((size_t)p->widths[l] * maxpx);
+    cin = p->widths[l];
+  }
+  j->z = dalloc(maxpx);
+  j->dz = dalloc(maxpx);
+  j->S = dalloc((size_t)H * W);
+  j->Vbest = dalloc((size_t)H * W);
+  j->V = dalloc((size_t)H * W);
+  orc_stop_init(&j->st);
+  return j;
+}
+
+void orc_job_set_theta(orc_job* j, const double* theta) {
+  memcpy(j->theta, theta, sizeof(double) * j->np);
+}
+
+/* Forward through the eight conv layers, keeping every post-ReLU map in act[]. */
+static void forward_layers(const int widths[ORC_LAYERS], const double* theta, const size_t* ow,
+                           const size_t* ob, const double* img, int h, int w, double** act) {
+  const double* in = img;
+  int cin = 1;
+  for (int l = 0; l < ORC_LAYERS; ++l) {
+    orc_conv3x3_fwd(in, cin, h, w, theta + ow[l], theta + ob[l], widths[l], 1, act[l]);
+    in = act[l];
+    cin = widths[l];
+  }
+}
+
+double orc_job_step(orc_job* j, int pair) {
+  const int h = j->ph[pair], w = j->pw[pair];
+  const int npx = h * w;
+  const int* wd = j->p.widths;
+  j->lh = h;
+  j->lw = w;
+  forward_layers(wd, j->theta, j->ow, j->ob, j->pin[pair], h, w, j->act);
+  const int c8 = wd[ORC_LAYERS - 1];
+  const double* w9 = j->theta + j->ow[ORC_LAYERS];
+  orc_head_fwd(j->act[ORC_LAYERS - 1], c8, npx, w9, j->theta[j->ob[ORC_LAYERS]], j->z);
+  j->last_loss = orc_loss(j->z, j->ptg[pair], npx, j->p.loss_kind, j->dz);
+
+  /* backward: head */
+  double* g = j->grad;
+  memset(g, 0, sizeof(double) * j->np);
+  {
+    const double* a8 = j->act[ORC_LAYERS - 1];
+    double* gw9 = g + j->ow[ORC_LAYERS];
+    for (int c = 0; c < c8; ++c) {
+      double s = 0.0;
+      for (int p = 0; p < npx; ++p) s += j->dz[p] * a8[(size_t)c * npx + p];
+      gw9[c] = s;
+    }
+    double s = 0.0;
+    for (int p = 0; p < npx; ++p) s += j->dz[p];
+    g[j->ob[ORC_LAYERS]] = s;
+    double* d8 = j->delta[ORC_LAYERS - 1];
+    for (int c = 0; c < c8; ++c)
+      for (int p = 0; p < npx; ++p) {
+        const size_t i = (size_t)c * npx + p;
+        d8[i] = a8[i] > 0.0 ? j->dz[p] * w9[c] : 0.0;
+      }
+  }
+  /* backward: conv layers 8..1 */
+  for (int l = ORC_LAYERS - 1; l >= 0; --l) {
+    const double* in = l > 0 ? j->act[l - 1] : j->pin[pair];
+    const int cin = j->cin[l], cout = wd[l];
+    orc_conv3x3_wgrad(j->delta[l], cout, h, w, in, cin, g + j->ow[l], g + j->ob[l]);
+    if (l > 0) {
+      double* dprev = j->delta[l - 1];
+      orc_conv3x3_dgrad(j->delta[l], cout, h, w, j->theta + j->ow[l], cin, dprev);
+      const double* aprev = j->act[l - 1];
+      const size_t n = (size_t)cin * npx;
+      for (size_t i = 0; i < n; ++i)
+        if (!(aprev[i] > 0.0)) dprev[i] = 0.0;
+    }
+  }
+  j->t += 1;
+  orc_adam(j->theta, g, j->m, j->v, j->np, j->t, j->p.lr, j->p.beta1, j->p.beta2, j->p.eps);
+  return j->last_loss;
+}
+
+void orc_net_forward(const int widths[ORC_LAYERS], const double* theta, const double* img, int h,
+                     int w, double* v, double* z) {
+  size_t ow[ORC_LAYERS + 1], ob[ORC_LAYERS + 1];
+  param_offsets(widths, ow, ob);
+  const size_t npx = (size_t)h * w;
+  double* act[ORC_LAYERS];
+  for (int l = 0; l < ORC_LAYERS; ++l) act[l] = dalloc((size_t)widths[l] * npx);
+  forward_layers(widths, theta, ow, ob, img, h, w, act);
+  double* zz = dalloc(npx);
+  orc_head_fwd(act[ORC_LAYERS - 1], widths[ORC_LAYERS - 1], (int)npx, theta + ow[ORC_LAYERS],
+               theta[ob[ORC_LAYERS]], zz);
+  for (size_t p = 0; p < npx; ++p) {
+    if (v) v[p] = orc_sigmoid(zz[p]);
+    if (z) z[p] = zz[p];
+  }
+  free(zz);
+  for (int l = 0; l < ORC_LAYERS; ++l) free(act[l]);
+}
+
+/* Methods: after each epoch, run the full noisy image through the network and take the MSE
+ * between that output and the noisy image itself. */
+double orc_job_validate(orc_job* j, double* v) {
+  const size_t n = (size_t)j->H * j->W;
+  orc_net_forward(j->p.widths, j->theta, j->x, j->H, j->W, j->V, NULL);
+  double s = 0.0;
+  for (size_t i = 0; i < n; ++i) s += (j->V[i] - j->x[i]) * (j->V[i] - j->x[i]);
+  if (v) memcpy(v, j->V, sizeof(double) * n);
+  return s / (double)n;
+}
+
+double orc_job_epoch(orc_job* j) {
+  for (int k = 0; k < 4; ++k) orc_job_step(j, k);
+  const double s = orc_job_validate(j, NULL);
+  const size_t n = (size_t)j->H * j->W;
+  const int improved = orc_stop_update(&j->st, s, j->p.patience, j->p.incl_best);
+  if (improved) {
+    memcpy(j->Vbest, j->V, sizeof(double) * n);
+    for (size_t i = 0; i < n; ++i) j->S[i] = j->p.incl_best ? j->V[i] : 0.0;
+  } else {
+    for (size_t i = 0; i < n; ++i) j->S[i] += j->V[i];
+  }
+  return s;
+}
+
+void orc_job_run(orc_job* j, double* out) {
+  const size_t n = (size_t)j->H * j->W;
+  if (j->p.fixed_steps >= 0) {
+    for (int k = 0; k < j->p.fixed_steps; ++k) orc_job_step(j, k % 4);
+    orc_job_validate(j, out);
+    return;
+  }
+  while (!j->st.stopped) {
+    orc_job_epoch(j);
+    if (!j->st.stopped && j->p.max_epochs > 0 && j->st.epoch >= j->p.max_epochs) {
+      j->capped = 1;
+      break;
+    }
+  }
+  if (j->st.stopped) {
+    for (size_t i = 0; i < n; ++i) out[i] = j->S[i] / j->p.patience;
+  } else {
+    /* cap reached before the rule fired: average what the window holds so far */
+    const int cnt = j->st.since + (j->p.incl_best ? 1 : 0);
+    for (size_t i = 0; i < n; ++i) out[i] = cnt > 0 ? j->S[i] / cnt : j->Vbest[i];
+  }
+}
+
+size_t orc_job_get(const orc_job* j, int what, int layer, double* out) {
+  size_t n = 0;
+  const double* src = NULL;
+  const size_t lpx = (size_t)j->lh * j->lw;
+  switch (what) {
+    case ORC_THETA: src = j->theta; n = j->np; break;
+    case ORC_GRAD: src = j->grad; n = j->np; break;
+    case ORC_ADAM_M: src = j->m; n = j->np; break;
+    case ORC_ADAM_V: src = j->v; n = j->np; break;
+    case ORC_ACT:
+      if (layer < 1 || layer > ORC_LAYERS) return 0;
+      src = j->act[layer - 1]; n = (size_t)j->p.widths[layer - 1] * lpx; break;
+    case ORC_DELTA:
+      if (layer < 1 || layer > ORC_LAYERS) return 0;
+      src = j->delta[layer - 1]; n = (size_t)j->p.widths[layer - 1] * lpx; break;
+    case ORC_Z: src = j->z; n = lpx; break;
+    case ORC_DZ: src = j->dz; n = lpx; break;
+    case ORC_PAIR_IN:
+      if (layer < 0 || layer > 3) return 0;
+      src = j->pin[layer]; n = (size_t)j->ph[layer] * j->pw[layer]; break;
+    case ORC_PAIR_TGT:
+      if (layer < 0 || layer > 3) return 0;
+      src = j->ptg[layer]; n = (size_t)j->ph[layer] * j->pw[layer]; break;
+    case ORC_SUM: src = j->S; n = (size_t)j->H * j->W; break;
+    case ORC_VBEST: src = j->Vbest; n = (size_t)j->H * j->W; break;
+    default: return 0;
+  }
+  if (out) memcpy(out, src, sizeof(double) * n);
+  return n;
+}
+
+void orc_job_info(const orc_job* j, long* t, int* epoch, int* since, int* stopped, int* capped,
+                  double* best, double* last_loss, int dims[4]) {
+  if (t) *t = j->t;
+  if (epoch) *epoch = j->st.epoch;
+  if (since) *since = j->st.since;
+  if (stopped) *stopped = j->st.stopped;
+  if (capped) *capped = j->capped;
+  if (best) *best = j->st.best;
+  if (last_loss) *last_loss = j->last_loss;
+  if (dims) {
+    dims[0] = j->ph[0]; dims[1] = j->pw[0]; dims[2] = j->ph[2]; dims[3] = j->pw[2];
+  }
+}
+
+void orc_job_free(orc_job* j) {
+  if (!j) return;
+  free(j->x);
+  for (int k = 0; k < 4; ++k) free(j->sub[k]);
+  free(j->theta); free(j->grad); free(j->m); free(j->v);
+  for (int l = 0; l < ORC_LAYERS; ++l) { free(j->act[l]); free(j->delta[l]); }
+  free(j->z); free(j->dz); free(j->S); free(j->Vbest); free(j->V);
+  free(j);
+}
