@@ -1,0 +1,226 @@
+/*
+ * n2f.h -- C ABI of the GB300 (sm_103a) Noise2Fast library.
+ *
+ * Noise2Fast (Lequyer, Philip, Sharma & Pelletier, arXiv 2108.10209) denoises ONE noisy image
+ * x in R^{m x n} into f_theta(x) ~ s of the same size (Theoretical Background, Eq. 1-2) using
+ * only that image: checkerboard downsampling into four sub-images (Eq. 6-7 and the Methods'
+ * primed "left" equations), a small CNN (Methods, first paragraph: 3x3 conv + ReLU layers,
+ * then 1x1 conv + sigmoid) trained with BCE and Adam (lr 0.001, batch size 1) on the four
+ * input/target pairs of the Methods table, full-image validation after every epoch, and the
+ * stopping rule: stop once 100 epochs pass without a better validation MSE and output the
+ * average of the last 100 validation outputs (Methods, validation paragraph). The method is
+ * blind: no noise parameter is passed.
+ *
+ * Conventions
+ *   - Every entry point returns N2F_OK (0) or a negative N2F_E* code; n2f_strerror() gives
+ *     text, including the CUDA error message of the last N2F_EDEVICE on this thread.
+ *   - Images are row-major float32, H rows by W columns. "Host" pointers are ordinary CPU
+ *     memory; "device" pointers are CUDA global memory on the context's device.
+ *   - Nothing here takes or returns a PyTorch type. A stream is passed as a cudaStream_t
+ *     cast to void* (NULL = the legacy default stream).
+ *   - The library owns every device buffer it allocates (through the allocator in
+ *     n2f_config, cudaMalloc when none is given) and frees it when a job is collected,
+ *     cancelled or its context is destroyed.
+ *   - Thread safety: n2f_submit / n2f_poll / n2f_wait / n2f_result / n2f_cancel may be called
+ *     from any thread on the same context. Trainer and op-level calls are not thread-safe
+ *     per object.
+ */
+#ifndef N2F_H
+#define N2F_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------------------------ */
+#define N2F_OK 0
+#define N2F_EINVAL (-1)     /* NULL pointer, H or W < 2, non-finite pixel, bad struct_size/enum */
+#define N2F_ETOOBIG (-2)    /* the job can never fit the context's HBM budget */
+#define N2F_EAGAIN (-3)     /* result not ready yet */
+#define N2F_ENOENT (-4)     /* unknown or already collected job */
+#define N2F_ETIMEDOUT (-5)  /* a wait ran out of time */
+#define N2F_ENONFINITE (-6) /* training diverged: a non-finite validation score */
+#define N2F_EDEVICE (-7)    /* CUDA error (message kept for n2f_strerror) */
+#define N2F_ENOMEM (-8)     /* an allocation failed */
+#define N2F_ECANCELED (-9)  /* the job was cancelled */
+#define N2F_ENOTSUP (-10)   /* a combination this build does not provide */
+
+/* ---- enumerations ----------------------------------------------------------------------- */
+enum n2f_precision {
+  N2F_FP32 = 0, /* activations, weights and GEMM operands in float32 (plain form) */
+  N2F_BF16 = 1  /* GEMM operands and stored activations in bfloat16, FP32 accumulation,
+                   FP32 master weights, Adam and loss; FP64 validation-MSE reduction */
+};
+enum n2f_loss { N2F_LOSS_BCE = 0, N2F_LOSS_MSE = 1 };
+enum n2f_widths {
+  N2F_WIDTHS_PLIT = 0, /* 32,32,64,64,128,128,256,256: the Methods text read literally */
+  N2F_WIDTHS_W64 = 1   /* eight 64-channel layers */
+};
+enum n2f_engine {
+  N2F_ENGINE_AUTO = 0, /* tensor-core kernels where built for the precision, else SIMT */
+  N2F_ENGINE_SIMT = 1, /* CUDA-core implicit-GEMM kernels (the FP32 reference kernels) */
+  N2F_ENGINE_TC = 2    /* tcgen05/TMEM implicit-GEMM kernels for the C_in >= 32 layers */
+};
+enum n2f_job_state {
+  N2F_QUEUED = 0, N2F_RUNNING = 1, N2F_DONE = 2, N2F_FAILED = 3, N2F_CANCELED = 4
+};
+
+/* ---- configuration ---------------------------------------------------------------------- */
+typedef void* (*n2f_alloc_fn)(size_t bytes, void* user); /* device memory; NULL on failure */
+typedef void (*n2f_free_fn)(void* ptr, size_t bytes, void* user);
+
+typedef struct {
+  uint32_t struct_size;      /* sizeof(n2f_config) */
+  int device;                /* CUDA device ordinal */
+  uint64_t hbm_budget_bytes; /* admission budget for resident job state; 0 = 150 GB */
+  uint32_t max_slots;        /* jobs resident at once; 0 = 64 */
+  uint32_t lookahead;        /* epochs enqueued ahead of the stop check; 0 = 2 */
+  n2f_alloc_fn alloc;        /* optional device allocator (e.g. a framework's caching one) */
+  n2f_free_fn free;
+  void* alloc_user;
+} n2f_config;
+
+/* Per-image parameters. Defaults (n2f_params_default) follow the Methods section; the Adam
+ * moments and epsilon are Kingma & Ba's defaults (the paper cites Adam without them). */
+typedef struct {
+  uint32_t struct_size; /* sizeof(n2f_params) */
+  float lr;             /* 1e-3 */
+  float beta1, beta2;   /* 0.9, 0.999 */
+  float eps;            /* 1e-8 */
+  uint32_t patience;    /* 100 */
+  uint32_t max_epochs;  /* safety cap, 0 = none */
+  int32_t fixed_steps;  /* -1: stopping rule; k >= 0: k steps (pairs cycled), one validation */
+  uint64_t seed;        /* SplitMix64 seed of the initial weights */
+  int32_t precision;    /* enum n2f_precision */
+  int32_t loss;         /* enum n2f_loss */
+  int32_t widths;       /* enum n2f_widths */
+  int32_t incl_best;    /* 0: the window is the 100 epochs after the best (the reading used) */
+  int32_t engine;       /* enum n2f_engine */
+} n2f_params;
+
+typedef struct {
+  uint32_t struct_size;  /* sizeof(n2f_status) */
+  int32_t state;         /* enum n2f_job_state */
+  int32_t error;         /* N2F_E* when FAILED */
+  uint32_t epoch;        /* epochs completed */
+  uint32_t steps;        /* Adam steps taken */
+  uint32_t since;        /* epochs since the best */
+  uint32_t stopped;      /* 1: the stopping rule fired, 2: max_epochs reached */
+  uint32_t H, W;
+  double best_mse;       /* best validation MSE */
+  double last_loss;      /* training loss of the last step */
+  double device_ms;      /* GPU time from admission to the result being ready */
+  double latency_ms;     /* host time from n2f_submit to DONE */
+  double t_start_ms;     /* device timestamps of admission and completion, relative to the */
+  double t_done_ms;      /* context's creation (CUDA events), for makespan measurements    */
+} n2f_status;
+
+typedef struct n2f_ctx n2f_ctx;
+typedef uint64_t n2f_job;
+
+void n2f_config_default(n2f_config* cfg);
+void n2f_params_default(n2f_params* p);
+const char* n2f_strerror(int code);
+
+/* ---- job API (the serving boundary) ----------------------------------------------------- */
+/* Creates a context on cfg->device with a scheduler thread. cfg may be NULL (defaults). */
+int n2f_create(n2f_ctx** out, const n2f_config* cfg);
+/* Stops the scheduler, cancels unfinished jobs and frees everything. */
+void n2f_destroy(n2f_ctx* ctx);
+/* Queues one H x W image (host memory, copied before return). p may be NULL (defaults).
+ * Errors: EINVAL (NULL, H or W < 2, non-finite pixel, bad params), ETOOBIG. */
+int n2f_submit(n2f_ctx* ctx, const float* image, int H, int W, const n2f_params* p, n2f_job* out);
+/* Same, for an image already in device memory (copied on the device before the job runs;
+ * the caller must keep it valid until n2f_poll reports RUNNING or later). */
+int n2f_submit_device(n2f_ctx* ctx, const float* dimage, int H, int W, const n2f_params* p,
+                      n2f_job* out);
+/* Same, for a 16-bit microscope image, normalised on the device as value / 65535. */
+int n2f_submit_u16(n2f_ctx* ctx, const uint16_t* image, int H, int W, const n2f_params* p,
+                   n2f_job* out);
+/* Status snapshot; never blocks. */
+int n2f_poll(n2f_ctx* ctx, n2f_job job, n2f_status* st);
+/* Blocks until the job is DONE/FAILED/CANCELED or timeout_ms passes (< 0: no limit). */
+int n2f_wait(n2f_ctx* ctx, n2f_job job, int timeout_ms);
+/* Copies the H*W denoised floats to host memory and releases the job.
+ * EAGAIN while queued or running. A FAILED or CANCELED job is released too and its error
+ * code (ENONFINITE, EDEVICE, ECANCELED, ...) is returned instead of an image. */
+int n2f_result(n2f_ctx* ctx, n2f_job job, float* out, size_t out_elems);
+/* Same, into device memory (the copy is complete when the call returns). */
+int n2f_result_device(n2f_ctx* ctx, n2f_job job, float* dout, size_t out_elems);
+/* Cancels a queued or running job; its resources are freed by the scheduler. */
+int n2f_cancel(n2f_ctx* ctx, n2f_job job);
+
+typedef struct {
+  uint32_t struct_size;
+  uint64_t kernel_launches; /* kernels this context has launched */
+  uint64_t bytes_resident;  /* device bytes held by admitted jobs */
+  uint32_t jobs_queued, jobs_running, jobs_done;
+} n2f_ctx_stats;
+int n2f_stats(n2f_ctx* ctx, n2f_ctx_stats* st);
+
+/* ---- trainer API: one job's device state, stepped by the caller (parity tests) ----------
+ * A trainer runs on the caller's stream; calls enqueue work and return. Exports synchronise
+ * the stream and return values converted to float64 in the layouts of the CPU oracle:
+ * NCHW maps, weights [C_out][C_in][3][3], the flat parameter order of n2f_param_count. */
+typedef struct n2f_trainer n2f_trainer;
+int n2f_trainer_create(n2f_trainer** out, const float* image, int H, int W, const n2f_params* p,
+                       void* stream);          /* image: host memory */
+void n2f_trainer_destroy(n2f_trainer* tr);
+int n2f_trainer_step(n2f_trainer* tr, int pair); /* one Adam step on pair 0..3 (Methods table) */
+int n2f_trainer_validate(n2f_trainer* tr);       /* full-image forward + MSE + stop rule */
+int n2f_trainer_epoch(n2f_trainer* tr);          /* four steps + validate */
+int n2f_trainer_run(n2f_trainer* tr, int max_epochs); /* epochs until the rule fires or cap */
+int n2f_trainer_finish(n2f_trainer* tr);         /* computes the output image on the device */
+int n2f_trainer_set_theta(n2f_trainer* tr, const double* theta, size_t n);
+enum n2f_export {
+  N2F_X_THETA = 0, N2F_X_GRAD = 1, N2F_X_ADAM_M = 2, N2F_X_ADAM_V = 3, /* flat */
+  N2F_X_ACT = 4,    /* post-ReLU map of layer 1..8 from the last step, C*h*w */
+  N2F_X_DELTA = 5,  /* dL/d(pre-activation) of layer 1..8 from the last step, C*h*w */
+  N2F_X_DZ = 7,     /* dL/dz of the last step, h*w */
+  N2F_X_PAIR = 8,   /* sub-image 0..3 = up_e, up_o, lf_e, lf_o */
+  N2F_X_VAL = 9,    /* last validation output, H*W */
+  N2F_X_SUM = 10,   /* running output sum, H*W */
+  N2F_X_OUT = 11    /* output image (after n2f_trainer_finish), H*W */
+};
+/* Returns the number of values through *n_out; out may be NULL to query the size. */
+int n2f_trainer_export(n2f_trainer* tr, int what, int index, double* out, size_t cap,
+                       size_t* n_out);
+int n2f_trainer_status(n2f_trainer* tr, n2f_status* st);
+uint64_t n2f_trainer_launches(const n2f_trainer* tr);
+
+/* Number of parameters of the network (n2f_widths). */
+size_t n2f_param_count(int widths);
+
+/* ---- op-level entry points (device pointers, caller's stream; parity of single kernels) --
+ * "CG layout": channel-grouped maps, act[g][y][x][k] with g = c / G, k = c % G and
+ * G = 4 (float32) or 8 (bfloat16), i.e. one 16-byte group per pixel and group. */
+
+/* Checkerboard gather (Eq. 6-7 and the Methods' "left" equations; odd images read as the
+ * order-preserving compaction of the pixels with i+j odd). x: H*W floats; up_e/up_o:
+ * H*(W/2); lf_e/lf_o: (H/2)*W. Exact copies. */
+int n2f_checker_gather(const float* x, int H, int W, float* up_e, float* up_o, float* lf_e,
+                       float* lf_o, void* stream);
+/* NCHW float32 <-> CG layout of the given precision (C a multiple of G). */
+int n2f_pack_cg(const float* nchw, int C, int H, int W, int precision, void* cg, void* stream);
+int n2f_unpack_cg(const void* cg, int C, int H, int W, int precision, float* nchw, void* stream);
+/* One 3x3 convolution layer with zero "same" padding (Methods; Fig. 2a):
+ *   forward (mode 0):  out = ReLU(conv(in, w) + b)
+ *   dgrad   (mode 1):  out = conv^T(in, w) * [mask > 0]   (in = dL/d pre-activation of this
+ *                      layer, mask = the layer's input activation, out has C_in channels)
+ * in/out/mask in CG layout of `precision`; w: float32 [C_out][C_in][3][3] (device), b: C_out.
+ * C_in, C_out in {32, 64, 128, 256} for the tensor-core engine; multiples of G for SIMT. */
+int n2f_conv3x3(int mode, int engine, int precision, const void* in, int cin, int cout, int H,
+                int W, const float* w, const float* b, const void* mask, void* out,
+                void* stream);
+/* Weight/bias gradient of one 3x3 layer: dw[C_out][C_in][3][3] and db[C_out] (float32,
+ * overwritten) from dout (CG, C_out channels) and in (CG, C_in channels). */
+int n2f_conv3x3_wgrad(int engine, int precision, const void* dout, const void* in, int cin,
+                      int cout, int H, int W, float* dw, float* db, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* N2F_H */

@@ -1,0 +1,855 @@
+// C ABI of the library: defaults, the trainer API, op-level entry points and the job
+// scheduler (admission by HBM budget, epochs enqueued ahead of a device-side stop flag,
+// several jobs resident at once on their own streams).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "trainer.h"
+
+using namespace n2f;
+
+#define CKR(expr)                                            \
+  do {                                                       \
+    cudaError_t _e = (expr);                                 \
+    if (_e != cudaSuccess) return set_cuda_error(_e, #expr); \
+  } while (0)
+
+extern "C" {
+
+void n2f_config_default(n2f_config* c) {
+  memset(c, 0, sizeof(*c));
+  c->struct_size = sizeof(n2f_config);
+  c->device = 0;
+  c->hbm_budget_bytes = 150ull << 30;
+  c->max_slots = 64;
+  c->lookahead = 2;
+}
+
+void n2f_params_default(n2f_params* p) {
+  memset(p, 0, sizeof(*p));
+  p->struct_size = sizeof(n2f_params);
+  p->lr = 1e-3f;
+  p->beta1 = 0.9f;
+  p->beta2 = 0.999f;
+  p->eps = 1e-8f;
+  p->patience = 100;
+  p->max_epochs = 0;
+  p->fixed_steps = -1;
+  p->seed = 0;
+  p->precision = N2F_FP32;
+  p->loss = N2F_LOSS_BCE;
+  p->widths = N2F_WIDTHS_PLIT;
+  p->incl_best = 0;
+  p->engine = N2F_ENGINE_AUTO;
+}
+
+const char* n2f_strerror(int code) {
+  switch (code) {
+    case N2F_OK: return "ok";
+    case N2F_EINVAL: return "invalid argument";
+    case N2F_ETOOBIG: return "job can never fit the HBM budget";
+    case N2F_EAGAIN: return "result not ready";
+    case N2F_ENOENT: return "unknown or collected job";
+    case N2F_ETIMEDOUT: return "wait timed out";
+    case N2F_ENONFINITE: return "training diverged (non-finite validation score)";
+    case N2F_EDEVICE: return tl_error.empty() ? "CUDA error" : tl_error.c_str();
+    case N2F_ENOMEM: return tl_error.empty() ? "out of memory" : tl_error.c_str();
+    case N2F_ECANCELED: return "job cancelled";
+    case N2F_ENOTSUP: return "not supported by this build";
+    default: return "unknown error";
+  }
+}
+
+size_t n2f_param_count(int widths) {
+  NetShape s;
+  s.init(widths);
+  return s.count;
+}
+
+}  // extern "C"
+
+static int check_params(const n2f_params* p) {
+  if (!p || p->struct_size != sizeof(n2f_params)) return N2F_EINVAL;
+  if (p->precision != N2F_FP32 && p->precision != N2F_BF16) return N2F_EINVAL;
+  if (p->loss != N2F_LOSS_BCE && p->loss != N2F_LOSS_MSE) return N2F_EINVAL;
+  if (p->widths != N2F_WIDTHS_PLIT && p->widths != N2F_WIDTHS_W64) return N2F_EINVAL;
+  if (p->engine < N2F_ENGINE_AUTO || p->engine > N2F_ENGINE_TC) return N2F_EINVAL;
+  if (!(p->lr > 0.f) || !(p->beta1 >= 0.f && p->beta1 < 1.f) ||
+      !(p->beta2 >= 0.f && p->beta2 < 1.f) || !(p->eps > 0.f))
+    return N2F_EINVAL;
+  if (p->fixed_steps < 0 && p->patience < 1) return N2F_EINVAL;
+  if (p->incl_best && p->patience < 2) return N2F_EINVAL;
+  return N2F_OK;
+}
+
+static int check_image(int H, int W) {
+  if (H < 2 || W < 2) return N2F_EINVAL;
+  if ((size_t)H * W > ((size_t)1 << 31)) return N2F_EINVAL;
+  return N2F_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Trainer API
+struct n2f_trainer {
+  Trainer t;
+  bool own_stream;
+};
+
+extern "C" int n2f_trainer_create(n2f_trainer** out, const float* image, int H, int W,
+                                  const n2f_params* p, void* stream) {
+  if (!out || !image) return N2F_EINVAL;
+  n2f_params def;
+  n2f_params_default(&def);
+  if (!p) p = &def;
+  int rc = check_params(p);
+  if (rc) return rc;
+  if ((rc = check_image(H, W))) return rc;
+  for (size_t i = 0; i < (size_t)H * W; ++i)
+    if (!isfinite(image[i])) return N2F_EINVAL;
+  n2f_trainer* tr = new n2f_trainer();
+  tr->own_stream = false;
+  if ((rc = trainer_configure(&tr->t, H, W, p, 1))) {
+    delete tr;
+    return rc;
+  }
+  Allocator al;
+  if ((rc = trainer_init(&tr->t, al, (cudaStream_t)stream, 0))) {
+    delete tr;
+    return rc;
+  }
+  cudaError_t e = cudaMemcpyAsync(tr->t.x, image, sizeof(float) * H * W, cudaMemcpyHostToDevice,
+                                  tr->t.st);
+  if (e != cudaSuccess) {
+    trainer_release(&tr->t);
+    delete tr;
+    return set_cuda_error(e, "image upload");
+  }
+  if ((rc = trainer_start(&tr->t, 0))) {
+    trainer_release(&tr->t);
+    delete tr;
+    return rc;
+  }
+  *out = tr;
+  return N2F_OK;
+}
+
+extern "C" void n2f_trainer_destroy(n2f_trainer* tr) {
+  if (!tr) return;
+  cudaStreamSynchronize(tr->t.st);
+  trainer_release(&tr->t);
+  delete tr;
+}
+
+extern "C" int n2f_trainer_step(n2f_trainer* tr, int pair) {
+  if (!tr || pair < 0 || pair > 3) return N2F_EINVAL;
+  return trainer_step(&tr->t, pair);
+}
+
+extern "C" int n2f_trainer_validate(n2f_trainer* tr) {
+  if (!tr) return N2F_EINVAL;
+  return trainer_validate(&tr->t);
+}
+
+extern "C" int n2f_trainer_epoch(n2f_trainer* tr) {
+  if (!tr) return N2F_EINVAL;
+  return trainer_epoch(&tr->t);
+}
+
+extern "C" int n2f_trainer_run(n2f_trainer* tr, int max_epochs) {
+  if (!tr) return N2F_EINVAL;
+  Trainer* t = &tr->t;
+  if (t->fixed_mode) {
+    for (int k = 0; k < t->prm.fixed_steps; ++k) {
+      int rc = trainer_step(t, k % 4);
+      if (rc) return rc;
+    }
+    int rc = trainer_validate(t);
+    if (rc) return rc;
+    return trainer_finish(t);
+  }
+  DevState s;
+  for (int e = 0; max_epochs <= 0 || e < max_epochs; e += 4) {
+    for (int k = 0; k < 4; ++k) {
+      int rc = trainer_epoch(t);
+      if (rc) return rc;
+    }
+    int rc = trainer_read_state(t, &s);
+    if (rc) return rc;
+    if (s.stopped) break;
+  }
+  return trainer_finish(t);
+}
+
+extern "C" int n2f_trainer_finish(n2f_trainer* tr) {
+  if (!tr) return N2F_EINVAL;
+  return trainer_finish(&tr->t);
+}
+
+extern "C" int n2f_trainer_set_theta(n2f_trainer* tr, const double* theta, size_t n) {
+  if (!tr || !theta || n != tr->t.net.count) return N2F_EINVAL;
+  std::vector<float> f(n);
+  for (size_t i = 0; i < n; ++i) f[i] = (float)theta[i];
+  CKR(cudaMemcpyAsync(tr->t.theta, f.data(), n * sizeof(float), cudaMemcpyHostToDevice,
+                      tr->t.st));
+  CKR(cudaStreamSynchronize(tr->t.st));
+  return trainer_repack(&tr->t);
+}
+
+// Copies a device float array, or a CG map converted to NCHW, into host doubles.
+static int export_floats(cudaStream_t st, const float* d, size_t n, double* out) {
+  std::vector<float> h(n);
+  CKR(cudaMemcpyAsync(h.data(), d, n * sizeof(float), cudaMemcpyDeviceToHost, st));
+  CKR(cudaStreamSynchronize(st));
+  for (size_t i = 0; i < n; ++i) out[i] = h[i];
+  return N2F_OK;
+}
+
+static int export_cg(Trainer* t, const void* cg, int C, int h, int w, double* out) {
+  const size_t n = (size_t)C * h * w;
+  float* tmp = nullptr;
+  CKR(cudaMallocAsync((void**)&tmp, n * sizeof(float), t->st));
+  cudaError_t e = launch_unpack_cg(cg, C, h, w, t->bf16, tmp, t->st);
+  int rc = e == cudaSuccess ? export_floats(t->st, tmp, n, out) : set_cuda_error(e, "unpack");
+  cudaFreeAsync(tmp, t->st);
+  cudaStreamSynchronize(t->st);
+  return rc;
+}
+
+extern "C" int n2f_trainer_export(n2f_trainer* tr, int what, int index, double* out, size_t cap,
+                                  size_t* n_out) {
+  if (!tr) return N2F_EINVAL;
+  Trainer* t = &tr->t;
+  const int h = t->ph[t->last_pair], w = t->pw[t->last_pair];
+  size_t n = 0;
+  switch (what) {
+    case N2F_X_THETA: case N2F_X_GRAD: case N2F_X_ADAM_M: case N2F_X_ADAM_V: n = t->net.count; break;
+    case N2F_X_ACT: case N2F_X_DELTA:
+      if (index < 1 || index > kLayers) return N2F_EINVAL;
+      n = (size_t)t->net.widths[index - 1] * h * w;
+      break;
+    case N2F_X_DZ: n = (size_t)h * w; break;
+    case N2F_X_PAIR:
+      if (index < 0 || index > 3) return N2F_EINVAL;
+      n = (size_t)t->ph[index] * t->pw[index];
+      break;
+    case N2F_X_VAL: case N2F_X_SUM: case N2F_X_OUT: n = t->N; break;
+    default: return N2F_EINVAL;
+  }
+  if (n_out) *n_out = n;
+  if (!out) return N2F_OK;
+  if (cap < n) return N2F_EINVAL;
+  switch (what) {
+    case N2F_X_THETA: return export_floats(t->st, t->theta, n, out);
+    case N2F_X_GRAD: return export_floats(t->st, t->grad, n, out);
+    case N2F_X_ADAM_M: return export_floats(t->st, t->m, n, out);
+    case N2F_X_ADAM_V: return export_floats(t->st, t->v, n, out);
+    case N2F_X_ACT: return export_cg(t, t->act[index - 1], t->net.widths[index - 1], h, w, out);
+    case N2F_X_DELTA: return export_cg(t, t->dkeep[index - 1], t->net.widths[index - 1], h, w, out);
+    case N2F_X_DZ: return export_floats(t->st, t->dz, n, out);
+    case N2F_X_PAIR: return export_floats(t->st, t->sub[index], n, out);
+    case N2F_X_VAL: return export_floats(t->st, t->V, n, out);
+    case N2F_X_SUM: return export_floats(t->st, t->S, n, out);
+    case N2F_X_OUT: return export_floats(t->st, t->out, n, out);
+  }
+  return N2F_EINVAL;
+}
+
+extern "C" int n2f_trainer_status(n2f_trainer* tr, n2f_status* st) {
+  if (!tr || !st || st->struct_size != sizeof(n2f_status)) return N2F_EINVAL;
+  DevState s;
+  int rc = trainer_read_state(&tr->t, &s);
+  if (rc) return rc;
+  fill_status(&tr->t, s, st);
+  st->state = s.stopped ? N2F_DONE : N2F_RUNNING;
+  st->error = s.stopped == 3 ? N2F_ENONFINITE : N2F_OK;
+  if (s.stopped == 3) st->state = N2F_FAILED;
+  return N2F_OK;
+}
+
+extern "C" uint64_t n2f_trainer_launches(const n2f_trainer* tr) { return tr ? tr->t.launches : 0; }
+
+// ------------------------------------------------------------------------------------------
+// Op-level entry points
+extern "C" int n2f_checker_gather(const float* x, int H, int W, float* up_e, float* up_o,
+                                  float* lf_e, float* lf_o, void* stream) {
+  if (!x || !up_e || !up_o || !lf_e || !lf_o || check_image(H, W)) return N2F_EINVAL;
+  CKR(launch_gather(x, H, W, up_e, up_o, lf_e, lf_o, (cudaStream_t)stream));
+  return N2F_OK;
+}
+
+extern "C" int n2f_pack_cg(const float* nchw, int C, int H, int W, int precision, void* cg,
+                           void* stream) {
+  const int G = precision == N2F_BF16 ? 8 : 4;
+  if (!nchw || !cg || C < G || C % G || H < 1 || W < 1) return N2F_EINVAL;
+  CKR(launch_pack_cg(nchw, C, H, W, precision == N2F_BF16, cg, (cudaStream_t)stream));
+  return N2F_OK;
+}
+
+extern "C" int n2f_unpack_cg(const void* cg, int C, int H, int W, int precision, float* nchw,
+                             void* stream) {
+  const int G = precision == N2F_BF16 ? 8 : 4;
+  if (!nchw || !cg || C < G || C % G || H < 1 || W < 1) return N2F_EINVAL;
+  CKR(launch_unpack_cg(cg, C, H, W, precision == N2F_BF16, nchw, (cudaStream_t)stream));
+  return N2F_OK;
+}
+
+static int resolve_engine(int engine, int cin, int cout) {
+  if (engine == N2F_ENGINE_SIMT) return N2F_ENGINE_SIMT;
+  const bool tc = tc_supported(cin, cout);
+  if (engine == N2F_ENGINE_TC) return tc ? N2F_ENGINE_TC : -1;
+  return tc ? N2F_ENGINE_TC : N2F_ENGINE_SIMT;
+}
+
+extern "C" int n2f_conv3x3(int mode, int engine, int precision, const void* in, int cin, int cout,
+                           int H, int W, const float* w, const float* b, const void* mask,
+                           void* out, void* stream) {
+  if (!in || !out || !w || (mode == 0 && !b) || (mode == 1 && !mask) || H < 1 || W < 1 ||
+      cin % 8 || cout % 8 || cin < 8 || cout < 8 || (mode != 0 && mode != 1))
+    return N2F_EINVAL;
+  const int bf16 = precision == N2F_BF16;
+  const int eng = resolve_engine(engine, cin, cout);
+  if (eng < 0) return N2F_ENOTSUP;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t nw = (size_t)cin * cout * 9;
+  const size_t es = bf16 ? 2 : 4;
+  char* buf = nullptr;
+  const size_t bytes = 2 * nw * sizeof(float) + 4 * nw * es + 4096;
+  CKR(cudaMallocAsync((void**)&buf, bytes, st));
+  float* fwd = (float*)buf;
+  float* dgr = fwd + nw;
+  char* tc0 = (char*)(dgr + nw);
+  void *tcf = nullptr, *tcd = nullptr;
+  float *tcf_lo = nullptr, *tcd_lo = nullptr;
+  if (eng == N2F_ENGINE_TC) {
+    tcf = tc0;
+    tcd = tc0 + nw * es;
+    if (!bf16) {
+      tcf_lo = (float*)(tc0 + 2 * nw * es);
+      tcd_lo = (float*)(tc0 + 3 * nw * es);
+    }
+  }
+  cudaError_t e = launch_pack_layer(w, cin, cout, fwd, dgr, tcf, tcd, tcf_lo, tcd_lo, bf16, st);
+  if (e == cudaSuccess) {
+    if (mode == 0) {
+      e = eng == N2F_ENGINE_TC
+              ? launch_conv_tc(0, bf16, in, cin, cout, H, W, tcf, b, nullptr, out, nullptr, st)
+              : launch_conv_simt(0, bf16, in, cin, cout, H, W, fwd, b, nullptr, out, nullptr, st);
+    } else {
+      // dgrad: `in` has C_out channels, `out` and `mask` have C_in
+      e = eng == N2F_ENGINE_TC
+              ? launch_conv_tc(1, bf16, in, cout, cin, H, W, tcd, nullptr, mask, out, nullptr, st)
+              : launch_conv_simt(1, bf16, in, cout, cin, H, W, dgr, nullptr, mask, out, nullptr,
+                                 st);
+    }
+  }
+  cudaFreeAsync(buf, st);
+  if (e != cudaSuccess) return set_cuda_error(e, "n2f_conv3x3");
+  return N2F_OK;
+}
+
+extern "C" int n2f_conv3x3_wgrad(int engine, int precision, const void* dout, const void* in,
+                                 int cin, int cout, int H, int W, float* dw, float* db,
+                                 void* stream) {
+  if (!dout || !in || !dw || !db || H < 1 || W < 1 || cin % 8 || cout % 8 || cin < 8 || cout < 8)
+    return N2F_EINVAL;
+  const int bf16 = precision == N2F_BF16;
+  const int eng = resolve_engine(engine, cin, cout);
+  if (eng < 0) return N2F_ENOTSUP;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t cap = (size_t)8 << 20;
+  float* part = nullptr;
+  CKR(cudaMallocAsync((void**)&part, cap * sizeof(float), st));
+  cudaError_t e =
+      eng == N2F_ENGINE_TC
+          ? launch_wgrad_tc(bf16, dout, in, cin, cout, H, W, part, cap, dw, db, nullptr, st)
+          : launch_wgrad_simt(bf16, dout, in, cin, cout, H, W, part, cap, dw, db, nullptr, st);
+  cudaFreeAsync(part, st);
+  if (e != cudaSuccess) return set_cuda_error(e, "n2f_conv3x3_wgrad");
+  return N2F_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Job scheduler
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Job {
+  n2f_job id = 0;
+  int H = 0, W = 0;
+  n2f_params prm;
+  int src_kind = 0;  // 0 host f32, 1 device f32, 2 host u16
+  float* pin_in = nullptr;
+  uint16_t* pin_u16 = nullptr;
+  const float* dev_in = nullptr;
+  float* pin_out = nullptr;
+  std::atomic<int> state{N2F_QUEUED};
+  int error = 0;
+  bool cancel = false;
+  Trainer tr;
+  size_t bytes = 0;
+  cudaStream_t st = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_done = nullptr;
+  // ring of host mirrors of the device state, one per epoch in flight
+  DevState* hst = nullptr;
+  cudaEvent_t ev_ep[8] = {};
+  int ring = 0;
+  uint64_t ep_enq = 0, ep_seen = 0;
+  bool finishing = false, result_enq = false;
+  DevState last;
+  Clock::time_point t_submit, t_done;
+  double device_ms = 0, t0_ms = 0, t1_ms = 0;
+};
+
+}  // namespace
+
+struct n2f_ctx {
+  n2f_config cfg;
+  Allocator al;
+  std::thread worker;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Job*> queue;
+  std::vector<Job*> active;
+  std::unordered_map<n2f_job, Job*> jobs;
+  bool stop = false;
+  uint64_t next_id = 1;
+  uint64_t launches = 0;
+  size_t bytes_resident = 0;
+  uint32_t n_done = 0;
+  cudaEvent_t ev_ref = nullptr;
+};
+
+static void free_job_host(Job* j) {
+  if (j->pin_in) cudaFreeHost(j->pin_in);
+  if (j->pin_u16) cudaFreeHost(j->pin_u16);
+  if (j->pin_out) cudaFreeHost(j->pin_out);
+  if (j->hst) cudaFreeHost(j->hst);
+  j->pin_in = nullptr;
+  j->pin_u16 = nullptr;
+  j->pin_out = nullptr;
+  j->hst = nullptr;
+}
+
+static void release_device(n2f_ctx* c, Job* j) {
+  if (j->st) cudaStreamSynchronize(j->st);
+  trainer_release(&j->tr);
+  for (int k = 0; k < 8; ++k)
+    if (j->ev_ep[k]) cudaEventDestroy(j->ev_ep[k]), j->ev_ep[k] = nullptr;
+  if (j->ev_start) cudaEventDestroy(j->ev_start), j->ev_start = nullptr;
+  if (j->ev_done) cudaEventDestroy(j->ev_done), j->ev_done = nullptr;
+  if (j->st) cudaStreamDestroy(j->st), j->st = nullptr;
+  std::lock_guard<std::mutex> g(c->mu);
+  c->bytes_resident -= j->bytes;
+}
+
+static void finish_job(n2f_ctx* c, Job* j, int state, int err) {
+  j->t_done = Clock::now();
+  j->error = err;
+  release_device(c, j);
+  {
+    std::lock_guard<std::mutex> g(c->mu);
+    j->state.store(state);
+    c->active.erase(std::remove(c->active.begin(), c->active.end(), j), c->active.end());
+    c->n_done += 1;
+  }
+  c->cv_done.notify_all();
+}
+
+// Creates the device state of a job and enqueues upload, gather and initialisation.
+static int admit(n2f_ctx* c, Job* j) {
+  LaunchScope ls(&c->launches);
+  CKR(cudaStreamCreateWithFlags(&j->st, cudaStreamNonBlocking));
+  CKR(cudaEventCreate(&j->ev_start));
+  CKR(cudaEventCreate(&j->ev_done));
+  j->ring = (int)std::min<uint32_t>(8, std::max<uint32_t>(2, c->cfg.lookahead + 1));
+  for (int k = 0; k < j->ring; ++k) CKR(cudaEventCreateWithFlags(&j->ev_ep[k], cudaEventDisableTiming));
+  CKR(cudaMallocHost((void**)&j->hst, sizeof(DevState) * j->ring));
+  CKR(cudaMallocHost((void**)&j->pin_out, sizeof(float) * (size_t)j->H * j->W));
+  int rc = trainer_init(&j->tr, c->al, j->st, j->src_kind == 2);
+  if (rc) return rc;
+  CKR(cudaEventRecord(j->ev_start, j->st));
+  const size_t n = (size_t)j->H * j->W;
+  if (j->src_kind == 0)
+    CKR(cudaMemcpyAsync(j->tr.x, j->pin_in, n * sizeof(float), cudaMemcpyHostToDevice, j->st));
+  else if (j->src_kind == 1)
+    CKR(cudaMemcpyAsync(j->tr.x, j->dev_in, n * sizeof(float), cudaMemcpyDeviceToDevice, j->st));
+  else
+    CKR(cudaMemcpyAsync(j->tr.in_u16, j->pin_u16, n * sizeof(uint16_t), cudaMemcpyHostToDevice,
+                        j->st));
+  rc = trainer_start(&j->tr, j->src_kind == 2);
+  if (rc) return rc;
+  if (j->tr.fixed_mode) {
+    for (int k = 0; k < j->prm.fixed_steps; ++k)
+      if ((rc = trainer_step(&j->tr, k % 4))) return rc;
+    if ((rc = trainer_validate(&j->tr))) return rc;
+    j->finishing = true;
+  }
+  return N2F_OK;
+}
+
+// Advances one running job without blocking. Returns true if it enqueued or finished work.
+static bool progress(n2f_ctx* c, Job* j) {
+  LaunchScope ls(&c->launches);
+  bool did = false;
+  int rc = 0;
+  if (j->cancel) {
+    finish_job(c, j, N2F_CANCELED, N2F_ECANCELED);
+    return true;
+  }
+  if (!j->finishing) {
+    while (j->ep_seen < j->ep_enq) {
+      const int slot = (int)(j->ep_seen % j->ring);
+      const cudaError_t q = cudaEventQuery(j->ev_ep[slot]);
+      if (q == cudaErrorNotReady) break;
+      if (q != cudaSuccess) {
+        set_cuda_error(q, "epoch");
+        finish_job(c, j, N2F_FAILED, N2F_EDEVICE);
+        return true;
+      }
+      {
+        std::lock_guard<std::mutex> g(c->mu);
+        j->last = j->hst[slot];
+      }
+      j->ep_seen += 1;
+      did = true;
+      if (j->last.stopped) {
+        j->finishing = true;
+        break;
+      }
+    }
+    const uint32_t la = std::max<uint32_t>(1, c->cfg.lookahead);
+    while (!j->finishing && j->ep_enq - j->ep_seen < la) {
+      if ((rc = trainer_epoch(&j->tr))) break;
+      const int slot = (int)(j->ep_enq % j->ring);
+      cudaError_t e = cudaMemcpyAsync(&j->hst[slot], j->tr.state, sizeof(DevState),
+                                      cudaMemcpyDeviceToHost, j->st);
+      if (e == cudaSuccess) e = cudaEventRecord(j->ev_ep[slot], j->st);
+      if (e != cudaSuccess) {
+        rc = set_cuda_error(e, "epoch enqueue");
+        break;
+      }
+      j->ep_enq += 1;
+      did = true;
+    }
+    if (rc) {
+      finish_job(c, j, N2F_FAILED, rc);
+      return true;
+    }
+  }
+  if (j->finishing && !j->result_enq) {
+    rc = trainer_finish(&j->tr);
+    cudaError_t e = cudaSuccess;
+    if (!rc) {
+      e = cudaMemcpyAsync(j->pin_out, j->tr.out, sizeof(float) * j->tr.N, cudaMemcpyDeviceToHost,
+                          j->st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(&j->hst[0], j->tr.state, sizeof(DevState),
+                                                cudaMemcpyDeviceToHost, j->st);
+      if (e == cudaSuccess) e = cudaEventRecord(j->ev_done, j->st);
+      if (e != cudaSuccess) rc = set_cuda_error(e, "result enqueue");
+    }
+    if (rc) {
+      finish_job(c, j, N2F_FAILED, rc);
+      return true;
+    }
+    j->result_enq = true;
+    did = true;
+  }
+  if (j->result_enq) {
+    const cudaError_t q = cudaEventQuery(j->ev_done);
+    if (q == cudaErrorNotReady) return did;
+    if (q != cudaSuccess) {
+      set_cuda_error(q, "result");
+      finish_job(c, j, N2F_FAILED, N2F_EDEVICE);
+      return true;
+    }
+    {
+      std::lock_guard<std::mutex> g(c->mu);
+      j->last = j->hst[0];
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, j->ev_start, j->ev_done);
+    j->device_ms = ms;
+    float a = 0.f, b = 0.f;
+    cudaEventElapsedTime(&a, c->ev_ref, j->ev_start);
+    cudaEventElapsedTime(&b, c->ev_ref, j->ev_done);
+    j->t0_ms = a;
+    j->t1_ms = b;
+    const bool bad = j->last.stopped == 3;
+    finish_job(c, j, bad ? N2F_FAILED : N2F_DONE, bad ? N2F_ENONFINITE : N2F_OK);
+    return true;
+  }
+  return did;
+}
+
+static void worker_main(n2f_ctx* c) {
+  cudaSetDevice(c->cfg.device);
+  for (;;) {
+    std::vector<Job*> to_admit;
+    {
+      std::unique_lock<std::mutex> lk(c->mu);
+      if (c->active.empty() && c->queue.empty())
+        c->cv_work.wait(lk, [&] { return c->stop || !c->queue.empty(); });
+      if (c->stop) break;
+      while (!c->queue.empty() && c->active.size() + to_admit.size() < c->cfg.max_slots) {
+        Job* j = c->queue.front();
+        if (j->cancel) {
+          c->queue.pop_front();
+          j->state.store(N2F_CANCELED);
+          j->error = N2F_ECANCELED;
+          c->cv_done.notify_all();
+          continue;
+        }
+        if (c->bytes_resident + j->bytes > c->cfg.hbm_budget_bytes) break;  // FIFO admission
+        c->queue.pop_front();
+        c->bytes_resident += j->bytes;
+        to_admit.push_back(j);
+      }
+    }
+    for (Job* j : to_admit) {
+      {
+        std::lock_guard<std::mutex> g(c->mu);
+        c->active.push_back(j);
+      }
+      j->state.store(N2F_RUNNING);
+      int rc = admit(c, j);
+      if (rc) finish_job(c, j, N2F_FAILED, rc);
+    }
+    std::vector<Job*> act;
+    {
+      std::lock_guard<std::mutex> g(c->mu);
+      act = c->active;
+    }
+    bool any = false;
+    for (Job* j : act) any |= progress(c, j);
+    if (!any && !act.empty()) std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+}
+
+extern "C" int n2f_create(n2f_ctx** out, const n2f_config* cfg) {
+  if (!out) return N2F_EINVAL;
+  n2f_config def;
+  n2f_config_default(&def);
+  if (!cfg) cfg = &def;
+  if (cfg->struct_size != sizeof(n2f_config)) return N2F_EINVAL;
+  int ndev = 0;
+  CKR(cudaGetDeviceCount(&ndev));
+  if (cfg->device < 0 || cfg->device >= ndev) return N2F_EINVAL;
+  CKR(cudaSetDevice(cfg->device));
+  n2f_ctx* c = new n2f_ctx();
+  c->cfg = *cfg;
+  if (!c->cfg.hbm_budget_bytes) c->cfg.hbm_budget_bytes = 150ull << 30;
+  if (!c->cfg.max_slots) c->cfg.max_slots = 64;
+  if (!c->cfg.lookahead) c->cfg.lookahead = 2;
+  c->al.alloc = cfg->alloc;
+  c->al.free = cfg->free;
+  c->al.user = cfg->alloc_user;
+  cudaError_t e = cudaEventCreate(&c->ev_ref);
+  if (e == cudaSuccess) e = cudaEventRecord(c->ev_ref, 0);
+  if (e == cudaSuccess) e = cudaEventSynchronize(c->ev_ref);
+  if (e != cudaSuccess) {
+    delete c;
+    return set_cuda_error(e, "n2f_create");
+  }
+  c->worker = std::thread(worker_main, c);
+  *out = c;
+  return N2F_OK;
+}
+
+extern "C" void n2f_destroy(n2f_ctx* c) {
+  if (!c) return;
+  {
+    std::lock_guard<std::mutex> g(c->mu);
+    c->stop = true;
+  }
+  c->cv_work.notify_all();
+  if (c->worker.joinable()) c->worker.join();
+  for (Job* j : c->active) {
+    release_device(c, j);
+    j->state.store(N2F_CANCELED);
+  }
+  for (auto& kv : c->jobs) {
+    free_job_host(kv.second);
+    delete kv.second;
+  }
+  if (c->ev_ref) cudaEventDestroy(c->ev_ref);
+  delete c;
+}
+
+static int submit_common(n2f_ctx* c, int kind, const void* image, int H, int W,
+                         const n2f_params* p, n2f_job* out) {
+  if (!c || !image || !out) return N2F_EINVAL;
+  n2f_params def;
+  n2f_params_default(&def);
+  if (!p) p = &def;
+  int rc = check_params(p);
+  if (rc) return rc;
+  if ((rc = check_image(H, W))) return rc;
+  const size_t n = (size_t)H * W;
+  if (kind == 0) {
+    const float* f = (const float*)image;
+    for (size_t i = 0; i < n; ++i)
+      if (!isfinite(f[i])) return N2F_EINVAL;
+  }
+  Job* j = new Job();
+  j->H = H;
+  j->W = W;
+  j->prm = *p;
+  j->src_kind = kind;
+  if ((rc = trainer_configure(&j->tr, H, W, p, 0))) {
+    delete j;
+    return rc;
+  }
+  j->bytes = trainer_bytes(H, W, p, 0);
+  if (j->bytes > c->cfg.hbm_budget_bytes) {
+    delete j;
+    return N2F_ETOOBIG;
+  }
+  cudaError_t e = cudaSuccess;
+  if (kind == 0) {
+    e = cudaMallocHost((void**)&j->pin_in, n * sizeof(float));
+    if (e == cudaSuccess) memcpy(j->pin_in, image, n * sizeof(float));
+  } else if (kind == 2) {
+    e = cudaMallocHost((void**)&j->pin_u16, n * sizeof(uint16_t));
+    if (e == cudaSuccess) memcpy(j->pin_u16, image, n * sizeof(uint16_t));
+  } else {
+    j->dev_in = (const float*)image;
+  }
+  if (e != cudaSuccess) {
+    free_job_host(j);
+    delete j;
+    return set_cuda_error(e, "pinned staging");
+  }
+  j->t_submit = Clock::now();
+  {
+    std::lock_guard<std::mutex> g(c->mu);
+    j->id = c->next_id++;
+    c->jobs[j->id] = j;
+    c->queue.push_back(j);
+  }
+  c->cv_work.notify_all();
+  *out = j->id;
+  return N2F_OK;
+}
+
+extern "C" int n2f_submit(n2f_ctx* c, const float* image, int H, int W, const n2f_params* p,
+                          n2f_job* out) {
+  return submit_common(c, 0, image, H, W, p, out);
+}
+extern "C" int n2f_submit_device(n2f_ctx* c, const float* dimage, int H, int W,
+                                 const n2f_params* p, n2f_job* out) {
+  return submit_common(c, 1, dimage, H, W, p, out);
+}
+extern "C" int n2f_submit_u16(n2f_ctx* c, const uint16_t* image, int H, int W,
+                              const n2f_params* p, n2f_job* out) {
+  return submit_common(c, 2, image, H, W, p, out);
+}
+
+static Job* find(n2f_ctx* c, n2f_job id) {
+  auto it = c->jobs.find(id);
+  return it == c->jobs.end() ? nullptr : it->second;
+}
+
+extern "C" int n2f_poll(n2f_ctx* c, n2f_job id, n2f_status* st) {
+  if (!c || !st || st->struct_size != sizeof(n2f_status)) return N2F_EINVAL;
+  std::lock_guard<std::mutex> g(c->mu);
+  Job* j = find(c, id);
+  if (!j) return N2F_ENOENT;
+  const uint32_t ss = st->struct_size;
+  memset(st, 0, sizeof(*st));
+  st->struct_size = ss;
+  st->state = j->state.load();
+  st->error = j->error;
+  fill_status(&j->tr, j->last, st);
+  st->H = (uint32_t)j->H;
+  st->W = (uint32_t)j->W;
+  st->device_ms = j->device_ms;
+  st->t_start_ms = j->t0_ms;
+  st->t_done_ms = j->t1_ms;
+  if (st->state >= N2F_DONE)
+    st->latency_ms = std::chrono::duration<double, std::milli>(j->t_done - j->t_submit).count();
+  return N2F_OK;
+}
+
+extern "C" int n2f_wait(n2f_ctx* c, n2f_job id, int timeout_ms) {
+  if (!c) return N2F_EINVAL;
+  std::unique_lock<std::mutex> lk(c->mu);
+  Job* j = find(c, id);
+  if (!j) return N2F_ENOENT;
+  auto done = [&] { return j->state.load() >= N2F_DONE; };
+  if (timeout_ms < 0)
+    c->cv_done.wait(lk, done);
+  else if (!c->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), done))
+    return N2F_ETIMEDOUT;
+  return N2F_OK;
+}
+
+static int take_result(n2f_ctx* c, n2f_job id, float* out, size_t n, bool device) {
+  if (!c || !out) return N2F_EINVAL;
+  Job* j;
+  {
+    std::lock_guard<std::mutex> g(c->mu);
+    j = find(c, id);
+    if (!j) return N2F_ENOENT;
+    const int s = j->state.load();
+    if (s < N2F_DONE) return N2F_EAGAIN;
+    if (s != N2F_DONE) {
+      const int err = j->error ? j->error : N2F_EDEVICE;
+      c->jobs.erase(id);
+      free_job_host(j);
+      delete j;
+      return err;
+    }
+    if (n < (size_t)j->H * j->W) return N2F_EINVAL;
+  }
+  const size_t bytes = sizeof(float) * (size_t)j->H * j->W;
+  if (device) {
+    CKR(cudaMemcpy(out, j->pin_out, bytes, cudaMemcpyHostToDevice));
+  } else {
+    memcpy(out, j->pin_out, bytes);
+  }
+  std::lock_guard<std::mutex> g(c->mu);
+  c->jobs.erase(id);
+  free_job_host(j);
+  delete j;
+  return N2F_OK;
+}
+
+extern "C" int n2f_result(n2f_ctx* c, n2f_job id, float* out, size_t out_elems) {
+  return take_result(c, id, out, out_elems, false);
+}
+extern "C" int n2f_result_device(n2f_ctx* c, n2f_job id, float* dout, size_t out_elems) {
+  return take_result(c, id, dout, out_elems, true);
+}
+
+extern "C" int n2f_cancel(n2f_ctx* c, n2f_job id) {
+  if (!c) return N2F_EINVAL;
+  std::lock_guard<std::mutex> g(c->mu);
+  Job* j = find(c, id);
+  if (!j) return N2F_ENOENT;
+  if (j->state.load() >= N2F_DONE) return N2F_OK;
+  j->cancel = true;
+  c->cv_work.notify_all();
+  return N2F_OK;
+}
+
+extern "C" int n2f_stats(n2f_ctx* c, n2f_ctx_stats* st) {
+  if (!c || !st || st->struct_size != sizeof(n2f_ctx_stats)) return N2F_EINVAL;
+  std::lock_guard<std::mutex> g(c->mu);
+  st->kernel_launches = c->launches;
+  st->bytes_resident = c->bytes_resident;
+  st->jobs_queued = (uint32_t)c->queue.size();
+  st->jobs_running = (uint32_t)c->active.size();
+  st->jobs_done = c->n_done;
+  return N2F_OK;
+}

@@ -1,0 +1,730 @@
+// Memory-bound kernels of the Noise2Fast path: checkerboard gather, weight init, Adam with
+// weight packing, CG-layout packing, the one-channel first layer, the head (1x1 conv +
+// sigmoid + loss), the FP64 validation reduction, the stopping rule and output averaging.
+#include <math.h>
+
+#include "cg_util.cuh"
+#include "n2f_internal.h"
+#include "tc_layout.cuh"
+
+namespace n2f {
+
+thread_local uint64_t* tl_launch_counter = nullptr;
+
+#define N2F_LAUNCH_CHECK() \
+  do {                     \
+    count_launch();        \
+    return cudaGetLastError(); \
+  } while (0)
+
+static inline unsigned nblocks(size_t n, int per) { return (unsigned)((n + per - 1) / per); }
+
+// ---------------------------------------------------------------------------------------------
+// Checkerboard downsampling (Theoretical Background Eq. 6-7; Methods, the "left" equations).
+// Odd images: the pixels with i+j odd, compacted in order. Pure copies, bit-exact.
+__global__ void k_gather(const float* __restrict__ x, int H, int W, float* __restrict__ ue,
+                         float* __restrict__ uo, float* __restrict__ le, float* __restrict__ lo) {
+  const int hw = W >> 1, hh = H >> 1;
+  const size_t nup = (size_t)H * hw, nlf = (size_t)hh * W;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < nup + nlf;
+       t += (size_t)gridDim.x * blockDim.x) {
+    if (t < nup) {
+      const int i = (int)(t / hw), j = (int)(t % hw);
+      const float* row = x + (size_t)i * W;
+      ue[t] = row[2 * j + (i & 1)];
+      uo[t] = row[2 * j + 1 - (i & 1)];
+    } else {
+      const size_t u = t - nup;
+      const int i = (int)(u / W), j = (int)(u % W);
+      le[u] = x[(size_t)(2 * i + (j & 1)) * W + j];
+      lo[u] = x[(size_t)(2 * i + 1 - (j & 1)) * W + j];
+    }
+  }
+}
+
+cudaError_t launch_gather(const float* x, int H, int W, float* ue, float* uo, float* le, float* lo,
+                          cudaStream_t st) {
+  const size_t n = (size_t)H * (W / 2) + (size_t)(H / 2) * W;
+  unsigned g = nblocks(n, 256);
+  if (g > 152u * 16) g = 152u * 16;
+  k_gather<<<g, 256, 0, st>>>(x, H, W, ue, uo, le, lo);
+  N2F_LAUNCH_CHECK();
+}
+
+__global__ void k_u16(const uint16_t* __restrict__ in, float* __restrict__ out, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    out[i] = (float)in[i] / 65535.0f;
+}
+
+cudaError_t launch_u16_to_f32(const uint16_t* in, float* out, size_t n, cudaStream_t st) {
+  unsigned g = nblocks(n, 256);
+  if (g > 152u * 16) g = 152u * 16;
+  k_u16<<<g, 256, 0, st>>>(in, out, n);
+  N2F_LAUNCH_CHECK();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Initial weights: element k of the flat vector is U(-1/sqrt(fan_in), +1/sqrt(fan_in)) drawn
+// from output k of SplitMix64 (Steele, Lea & Flood 2014), rounded to float32. Only exact IEEE
+// double operations are used, so the values equal any other correct implementation's.
+struct InitArgs {
+  unsigned long long seg_end[kLayers + 1];  // first index after layer l (weights + bias)
+  double bound[kLayers + 1];
+  unsigned long long count, seed;
+};
+
+__device__ __forceinline__ unsigned long long splitmix64_at(unsigned long long seed,
+                                                            unsigned long long k) {
+  unsigned long long z = seed + (k + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__global__ void k_init(float* __restrict__ theta, InitArgs a) {
+  for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+       k < a.count; k += (unsigned long long)gridDim.x * blockDim.x) {
+    int l = 0;
+    while (l < kLayers && k >= a.seg_end[l]) ++l;
+    const double u = (double)(splitmix64_at(a.seed, k) >> 11) * 0x1.0p-53;
+    const double v = __dmul_rn(__dsub_rn(__dmul_rn(2.0, u), 1.0), a.bound[l]);
+    theta[k] = __double2float_rn(v);
+  }
+}
+
+cudaError_t launch_init_params(float* theta, const NetShape& net, uint64_t seed, cudaStream_t st) {
+  InitArgs a;
+  int cin = 1;
+  for (int l = 0; l <= kLayers; ++l) {
+    const int fan = l < kLayers ? cin * 9 : cin;
+    a.bound[l] = 1.0 / sqrt((double)fan);
+    a.seg_end[l] = l < kLayers ? net.w_off[l + 1] : net.count;
+    if (l < kLayers) cin = net.widths[l];
+  }
+  a.count = net.count;
+  a.seed = seed;
+  unsigned g = nblocks(net.count, 256);
+  if (g > 152u * 8) g = 152u * 8;
+  k_init<<<g, 256, 0, st>>>(theta, a);
+  N2F_LAUNCH_CHECK();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Writes weight W[o][c][tap] of one layer into every operand copy that is present:
+//   SIMT forward  [C_in/8][tap][8][C_out]   (first layer: [C_out][9])
+//   SIMT dgrad    [C_out/8][8 - tap][8][C_in]
+//   tensor core   tc_layout.cuh order, forward (rows o, k = tap*C_in + c) and dgrad
+//                 (rows c, k = (8 - tap)*C_out + o); bf16, or a TF32 hi part + residual.
+__device__ __forceinline__ void pack_one(float* fwd, float* dgr, void* tcf, void* tcd,
+                                         float* tcf_lo, float* tcd_lo, int tc_bf16, int cin,
+                                         int cout, int o, int c, int tap, float th) {
+  if (cin == 1) {
+    if (fwd) fwd[(size_t)o * 9 + tap] = th;
+    return;
+  }
+  if (fwd) fwd[(((size_t)(c >> 3) * 9 + tap) * 8 + (c & 7)) * cout + o] = th;
+  if (dgr) dgr[(((size_t)(o >> 3) * 9 + (8 - tap)) * 8 + (o & 7)) * cin + c] = th;
+  if (tcf) {
+    const size_t fi = tc_index_cfg(tc_cfg(cin, cout, tc_bf16), cin, o, tap, c);
+    const size_t di = tc_index_cfg(tc_cfg(cout, cin, tc_bf16), cout, c, 8 - tap, o);
+    if (tc_bf16) {
+      ((__nv_bfloat16*)tcf)[fi] = __float2bfloat16_rn(th);
+      ((__nv_bfloat16*)tcd)[di] = __float2bfloat16_rn(th);
+    } else {
+      // 3xTF32 split: hi keeps the 10 explicit TF32 mantissa bits (exact as TF32), lo = th - hi
+      const float hi = __uint_as_float(__float_as_uint(th) & 0xFFFFE000u);
+      const float lo = th - hi;
+      ((float*)tcf)[fi] = hi;
+      tcf_lo[fi] = lo;
+      ((float*)tcd)[di] = hi;
+      tcd_lo[di] = lo;
+    }
+  }
+}
+
+// Adam (Kingma & Ba, Algorithm 1; Methods: lr 0.001), fused with writing the packed weight
+// copies the convolution kernels read. update = 0 only packs (after init / set_theta).
+__global__ void k_adam(PackArgs pa, const float* __restrict__ grad, float* __restrict__ m,
+                       float* __restrict__ v, float lr, float b1, float b2, float eps,
+                       const DevState* __restrict__ state, int update) {
+  if (update && state->stopped) return;
+  float bc1 = 1.f, bc2 = 1.f;
+  if (update) {
+    bc1 = state->bc1;
+    bc2 = state->bc2;
+  }
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+       i < pa.count; i += (unsigned long long)gridDim.x * blockDim.x) {
+    float th = pa.theta[i];
+    if (update) {
+      const float g = grad[i];
+      const float mi = b1 * m[i] + (1.f - b1) * g;
+      const float vi = b2 * v[i] + (1.f - b2) * g * g;
+      m[i] = mi;
+      v[i] = vi;
+      th -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+      pa.theta[i] = th;
+    }
+    int l = 0;
+    while (l < kLayers && i >= pa.w_off[l + 1]) ++l;
+    if (l == kLayers || i >= pa.b_off[l]) continue;  // head or a bias: read from theta
+    const int cin = l == 0 ? 1 : pa.widths[l - 1], cout = pa.widths[l];
+    const size_t j = i - pa.w_off[l];
+    const int o = (int)(j / ((size_t)cin * 9));
+    const int rem = (int)(j % ((size_t)cin * 9));
+    pack_one(pa.fwd[l], pa.dgr[l], pa.tcf[l], pa.tcd[l], pa.tcf_lo[l], pa.tcd_lo[l], pa.tc_bf16,
+             cin, cout, o, rem / 9, rem % 9, th);
+  }
+}
+
+// Packs one canonical [C_out][C_in][3][3] weight tensor into the kernels' operand copies.
+__global__ void k_pack_layer(const float* __restrict__ w, int cin, int cout, float* fwd,
+                             float* dgr, void* tcf, void* tcd, float* tcf_lo, float* tcd_lo,
+                             int tc_bf16) {
+  const size_t n = (size_t)cout * cin * 9;
+  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < n;
+       j += (size_t)gridDim.x * blockDim.x) {
+    const int o = (int)(j / ((size_t)cin * 9));
+    const int rem = (int)(j % ((size_t)cin * 9));
+    pack_one(fwd, dgr, tcf, tcd, tcf_lo, tcd_lo, tc_bf16, cin, cout, o, rem / 9, rem % 9, w[j]);
+  }
+}
+
+cudaError_t launch_pack_layer(const float* w, int cin, int cout, float* fwd, float* dgr, void* tcf,
+                              void* tcd, float* tcf_lo, float* tcd_lo, int tc_bf16,
+                              cudaStream_t st) {
+  unsigned g = nblocks((size_t)cout * cin * 9, 256);
+  if (g > 152u * 8) g = 152u * 8;
+  k_pack_layer<<<g, 256, 0, st>>>(w, cin, cout, fwd, dgr, tcf, tcd, tcf_lo, tcd_lo, tc_bf16);
+  N2F_LAUNCH_CHECK();
+}
+
+cudaError_t launch_adam(const PackArgs& pa, const float* grad, float* m, float* v, float lr,
+                        float b1, float b2, float eps, const DevState* state, int update,
+                        cudaStream_t st) {
+  unsigned g = nblocks(pa.count, 256);
+  if (g > 152u * 8) g = 152u * 8;
+  k_adam<<<g, 256, 0, st>>>(pa, grad, m, v, lr, b1, b2, eps, state, update);
+  N2F_LAUNCH_CHECK();
+}
+
+// ---------------------------------------------------------------------------------------------
+// NCHW float <-> CG layout.
+template <typename T>
+__global__ void k_pack_cg(const float* __restrict__ src, int C, size_t npx, T* __restrict__ dst) {
+  constexpr int G = CGTraits<T>::G;
+  const size_t n = (size_t)C * npx;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const int c = (int)(i / npx);
+    const size_t p = i % npx;
+    dst[((size_t)(c / G) * npx + p) * G + (c % G)] = CGTraits<T>::from_float(src[i]);
+  }
+}
+
+template <typename T, typename D>
+__global__ void k_unpack_cg(const T* __restrict__ src, int C, size_t npx, D* __restrict__ dst) {
+  constexpr int G = CGTraits<T>::G;
+  const size_t n = (size_t)C * npx;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const int c = (int)(i / npx);
+    const size_t p = i % npx;
+    dst[i] = (D)CGTraits<T>::to_float(src[((size_t)(c / G) * npx + p) * G + (c % G)]);
+  }
+}
+
+cudaError_t launch_pack_cg(const float* nchw, int C, int H, int W, int bf16, void* cg,
+                           cudaStream_t st) {
+  const size_t npx = (size_t)H * W;
+  unsigned g = nblocks((size_t)C * npx, 256);
+  if (g > 152u * 16) g = 152u * 16;
+  if (bf16)
+    k_pack_cg<__nv_bfloat16><<<g, 256, 0, st>>>(nchw, C, npx, (__nv_bfloat16*)cg);
+  else
+    k_pack_cg<float><<<g, 256, 0, st>>>(nchw, C, npx, (float*)cg);
+  N2F_LAUNCH_CHECK();
+}
+
+cudaError_t launch_unpack_cg(const void* cg, int C, int H, int W, int bf16, float* nchw,
+                             cudaStream_t st) {
+  const size_t npx = (size_t)H * W;
+  unsigned g = nblocks((size_t)C * npx, 256);
+  if (g > 152u * 16) g = 152u * 16;
+  if (bf16)
+    k_unpack_cg<__nv_bfloat16, float><<<g, 256, 0, st>>>((const __nv_bfloat16*)cg, C, npx, nchw);
+  else
+    k_unpack_cg<float, float><<<g, 256, 0, st>>>((const float*)cg, C, npx, nchw);
+  N2F_LAUNCH_CHECK();
+}
+
+cudaError_t launch_unpack_cg_f64(const void* cg, int C, int H, int W, int bf16, double* out,
+                                 cudaStream_t st) {
+  const size_t npx = (size_t)H * W;
+  unsigned g = nblocks((size_t)C * npx, 256);
+  if (g > 152u * 16) g = 152u * 16;
+  if (bf16)
+    k_unpack_cg<__nv_bfloat16, double><<<g, 256, 0, st>>>((const __nv_bfloat16*)cg, C, npx, out);
+  else
+    k_unpack_cg<float, double><<<g, 256, 0, st>>>((const float*)cg, C, npx, out);
+  N2F_LAUNCH_CHECK();
+}
+
+// ---------------------------------------------------------------------------------------------
+// First layer, C_in = 1 (Methods: the first 3x3 convolution sees the one-channel image).
+// One thread per pixel: nine taps from the image (zero outside), C outputs + bias, ReLU.
+template <typename T>
+__global__ void __launch_bounds__(256) k_conv1_fwd(const float* __restrict__ img, int H, int W,
+                                                   const float* __restrict__ w,
+                                                   const float* __restrict__ b, int C,
+                                                   T* __restrict__ out, const int* skip) {
+  if (skip && *skip) return;
+  constexpr int G = CGTraits<T>::G;
+  __shared__ float sw[64 * 9], sb[64];
+  for (int i = threadIdx.x; i < C * 9; i += blockDim.x) sw[i] = w[i];
+  for (int i = threadIdx.x; i < C; i += blockDim.x) sb[i] = b[i];
+  __syncthreads();
+  const size_t npx = (size_t)H * W;
+  const size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (p >= npx) return;
+  const int y = (int)(p / W), x = (int)(p % W);
+  float t[9];
+#pragma unroll
+  for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+    for (int kx = 0; kx < 3; ++kx) {
+      const int yy = y + ky - 1, xx = x + kx - 1;
+      t[ky * 3 + kx] = (yy >= 0 && yy < H && xx >= 0 && xx < W) ? img[(size_t)yy * W + xx] : 0.f;
+    }
+  for (int g = 0; g < C / G; ++g) {
+    float v[G];
+#pragma unroll
+    for (int k = 0; k < G; ++k) {
+      const int o = g * G + k;
+      float s = sb[o];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) s += sw[o * 9 + q] * t[q];
+      v[k] = s > 0.f ? s : 0.f;
+    }
+    store_group<T>(out, (size_t)g * npx + p, v);
+  }
+}
+
+cudaError_t launch_conv1_fwd(const float* img, int H, int W, const float* w, const float* b, int C,
+                             int bf16, void* out, const int* skip, cudaStream_t st) {
+  if (C > 64) return cudaErrorInvalidValue;
+  const size_t npx = (size_t)H * W;
+  if (bf16)
+    k_conv1_fwd<__nv_bfloat16><<<nblocks(npx, 256), 256, 0, st>>>(img, H, W, w, b, C,
+                                                                  (__nv_bfloat16*)out, skip);
+  else
+    k_conv1_fwd<float><<<nblocks(npx, 256), 256, 0, st>>>(img, H, W, w, b, C, (float*)out, skip);
+  N2F_LAUNCH_CHECK();
+}
+
+// First-layer weight gradient: dW[o][tap] = sum_p d(p,o) x(p + tap), db[o] = sum_p d(p,o).
+// Block s sums pixel tiles s, s+S, ... in order; the partials are reduced in block order.
+template <typename T>
+__global__ void __launch_bounds__(256) k_conv1_wgrad(const T* __restrict__ dout,
+                                                     const float* __restrict__ img, int H, int W,
+                                                     int C, float* __restrict__ part,
+                                                     const int* skip) {
+  if (skip && *skip) return;
+  constexpr int G = CGTraits<T>::G;
+  constexpr int TP = 128;
+  __shared__ float sD[TP][64 + 1];
+  __shared__ float sX[TP][9];
+  const size_t npx = (size_t)H * W;
+  const int Q = C * 10;  // (o, tap) pairs then the C biases
+  float acc[3] = {0.f, 0.f, 0.f};
+  const size_t ntiles = (npx + TP - 1) / TP;
+  for (size_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const size_t p0 = tile * TP;
+    __syncthreads();
+    for (int i = threadIdx.x; i < TP * (C / G); i += blockDim.x) {
+      const int pp = i % TP, g = i / TP;
+      const size_t p = p0 + pp;
+      float v[G];
+      if (p < npx) {
+        load_group<T>(dout, (size_t)g * npx + p, v);
+      } else {
+#pragma unroll
+        for (int k = 0; k < G; ++k) v[k] = 0.f;
+      }
+#pragma unroll
+      for (int k = 0; k < G; ++k) sD[pp][g * G + k] = v[k];
+    }
+    for (int i = threadIdx.x; i < TP * 9; i += blockDim.x) {
+      const int pp = i / 9, q = i % 9;
+      const size_t p = p0 + pp;
+      float v = 0.f;
+      if (p < npx) {
+        const int y = (int)(p / W) + q / 3 - 1, x = (int)(p % W) + q % 3 - 1;
+        if (y >= 0 && y < H && x >= 0 && x < W) v = img[(size_t)y * W + x];
+      }
+      sX[pp][q] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const int qi = threadIdx.x + r * 256;
+      if (qi >= Q) break;
+      float s = acc[r];
+      if (qi < C * 9) {
+        const int o = qi / 9, q = qi % 9;
+        for (int pp = 0; pp < TP; ++pp) s += sD[pp][o] * sX[pp][q];
+      } else {
+        const int o = qi - C * 9;
+        for (int pp = 0; pp < TP; ++pp) s += sD[pp][o];
+      }
+      acc[r] = s;
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const int qi = threadIdx.x + r * 256;
+    if (qi < Q) part[(size_t)blockIdx.x * Q + qi] = acc[r];
+  }
+}
+
+// out[q] = sum_{s < S} part[s * Q + q] (ascending s). Canonical placement of dW and db.
+__global__ void k_reduce_conv1(const float* __restrict__ part, int S, int C, float* __restrict__ gw,
+                               float* __restrict__ gb, const int* skip) {
+  if (skip && *skip) return;
+  const int Q = C * 10;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < Q; q += gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int k = 0; k < S; ++k) s += part[(size_t)k * Q + q];
+    if (q < C * 9)
+      gw[q] = s;  // [o][0][ky][kx] == o * 9 + tap
+    else
+      gb[q - C * 9] = s;
+  }
+}
+
+cudaError_t launch_conv1_wgrad(const void* dout, const float* img, int H, int W, int C, int bf16,
+                               float* part, size_t part_cap, float* gw, float* gb,
+                               const int* skip, cudaStream_t st) {
+  if (C > 64) return cudaErrorInvalidValue;
+  const size_t npx = (size_t)H * W;
+  const int Q = C * 10;
+  int S = (int)((npx + 127) / 128);
+  if (S > 304) S = 304;
+  if ((size_t)S * Q > part_cap) S = (int)(part_cap / Q);
+  if (S < 1) return cudaErrorInvalidValue;
+  if (bf16)
+    k_conv1_wgrad<__nv_bfloat16><<<S, 256, 0, st>>>((const __nv_bfloat16*)dout, img, H, W, C,
+                                                    part, skip);
+  else
+    k_conv1_wgrad<float><<<S, 256, 0, st>>>((const float*)dout, img, H, W, C, part, skip);
+  count_launch();
+  k_reduce_conv1<<<nblocks(Q, 128), 128, 0, st>>>(part, S, C, gw, gb, skip);
+  N2F_LAUNCH_CHECK();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Head, training step (Methods: 1x1 convolution, sigmoid, BCE loss against the target).
+// One thread per pixel: z = b + w . a8, dL/dz = (sigmoid(z) - y) / P in the logit form of BCE
+// (MSE alternative: 2 (s - y) s (1 - s) / P), delta_8 = dL/dz * w * [a8 > 0], and per-block
+// partial sums of dL/dz * a8 (head weight gradient), dL/dz (head bias) and the loss (FP64).
+__device__ __forceinline__ float sigmoid_f(float z) {
+  if (z >= 0.f) return 1.f / (1.f + expf(-z));
+  const float e = expf(z);
+  return e / (1.f + e);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_head_train(const T* __restrict__ a8, int C, int npx,
+                                                    const float* __restrict__ w9,
+                                                    const float* __restrict__ b9,
+                                                    const float* __restrict__ tgt, int loss_kind,
+                                                    float* __restrict__ dzbuf, T* __restrict__ d8,
+                                                    double* __restrict__ loss_part,
+                                                    float* __restrict__ hpart, const int* skip) {
+  if (skip && *skip) return;
+  constexpr int G = CGTraits<T>::G;
+  __shared__ float sw[256];
+  __shared__ float sred[8][257];
+  __shared__ double sl[8];
+  for (int i = threadIdx.x; i < C; i += blockDim.x) sw[i] = w9[i];
+  __syncthreads();
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = p < npx;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float z = b9[0];
+  if (live)
+    for (int g = 0; g < C / G; ++g) {
+      float v[G];
+      load_group<T>(a8, (size_t)g * npx + p, v);
+#pragma unroll
+      for (int k = 0; k < G; ++k) z += sw[g * G + k] * v[k];
+    }
+  float dz = 0.f;
+  double lterm = 0.0;
+  if (live) {
+    const float s = sigmoid_f(z), y = tgt[p];
+    if (loss_kind == 0) {
+      dz = (s - y) / (float)npx;
+      const float sp = fmaxf(z, 0.f) + log1pf(expf(-fabsf(z)));
+      lterm = (double)sp - (double)y * (double)z;
+    } else {
+      dz = 2.f * (s - y) * s * (1.f - s) / (float)npx;
+      lterm = (double)(s - y) * (double)(s - y);
+    }
+    dzbuf[p] = dz;
+  }
+  for (int g = 0; g < C / G; ++g) {
+    float v[G];
+    if (live) {
+      load_group<T>(a8, (size_t)g * npx + p, v);
+      float d[G];
+#pragma unroll
+      for (int k = 0; k < G; ++k) d[k] = v[k] > 0.f ? dz * sw[g * G + k] : 0.f;
+      store_group<T>(d8, (size_t)g * npx + p, d);
+    } else {
+#pragma unroll
+      for (int k = 0; k < G; ++k) v[k] = 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < G; ++k) {
+      float c = dz * v[k];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+      if (lane == 0) sred[warp][g * G + k] = c;
+    }
+  }
+  {
+    float c = dz;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+    if (lane == 0) sred[warp][C] = c;
+    double l = lterm;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) l += __shfl_xor_sync(0xffffffffu, l, off);
+    if (lane == 0) sl[warp] = l;
+  }
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  for (int q = threadIdx.x; q <= C; q += blockDim.x) {
+    float s = 0.f;
+    for (int k = 0; k < nw; ++k) s += sred[k][q];
+    hpart[(size_t)blockIdx.x * (C + 1) + q] = s;
+  }
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int k = 0; k < nw; ++k) s += sl[k];
+    loss_part[blockIdx.x] = s;
+  }
+}
+
+cudaError_t launch_head_train(const void* a8, int C, int npx, const float* w9, const float* b9,
+                              const float* tgt, int loss_kind, int bf16, float* dz, void* d8,
+                              double* loss_part, float* hpart, int* nblk_out, const int* skip,
+                              cudaStream_t st) {
+  if (C > 256) return cudaErrorInvalidValue;
+  const unsigned nb = nblocks(npx, 256);
+  *nblk_out = (int)nb;
+  if (bf16)
+    k_head_train<__nv_bfloat16><<<nb, 256, 0, st>>>((const __nv_bfloat16*)a8, C, npx, w9, b9, tgt,
+                                                    loss_kind, dz, (__nv_bfloat16*)d8, loss_part,
+                                                    hpart, skip);
+  else
+    k_head_train<float><<<nb, 256, 0, st>>>((const float*)a8, C, npx, w9, b9, tgt, loss_kind, dz,
+                                            (float*)d8, loss_part, hpart, skip);
+  N2F_LAUNCH_CHECK();
+}
+
+// Ordered sums of the head partials; advances Adam's step counter and bias corrections.
+__global__ void k_step_finish(const float* __restrict__ hpart, const double* __restrict__ lpart,
+                              int nblk, int C, int npx, float* __restrict__ gw9,
+                              float* __restrict__ gb9, DevState* state, float b1, float b2) {
+  if (state->stopped) return;
+  for (int q = threadIdx.x; q <= C; q += blockDim.x) {
+    float s = 0.f;
+    for (int k = 0; k < nblk; ++k) s += hpart[(size_t)k * (C + 1) + q];
+    if (q < C)
+      gw9[q] = s;
+    else
+      gb9[0] = s;
+  }
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int k = 0; k < nblk; ++k) s += lpart[k];
+    state->loss = s / (double)npx;
+    state->t += 1;
+    state->b1t *= (double)b1;
+    state->b2t *= (double)b2;
+    state->bc1 = (float)(1.0 - state->b1t);
+    state->bc2 = (float)(1.0 - state->b2t);
+  }
+}
+
+cudaError_t launch_step_finish(const float* hpart, const double* loss_part, int nblk, int C,
+                               int npx, float* gw9, float* gb9, DevState* state, float b1,
+                               float b2, cudaStream_t st) {
+  k_step_finish<<<1, 256, 0, st>>>(hpart, loss_part, nblk, C, npx, gw9, gb9, state, b1, b2);
+  N2F_LAUNCH_CHECK();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Validation head (Methods: after each epoch the full noisy image goes through the network
+// and the MSE against the noisy image is taken). V = sigmoid(z); (V - x)^2 summed in FP64.
+template <typename T>
+__global__ void __launch_bounds__(256) k_head_val(const T* __restrict__ a8, int C, int npx,
+                                                  const float* __restrict__ w9,
+                                                  const float* __restrict__ b9,
+                                                  const float* __restrict__ x,
+                                                  float* __restrict__ V,
+                                                  double* __restrict__ mse_part, const int* skip) {
+  if (skip && *skip) return;
+  constexpr int G = CGTraits<T>::G;
+  __shared__ float sw[256];
+  __shared__ double sl[8];
+  for (int i = threadIdx.x; i < C; i += blockDim.x) sw[i] = w9[i];
+  __syncthreads();
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  double e2 = 0.0;
+  if (p < npx) {
+    float z = b9[0];
+    for (int g = 0; g < C / G; ++g) {
+      float v[G];
+      load_group<T>(a8, (size_t)g * npx + p, v);
+#pragma unroll
+      for (int k = 0; k < G; ++k) z += sw[g * G + k] * v[k];
+    }
+    const float s = sigmoid_f(z);
+    V[p] = s;
+    const double e = (double)s - (double)x[p];
+    e2 = e * e;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) e2 += __shfl_xor_sync(0xffffffffu, e2, off);
+  if ((threadIdx.x & 31) == 0) sl[threadIdx.x >> 5] = e2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += sl[k];
+    mse_part[blockIdx.x] = s;
+  }
+}
+
+cudaError_t launch_head_val(const void* a8, int C, int npx, const float* w9, const float* b9,
+                            const float* x, int bf16, float* V, double* mse_part, int* nblk_out,
+                            const int* skip, cudaStream_t st) {
+  if (C > 256) return cudaErrorInvalidValue;
+  const unsigned nb = nblocks(npx, 256);
+  *nblk_out = (int)nb;
+  if (bf16)
+    k_head_val<__nv_bfloat16><<<nb, 256, 0, st>>>((const __nv_bfloat16*)a8, C, npx, w9, b9, x, V,
+                                                  mse_part, skip);
+  else
+    k_head_val<float><<<nb, 256, 0, st>>>((const float*)a8, C, npx, w9, b9, x, V, mse_part, skip);
+  N2F_LAUNCH_CHECK();
+}
+
+// Stop rule (Methods: terminate once one hundred epochs pass without improving the best
+// validation score). Strict improvement; the first epoch always sets the best.
+__global__ void k_val_decide(const double* __restrict__ part, int nblk, double npx,
+                             DevState* state, int fixed_mode) {
+  __shared__ double sp[256];
+  double s = 0.0;
+  for (int k = threadIdx.x; k < nblk; k += blockDim.x) s += part[k];
+  sp[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  if (!fixed_mode && state->stopped) {
+    state->decision = -1;
+    return;
+  }
+  double tot = 0.0;
+  for (int k = 0; k < (int)blockDim.x; ++k) tot += sp[k];
+  const double mse = tot / npx;
+  state->last_mse = mse;
+  if (fixed_mode) {
+    state->decision = -1;
+    return;
+  }
+  if (!isfinite(mse)) {
+    state->stopped = 3;
+    state->decision = -1;
+    return;
+  }
+  state->epoch += 1;
+  if (mse < state->best) {
+    state->best = mse;
+    state->since = 0;
+    state->decision = 1;
+  } else {
+    state->since += 1;
+    state->decision = 0;
+  }
+  if (state->since >= (state->incl_best ? state->patience - 1 : state->patience))
+    state->stopped = 1;
+  else if (state->max_epochs > 0 && state->epoch >= state->max_epochs)
+    state->stopped = 2;
+}
+
+cudaError_t launch_val_decide(const double* mse_part, int nblk, size_t npx, DevState* state,
+                              int fixed_mode, cudaStream_t st) {
+  k_val_decide<<<1, 256, 0, st>>>(mse_part, nblk, (double)npx, state, fixed_mode);
+  N2F_LAUNCH_CHECK();
+}
+
+// Output averaging (Methods: the output is the average of the last one hundred validation
+// outputs). The running sum restarts at every new best, so at the stop it holds exactly the
+// outputs of the epochs after the best.
+__global__ void k_val_accum(const float* __restrict__ V, float* __restrict__ S,
+                            float* __restrict__ Vbest, size_t n, const DevState* __restrict__ st) {
+  const int d = st->decision;
+  if (d < 0) return;
+  const int incl = st->incl_best;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const float v = V[i];
+    if (d == 1) {
+      Vbest[i] = v;
+      S[i] = incl ? v : 0.f;
+    } else {
+      S[i] += v;
+    }
+  }
+}
+
+cudaError_t launch_val_accum(const float* V, float* S, float* Vbest, size_t n,
+                             const DevState* state, cudaStream_t st) {
+  unsigned g = nblocks(n, 256);
+  if (g > 152u * 8) g = 152u * 8;
+  k_val_accum<<<g, 256, 0, st>>>(V, S, Vbest, n, state);
+  N2F_LAUNCH_CHECK();
+}
+
+__global__ void k_result(const float* __restrict__ V, const float* __restrict__ S,
+                         const float* __restrict__ Vbest, float* __restrict__ out, size_t n,
+                         const DevState* __restrict__ st, int fixed_mode) {
+  int mode;  // 0: V, 1: S / cnt, 2: Vbest
+  float cnt = 1.f;
+  if (fixed_mode) {
+    mode = 0;
+  } else if (st->stopped == 1) {
+    mode = 1;
+    cnt = (float)st->patience;
+  } else {
+    const int c = st->since + (st->incl_best ? 1 : 0);
+    mode = c > 0 ? 1 : 2;
+    cnt = (float)c;
+  }
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    out[i] = mode == 0 ? V[i] : (mode == 1 ? S[i] / cnt : Vbest[i]);
+}
+
+cudaError_t launch_result(const float* V, const float* S, const float* Vbest, float* out, size_t n,
+                          const DevState* state, int fixed_mode, cudaStream_t st) {
+  unsigned g = nblocks(n, 256);
+  if (g > 152u * 8) g = 152u * 8;
+  k_result<<<g, 256, 0, st>>>(V, S, Vbest, out, n, state, fixed_mode);
+  N2F_LAUNCH_CHECK();
+}
+
+}  // namespace n2f

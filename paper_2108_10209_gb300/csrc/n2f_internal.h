@@ -1,0 +1,145 @@
+// Internal declarations of the sm_103a Noise2Fast library (not part of the C ABI).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/n2f.h"
+
+namespace n2f {
+
+constexpr int kLayers = 8;  // eight 3x3 conv + ReLU layers, then the 1x1 + sigmoid head
+
+// Flat parameter vector in the canonical order: for l = 1..8: W_l[C_out][C_in][3][3], b_l;
+// then head w[C_8], b. Kernels read weights from packed copies (see Packing), never from it.
+struct NetShape {
+  int widths[kLayers];
+  size_t w_off[kLayers + 1], b_off[kLayers + 1], count;
+  int cin(int l) const { return l == 0 ? 1 : widths[l - 1]; }
+  int cmax() const {
+    int m = 0;
+    for (int l = 0; l < kLayers; ++l) m = widths[l] > m ? widths[l] : m;
+    return m;
+  }
+  int csum() const {
+    int s = 0;
+    for (int l = 0; l < kLayers; ++l) s += widths[l];
+    return s;
+  }
+  void init(int which);
+};
+
+// Device-resident per-job scalars (updated only by kernels, so CUDA graphs can replay epochs).
+struct DevState {
+  double best;      // best validation MSE (+inf before the first epoch)
+  double last_mse;  // MSE of the last validation
+  double loss;      // training loss of the last step
+  int since;        // epochs since the best
+  int epoch;        // validations done under the stop rule
+  int stopped;      // 0 running, 1 rule fired, 2 max_epochs reached, 3 non-finite
+  int t;            // Adam steps taken
+  int decision;     // last validation: 1 new best, 0 joins the window, -1 ignored
+  int patience, max_epochs, incl_best;
+  float bc1, bc2;   // Adam bias corrections 1 - beta^t of the current step
+  double b1t, b2t;  // beta1^t, beta2^t
+};
+
+// Packed weight copies written by the init/Adam kernels, one per layer l = 0..7:
+//   fwd : [C_in/8][9][8][C_out] f32 (tap = 3*ky + kx; layer 1: [C_out][9]) -- SIMT forward
+//   dgr : [C_out/8][9][8][C_in] f32, tap rotated to 8 - tap                -- SIMT dgrad
+//   tcf/tcd : the same two matrices in the tensor-core operand order (tc_layout.cuh), bf16,
+//             or float32 TF32-hi parts with the residuals in tcf_lo/tcd_lo (3xTF32 form)
+struct PackArgs {
+  float* theta;
+  float* fwd[kLayers];
+  float* dgr[kLayers];
+  void* tcf[kLayers];
+  void* tcd[kLayers];
+  float* tcf_lo[kLayers];
+  float* tcd_lo[kLayers];
+  int widths[kLayers];
+  unsigned long long w_off[kLayers + 1], b_off[kLayers + 1];
+  unsigned long long count;
+  int tc_bf16;  // tensor-core copies in bf16 (1) or f32 (0); tcf[l] == nullptr: none
+};
+
+// ---- kernel launchers (kernels_*.cu); all enqueue on `st` and return cudaError_t ----------
+cudaError_t launch_gather(const float* x, int H, int W, float* ue, float* uo, float* le, float* lo,
+                          cudaStream_t st);
+cudaError_t launch_u16_to_f32(const uint16_t* in, float* out, size_t n, cudaStream_t st);
+cudaError_t launch_init_params(float* theta, const NetShape& net, uint64_t seed, cudaStream_t st);
+cudaError_t launch_adam(const PackArgs& pa, const float* grad, float* m, float* v, float lr,
+                        float b1, float b2, float eps, const DevState* state, int update,
+                        cudaStream_t st);
+cudaError_t launch_pack_layer(const float* w, int cin, int cout, float* fwd, float* dgr, void* tcf,
+                              void* tcd, float* tcf_lo, float* tcd_lo, int tc_bf16,
+                              cudaStream_t st);
+cudaError_t launch_pack_cg(const float* nchw, int C, int H, int W, int bf16, void* cg,
+                           cudaStream_t st);
+cudaError_t launch_unpack_cg(const void* cg, int C, int H, int W, int bf16, float* nchw,
+                             cudaStream_t st);
+cudaError_t launch_unpack_cg_f64(const void* cg, int C, int H, int W, int bf16, double* out,
+                                 cudaStream_t st);
+
+// First layer (C_in = 1): image plane -> CG map with bias + ReLU.
+cudaError_t launch_conv1_fwd(const float* img, int H, int W, const float* w /*[C][9]*/,
+                             const float* b, int C, int bf16, void* out, const int* skip,
+                             cudaStream_t st);
+// First layer weight gradient: partials then ordered reduce into grad (canonical order).
+cudaError_t launch_conv1_wgrad(const void* dout, const float* img, int H, int W, int C, int bf16,
+                               float* part, size_t part_cap, float* gw, float* gb,
+                               const int* skip, cudaStream_t st);
+
+// SIMT implicit-GEMM 3x3 layers (C_in, C_out multiples of 8).
+// mode 0: out = ReLU(conv(in, wk) + b);  mode 1: out = conv(in, wk) * [mask > 0]
+// wk: [C_in/8][9][8][C_out] f32 (for dgrad: the rotated transpose, "C_out" = layer C_in)
+cudaError_t launch_conv_simt(int mode, int bf16, const void* in, int cin, int cout, int H, int W,
+                             const float* wk, const float* b, const void* mask, void* out,
+                             const int* skip, cudaStream_t st);
+// SIMT weight gradient: dW[o][c][ky][kx] (canonical order) and db[o] from CG maps.
+cudaError_t launch_wgrad_simt(int bf16, const void* dout, const void* in, int cin, int cout, int H,
+                              int W, float* part, size_t part_cap, float* gw, float* gb,
+                              const int* skip, cudaStream_t st);
+
+// Tensor-core (tcgen05) kernels; return cudaErrorNotSupported when a shape is not covered.
+bool tc_supported(int cin, int cout);
+cudaError_t launch_conv_tc(int mode, int bf16, const void* in, int cin, int cout, int H, int W,
+                           const void* wtc, const float* b, const void* mask, void* out,
+                           const int* skip, cudaStream_t st);
+cudaError_t launch_wgrad_tc(int bf16, const void* dout, const void* in, int cin, int cout, int H,
+                            int W, float* part, size_t part_cap, float* gw, float* gb,
+                            const int* skip, cudaStream_t st);
+size_t tc_weight_elems(int cin, int cout);  // elements of one packed tensor-core weight copy
+
+// Head (1x1 conv + sigmoid), training: z, loss partials, dL/dz, delta_8, head-grad partials.
+cudaError_t launch_head_train(const void* a8, int C, int npx, const float* w9, const float* b9,
+                              const float* tgt, int loss_kind, int bf16, float* dz, void* d8,
+                              double* loss_part, float* hpart, int* nblk_out, const int* skip,
+                              cudaStream_t st);
+// Sums head-grad and loss partials in a fixed order, advances the Adam step counter.
+cudaError_t launch_step_finish(const float* hpart, const double* loss_part, int nblk, int C,
+                               int npx, float* gw9, float* gb9, DevState* state, float b1,
+                               float b2, cudaStream_t st);
+// Head, validation: V = sigmoid(z), FP64 partial sums of (V - x)^2.
+cudaError_t launch_head_val(const void* a8, int C, int npx, const float* w9, const float* b9,
+                            const float* x, int bf16, float* V, double* mse_part, int* nblk_out,
+                            const int* skip, cudaStream_t st);
+// Stop rule: reduce the MSE partials (fixed order), update best/since/epoch/stopped.
+cudaError_t launch_val_decide(const double* mse_part, int nblk, size_t npx, DevState* state,
+                              int fixed_mode, cudaStream_t st);
+// Output averaging: S = 0 / V (new best) or S += V; Vbest = V on a new best.
+cudaError_t launch_val_accum(const float* V, float* S, float* Vbest, size_t n,
+                             const DevState* state, cudaStream_t st);
+// Result: S / patience, S / count, Vbest or V (fixed-step mode).
+cudaError_t launch_result(const float* V, const float* S, const float* Vbest, float* out, size_t n,
+                          const DevState* state, int fixed_mode, cudaStream_t st);
+
+// Count of kernel launches made by this thread's current owner (see LaunchCounter).
+extern thread_local uint64_t* tl_launch_counter;
+inline void count_launch(int n = 1) {
+  if (tl_launch_counter) *tl_launch_counter += (uint64_t)n;
+}
+
+}  // namespace n2f

@@ -1,0 +1,42 @@
+// Global layout of the tensor-core weight operand (written by the Adam/pack kernel, read by
+// the tcgen05 convolution kernels with one bulk copy per pipeline stage).
+//
+// The GEMM of a 3x3 layer is D[px][n] = sum_k A[px][k] * B[n][k] with k = tap * C_in + c.
+// B is stored as a sequence of stage images; one stage = NT output rows x 9 taps x KC input
+// channels, laid out exactly as the K-major, no-swizzle shared-memory operand expects:
+//   [tap][k-slab of 16 bytes][row (NT)][16 bytes]
+// so that 8 rows x 16 bytes form one contiguous 128-byte core matrix. Stages are ordered
+// (n-tile, channel chunk). The float32 (3xTF32) form keeps two such arrays, hi and lo.
+#pragma once
+#include <stddef.h>
+
+namespace n2f {
+
+struct TcCfg {
+  int NT;  // output rows (N) per CTA
+  int KC;  // input channels per pipeline stage
+  int GE;  // elements per 16 bytes
+};
+
+__host__ __device__ __forceinline__ TcCfg tc_cfg(int cin, int cout, int bf16) {
+  TcCfg c;
+  c.GE = bf16 ? 8 : 4;
+  c.NT = bf16 ? (cout < 256 ? cout : 256) : (cout < 128 ? cout : 128);
+  c.KC = bf16 ? 16 : 8;
+  (void)cin;
+  return c;
+}
+
+// Element offset of B[r][tap * cin + c] in the packed array.
+__host__ __device__ __forceinline__ size_t tc_index_cfg(const TcCfg& f, int cin, int r, int tap,
+                                                         int c) {
+  const int nchunks = cin / f.KC;
+  const int nslab = f.KC / f.GE;
+  const int nt = r / f.NT, rr = r % f.NT;
+  const int chunk = c / f.KC, cc = c % f.KC;
+  const int slab = cc / f.GE, e = cc % f.GE;
+  const size_t stage = (size_t)nt * nchunks + chunk;
+  return (((stage * 9 + tap) * nslab + slab) * f.NT + rr) * f.GE + e;
+}
+
+}  // namespace n2f

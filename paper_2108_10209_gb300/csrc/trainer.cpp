@@ -1,0 +1,376 @@
+// Step executor: one job's device state and the kernel sequence of a training step, a
+// validation pass and an epoch (Methods, "Noise2Fast Implementation Details").
+#include "trainer.h"
+
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+namespace n2f {
+
+thread_local std::string tl_error;
+
+int set_cuda_error(cudaError_t e, const char* where) {
+  tl_error = std::string(where) + ": " + cudaGetErrorString(e);
+  return N2F_EDEVICE;
+}
+
+void NetShape::init(int which) {
+  for (int l = 0; l < kLayers; ++l) {
+    static const int plit[kLayers] = {32, 32, 64, 64, 128, 128, 256, 256};
+    widths[l] = which == N2F_WIDTHS_W64 ? 64 : plit[l];
+  }
+  size_t n = 0;
+  int cin = 1;
+  for (int l = 0; l < kLayers; ++l) {
+    w_off[l] = n;
+    n += (size_t)widths[l] * cin * 9;
+    b_off[l] = n;
+    n += widths[l];
+    cin = widths[l];
+  }
+  w_off[kLayers] = n;
+  b_off[kLayers] = n + cin;
+  count = n + cin + 1;
+}
+
+void* dev_alloc(const Allocator& a, size_t bytes) {
+  if (a.alloc) return a.alloc(bytes, a.user);
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void dev_free(const Allocator& a, void* p, size_t bytes) {
+  if (!p) return;
+  if (a.free)
+    a.free(p, bytes, a.user);
+  else
+    cudaFree(p);
+}
+
+namespace {
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct Carver {
+  size_t off = 0;
+  char* base = nullptr;
+  template <typename T>
+  T* take(size_t elems) {
+    off = align_up(off, 256);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += elems * sizeof(T);
+    return p;
+  }
+};
+
+}  // namespace
+
+static int layer_engine(const Trainer* t, int l) {
+  if (l == 0) return N2F_ENGINE_SIMT;
+  const int e = t->prm.engine;
+  const bool tc = tc_supported(t->net.cin(l), t->net.widths[l]);
+  if (e == N2F_ENGINE_SIMT) return N2F_ENGINE_SIMT;
+  if (e == N2F_ENGINE_TC) return tc ? N2F_ENGINE_TC : -1;
+  return tc ? N2F_ENGINE_TC : N2F_ENGINE_SIMT;
+}
+
+// Carves every buffer out of one slab; with base == nullptr it only measures.
+static size_t layout(Trainer* t, char* base) {
+  Carver c;
+  c.base = base;
+  const NetShape& net = t->net;
+  const size_t es = t->bf16 ? 2 : 4;
+  t->x = c.take<float>(t->N);
+  for (int k = 0; k < 4; ++k) t->sub[k] = c.take<float>((size_t)t->ph[k] * t->pw[k]);
+  t->theta = c.take<float>(net.count);
+  t->grad = c.take<float>(net.count);
+  t->m = c.take<float>(net.count);
+  t->v = c.take<float>(net.count);
+  memset(&t->pa, 0, sizeof(t->pa));
+  for (int l = 0; l < kLayers; ++l) {
+    const size_t nw = (size_t)net.widths[l] * net.cin(l) * 9;
+    t->pa.fwd[l] = c.take<float>(nw);
+    t->pa.dgr[l] = l > 0 ? c.take<float>(nw) : nullptr;
+    if (l > 0 && t->engine[l] == N2F_ENGINE_TC) {
+      t->pa.tcf[l] = c.take<char>(nw * es);
+      t->pa.tcd[l] = c.take<char>(nw * es);
+      if (!t->bf16) {
+        t->pa.tcf_lo[l] = c.take<float>(nw);
+        t->pa.tcd_lo[l] = c.take<float>(nw);
+      }
+    }
+  }
+  // activations / deltas (training) alias the validation ping-pong buffers
+  const size_t Cmax = net.cmax(), Csum = net.csum();
+  const size_t train_elems = Csum * t->maxP + (t->keep_deltas ? Csum : 2 * Cmax) * t->maxP;
+  const size_t val_elems = 2 * Cmax * t->N;
+  char* region = c.take<char>(std::max(train_elems, val_elems) * es);
+  if (base) {
+    size_t o = 0;
+    for (int l = 0; l < kLayers; ++l) {
+      t->act[l] = region + o * es;
+      o += (size_t)net.widths[l] * t->maxP;
+    }
+    if (t->keep_deltas) {
+      for (int l = 0; l < kLayers; ++l) {
+        t->dkeep[l] = region + o * es;
+        o += (size_t)net.widths[l] * t->maxP;
+      }
+      t->dl[0] = t->dl[1] = nullptr;
+    } else {
+      t->dl[0] = region + o * es;
+      t->dl[1] = region + (o + Cmax * t->maxP) * es;
+    }
+    t->vb[0] = region;
+    t->vb[1] = region + Cmax * t->N * es;
+  }
+  t->dz = c.take<float>(t->maxP);
+  t->V = c.take<float>(t->N);
+  t->S = c.take<float>(t->N);
+  t->Vbest = c.take<float>(t->N);
+  t->out = c.take<float>(t->N);
+  t->nblk_max = (int)((std::max(t->maxP, t->N) + 255) / 256);
+  t->lpart = c.take<double>(t->nblk_max);
+  t->mpart = c.take<double>(t->nblk_max);
+  t->hpart = c.take<float>((size_t)t->nblk_max * (Cmax + 1));
+  t->wpart_cap = (size_t)6 << 20;
+  t->wpart = c.take<float>(t->wpart_cap);
+  t->state = c.take<DevState>(1);
+  t->in_u16 = c.take<uint16_t>(t->want_u16 ? t->N : 0);
+  return align_up(c.off, 256);
+}
+
+size_t trainer_bytes(int H, int W, const n2f_params* p, int keep_deltas) {
+  Trainer t;
+  if (trainer_configure(&t, H, W, p, keep_deltas) != N2F_OK) return 0;
+  return layout(&t, nullptr);
+}
+
+int trainer_configure(Trainer* t, int H, int W, const n2f_params* p, int keep_deltas) {
+  t->prm = *p;
+  t->H = H;
+  t->W = W;
+  t->N = (size_t)H * W;
+  t->ph[0] = t->ph[1] = H;
+  t->pw[0] = t->pw[1] = W / 2;
+  t->ph[2] = t->ph[3] = H / 2;
+  t->pw[2] = t->pw[3] = W;
+  t->maxP = std::max((size_t)H * (W / 2), (size_t)(H / 2) * W);
+  t->net.init(p->widths);
+  t->bf16 = p->precision == N2F_BF16;
+  t->keep_deltas = keep_deltas;
+  t->fixed_mode = p->fixed_steps >= 0;
+  for (int l = 0; l < kLayers; ++l) {
+    t->engine[l] = layer_engine(t, l);
+    if (t->engine[l] < 0) return N2F_ENOTSUP;
+  }
+  return N2F_OK;
+}
+
+int trainer_init(Trainer* t, const Allocator& al, cudaStream_t st, int want_u16) {
+  t->al = al;
+  t->st = st;
+  t->want_u16 = want_u16;
+  t->slab_bytes = layout(t, nullptr);
+  t->slab = (char*)dev_alloc(al, t->slab_bytes);
+  if (!t->slab) {
+    tl_error = "device allocation of the job state failed";
+    return N2F_ENOMEM;
+  }
+  layout(t, t->slab);
+  PackArgs& pa = t->pa;
+  pa.theta = t->theta;
+  for (int l = 0; l < kLayers; ++l) pa.widths[l] = t->net.widths[l];
+  for (int l = 0; l <= kLayers; ++l) {
+    pa.w_off[l] = t->net.w_off[l];
+    pa.b_off[l] = t->net.b_off[l];
+  }
+  pa.count = t->net.count;
+  pa.tc_bf16 = t->bf16;
+  return N2F_OK;
+}
+
+void trainer_release(Trainer* t) {
+  if (t->slab) dev_free(t->al, t->slab, t->slab_bytes);
+  t->slab = nullptr;
+}
+
+#define CK(expr)                                            \
+  do {                                                      \
+    cudaError_t _e = (expr);                                \
+    if (_e != cudaSuccess) return set_cuda_error(_e, #expr); \
+  } while (0)
+
+// Image already in t->x (or t->in_u16): gather, initial weights, packed copies, state.
+int trainer_start(Trainer* t, int from_u16) {
+  LaunchScope ls(&t->launches);
+  cudaStream_t st = t->st;
+  if (from_u16) CK(launch_u16_to_f32(t->in_u16, t->x, t->N, st));
+  CK(launch_gather(t->x, t->H, t->W, t->sub[0], t->sub[1], t->sub[2], t->sub[3], st));
+  CK(launch_init_params(t->theta, t->net, t->prm.seed, st));
+  CK(cudaMemsetAsync(t->m, 0, t->net.count * sizeof(float), st));
+  CK(cudaMemsetAsync(t->v, 0, t->net.count * sizeof(float), st));
+  CK(cudaMemsetAsync(t->grad, 0, t->net.count * sizeof(float), st));
+  CK(cudaMemsetAsync(t->S, 0, t->N * sizeof(float), st));
+  CK(cudaMemsetAsync(t->Vbest, 0, t->N * sizeof(float), st));
+  CK(cudaMemsetAsync(t->V, 0, t->N * sizeof(float), st));
+  DevState s;
+  memset(&s, 0, sizeof(s));
+  s.best = INFINITY;
+  s.patience = (int)t->prm.patience;
+  s.max_epochs = (int)t->prm.max_epochs;
+  s.incl_best = t->prm.incl_best;
+  s.b1t = 1.0;
+  s.b2t = 1.0;
+  s.bc1 = s.bc2 = 1.f;
+  s.decision = -1;
+  t->hstate_init = s;
+  CK(cudaMemcpyAsync(t->state, &t->hstate_init, sizeof(DevState), cudaMemcpyHostToDevice, st));
+  CK(launch_adam(t->pa, t->grad, t->m, t->v, 0.f, 0.f, 0.f, 0.f, t->state, 0, st));
+  return N2F_OK;
+}
+
+int trainer_repack(Trainer* t) {
+  LaunchScope ls(&t->launches);
+  CK(launch_adam(t->pa, t->grad, t->m, t->v, 0.f, 0.f, 0.f, 0.f, t->state, 0, t->st));
+  return N2F_OK;
+}
+
+static int conv_layer(Trainer* t, int l, const void* in, void* out, int H, int W,
+                      const int* skip) {
+  const int cin = t->net.cin(l), cout = t->net.widths[l];
+  const float* b = t->theta + t->net.b_off[l];
+  if (l == 0) {
+    CK(launch_conv1_fwd((const float*)in, H, W, t->pa.fwd[0], b, cout, t->bf16, out, skip, t->st));
+  } else if (t->engine[l] == N2F_ENGINE_TC) {
+    CK(launch_conv_tc(0, t->bf16, in, cin, cout, H, W, t->pa.tcf[l], b, nullptr, out, skip,
+                      t->st));
+  } else {
+    CK(launch_conv_simt(0, t->bf16, in, cin, cout, H, W, t->pa.fwd[l], b, nullptr, out, skip,
+                        t->st));
+  }
+  return N2F_OK;
+}
+
+int trainer_step(Trainer* t, int pair) {
+  LaunchScope ls(&t->launches);
+  const int h = t->ph[pair], w = t->pw[pair];
+  const int npx = h * w;
+  const NetShape& net = t->net;
+  const int* skip = t->fixed_mode ? nullptr : &t->state->stopped;
+  const float* in = t->sub[pair];
+  const float* tgt = t->sub[pair ^ 1];  // Methods table: even <-> odd of the same kind
+  t->last_pair = pair;
+  // forward, keeping every post-ReLU map
+  const void* cur = in;
+  for (int l = 0; l < kLayers; ++l) {
+    int rc = conv_layer(t, l, cur, t->act[l], h, w, skip);
+    if (rc) return rc;
+    cur = t->act[l];
+  }
+  // head: loss, dL/dz, delta_8, head-grad partials
+  const int C8 = net.widths[kLayers - 1];
+  void* d8 = t->keep_deltas ? t->dkeep[kLayers - 1] : t->dl[0];
+  int nblk = 0;
+  CK(launch_head_train(t->act[kLayers - 1], C8, npx, t->theta + net.w_off[kLayers],
+                       t->theta + net.b_off[kLayers], tgt, t->prm.loss, t->bf16, t->dz, d8,
+                       t->lpart, t->hpart, &nblk, skip, t->st));
+  CK(launch_step_finish(t->hpart, t->lpart, nblk, C8, npx, t->grad + net.w_off[kLayers],
+                        t->grad + net.b_off[kLayers], t->state, t->prm.beta1, t->prm.beta2,
+                        t->st));
+  // backward through the 3x3 layers
+  void* dcur = d8;
+  int pp = 0;
+  for (int l = kLayers - 1; l >= 0; --l) {
+    const int cin = net.cin(l), cout = net.widths[l];
+    float* gw = t->grad + net.w_off[l];
+    float* gb = t->grad + net.b_off[l];
+    if (l == 0) {
+      CK(launch_conv1_wgrad(dcur, in, h, w, cout, t->bf16, t->wpart, t->wpart_cap, gw, gb, skip,
+                            t->st));
+      break;
+    }
+    if (t->engine[l] == N2F_ENGINE_TC) {
+      CK(launch_wgrad_tc(t->bf16, dcur, t->act[l - 1], cin, cout, h, w, t->wpart, t->wpart_cap,
+                         gw, gb, skip, t->st));
+    } else {
+      CK(launch_wgrad_simt(t->bf16, dcur, t->act[l - 1], cin, cout, h, w, t->wpart,
+                           t->wpart_cap, gw, gb, skip, t->st));
+    }
+    void* dnext = t->keep_deltas ? t->dkeep[l - 1] : t->dl[pp ^ 1];
+    if (t->engine[l] == N2F_ENGINE_TC) {
+      CK(launch_conv_tc(1, t->bf16, dcur, cout, cin, h, w, t->pa.tcd[l], nullptr, t->act[l - 1],
+                        dnext, skip, t->st));
+    } else {
+      CK(launch_conv_simt(1, t->bf16, dcur, cout, cin, h, w, t->pa.dgr[l], nullptr,
+                          t->act[l - 1], dnext, skip, t->st));
+    }
+    dcur = dnext;
+    pp ^= 1;
+  }
+  CK(launch_adam(t->pa, t->grad, t->m, t->v, t->prm.lr, t->prm.beta1, t->prm.beta2, t->prm.eps,
+                 t->state, 1, t->st));
+  t->steps_enqueued += 1;
+  return N2F_OK;
+}
+
+int trainer_validate(Trainer* t) {
+  LaunchScope ls(&t->launches);
+  const NetShape& net = t->net;
+  const int* skip = t->fixed_mode ? nullptr : &t->state->stopped;
+  const void* cur = t->x;
+  int pp = 0;
+  for (int l = 0; l < kLayers; ++l) {
+    int rc = conv_layer(t, l, cur, t->vb[pp], t->H, t->W, skip);
+    if (rc) return rc;
+    cur = t->vb[pp];
+    pp ^= 1;
+  }
+  int nblk = 0;
+  CK(launch_head_val(cur, net.widths[kLayers - 1], (int)t->N, t->theta + net.w_off[kLayers],
+                     t->theta + net.b_off[kLayers], t->x, t->bf16, t->V, t->mpart, &nblk, skip,
+                     t->st));
+  CK(launch_val_decide(t->mpart, nblk, t->N, t->state, t->fixed_mode, t->st));
+  if (!t->fixed_mode) CK(launch_val_accum(t->V, t->S, t->Vbest, t->N, t->state, t->st));
+  return N2F_OK;
+}
+
+int trainer_epoch(Trainer* t) {
+  for (int k = 0; k < 4; ++k) {
+    int rc = trainer_step(t, k);
+    if (rc) return rc;
+  }
+  return trainer_validate(t);
+}
+
+int trainer_finish(Trainer* t) {
+  LaunchScope ls(&t->launches);
+  CK(launch_result(t->V, t->S, t->Vbest, t->out, t->N, t->state, t->fixed_mode, t->st));
+  return N2F_OK;
+}
+
+int trainer_read_state(Trainer* t, DevState* s) {
+  CK(cudaMemcpyAsync(s, t->state, sizeof(DevState), cudaMemcpyDeviceToHost, t->st));
+  CK(cudaStreamSynchronize(t->st));
+  return N2F_OK;
+}
+
+void fill_status(const Trainer* t, const DevState& s, n2f_status* st) {
+  st->epoch = (uint32_t)s.epoch;
+  st->steps = (uint32_t)s.t;
+  st->since = (uint32_t)s.since;
+  st->stopped = (uint32_t)(s.stopped == 3 ? 0 : s.stopped);
+  st->H = (uint32_t)t->H;
+  st->W = (uint32_t)t->W;
+  st->best_mse = s.best;
+  st->last_loss = s.loss;
+}
+
+}  // namespace n2f

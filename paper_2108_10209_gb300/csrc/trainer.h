@@ -1,0 +1,75 @@
+// Step executor of one Noise2Fast job (host side).
+#pragma once
+#include <string>
+
+#include "n2f_internal.h"
+
+namespace n2f {
+
+extern thread_local std::string tl_error;
+int set_cuda_error(cudaError_t e, const char* where);
+
+struct Allocator {
+  n2f_alloc_fn alloc = nullptr;
+  n2f_free_fn free = nullptr;
+  void* user = nullptr;
+};
+void* dev_alloc(const Allocator& a, size_t bytes);
+void dev_free(const Allocator& a, void* p, size_t bytes);
+
+// Counts the kernels enqueued while it is alive into *dst.
+struct LaunchScope {
+  uint64_t* prev;
+  explicit LaunchScope(uint64_t* dst) : prev(tl_launch_counter) { tl_launch_counter = dst; }
+  ~LaunchScope() { tl_launch_counter = prev; }
+};
+
+struct Trainer {
+  NetShape net;
+  n2f_params prm;
+  int H = 0, W = 0;
+  size_t N = 0;
+  int ph[4], pw[4];  // pair sizes: up (H x W/2) twice, left (H/2 x W) twice
+  size_t maxP = 0;
+  int bf16 = 0, keep_deltas = 0, fixed_mode = 0, want_u16 = 0;
+  int engine[kLayers];
+  cudaStream_t st = nullptr;
+  Allocator al;
+  char* slab = nullptr;
+  size_t slab_bytes = 0;
+  uint64_t launches = 0;
+  // device buffers (views into the slab)
+  float *x = nullptr, *sub[4] = {nullptr, nullptr, nullptr, nullptr};
+  float *theta = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
+  PackArgs pa;
+  void* act[kLayers] = {};
+  void* dkeep[kLayers] = {};
+  void* dl[2] = {};
+  void* vb[2] = {};
+  float *dz = nullptr, *V = nullptr, *S = nullptr, *Vbest = nullptr, *out = nullptr;
+  double *lpart = nullptr, *mpart = nullptr;
+  float* hpart = nullptr;
+  float* wpart = nullptr;
+  size_t wpart_cap = 0;
+  int nblk_max = 0;
+  DevState* state = nullptr;
+  uint16_t* in_u16 = nullptr;
+  DevState hstate_init;
+  int last_pair = 0;
+  uint64_t steps_enqueued = 0;
+};
+
+int trainer_configure(Trainer* t, int H, int W, const n2f_params* p, int keep_deltas);
+size_t trainer_bytes(int H, int W, const n2f_params* p, int keep_deltas);
+int trainer_init(Trainer* t, const Allocator& al, cudaStream_t st, int want_u16);
+void trainer_release(Trainer* t);
+int trainer_start(Trainer* t, int from_u16);
+int trainer_repack(Trainer* t);
+int trainer_step(Trainer* t, int pair);
+int trainer_validate(Trainer* t);
+int trainer_epoch(Trainer* t);
+int trainer_finish(Trainer* t);
+int trainer_read_state(Trainer* t, DevState* s);
+void fill_status(const Trainer* t, const DevState& s, n2f_status* st);
+
+}  // namespace n2f

@@ -1,0 +1,391 @@
+"""Python binding of the C ABI in ``include/n2f.h`` (ctypes; argument marshalling only).
+
+Every step of the denoising path runs in ``libn2f.so``; this module only converts Python
+arguments (numpy arrays, torch CUDA tensors, streams) into the plain pointers and sizes the
+C functions take. If the library has not been built, importing this module raises: there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libn2f.so")
+
+N2F_OK, N2F_EINVAL, N2F_ETOOBIG, N2F_EAGAIN, N2F_ENOENT = 0, -1, -2, -3, -4
+N2F_ETIMEDOUT, N2F_ENONFINITE, N2F_EDEVICE, N2F_ENOMEM, N2F_ECANCELED, N2F_ENOTSUP = (
+    -5, -6, -7, -8, -9, -10)
+N2F_FP32, N2F_BF16 = 0, 1
+N2F_LOSS_BCE, N2F_LOSS_MSE = 0, 1
+N2F_WIDTHS_PLIT, N2F_WIDTHS_W64 = 0, 1
+N2F_ENGINE_AUTO, N2F_ENGINE_SIMT, N2F_ENGINE_TC = 0, 1, 2
+N2F_QUEUED, N2F_RUNNING, N2F_DONE, N2F_FAILED, N2F_CANCELED = range(5)
+(N2F_X_THETA, N2F_X_GRAD, N2F_X_ADAM_M, N2F_X_ADAM_V, N2F_X_ACT, N2F_X_DELTA) = range(6)
+N2F_X_DZ, N2F_X_PAIR, N2F_X_VAL, N2F_X_SUM, N2F_X_OUT = 7, 8, 9, 10, 11
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
+
+
+class Config(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("device", C.c_int), ("hbm_budget_bytes", C.c_uint64),
+                ("max_slots", C.c_uint32), ("lookahead", C.c_uint32), ("alloc", ALLOC_FN),
+                ("free", FREE_FN), ("alloc_user", C.c_void_p)]
+
+
+class Params(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("lr", C.c_float), ("beta1", C.c_float),
+                ("beta2", C.c_float), ("eps", C.c_float), ("patience", C.c_uint32),
+                ("max_epochs", C.c_uint32), ("fixed_steps", C.c_int32), ("seed", C.c_uint64),
+                ("precision", C.c_int32), ("loss", C.c_int32), ("widths", C.c_int32),
+                ("incl_best", C.c_int32), ("engine", C.c_int32)]
+
+
+class Status(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("state", C.c_int32), ("error", C.c_int32),
+                ("epoch", C.c_uint32), ("steps", C.c_uint32), ("since", C.c_uint32),
+                ("stopped", C.c_uint32), ("H", C.c_uint32), ("W", C.c_uint32),
+                ("best_mse", C.c_double), ("last_loss", C.c_double), ("device_ms", C.c_double),
+                ("latency_ms", C.c_double), ("t_start_ms", C.c_double), ("t_done_ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "struct_size"}
+
+
+class CtxStats(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("kernel_launches", C.c_uint64),
+                ("bytes_resident", C.c_uint64), ("jobs_queued", C.c_uint32),
+                ("jobs_running", C.c_uint32), ("jobs_done", C.c_uint32)]
+
+
+# name -> (restype, argtypes); the exported C ABI, one line per function of include/n2f.h
+_P, _I, _Z, _U64, _D = C.c_void_p, C.c_int, C.c_size_t, C.c_uint64, C.c_double
+SIGNATURES = {
+    "n2f_config_default": (None, [C.POINTER(Config)]),
+    "n2f_params_default": (None, [C.POINTER(Params)]),
+    "n2f_strerror": (C.c_char_p, [_I]),
+    "n2f_create": (_I, [C.POINTER(_P), C.POINTER(Config)]),
+    "n2f_destroy": (None, [_P]),
+    "n2f_submit": (_I, [_P, _P, _I, _I, C.POINTER(Params), C.POINTER(_U64)]),
+    "n2f_submit_device": (_I, [_P, _P, _I, _I, C.POINTER(Params), C.POINTER(_U64)]),
+    "n2f_submit_u16": (_I, [_P, _P, _I, _I, C.POINTER(Params), C.POINTER(_U64)]),
+    "n2f_poll": (_I, [_P, _U64, C.POINTER(Status)]),
+    "n2f_wait": (_I, [_P, _U64, _I]),
+    "n2f_result": (_I, [_P, _U64, _P, _Z]),
+    "n2f_result_device": (_I, [_P, _U64, _P, _Z]),
+    "n2f_cancel": (_I, [_P, _U64]),
+    "n2f_stats": (_I, [_P, C.POINTER(CtxStats)]),
+    "n2f_trainer_create": (_I, [C.POINTER(_P), _P, _I, _I, C.POINTER(Params), _P]),
+    "n2f_trainer_destroy": (None, [_P]),
+    "n2f_trainer_step": (_I, [_P, _I]),
+    "n2f_trainer_validate": (_I, [_P]),
+    "n2f_trainer_epoch": (_I, [_P]),
+    "n2f_trainer_run": (_I, [_P, _I]),
+    "n2f_trainer_finish": (_I, [_P]),
+    "n2f_trainer_set_theta": (_I, [_P, _P, _Z]),
+    "n2f_trainer_export": (_I, [_P, _I, _I, _P, _Z, C.POINTER(_Z)]),
+    "n2f_trainer_status": (_I, [_P, C.POINTER(Status)]),
+    "n2f_trainer_launches": (_U64, [_P]),
+    "n2f_param_count": (_Z, [_I]),
+    "n2f_checker_gather": (_I, [_P, _I, _I, _P, _P, _P, _P, _P]),
+    "n2f_pack_cg": (_I, [_P, _I, _I, _I, _I, _P, _P]),
+    "n2f_unpack_cg": (_I, [_P, _I, _I, _I, _I, _P, _P]),
+    "n2f_conv3x3": (_I, [_I, _I, _I, _P, _I, _I, _I, _I, _P, _P, _P, _P, _P]),
+    "n2f_conv3x3_wgrad": (_I, [_I, _I, _P, _P, _I, _I, _I, _I, _P, _P, _P]),
+}
+
+_lib = None
+
+
+def lib():
+    """Loads ``libn2f.so``; raises if it was not built (no fallback exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with "
+                              "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+class N2FError(RuntimeError):
+    def __init__(self, code, where=""):
+        self.code = code
+        msg = lib().n2f_strerror(code)
+        super().__init__(f"{where}: {code} ({msg.decode() if msg else '?'})")
+
+
+def check(code, where=""):
+    if code != N2F_OK:
+        raise N2FError(code, where)
+    return code
+
+
+def params(**kw) -> Params:
+    p = Params()
+    lib().n2f_params_default(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def param_count(widths=N2F_WIDTHS_PLIT) -> int:
+    return int(lib().n2f_param_count(widths))
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+# ---- job API ---------------------------------------------------------------------------------
+
+class Context:
+    """A scheduler context (``n2f_create``); device memory comes from torch's caching allocator
+    unless ``torch_alloc=False`` (then the library calls cudaMalloc itself)."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, max_slots: int = 0,
+                 lookahead: int = 0, torch_alloc: bool = True):
+        cfg = Config()
+        lib().n2f_config_default(C.byref(cfg))
+        cfg.device = device
+        if hbm_budget_bytes:
+            cfg.hbm_budget_bytes = hbm_budget_bytes
+        if max_slots:
+            cfg.max_slots = max_slots
+        if lookahead:
+            cfg.lookahead = lookahead
+        self._keep = []
+        if torch_alloc:
+            import torch
+
+            def _alloc(nbytes, user):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(nbytes), device=device)
+                except Exception:
+                    return None
+
+            def _free(ptr, nbytes, user):
+                torch.cuda.caching_allocator_delete(ptr)
+
+            a, f = ALLOC_FN(_alloc), FREE_FN(_free)
+            self._keep += [a, f]
+            cfg.alloc, cfg.free = a, f
+        self.h = C.c_void_p()
+        check(lib().n2f_create(C.byref(self.h), C.byref(cfg)), "n2f_create")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().n2f_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def submit(self, image: np.ndarray, p: Params | None = None) -> int:
+        img = np.ascontiguousarray(image, dtype=np.float32)
+        H, W = img.shape
+        job = C.c_uint64()
+        check(lib().n2f_submit(self.h, img.ctypes.data_as(C.c_void_p), H, W,
+                               C.byref(p) if p else None, C.byref(job)), "n2f_submit")
+        return job.value
+
+    def submit_u16(self, image: np.ndarray, p: Params | None = None) -> int:
+        img = np.ascontiguousarray(image, dtype=np.uint16)
+        H, W = img.shape
+        job = C.c_uint64()
+        check(lib().n2f_submit_u16(self.h, img.ctypes.data_as(C.c_void_p), H, W,
+                                   C.byref(p) if p else None, C.byref(job)), "n2f_submit_u16")
+        return job.value
+
+    def submit_device(self, dimage, p: Params | None = None) -> int:
+        """dimage: a contiguous float32 CUDA tensor (H, W) that stays valid until RUNNING."""
+        H, W = dimage.shape
+        job = C.c_uint64()
+        check(lib().n2f_submit_device(self.h, _ptr(dimage), H, W, C.byref(p) if p else None,
+                                      C.byref(job)), "n2f_submit_device")
+        return job.value
+
+    def poll(self, job: int) -> Status:
+        st = Status()
+        st.struct_size = C.sizeof(Status)
+        check(lib().n2f_poll(self.h, job, C.byref(st)), "n2f_poll")
+        return st
+
+    def wait(self, job: int, timeout_ms: int = -1) -> int:
+        return lib().n2f_wait(self.h, job, timeout_ms)
+
+    def result(self, job: int, shape) -> np.ndarray:
+        out = np.empty(shape, np.float32)
+        check(lib().n2f_result(self.h, job, out.ctypes.data_as(C.c_void_p), out.size),
+              "n2f_result")
+        return out
+
+    def result_device(self, job: int, dout) -> None:
+        check(lib().n2f_result_device(self.h, job, _ptr(dout), dout.numel()), "n2f_result_device")
+
+    def cancel(self, job: int) -> int:
+        return lib().n2f_cancel(self.h, job)
+
+    def stats(self) -> dict:
+        st = CtxStats()
+        st.struct_size = C.sizeof(CtxStats)
+        check(lib().n2f_stats(self.h, C.byref(st)), "n2f_stats")
+        return {k: getattr(st, k) for k, _ in st._fields_ if k != "struct_size"}
+
+
+def denoise(image: np.ndarray, p: Params | None = None, ctx: Context | None = None) -> np.ndarray:
+    """One image through the whole path (submit, wait, result)."""
+    own = ctx is None
+    ctx = ctx or Context()
+    try:
+        j = ctx.submit(image, p)
+        ctx.wait(j)
+        return ctx.result(j, image.shape)
+    finally:
+        if own:
+            ctx.close()
+
+
+# ---- trainer API -----------------------------------------------------------------------------
+
+class Trainer:
+    """One job's device state stepped from Python (``n2f_trainer_*``)."""
+
+    def __init__(self, image: np.ndarray, p: Params | None = None, stream=None):
+        img = np.ascontiguousarray(image, dtype=np.float32)
+        self.H, self.W = img.shape
+        self.h = C.c_void_p()
+        check(lib().n2f_trainer_create(C.byref(self.h), img.ctypes.data_as(C.c_void_p), self.H,
+                                       self.W, C.byref(p) if p else None,
+                                       _stream_ptr(stream) if stream is not False else None),
+              "n2f_trainer_create")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().n2f_trainer_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, pair: int):
+        check(lib().n2f_trainer_step(self.h, pair), "n2f_trainer_step")
+
+    def validate(self):
+        check(lib().n2f_trainer_validate(self.h), "n2f_trainer_validate")
+
+    def epoch(self):
+        check(lib().n2f_trainer_epoch(self.h), "n2f_trainer_epoch")
+
+    def run(self, max_epochs: int = 0):
+        check(lib().n2f_trainer_run(self.h, max_epochs), "n2f_trainer_run")
+
+    def finish(self):
+        check(lib().n2f_trainer_finish(self.h), "n2f_trainer_finish")
+
+    def set_theta(self, theta: np.ndarray):
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        check(lib().n2f_trainer_set_theta(self.h, th.ctypes.data_as(C.c_void_p), th.size),
+              "n2f_trainer_set_theta")
+
+    def export(self, what: int, index: int = 0) -> np.ndarray:
+        n = C.c_size_t()
+        check(lib().n2f_trainer_export(self.h, what, index, None, 0, C.byref(n)), "export size")
+        out = np.empty(n.value, np.float64)
+        check(lib().n2f_trainer_export(self.h, what, index, out.ctypes.data_as(C.c_void_p),
+                                       out.size, C.byref(n)), "n2f_trainer_export")
+        return out
+
+    def status(self) -> Status:
+        st = Status()
+        st.struct_size = C.sizeof(Status)
+        check(lib().n2f_trainer_status(self.h, C.byref(st)), "n2f_trainer_status")
+        return st
+
+    def launches(self) -> int:
+        return int(lib().n2f_trainer_launches(self.h))
+
+
+# ---- op-level entry points (torch CUDA tensors in, on the current stream) --------------------
+
+def checker_gather(x, stream=None):
+    import torch
+    H, W = x.shape
+    ue = torch.empty((H, W // 2), dtype=torch.float32, device=x.device)
+    uo = torch.empty_like(ue)
+    le = torch.empty((H // 2, W), dtype=torch.float32, device=x.device)
+    lo = torch.empty_like(le)
+    check(lib().n2f_checker_gather(_ptr(x), H, W, _ptr(ue), _ptr(uo), _ptr(le), _ptr(lo),
+                                   _stream_ptr(stream)), "n2f_checker_gather")
+    return ue, uo, le, lo
+
+
+def pack_cg(nchw, precision=N2F_FP32, stream=None):
+    import torch
+    Cc, H, W = nchw.shape
+    es = 2 if precision == N2F_BF16 else 4
+    out = torch.empty(Cc * H * W * es, dtype=torch.uint8, device=nchw.device)
+    check(lib().n2f_pack_cg(_ptr(nchw), Cc, H, W, precision, _ptr(out), _stream_ptr(stream)),
+          "n2f_pack_cg")
+    return out
+
+
+def unpack_cg(cg, Cc, H, W, precision=N2F_FP32, stream=None):
+    import torch
+    out = torch.empty((Cc, H, W), dtype=torch.float32, device=cg.device)
+    check(lib().n2f_unpack_cg(_ptr(cg), Cc, H, W, precision, _ptr(out), _stream_ptr(stream)),
+          "n2f_unpack_cg")
+    return out
+
+
+def conv3x3(mode, inp_cg, cin, cout, H, W, w, b=None, mask_cg=None, precision=N2F_FP32,
+            engine=N2F_ENGINE_AUTO, stream=None):
+    """mode 0: forward (returns C_out CG map); mode 1: dgrad (inp has C_out, returns C_in)."""
+    import torch
+    es = 2 if precision == N2F_BF16 else 4
+    cres = cout if mode == 0 else cin
+    out = torch.empty(cres * H * W * es, dtype=torch.uint8, device=inp_cg.device)
+    check(lib().n2f_conv3x3(mode, engine, precision, _ptr(inp_cg), cin, cout, H, W, _ptr(w),
+                            _ptr(b) if b is not None else None,
+                            _ptr(mask_cg) if mask_cg is not None else None, _ptr(out),
+                            _stream_ptr(stream)), "n2f_conv3x3")
+    return out
+
+
+def conv3x3_wgrad(dout_cg, in_cg, cin, cout, H, W, precision=N2F_FP32, engine=N2F_ENGINE_AUTO,
+                  stream=None):
+    import torch
+    dw = torch.empty((cout, cin, 3, 3), dtype=torch.float32, device=dout_cg.device)
+    db = torch.empty((cout,), dtype=torch.float32, device=dout_cg.device)
+    check(lib().n2f_conv3x3_wgrad(engine, precision, _ptr(dout_cg), _ptr(in_cg), cin, cout, H, W,
+                                  _ptr(dw), _ptr(db), _stream_ptr(stream)), "n2f_conv3x3_wgrad")
+    return dw, db

@@ -1,0 +1,82 @@
+"""The C-ABI library loads without a GPU and exports every entry point of include/n2f.h, and the
+Python binding's struct layouts agree with what a C compiler makes of the header."""
+import ctypes as C
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HDR = os.path.join(ROOT, "include", "n2f.h")
+
+
+@pytest.fixture(scope="module")
+def n2f():
+    import __graft_entry__ as g
+    g.build_library()
+    from paper_2108_10209_gb300 import n2f as mod
+    mod.lib()
+    return mod
+
+
+def declared_functions():
+    text = open(HDR).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = set(re.findall(r"\b(n2f_[a-z0-9_]+)\s*\(", text))
+    return sorted(n for n in names if not n.endswith("_fn"))
+
+
+def test_every_declared_function_is_exported_and_bound(n2f):
+    names = declared_functions()
+    assert len(names) >= 30
+    L = C.CDLL(n2f.LIB_PATH)
+    for name in names:
+        assert hasattr(L, name), name
+        assert name in n2f.SIGNATURES, name
+    assert set(n2f.SIGNATURES) == set(names)
+
+
+def test_struct_layouts_match_the_header(n2f):
+    src = r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "n2f.h"
+int main(void) {
+  printf("%zu %zu %zu %zu\n", sizeof(n2f_config), sizeof(n2f_params), sizeof(n2f_status),
+         sizeof(n2f_ctx_stats));
+  printf("%zu %zu %zu\n", offsetof(n2f_params, seed), offsetof(n2f_params, engine),
+         offsetof(n2f_status, t_done_ms));
+  return 0;
+}'''
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        exe = os.path.join(d, "t")
+        open(c, "w").write(src)
+        subprocess.run(["gcc", "-std=c99", "-I", os.path.dirname(HDR), c, "-o", exe], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
+    sizes = [int(v) for v in out]
+    assert sizes[:4] == [C.sizeof(n2f.Config), C.sizeof(n2f.Params), C.sizeof(n2f.Status),
+                         C.sizeof(n2f.CtxStats)]
+    assert sizes[4:] == [n2f.Params.seed.offset, n2f.Params.engine.offset,
+                         n2f.Status.t_done_ms.offset]
+
+
+def test_defaults_follow_the_methods_section(n2f):
+    p = n2f.params()
+    assert abs(p.lr - 1e-3) < 1e-9 and p.patience == 100 and p.fixed_steps == -1
+    assert p.precision == n2f.N2F_FP32 and p.loss == n2f.N2F_LOSS_BCE
+    assert abs(p.beta1 - 0.9) < 1e-7 and abs(p.beta2 - 0.999) < 1e-7
+
+
+def test_param_counts_agree_with_the_oracle(n2f):
+    import oracle
+    assert n2f.param_count(n2f.N2F_WIDTHS_PLIT) == oracle.param_count(oracle.WIDTHS_PLIT)
+    assert n2f.param_count(n2f.N2F_WIDTHS_W64) == oracle.param_count(oracle.WIDTHS_W64)
+
+
+def test_error_strings(n2f):
+    L = n2f.lib()
+    for code in range(0, -11, -1):
+        assert L.n2f_strerror(code)

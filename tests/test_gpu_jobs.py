@@ -1,0 +1,127 @@
+"""The job API (n2f_create / n2f_submit / n2f_poll / n2f_result) on the GPU: semantics, error
+paths, results independent of the job mix, and what the trained network gains."""
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def n2f():
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_2108_10209_gb300 import n2f as mod
+    torch.cuda.set_device(0)
+    return mod
+
+
+def _img(h, w, seed):
+    from paper_2108_10209_gb300 import synth
+    clean = synth.blobs(h, w, seed=seed)
+    return clean, (clean + synth.rng(seed + 1).normal(0, 0.1, (h, w))).astype(np.float32)
+
+
+def test_submit_poll_result_and_errors(n2f):
+    with n2f.Context() as ctx:
+        _, x = _img(20, 34, 1)
+        p = n2f.params(seed=2, fixed_steps=5, widths=1)
+        j = ctx.submit(x, p)
+        assert ctx.wait(j, 120000) == 0
+        st = ctx.poll(j)
+        assert st.state == n2f.N2F_DONE and st.steps == 5 and st.H == 20 and st.W == 34
+        assert st.device_ms > 0 and st.t_done_ms >= st.t_start_ms
+        out = ctx.result(j, x.shape)
+        with pytest.raises(n2f.N2FError) as e:
+            ctx.poll(j)  # collected
+        assert e.value.code == n2f.N2F_ENOENT
+        tr = n2f.Trainer(x, p)
+        tr.run()
+        assert np.array_equal(out.astype(np.float64), tr.export(n2f.N2F_X_OUT))
+        bad = x.copy()
+        bad[3, 4] = np.nan
+        for args in ((bad, p), (np.zeros((1, 8), np.float32), p)):
+            with pytest.raises(n2f.N2FError) as e:
+                ctx.submit(*args)
+            assert e.value.code == n2f.N2F_EINVAL
+        with pytest.raises(n2f.N2FError) as e:
+            ctx.submit(x, n2f.params(precision=7))
+        assert e.value.code == n2f.N2F_EINVAL
+
+
+def test_odd_sizes_and_u16_input(n2f):
+    from paper_2108_10209_gb300 import synth
+    _, x = _img(33, 17, 5)
+    q = synth.to_u16(x)
+    p = n2f.params(seed=4, fixed_steps=3, widths=1)
+    with n2f.Context() as ctx:
+        a = ctx.submit_u16(q, p)
+        b = ctx.submit((q.astype(np.float32) / np.float32(65535.0)), p)
+        ctx.wait(a)
+        ctx.wait(b)
+        oa, ob = ctx.result(a, q.shape), ctx.result(b, q.shape)
+    assert np.array_equal(oa, ob)
+    ref, _ = oracle.denoise(synth.from_u16(q).astype(np.float32).astype(np.float64),
+                            oracle.Params(widths=oracle.WIDTHS_W64, seed=4, fixed_steps=3))
+    assert float(np.max(np.abs(oa - ref))) < 2e-3
+
+
+def test_results_do_not_depend_on_the_job_mix(n2f):
+    # Each job runs on its own device state and stream with deterministic kernels (fixed
+    # reduction orders, no atomics), so a job's output is bit-identical alone and in a mix.
+    p = n2f.params(seed=9, patience=4, max_epochs=12, widths=1)
+    _, x0 = _img(24, 24, 11)
+    with n2f.Context() as ctx:
+        j = ctx.submit(x0, p)
+        ctx.wait(j)
+        alone = ctx.result(j, x0.shape)
+    with n2f.Context(max_slots=8) as ctx:
+        others = []
+        for k in range(6):
+            _, xk = _img(16 + 4 * k, 40 - 2 * k, 20 + k)
+            others.append((ctx.submit(xk, n2f.params(seed=k, patience=3, widths=k % 2)), xk.shape))
+        j = ctx.submit(x0, p)
+        for jk, shp in others:
+            ctx.wait(jk)
+            ctx.result(jk, shp)
+        ctx.wait(j)
+        mixed = ctx.result(j, x0.shape)
+    assert np.array_equal(alone, mixed)
+
+
+def test_cancel(n2f):
+    _, x = _img(64, 64, 3)
+    with n2f.Context() as ctx:
+        j = ctx.submit(x, n2f.params(seed=1, patience=1000))
+        assert ctx.cancel(j) == 0
+        assert ctx.wait(j, 60000) == 0
+        assert ctx.poll(j).state == n2f.N2F_CANCELED
+        with pytest.raises(n2f.N2FError) as e:
+            ctx.result(j, x.shape)
+        assert e.value.code == n2f.N2F_ECANCELED
+
+
+def test_trained_network_gains_over_the_untrained_path(n2f):
+    # The learned part: the network trained by the library's own forward/backward kernels on
+    # the four checkerboard pairs denoises the full image; without training (zero steps) the
+    # same path outputs the untrained network, and a 3x3 mean filter is the non-learned baseline.
+    from paper_2108_10209_gb300 import synth
+    clean, noisy = synth.image_cells(96, 96, sigma=25 / 255, seed=7)
+    with n2f.Context() as ctx:
+        j = ctx.submit(noisy, n2f.params(seed=0))
+        j0 = ctx.submit(noisy, n2f.params(seed=0, fixed_steps=0))
+        ctx.wait(j)
+        ctx.wait(j0)
+        st = ctx.poll(j)
+        out, out0 = ctx.result(j, noisy.shape), ctx.result(j0, noisy.shape)
+    pad = np.pad(noisy, 1, mode="reflect")
+    mean3 = sum(pad[dy:dy + 96, dx:dx + 96] for dy in range(3) for dx in range(3)) / 9
+    p_noisy, p_out, p_out0 = synth.psnr(noisy, clean), synth.psnr(out, clean), synth.psnr(out0, clean)
+    p_mean = synth.psnr(mean3, clean)
+    print(f"PSNR noisy {p_noisy:.2f}  untrained {p_out0:.2f}  mean3x3 {p_mean:.2f}  "
+          f"Noise2Fast {p_out:.2f} dB (stop epoch {st.epoch})")
+    assert st.stopped == 1 and st.epoch >= 101
+    assert p_out > p_noisy + 3.0
+    assert p_out > p_out0 + 5.0
