@@ -194,15 +194,30 @@ double orc_sigmoid(double z) {
 static double softplus(double z) { return (z > 0.0 ? z : 0.0) + log1p(exp(-fabs(z))); }
 
 /* Methods: BCE loss between the target and the network output (batch size 1, mean over pixels).
- * The noisy targets are not clipped, so the logit form softplus(z) - y z is used: it equals
- * -[y log s + (1-y) log(1-s)] with s = sigmoid(z) for every real y. */
+ * The noisy targets are not clipped (Compared Methods, Self2Self paragraph), so y may leave
+ * [0, 1], where -[y log s + (1-y) log(1-s)] is unbounded below as s -> 0 or 1. The loss is the
+ * usual library definition of BCE, with each log term clamped at -100, and the logs are taken
+ * in logit space (log s = -softplus(-z), log(1-s) = -softplus(z)):
+ *   L = (1/P) sum -y max(log s, -100) - (1-y) max(log(1-s), -100)
+ *   dL/dz = (s - y)/P where neither clamp is active; otherwise the unclamped terms' derivatives,
+ *   -y (1-s) [log s > -100] + (1-y) s [log(1-s) > -100], over P.
+ * loss_kind 1 is the MSE alternative the paper mentions: L = (1/P) sum (s-y)^2. */
 double orc_loss(const double* z, const double* y, int npx, int loss_kind, double* dz) {
   double L = 0.0;
   for (int p = 0; p < npx; ++p) {
     const double s = orc_sigmoid(z[p]);
     if (loss_kind == 0) {
-      L += softplus(z[p]) - y[p] * z[p];
-      if (dz) dz[p] = (s - y[p]) / npx;
+      const double lp = -softplus(-z[p]), lq = -softplus(z[p]);
+      const int m1 = lp > -100.0, m2 = lq > -100.0;
+      L += -y[p] * (m1 ? lp : -100.0) - (1.0 - y[p]) * (m2 ? lq : -100.0);
+      if (dz) {
+        double g;
+        if (m1 && m2)
+          g = s - y[p];
+        else
+          g = (m1 ? -y[p] * (1.0 - s) : 0.0) + (m2 ? (1.0 - y[p]) * s : 0.0);
+        dz[p] = g / npx;
+      }
     } else {
       L += (s - y[p]) * (s - y[p]);
       if (dz) dz[p] = 2.0 * (s - y[p]) * s * (1.0 - s) / npx;

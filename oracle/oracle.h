@@ -69,8 +69,9 @@ void orc_head_fwd(const double* a, int c, int npx, const double* w, double b, do
 double orc_sigmoid(double z);
 
 /* Training loss (Methods: binary cross-entropy between the network output and the target).
- * BCE(sigmoid(z), y) in logit form: L = (1/P) sum softplus(z) - y z,  dL/dz = (sigmoid(z)-y)/P.
- * loss_kind 1 is the MSE alternative the paper mentions: L = (1/P) sum (sigmoid(z)-y)^2. */
+ * BCE(s, y), s = sigmoid(z), with each log term clamped at -100 (bounded for the unclipped
+ * targets y outside [0, 1]); logs evaluated in logit space. dL/dz = (s - y)/P away from the
+ * clamps. loss_kind 1 is the MSE alternative the paper mentions: L = (1/P) sum (s - y)^2. */
 double orc_loss(const double* z, const double* y, int npx, int loss_kind, double* dz);
 
 /* Adam (Kingma & Ba, Algorithm 1), step t >= 1, no weight decay. */

@@ -187,10 +187,24 @@ def test_bce_closed_forms():
     assert abs(oracle.sigmoid(-800.0)) < 1e-300 and oracle.sigmoid(800.0) == 1.0
 
 
+def test_bce_clamp_bounds_the_loss_for_unclipped_targets():
+    # Targets outside [0, 1] (the noisy images are not clipped): with the log terms clamped at
+    # -100 the loss is bounded and its gradient vanishes once the clamp is active.
+    # z = 150, y = 1.2: log s ~ -e^-150, log(1-s) = -150 -> -100:  L = 0.2 * (-100) = -20
+    L, dz = oracle.loss(np.array([150.0]), np.array([1.2]), 0)
+    assert abs(L - (-20.0)) < 1e-12 and abs(dz[0]) < 1e-60
+    # z = -150, y = -0.3: log s = -150 -> -100, log(1-s) ~ -e^-150:  L = 0.3 * (-100) = -30
+    L, dz = oracle.loss(np.array([-150.0]), np.array([-0.3]), 0)
+    assert abs(L - (-30.0)) < 1e-12 and 0 < dz[0] < 1e-60
+    # just inside the clamps the gradient is (s - y)
+    L, dz = oracle.loss(np.array([99.0]), np.array([1.2]), 0)
+    assert abs(dz[0] - (oracle.sigmoid(99.0) - 1.2)) < 1e-15
+
+
 @pytest.mark.parametrize("kind", [0, 1])
 def test_loss_matches_torch(kind):
     r = _rng(7)
-    z = r.normal(scale=3, size=(5, 6)); y = r.uniform(-0.3, 1.3, size=(5, 6))
+    z = r.normal(scale=2, size=(5, 6)); y = r.uniform(-0.3, 1.3, size=(5, 6))
     zt = torch.tensor(z, requires_grad=True)
     if kind == 0:
         Lt = F.binary_cross_entropy_with_logits(zt, torch.tensor(y))
