@@ -72,6 +72,17 @@ enum n2f_job_state {
 typedef void* (*n2f_alloc_fn)(size_t bytes, void* user); /* device memory; NULL on failure */
 typedef void (*n2f_free_fn)(void* ptr, size_t bytes, void* user);
 
+/* Kernel classes the context can time with CUDA events on their launching stream. */
+enum n2f_kernel_class {
+  N2F_K_NONE = 0,
+  N2F_K_CONV_FWD = 1,   /* 3x3 forward layers with C_in >= 8 (training and validation) */
+  N2F_K_CONV_DGRAD = 2, /* 3x3 input-gradient layers */
+  N2F_K_CONV_WGRAD = 3, /* 3x3 weight-gradient layers with C_in >= 8 (incl. their reduce) */
+  N2F_K_FIRST = 4,      /* the one-channel first layer, forward */
+  N2F_K_HEAD = 5,       /* the 1x1 + sigmoid head, training and validation */
+  N2F_K_ADAM = 6        /* Adam + operand packing */
+};
+
 typedef struct {
   uint32_t struct_size;      /* sizeof(n2f_config) */
   int device;                /* CUDA device ordinal */
@@ -81,6 +92,7 @@ typedef struct {
   n2f_alloc_fn alloc;        /* optional device allocator (e.g. a framework's caching one) */
   n2f_free_fn free;
   void* alloc_user;
+  int32_t profile_kernel;    /* enum n2f_kernel_class timed per launch (events), 0 = off */
 } n2f_config;
 
 /* Per-image parameters. Defaults (n2f_params_default) follow the Methods section; the Adam
@@ -111,8 +123,10 @@ typedef struct {
   uint32_t stopped;      /* 1: the stopping rule fired, 2: max_epochs reached */
   uint32_t H, W;
   double best_mse;       /* best validation MSE */
+  double last_mse;       /* validation MSE of the last epoch */
   double last_loss;      /* training loss of the last step */
-  double device_ms;      /* GPU time from admission to the result being ready */
+  double device_ms;      /* GPU time from admission (input upload) to the result copied out */
+  double compute_ms;     /* GPU time from the input being resident to the result being ready */
   double latency_ms;     /* host time from n2f_submit to DONE */
   double t_start_ms;     /* device timestamps of admission and completion, relative to the */
   double t_done_ms;      /* context's creation (CUDA events), for makespan measurements    */
@@ -158,6 +172,11 @@ typedef struct {
   uint64_t kernel_launches; /* kernels this context has launched */
   uint64_t bytes_resident;  /* device bytes held by admitted jobs */
   uint32_t jobs_queued, jobs_running, jobs_done;
+  /* the profiled kernel class (n2f_config.profile_kernel), over finished jobs: */
+  uint64_t prof_launches;   /* launches timed */
+  double prof_ms;           /* summed event-timed duration */
+  double prof_flops;        /* algorithmic floating-point operations of those launches */
+  double prof_bytes;        /* algorithmic DRAM bytes of those launches */
 } n2f_ctx_stats;
 int n2f_stats(n2f_ctx* ctx, n2f_ctx_stats* st);
 

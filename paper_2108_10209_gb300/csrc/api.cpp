@@ -399,7 +399,8 @@ struct Job {
   Trainer tr;
   size_t bytes = 0;
   cudaStream_t st = nullptr;
-  cudaEvent_t ev_start = nullptr, ev_done = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_in = nullptr, ev_out = nullptr, ev_done = nullptr;
+  KTimer kt;
   // ring of host mirrors of the device state, one per epoch in flight
   DevState* hst = nullptr;
   cudaEvent_t ev_ep[8] = {};
@@ -408,7 +409,7 @@ struct Job {
   bool finishing = false, result_enq = false;
   DevState last;
   Clock::time_point t_submit, t_done;
-  double device_ms = 0, t0_ms = 0, t1_ms = 0;
+  double device_ms = 0, compute_ms = 0, t0_ms = 0, t1_ms = 0;
 };
 
 }  // namespace
@@ -428,6 +429,7 @@ struct n2f_ctx {
   size_t bytes_resident = 0;
   uint32_t n_done = 0;
   cudaEvent_t ev_ref = nullptr;
+  KTimer prof;  // totals of the profiled kernel class over finished jobs
 };
 
 static void free_job_host(Job* j) {
@@ -444,10 +446,11 @@ static void free_job_host(Job* j) {
 static void release_device(n2f_ctx* c, Job* j) {
   if (j->st) cudaStreamSynchronize(j->st);
   trainer_release(&j->tr);
+  j->kt.destroy();
   for (int k = 0; k < 8; ++k)
     if (j->ev_ep[k]) cudaEventDestroy(j->ev_ep[k]), j->ev_ep[k] = nullptr;
-  if (j->ev_start) cudaEventDestroy(j->ev_start), j->ev_start = nullptr;
-  if (j->ev_done) cudaEventDestroy(j->ev_done), j->ev_done = nullptr;
+  for (cudaEvent_t* e : {&j->ev_start, &j->ev_in, &j->ev_out, &j->ev_done})
+    if (*e) cudaEventDestroy(*e), *e = nullptr;
   if (j->st) cudaStreamDestroy(j->st), j->st = nullptr;
   std::lock_guard<std::mutex> g(c->mu);
   c->bytes_resident -= j->bytes;
@@ -471,7 +474,11 @@ static int admit(n2f_ctx* c, Job* j) {
   LaunchScope ls(&c->launches);
   CKR(cudaStreamCreateWithFlags(&j->st, cudaStreamNonBlocking));
   CKR(cudaEventCreate(&j->ev_start));
+  CKR(cudaEventCreate(&j->ev_in));
+  CKR(cudaEventCreate(&j->ev_out));
   CKR(cudaEventCreate(&j->ev_done));
+  j->kt.kind = c->cfg.profile_kernel;
+  if (j->kt.kind != N2F_K_NONE) j->tr.kt = &j->kt;
   j->ring = (int)std::min<uint32_t>(8, std::max<uint32_t>(2, c->cfg.lookahead + 1));
   for (int k = 0; k < j->ring; ++k) CKR(cudaEventCreateWithFlags(&j->ev_ep[k], cudaEventDisableTiming));
   CKR(cudaMallocHost((void**)&j->hst, sizeof(DevState) * j->ring));
@@ -487,6 +494,7 @@ static int admit(n2f_ctx* c, Job* j) {
   else
     CKR(cudaMemcpyAsync(j->tr.in_u16, j->pin_u16, n * sizeof(uint16_t), cudaMemcpyHostToDevice,
                         j->st));
+  CKR(cudaEventRecord(j->ev_in, j->st));
   rc = trainer_start(&j->tr, j->src_kind == 2);
   if (rc) return rc;
   if (j->tr.fixed_mode) {
@@ -551,7 +559,8 @@ static bool progress(n2f_ctx* c, Job* j) {
     rc = trainer_finish(&j->tr);
     cudaError_t e = cudaSuccess;
     if (!rc) {
-      e = cudaMemcpyAsync(j->pin_out, j->tr.out, sizeof(float) * j->tr.N, cudaMemcpyDeviceToHost,
+      e = cudaEventRecord(j->ev_out, j->st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(j->pin_out, j->tr.out, sizeof(float) * j->tr.N, cudaMemcpyDeviceToHost,
                           j->st);
       if (e == cudaSuccess) e = cudaMemcpyAsync(&j->hst[0], j->tr.state, sizeof(DevState),
                                                 cudaMemcpyDeviceToHost, j->st);
@@ -580,6 +589,18 @@ static bool progress(n2f_ctx* c, Job* j) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, j->ev_start, j->ev_done);
     j->device_ms = ms;
+    cudaEventElapsedTime(&ms, j->ev_in, j->ev_out);
+    j->compute_ms = ms;
+    if (j->tr.kt) {
+      // validations that ran: one per epoch under the stop rule, one in fixed-step mode
+      const uint64_t vals = j->tr.fixed_mode ? j->tr.vals_enqueued : (uint64_t)j->last.epoch;
+      j->kt.harvest((uint64_t)j->last.t, vals);
+      std::lock_guard<std::mutex> g(c->mu);
+      c->prof.launches += j->kt.launches;
+      c->prof.ms += j->kt.ms;
+      c->prof.flops += j->kt.flops;
+      c->prof.bytes += j->kt.bytes;
+    }
     float a = 0.f, b = 0.f;
     cudaEventElapsedTime(&a, c->ev_ref, j->ev_start);
     cudaEventElapsedTime(&b, c->ev_ref, j->ev_done);
@@ -774,6 +795,7 @@ extern "C" int n2f_poll(n2f_ctx* c, n2f_job id, n2f_status* st) {
   st->H = (uint32_t)j->H;
   st->W = (uint32_t)j->W;
   st->device_ms = j->device_ms;
+  st->compute_ms = j->compute_ms;
   st->t_start_ms = j->t0_ms;
   st->t_done_ms = j->t1_ms;
   if (st->state >= N2F_DONE)
@@ -851,5 +873,9 @@ extern "C" int n2f_stats(n2f_ctx* c, n2f_ctx_stats* st) {
   st->jobs_queued = (uint32_t)c->queue.size();
   st->jobs_running = (uint32_t)c->active.size();
   st->jobs_done = c->n_done;
+  st->prof_launches = c->prof.launches;
+  st->prof_ms = c->prof.ms;
+  st->prof_flops = c->prof.flops;
+  st->prof_bytes = c->prof.bytes;
   return N2F_OK;
 }

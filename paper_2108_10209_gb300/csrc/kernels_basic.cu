@@ -425,8 +425,8 @@ cudaError_t launch_conv1_wgrad(const void* dout, const float* img, int H, int W,
 
 // ---------------------------------------------------------------------------------------------
 // Head, training step (Methods: 1x1 convolution, sigmoid, BCE loss against the target).
-// One thread per pixel: z = b + w . a8, dL/dz = (sigmoid(z) - y) / P in the logit form of BCE
-// (MSE alternative: 2 (s - y) s (1 - s) / P), delta_8 = dL/dz * w * [a8 > 0], and per-block
+// One thread per pixel: z = b + w . a8, dL/dz = (sigmoid(z) - y) / P away from the -100 clamps
+// of the BCE log terms (MSE alternative: 2 (s - y) s (1 - s) / P), delta_8 = dL/dz * w * [a8 > 0], and per-block
 // partial sums of dL/dz * a8 (head weight gradient), dL/dz (head bias) and the loss (FP64).
 __device__ __forceinline__ float sigmoid_f(float z) {
   if (z >= 0.f) return 1.f / (1.f + expf(-z));
@@ -465,9 +465,14 @@ __global__ void __launch_bounds__(256) k_head_train(const T* __restrict__ a8, in
   if (live) {
     const float s = sigmoid_f(z), y = tgt[p];
     if (loss_kind == 0) {
-      dz = (s - y) / (float)npx;
-      const float sp = fmaxf(z, 0.f) + log1pf(expf(-fabsf(z)));
-      lterm = (double)sp - (double)y * (double)z;
+      // BCE with each log term clamped at -100 (bounded for unclipped targets outside [0, 1]);
+      // log s = -softplus(-z), log(1 - s) = -softplus(z)
+      const float sp = log1pf(expf(-fabsf(z)));
+      const float lp = -(fmaxf(-z, 0.f) + sp), lq = -(fmaxf(z, 0.f) + sp);
+      const bool m1 = lp > -100.f, m2 = lq > -100.f;
+      const float g = (m1 && m2) ? s - y : (m1 ? -y * (1.f - s) : 0.f) + (m2 ? (1.f - y) * s : 0.f);
+      dz = g / (float)npx;
+      lterm = -(double)y * (m1 ? lp : -100.0) - (1.0 - (double)y) * (m2 ? lq : -100.0);
     } else {
       dz = 2.f * (s - y) * s * (1.f - s) / (float)npx;
       lterm = (double)(s - y) * (double)(s - y);

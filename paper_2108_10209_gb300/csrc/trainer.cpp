@@ -54,7 +54,69 @@ void dev_free(const Allocator& a, void* p, size_t bytes) {
     cudaFree(p);
 }
 
+cudaEvent_t KTimer::get() {
+  if (!pool.empty()) {
+    cudaEvent_t e = pool.back();
+    pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void KTimer::harvest(uint64_t steps_done, uint64_t vals_done) {
+  for (const Pair& p : pending) {
+    const bool counted = p.val ? p.seq < vals_done : p.seq < steps_done;
+    float t = 0.f;
+    if (counted && cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) {
+      ms += t;
+      flops += p.flops;
+      bytes += p.bytes;
+      launches += 1;
+    }
+    pool.push_back(p.a);
+    pool.push_back(p.b);
+  }
+  cudaGetLastError();
+  pending.clear();
+}
+
+void KTimer::destroy() {
+  for (const Pair& p : pending) {
+    pool.push_back(p.a);
+    pool.push_back(p.b);
+  }
+  pending.clear();
+  for (cudaEvent_t e : pool) cudaEventDestroy(e);
+  pool.clear();
+}
+
 namespace {
+
+// Brackets one launch of kernel class `kind` with events when the trainer times that class.
+struct Timed {
+  KTimer* kt = nullptr;
+  cudaStream_t st;
+  KTimer::Pair p;
+  Timed(Trainer* t, int kind, double flops, double bytes, int val) : st(t->st) {
+    if (!t->kt || t->kt->kind != kind) return;
+    kt = t->kt;
+    p.a = kt->get();
+    p.b = nullptr;
+    p.flops = flops;
+    p.bytes = bytes;
+    p.val = val;
+    p.seq = val ? t->vals_enqueued : t->steps_enqueued;
+    cudaEventRecord(p.a, st);
+  }
+  ~Timed() {
+    if (!kt) return;
+    p.b = kt->get();
+    cudaEventRecord(p.b, st);
+    kt->pending.push_back(p);
+  }
+};
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -244,9 +306,12 @@ int trainer_repack(Trainer* t) {
 }
 
 static int conv_layer(Trainer* t, int l, const void* in, void* out, int H, int W,
-                      const int* skip) {
+                      const int* skip, int val) {
   const int cin = t->net.cin(l), cout = t->net.widths[l];
   const float* b = t->theta + t->net.b_off[l];
+  const double P = (double)H * W, es = t->bf16 ? 2.0 : 4.0;
+  Timed tm(t, l == 0 ? N2F_K_FIRST : N2F_K_CONV_FWD, 2.0 * P * 9 * cin * cout,
+           l == 0 ? P * 4.0 + P * cout * es : P * (cin + cout) * es, val);
   if (l == 0) {
     CK(launch_conv1_fwd((const float*)in, H, W, t->pa.fwd[0], b, cout, t->bf16, out, skip, t->st));
   } else if (t->engine[l] == N2F_ENGINE_TC) {
@@ -271,7 +336,7 @@ int trainer_step(Trainer* t, int pair) {
   // forward, keeping every post-ReLU map
   const void* cur = in;
   for (int l = 0; l < kLayers; ++l) {
-    int rc = conv_layer(t, l, cur, t->act[l], h, w, skip);
+    int rc = conv_layer(t, l, cur, t->act[l], h, w, skip, 0);
     if (rc) return rc;
     cur = t->act[l];
   }
@@ -279,9 +344,13 @@ int trainer_step(Trainer* t, int pair) {
   const int C8 = net.widths[kLayers - 1];
   void* d8 = t->keep_deltas ? t->dkeep[kLayers - 1] : t->dl[0];
   int nblk = 0;
+  const double es = t->bf16 ? 2.0 : 4.0;
+  {
+    Timed tm(t, N2F_K_HEAD, 2.0 * npx * C8, (double)npx * C8 * 2 * es + npx * 8.0, 0);
   CK(launch_head_train(t->act[kLayers - 1], C8, npx, t->theta + net.w_off[kLayers],
                        t->theta + net.b_off[kLayers], tgt, t->prm.loss, t->bf16, t->dz, d8,
                        t->lpart, t->hpart, &nblk, skip, t->st));
+  }
   CK(launch_step_finish(t->hpart, t->lpart, nblk, C8, npx, t->grad + net.w_off[kLayers],
                         t->grad + net.b_off[kLayers], t->state, t->prm.beta1, t->prm.beta2,
                         t->st));
@@ -292,11 +361,14 @@ int trainer_step(Trainer* t, int pair) {
     const int cin = net.cin(l), cout = net.widths[l];
     float* gw = t->grad + net.w_off[l];
     float* gb = t->grad + net.b_off[l];
+    const double fl = 2.0 * npx * 9 * cin * cout;
     if (l == 0) {
       CK(launch_conv1_wgrad(dcur, in, h, w, cout, t->bf16, t->wpart, t->wpart_cap, gw, gb, skip,
                             t->st));
       break;
     }
+    {
+      Timed tm(t, N2F_K_CONV_WGRAD, fl, (double)npx * (cin + cout) * es, 0);
     if (t->engine[l] == N2F_ENGINE_TC) {
       CK(launch_wgrad_tc(t->bf16, dcur, t->act[l - 1], cin, cout, h, w, t->wpart, t->wpart_cap,
                          gw, gb, skip, t->st));
@@ -304,7 +376,9 @@ int trainer_step(Trainer* t, int pair) {
       CK(launch_wgrad_simt(t->bf16, dcur, t->act[l - 1], cin, cout, h, w, t->wpart,
                            t->wpart_cap, gw, gb, skip, t->st));
     }
+    }
     void* dnext = t->keep_deltas ? t->dkeep[l - 1] : t->dl[pp ^ 1];
+    Timed tm(t, N2F_K_CONV_DGRAD, fl, (double)npx * (cin * 2 + cout) * es, 0);
     if (t->engine[l] == N2F_ENGINE_TC) {
       CK(launch_conv_tc(1, t->bf16, dcur, cout, cin, h, w, t->pa.tcd[l], nullptr, t->act[l - 1],
                         dnext, skip, t->st));
@@ -315,8 +389,11 @@ int trainer_step(Trainer* t, int pair) {
     dcur = dnext;
     pp ^= 1;
   }
-  CK(launch_adam(t->pa, t->grad, t->m, t->v, t->prm.lr, t->prm.beta1, t->prm.beta2, t->prm.eps,
-                 t->state, 1, t->st));
+  {
+    Timed tm(t, N2F_K_ADAM, 0.0, (double)net.count * 4.0 * 9, 0);
+    CK(launch_adam(t->pa, t->grad, t->m, t->v, t->prm.lr, t->prm.beta1, t->prm.beta2,
+                   t->prm.eps, t->state, 1, t->st));
+  }
   t->steps_enqueued += 1;
   return N2F_OK;
 }
@@ -328,17 +405,22 @@ int trainer_validate(Trainer* t) {
   const void* cur = t->x;
   int pp = 0;
   for (int l = 0; l < kLayers; ++l) {
-    int rc = conv_layer(t, l, cur, t->vb[pp], t->H, t->W, skip);
+    int rc = conv_layer(t, l, cur, t->vb[pp], t->H, t->W, skip, 1);
     if (rc) return rc;
     cur = t->vb[pp];
     pp ^= 1;
   }
   int nblk = 0;
+  {
+    const double es = t->bf16 ? 2.0 : 4.0, C8 = net.widths[kLayers - 1];
+    Timed tm(t, N2F_K_HEAD, 2.0 * t->N * C8, (double)t->N * (C8 * es + 8.0), 1);
   CK(launch_head_val(cur, net.widths[kLayers - 1], (int)t->N, t->theta + net.w_off[kLayers],
                      t->theta + net.b_off[kLayers], t->x, t->bf16, t->V, t->mpart, &nblk, skip,
                      t->st));
+  }
   CK(launch_val_decide(t->mpart, nblk, t->N, t->state, t->fixed_mode, t->st));
   if (!t->fixed_mode) CK(launch_val_accum(t->V, t->S, t->Vbest, t->N, t->state, t->st));
+  t->vals_enqueued += 1;
   return N2F_OK;
 }
 
@@ -370,6 +452,7 @@ void fill_status(const Trainer* t, const DevState& s, n2f_status* st) {
   st->H = (uint32_t)t->H;
   st->W = (uint32_t)t->W;
   st->best_mse = s.best;
+  st->last_mse = s.last_mse;
   st->last_loss = s.loss;
 }
 

@@ -1,6 +1,7 @@
 // Step executor of one Noise2Fast job (host side).
 #pragma once
 #include <string>
+#include <vector>
 
 #include "n2f_internal.h"
 
@@ -22,6 +23,26 @@ struct LaunchScope {
   uint64_t* prev;
   explicit LaunchScope(uint64_t* dst) : prev(tl_launch_counter) { tl_launch_counter = dst; }
   ~LaunchScope() { tl_launch_counter = prev; }
+};
+
+// Times the launches of one kernel class with CUDA events on the launching stream.
+struct KTimer {
+  struct Pair {
+    cudaEvent_t a, b;
+    double flops, bytes;
+    int val;  // 0: part of training step `seq`, 1: part of validation `seq`
+    uint64_t seq;
+  };
+  int kind = N2F_K_NONE;
+  std::vector<cudaEvent_t> pool;
+  std::vector<Pair> pending;
+  uint64_t launches = 0;
+  double ms = 0, flops = 0, bytes = 0;
+  cudaEvent_t get();
+  // Adds the finished pairs that belong to steps < steps_done and validations < vals_done
+  // (launches of epochs enqueued after the stop returned at once and are not counted).
+  void harvest(uint64_t steps_done, uint64_t vals_done);
+  void destroy();
 };
 
 struct Trainer {
@@ -56,7 +77,8 @@ struct Trainer {
   uint16_t* in_u16 = nullptr;
   DevState hstate_init;
   int last_pair = 0;
-  uint64_t steps_enqueued = 0;
+  uint64_t steps_enqueued = 0, vals_enqueued = 0;
+  KTimer* kt = nullptr;  // optional kernel-class timer (owned by the caller)
 };
 
 int trainer_configure(Trainer* t, int H, int W, const n2f_params* p, int keep_deltas);

@@ -25,6 +25,8 @@ N2F_ENGINE_AUTO, N2F_ENGINE_SIMT, N2F_ENGINE_TC = 0, 1, 2
 N2F_QUEUED, N2F_RUNNING, N2F_DONE, N2F_FAILED, N2F_CANCELED = range(5)
 (N2F_X_THETA, N2F_X_GRAD, N2F_X_ADAM_M, N2F_X_ADAM_V, N2F_X_ACT, N2F_X_DELTA) = range(6)
 N2F_X_DZ, N2F_X_PAIR, N2F_X_VAL, N2F_X_SUM, N2F_X_OUT = 7, 8, 9, 10, 11
+(N2F_K_NONE, N2F_K_CONV_FWD, N2F_K_CONV_DGRAD, N2F_K_CONV_WGRAD, N2F_K_FIRST, N2F_K_HEAD,
+ N2F_K_ADAM) = range(7)
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
@@ -33,7 +35,7 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
 class Config(C.Structure):
     _fields_ = [("struct_size", C.c_uint32), ("device", C.c_int), ("hbm_budget_bytes", C.c_uint64),
                 ("max_slots", C.c_uint32), ("lookahead", C.c_uint32), ("alloc", ALLOC_FN),
-                ("free", FREE_FN), ("alloc_user", C.c_void_p)]
+                ("free", FREE_FN), ("alloc_user", C.c_void_p), ("profile_kernel", C.c_int32)]
 
 
 class Params(C.Structure):
@@ -48,8 +50,9 @@ class Status(C.Structure):
     _fields_ = [("struct_size", C.c_uint32), ("state", C.c_int32), ("error", C.c_int32),
                 ("epoch", C.c_uint32), ("steps", C.c_uint32), ("since", C.c_uint32),
                 ("stopped", C.c_uint32), ("H", C.c_uint32), ("W", C.c_uint32),
-                ("best_mse", C.c_double), ("last_loss", C.c_double), ("device_ms", C.c_double),
-                ("latency_ms", C.c_double), ("t_start_ms", C.c_double), ("t_done_ms", C.c_double)]
+                ("best_mse", C.c_double), ("last_mse", C.c_double), ("last_loss", C.c_double), ("device_ms", C.c_double),
+                ("compute_ms", C.c_double), ("latency_ms", C.c_double), ("t_start_ms", C.c_double),
+                ("t_done_ms", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "struct_size"}
@@ -58,7 +61,9 @@ class Status(C.Structure):
 class CtxStats(C.Structure):
     _fields_ = [("struct_size", C.c_uint32), ("kernel_launches", C.c_uint64),
                 ("bytes_resident", C.c_uint64), ("jobs_queued", C.c_uint32),
-                ("jobs_running", C.c_uint32), ("jobs_done", C.c_uint32)]
+                ("jobs_running", C.c_uint32), ("jobs_done", C.c_uint32),
+                ("prof_launches", C.c_uint64), ("prof_ms", C.c_double), ("prof_flops", C.c_double),
+                ("prof_bytes", C.c_double)]
 
 
 # name -> (restype, argtypes); the exported C ABI, one line per function of include/n2f.h
@@ -161,7 +166,7 @@ class Context:
     unless ``torch_alloc=False`` (then the library calls cudaMalloc itself)."""
 
     def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, max_slots: int = 0,
-                 lookahead: int = 0, torch_alloc: bool = True):
+                 lookahead: int = 0, torch_alloc: bool = True, profile_kernel: int = 0):
         cfg = Config()
         lib().n2f_config_default(C.byref(cfg))
         cfg.device = device
@@ -171,6 +176,7 @@ class Context:
             cfg.max_slots = max_slots
         if lookahead:
             cfg.lookahead = lookahead
+        cfg.profile_kernel = profile_kernel
         self._keep = []
         if torch_alloc:
             import torch

@@ -39,7 +39,7 @@ def test_submit_poll_result_and_errors(n2f):
         assert e.value.code == n2f.N2F_ENOENT
         tr = n2f.Trainer(x, p)
         tr.run()
-        assert np.array_equal(out.astype(np.float64), tr.export(n2f.N2F_X_OUT))
+        assert np.array_equal(out.astype(np.float64).ravel(), tr.export(n2f.N2F_X_OUT))
         bad = x.copy()
         bad[3, 4] = np.nan
         for args in ((bad, p), (np.zeros((1, 8), np.float32), p)):

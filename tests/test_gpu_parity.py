@@ -118,6 +118,9 @@ def test_single_step_activations_and_gradients(n2f, widths):
     job = oracle.Job(noisy, oracle.Params(widths=ow, seed=0))
     sl = layer_slices(ow)
     for pair in (0, 2, 1, 3):
+        # both sides start the step from the same (float32) weights: after a step, Adam moves
+        # weights whose gradient is below the numerical noise by +-lr with an undetermined sign
+        job.set_theta(tr.export(n2f.N2F_X_THETA))
         tr.step(pair)
         job.step(pair)
         for l in range(1, 9):
@@ -175,7 +178,7 @@ def test_stop_rule_run_matches_oracle(n2f):
     out = tr.export(n2f.N2F_X_OUT)
     if st.epoch == info["epoch"]:
         assert st.stopped == (1 if info["stopped"] else 2)
-        assert float(np.max(np.abs(out - ref))) <= MAXABS_TOL
+        assert float(np.max(np.abs(out - ref.ravel()))) <= MAXABS_TOL
     else:
         # a near-tie of two validation scores may flip a decision between FP32 and FP64;
         # then the run is compared at the oracle's stop epoch
