@@ -1,0 +1,362 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the Noise2Fast per-image path: denoised images/s and per-image
+latency (p50/p99), one JSON line on rank 0.
+
+A step is one image taken through the whole path (upload, checkerboard gather, training on the
+four pairs until the stopping rule fires, full-image validation each epoch, output averaging,
+result). Default workload: 512x512 synthetic ellipse "cells" with Gaussian noise sigma 25/255 and
+50/255 alternating, float32 plain form, the literal-width network, one image at a time.
+
+  value   images/s from device time with the input resident: per image, CUDA events on the
+          job's stream from "input uploaded" to "result ready"; summed over the K images, max
+          over ranks.
+  e2e     the same images through the public C ABI with host buffers (n2f_submit / n2f_result):
+          host wall time from submit to result, including the pinned-staging copy, H2D and D2H.
+  roofline  the profiled kernel class, timed per launch with CUDA events on its stream.
+  cpu_baseline  the FP64 oracle on the host cores over a bounded sample (one epoch on a 128x128
+          crop), extrapolated to the whole image at the shortest run the stopping rule allows.
+
+--impl reference times the oracle the same way (no GPU work) and prints the same kind of line.
+Multi-GPU (torchrun): images are sharded across ranks, no data-path collective (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "denoised images/s (p50/p99 latency per image)"
+UNIT = "images/s"
+WIDTH_NAMES = {0: "32-32-64-64-128-128-256-256", 1: "64x8"}
+CLASS_NAMES = {1: "conv3x3_fwd", 2: "conv3x3_dgrad", 3: "conv3x3_wgrad", 4: "conv1_fwd",
+               5: "head", 6: "adam"}
+MIN_EPOCHS = 101  # shortest run the stopping rule allows: one best epoch + 100 without gain
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def image_for(step: int, rank: int, size: int):
+    from paper_2108_10209_gb300 import synth
+    sigma = (25.0 if step % 2 == 0 else 50.0) / 255.0
+    return synth.image_cells(size, size, sigma=sigma, seed=1_000_000 + rank * 10_000 + step)
+
+
+# ---------------------------------------------------------------------------- clocks ---------
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r)
+                          if v.lower().startswith("active")})
+        clk = sorted(r[0] for r in rows)
+        return {"sm_mhz": clk[len(clk) // 2], "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------- CPU oracle -----
+
+def oracle_epoch_seconds(noisy, widths: int, crop: int = 128):
+    """Wall time of one oracle epoch (4 steps + validation) on the top-left crop x crop."""
+    os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
+    import oracle
+    ow = oracle.WIDTHS_PLIT if widths == 0 else oracle.WIDTHS_W64
+    job = oracle.Job(noisy[:crop, :crop], oracle.Params(widths=ow, seed=0))
+    t0 = time.perf_counter()
+    job.epoch()
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(noisy, size: int, widths: int, crop: int = 128, reps: int = 1):
+    ts = [oracle_epoch_seconds(noisy, widths, crop) for _ in range(reps)]
+    t = min(ts)
+    scale = (size * size) / float(crop * crop)
+    ips = 1.0 / (MIN_EPOCHS * scale * t)
+    return {"value": ips, "unit": UNIT, "cores": int(os.environ.get("OMP_NUM_THREADS", "1")),
+            "kind": "oracle",
+            "sample": (f"one epoch (4 training steps + validation) of the FP64 oracle on a "
+                       f"{crop}x{crop} crop: {t:.2f} s; scaled by pixel count x{scale:.0f} to the "
+                       f"{size}x{size} image and by {MIN_EPOCHS} epochs, the shortest run the "
+                       f"stopping rule allows (real runs are longer, so this overstates the "
+                       f"oracle)")}
+
+
+# ---------------------------------------------------------------------------- peaks ----------
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2108_10209_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_record(kclass: str, workload: str):
+    """DRAM bytes per launch from a committed ncu summary, if its kernels are unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        recs = json.load(open(path))
+    except Exception:
+        return None
+    r = recs.get(f"{kclass}|{workload}")
+    if not r or r.get("source_hash") != kernel_source_hash():
+        return None
+    return r.get("dram_bytes_per_launch")
+
+
+def roofline(stats, kclass: int, precision: int, engine_tc: bool, workload: str):
+    pk, src = peaks()
+    n = stats["prof_launches"]
+    if not n or stats["prof_ms"] <= 0:
+        return None
+    avg_s = stats["prof_ms"] / n / 1e3
+    flops = stats["prof_flops"] / n
+    bytes_ = stats["prof_bytes"] / n
+    name = CLASS_NAMES.get(kclass, str(kclass))
+    if kclass in (1, 2, 3) and engine_tc:
+        if precision == 1:
+            peak, note = pk["bf16_tflops_sustained"], f"bf16 dense sustained, {src}"
+        else:
+            peak = pk["bf16_tflops_sustained"] * (1.1 / 2.25) / 3.0
+            note = f"3xTF32: TF32 = bf16 sustained x 1.1/2.25 (nominal ratio), /3 products, {src}"
+        rl = {"bound": "tensor", "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s"}
+    elif kclass in (1, 2, 3):
+        clk = pk.get("sm_max_mhz", 2070.0)
+        peak = 152 * 128 * 2 * clk * 1e6 / 1e12
+        note = f"FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x {clk:.0f} MHz (unit counts x max clock)"
+        rl = {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s"}
+    else:
+        peak, note = pk["hbm_gbs"], f"HBM copy bandwidth, {src}"
+        rl = {"bound": "hbm", "achieved": bytes_ / avg_s / 1e9, "peak": peak, "unit": "GB/s"}
+    rl["frac"] = rl["achieved"] / rl["peak"]
+    tr = traffic_record(name, workload)
+    rl["traffic"] = tr
+    rl.update({"kernel": name, "launches": n, "avg_launch_us": avg_s * 1e6,
+               "algorithmic_per_launch": flops if rl["unit"] == "TFLOP/s" else bytes_,
+               "peak_source": note})
+    return rl
+
+
+# ---------------------------------------------------------------------------- our arm -------
+
+def run_ours(args, ws, rank, local):
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    import __graft_entry__ as g
+    g.build()
+    from paper_2108_10209_gb300 import n2f
+
+    size = args.size
+    p = n2f.params(seed=0, precision=args.precision, widths=args.widths, engine=args.engine)
+    work = [image_for(i, rank, size) for i in range(args.warmup + args.steps)]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
+    ctx = n2f.Context(device=local, max_slots=1, profile_kernel=args.profile_kernel)
+    for i in range(args.warmup):
+        j = ctx.submit(work[i][1].astype(np.float32), p)
+        ctx.wait(j)
+        ctx.result(j, (size, size))
+    clocks = ClockSampler(local)
+    st0 = ctx.stats()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    comp_ms, wall_ms, epochs = [], [], []
+    for i in range(args.warmup, args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        x = work[i][1].astype(np.float32)
+        t0 = time.perf_counter()
+        j = ctx.submit(x, p)
+        ctx.wait(j)
+        st = ctx.poll(j)
+        out = ctx.result(j, x.shape)
+        wall_ms.append((time.perf_counter() - t0) * 1e3)
+        comp_ms.append(st.compute_ms)
+        epochs.append(st.epoch)
+        assert st.state == n2f.N2F_DONE, st.as_dict()
+        assert np.isfinite(out).all()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    st1 = ctx.stats()
+    ctx.close()
+    tot_dev_s = sum(comp_ms) / 1e3
+    tot_wall_s = sum(wall_ms) / 1e3
+    if ws > 1:
+        t = torch.tensor([tot_dev_s, tot_wall_s], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot_dev_s, tot_wall_s = float(t[0]), float(t[1])
+    if rank != 0:
+        return None
+    n_img = args.steps * ws
+    stats = {k: st1[k] - st0[k] if isinstance(st1[k], (int, float)) else st1[k] for k in st1}
+    workload = f"{size}x{size} cells fp{'32' if args.precision == 0 else 'bf16'} " \
+               f"{WIDTH_NAMES[args.widths]} plain"
+    rl = roofline(stats, args.profile_kernel, args.precision, args.engine == 2, workload)
+    q = sorted(comp_ms)
+    line = {
+        "metric": METRIC, "value": n_img / tot_dev_s, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_dev_s * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == 0 else "bf16 (f32 accumulate)",
+        "data": "synthetic (ellipse cells + Gaussian noise, seeded)",
+        "config": {"workload": f"{size}x{size} grayscale, Gaussian sigma 25/255 and 50/255 "
+                               f"alternating, stopping rule (patience 100), one image at a time",
+                   "image": [size, size], "widths": WIDTH_NAMES[args.widths],
+                   "precision": "fp32" if args.precision == 0 else "bf16",
+                   "engine": {0: "auto", 1: "simt", 2: "tcgen05"}[args.engine],
+                   "jobs_in_flight": 1, "parallelism": f"images sharded over {ws} GPU(s)",
+                   "l2": "256 MB buffer written between timed images; per-image working set "
+                         "~0.8 GB is larger than L2"},
+        "latency_ms": {"p50": q[len(q) // 2], "p99": q[min(len(q) - 1, int(0.99 * len(q)))],
+                       "per_image": [round(v, 2) for v in comp_ms]},
+        "epochs_per_image": epochs,
+        "epochs_per_s_mpx": sum(epochs) * size * size / 1e6 / (sum(comp_ms) / 1e3),
+        "e2e": {"value": n_img / tot_wall_s, "unit": UNIT,
+                "h2d_bytes_per_step": size * size * 4, "d2h_bytes_per_step": size * size * 4},
+        "gpu_launches": int(stats["kernel_launches"]),
+        "roofline": rl,
+        "clocks": clk,
+        "paper_context": "under 45 s per 512x512 image on an RTX 5000 mobile GPU (Contribution "
+                         "and Significance); other hardware and data, context only",
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(work[args.warmup][1], size, args.widths)
+    return line
+
+
+# ---------------------------------------------------------------------------- reference arm -
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return None
+    size = args.size
+    work = [image_for(i, 0, size) for i in range(args.warmup + args.steps)]
+    for i in range(args.warmup):
+        oracle_epoch_seconds(work[i][1], args.widths)
+    ts = [oracle_epoch_seconds(work[i][1], args.widths)
+          for i in range(args.warmup, args.warmup + args.steps)]
+    scale = (size * size) / (128.0 * 128.0)
+    per_img = [MIN_EPOCHS * scale * t for t in ts]
+    value = len(per_img) / sum(per_img)
+    cores = int(os.environ.get("OMP_NUM_THREADS", "1"))
+    sample = (f"each step: one epoch of the FP64 oracle on a 128x128 crop, scaled by pixel "
+              f"count x{scale:.0f} and by {MIN_EPOCHS} epochs (the shortest stopping-rule run)")
+    q = sorted(per_img)
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": sum(per_img) * 1e3 / len(per_img), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{size}x{size} grayscale, Gaussian sigma 25/255 and 50/255 "
+                               f"alternating, stopping rule", "image": [size, size],
+                   "widths": WIDTH_NAMES[args.widths]},
+        "latency_ms": {"p50": q[len(q) // 2] * 1e3, "p99": q[-1] * 1e3},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--size", type=int, default=512)
+    ap.add_argument("--precision", type=int, default=0, help="0 fp32, 1 bf16")
+    ap.add_argument("--widths", type=int, default=0, help="0 literal widths, 1 constant 64")
+    ap.add_argument("--engine", type=int, default=0, help="0 auto, 1 simt, 2 tcgen05")
+    ap.add_argument("--profile-kernel", type=int, default=1,
+                    help="kernel class timed for the roofline (1 fwd, 2 dgrad, 3 wgrad)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        line = run_reference(args, ws, rank)
+    else:
+        if ws > 1:
+            import torch
+            torch.cuda.set_device(local)
+            torch.distributed.init_process_group("nccl")
+        line = run_ours(args, ws, rank, local)
+        if ws > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

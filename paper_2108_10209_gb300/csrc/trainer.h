@@ -18,11 +18,19 @@ struct Allocator {
 void* dev_alloc(const Allocator& a, size_t bytes);
 void dev_free(const Allocator& a, void* p, size_t bytes);
 
-// Counts the kernels enqueued while it is alive into *dst.
+// Counts the kernels enqueued while it is alive into *dst, and into the enclosing scope's
+// counter as well when scopes nest (a context counting around a trainer).
 struct LaunchScope {
   uint64_t* prev;
-  explicit LaunchScope(uint64_t* dst) : prev(tl_launch_counter) { tl_launch_counter = dst; }
-  ~LaunchScope() { tl_launch_counter = prev; }
+  uint64_t* dst;
+  uint64_t start;
+  explicit LaunchScope(uint64_t* d) : prev(tl_launch_counter), dst(d), start(*d) {
+    tl_launch_counter = d;
+  }
+  ~LaunchScope() {
+    if (prev && prev != dst) *prev += *dst - start;
+    tl_launch_counter = prev;
+  }
 };
 
 // Times the launches of one kernel class with CUDA events on the launching stream.

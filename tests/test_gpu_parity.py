@@ -110,36 +110,95 @@ def _small_case():
     return synth.image_small(seed=0)
 
 
+def _step_snapshot(tr, n2f):
+    return {k: tr.export(w) for k, w in (("theta", n2f.N2F_X_THETA), ("m", n2f.N2F_X_ADAM_M),
+                                          ("v", n2f.N2F_X_ADAM_V))}
+
+
+@pytest.mark.parametrize("widths", [0, 1])
+def test_single_step_per_kernel_parity(n2f, widths):
+    """Every kernel of a training step against the oracle on the GPU's own inputs of that step
+    (so both sides take the same ReLU decisions): forward layers, head, loss gradient, dgrad,
+    wgrad and Adam, each within 1e-4 of the largest reference value."""
+    clean, noisy = _small_case()
+    ow = oracle.WIDTHS_PLIT if widths == 0 else oracle.WIDTHS_W64
+    tr = n2f.Trainer(noisy, n2f.params(seed=0, widths=widths))
+    sl = layer_slices(ow)
+    for t, pair in enumerate((0, 2, 1, 3), start=1):
+        before = _step_snapshot(tr, n2f)
+        tr.step(pair)
+        h, w = (32, 16) if pair < 2 else (16, 32)
+        inp = tr.export(n2f.N2F_X_PAIR, pair).reshape(1, h, w)
+        tgt = tr.export(n2f.N2F_X_PAIR, pair ^ 1).reshape(h, w)
+        parts = oracle.unpack(ow, before["theta"])
+        act = [tr.export(n2f.N2F_X_ACT, l).reshape(ow[l - 1], h, w) for l in range(1, 9)]
+        dlt = [tr.export(n2f.N2F_X_DELTA, l).reshape(ow[l - 1], h, w) for l in range(1, 9)]
+        grad = tr.export(n2f.N2F_X_GRAD)
+        prev = [inp] + act[:-1]
+        for l in range(8):
+            ref = oracle.conv3x3_fwd(prev[l], parts[l][0], parts[l][1], relu=True)
+            assert rel_err(act[l], ref) < REL_STEP, ("fwd", pair, l + 1)
+        z = oracle.head_fwd(act[7], parts[8][0], parts[8][1][0])
+        _, dz_ref = oracle.loss(z, tgt, 0)
+        dz = tr.export(n2f.N2F_X_DZ).reshape(h, w)
+        assert rel_err(dz, dz_ref) < REL_STEP, ("dz", pair)
+        d8 = dz[None] * parts[8][0][:, None, None] * (act[7] > 0)
+        assert rel_err(dlt[7], d8) < REL_STEP, ("delta8", pair)
+        gw9 = np.einsum("p,cp->c", dz.ravel(), act[7].reshape(ow[7], -1))
+        assert rel_err(grad[sl[8][0]], gw9) < REL_STEP and rel_err(grad[sl[8][1]], [dz.sum()]) < REL_STEP
+        for l in range(7, -1, -1):
+            dw, db = oracle.conv3x3_wgrad(dlt[l], prev[l])
+            assert rel_err(grad[sl[l][0]], dw) < REL_STEP, ("wgrad", pair, l + 1)
+            assert rel_err(grad[sl[l][1]], db) < REL_STEP, ("bgrad", pair, l + 1)
+            if l > 0:
+                dref = oracle.conv3x3_dgrad(dlt[l], parts[l][0]) * (act[l - 1] > 0)
+                assert rel_err(dlt[l - 1], dref) < REL_STEP, ("dgrad", pair, l + 1)
+        th, m, v = before["theta"].copy(), before["m"].copy(), before["v"].copy()
+        oracle.adam(th, grad.copy(), m, v, t)
+        assert rel_err(tr.export(n2f.N2F_X_ADAM_M), m) < REL_STEP
+        assert rel_err(tr.export(n2f.N2F_X_ADAM_V), v) < REL_STEP
+        got = tr.export(n2f.N2F_X_THETA)
+        for ws, bs in sl:
+            for s_ in (ws, bs):
+                # theta moves by ~lr per step: compare the update, not theta's magnitude
+                assert rel_err(got[s_] - before["theta"][s_], th[s_] - before["theta"][s_]) < REL_STEP
+
+
 @pytest.mark.parametrize("widths", [0, 1])
 def test_single_step_activations_and_gradients(n2f, widths):
+    """The whole step chained (oracle from the same weights, its own activations): the ReLU
+    mask is a decision floating point takes, so a pre-activation within rounding of zero may be
+    switched differently on the two sides. Such units must be rare and sit at a near-zero
+    pre-activation; tensors downstream of one (deltas and gradients of lower layers) are held to
+    1e-3 and every other tensor to 1e-4."""
     clean, noisy = _small_case()
     ow = oracle.WIDTHS_PLIT if widths == 0 else oracle.WIDTHS_W64
     tr = n2f.Trainer(noisy, n2f.params(seed=0, widths=widths))
     job = oracle.Job(noisy, oracle.Params(widths=ow, seed=0))
     sl = layer_slices(ow)
     for pair in (0, 2, 1, 3):
-        # both sides start the step from the same (float32) weights: after a step, Adam moves
-        # weights whose gradient is below the numerical noise by +-lr with an undetermined sign
         job.set_theta(tr.export(n2f.N2F_X_THETA))
         tr.step(pair)
         job.step(pair)
+        flips = []
         for l in range(1, 9):
-            assert rel_err(tr.export(n2f.N2F_X_ACT, l), job.get(oracle.ACT, l)) < REL_STEP, (pair, l)
-            assert rel_err(tr.export(n2f.N2F_X_DELTA, l), job.get(oracle.DELTA, l)) < REL_STEP, (pair, l)
+            a, ao = tr.export(n2f.N2F_X_ACT, l), job.get(oracle.ACT, l)
+            assert rel_err(a, ao) < REL_STEP, (pair, l)
+            flip = (a > 0) != (ao > 0)
+            scale = np.max(np.abs(ao))
+            assert np.all(np.abs(ao[flip]) <= 1e-5 * scale) and np.all(np.abs(a[flip]) <= 1e-5 * scale)
+            assert flip.sum() <= max(2, 1e-4 * flip.size), (pair, l, int(flip.sum()))
+            flips.append(int(flip.sum()))
         assert rel_err(tr.export(n2f.N2F_X_DZ), job.get(oracle.DZ)) < REL_STEP
         g, go = tr.export(n2f.N2F_X_GRAD), job.get(oracle.GRAD)
-        for ws, bs in sl:
-            assert rel_err(g[ws], go[ws]) < REL_STEP and rel_err(g[bs], go[bs]) < REL_STEP
-        # Adam moves an element by about lr * sign(g); where |g| sits below the gradients'
-        # numerical noise the sign is not determined by the data, so theta is compared where
-        # the gradient is resolved and bounded by the step size elsewhere.
-        th, tho = tr.export(n2f.N2F_X_THETA), job.get(oracle.THETA)
-        for ws, bs in sl:
-            for s in (ws, bs):
-                resolved = np.abs(go[s]) > 1e-3 * np.max(np.abs(go[s]))
-                diff = np.abs(th[s] - tho[s])
-                assert np.all(diff[resolved] <= 1e-4 * np.max(np.abs(tho[s])) + 1e-6)
-                assert np.all(diff <= 2.5e-3 * (pair + 1))
+        for l in range(8, 0, -1):
+            upstream = sum(flips[l - 1:])  # masks applied on the way from the head down to l
+            tol = REL_STEP if upstream == 0 else 10 * REL_STEP
+            d, do = tr.export(n2f.N2F_X_DELTA, l), job.get(oracle.DELTA, l)
+            assert rel_err(d, do) < tol, (pair, l, flips)
+            ws, bs = sl[l - 1]
+            assert rel_err(g[ws], go[ws]) < tol and rel_err(g[bs], go[bs]) < tol, (pair, l, flips)
+        print(f"pair {pair}: ReLU decisions differing per layer {flips}")
 
 
 def test_zero_steps_equals_one_forward_pass(n2f):
