@@ -166,16 +166,19 @@ def test_single_step_per_kernel_parity(n2f, widths):
 
 @pytest.mark.parametrize("widths", [0, 1])
 def test_single_step_activations_and_gradients(n2f, widths):
-    """The whole step chained (oracle from the same weights, its own activations): the ReLU
-    mask is a decision floating point takes, so a pre-activation within rounding of zero may be
-    switched differently on the two sides. Such units must be rare and sit at a near-zero
-    pre-activation; tensors downstream of one (deltas and gradients of lower layers) are held to
-    1e-3 and every other tensor to 1e-4."""
+    """The whole step chained (oracle from the same weights, its own activations). The ReLU
+    mask is a decision floating point takes: a pre-activation within rounding of zero may be
+    switched on one side and off on the other, and the switched unit then carries a
+    full-size delta on one side only, which the next dgrad spreads over all its outputs. Such
+    units must be rare and sit at a near-zero pre-activation; deltas and gradients are compared
+    (1e-4) wherever no mask above them differs, and at least one step must be free of such
+    units. The per-kernel test above holds every kernel to 1e-4 on identical inputs."""
     clean, noisy = _small_case()
     ow = oracle.WIDTHS_PLIT if widths == 0 else oracle.WIDTHS_W64
     tr = n2f.Trainer(noisy, n2f.params(seed=0, widths=widths))
     job = oracle.Job(noisy, oracle.Params(widths=ow, seed=0))
     sl = layer_slices(ow)
+    clean_steps = 0
     for pair in (0, 2, 1, 3):
         job.set_theta(tr.export(n2f.N2F_X_THETA))
         tr.step(pair)
@@ -191,14 +194,18 @@ def test_single_step_activations_and_gradients(n2f, widths):
             flips.append(int(flip.sum()))
         assert rel_err(tr.export(n2f.N2F_X_DZ), job.get(oracle.DZ)) < REL_STEP
         g, go = tr.export(n2f.N2F_X_GRAD), job.get(oracle.GRAD)
+        compared = 0
         for l in range(8, 0, -1):
-            upstream = sum(flips[l - 1:])  # masks applied on the way from the head down to l
-            tol = REL_STEP if upstream == 0 else 10 * REL_STEP
+            if sum(flips[l - 1:]):  # a mask on the way from the head down to layer l differs
+                continue
             d, do = tr.export(n2f.N2F_X_DELTA, l), job.get(oracle.DELTA, l)
-            assert rel_err(d, do) < tol, (pair, l, flips)
+            assert rel_err(d, do) < REL_STEP, (pair, l, flips)
             ws, bs = sl[l - 1]
-            assert rel_err(g[ws], go[ws]) < tol and rel_err(g[bs], go[bs]) < tol, (pair, l, flips)
-        print(f"pair {pair}: ReLU decisions differing per layer {flips}")
+            assert rel_err(g[ws], go[ws]) < REL_STEP and rel_err(g[bs], go[bs]) < REL_STEP
+            compared += 1
+        clean_steps += compared == 8
+        print(f"pair {pair}: ReLU decisions differing per layer {flips}, layers compared {compared}")
+    assert clean_steps >= 1
 
 
 def test_zero_steps_equals_one_forward_pass(n2f):
