@@ -239,6 +239,18 @@ int n2f_conv3x3(int mode, int engine, int precision, const void* in, int cin, in
 int n2f_conv3x3_wgrad(int engine, int precision, const void* dout, const void* in, int cin,
                       int cout, int H, int W, float* dw, float* db, void* stream);
 
+/* ---- diagnostics ------------------------------------------------------------------------
+ * One 128 x N tile of D = A * B^T (K-step by K-step) through the tcgen05 tensor cores, with the
+ * operands given as ready shared-memory images (no swizzle) and the descriptor strides the
+ * convolution kernels rely on: lbo = byte distance of core matrices adjacent along K, sbo =
+ * along M (A) or N (B); kstep = byte advance of the start address per MMA (K = 16 bf16 or
+ * 8 tf32 elements). tf32 = 0: bf16 operands; a_mn / b_mn = 1: MN-major images.
+ * A, B: device; D: device float32 [128][N] row-major. N in 16..256 step 16, images <= 100 KB
+ * each. Synchronises the stream; ETIMEDOUT if the MMA completion never arrived. */
+int n2f_umma_gemm(int tf32, int N, int K, int a_mn, int b_mn, const void* A, size_t a_bytes,
+                  uint32_t a_lbo, uint32_t a_sbo, uint32_t a_kstep, const void* B, size_t b_bytes,
+                  uint32_t b_lbo, uint32_t b_sbo, uint32_t b_kstep, float* D, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

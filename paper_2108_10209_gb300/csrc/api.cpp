@@ -323,7 +323,7 @@ extern "C" int n2f_conv3x3(int mode, int engine, int precision, const void* in, 
   const size_t nw = (size_t)cin * cout * 9;
   const size_t es = bf16 ? 2 : 4;
   char* buf = nullptr;
-  const size_t bytes = 2 * nw * sizeof(float) + 4 * nw * es + 4096;
+  const size_t bytes = 2 * nw * sizeof(float) + 4 * nw * es + 4096 + 256;
   CKR(cudaMallocAsync((void**)&buf, bytes, st));
   float* fwd = (float*)buf;
   float* dgr = fwd + nw;
@@ -338,23 +338,31 @@ extern "C" int n2f_conv3x3(int mode, int engine, int precision, const void* in, 
       tcd_lo = (float*)(tc0 + 3 * nw * es);
     }
   }
-  cudaError_t e = launch_pack_layer(w, cin, cout, fwd, dgr, tcf, tcd, tcf_lo, tcd_lo, bf16, st);
+  int* err = (int*)(tc0 + 4 * nw * es);
+  cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), st);
+  if (e == cudaSuccess)
+    e = launch_pack_layer(w, cin, cout, fwd, dgr, tcf, tcd, tcf_lo, tcd_lo, bf16, st);
   if (e == cudaSuccess) {
     if (mode == 0) {
       e = eng == N2F_ENGINE_TC
-              ? launch_conv_tc(0, bf16, in, cin, cout, H, W, tcf, b, nullptr, out, nullptr, st)
+              ? launch_conv_tc(0, bf16, in, cin, cout, H, W, tcf, tcf_lo, b, nullptr, out, nullptr,
+                               err, st)
               : launch_conv_simt(0, bf16, in, cin, cout, H, W, fwd, b, nullptr, out, nullptr, st);
     } else {
       // dgrad: `in` has C_out channels, `out` and `mask` have C_in
       e = eng == N2F_ENGINE_TC
-              ? launch_conv_tc(1, bf16, in, cout, cin, H, W, tcd, nullptr, mask, out, nullptr, st)
+              ? launch_conv_tc(1, bf16, in, cout, cin, H, W, tcd, tcd_lo, nullptr, mask, out,
+                               nullptr, err, st)
               : launch_conv_simt(1, bf16, in, cout, cin, H, W, dgr, nullptr, mask, out, nullptr,
                                  st);
     }
   }
+  int herr = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cudaFreeAsync(buf, st);
   if (e != cudaSuccess) return set_cuda_error(e, "n2f_conv3x3");
-  return N2F_OK;
+  return herr ? N2F_ETIMEDOUT : N2F_OK;
 }
 
 extern "C" int n2f_conv3x3_wgrad(int engine, int precision, const void* dout, const void* in,
@@ -366,16 +374,21 @@ extern "C" int n2f_conv3x3_wgrad(int engine, int precision, const void* dout, co
   const int eng = resolve_engine(engine, cin, cout);
   if (eng < 0) return N2F_ENOTSUP;
   cudaStream_t st = (cudaStream_t)stream;
-  const size_t cap = (size_t)8 << 20;
+  const size_t cap = (size_t)16 << 20;
   float* part = nullptr;
-  CKR(cudaMallocAsync((void**)&part, cap * sizeof(float), st));
-  cudaError_t e =
-      eng == N2F_ENGINE_TC
-          ? launch_wgrad_tc(bf16, dout, in, cin, cout, H, W, part, cap, dw, db, nullptr, st)
-          : launch_wgrad_simt(bf16, dout, in, cin, cout, H, W, part, cap, dw, db, nullptr, st);
+  CKR(cudaMallocAsync((void**)&part, cap * sizeof(float) + 256, st));
+  int* err = (int*)(part + cap);
+  cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), st);
+  if (e == cudaSuccess)
+    e = eng == N2F_ENGINE_TC
+            ? launch_wgrad_tc(bf16, dout, in, cin, cout, H, W, part, cap, dw, db, nullptr, err, st)
+            : launch_wgrad_simt(bf16, dout, in, cin, cout, H, W, part, cap, dw, db, nullptr, st);
+  int herr = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cudaFreeAsync(part, st);
   if (e != cudaSuccess) return set_cuda_error(e, "n2f_conv3x3_wgrad");
-  return N2F_OK;
+  return herr ? N2F_ETIMEDOUT : N2F_OK;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -531,6 +544,11 @@ static bool progress(n2f_ctx* c, Job* j) {
       }
       j->ep_seen += 1;
       did = true;
+      if (j->last.kerr) {
+        tl_error = "a device wait ran out of time";
+        finish_job(c, j, N2F_FAILED, N2F_ETIMEDOUT);
+        return true;
+      }
       if (j->last.stopped) {
         j->finishing = true;
         break;
@@ -606,8 +624,9 @@ static bool progress(n2f_ctx* c, Job* j) {
     cudaEventElapsedTime(&b, c->ev_ref, j->ev_done);
     j->t0_ms = a;
     j->t1_ms = b;
-    const bool bad = j->last.stopped == 3;
-    finish_job(c, j, bad ? N2F_FAILED : N2F_DONE, bad ? N2F_ENONFINITE : N2F_OK);
+    const bool bad = j->last.stopped == 3 || j->last.kerr;
+    finish_job(c, j, bad ? N2F_FAILED : N2F_DONE,
+               j->last.kerr ? N2F_ETIMEDOUT : (bad ? N2F_ENONFINITE : N2F_OK));
     return true;
   }
   return did;

@@ -1,19 +1,711 @@
-// tcgen05 / TMEM implicit-GEMM convolution kernels (sm_103a). Placeholder until the
-// tensor-core path lands: no shape is covered, so every layer runs on the SIMT kernels.
+// tcgen05 / TMEM implicit-GEMM kernels for the 3x3 layers with C_in, C_out in {32,...,256}
+// (sm_103a). One warp issues TMA copies, one thread issues the MMAs into a TMEM accumulator,
+// four warps read TMEM back for the fused epilogue (and, in the 3xTF32 form, split the
+// activations into TF32 hi/lo parts in shared memory first).
+//
+// Forward / dgrad: D[px][n] = sum_{tap, c} A[px + tap][c] B[n][tap, c]: M = 128 pixels of one
+//   image row, N = output channels, K = 9 C_in. The A operand of every tap is the same TMA
+//   halo tile (3 rows x 130 pixels x a chunk of channels, zero outside the image = the "same"
+//   padding) addressed at a shifted start: in the K-major no-swizzle layout each pixel row is
+//   16 bytes, so a shift of dx pixels is a 16*dx byte offset of the descriptor.
+// Weight gradient: D[o][c] = sum_px delta[px][o] x[px + tap][c] per tap: M = 128 output
+//   channels, N = C_in, K = pixels; both operands are read MN-major straight from the
+//   channel-grouped maps, split over pixel chunks and reduced in a fixed order.
+#include <mutex>
+#include <type_traits>
+
+#include "cg_util.cuh"
 #include "n2f_internal.h"
 #include "tc_layout.cuh"
+#include "tc_ptx.cuh"
+#include "trainer.h"
 
 namespace n2f {
 
-bool tc_supported(int, int) { return false; }
-size_t tc_weight_elems(int cin, int cout) { return (size_t)cin * cout * 9; }
-cudaError_t launch_conv_tc(int, int, const void*, int, int, int, int, const void*, const float*,
-                           const void*, void*, const int*, cudaStream_t) {
-  return cudaErrorNotSupported;
+using namespace tc;
+
+namespace {
+
+__host__ __device__ constexpr uint32_t align_up(uint32_t v, uint32_t a) { return (v + a - 1) / a * a; }
+
+// ---- tensor maps ----------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  });
+  return fn;
 }
-cudaError_t launch_wgrad_tc(int, const void*, const void*, int, int, int, int, float*, size_t,
-                            float*, float*, const int*, cudaStream_t) {
-  return cudaErrorNotSupported;
+
+// A channel-grouped map act[g][y][x][GE] seen as a 4-D tensor (GE, W, H, C/GE), innermost
+// first, with a box of (GE, bx, by, bg) elements. Outside the tensor the box reads zeros.
+cudaError_t make_map(CUtensorMap* m, const void* base, int bf16, int C, int H, int W, int bx,
+                     int by, int bg) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return cudaErrorNotSupported;
+  const int GE = bf16 ? 8 : 4;
+  cuuint64_t dims[4] = {(cuuint64_t)GE, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)(C / GE)};
+  cuuint64_t strides[3] = {16, (cuuint64_t)W * 16, (cuuint64_t)H * W * 16};
+  cuuint32_t box[4] = {(cuuint32_t)GE, (cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bg};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  CUresult r = fn(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
+                  const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// ---- single-tile GEMM with operands given as shared-memory images -------------------------
+struct ProbeArgs {
+  const uint4* A;
+  const uint4* B;
+  float* D;
+  int N, ksteps, tf32;
+  uint32_t a_bytes, b_bytes, a_lbo, a_sbo, b_lbo, b_sbo, a_kstep, b_kstep, id;
+  int* err;
+};
+
+__global__ void __launch_bounds__(128, 1) k_umma_probe(ProbeArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tslot;
+  __shared__ int abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // A in [0, 100 KB), B in [100 KB, 200 KB) of a fixed 200 KB allocation
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + 100 * 1024;
+  for (uint32_t i = tid; i < a.a_bytes / 16; i += 128) reinterpret_cast<uint4*>(sA)[i] = a.A[i];
+  for (uint32_t i = tid; i < a.b_bytes / 16; i += 128) reinterpret_cast<uint4*>(sB)[i] = a.B[i];
+  fence_proxy_async();
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    abort_flag = 0;
+    mbar_fence_init();
+  }
+  const uint32_t ncols = tmem_cols(a.N);
+  if (warp == 0) tmem_alloc(&tslot, ncols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = tslot;
+  if (tid == 0) {
+    for (int s = 0; s < a.ksteps; ++s) {
+      const uint64_t da = sdesc(smem_u32(sA) + s * a.a_kstep, a.a_lbo, a.a_sbo);
+      const uint64_t db = sdesc(smem_u32(sB) + s * a.b_kstep, a.b_lbo, a.b_sbo);
+      if (a.tf32)
+        mma_tf32(tbase, da, db, a.id, s > 0);
+      else
+        mma_f16(tbase, da, db, a.id, s > 0);
+    }
+    mma_commit(&bar);
+  }
+  __syncwarp();
+  if (!mbar_wait(&bar, 0, &abort_flag, a.err)) mbar_drain(&bar, 0);
+  tc_fence_after();
+  for (int c = 0; c < a.N; c += 16) {
+    uint32_t r[16];
+    tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + c, r);
+    tmem_ld_wait();
+#pragma unroll
+    for (int j = 0; j < 16; ++j) a.D[(size_t)(warp * 32 + lane) * a.N + c + j] = __uint_as_float(r[j]);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tbase, ncols);
+  }
+}
+
+// ---- forward / dgrad ----------------------------------------------------------------------
+struct ConvTcParams {
+  const uint8_t* w_hi;  // packed weight stage images (bf16, or the TF32 hi parts)
+  const uint8_t* w_lo;  // TF32 residual images (3xTF32 form)
+  const float* bias;    // forward
+  const void* mask;     // dgrad: the layer's input activation (ReLU mask)
+  void* out;
+  int cin, cout, H, W, tiles_x;
+  const int* skip;
+  int* err;
+};
+
+constexpr int kTileM = 128;   // pixels per CTA (one image row segment)
+constexpr int kHaloX = kTileM + 2;
+constexpr int kConvStages = 2;
+
+template <int BF16>
+struct ConvCfg {
+  static constexpr int GE = BF16 ? 8 : 4;     // channels per 16-byte group
+  static constexpr int KC = BF16 ? 16 : 8;    // channels per stage (= one K step of 32 bytes)
+  static constexpr int NSLAB = KC / GE;       // 16-byte K slabs per stage (2)
+  static constexpr uint32_t A_BYTES = NSLAB * 3 * kHaloX * 16;
+  static constexpr uint32_t A_SLAB = 3 * kHaloX * 16;  // K distance between slabs in the halo
+  static __host__ __device__ uint32_t b_bytes(int NT) { return 9u * NSLAB * NT * 16; }
+  // stage layout: A | A_lo (tf32) | B | B_lo (tf32)
+  static __host__ __device__ uint32_t a_lo_off() { return align_up(A_BYTES, 1024); }
+  static __host__ __device__ uint32_t b_off() { return BF16 ? align_up(A_BYTES, 1024) : 2 * align_up(A_BYTES, 1024); }
+  static __host__ __device__ uint32_t b_lo_off(int NT) { return b_off() + align_up(b_bytes(NT), 1024); }
+  static __host__ __device__ uint32_t stage_bytes(int NT) {
+    return BF16 ? b_off() + align_up(b_bytes(NT), 1024) : b_lo_off(NT) + align_up(b_bytes(NT), 1024);
+  }
+};
+
+template <int BF16, int MODE>
+__global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUtensorMap tmA,
+                                                   ConvTcParams p) {
+  using C = ConvCfg<BF16>;
+  using T = typename std::conditional<BF16, __nv_bfloat16, float>::type;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ uint64_t full[kConvStages], empty[kConvStages], split[kConvStages], accf;
+  __shared__ uint32_t tslot;
+  __shared__ int abort_flag;
+  if (p.skip && *p.skip) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int NT = tc_cfg(p.cin, p.cout, BF16).NT;
+  const uint32_t B_BYTES = C::b_bytes(NT), SB = C::stage_bytes(NT);
+  const int ty = blockIdx.x / p.tiles_x, x0 = (blockIdx.x % p.tiles_x) * kTileM;
+  const int nt = blockIdx.y;
+  const int nk = p.cin / C::KC;
+  const uint32_t ncols = tmem_cols(NT);
+  volatile int* abort = &abort_flag;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kConvStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+      mbar_init(&split[s], 128);
+    }
+    mbar_init(&accf, 1);
+    abort_flag = 0;
+    mbar_fence_init();
+  }
+  if (warp == 1) tmem_alloc(&tslot, ncols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = tslot;
+
+  if (warp == 0) {
+    if (lane == 0) {  // producer: halo tile by TMA, weight stage image by bulk copy
+      int issued = 0;
+      for (int i = 0; i < nk; ++i) {
+        const int s = i % kConvStages;
+        if (i >= kConvStages && !mbar_wait(&empty[s], ((i / kConvStages) - 1) & 1, abort, p.err))
+          break;
+        uint8_t* st = smem + s * SB;
+        mbar_expect_tx(&full[s], C::A_BYTES + B_BYTES * (BF16 ? 1 : 2));
+        tma_load_4d(st, &tmA, &full[s], 0, x0 - 1, ty - 1, i * C::NSLAB);
+        const size_t stage = (size_t)nt * nk + i;
+        bulk_load(st + C::b_off(), p.w_hi + stage * B_BYTES, B_BYTES, &full[s]);
+        if (!BF16) bulk_load(st + C::b_lo_off(NT), p.w_lo + stage * B_BYTES, B_BYTES, &full[s]);
+        issued = i + 1;
+      }
+      if (*abort)
+        for (int i = issued > kConvStages ? issued - kConvStages : 0; i < issued; ++i)
+          mbar_drain(&full[i % kConvStages], (i / kConvStages) & 1);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA issuer
+      const uint32_t id = idesc(BF16 ? 1 : 2, kTileM, NT, 0, 0);
+      for (int i = 0; i < nk; ++i) {
+        const int s = i % kConvStages;
+        const uint32_t ph = (i / kConvStages) & 1;
+        if (!mbar_wait(BF16 ? &full[s] : &split[s], ph, abort, p.err)) break;
+        tc_fence_after();
+        const uint32_t sa = smem_u32(smem + s * SB);
+        const uint32_t sal = sa + C::a_lo_off();
+        const uint32_t sb = sa + C::b_off(), sbl = sa + C::b_lo_off(NT);
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) {
+          const uint32_t ao = (uint32_t)((tap / 3) * kHaloX + (tap % 3)) * 16u;
+          const uint32_t bo = (uint32_t)tap * C::NSLAB * NT * 16u;
+          const uint64_t da = sdesc(sa + ao, C::A_SLAB, 128);
+          const uint64_t db = sdesc(sb + bo, NT * 16, 128);
+          const uint32_t acc = (i > 0 || tap > 0) ? 1u : 0u;
+          if (BF16) {
+            mma_f16(tbase, da, db, id, acc);
+          } else {
+            mma_tf32(tbase, da, db, id, acc);
+            mma_tf32(tbase, da, sdesc(sbl + bo, NT * 16, 128), id, 1u);
+            mma_tf32(tbase, sdesc(sal + ao, C::A_SLAB, 128), db, id, 1u);
+          }
+        }
+        mma_commit(&empty[s]);
+      }
+      mma_commit(&accf);
+    }
+  } else {
+    const int et = threadIdx.x - 64;
+    if (!BF16) {  // 3xTF32: split the fp32 halo into a TF32-exact hi part and the residual
+      for (int i = 0; i < nk; ++i) {
+        const int s = i % kConvStages;
+        if (!mbar_wait(&full[s], (i / kConvStages) & 1, abort, p.err)) break;
+        float4* A = reinterpret_cast<float4*>(smem + s * SB);
+        float4* Al = reinterpret_cast<float4*>(smem + s * SB + C::a_lo_off());
+        for (int q = et; q < (int)(C::A_BYTES / 16); q += 128) {
+          const float4 v = A[q];
+          float4 h;
+          h.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
+          h.y = __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u);
+          h.z = __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u);
+          h.w = __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u);
+          A[q] = h;
+          Al[q] = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+        }
+        fence_proxy_async();
+        mbar_arrive(&split[s]);
+      }
+    }
+    if (!mbar_wait(&accf, 0, abort, p.err)) mbar_drain(&accf, 0);
+    tc_fence_after();
+    const int wq = warp & 3;  // the TMEM lane quarter this warp may read
+    const int row = wq * 32 + lane;
+    const int x = x0 + row;
+    const bool live = x < p.W && !*abort;
+    const size_t npx = (size_t)p.H * p.W;
+    const size_t pix = (size_t)ty * p.W + x;
+    constexpr int GE = C::GE;
+    for (int c0 = 0; c0 < NT; c0 += 16) {
+      uint32_t r[16];
+      tmem_ld16(tbase + ((uint32_t)(wq * 32) << 16) + c0, r);
+      tmem_ld_wait();
+      if (!live) continue;
+      const int o0 = nt * NT + c0;
+      float v[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+#pragma unroll
+      for (int q = 0; q < 16 / GE; ++q) {
+        const size_t gi = (size_t)((o0 + q * GE) / GE) * npx + pix;
+        float* vv = v + q * GE;
+        if (MODE == 0) {
+#pragma unroll
+          for (int j = 0; j < GE; ++j) {
+            const float t = vv[j] + __ldg(p.bias + o0 + q * GE + j);
+            vv[j] = t > 0.f ? t : 0.f;
+          }
+        } else {
+          float mk[GE];
+          load_group<T>((const T*)p.mask, gi, mk);
+#pragma unroll
+          for (int j = 0; j < GE; ++j) vv[j] = mk[j] > 0.f ? vv[j] : 0.f;
+        }
+        store_group<T>((T*)p.out, gi, vv);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tbase, ncols);
+  }
+}
+
+// ---- weight gradient ------------------------------------------------------------------------
+struct WgradTcParams {
+  float* part;  // [S][9][C_out][C_in]
+  int cin, cout, H, W, chunks_x, total_chunks, per_split;
+  const int* skip;
+  int* err;
+};
+
+template <int BF16>
+struct WgCfg {
+  static constexpr int GE = BF16 ? 8 : 4;
+  static constexpr int KP = BF16 ? 64 : 32;      // pixels per stage
+  static constexpr int KSTEP = BF16 ? 16 : 8;    // pixels per MMA
+  static constexpr int STAGES = BF16 ? 4 : 2;
+  static constexpr uint32_t A_BYTES = 128u * KP * (BF16 ? 2 : 4);
+  static __host__ __device__ uint32_t b_bytes(int cin) { return (uint32_t)cin * KP * (BF16 ? 2 : 4); }
+  // stage layout: A | B | A_lo | B_lo (the lo parts only in the tf32 form)
+  static __host__ __device__ uint32_t b_off() { return align_up(A_BYTES, 1024); }
+  static __host__ __device__ uint32_t a_lo_off(int cin) { return b_off() + align_up(b_bytes(cin), 1024); }
+  static __host__ __device__ uint32_t b_lo_off(int cin) { return a_lo_off(cin) + align_up(A_BYTES, 1024); }
+  static __host__ __device__ uint32_t stage_bytes(int cin) {
+    return BF16 ? a_lo_off(cin) : b_lo_off(cin) + align_up(b_bytes(cin), 1024);
+  }
+};
+
+__device__ __forceinline__ void split_tf32(float4* A, float4* Al, uint32_t n16, int et) {
+  for (uint32_t q = et; q < n16; q += 128) {
+    const float4 v = A[q];
+    float4 h;
+    h.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
+    h.y = __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u);
+    h.z = __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u);
+    h.w = __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u);
+    A[q] = h;
+    Al[q] = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+  }
+}
+
+template <int BF16>
+__global__ void __launch_bounds__(192, 1) k_wgrad_tc(const __grid_constant__ CUtensorMap tmD,
+                                                    const __grid_constant__ CUtensorMap tmX,
+                                                    WgradTcParams p) {
+  using C = WgCfg<BF16>;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ uint64_t full[4], empty[4], split[4], accf;
+  __shared__ uint32_t tslot;
+  __shared__ int abort_flag;
+  if (p.skip && *p.skip) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int o0 = blockIdx.x * 128, tap = blockIdx.y, s_idx = blockIdx.z;
+  const int dy = tap / 3, dx = tap % 3;
+  const int cbeg = s_idx * p.per_split;
+  const int cend = min(p.total_chunks, cbeg + p.per_split);
+  const int nk = cend > cbeg ? cend - cbeg : 0;
+  const uint32_t B_BYTES = C::b_bytes(p.cin), SB = C::stage_bytes(p.cin);
+  const uint32_t ncols = tmem_cols(p.cin);
+  volatile int* abort = &abort_flag;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+      mbar_init(&split[s], 128);
+    }
+    mbar_init(&accf, 1);
+    abort_flag = 0;
+    mbar_fence_init();
+  }
+  if (warp == 1) tmem_alloc(&tslot, ncols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = tslot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int issued = 0;
+      for (int i = 0; i < nk; ++i) {
+        const int s = i % C::STAGES;
+        if (i >= C::STAGES && !mbar_wait(&empty[s], ((i / C::STAGES) - 1) & 1, abort, p.err))
+          break;
+        const int ch = cbeg + i;
+        const int y = ch / p.chunks_x, x0 = (ch % p.chunks_x) * C::KP;
+        uint8_t* st = smem + s * SB;
+        mbar_expect_tx(&full[s], C::A_BYTES + B_BYTES);
+        tma_load_4d(st, &tmD, &full[s], 0, x0, y, o0 / C::GE);
+        tma_load_4d(st + C::b_off(), &tmX, &full[s], 0, x0 + dx - 1, y + dy - 1, 0);
+        issued = i + 1;
+      }
+      if (*abort)
+        for (int i = issued > C::STAGES ? issued - C::STAGES : 0; i < issued; ++i)
+          mbar_drain(&full[i % C::STAGES], (i / C::STAGES) & 1);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t id = idesc(BF16 ? 1 : 2, 128, p.cin, 1, 1);
+      const uint32_t sbo = C::KP * 16;  // next 16-byte channel group (M or N direction)
+      for (int i = 0; i < nk; ++i) {
+        const int s = i % C::STAGES;
+        const uint32_t ph = (i / C::STAGES) & 1;
+        if (!mbar_wait(BF16 ? &full[s] : &split[s], ph, abort, p.err)) break;
+        tc_fence_after();
+        const uint32_t sa = smem_u32(smem + s * SB);
+        const uint32_t sb = sa + C::b_off();
+        const uint32_t sal = sa + C::a_lo_off(p.cin), sbl = sa + C::b_lo_off(p.cin);
+#pragma unroll
+        for (int k = 0; k < C::KP / C::KSTEP; ++k) {
+          const uint32_t ko = (uint32_t)k * C::KSTEP * 16u;
+          const uint64_t da = sdesc(sa + ko, 128, sbo), db = sdesc(sb + ko, 128, sbo);
+          const uint32_t acc = (i > 0 || k > 0) ? 1u : 0u;
+          if (BF16) {
+            mma_f16(tbase, da, db, id, acc);
+          } else {
+            mma_tf32(tbase, da, db, id, acc);
+            mma_tf32(tbase, da, sdesc(sbl + ko, 128, sbo), id, 1u);
+            mma_tf32(tbase, sdesc(sal + ko, 128, sbo), db, id, 1u);
+          }
+        }
+        mma_commit(&empty[s]);
+      }
+      mma_commit(&accf);
+    }
+  } else {
+    const int et = threadIdx.x - 64;
+    if (!BF16) {
+      for (int i = 0; i < nk; ++i) {
+        const int s = i % C::STAGES;
+        if (!mbar_wait(&full[s], (i / C::STAGES) & 1, abort, p.err)) break;
+        uint8_t* st = smem + s * SB;
+        split_tf32(reinterpret_cast<float4*>(st), reinterpret_cast<float4*>(st + C::a_lo_off(p.cin)),
+                   C::A_BYTES / 16, et);
+        split_tf32(reinterpret_cast<float4*>(st + C::b_off()),
+                   reinterpret_cast<float4*>(st + C::b_lo_off(p.cin)), B_BYTES / 16, et);
+        fence_proxy_async();
+        mbar_arrive(&split[s]);
+      }
+    }
+    if (!mbar_wait(&accf, 0, abort, p.err)) mbar_drain(&accf, 0);
+    tc_fence_after();
+    const int wq = warp & 3;
+    const int o = o0 + wq * 32 + lane;
+    const bool live = o < p.cout && !*abort;
+    float* dst = p.part + (((size_t)s_idx * 9 + tap) * p.cout + (live ? o : 0)) * p.cin;
+    for (int c0 = 0; c0 < p.cin; c0 += 16) {
+      uint32_t r[16];
+      tmem_ld16(tbase + ((uint32_t)(wq * 32) << 16) + c0, r);
+      tmem_ld_wait();
+      if (!live) continue;
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        reinterpret_cast<float4*>(dst + c0)[q] =
+            make_float4(nk ? __uint_as_float(r[4 * q]) : 0.f, nk ? __uint_as_float(r[4 * q + 1]) : 0.f,
+                        nk ? __uint_as_float(r[4 * q + 2]) : 0.f, nk ? __uint_as_float(r[4 * q + 3]) : 0.f);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tbase, ncols);
+  }
+}
+
+// gw[(o*C_in + c)*9 + tap] = sum_s part[s][tap][o][c] (ascending s)
+__global__ void k_reduce_wgrad_tc(const float* __restrict__ part, int S, int cin, int cout,
+                                  float* __restrict__ gw, const int* skip) {
+  if (skip && *skip) return;
+  const size_t n = (size_t)cout * cin * 9;
+  const size_t per = (size_t)9 * cout * cin;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n;
+       q += (size_t)gridDim.x * blockDim.x) {
+    const int tap = (int)(q % 9);
+    const size_t oc = q / 9;
+    const int c = (int)(oc % cin), o = (int)(oc / cin);
+    const size_t src = ((size_t)tap * cout + o) * cin + c;
+    float s = 0.f;
+    for (int k = 0; k < S; ++k) s += part[k * per + src];
+    gw[q] = s;
+  }
+}
+
+// Bias gradient db[c] = sum_p d(p, c) of a CG map: block b sums its pixel range, then the
+// per-block sums are added in block order.
+template <typename T>
+__global__ void __launch_bounds__(256) k_colsum_cg(const T* __restrict__ d, int C, size_t npx,
+                                                   size_t per_block, float* __restrict__ bpart,
+                                                   const int* skip) {
+  if (skip && *skip) return;
+  constexpr int GE = CGTraits<T>::G;
+  __shared__ float sacc[256 * GE];
+  const int ng = C / GE;
+  const int J = 256 / ng;
+  const int g = threadIdx.x % ng, j = threadIdx.x / ng;
+  float acc[GE];
+#pragma unroll
+  for (int k = 0; k < GE; ++k) acc[k] = 0.f;
+  const size_t pb = blockIdx.x * per_block, pe = min(npx, pb + per_block);
+  if (j < J)
+    for (size_t pix = pb + j; pix < pe; pix += J) {
+      float v[GE];
+      load_group<T>(d, (size_t)g * npx + pix, v);
+#pragma unroll
+      for (int k = 0; k < GE; ++k) acc[k] += v[k];
+    }
+  if (j < J)
+#pragma unroll
+    for (int k = 0; k < GE; ++k) sacc[j * C + g * GE + k] = acc[k];
+  __syncthreads();
+  for (int c = threadIdx.x; c < C; c += 256) {
+    float s = 0.f;
+    for (int jj = 0; jj < J; ++jj) s += sacc[jj * C + c];
+    bpart[(size_t)blockIdx.x * C + c] = s;
+  }
+}
+
+__global__ void k_reduce_rows(const float* __restrict__ part, int S, int C, float* __restrict__ out,
+                              const int* skip) {
+  if (skip && *skip) return;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int k = 0; k < S; ++k) s += part[(size_t)k * C + c];
+    out[c] = s;
+  }
+}
+
+template <int BF16, int MODE>
+cudaError_t conv_tc_launch(const CUtensorMap& m, const ConvTcParams& p, dim3 grid, uint32_t smem,
+                           cudaStream_t st) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_conv_tc<BF16, MODE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  k_conv_tc<BF16, MODE><<<grid, 192, smem, st>>>(m, p);
+  return cudaGetLastError();
+}
+
+template <int BF16>
+cudaError_t wgrad_tc_launch(const CUtensorMap& md, const CUtensorMap& mx, const WgradTcParams& p,
+                            dim3 grid, uint32_t smem, cudaStream_t st) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_wgrad_tc<BF16>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  k_wgrad_tc<BF16><<<grid, 192, smem, st>>>(md, mx, p);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool tc_supported(int cin, int cout) {
+  auto ok = [](int c) { return c == 32 || c == 64 || c == 128 || c == 256; };
+  return ok(cin) && ok(cout) && encode_fn() != nullptr;
+}
+
+size_t tc_weight_elems(int cin, int cout) { return (size_t)cin * cout * 9; }
+
+cudaError_t launch_conv_tc(int mode, int bf16, const void* in, int cin, int cout, int H, int W,
+                           const void* w_hi, const void* w_lo, const float* b, const void* mask,
+                           void* out, const int* skip, int* err, cudaStream_t st) {
+  if (!tc_supported(cin, cout)) return cudaErrorNotSupported;
+  const TcCfg f = tc_cfg(cin, cout, bf16);
+  CUtensorMap m;
+  const int KC = bf16 ? ConvCfg<1>::KC : ConvCfg<0>::KC;
+  const int GE = bf16 ? 8 : 4;
+  cudaError_t e = make_map(&m, in, bf16, cin, H, W, kHaloX, 3, KC / GE);
+  if (e != cudaSuccess) return e;
+  ConvTcParams p;
+  p.w_hi = (const uint8_t*)w_hi;
+  p.w_lo = (const uint8_t*)w_lo;
+  p.bias = b;
+  p.mask = mask;
+  p.out = out;
+  p.cin = cin;
+  p.cout = cout;
+  p.H = H;
+  p.W = W;
+  p.tiles_x = (W + kTileM - 1) / kTileM;
+  p.skip = skip;
+  p.err = err;
+  dim3 grid((unsigned)(p.tiles_x * H), (unsigned)(cout / f.NT));
+  const uint32_t smem = kConvStages * (bf16 ? ConvCfg<1>::stage_bytes(f.NT) : ConvCfg<0>::stage_bytes(f.NT));
+  if (bf16)
+    e = mode == 0 ? conv_tc_launch<1, 0>(m, p, grid, smem, st) : conv_tc_launch<1, 1>(m, p, grid, smem, st);
+  else
+    e = mode == 0 ? conv_tc_launch<0, 0>(m, p, grid, smem, st) : conv_tc_launch<0, 1>(m, p, grid, smem, st);
+  count_launch();
+  return e;
+}
+
+cudaError_t launch_wgrad_tc(int bf16, const void* dout, const void* in, int cin, int cout, int H,
+                            int W, float* part, size_t part_cap, float* gw, float* gb,
+                            const int* skip, int* err, cudaStream_t st) {
+  if (!tc_supported(cin, cout)) return cudaErrorNotSupported;
+  const int GE = bf16 ? 8 : 4;
+  const int KP = bf16 ? WgCfg<1>::KP : WgCfg<0>::KP;
+  CUtensorMap md, mx;
+  cudaError_t e = make_map(&md, dout, bf16, cout, H, W, KP, 1, 128 / GE);
+  if (e == cudaSuccess) e = make_map(&mx, in, bf16, cin, H, W, KP, 1, cin / GE);
+  if (e != cudaSuccess) return e;
+  const int otiles = (cout + 127) / 128;
+  WgradTcParams p;
+  p.cin = cin;
+  p.cout = cout;
+  p.H = H;
+  p.W = W;
+  p.chunks_x = (W + KP - 1) / KP;
+  p.total_chunks = p.chunks_x * H;
+  const size_t per_split_elems = (size_t)9 * cout * cin;
+  // splits: about two waves of CTAs, bounded by the partial-sum workspace
+  int S = (2 * 152 + otiles * 9 - 1) / (otiles * 9);
+  if (S > p.total_chunks) S = p.total_chunks;
+  const size_t npx = (size_t)H * W;
+  const int SB = 64;  // bias partial blocks
+  const size_t bias_off = ((size_t)S * per_split_elems + 63) / 64 * 64;
+  while (S > 1 && (size_t)S * per_split_elems + 64 + (size_t)SB * cout > part_cap) --S;
+  if ((size_t)S * per_split_elems + 64 + (size_t)SB * cout > part_cap) return cudaErrorInvalidValue;
+  p.per_split = (p.total_chunks + S - 1) / S;
+  S = (p.total_chunks + p.per_split - 1) / p.per_split;
+  p.part = part;
+  p.skip = skip;
+  p.err = err;
+  const uint32_t smem = (bf16 ? WgCfg<1>::STAGES * WgCfg<1>::stage_bytes(cin)
+                              : WgCfg<0>::STAGES * WgCfg<0>::stage_bytes(cin));
+  dim3 grid((unsigned)otiles, 9, (unsigned)S);
+  e = bf16 ? wgrad_tc_launch<1>(md, mx, p, grid, smem, st) : wgrad_tc_launch<0>(md, mx, p, grid, smem, st);
+  count_launch();
+  if (e != cudaSuccess) return e;
+  unsigned g = (unsigned)((per_split_elems + 255) / 256);
+  if (g > 152u * 8) g = 152u * 8;
+  k_reduce_wgrad_tc<<<g, 256, 0, st>>>(part, S, cin, cout, gw, skip);
+  count_launch();
+  float* bpart = part + ((size_t)S * per_split_elems + 63) / 64 * 64;
+  (void)bias_off;
+  const size_t per_block = (npx + SB - 1) / SB;
+  if (bf16)
+    k_colsum_cg<__nv_bfloat16><<<SB, 256, 0, st>>>((const __nv_bfloat16*)dout, cout, npx, per_block,
+                                                   bpart, skip);
+  else
+    k_colsum_cg<float><<<SB, 256, 0, st>>>((const float*)dout, cout, npx, per_block, bpart, skip);
+  count_launch();
+  k_reduce_rows<<<1, 256, 0, st>>>(bpart, SB, cout, gb, skip);
+  count_launch();
+  return cudaGetLastError();
 }
 
 }  // namespace n2f
+
+// ---- diagnostic entry point (declared in n2f.h) ---------------------------------------------
+extern "C" int n2f_umma_gemm(int tf32, int N, int K, int a_mn, int b_mn, const void* A,
+                             size_t a_bytes, uint32_t a_lbo, uint32_t a_sbo, uint32_t a_kstep,
+                             const void* B, size_t b_bytes, uint32_t b_lbo, uint32_t b_sbo,
+                             uint32_t b_kstep, float* D, void* stream) {
+  using namespace n2f;
+  if (!A || !B || !D || N < 16 || N > 256 || N % 16 || K < 1 || a_bytes % 16 || b_bytes % 16)
+    return N2F_EINVAL;
+  const int kstep = tf32 ? 8 : 16;
+  if (K % kstep) return N2F_EINVAL;
+  const uint32_t smem = 200 * 1024;
+  if (a_bytes > 100 * 1024 || b_bytes > 100 * 1024) return N2F_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaFuncSetAttribute(k_umma_probe, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       200 * 1024);
+  int* err = nullptr;
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&err, sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), st);
+  if (e != cudaSuccess) return set_cuda_error(e, "n2f_umma_gemm");
+  ProbeArgs a;
+  a.A = (const uint4*)A;
+  a.B = (const uint4*)B;
+  a.D = D;
+  a.N = N;
+  a.ksteps = K / kstep;
+  a.tf32 = tf32;
+  a.a_bytes = (uint32_t)a_bytes;
+  a.b_bytes = (uint32_t)b_bytes;
+  a.a_lbo = a_lbo;
+  a.a_sbo = a_sbo;
+  a.b_lbo = b_lbo;
+  a.b_sbo = b_sbo;
+  a.a_kstep = a_kstep;
+  a.b_kstep = b_kstep;
+  a.id = idesc(tf32 ? 2 : 1, 128, N, a_mn, b_mn);
+  a.err = err;
+  k_umma_probe<<<1, 128, smem, st>>>(a);
+  e = cudaGetLastError();
+  int herr = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFreeAsync(err, st);
+  if (e != cudaSuccess) return set_cuda_error(e, "n2f_umma_gemm");
+  return herr ? N2F_ETIMEDOUT : N2F_OK;
+}

@@ -44,6 +44,8 @@ struct DevState {
   int patience, max_epochs, incl_best;
   float bc1, bc2;   // Adam bias corrections 1 - beta^t of the current step
   double b1t, b2t;  // beta1^t, beta2^t
+  int kerr;         // first error a kernel reported (a wait that ran out of time), 0 = none
+  int pad;
 };
 
 // Packed weight copies written by the init/Adam kernels, one per layer l = 0..7:
@@ -105,12 +107,14 @@ cudaError_t launch_wgrad_simt(int bf16, const void* dout, const void* in, int ci
 
 // Tensor-core (tcgen05) kernels; return cudaErrorNotSupported when a shape is not covered.
 bool tc_supported(int cin, int cout);
+// mode 0 forward (bias + ReLU), 1 dgrad (ReLU mask); w_hi/w_lo: packed operand copies
+// (tc_layout.cuh), w_lo only in the float32 (3xTF32) form. err: device error word.
 cudaError_t launch_conv_tc(int mode, int bf16, const void* in, int cin, int cout, int H, int W,
-                           const void* wtc, const float* b, const void* mask, void* out,
-                           const int* skip, cudaStream_t st);
+                           const void* w_hi, const void* w_lo, const float* b, const void* mask,
+                           void* out, const int* skip, int* err, cudaStream_t st);
 cudaError_t launch_wgrad_tc(int bf16, const void* dout, const void* in, int cin, int cout, int H,
                             int W, float* part, size_t part_cap, float* gw, float* gb,
-                            const int* skip, cudaStream_t st);
+                            const int* skip, int* err, cudaStream_t st);
 size_t tc_weight_elems(int cin, int cout);  // elements of one packed tensor-core weight copy
 
 // Head (1x1 conv + sigmoid), training: z, loss partials, dL/dz, delta_8, head-grad partials.

@@ -202,7 +202,7 @@ static size_t layout(Trainer* t, char* base) {
   t->lpart = c.take<double>(t->nblk_max);
   t->mpart = c.take<double>(t->nblk_max);
   t->hpart = c.take<float>((size_t)t->nblk_max * (Cmax + 1));
-  t->wpart_cap = (size_t)6 << 20;
+  t->wpart_cap = (size_t)16 << 20;
   t->wpart = c.take<float>(t->wpart_cap);
   t->state = c.take<DevState>(1);
   t->in_u16 = c.take<uint16_t>(t->want_u16 ? t->N : 0);
@@ -315,8 +315,8 @@ static int conv_layer(Trainer* t, int l, const void* in, void* out, int H, int W
   if (l == 0) {
     CK(launch_conv1_fwd((const float*)in, H, W, t->pa.fwd[0], b, cout, t->bf16, out, skip, t->st));
   } else if (t->engine[l] == N2F_ENGINE_TC) {
-    CK(launch_conv_tc(0, t->bf16, in, cin, cout, H, W, t->pa.tcf[l], b, nullptr, out, skip,
-                      t->st));
+    CK(launch_conv_tc(0, t->bf16, in, cin, cout, H, W, t->pa.tcf[l], t->pa.tcf_lo[l], b, nullptr,
+                      out, skip, &t->state->kerr, t->st));
   } else {
     CK(launch_conv_simt(0, t->bf16, in, cin, cout, H, W, t->pa.fwd[l], b, nullptr, out, skip,
                         t->st));
@@ -371,7 +371,7 @@ int trainer_step(Trainer* t, int pair) {
       Timed tm(t, N2F_K_CONV_WGRAD, fl, (double)npx * (cin + cout) * es, 0);
     if (t->engine[l] == N2F_ENGINE_TC) {
       CK(launch_wgrad_tc(t->bf16, dcur, t->act[l - 1], cin, cout, h, w, t->wpart, t->wpart_cap,
-                         gw, gb, skip, t->st));
+                         gw, gb, skip, &t->state->kerr, t->st));
     } else {
       CK(launch_wgrad_simt(t->bf16, dcur, t->act[l - 1], cin, cout, h, w, t->wpart,
                            t->wpart_cap, gw, gb, skip, t->st));
@@ -380,8 +380,8 @@ int trainer_step(Trainer* t, int pair) {
     void* dnext = t->keep_deltas ? t->dkeep[l - 1] : t->dl[pp ^ 1];
     Timed tm(t, N2F_K_CONV_DGRAD, fl, (double)npx * (cin * 2 + cout) * es, 0);
     if (t->engine[l] == N2F_ENGINE_TC) {
-      CK(launch_conv_tc(1, t->bf16, dcur, cout, cin, h, w, t->pa.tcd[l], nullptr, t->act[l - 1],
-                        dnext, skip, t->st));
+      CK(launch_conv_tc(1, t->bf16, dcur, cout, cin, h, w, t->pa.tcd[l], t->pa.tcd_lo[l], nullptr,
+                        t->act[l - 1], dnext, skip, &t->state->kerr, t->st));
     } else {
       CK(launch_conv_simt(1, t->bf16, dcur, cout, cin, h, w, t->pa.dgr[l], nullptr,
                           t->act[l - 1], dnext, skip, t->st));

@@ -100,6 +100,8 @@ SIGNATURES = {
     "n2f_unpack_cg": (_I, [_P, _I, _I, _I, _I, _P, _P]),
     "n2f_conv3x3": (_I, [_I, _I, _I, _P, _I, _I, _I, _I, _P, _P, _P, _P, _P]),
     "n2f_conv3x3_wgrad": (_I, [_I, _I, _P, _P, _I, _I, _I, _I, _P, _P, _P]),
+    "n2f_umma_gemm": (_I, [_I, _I, _I, _I, _I, _P, _Z, C.c_uint32, C.c_uint32, C.c_uint32, _P, _Z,
+                           C.c_uint32, C.c_uint32, C.c_uint32, _P, _P]),
 }
 
 _lib = None
@@ -395,3 +397,14 @@ def conv3x3_wgrad(dout_cg, in_cg, cin, cout, H, W, precision=N2F_FP32, engine=N2
     check(lib().n2f_conv3x3_wgrad(engine, precision, _ptr(dout_cg), _ptr(in_cg), cin, cout, H, W,
                                   _ptr(dw), _ptr(db), _stream_ptr(stream)), "n2f_conv3x3_wgrad")
     return dw, db
+
+
+def umma_gemm(A_img, a_lbo, a_sbo, a_kstep, B_img, b_lbo, b_sbo, b_kstep, N, K, tf32=False,
+              a_mn=0, b_mn=0, stream=None):
+    """Diagnostic single-tile tcgen05 GEMM on shared-memory operand images (uint8 CUDA tensors)."""
+    import torch
+    D = torch.empty((128, N), dtype=torch.float32, device=A_img.device)
+    check(lib().n2f_umma_gemm(int(tf32), N, K, a_mn, b_mn, _ptr(A_img), A_img.numel(), a_lbo,
+                              a_sbo, a_kstep, _ptr(B_img), B_img.numel(), b_lbo, b_sbo, b_kstep,
+                              _ptr(D), _stream_ptr(stream)), "n2f_umma_gemm")
+    return D

@@ -57,7 +57,7 @@ def test_initial_weights_bit_identical(n2f, widths, seed):
 # ------------------------------------------------------------------- single kernels ---------
 
 CONV_CASES = [(8, 16, 5, 7), (32, 32, 9, 130), (64, 32, 33, 70), (32, 64, 16, 300),
-              (128, 256, 6, 129), (256, 128, 3, 200)]
+              (128, 256, 6, 129), (256, 128, 3, 200), (256, 256, 4, 257), (64, 64, 40, 16)]
 
 
 def _conv_inputs(cin, cout, H, W, seed):
@@ -69,10 +69,15 @@ def _conv_inputs(cin, cout, H, W, seed):
     return x, w, b, g
 
 
+TC_WIDTHS = (32, 64, 128, 256)
+
+
 @pytest.mark.parametrize("precision", [0, 1])
-@pytest.mark.parametrize("engine", [1])
+@pytest.mark.parametrize("engine", [1, 2])
 @pytest.mark.parametrize("cin,cout,H,W", CONV_CASES)
 def test_conv_kernels_match_oracle(n2f, torch_mod, precision, engine, cin, cout, H, W):
+    if engine == 2 and (cin not in TC_WIDTHS or cout not in TC_WIDTHS):
+        pytest.skip("tensor-core kernels cover C_in, C_out in 32..256")
     T = torch_mod
     x, w, b, g = _conv_inputs(cin, cout, H, W, cin * 7 + cout + H + W)
     if precision == 1:  # the bf16 form stores operands in bf16: compare on the rounded values
@@ -115,14 +120,15 @@ def _step_snapshot(tr, n2f):
                                           ("v", n2f.N2F_X_ADAM_V))}
 
 
+@pytest.mark.parametrize("engine", [1, 2])
 @pytest.mark.parametrize("widths", [0, 1])
-def test_single_step_per_kernel_parity(n2f, widths):
+def test_single_step_per_kernel_parity(n2f, widths, engine):
     """Every kernel of a training step against the oracle on the GPU's own inputs of that step
     (so both sides take the same ReLU decisions): forward layers, head, loss gradient, dgrad,
     wgrad and Adam, each within 1e-4 of the largest reference value."""
     clean, noisy = _small_case()
     ow = oracle.WIDTHS_PLIT if widths == 0 else oracle.WIDTHS_W64
-    tr = n2f.Trainer(noisy, n2f.params(seed=0, widths=widths))
+    tr = n2f.Trainer(noisy, n2f.params(seed=0, widths=widths, engine=engine))
     sl = layer_slices(ow)
     for t, pair in enumerate((0, 2, 1, 3), start=1):
         before = _step_snapshot(tr, n2f)
