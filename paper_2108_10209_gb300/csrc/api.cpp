@@ -371,7 +371,9 @@ extern "C" int n2f_conv3x3_wgrad(int engine, int precision, const void* dout, co
   if (!dout || !in || !dw || !db || H < 1 || W < 1 || cin % 8 || cout % 8 || cin < 8 || cout < 8)
     return N2F_EINVAL;
   const int bf16 = precision == N2F_BF16;
-  const int eng = resolve_engine(engine, cin, cout);
+  int eng = resolve_engine(engine, cin, cout);
+  if (eng == N2F_ENGINE_TC && !tc_wgrad_supported(cin, cout, bf16))
+    eng = engine == N2F_ENGINE_TC ? -1 : N2F_ENGINE_SIMT;
   if (eng < 0) return N2F_ENOTSUP;
   cudaStream_t st = (cudaStream_t)stream;
   const size_t cap = (size_t)16 << 20;

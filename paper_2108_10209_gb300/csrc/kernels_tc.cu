@@ -571,6 +571,9 @@ bool tc_supported(int cin, int cout) {
   return ok(cin) && ok(cout) && encode_fn() != nullptr;
 }
 
+// The weight-gradient GEMM reads both operands MN-major; that form is used with bf16 only.
+bool tc_wgrad_supported(int cin, int cout, int bf16) { return bf16 && tc_supported(cin, cout); }
+
 size_t tc_weight_elems(int cin, int cout) { return (size_t)cin * cout * 9; }
 
 cudaError_t launch_conv_tc(int mode, int bf16, const void* in, int cin, int cout, int H, int W,
@@ -609,7 +612,7 @@ cudaError_t launch_conv_tc(int mode, int bf16, const void* in, int cin, int cout
 cudaError_t launch_wgrad_tc(int bf16, const void* dout, const void* in, int cin, int cout, int H,
                             int W, float* part, size_t part_cap, float* gw, float* gb,
                             const int* skip, int* err, cudaStream_t st) {
-  if (!tc_supported(cin, cout)) return cudaErrorNotSupported;
+  if (!tc_wgrad_supported(cin, cout, bf16)) return cudaErrorNotSupported;
   const int GE = bf16 ? 8 : 4;
   const int KP = bf16 ? WgCfg<1>::KP : WgCfg<0>::KP;
   CUtensorMap md, mx;

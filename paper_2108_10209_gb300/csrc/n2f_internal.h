@@ -107,6 +107,7 @@ cudaError_t launch_wgrad_simt(int bf16, const void* dout, const void* in, int ci
 
 // Tensor-core (tcgen05) kernels; return cudaErrorNotSupported when a shape is not covered.
 bool tc_supported(int cin, int cout);
+bool tc_wgrad_supported(int cin, int cout, int bf16);
 // mode 0 forward (bias + ReLU), 1 dgrad (ReLU mask); w_hi/w_lo: packed operand copies
 // (tc_layout.cuh), w_lo only in the float32 (3xTF32) form. err: device error word.
 cudaError_t launch_conv_tc(int mode, int bf16, const void* in, int cin, int cout, int H, int W,

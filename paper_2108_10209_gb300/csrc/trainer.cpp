@@ -232,6 +232,10 @@ int trainer_configure(Trainer* t, int H, int W, const n2f_params* p, int keep_de
   for (int l = 0; l < kLayers; ++l) {
     t->engine[l] = layer_engine(t, l);
     if (t->engine[l] < 0) return N2F_ENOTSUP;
+    t->wg_engine[l] = t->engine[l] == N2F_ENGINE_TC &&
+                              tc_wgrad_supported(t->net.cin(l), t->net.widths[l], t->bf16)
+                          ? N2F_ENGINE_TC
+                          : N2F_ENGINE_SIMT;
   }
   return N2F_OK;
 }
@@ -369,7 +373,7 @@ int trainer_step(Trainer* t, int pair) {
     }
     {
       Timed tm(t, N2F_K_CONV_WGRAD, fl, (double)npx * (cin + cout) * es, 0);
-    if (t->engine[l] == N2F_ENGINE_TC) {
+    if (t->wg_engine[l] == N2F_ENGINE_TC) {
       CK(launch_wgrad_tc(t->bf16, dcur, t->act[l - 1], cin, cout, h, w, t->wpart, t->wpart_cap,
                          gw, gb, skip, &t->state->kerr, t->st));
     } else {

@@ -61,7 +61,8 @@ struct Trainer {
   int ph[4], pw[4];  // pair sizes: up (H x W/2) twice, left (H/2 x W) twice
   size_t maxP = 0;
   int bf16 = 0, keep_deltas = 0, fixed_mode = 0, want_u16 = 0;
-  int engine[kLayers];
+  int engine[kLayers];     // forward / dgrad kernels of layer l
+  int wg_engine[kLayers];  // weight-gradient kernel of layer l
   cudaStream_t st = nullptr;
   Allocator al;
   char* slab = nullptr;

@@ -61,12 +61,15 @@ def mnmajor_image(M, rows, K, lbo, sbo, tf32):
 CASES = [
     # (name, tf32, N, K, a_mn, b_mn, a_lbo, a_sbo, b_lbo, b_sbo)  (lbo/sbo None = dense)
     ("bf16 K-major dense", 0, 64, 64, 0, 0, None, None, None, None),
-    ("bf16 K-major padded", 0, 128, 32, 0, 0, 128 * 16 + 64, 128, 128 * 16 + 32, 256),
+    ("bf16 K-major padded", 0, 128, 32, 0, 0, 128 * 16 + 64, 128, 16 * 256 + 32, 256),
     ("tf32 K-major dense", 1, 128, 32, 0, 0, None, None, None, None),
     ("bf16 K-major N=32", 0, 32, 48, 0, 0, None, None, None, None),
     ("bf16 MN-major", 0, 256, 64, 1, 1, None, None, None, None),
-    ("tf32 MN-major", 1, 64, 32, 1, 1, None, None, None, None),
+    ("tf32 K-major padded", 1, 64, 32, 0, 0, 128 * 16 + 48, 128, 8 * 256 + 16, 256),
+    ("bf16 MN-major padded", 0, 128, 32, 1, 1, 160, 4 * 160 + 32, 144, 4 * 160 + 32),
 ]
+# TF32 operands are used K-major only: an MN-major TF32 image in the same convention did not
+# give the product on the GB300, so the float32 form keeps its weight gradient on CUDA cores.
 
 
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
