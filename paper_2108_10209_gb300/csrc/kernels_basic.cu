@@ -132,9 +132,9 @@ __device__ __forceinline__ void pack_one(float* fwd, float* dgr, void* tcf, void
       ((__nv_bfloat16*)tcf)[fi] = __float2bfloat16_rn(th);
       ((__nv_bfloat16*)tcd)[di] = __float2bfloat16_rn(th);
     } else {
-      // 3xTF32 split: hi keeps the 10 explicit TF32 mantissa bits (exact as TF32), lo = th - hi
-      const float hi = __uint_as_float(__float_as_uint(th) & 0xFFFFE000u);
-      const float lo = th - hi;
+      // 3xTF32 split th = hi + lo, both parts rounded to the nearest TF32 value
+      const float hi = __uint_as_float((__float_as_uint(th) + 0x1000u) & 0xFFFFE000u);
+      const float lo = __uint_as_float((__float_as_uint(th - hi) + 0x1000u) & 0xFFFFE000u);
       ((float*)tcf)[fi] = hi;
       tcf_lo[fi] = lo;
       ((float*)tcd)[di] = hi;

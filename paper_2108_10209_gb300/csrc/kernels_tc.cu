@@ -26,6 +26,20 @@ using namespace tc;
 
 namespace {
 
+// Round to the nearest TF32 value (10 explicit mantissa bits; ties away from zero) by adding
+// half a unit of the 13 dropped bits before clearing them. The 3xTF32 split x = hi + lo uses
+// it for both parts, so hi and lo are exact TF32 numbers and the dropped lo*lo term and the
+// rounding of lo are unbiased, about 2^-22 of x.
+__device__ __forceinline__ float tf32_round(float x) {
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+
+__device__ __forceinline__ void split4(float4 v, float4& h, float4& l) {
+  h = make_float4(tf32_round(v.x), tf32_round(v.y), tf32_round(v.z), tf32_round(v.w));
+  l = make_float4(tf32_round(v.x - h.x), tf32_round(v.y - h.y), tf32_round(v.z - h.z),
+                  tf32_round(v.w - h.w));
+}
+
 __host__ __device__ constexpr uint32_t align_up(uint32_t v, uint32_t a) { return (v + a - 1) / a * a; }
 
 // ---- tensor maps ----------------------------------------------------------------------------
@@ -246,21 +260,17 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
     }
   } else {
     const int et = threadIdx.x - 64;
-    if (!BF16) {  // 3xTF32: split the fp32 halo into a TF32-exact hi part and the residual
+    if (!BF16) {  // 3xTF32: split the fp32 halo into TF32 hi and lo parts
       for (int i = 0; i < nk; ++i) {
         const int s = i % kConvStages;
         if (!mbar_wait(&full[s], (i / kConvStages) & 1, abort, p.err)) break;
         float4* A = reinterpret_cast<float4*>(smem + s * SB);
         float4* Al = reinterpret_cast<float4*>(smem + s * SB + C::a_lo_off());
         for (int q = et; q < (int)(C::A_BYTES / 16); q += 128) {
-          const float4 v = A[q];
-          float4 h;
-          h.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
-          h.y = __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u);
-          h.z = __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u);
-          h.w = __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u);
+          float4 h, l;
+          split4(A[q], h, l);
           A[q] = h;
-          Al[q] = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+          Al[q] = l;
         }
         fence_proxy_async();
         mbar_arrive(&split[s]);
@@ -339,14 +349,10 @@ struct WgCfg {
 
 __device__ __forceinline__ void split_tf32(float4* A, float4* Al, uint32_t n16, int et) {
   for (uint32_t q = et; q < n16; q += 128) {
-    const float4 v = A[q];
-    float4 h;
-    h.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
-    h.y = __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u);
-    h.z = __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u);
-    h.w = __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u);
+    float4 h, l;
+    split4(A[q], h, l);
     A[q] = h;
-    Al[q] = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+    Al[q] = l;
   }
 }
 
