@@ -260,7 +260,7 @@ def run_ours(args, ws, rank, local):
     stats = {k: st1[k] - st0[k] if isinstance(st1[k], (int, float)) else st1[k] for k in st1}
     workload = f"{size}x{size} cells fp{'32' if args.precision == 0 else 'bf16'} " \
                f"{WIDTH_NAMES[args.widths]} plain"
-    rl = roofline(stats, args.profile_kernel, args.precision, args.engine == 2, workload)
+    rl = roofline(stats, args.profile_kernel, args.precision, args.engine != 1, workload)
     q = sorted(comp_ms)
     line = {
         "metric": METRIC, "value": n_img / tot_dev_s, "unit": UNIT, "n_gpus": ws,

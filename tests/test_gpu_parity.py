@@ -172,20 +172,28 @@ def test_single_step_per_kernel_parity(n2f, widths, engine):
                 assert rel_err(got[s_] - before["theta"][s_], th[s_] - before["theta"][s_]) < REL_STEP
 
 
+@pytest.mark.parametrize("engine", [1, 2])
 @pytest.mark.parametrize("widths", [0, 1])
-def test_single_step_activations_and_gradients(n2f, widths):
+def test_single_step_activations_and_gradients(n2f, widths, engine):
     """The whole step chained (oracle from the same weights, its own activations). The ReLU
     mask is a decision floating point takes: a pre-activation within rounding of zero may be
     switched on one side and off on the other, and the switched unit then carries a
     full-size delta on one side only, which the next dgrad spreads over all its outputs. Such
     units must be rare and sit at a near-zero pre-activation; deltas and gradients are compared
     (1e-4) wherever no mask above them differs, and at least one step must be free of such
-    units. The per-kernel test above holds every kernel to 1e-4 on identical inputs."""
+    units. The per-kernel test above holds every kernel to 1e-4 on identical inputs.
+
+    Engines: the CUDA-core kernels compute in float32 and hold every tensor to 1e-4. The
+    tensor-core float32 form multiplies in 3xTF32 (about 2^-22 per product instead of 2^-24);
+    activations and deltas stay within 1e-4, but a weight gradient is a sum over every pixel
+    with strong sign cancellation, which magnifies that difference relative to its largest
+    element, so weight gradients on that engine are held to 1e-3."""
     clean, noisy = _small_case()
     ow = oracle.WIDTHS_PLIT if widths == 0 else oracle.WIDTHS_W64
-    tr = n2f.Trainer(noisy, n2f.params(seed=0, widths=widths))
+    tr = n2f.Trainer(noisy, n2f.params(seed=0, widths=widths, engine=engine))
     job = oracle.Job(noisy, oracle.Params(widths=ow, seed=0))
     sl = layer_slices(ow)
+    gtol = REL_STEP if engine == 1 else 10 * REL_STEP
     clean_steps = 0
     for pair in (0, 2, 1, 3):
         job.set_theta(tr.export(n2f.N2F_X_THETA))
@@ -209,7 +217,7 @@ def test_single_step_activations_and_gradients(n2f, widths):
             d, do = tr.export(n2f.N2F_X_DELTA, l), job.get(oracle.DELTA, l)
             assert rel_err(d, do) < REL_STEP, (pair, l, flips)
             ws, bs = sl[l - 1]
-            assert rel_err(g[ws], go[ws]) < REL_STEP and rel_err(g[bs], go[bs]) < REL_STEP
+            assert rel_err(g[ws], go[ws]) < gtol and rel_err(g[bs], go[bs]) < gtol, (pair, l)
             compared += 1
         clean_steps += compared == 8
         print(f"pair {pair}: ReLU decisions differing per layer {flips}, layers compared {compared}")
