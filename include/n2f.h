@@ -235,9 +235,7 @@ int n2f_conv3x3(int mode, int engine, int precision, const void* in, int cin, in
                 int W, const float* w, const float* b, const void* mask, void* out,
                 void* stream);
 /* Weight/bias gradient of one 3x3 layer: dw[C_out][C_in][3][3] and db[C_out] (float32,
- * overwritten) from dout (CG, C_out channels) and in (CG, C_in channels). The tensor-core
- * weight gradient exists for bfloat16 only (ENOTSUP for engine TC with float32; AUTO picks
- * the CUDA-core kernel there). */
+ * overwritten) from dout (CG, C_out channels) and in (CG, C_in channels). */
 int n2f_conv3x3_wgrad(int engine, int precision, const void* dout, const void* in, int cin,
                       int cout, int H, int W, float* dw, float* db, void* stream);
 

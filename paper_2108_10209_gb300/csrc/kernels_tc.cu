@@ -331,28 +331,64 @@ struct WgradTcParams {
 };
 
 template <int BF16>
-struct WgCfg {
-  static constexpr int GE = BF16 ? 8 : 4;
-  static constexpr int KP = BF16 ? 64 : 32;      // pixels per stage
-  static constexpr int KSTEP = BF16 ? 16 : 8;    // pixels per MMA
-  static constexpr int STAGES = BF16 ? 4 : 2;
-  static constexpr uint32_t A_BYTES = 128u * KP * (BF16 ? 2 : 4);
-  static __host__ __device__ uint32_t b_bytes(int cin) { return (uint32_t)cin * KP * (BF16 ? 2 : 4); }
-  // stage layout: A | B | A_lo | B_lo (the lo parts only in the tf32 form)
+struct WgCfg;
+
+// bf16: both operands MN-major straight from the TMA tiles.
+// stage: A (delta, 128 channels x KP px) | B (x, C_in x KP px)
+template <>
+struct WgCfg<1> {
+  static constexpr int GE = 8;
+  static constexpr int KP = 64;     // pixels per stage
+  static constexpr int KSTEP = 16;  // pixels per MMA
+  static constexpr int STAGES = 4;
+  static constexpr uint32_t A_BYTES = 128u * KP * 2;
+  static __host__ __device__ uint32_t b_bytes(int cin) { return (uint32_t)cin * KP * 2; }
   static __host__ __device__ uint32_t b_off() { return align_up(A_BYTES, 1024); }
-  static __host__ __device__ uint32_t a_lo_off(int cin) { return b_off() + align_up(b_bytes(cin), 1024); }
-  static __host__ __device__ uint32_t b_lo_off(int cin) { return a_lo_off(cin) + align_up(A_BYTES, 1024); }
-  static __host__ __device__ uint32_t stage_bytes(int cin) {
-    return BF16 ? a_lo_off(cin) : b_lo_off(cin) + align_up(b_bytes(cin), 1024);
-  }
+  static __host__ __device__ uint32_t stage_bytes(int cin) { return b_off() + align_up(b_bytes(cin), 1024); }
 };
 
-__device__ __forceinline__ void split_tf32(float4* A, float4* Al, uint32_t n16, int et) {
-  for (uint32_t q = et; q < n16; q += 128) {
-    float4 h, l;
-    split4(A[q], h, l);
-    A[q] = h;
-    Al[q] = l;
+// float32 (3xTF32): TF32 operands are read K-major, so the split pass that forms the hi and lo
+// parts also transposes the MN-major TMA tiles: K-major image = 4-pixel K slabs of all rows,
+// row r at 16 r bytes inside a slab (8-row core matrices 128 bytes apart).
+// stage: raw A | raw B | hi A | hi B | lo A | lo B
+template <>
+struct WgCfg<0> {
+  static constexpr int GE = 4;
+  static constexpr int KP = 16;
+  static constexpr int KSTEP = 8;
+  static constexpr int STAGES = 2;
+  static constexpr uint32_t A_BYTES = 128u * KP * 4;
+  static __host__ __device__ uint32_t b_bytes(int cin) { return (uint32_t)cin * KP * 4; }
+  static __host__ __device__ uint32_t b_off() { return align_up(A_BYTES, 1024); }
+  static __host__ __device__ uint32_t part(int cin) { return b_off() + align_up(b_bytes(cin), 1024); }
+  static __host__ __device__ uint32_t hi_off() { return 0; }  // relative to part(): hi, then lo
+  static __host__ __device__ uint32_t stage_bytes(int cin) { return 3 * part(cin); }
+};
+
+// Transposing 3xTF32 split of one [rows/4 groups][KP px][4 ch] tile into K-major hi and lo
+// images [KP/4 slabs][rows][4 px]: thread block unit = 4 channels x 4 pixels.
+__device__ __forceinline__ void split_transpose(const float* raw, float* hi, float* lo, int rows,
+                                                int kp, int et) {
+  const int units = (rows / 4) * (kp / 4);
+  const uint32_t slab = (uint32_t)rows * 4;  // floats per 4-pixel K slab
+  for (int u = et; u < units; u += 128) {
+    const int g = u / (kp / 4), pb = u % (kp / 4);
+    const float4* src = reinterpret_cast<const float4*>(raw) + (size_t)g * kp + pb * 4;
+    float v[4][4];  // [pixel][channel]
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float4 t = src[q];
+      v[q][0] = t.x; v[q][1] = t.y; v[q][2] = t.z; v[q][3] = t.w;
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float4 x = make_float4(v[0][j], v[1][j], v[2][j], v[3][j]);
+      float4 h, l;
+      split4(x, h, l);
+      const uint32_t off = pb * slab + (uint32_t)(4 * g + j) * 4;
+      *reinterpret_cast<float4*>(hi + off) = h;
+      *reinterpret_cast<float4*>(lo + off) = l;
+    }
   }
 }
 
@@ -412,27 +448,30 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc(const __grid_constant__ CUt
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t id = idesc(BF16 ? 1 : 2, 128, p.cin, 1, 1);
-      const uint32_t sbo = C::KP * 16;  // next 16-byte channel group (M or N direction)
+      const uint32_t id = idesc(BF16 ? 1 : 2, 128, p.cin, BF16 ? 1 : 0, BF16 ? 1 : 0);
       for (int i = 0; i < nk; ++i) {
         const int s = i % C::STAGES;
         const uint32_t ph = (i / C::STAGES) & 1;
         if (!mbar_wait(BF16 ? &full[s] : &split[s], ph, abort, p.err)) break;
         tc_fence_after();
         const uint32_t sa = smem_u32(smem + s * SB);
-        const uint32_t sb = sa + C::b_off();
-        const uint32_t sal = sa + C::a_lo_off(p.cin), sbl = sa + C::b_lo_off(p.cin);
 #pragma unroll
         for (int k = 0; k < C::KP / C::KSTEP; ++k) {
-          const uint32_t ko = (uint32_t)k * C::KSTEP * 16u;
-          const uint64_t da = sdesc(sa + ko, 128, sbo), db = sdesc(sb + ko, 128, sbo);
           const uint32_t acc = (i > 0 || k > 0) ? 1u : 0u;
-          if (BF16) {
-            mma_f16(tbase, da, db, id, acc);
+          if constexpr (BF16) {
+            // MN-major: K-adjacent core matrices (8 px) 128 B apart, channel groups KP*16 apart
+            const uint32_t ko = (uint32_t)k * C::KSTEP * 16u, sbo = C::KP * 16;
+            mma_f16(tbase, sdesc(sa + ko, 128, sbo), sdesc(sa + C::b_off() + ko, 128, sbo), id, acc);
           } else {
-            mma_tf32(tbase, da, db, id, acc);
-            mma_tf32(tbase, da, sdesc(sbl + ko, 128, sbo), id, 1u);
-            mma_tf32(tbase, sdesc(sal + ko, 128, sbo), db, id, 1u);
+            // K-major: 4-pixel slabs of all rows (A: 128 rows, B: C_in rows), one MMA = 2 slabs
+            const uint32_t la = 128u * 16u, lb = (uint32_t)p.cin * 16u;
+            const uint32_t part = C::part(p.cin);
+            const uint32_t hA = sa + part, hB = hA + C::b_off();
+            const uint32_t lA = sa + 2 * part, lB = lA + C::b_off();
+            const uint64_t dah = sdesc(hA + k * 2 * la, la, 128), dbh = sdesc(hB + k * 2 * lb, lb, 128);
+            mma_tf32(tbase, dah, dbh, id, acc);
+            mma_tf32(tbase, dah, sdesc(lB + k * 2 * lb, lb, 128), id, 1u);
+            mma_tf32(tbase, sdesc(lA + k * 2 * la, la, 128), dbh, id, 1u);
           }
         }
         mma_commit(&empty[s]);
@@ -441,15 +480,17 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc(const __grid_constant__ CUt
     }
   } else {
     const int et = threadIdx.x - 64;
-    if (!BF16) {
+    if constexpr (!BF16) {
       for (int i = 0; i < nk; ++i) {
         const int s = i % C::STAGES;
         if (!mbar_wait(&full[s], (i / C::STAGES) & 1, abort, p.err)) break;
         uint8_t* st = smem + s * SB;
-        split_tf32(reinterpret_cast<float4*>(st), reinterpret_cast<float4*>(st + C::a_lo_off(p.cin)),
-                   C::A_BYTES / 16, et);
-        split_tf32(reinterpret_cast<float4*>(st + C::b_off()),
-                   reinterpret_cast<float4*>(st + C::b_lo_off(p.cin)), B_BYTES / 16, et);
+        const uint32_t part = C::part(p.cin);
+        split_transpose(reinterpret_cast<const float*>(st), reinterpret_cast<float*>(st + part),
+                        reinterpret_cast<float*>(st + 2 * part), 128, C::KP, et);
+        split_transpose(reinterpret_cast<const float*>(st + C::b_off()),
+                        reinterpret_cast<float*>(st + part + C::b_off()),
+                        reinterpret_cast<float*>(st + 2 * part + C::b_off()), p.cin, C::KP, et);
         fence_proxy_async();
         mbar_arrive(&split[s]);
       }
@@ -577,8 +618,10 @@ bool tc_supported(int cin, int cout) {
   return ok(cin) && ok(cout) && encode_fn() != nullptr;
 }
 
-// The weight-gradient GEMM reads both operands MN-major; that form is used with bf16 only.
-bool tc_wgrad_supported(int cin, int cout, int bf16) { return bf16 && tc_supported(cin, cout); }
+bool tc_wgrad_supported(int cin, int cout, int bf16) {
+  (void)bf16;
+  return tc_supported(cin, cout);
+}
 
 size_t tc_weight_elems(int cin, int cout) { return (size_t)cin * cout * 9; }
 

@@ -95,9 +95,7 @@ def test_conv_kernels_match_oracle(n2f, torch_mod, precision, engine, cin, cout,
                                   engine=engine), cout, H, W, precision).cpu().numpy()
     d = n2f.unpack_cg(n2f.conv3x3(1, gc, cin, cout, H, W, wd, mask_cg=xc, precision=precision,
                                   engine=engine), cin, H, W, precision).cpu().numpy()
-    # the tensor-core weight gradient exists for bf16 only (AUTO = CUDA cores for float32)
-    wg_engine = engine if precision == 1 else min(engine, 1)
-    dw, db = n2f.conv3x3_wgrad(gc, xc, cin, cout, H, W, precision=precision, engine=wg_engine)
+    dw, db = n2f.conv3x3_wgrad(gc, xc, cin, cout, H, W, precision=precision, engine=engine)
     dw, db = dw.cpu().numpy(), db.cpu().numpy()
     y_ref = oracle.conv3x3_fwd(x, wq, bq, relu=True)
     d_ref = oracle.conv3x3_dgrad(g, wq) * (x > 0)

@@ -69,7 +69,8 @@ CASES = [
     ("bf16 MN-major padded", 0, 128, 32, 1, 1, 160, 4 * 160 + 32, 144, 4 * 160 + 32),
 ]
 # TF32 operands are used K-major only: an MN-major TF32 image in the same convention did not
-# give the product on the GB300, so the float32 form keeps its weight gradient on CUDA cores.
+# give the product on the GB300, so the float32-form weight gradient transposes its operands
+# to K-major while splitting them into TF32 hi and lo parts.
 
 
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
