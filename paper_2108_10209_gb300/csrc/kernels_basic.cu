@@ -540,23 +540,22 @@ cudaError_t launch_head_train(const void* a8, int C, int npx, const float* w9, c
   N2F_LAUNCH_CHECK();
 }
 
-// Ordered sums of the head partials; advances Adam's step counter and bias corrections.
-__global__ void k_step_finish(const float* __restrict__ hpart, const double* __restrict__ lpart,
-                              int nblk, int C, int npx, float* __restrict__ gw9,
-                              float* __restrict__ gb9, DevState* state, float b1, float b2) {
+// Loss sum (fixed tree over the per-block partials) and Adam's step counter and bias
+// corrections; the head-gradient partials are summed by the column reducer.
+__global__ void k_step_finish(const double* __restrict__ lpart, int nblk, int npx, DevState* state,
+                              float b1, float b2) {
   if (state->stopped) return;
-  for (int q = threadIdx.x; q <= C; q += blockDim.x) {
-    float s = 0.f;
-    for (int k = 0; k < nblk; ++k) s += hpart[(size_t)k * (C + 1) + q];
-    if (q < C)
-      gw9[q] = s;
-    else
-      gb9[0] = s;
+  __shared__ double sh[256];
+  double s = 0.0;
+  for (int k = threadIdx.x; k < nblk; k += blockDim.x) s += lpart[k];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
   }
   if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int k = 0; k < nblk; ++k) s += lpart[k];
-    state->loss = s / (double)npx;
+    state->loss = sh[0] / (double)npx;
     state->t += 1;
     state->b1t *= (double)b1;
     state->b2t *= (double)b2;
@@ -568,7 +567,11 @@ __global__ void k_step_finish(const float* __restrict__ hpart, const double* __r
 cudaError_t launch_step_finish(const float* hpart, const double* loss_part, int nblk, int C,
                                int npx, float* gw9, float* gb9, DevState* state, float b1,
                                float b2, cudaStream_t st) {
-  k_step_finish<<<1, 256, 0, st>>>(hpart, loss_part, nblk, C, npx, gw9, gb9, state, b1, b2);
+  // gw9[0..C) and gb9 (= gw9 + C in the flat vector) are the columns of hpart
+  if (gb9 != gw9 + C) return cudaErrorInvalidValue;
+  cudaError_t e = launch_reduce_cols(hpart, nblk, C + 1, gw9, &state->stopped, st);
+  if (e != cudaSuccess) return e;
+  k_step_finish<<<1, 256, 0, st>>>(loss_part, nblk, npx, state, b1, b2);
   N2F_LAUNCH_CHECK();
 }
 

@@ -359,24 +359,35 @@ struct WgCfg<0> {
   static constexpr int STAGES = 2;
   static constexpr uint32_t A_BYTES = 128u * KP * 4;
   static __host__ __device__ uint32_t b_bytes(int cin) { return (uint32_t)cin * KP * 4; }
+  // K-major split images use a slab stride of rows*16 + 16 bytes (bank-conflict-free stores)
+  static __host__ __device__ uint32_t slab(int rows) { return (uint32_t)rows * 16u + 16u; }
+  static __host__ __device__ uint32_t kimg(int rows) { return (KP / 4) * slab(rows); }
+  static __host__ __device__ uint32_t raw_bytes(int cin) { return align_up(A_BYTES, 1024) + align_up(b_bytes(cin), 1024); }
   static __host__ __device__ uint32_t b_off() { return align_up(A_BYTES, 1024); }
-  static __host__ __device__ uint32_t part(int cin) { return b_off() + align_up(b_bytes(cin), 1024); }
-  static __host__ __device__ uint32_t hi_off() { return 0; }  // relative to part(): hi, then lo
-  static __host__ __device__ uint32_t stage_bytes(int cin) { return 3 * part(cin); }
+  // hi | lo images, each [A (128 rows) | B (C_in rows)]
+  static __host__ __device__ uint32_t kpart(int cin) { return align_up(kimg(128), 1024) + align_up(kimg(cin), 1024); }
+  static __host__ __device__ uint32_t kb_off() { return align_up(kimg(128), 1024); }
+  static __host__ __device__ uint32_t hi_off(int cin) { return raw_bytes(cin); }
+  static __host__ __device__ uint32_t lo_off(int cin) { return raw_bytes(cin) + kpart(cin); }
+  static __host__ __device__ uint32_t stage_bytes(int cin) { return raw_bytes(cin) + 2 * kpart(cin); }
 };
 
 // Transposing 3xTF32 split of one [rows/4 groups][KP px][4 ch] tile into K-major hi and lo
-// images [KP/4 slabs][rows][4 px]: thread block unit = 4 channels x 4 pixels.
+// images [KP/4 slabs][rows][4 px] with a slab stride of rows*16 + 16 bytes. A thread handles a
+// 4-channel x 4-pixel unit; reads are rotated by the unit's pixel block so a quarter warp touches
+// distinct banks, and the padded slab stride does the same for the stores.
 __device__ __forceinline__ void split_transpose(const float* raw, float* hi, float* lo, int rows,
                                                 int kp, int et) {
-  const int units = (rows / 4) * (kp / 4);
-  const uint32_t slab = (uint32_t)rows * 4;  // floats per 4-pixel K slab
+  const int pbs = kp / 4;
+  const int units = (rows / 4) * pbs;
+  const uint32_t slab = (uint32_t)rows * 4 + 4;  // floats
   for (int u = et; u < units; u += 128) {
-    const int g = u / (kp / 4), pb = u % (kp / 4);
+    const int g = u / pbs, pb = u % pbs;
     const float4* src = reinterpret_cast<const float4*>(raw) + (size_t)g * kp + pb * 4;
     float v[4][4];  // [pixel][channel]
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int r = 0; r < 4; ++r) {
+      const int q = (r + pb) & 3;
       const float4 t = src[q];
       v[q][0] = t.x; v[q][1] = t.y; v[q][2] = t.z; v[q][3] = t.w;
     }
@@ -464,10 +475,9 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc(const __grid_constant__ CUt
             mma_f16(tbase, sdesc(sa + ko, 128, sbo), sdesc(sa + C::b_off() + ko, 128, sbo), id, acc);
           } else {
             // K-major: 4-pixel slabs of all rows (A: 128 rows, B: C_in rows), one MMA = 2 slabs
-            const uint32_t la = 128u * 16u, lb = (uint32_t)p.cin * 16u;
-            const uint32_t part = C::part(p.cin);
-            const uint32_t hA = sa + part, hB = hA + C::b_off();
-            const uint32_t lA = sa + 2 * part, lB = lA + C::b_off();
+            const uint32_t la = C::slab(128), lb = C::slab(p.cin);
+            const uint32_t hA = sa + C::hi_off(p.cin), hB = hA + C::kb_off();
+            const uint32_t lA = sa + C::lo_off(p.cin), lB = lA + C::kb_off();
             const uint64_t dah = sdesc(hA + k * 2 * la, la, 128), dbh = sdesc(hB + k * 2 * lb, lb, 128);
             mma_tf32(tbase, dah, dbh, id, acc);
             mma_tf32(tbase, dah, sdesc(lB + k * 2 * lb, lb, 128), id, 1u);
@@ -485,12 +495,12 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc(const __grid_constant__ CUt
         const int s = i % C::STAGES;
         if (!mbar_wait(&full[s], (i / C::STAGES) & 1, abort, p.err)) break;
         uint8_t* st = smem + s * SB;
-        const uint32_t part = C::part(p.cin);
-        split_transpose(reinterpret_cast<const float*>(st), reinterpret_cast<float*>(st + part),
-                        reinterpret_cast<float*>(st + 2 * part), 128, C::KP, et);
+        const uint32_t hi = C::hi_off(p.cin), lo = C::lo_off(p.cin);
+        split_transpose(reinterpret_cast<const float*>(st), reinterpret_cast<float*>(st + hi),
+                        reinterpret_cast<float*>(st + lo), 128, C::KP, et);
         split_transpose(reinterpret_cast<const float*>(st + C::b_off()),
-                        reinterpret_cast<float*>(st + part + C::b_off()),
-                        reinterpret_cast<float*>(st + 2 * part + C::b_off()), p.cin, C::KP, et);
+                        reinterpret_cast<float*>(st + hi + C::kb_off()),
+                        reinterpret_cast<float*>(st + lo + C::kb_off()), p.cin, C::KP, et);
         fence_proxy_async();
         mbar_arrive(&split[s]);
       }
@@ -573,15 +583,34 @@ __global__ void __launch_bounds__(256) k_colsum_cg(const T* __restrict__ d, int 
   }
 }
 
-__global__ void k_reduce_rows(const float* __restrict__ part, int S, int C, float* __restrict__ out,
+}  // namespace
+
+// out[c] = sum_{r < R} part[r * C + c]: one block per column, each thread sums a fixed strided
+// subset of rows in order, then a fixed tree: deterministic for a given R.
+__global__ void k_reduce_cols(const float* __restrict__ part, int R, int C, float* __restrict__ out,
                               const int* skip) {
   if (skip && *skip) return;
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
-    float s = 0.f;
-    for (int k = 0; k < S; ++k) s += part[(size_t)k * C + c];
-    out[c] = s;
+  __shared__ float sh[256];
+  const int c = blockIdx.x;
+  float s = 0.f;
+  for (int r = threadIdx.x; r < R; r += blockDim.x) s += part[(size_t)r * C + c];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
   }
+  if (threadIdx.x == 0) out[c] = sh[0];
 }
+
+cudaError_t launch_reduce_cols(const float* part, int R, int C, float* out, const int* skip,
+                               cudaStream_t st) {
+  k_reduce_cols<<<C, 256, 0, st>>>(part, R, C, out, skip);
+  count_launch();
+  return cudaGetLastError();
+}
+
+namespace {
 
 template <int BF16, int MODE>
 cudaError_t conv_tc_launch(const CUtensorMap& m, const ConvTcParams& p, dim3 grid, uint32_t smem,
@@ -677,11 +706,17 @@ cudaError_t launch_wgrad_tc(int bf16, const void* dout, const void* in, int cin,
   p.chunks_x = (W + KP - 1) / KP;
   p.total_chunks = p.chunks_x * H;
   const size_t per_split_elems = (size_t)9 * cout * cin;
-  // splits: about two waves of CTAs, bounded by the partial-sum workspace
-  int S = (2 * 152 + otiles * 9 - 1) / (otiles * 9);
+  // splits: two waves of the CTAs that fit per SM (rounded down, so no nearly empty wave),
+  // bounded by the partial-sum workspace
+  const uint32_t smem_need = (bf16 ? WgCfg<1>::STAGES * WgCfg<1>::stage_bytes(cin)
+                                   : WgCfg<0>::STAGES * WgCfg<0>::stage_bytes(cin));
+  const int per_sm = (int)((227u * 1024u) / (smem_need + 2048u));
+  int S = (2 * 152 * (per_sm > 0 ? per_sm : 1)) / (otiles * 9);
+  if (S < 1) S = 1;
   if (S > p.total_chunks) S = p.total_chunks;
   const size_t npx = (size_t)H * W;
-  const int SB = 64;  // bias partial blocks
+  int SB = (int)((npx + 511) / 512);  // bias partial blocks
+  if (SB > 1024) SB = 1024;
   const size_t bias_off = ((size_t)S * per_split_elems + 63) / 64 * 64;
   while (S > 1 && (size_t)S * per_split_elems + 64 + (size_t)SB * cout > part_cap) --S;
   if ((size_t)S * per_split_elems + 64 + (size_t)SB * cout > part_cap) return cudaErrorInvalidValue;
@@ -709,9 +744,7 @@ cudaError_t launch_wgrad_tc(int bf16, const void* dout, const void* in, int cin,
   else
     k_colsum_cg<float><<<SB, 256, 0, st>>>((const float*)dout, cout, npx, per_block, bpart, skip);
   count_launch();
-  k_reduce_rows<<<1, 256, 0, st>>>(bpart, SB, cout, gb, skip);
-  count_launch();
-  return cudaGetLastError();
+  return launch_reduce_cols(bpart, SB, cout, gb, skip, st);
 }
 
 }  // namespace n2f
