@@ -239,6 +239,23 @@ int n2f_conv3x3(int mode, int engine, int precision, const void* in, int cin, in
 int n2f_conv3x3_wgrad(int engine, int precision, const void* dout, const void* in, int cin,
                       int cout, int H, int W, float* dw, float* db, void* stream);
 
+/* Allocation-free variant of n2f_conv3x3_wgrad (same arguments, same results up to the
+ * summation order of the pixel splits). The paper has no counterpart: this exists for callers
+ * that cannot allocate device memory when they need a weight gradient -- a process whose device
+ * memory is wholly reserved by another allocator (a framework's caching pool or a fixed arena),
+ * where a cudaMalloc would fail or fragment it, or a latency-bound loop that must not block on
+ * the CUDA allocator. The partial-sum workspace is a fixed 16 MiB device array compiled into the
+ * library: every GPU the library is loaded on holds it until the process exits, and nothing is
+ * allocated or freed per call (no cudaMalloc / cudaFree / cudaMallocAsync).
+ *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ *    that device current; make that first call before any stream capture on that device.
+ *  - All calls share the one array and it keeps the last call's contents: calls that can overlap
+ *    on the GPU (different streams, or several host threads) race and must be serialised.
+ *  - A layer needs 9*C_in*C_out + 1025*C_out + 64 floats of the 4 Mi-float array; larger layers
+ *    return N2F_ETOOBIG. Synchronises the stream; N2F_ETIMEDOUT if a kernel wait ran out. */
+int n2f_conv3x3_wgrad_noalloc(int engine, int precision, const void* dout, const void* in, int cin,
+                              int cout, int H, int W, float* dw, float* db, void* stream);
+
 /* ---- diagnostics ------------------------------------------------------------------------
  * One 128 x N tile of D = A * B^T (K-step by K-step) through the tcgen05 tensor cores, with the
  * operands given as ready shared-memory images (no swizzle) and the descriptor strides the

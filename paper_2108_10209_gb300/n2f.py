@@ -100,6 +100,7 @@ SIGNATURES = {
     "n2f_unpack_cg": (_I, [_P, _I, _I, _I, _I, _P, _P]),
     "n2f_conv3x3": (_I, [_I, _I, _I, _P, _I, _I, _I, _I, _P, _P, _P, _P, _P]),
     "n2f_conv3x3_wgrad": (_I, [_I, _I, _P, _P, _I, _I, _I, _I, _P, _P, _P]),
+    "n2f_conv3x3_wgrad_noalloc": (_I, [_I, _I, _P, _P, _I, _I, _I, _I, _P, _P, _P]),
     "n2f_umma_gemm": (_I, [_I, _I, _I, _I, _I, _P, _Z, C.c_uint32, C.c_uint32, C.c_uint32, _P, _Z,
                            C.c_uint32, C.c_uint32, C.c_uint32, _P, _P]),
 }
@@ -408,3 +409,12 @@ def umma_gemm(A_img, a_lbo, a_sbo, a_kstep, B_img, b_lbo, b_sbo, b_kstep, N, K, 
                               a_sbo, a_kstep, _ptr(B_img), B_img.numel(), b_lbo, b_sbo, b_kstep,
                               _ptr(D), _stream_ptr(stream)), "n2f_umma_gemm")
     return D
+
+
+def conv3x3_wgrad_noalloc(dout_cg, in_cg, cin, cout, H, W, dw, db, precision=N2F_FP32,
+                          engine=N2F_ENGINE_AUTO, stream=None):
+    """n2f_conv3x3_wgrad_noalloc into caller-provided dw [C_out][C_in][3][3] and db [C_out]
+    (float32 CUDA tensors); the library allocates nothing for the call."""
+    check(lib().n2f_conv3x3_wgrad_noalloc(engine, precision, _ptr(dout_cg), _ptr(in_cg), cin, cout,
+                                          H, W, _ptr(dw), _ptr(db), _stream_ptr(stream)),
+          "n2f_conv3x3_wgrad_noalloc")
