@@ -531,6 +531,159 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc(const __grid_constant__ CUt
   }
 }
 
+// ---- bf16 weight gradient, several taps per CTA -----------------------------------------
+// A CTA covers a group of taps that share image rows: the x halo tile (R rows x (KP + 2)
+// pixels x C_in, MN-major) is loaded once per pixel chunk and each tap's B operand is the
+// same tile at a descriptor offset of (row, dx) pixels (16 bytes per pixel). The group's
+// accumulators sit side by side in TMEM (taps x C_in <= 512 columns).
+struct TapGroups {
+  int n;                                  // groups
+  int first[9], count[9], row0[9];        // taps first..first+count-1, rows row0..row0+R-1
+  int R;                                  // halo rows (same for every group)
+};
+
+TapGroups tap_groups(int cin) {
+  TapGroups g{};
+  if (cin <= 32) {  // 9 x 32 = 288 columns: all taps, 3-row halo
+    g.n = 1; g.first[0] = 0; g.count[0] = 9; g.row0[0] = 0; g.R = 3;
+  } else if (cin <= 128) {  // one row of 3 taps per group
+    g.n = 3; g.R = 1;
+    for (int r = 0; r < 3; ++r) { g.first[r] = 3 * r; g.count[r] = 3; g.row0[r] = r; }
+  } else {  // C_in = 256: two taps fill TMEM, (dx 0-1) and (dx 2) per row
+    g.n = 6; g.R = 1;
+    for (int r = 0; r < 3; ++r) {
+      g.first[2 * r] = 3 * r; g.count[2 * r] = 2; g.row0[2 * r] = r;
+      g.first[2 * r + 1] = 3 * r + 2; g.count[2 * r + 1] = 1; g.row0[2 * r + 1] = r;
+    }
+  }
+  return g;
+}
+
+struct WgBf16Params {
+  float* part;  // [S][9][C_out][C_in]
+  int cin, cout, H, W, chunks_x, total_chunks, per_split;
+  TapGroups tg;
+  const int* skip;
+  int* err;
+};
+
+constexpr int kWbKP = 64;       // pixels per stage
+constexpr int kWbStages = 3;
+constexpr uint32_t kWbA = 128u * kWbKP * 2;  // delta tile, 128 channels (zero-filled past C_out)
+
+__host__ __device__ inline uint32_t wb_b_bytes(int cin, int R) {
+  return (uint32_t)(cin / 8) * R * (kWbKP + 2) * 16;
+}
+__host__ __device__ inline uint32_t wb_stage(int cin, int R) {
+  return align_up(kWbA, 1024) + align_up(wb_b_bytes(cin, R), 1024);
+}
+
+__global__ void __launch_bounds__(192, 1) k_wgrad_tc_bf16(const __grid_constant__ CUtensorMap tmD,
+                                                         const __grid_constant__ CUtensorMap tmX,
+                                                         WgBf16Params p) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ uint64_t full[kWbStages], empty[kWbStages], accf;
+  __shared__ uint32_t tslot;
+  __shared__ int abort_flag;
+  if (p.skip && *p.skip) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int o0 = blockIdx.x * 128, grp = blockIdx.y, s_idx = blockIdx.z;
+  const int t0 = p.tg.first[grp], nt = p.tg.count[grp], r0 = p.tg.row0[grp], R = p.tg.R;
+  const int cbeg = s_idx * p.per_split;
+  const int cend = min(p.total_chunks, cbeg + p.per_split);
+  const int nk = cend > cbeg ? cend - cbeg : 0;
+  const uint32_t BB = wb_b_bytes(p.cin, R), SB = wb_stage(p.cin, R);
+  const uint32_t b_off = align_up(kWbA, 1024);
+  const uint32_t ncols = tmem_cols(nt * p.cin);
+  volatile int* abort = &abort_flag;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kWbStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(&accf, 1);
+    abort_flag = 0;
+    mbar_fence_init();
+  }
+  if (warp == 1) tmem_alloc(&tslot, ncols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = tslot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int issued = 0;
+      for (int i = 0; i < nk; ++i) {
+        const int s = i % kWbStages;
+        if (i >= kWbStages && !mbar_wait(&empty[s], ((i / kWbStages) - 1) & 1, abort, p.err))
+          break;
+        const int ch = cbeg + i;
+        const int y = ch / p.chunks_x, x0 = (ch % p.chunks_x) * kWbKP;
+        uint8_t* st = smem + s * SB;
+        mbar_expect_tx(&full[s], kWbA + BB);
+        tma_load_4d(st, &tmD, &full[s], 0, x0, y, o0 / 8);
+        tma_load_4d(st + b_off, &tmX, &full[s], 0, x0 - 1, y + r0 - 1, 0);
+        issued = i + 1;
+      }
+      if (*abort)
+        for (int i = issued > kWbStages ? issued - kWbStages : 0; i < issued; ++i)
+          mbar_drain(&full[i % kWbStages], (i / kWbStages) & 1);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t id = idesc(1, 128, p.cin, 1, 1);
+      const uint32_t a_sbo = kWbKP * 16;                    // next 8-channel group of delta
+      const uint32_t b_sbo = (uint32_t)R * (kWbKP + 2) * 16;  // next 8-channel group of x
+      for (int i = 0; i < nk; ++i) {
+        const int s = i % kWbStages;
+        if (!mbar_wait(&full[s], (i / kWbStages) & 1, abort, p.err)) break;
+        tc_fence_after();
+        const uint32_t sa = smem_u32(smem + s * SB), sb = sa + b_off;
+        for (int j = 0; j < nt; ++j) {
+          const int tap = t0 + j;
+          const uint32_t boff = (uint32_t)(((tap / 3) - r0) * (kWbKP + 2) + (tap % 3)) * 16u;
+#pragma unroll
+          for (int k = 0; k < kWbKP / 16; ++k) {
+            const uint32_t ko = (uint32_t)k * 16u * 16u;
+            mma_f16(tbase + (uint32_t)(j * p.cin), sdesc(sa + ko, 128, a_sbo),
+                    sdesc(sb + boff + ko, 128, b_sbo), id, (i > 0 || k > 0) ? 1u : 0u);
+          }
+        }
+        mma_commit(&empty[s]);
+      }
+      mma_commit(&accf);
+    }
+  } else {
+    if (!mbar_wait(&accf, 0, abort, p.err)) mbar_drain(&accf, 0);
+    tc_fence_after();
+    const int wq = warp & 3;
+    const int o = o0 + wq * 32 + lane;
+    const bool live = o < p.cout && !*abort;
+    for (int j = 0; j < nt; ++j) {
+      const int tap = t0 + j;
+      float* dst = p.part + (((size_t)s_idx * 9 + tap) * p.cout + (live ? o : 0)) * p.cin;
+      for (int c0 = 0; c0 < p.cin; c0 += 16) {
+        uint32_t r[16];
+        tmem_ld16(tbase + ((uint32_t)(wq * 32) << 16) + (uint32_t)(j * p.cin + c0), r);
+        tmem_ld_wait();
+        if (!live) continue;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          reinterpret_cast<float4*>(dst + c0)[q] = make_float4(
+              nk ? __uint_as_float(r[4 * q]) : 0.f, nk ? __uint_as_float(r[4 * q + 1]) : 0.f,
+              nk ? __uint_as_float(r[4 * q + 2]) : 0.f, nk ? __uint_as_float(r[4 * q + 3]) : 0.f);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tbase, ncols);
+  }
+}
+
 // gw[(o*C_in + c)*9 + tap] = sum_s part[s][tap][o][c] (ascending s)
 __global__ void k_reduce_wgrad_tc(const float* __restrict__ part, int S, int cin, int cout,
                                   float* __restrict__ gw, const int* skip) {
@@ -687,10 +840,72 @@ cudaError_t launch_conv_tc(int mode, int bf16, const void* in, int cin, int cout
   return e;
 }
 
+static cudaError_t launch_wgrad_tc_bf16(const void* dout, const void* in, int cin, int cout, int H,
+                                        int W, float* part, size_t part_cap, float* gw, float* gb,
+                                        const int* skip, int* err, cudaStream_t st) {
+  const TapGroups tg = tap_groups(cin);
+  CUtensorMap md, mx;
+  cudaError_t e = make_map(&md, dout, 1, cout, H, W, kWbKP, 1, 16);
+  if (e == cudaSuccess) e = make_map(&mx, in, 1, cin, H, W, kWbKP + 2, tg.R, cin / 8);
+  if (e != cudaSuccess) return e;
+  const int otiles = (cout + 127) / 128;
+  WgBf16Params p;
+  p.cin = cin;
+  p.cout = cout;
+  p.H = H;
+  p.W = W;
+  p.chunks_x = (W + kWbKP - 1) / kWbKP;
+  p.total_chunks = p.chunks_x * H;
+  p.tg = tg;
+  const size_t per_split_elems = (size_t)9 * cout * cin;
+  uint32_t smem = kWbStages * wb_stage(cin, tg.R);
+  int maxcols = 0;
+  for (int g = 0; g < tg.n; ++g) maxcols = tg.count[g] * cin > maxcols ? tg.count[g] * cin : maxcols;
+  // a CTA holding more than half of TMEM keeps the SM to itself
+  if (tmem_cols(maxcols) > 256 && smem < 116u * 1024u) smem = 116u * 1024u;
+  const int per_sm = (int)((227u * 1024u) / (smem + 2048u));
+  const int ctas = otiles * tg.n;
+  int S = (2 * 152 * (per_sm > 0 ? per_sm : 1)) / ctas;
+  if (S < 1) S = 1;
+  if (S > p.total_chunks) S = p.total_chunks;
+  const size_t npx = (size_t)H * W;
+  int SB = (int)((npx + 511) / 512);
+  if (SB > 1024) SB = 1024;
+  while (S > 1 && (size_t)S * per_split_elems + 64 + (size_t)SB * cout > part_cap) --S;
+  if ((size_t)S * per_split_elems + 64 + (size_t)SB * cout > part_cap) return cudaErrorInvalidValue;
+  p.per_split = (p.total_chunks + S - 1) / S;
+  S = (p.total_chunks + p.per_split - 1) / p.per_split;
+  p.part = part;
+  p.skip = skip;
+  p.err = err;
+  static bool attr_set = false;
+  if (!attr_set) {
+    e = cudaFuncSetAttribute(k_wgrad_tc_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  k_wgrad_tc_bf16<<<dim3((unsigned)otiles, (unsigned)tg.n, (unsigned)S), 192, smem, st>>>(md, mx, p);
+  count_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  unsigned g = (unsigned)((per_split_elems + 255) / 256);
+  if (g > 152u * 8) g = 152u * 8;
+  k_reduce_wgrad_tc<<<g, 256, 0, st>>>(part, S, cin, cout, gw, skip);
+  count_launch();
+  float* bpart = part + ((size_t)S * per_split_elems + 63) / 64 * 64;
+  const size_t per_block = (npx + SB - 1) / SB;
+  k_colsum_cg<__nv_bfloat16><<<SB, 256, 0, st>>>((const __nv_bfloat16*)dout, cout, npx, per_block,
+                                                 bpart, skip);
+  count_launch();
+  return launch_reduce_cols(bpart, SB, cout, gb, skip, st);
+}
+
 cudaError_t launch_wgrad_tc(int bf16, const void* dout, const void* in, int cin, int cout, int H,
                             int W, float* part, size_t part_cap, float* gw, float* gb,
                             const int* skip, int* err, cudaStream_t st) {
   if (!tc_wgrad_supported(cin, cout, bf16)) return cudaErrorNotSupported;
+  if (bf16)
+    return launch_wgrad_tc_bf16(dout, in, cin, cout, H, W, part, part_cap, gw, gb, skip, err, st);
   const int GE = bf16 ? 8 : 4;
   const int KP = bf16 ? WgCfg<1>::KP : WgCfg<0>::KP;
   CUtensorMap md, mx;
