@@ -227,7 +227,7 @@ def run_ours(args, ws, rank, local):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    comp_ms, wall_ms, epochs = [], [], []
+    comp_ms, wall_ms, epochs, outs = [], [], [], []
     for i in range(args.warmup, args.warmup + args.steps):
         flush.zero_()
         torch.cuda.synchronize()
@@ -242,6 +242,7 @@ def run_ours(args, ws, rank, local):
         epochs.append(st.epoch)
         assert st.state == n2f.N2F_DONE, st.as_dict()
         assert np.isfinite(out).all()
+        outs.append(out)
     torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
@@ -288,9 +289,137 @@ def run_ours(args, ws, rank, local):
         "paper_context": "under 45 s per 512x512 image on an RTX 5000 mobile GPU (Contribution "
                          "and Significance); other hardware and data, context only",
     }
+    from paper_2108_10209_gb300 import synth
+    line["psnr_db"] = [round(synth.psnr(o, work[args.warmup + k][0]), 3)
+                       for k, o in enumerate(outs)]
+    if args.compare_batch > 0 and args.precision == 0:
+        line["bf16_batched"] = bf16_batched_compare(
+            n2f, work[args.warmup:args.warmup + args.steps], outs, args.widths, args.compare_batch)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(work[args.warmup][1], size, args.widths)
     return line
+
+
+# ---------------------------------------------------------------------------- batched / serving
+
+def run_jobs(ctx, n2f, jobs, p_of, submit_times=None):
+    """Submits jobs (list of (noisy float32 array)), optionally at host times (seconds from
+    start), waits for all, returns per-job dicts and the host/device makespans."""
+    import numpy as np
+    t0 = time.perf_counter()
+    ids, t_sub = [], []
+    pending = list(range(len(jobs)))
+    results = [None] * len(jobs)
+    next_i = 0
+    while next_i < len(jobs):
+        if submit_times is not None:
+            wait = submit_times[next_i] - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(min(wait, 0.002))
+                continue
+        x = jobs[next_i]
+        t_sub.append(time.perf_counter())
+        ids.append(ctx.submit(x, p_of(next_i)))
+        next_i += 1
+    for i, j in enumerate(ids):
+        ctx.wait(j)
+        st = ctx.poll(j)
+        out = ctx.result(j, jobs[i].shape)
+        assert st.state == n2f.N2F_DONE, st.as_dict()
+        results[i] = dict(out=out, latency_ms=st.latency_ms, compute_ms=st.compute_ms,
+                          device_ms=st.device_ms, t0=st.t_start_ms, t1=st.t_done_ms,
+                          epoch=st.epoch, H=st.H, W=st.W)
+    host_s = time.perf_counter() - t0
+    dev_s = (max(r["t1"] for r in results) - min(r["t0"] for r in results)) / 1e3
+    return results, host_s, dev_s
+
+
+def pct(v, q):
+    v = sorted(v)
+    return v[min(len(v) - 1, int(q * len(v)))]
+
+
+def bf16_batched_compare(n2f, noisy_clean, fp32_outs, widths, batch):
+    """The same images (plus more, up to `batch`) through the bf16 form, submitted together."""
+    from paper_2108_10209_gb300 import synth
+    imgs = [nc for nc in noisy_clean]
+    k = len(imgs)
+    i = 0
+    while len(imgs) < batch:
+        imgs.append(image_for(100 + i, 0, imgs[0][1].shape[0]))
+        i += 1
+    p = n2f.params(seed=0, precision=1, widths=widths)
+    with n2f.Context(max_slots=batch) as ctx:
+        res, host_s, dev_s = run_jobs(ctx, n2f, [nc[1].astype("float32") for nc in imgs],
+                                      lambda _: p)
+    dps = [synth.psnr(res[j]["out"], imgs[j][0]) - synth.psnr(fp32_outs[j], imgs[j][0])
+           for j in range(k)]
+    lat = [r["latency_ms"] for r in res]
+    return {"value": len(res) / dev_s, "unit": UNIT, "jobs": len(res), "jobs_in_flight": batch,
+            "precision": "bf16", "e2e": len(res) / host_s,
+            "latency_ms": {"p50": pct(lat, 0.5), "p99": pct(lat, 0.99)},
+            "psnr_bf16_minus_fp32_db": [round(d, 4) for d in dps],
+            "epochs": [r["epoch"] for r in res]}
+
+
+def run_batched(args, n2f):
+    """64 independent jobs, sizes uniform over {256^2, 512^2, 768x512, 1024x768}, sigma
+    U[15, 50]/255, all submitted at once; stopping rule each."""
+    from paper_2108_10209_gb300 import synth
+    jobs = synth.batch_jobs(args.jobs)
+    imgs = [synth.image_cells(j["h"], j["w"], sigma=j["sigma"], seed=j["seed"]) for j in jobs]
+    p = n2f.params(seed=0, precision=args.precision, widths=args.widths, engine=args.engine)
+    with n2f.Context(max_slots=args.jobs) as ctx:
+        warm = synth.image_cells(256, 256, seed=7)
+        run_jobs(ctx, n2f, [warm[1].astype("float32")], lambda _: p)
+        st0 = ctx.stats()
+        res, host_s, dev_s = run_jobs(ctx, n2f, [im[1].astype("float32") for im in imgs],
+                                      lambda _: p)
+        st1 = ctx.stats()
+    lat = [r["latency_ms"] for r in res]
+    mpx = sum(r["H"] * r["W"] for r in res) / 1e6
+    return {
+        "metric": METRIC, "value": len(res) / dev_s, "unit": UNIT, "n_gpus": 1, "steps": 1,
+        "warmup": 1, "ms_per_step": dev_s * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16 (f32 accumulate)" if args.precision else "f32",
+        "data": "synthetic (ellipse cells + Gaussian noise, seeded)",
+        "config": {"workload": f"{args.jobs} jobs, sizes uniform over 256x256, 512x512, 768x512, "
+                               "1024x768, sigma U[15,50]/255, stopping rule, all in flight",
+                   "widths": WIDTH_NAMES[args.widths],
+                   "precision": "bf16" if args.precision else "fp32", "jobs_in_flight": args.jobs},
+        "latency_ms": {"p50": pct(lat, 0.5), "p99": pct(lat, 0.99)},
+        "megapixels": mpx, "mpx_per_s": mpx / dev_s,
+        "e2e": {"value": len(res) / host_s, "unit": UNIT,
+                "h2d_bytes_per_step": int(mpx * 4e6), "d2h_bytes_per_step": int(mpx * 4e6)},
+        "gpu_launches": int(st1["kernel_launches"] - st0["kernel_launches"]),
+        "epochs": [r["epoch"] for r in res],
+    }
+
+
+def run_serving(args, n2f):
+    """Poisson arrivals of u16-quantised images, sides log-uniform in [256, 2048] (square),
+    Gaussian or Poisson-Gaussian noise; latency = submit to result ready (host clock)."""
+    import numpy as np
+    from paper_2108_10209_gb300 import synth
+    reqs = synth.serving_stream(args.jobs, rate=args.rate, smin=256, smax=args.max_side)
+    imgs = [synth.make_serving_image(r)[0].astype(np.float32) for r in reqs]
+    t_arr = [r["t"] for r in reqs]
+    p = n2f.params(seed=0, precision=args.precision, widths=args.widths, engine=args.engine)
+    with n2f.Context(max_slots=args.slots) as ctx:
+        res, host_s, dev_s = run_jobs(ctx, n2f, imgs, lambda _: p, submit_times=t_arr)
+    lat = [r["latency_ms"] for r in res]
+    return {
+        "metric": METRIC, "value": len(res) / host_s, "unit": UNIT, "n_gpus": 1,
+        "steps": 1, "warmup": 0, "ms_per_step": host_s * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16 (f32 accumulate)" if args.precision else "f32",
+        "data": "synthetic (ellipse cells, Gaussian or Poisson-Gaussian, u16-quantised)",
+        "config": {"workload": f"{args.jobs} requests, Poisson arrivals at {args.rate}/s, square "
+                               f"sides log-uniform 256..{args.max_side}, stopping rule",
+                   "slots": args.slots, "widths": WIDTH_NAMES[args.widths]},
+        "latency_ms": {"p50": pct(lat, 0.5), "p99": pct(lat, 0.99), "max": max(lat)},
+        "offered_rate": args.rate, "completed": len(res),
+    }
 
 
 # ---------------------------------------------------------------------------- reference arm -
@@ -340,6 +469,13 @@ def main():
     ap.add_argument("--profile-kernel", type=int, default=1,
                     help="kernel class timed for the roofline (1 fwd, 2 dgrad, 3 wgrad)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--form", default="plain", choices=["plain", "batched", "serving"])
+    ap.add_argument("--compare-batch", type=int, default=16,
+                    help="plain form: also run this many images in the bf16 form together (0 = off)")
+    ap.add_argument("--jobs", type=int, default=64, help="batched / serving: number of images")
+    ap.add_argument("--rate", type=float, default=5.0, help="serving: arrivals per second")
+    ap.add_argument("--slots", type=int, default=64, help="serving: jobs resident at once")
+    ap.add_argument("--max-side", type=int, default=2048, help="serving: largest image side")
     args = ap.parse_args()
     os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
     ws, rank, local = dist_env()
@@ -350,7 +486,17 @@ def main():
             import torch
             torch.cuda.set_device(local)
             torch.distributed.init_process_group("nccl")
-        line = run_ours(args, ws, rank, local)
+        if args.form == "plain":
+            line = run_ours(args, ws, rank, local)
+        else:
+            import torch
+            torch.cuda.set_device(local)
+            import __graft_entry__ as g
+            g.build()
+            from paper_2108_10209_gb300 import n2f
+            line = run_batched(args, n2f) if args.form == "batched" else run_serving(args, n2f)
+            if rank != 0:
+                line = None
         if ws > 1:
             import torch
             torch.distributed.destroy_process_group()

@@ -93,6 +93,9 @@ typedef struct {
   n2f_free_fn free;
   void* alloc_user;
   int32_t profile_kernel;    /* enum n2f_kernel_class timed per launch (events), 0 = off */
+  int32_t use_graphs;        /* 1: each job's epoch is captured once as a CUDA graph and
+                                replayed (default); 0: kernels are launched one by one.
+                                Per-launch kernel timing always launches one by one. */
 } n2f_config;
 
 /* Per-image parameters. Defaults (n2f_params_default) follow the Methods section; the Adam

@@ -33,6 +33,7 @@ void n2f_config_default(n2f_config* c) {
   c->hbm_budget_bytes = 150ull << 30;
   c->max_slots = 64;
   c->lookahead = 2;
+  c->use_graphs = 1;
 }
 
 void n2f_params_default(n2f_params* p) {
@@ -558,7 +559,10 @@ static bool progress(n2f_ctx* c, Job* j) {
     }
     const uint32_t la = std::max<uint32_t>(1, c->cfg.lookahead);
     while (!j->finishing && j->ep_enq - j->ep_seen < la) {
-      if ((rc = trainer_epoch(&j->tr))) break;
+      // epochs replay a captured graph unless a kernel class is being timed per launch
+      if ((rc = j->tr.kt || !c->cfg.use_graphs ? trainer_epoch(&j->tr)
+                                              : trainer_epoch_graph(&j->tr)))
+        break;
       const int slot = (int)(j->ep_enq % j->ring);
       cudaError_t e = cudaMemcpyAsync(&j->hst[slot], j->tr.state, sizeof(DevState),
                                       cudaMemcpyDeviceToHost, j->st);
@@ -690,6 +694,7 @@ extern "C" int n2f_create(n2f_ctx** out, const n2f_config* cfg) {
   CKR(cudaSetDevice(cfg->device));
   n2f_ctx* c = new n2f_ctx();
   c->cfg = *cfg;
+  if (c->cfg.use_graphs < 0) c->cfg.use_graphs = 1;
   if (!c->cfg.hbm_budget_bytes) c->cfg.hbm_budget_bytes = 150ull << 30;
   if (!c->cfg.max_slots) c->cfg.max_slots = 64;
   if (!c->cfg.lookahead) c->cfg.lookahead = 2;

@@ -768,13 +768,6 @@ namespace {
 template <int BF16, int MODE>
 cudaError_t conv_tc_launch(const CUtensorMap& m, const ConvTcParams& p, dim3 grid, uint32_t smem,
                            cudaStream_t st) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_conv_tc<BF16, MODE>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
   k_conv_tc<BF16, MODE><<<grid, 192, smem, st>>>(m, p);
   return cudaGetLastError();
 }
@@ -782,18 +775,37 @@ cudaError_t conv_tc_launch(const CUtensorMap& m, const ConvTcParams& p, dim3 gri
 template <int BF16>
 cudaError_t wgrad_tc_launch(const CUtensorMap& md, const CUtensorMap& mx, const WgradTcParams& p,
                             dim3 grid, uint32_t smem, cudaStream_t st) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_wgrad_tc<BF16>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
   k_wgrad_tc<BF16><<<grid, 192, smem, st>>>(md, mx, p);
   return cudaGetLastError();
 }
 
 }  // namespace
+
+// Sets the dynamic shared-memory limits of every tensor-core kernel and resolves the tensor-map
+// encoder, so that later launches (possibly inside a stream capture) do neither.
+cudaError_t tc_prepare() {
+  static std::once_flag once;
+  static cudaError_t result = cudaSuccess;
+  std::call_once(once, [] {
+    if (!encode_fn()) {
+      result = cudaErrorNotSupported;
+      return;
+    }
+    const int lim = 200 * 1024;
+    cudaError_t e = cudaSuccess;
+    auto set = [&](const void* f) {
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    };
+    set((const void*)k_conv_tc<1, 0>);
+    set((const void*)k_conv_tc<1, 1>);
+    set((const void*)k_conv_tc<0, 0>);
+    set((const void*)k_conv_tc<0, 1>);
+    set((const void*)k_wgrad_tc<0>);
+    set((const void*)k_wgrad_tc_bf16);
+    result = e;
+  });
+  return result;
+}
 
 bool tc_supported(int cin, int cout) {
   auto ok = [](int c) { return c == 32 || c == 64 || c == 128 || c == 256; };
@@ -811,6 +823,7 @@ cudaError_t launch_conv_tc(int mode, int bf16, const void* in, int cin, int cout
                            const void* w_hi, const void* w_lo, const float* b, const void* mask,
                            void* out, const int* skip, int* err, cudaStream_t st) {
   if (!tc_supported(cin, cout)) return cudaErrorNotSupported;
+  if (const cudaError_t pe = tc_prepare()) return pe;
   const TcCfg f = tc_cfg(cin, cout, bf16);
   CUtensorMap m;
   const int KC = bf16 ? ConvCfg<1>::KC : ConvCfg<0>::KC;
@@ -878,13 +891,6 @@ static cudaError_t launch_wgrad_tc_bf16(const void* dout, const void* in, int ci
   p.part = part;
   p.skip = skip;
   p.err = err;
-  static bool attr_set = false;
-  if (!attr_set) {
-    e = cudaFuncSetAttribute(k_wgrad_tc_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             200 * 1024);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
   k_wgrad_tc_bf16<<<dim3((unsigned)otiles, (unsigned)tg.n, (unsigned)S), 192, smem, st>>>(md, mx, p);
   count_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -904,6 +910,7 @@ cudaError_t launch_wgrad_tc(int bf16, const void* dout, const void* in, int cin,
                             int W, float* part, size_t part_cap, float* gw, float* gb,
                             const int* skip, int* err, cudaStream_t st) {
   if (!tc_wgrad_supported(cin, cout, bf16)) return cudaErrorNotSupported;
+  if (const cudaError_t pe = tc_prepare()) return pe;
   if (bf16)
     return launch_wgrad_tc_bf16(dout, in, cin, cout, H, W, part, part_cap, gw, gb, skip, err, st);
   const int GE = bf16 ? 8 : 4;

@@ -106,6 +106,7 @@ cudaError_t launch_wgrad_simt(int bf16, const void* dout, const void* in, int ci
                               const int* skip, cudaStream_t st);
 
 // Tensor-core (tcgen05) kernels; return cudaErrorNotSupported when a shape is not covered.
+cudaError_t tc_prepare();  // once per process, before any launch or capture
 bool tc_supported(int cin, int cout);
 bool tc_wgrad_supported(int cin, int cout, int bf16);
 // mode 0 forward (bias + ReLU), 1 dgrad (ReLU mask); w_hi/w_lo: packed operand copies

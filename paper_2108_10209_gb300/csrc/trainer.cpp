@@ -241,6 +241,12 @@ int trainer_configure(Trainer* t, int H, int W, const n2f_params* p, int keep_de
 }
 
 int trainer_init(Trainer* t, const Allocator& al, cudaStream_t st, int want_u16) {
+  for (int l = 0; l < kLayers; ++l)
+    if (t->engine[l] == N2F_ENGINE_TC) {
+      const cudaError_t e = tc_prepare();
+      if (e != cudaSuccess) return set_cuda_error(e, "tensor-core kernel set-up");
+      break;
+    }
   t->al = al;
   t->st = st;
   t->want_u16 = want_u16;
@@ -264,6 +270,8 @@ int trainer_init(Trainer* t, const Allocator& al, cudaStream_t st, int want_u16)
 }
 
 void trainer_release(Trainer* t) {
+  if (t->epoch_exec) cudaGraphExecDestroy(t->epoch_exec);
+  t->epoch_exec = nullptr;
   if (t->slab) dev_free(t->al, t->slab, t->slab_bytes);
   t->slab = nullptr;
 }
@@ -434,6 +442,37 @@ int trainer_epoch(Trainer* t) {
     if (rc) return rc;
   }
   return trainer_validate(t);
+}
+
+int trainer_epoch_graph(Trainer* t) {
+  if (!t->epoch_exec) {
+    uint64_t counted = 0;
+    cudaGraph_t g = nullptr;
+    {
+      LaunchScope ls(&counted);
+      CK(cudaStreamBeginCapture(t->st, cudaStreamCaptureModeThreadLocal));
+      const int rc = trainer_epoch(t);
+      const cudaError_t e = cudaStreamEndCapture(t->st, &g);
+      if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+      }
+      if (e != cudaSuccess) return set_cuda_error(e, "epoch graph capture");
+    }
+    const cudaError_t e = cudaGraphInstantiate(&t->epoch_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return set_cuda_error(e, "epoch graph instantiate");
+    t->epoch_kernels = counted;
+    // the captured calls advanced the enqueue counters once; the launch below is the epoch
+    t->steps_enqueued -= 4;
+    t->vals_enqueued -= 1;
+  }
+  CK(cudaGraphLaunch(t->epoch_exec, t->st));
+  t->steps_enqueued += 4;
+  t->vals_enqueued += 1;
+  t->launches += t->epoch_kernels;
+  count_launch((int)t->epoch_kernels);
+  return N2F_OK;
 }
 
 int trainer_finish(Trainer* t) {

@@ -88,6 +88,9 @@ struct Trainer {
   int last_pair = 0;
   uint64_t steps_enqueued = 0, vals_enqueued = 0;
   KTimer* kt = nullptr;  // optional kernel-class timer (owned by the caller)
+  // one epoch captured as a CUDA graph (everything it mutates lives in device memory)
+  cudaGraphExec_t epoch_exec = nullptr;
+  uint64_t epoch_kernels = 0;  // kernels in one captured epoch
 };
 
 int trainer_configure(Trainer* t, int H, int W, const n2f_params* p, int keep_deltas);
@@ -99,6 +102,8 @@ int trainer_repack(Trainer* t);
 int trainer_step(Trainer* t, int pair);
 int trainer_validate(Trainer* t);
 int trainer_epoch(Trainer* t);
+// Same as trainer_epoch, replaying a CUDA graph of the epoch captured on first use.
+int trainer_epoch_graph(Trainer* t);
 int trainer_finish(Trainer* t);
 int trainer_read_state(Trainer* t, DevState* s);
 void fill_status(const Trainer* t, const DevState& s, n2f_status* st);

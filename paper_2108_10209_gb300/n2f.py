@@ -35,7 +35,8 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
 class Config(C.Structure):
     _fields_ = [("struct_size", C.c_uint32), ("device", C.c_int), ("hbm_budget_bytes", C.c_uint64),
                 ("max_slots", C.c_uint32), ("lookahead", C.c_uint32), ("alloc", ALLOC_FN),
-                ("free", FREE_FN), ("alloc_user", C.c_void_p), ("profile_kernel", C.c_int32)]
+                ("free", FREE_FN), ("alloc_user", C.c_void_p), ("profile_kernel", C.c_int32),
+                ("use_graphs", C.c_int32)]
 
 
 class Params(C.Structure):
@@ -169,7 +170,8 @@ class Context:
     unless ``torch_alloc=False`` (then the library calls cudaMalloc itself)."""
 
     def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, max_slots: int = 0,
-                 lookahead: int = 0, torch_alloc: bool = True, profile_kernel: int = 0):
+                 lookahead: int = 0, torch_alloc: bool = True, profile_kernel: int = 0,
+                 use_graphs: bool = True):
         cfg = Config()
         lib().n2f_config_default(C.byref(cfg))
         cfg.device = device
@@ -180,6 +182,7 @@ class Context:
         if lookahead:
             cfg.lookahead = lookahead
         cfg.profile_kernel = profile_kernel
+        cfg.use_graphs = int(use_graphs)
         self._keep = []
         if torch_alloc:
             import torch
