@@ -323,213 +323,6 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
 }
 
 // ---- weight gradient ------------------------------------------------------------------------
-struct WgradTcParams {
-  float* part;  // [S][9][C_out][C_in]
-  int cin, cout, H, W, chunks_x, total_chunks, per_split;
-  const int* skip;
-  int* err;
-};
-
-template <int BF16>
-struct WgCfg;
-
-// bf16: both operands MN-major straight from the TMA tiles.
-// stage: A (delta, 128 channels x KP px) | B (x, C_in x KP px)
-template <>
-struct WgCfg<1> {
-  static constexpr int GE = 8;
-  static constexpr int KP = 64;     // pixels per stage
-  static constexpr int KSTEP = 16;  // pixels per MMA
-  static constexpr int STAGES = 4;
-  static constexpr uint32_t A_BYTES = 128u * KP * 2;
-  static __host__ __device__ uint32_t b_bytes(int cin) { return (uint32_t)cin * KP * 2; }
-  static __host__ __device__ uint32_t b_off() { return align_up(A_BYTES, 1024); }
-  static __host__ __device__ uint32_t stage_bytes(int cin) { return b_off() + align_up(b_bytes(cin), 1024); }
-};
-
-// float32 (3xTF32): TF32 operands are read K-major, so the split pass that forms the hi and lo
-// parts also transposes the MN-major TMA tiles: K-major image = 4-pixel K slabs of all rows,
-// row r at 16 r bytes inside a slab (8-row core matrices 128 bytes apart).
-// stage: raw A | raw B | hi A | hi B | lo A | lo B
-template <>
-struct WgCfg<0> {
-  static constexpr int GE = 4;
-  static constexpr int KP = 16;
-  static constexpr int KSTEP = 8;
-  static constexpr int STAGES = 2;
-  static constexpr uint32_t A_BYTES = 128u * KP * 4;
-  static __host__ __device__ uint32_t b_bytes(int cin) { return (uint32_t)cin * KP * 4; }
-  // K-major split images use a slab stride of rows*16 + 16 bytes (bank-conflict-free stores)
-  static __host__ __device__ uint32_t slab(int rows) { return (uint32_t)rows * 16u + 16u; }
-  static __host__ __device__ uint32_t kimg(int rows) { return (KP / 4) * slab(rows); }
-  static __host__ __device__ uint32_t raw_bytes(int cin) { return align_up(A_BYTES, 1024) + align_up(b_bytes(cin), 1024); }
-  static __host__ __device__ uint32_t b_off() { return align_up(A_BYTES, 1024); }
-  // hi | lo images, each [A (128 rows) | B (C_in rows)]
-  static __host__ __device__ uint32_t kpart(int cin) { return align_up(kimg(128), 1024) + align_up(kimg(cin), 1024); }
-  static __host__ __device__ uint32_t kb_off() { return align_up(kimg(128), 1024); }
-  static __host__ __device__ uint32_t hi_off(int cin) { return raw_bytes(cin); }
-  static __host__ __device__ uint32_t lo_off(int cin) { return raw_bytes(cin) + kpart(cin); }
-  static __host__ __device__ uint32_t stage_bytes(int cin) { return raw_bytes(cin) + 2 * kpart(cin); }
-};
-
-// Transposing 3xTF32 split of one [rows/4 groups][KP px][4 ch] tile into K-major hi and lo
-// images [KP/4 slabs][rows][4 px] with a slab stride of rows*16 + 16 bytes. A thread handles a
-// 4-channel x 4-pixel unit; reads are rotated by the unit's pixel block so a quarter warp touches
-// distinct banks, and the padded slab stride does the same for the stores.
-__device__ __forceinline__ void split_transpose(const float* raw, float* hi, float* lo, int rows,
-                                                int kp, int et) {
-  const int pbs = kp / 4;
-  const int units = (rows / 4) * pbs;
-  const uint32_t slab = (uint32_t)rows * 4 + 4;  // floats
-  for (int u = et; u < units; u += 128) {
-    const int g = u / pbs, pb = u % pbs;
-    const float4* src = reinterpret_cast<const float4*>(raw) + (size_t)g * kp + pb * 4;
-    float v[4][4];  // [pixel][channel]
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const int q = (r + pb) & 3;
-      const float4 t = src[q];
-      v[q][0] = t.x; v[q][1] = t.y; v[q][2] = t.z; v[q][3] = t.w;
-    }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const float4 x = make_float4(v[0][j], v[1][j], v[2][j], v[3][j]);
-      float4 h, l;
-      split4(x, h, l);
-      const uint32_t off = pb * slab + (uint32_t)(4 * g + j) * 4;
-      *reinterpret_cast<float4*>(hi + off) = h;
-      *reinterpret_cast<float4*>(lo + off) = l;
-    }
-  }
-}
-
-template <int BF16>
-__global__ void __launch_bounds__(192, 1) k_wgrad_tc(const __grid_constant__ CUtensorMap tmD,
-                                                    const __grid_constant__ CUtensorMap tmX,
-                                                    WgradTcParams p) {
-  using C = WgCfg<BF16>;
-  extern __shared__ __align__(1024) uint8_t smem[];
-  __shared__ uint64_t full[4], empty[4], split[4], accf;
-  __shared__ uint32_t tslot;
-  __shared__ int abort_flag;
-  if (p.skip && *p.skip) return;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int o0 = blockIdx.x * 128, tap = blockIdx.y, s_idx = blockIdx.z;
-  const int dy = tap / 3, dx = tap % 3;
-  const int cbeg = s_idx * p.per_split;
-  const int cend = min(p.total_chunks, cbeg + p.per_split);
-  const int nk = cend > cbeg ? cend - cbeg : 0;
-  const uint32_t B_BYTES = C::b_bytes(p.cin), SB = C::stage_bytes(p.cin);
-  const uint32_t ncols = tmem_cols(p.cin);
-  volatile int* abort = &abort_flag;
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < C::STAGES; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
-      mbar_init(&split[s], 128);
-    }
-    mbar_init(&accf, 1);
-    abort_flag = 0;
-    mbar_fence_init();
-  }
-  if (warp == 1) tmem_alloc(&tslot, ncols);
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tbase = tslot;
-
-  if (warp == 0) {
-    if (lane == 0) {
-      int issued = 0;
-      for (int i = 0; i < nk; ++i) {
-        const int s = i % C::STAGES;
-        if (i >= C::STAGES && !mbar_wait(&empty[s], ((i / C::STAGES) - 1) & 1, abort, p.err))
-          break;
-        const int ch = cbeg + i;
-        const int y = ch / p.chunks_x, x0 = (ch % p.chunks_x) * C::KP;
-        uint8_t* st = smem + s * SB;
-        mbar_expect_tx(&full[s], C::A_BYTES + B_BYTES);
-        tma_load_4d(st, &tmD, &full[s], 0, x0, y, o0 / C::GE);
-        tma_load_4d(st + C::b_off(), &tmX, &full[s], 0, x0 + dx - 1, y + dy - 1, 0);
-        issued = i + 1;
-      }
-      if (*abort)
-        for (int i = issued > C::STAGES ? issued - C::STAGES : 0; i < issued; ++i)
-          mbar_drain(&full[i % C::STAGES], (i / C::STAGES) & 1);
-    }
-  } else if (warp == 1) {
-    if (lane == 0) {
-      const uint32_t id = idesc(BF16 ? 1 : 2, 128, p.cin, BF16 ? 1 : 0, BF16 ? 1 : 0);
-      for (int i = 0; i < nk; ++i) {
-        const int s = i % C::STAGES;
-        const uint32_t ph = (i / C::STAGES) & 1;
-        if (!mbar_wait(BF16 ? &full[s] : &split[s], ph, abort, p.err)) break;
-        tc_fence_after();
-        const uint32_t sa = smem_u32(smem + s * SB);
-#pragma unroll
-        for (int k = 0; k < C::KP / C::KSTEP; ++k) {
-          const uint32_t acc = (i > 0 || k > 0) ? 1u : 0u;
-          if constexpr (BF16) {
-            // MN-major: K-adjacent core matrices (8 px) 128 B apart, channel groups KP*16 apart
-            const uint32_t ko = (uint32_t)k * C::KSTEP * 16u, sbo = C::KP * 16;
-            mma_f16(tbase, sdesc(sa + ko, 128, sbo), sdesc(sa + C::b_off() + ko, 128, sbo), id, acc);
-          } else {
-            // K-major: 4-pixel slabs of all rows (A: 128 rows, B: C_in rows), one MMA = 2 slabs
-            const uint32_t la = C::slab(128), lb = C::slab(p.cin);
-            const uint32_t hA = sa + C::hi_off(p.cin), hB = hA + C::kb_off();
-            const uint32_t lA = sa + C::lo_off(p.cin), lB = lA + C::kb_off();
-            const uint64_t dah = sdesc(hA + k * 2 * la, la, 128), dbh = sdesc(hB + k * 2 * lb, lb, 128);
-            mma_tf32(tbase, dah, dbh, id, acc);
-            mma_tf32(tbase, dah, sdesc(lB + k * 2 * lb, lb, 128), id, 1u);
-            mma_tf32(tbase, sdesc(lA + k * 2 * la, la, 128), dbh, id, 1u);
-          }
-        }
-        mma_commit(&empty[s]);
-      }
-      mma_commit(&accf);
-    }
-  } else {
-    const int et = threadIdx.x - 64;
-    if constexpr (!BF16) {
-      for (int i = 0; i < nk; ++i) {
-        const int s = i % C::STAGES;
-        if (!mbar_wait(&full[s], (i / C::STAGES) & 1, abort, p.err)) break;
-        uint8_t* st = smem + s * SB;
-        const uint32_t hi = C::hi_off(p.cin), lo = C::lo_off(p.cin);
-        split_transpose(reinterpret_cast<const float*>(st), reinterpret_cast<float*>(st + hi),
-                        reinterpret_cast<float*>(st + lo), 128, C::KP, et);
-        split_transpose(reinterpret_cast<const float*>(st + C::b_off()),
-                        reinterpret_cast<float*>(st + hi + C::kb_off()),
-                        reinterpret_cast<float*>(st + lo + C::kb_off()), p.cin, C::KP, et);
-        fence_proxy_async();
-        mbar_arrive(&split[s]);
-      }
-    }
-    if (!mbar_wait(&accf, 0, abort, p.err)) mbar_drain(&accf, 0);
-    tc_fence_after();
-    const int wq = warp & 3;
-    const int o = o0 + wq * 32 + lane;
-    const bool live = o < p.cout && !*abort;
-    float* dst = p.part + (((size_t)s_idx * 9 + tap) * p.cout + (live ? o : 0)) * p.cin;
-    for (int c0 = 0; c0 < p.cin; c0 += 16) {
-      uint32_t r[16];
-      tmem_ld16(tbase + ((uint32_t)(wq * 32) << 16) + c0, r);
-      tmem_ld_wait();
-      if (!live) continue;
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        reinterpret_cast<float4*>(dst + c0)[q] =
-            make_float4(nk ? __uint_as_float(r[4 * q]) : 0.f, nk ? __uint_as_float(r[4 * q + 1]) : 0.f,
-                        nk ? __uint_as_float(r[4 * q + 2]) : 0.f, nk ? __uint_as_float(r[4 * q + 3]) : 0.f);
-    }
-  }
-  tc_fence_before();
-  __syncthreads();
-  if (warp == 1) {
-    tc_fence_after();
-    tmem_dealloc(tbase, ncols);
-  }
-}
 
 // ---- bf16 weight gradient, several taps per CTA -----------------------------------------
 // A CTA covers a group of taps that share image rows: the x halo tile (R rows x (KP + 2)
@@ -684,6 +477,195 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc_bf16(const __grid_constant_
   }
 }
 
+// ---- float32 weight gradient as three bf16 parts per operand --------------------------------
+// Each fp32 value x is split into x = b0 + b1 + b2 (bf16, each the rounded remainder of the
+// previous) and D = sum of the six products b_i c_j with i + j <= 2; the three dropped products
+// are below 2^-25 of the true one. bf16 operands can be read MN-major, so the tap-grouped halo
+// scheme of the bf16 kernel applies unchanged: TMA brings the fp32 tiles, the four epilogue
+// warps write the three bf16 images of each, one MMA warp issues six MMAs per tap and K step.
+constexpr int kW3KP = 16;  // pixels per stage (one bf16 K step)
+constexpr int kW3Stages = 3;
+
+struct W3Layout {
+  uint32_t rawA, rawB, a[3], b[3], stage;
+};
+
+__host__ __device__ inline W3Layout w3_layout(int cin, int R) {
+  W3Layout L;
+  const uint32_t ra = 128u * kW3KP * 4;                         // [32 g4][16 px][16 B]
+  const uint32_t rb = (uint32_t)cin * R * (kW3KP + 2) * 4;     // [C/4][R][18 px][16 B]
+  const uint32_t pa = 128u * kW3KP * 2;                         // [16 g8][16 px][16 B]
+  const uint32_t pb = (uint32_t)cin * R * (kW3KP + 2) * 2;     // [C/8][R][18 px][16 B]
+  uint32_t o = 0;
+  L.rawA = o; o += align_up(ra, 1024);
+  L.rawB = o; o += align_up(rb, 1024);
+  for (int k = 0; k < 3; ++k) { L.a[k] = o; o += align_up(pa, 1024); }
+  for (int k = 0; k < 3; ++k) { L.b[k] = o; o += align_up(pb, 1024); }
+  L.stage = o;
+  return L;
+}
+
+// [G4][P][4] fp32 tile -> three [G4/2][P][8] bf16 tiles (rows of one 16-byte group each).
+__device__ __forceinline__ void split3_bf16(const float4* raw, uint4* b0, uint4* b1, uint4* b2,
+                                            int g8n, int P, int et) {
+  for (int u = et; u < g8n * P; u += 128) {
+    const int g8 = u / P, px = u % P;
+    const float4 lo4 = raw[(size_t)(2 * g8) * P + px], hi4 = raw[(size_t)(2 * g8 + 1) * P + px];
+    const float x[8] = {lo4.x, lo4.y, lo4.z, lo4.w, hi4.x, hi4.y, hi4.z, hi4.w};
+    unsigned w0[4], w1[4], w2[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      __nv_bfloat162 p0, p1, p2;
+      float r[2][3];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const float v = x[2 * q + h];
+        const float c0 = __bfloat162float(__float2bfloat16_rn(v));
+        const float c1 = __bfloat162float(__float2bfloat16_rn(v - c0));
+        const float c2 = __bfloat162float(__float2bfloat16_rn((v - c0) - c1));
+        r[h][0] = c0; r[h][1] = c1; r[h][2] = c2;
+      }
+      p0 = __floats2bfloat162_rn(r[0][0], r[1][0]);
+      p1 = __floats2bfloat162_rn(r[0][1], r[1][1]);
+      p2 = __floats2bfloat162_rn(r[0][2], r[1][2]);
+      w0[q] = *reinterpret_cast<unsigned*>(&p0);
+      w1[q] = *reinterpret_cast<unsigned*>(&p1);
+      w2[q] = *reinterpret_cast<unsigned*>(&p2);
+    }
+    b0[u] = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+    b1[u] = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+    b2[u] = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+  }
+}
+
+__global__ void __launch_bounds__(192, 1) k_wgrad_tc_f32(const __grid_constant__ CUtensorMap tmD,
+                                                        const __grid_constant__ CUtensorMap tmX,
+                                                        WgBf16Params p) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ uint64_t full[kW3Stages], empty[kW3Stages], split[kW3Stages], accf;
+  __shared__ uint32_t tslot;
+  __shared__ int abort_flag;
+  if (p.skip && *p.skip) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int o0 = blockIdx.x * 128, grp = blockIdx.y, s_idx = blockIdx.z;
+  const int t0 = p.tg.first[grp], nt = p.tg.count[grp], r0 = p.tg.row0[grp], R = p.tg.R;
+  const int cbeg = s_idx * p.per_split;
+  const int cend = min(p.total_chunks, cbeg + p.per_split);
+  const int nk = cend > cbeg ? cend - cbeg : 0;
+  const W3Layout L = w3_layout(p.cin, R);
+  const uint32_t RB = (uint32_t)p.cin * R * (kW3KP + 2) * 4;
+  const uint32_t ncols = tmem_cols(nt * p.cin);
+  volatile int* abort = &abort_flag;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kW3Stages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+      mbar_init(&split[s], 128);
+    }
+    mbar_init(&accf, 1);
+    abort_flag = 0;
+    mbar_fence_init();
+  }
+  if (warp == 1) tmem_alloc(&tslot, ncols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = tslot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int issued = 0;
+      for (int i = 0; i < nk; ++i) {
+        const int s = i % kW3Stages;
+        if (i >= kW3Stages && !mbar_wait(&empty[s], ((i / kW3Stages) - 1) & 1, abort, p.err))
+          break;
+        const int ch = cbeg + i;
+        const int y = ch / p.chunks_x, x0 = (ch % p.chunks_x) * kW3KP;
+        uint8_t* st = smem + s * L.stage;
+        mbar_expect_tx(&full[s], 128u * kW3KP * 4 + RB);
+        tma_load_4d(st + L.rawA, &tmD, &full[s], 0, x0, y, o0 / 4);
+        tma_load_4d(st + L.rawB, &tmX, &full[s], 0, x0 - 1, y + r0 - 1, 0);
+        issued = i + 1;
+      }
+      if (*abort)
+        for (int i = issued > kW3Stages ? issued - kW3Stages : 0; i < issued; ++i)
+          mbar_drain(&full[i % kW3Stages], (i / kW3Stages) & 1);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t id = idesc(1, 128, p.cin, 1, 1);
+      const uint32_t a_sbo = kW3KP * 16;                     // next 8-channel group of delta
+      const uint32_t b_sbo = (uint32_t)R * (kW3KP + 2) * 16;  // next 8-channel group of x
+      for (int i = 0; i < nk; ++i) {
+        const int s = i % kW3Stages;
+        if (!mbar_wait(&split[s], (i / kW3Stages) & 1, abort, p.err)) break;
+        tc_fence_after();
+        const uint32_t st = smem_u32(smem + s * L.stage);
+        uint64_t da[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) da[k] = sdesc(st + L.a[k], 128, a_sbo);
+        for (int j = 0; j < nt; ++j) {
+          const int tap = t0 + j;
+          const uint32_t boff = (uint32_t)(((tap / 3) - r0) * (kW3KP + 2) + (tap % 3)) * 16u;
+          uint64_t db[3];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) db[k] = sdesc(st + L.b[k] + boff, 128, b_sbo);
+          const uint32_t d = tbase + (uint32_t)(j * p.cin);
+          mma_f16(d, da[0], db[0], id, i > 0 ? 1u : 0u);
+          mma_f16(d, da[0], db[1], id, 1u);
+          mma_f16(d, da[1], db[0], id, 1u);
+          mma_f16(d, da[0], db[2], id, 1u);
+          mma_f16(d, da[1], db[1], id, 1u);
+          mma_f16(d, da[2], db[0], id, 1u);
+        }
+        mma_commit(&empty[s]);
+      }
+      mma_commit(&accf);
+    }
+  } else {
+    const int et = threadIdx.x - 64;
+    for (int i = 0; i < nk; ++i) {
+      const int s = i % kW3Stages;
+      if (!mbar_wait(&full[s], (i / kW3Stages) & 1, abort, p.err)) break;
+      uint8_t* st = smem + s * L.stage;
+      split3_bf16(reinterpret_cast<const float4*>(st + L.rawA), reinterpret_cast<uint4*>(st + L.a[0]),
+                  reinterpret_cast<uint4*>(st + L.a[1]), reinterpret_cast<uint4*>(st + L.a[2]), 16,
+                  kW3KP, et);
+      split3_bf16(reinterpret_cast<const float4*>(st + L.rawB), reinterpret_cast<uint4*>(st + L.b[0]),
+                  reinterpret_cast<uint4*>(st + L.b[1]), reinterpret_cast<uint4*>(st + L.b[2]),
+                  p.cin / 8, R * (kW3KP + 2), et);
+      fence_proxy_async();
+      mbar_arrive(&split[s]);
+    }
+    if (!mbar_wait(&accf, 0, abort, p.err)) mbar_drain(&accf, 0);
+    tc_fence_after();
+    const int wq = warp & 3;
+    const int o = o0 + wq * 32 + lane;
+    const bool live = o < p.cout && !*abort;
+    for (int j = 0; j < nt; ++j) {
+      const int tap = t0 + j;
+      float* dst = p.part + (((size_t)s_idx * 9 + tap) * p.cout + (live ? o : 0)) * p.cin;
+      for (int c0 = 0; c0 < p.cin; c0 += 16) {
+        uint32_t r[16];
+        tmem_ld16(tbase + ((uint32_t)(wq * 32) << 16) + (uint32_t)(j * p.cin + c0), r);
+        tmem_ld_wait();
+        if (!live) continue;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          reinterpret_cast<float4*>(dst + c0)[q] = make_float4(
+              nk ? __uint_as_float(r[4 * q]) : 0.f, nk ? __uint_as_float(r[4 * q + 1]) : 0.f,
+              nk ? __uint_as_float(r[4 * q + 2]) : 0.f, nk ? __uint_as_float(r[4 * q + 3]) : 0.f);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tbase, ncols);
+  }
+}
+
 // gw[(o*C_in + c)*9 + tap] = sum_s part[s][tap][o][c] (ascending s)
 __global__ void k_reduce_wgrad_tc(const float* __restrict__ part, int S, int cin, int cout,
                                   float* __restrict__ gw, const int* skip) {
@@ -772,13 +754,6 @@ cudaError_t conv_tc_launch(const CUtensorMap& m, const ConvTcParams& p, dim3 gri
   return cudaGetLastError();
 }
 
-template <int BF16>
-cudaError_t wgrad_tc_launch(const CUtensorMap& md, const CUtensorMap& mx, const WgradTcParams& p,
-                            dim3 grid, uint32_t smem, cudaStream_t st) {
-  k_wgrad_tc<BF16><<<grid, 192, smem, st>>>(md, mx, p);
-  return cudaGetLastError();
-}
-
 }  // namespace
 
 // Sets the dynamic shared-memory limits of every tensor-core kernel and resolves the tensor-map
@@ -800,8 +775,8 @@ cudaError_t tc_prepare() {
     set((const void*)k_conv_tc<1, 1>);
     set((const void*)k_conv_tc<0, 0>);
     set((const void*)k_conv_tc<0, 1>);
-    set((const void*)k_wgrad_tc<0>);
     set((const void*)k_wgrad_tc_bf16);
+    set((const void*)k_wgrad_tc_f32);
     result = e;
   });
   return result;
@@ -853,13 +828,16 @@ cudaError_t launch_conv_tc(int mode, int bf16, const void* in, int cin, int cout
   return e;
 }
 
-static cudaError_t launch_wgrad_tc_bf16(const void* dout, const void* in, int cin, int cout, int H,
-                                        int W, float* part, size_t part_cap, float* gw, float* gb,
-                                        const int* skip, int* err, cudaStream_t st) {
+// bf16 = 1: bf16 maps, k_wgrad_tc_bf16; bf16 = 0: float32 maps, k_wgrad_tc_f32 (three bf16 parts)
+static cudaError_t launch_wgrad_grouped(int bf16, const void* dout, const void* in, int cin,
+                                        int cout, int H, int W, float* part, size_t part_cap,
+                                        float* gw, float* gb, const int* skip, int* err,
+                                        cudaStream_t st) {
   const TapGroups tg = tap_groups(cin);
+  const int KP = bf16 ? kWbKP : kW3KP, GE = bf16 ? 8 : 4;
   CUtensorMap md, mx;
-  cudaError_t e = make_map(&md, dout, 1, cout, H, W, kWbKP, 1, 16);
-  if (e == cudaSuccess) e = make_map(&mx, in, 1, cin, H, W, kWbKP + 2, tg.R, cin / 8);
+  cudaError_t e = make_map(&md, dout, bf16, cout, H, W, KP, 1, 128 / GE);
+  if (e == cudaSuccess) e = make_map(&mx, in, bf16, cin, H, W, KP + 2, tg.R, cin / GE);
   if (e != cudaSuccess) return e;
   const int otiles = (cout + 127) / 128;
   WgBf16Params p;
@@ -867,11 +845,11 @@ static cudaError_t launch_wgrad_tc_bf16(const void* dout, const void* in, int ci
   p.cout = cout;
   p.H = H;
   p.W = W;
-  p.chunks_x = (W + kWbKP - 1) / kWbKP;
+  p.chunks_x = (W + KP - 1) / KP;
   p.total_chunks = p.chunks_x * H;
   p.tg = tg;
   const size_t per_split_elems = (size_t)9 * cout * cin;
-  uint32_t smem = kWbStages * wb_stage(cin, tg.R);
+  uint32_t smem = bf16 ? kWbStages * wb_stage(cin, tg.R) : kW3Stages * w3_layout(cin, tg.R).stage;
   int maxcols = 0;
   for (int g = 0; g < tg.n; ++g) maxcols = tg.count[g] * cin > maxcols ? tg.count[g] * cin : maxcols;
   // a CTA holding more than half of TMEM keeps the SM to itself
@@ -891,7 +869,11 @@ static cudaError_t launch_wgrad_tc_bf16(const void* dout, const void* in, int ci
   p.part = part;
   p.skip = skip;
   p.err = err;
-  k_wgrad_tc_bf16<<<dim3((unsigned)otiles, (unsigned)tg.n, (unsigned)S), 192, smem, st>>>(md, mx, p);
+  const dim3 grid((unsigned)otiles, (unsigned)tg.n, (unsigned)S);
+  if (bf16)
+    k_wgrad_tc_bf16<<<grid, 192, smem, st>>>(md, mx, p);
+  else
+    k_wgrad_tc_f32<<<grid, 192, smem, st>>>(md, mx, p);
   count_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   unsigned g = (unsigned)((per_split_elems + 255) / 256);
@@ -900,8 +882,11 @@ static cudaError_t launch_wgrad_tc_bf16(const void* dout, const void* in, int ci
   count_launch();
   float* bpart = part + ((size_t)S * per_split_elems + 63) / 64 * 64;
   const size_t per_block = (npx + SB - 1) / SB;
-  k_colsum_cg<__nv_bfloat16><<<SB, 256, 0, st>>>((const __nv_bfloat16*)dout, cout, npx, per_block,
-                                                 bpart, skip);
+  if (bf16)
+    k_colsum_cg<__nv_bfloat16><<<SB, 256, 0, st>>>((const __nv_bfloat16*)dout, cout, npx,
+                                                   per_block, bpart, skip);
+  else
+    k_colsum_cg<float><<<SB, 256, 0, st>>>((const float*)dout, cout, npx, per_block, bpart, skip);
   count_launch();
   return launch_reduce_cols(bpart, SB, cout, gb, skip, st);
 }
@@ -911,62 +896,8 @@ cudaError_t launch_wgrad_tc(int bf16, const void* dout, const void* in, int cin,
                             const int* skip, int* err, cudaStream_t st) {
   if (!tc_wgrad_supported(cin, cout, bf16)) return cudaErrorNotSupported;
   if (const cudaError_t pe = tc_prepare()) return pe;
-  if (bf16)
-    return launch_wgrad_tc_bf16(dout, in, cin, cout, H, W, part, part_cap, gw, gb, skip, err, st);
-  const int GE = bf16 ? 8 : 4;
-  const int KP = bf16 ? WgCfg<1>::KP : WgCfg<0>::KP;
-  CUtensorMap md, mx;
-  cudaError_t e = make_map(&md, dout, bf16, cout, H, W, KP, 1, 128 / GE);
-  if (e == cudaSuccess) e = make_map(&mx, in, bf16, cin, H, W, KP, 1, cin / GE);
-  if (e != cudaSuccess) return e;
-  const int otiles = (cout + 127) / 128;
-  WgradTcParams p;
-  p.cin = cin;
-  p.cout = cout;
-  p.H = H;
-  p.W = W;
-  p.chunks_x = (W + KP - 1) / KP;
-  p.total_chunks = p.chunks_x * H;
-  const size_t per_split_elems = (size_t)9 * cout * cin;
-  // splits: two waves of the CTAs that fit per SM (rounded down, so no nearly empty wave),
-  // bounded by the partial-sum workspace
-  const uint32_t smem_need = (bf16 ? WgCfg<1>::STAGES * WgCfg<1>::stage_bytes(cin)
-                                   : WgCfg<0>::STAGES * WgCfg<0>::stage_bytes(cin));
-  const int per_sm = (int)((227u * 1024u) / (smem_need + 2048u));
-  int S = (2 * 152 * (per_sm > 0 ? per_sm : 1)) / (otiles * 9);
-  if (S < 1) S = 1;
-  if (S > p.total_chunks) S = p.total_chunks;
-  const size_t npx = (size_t)H * W;
-  int SB = (int)((npx + 511) / 512);  // bias partial blocks
-  if (SB > 1024) SB = 1024;
-  const size_t bias_off = ((size_t)S * per_split_elems + 63) / 64 * 64;
-  while (S > 1 && (size_t)S * per_split_elems + 64 + (size_t)SB * cout > part_cap) --S;
-  if ((size_t)S * per_split_elems + 64 + (size_t)SB * cout > part_cap) return cudaErrorInvalidValue;
-  p.per_split = (p.total_chunks + S - 1) / S;
-  S = (p.total_chunks + p.per_split - 1) / p.per_split;
-  p.part = part;
-  p.skip = skip;
-  p.err = err;
-  const uint32_t smem = (bf16 ? WgCfg<1>::STAGES * WgCfg<1>::stage_bytes(cin)
-                              : WgCfg<0>::STAGES * WgCfg<0>::stage_bytes(cin));
-  dim3 grid((unsigned)otiles, 9, (unsigned)S);
-  e = bf16 ? wgrad_tc_launch<1>(md, mx, p, grid, smem, st) : wgrad_tc_launch<0>(md, mx, p, grid, smem, st);
-  count_launch();
-  if (e != cudaSuccess) return e;
-  unsigned g = (unsigned)((per_split_elems + 255) / 256);
-  if (g > 152u * 8) g = 152u * 8;
-  k_reduce_wgrad_tc<<<g, 256, 0, st>>>(part, S, cin, cout, gw, skip);
-  count_launch();
-  float* bpart = part + ((size_t)S * per_split_elems + 63) / 64 * 64;
-  (void)bias_off;
-  const size_t per_block = (npx + SB - 1) / SB;
-  if (bf16)
-    k_colsum_cg<__nv_bfloat16><<<SB, 256, 0, st>>>((const __nv_bfloat16*)dout, cout, npx, per_block,
-                                                   bpart, skip);
-  else
-    k_colsum_cg<float><<<SB, 256, 0, st>>>((const float*)dout, cout, npx, per_block, bpart, skip);
-  count_launch();
-  return launch_reduce_cols(bpart, SB, cout, gb, skip, st);
+  return launch_wgrad_grouped(bf16, dout, in, cin, cout, H, W, part, part_cap, gw, gb, skip, err,
+                              st);
 }
 
 }  // namespace n2f
