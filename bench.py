@@ -180,6 +180,9 @@ def roofline(stats, kclass: int, precision: int, engine_tc: bool, workload: str)
     if kclass in (1, 2, 3) and engine_tc:
         if precision == 1:
             peak, note = pk["bf16_tflops_sustained"], f"bf16 dense sustained, {src}"
+        elif kclass == 3:
+            peak = pk["bf16_tflops_sustained"] / 6.0
+            note = f"float32 as three bf16 parts, six bf16 products: bf16 sustained / 6, {src}"
         else:
             peak = pk["bf16_tflops_sustained"] * (1.1 / 2.25) / 3.0
             note = f"3xTF32: TF32 = bf16 sustained x 1.1/2.25 (nominal ratio), /3 products, {src}"
