@@ -154,8 +154,10 @@ struct ConvTcParams {
   int* err;
 };
 
-constexpr int kTileM = 128;   // pixels per CTA (one image row segment)
+constexpr int kTileM = 128;   // pixels per accumulator (one image row segment)
+constexpr int kRowsM = 2;     // image rows per CTA: each weight stage feeds two accumulators
 constexpr int kHaloX = kTileM + 2;
+constexpr int kHaloY = kRowsM + 2;
 constexpr int kConvStages = 2;
 
 template <int BF16>
@@ -163,8 +165,8 @@ struct ConvCfg {
   static constexpr int GE = BF16 ? 8 : 4;     // channels per 16-byte group
   static constexpr int KC = BF16 ? 16 : 8;    // channels per stage (= one K step of 32 bytes)
   static constexpr int NSLAB = KC / GE;       // 16-byte K slabs per stage (2)
-  static constexpr uint32_t A_BYTES = NSLAB * 3 * kHaloX * 16;
-  static constexpr uint32_t A_SLAB = 3 * kHaloX * 16;  // K distance between slabs in the halo
+  static constexpr uint32_t A_BYTES = NSLAB * kHaloY * kHaloX * 16;
+  static constexpr uint32_t A_SLAB = kHaloY * kHaloX * 16;  // K distance between halo slabs
   static __host__ __device__ uint32_t b_bytes(int NT) { return 9u * NSLAB * NT * 16; }
   // stage layout: A | A_lo (tf32) | B | B_lo (tf32)
   static __host__ __device__ uint32_t a_lo_off() { return align_up(A_BYTES, 1024); }
@@ -188,10 +190,10 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int NT = tc_cfg(p.cin, p.cout, BF16).NT;
   const uint32_t B_BYTES = C::b_bytes(NT), SB = C::stage_bytes(NT);
-  const int ty = blockIdx.x / p.tiles_x, x0 = (blockIdx.x % p.tiles_x) * kTileM;
+  const int ty = (blockIdx.x / p.tiles_x) * kRowsM, x0 = (blockIdx.x % p.tiles_x) * kTileM;
   const int nt = blockIdx.y;
   const int nk = p.cin / C::KC;
-  const uint32_t ncols = tmem_cols(NT);
+  const uint32_t ncols = tmem_cols(kRowsM * NT);
   volatile int* abort = &abort_flag;
   if (threadIdx.x == 0) {
     for (int s = 0; s < kConvStages; ++s) {
@@ -241,17 +243,21 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
         const uint32_t sb = sa + C::b_off(), sbl = sa + C::b_lo_off(NT);
 #pragma unroll
         for (int tap = 0; tap < 9; ++tap) {
-          const uint32_t ao = (uint32_t)((tap / 3) * kHaloX + (tap % 3)) * 16u;
           const uint32_t bo = (uint32_t)tap * C::NSLAB * NT * 16u;
-          const uint64_t da = sdesc(sa + ao, C::A_SLAB, 128);
           const uint64_t db = sdesc(sb + bo, NT * 16, 128);
           const uint32_t acc = (i > 0 || tap > 0) ? 1u : 0u;
-          if (BF16) {
-            mma_f16(tbase, da, db, id, acc);
-          } else {
-            mma_tf32(tbase, da, db, id, acc);
-            mma_tf32(tbase, da, sdesc(sbl + bo, NT * 16, 128), id, 1u);
-            mma_tf32(tbase, sdesc(sal + ao, C::A_SLAB, 128), db, id, 1u);
+#pragma unroll
+          for (int r = 0; r < kRowsM; ++r) {  // output row r reads halo rows r .. r + 2
+            const uint32_t ao = (uint32_t)((r + tap / 3) * kHaloX + (tap % 3)) * 16u;
+            const uint64_t da = sdesc(sa + ao, C::A_SLAB, 128);
+            const uint32_t d = tbase + (uint32_t)(r * NT);
+            if (BF16) {
+              mma_f16(d, da, db, id, acc);
+            } else {
+              mma_tf32(d, da, db, id, acc);
+              mma_tf32(d, da, sdesc(sbl + bo, NT * 16, 128), id, 1u);
+              mma_tf32(d, sdesc(sal + ao, C::A_SLAB, 128), db, id, 1u);
+            }
           }
         }
         mma_commit(&empty[s]);
@@ -281,16 +287,16 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
     const int wq = warp & 3;  // the TMEM lane quarter this warp may read
     const int row = wq * 32 + lane;
     const int x = x0 + row;
-    const bool live = x < p.W && !*abort;
     const size_t npx = (size_t)p.H * p.W;
-    const size_t pix = (size_t)ty * p.W + x;
     constexpr int GE = C::GE;
-    for (int c0 = 0; c0 < NT; c0 += 16) {
+    for (int c0 = 0; c0 < kRowsM * NT; c0 += 16) {
       uint32_t r[16];
       tmem_ld16(tbase + ((uint32_t)(wq * 32) << 16) + c0, r);
       tmem_ld_wait();
-      if (!live) continue;
-      const int o0 = nt * NT + c0;
+      const int yr = ty + c0 / NT;
+      if (x >= p.W || yr >= p.H || *abort) continue;
+      const size_t pix = (size_t)yr * p.W + x;
+      const int o0 = nt * NT + (c0 % NT);
       float v[16];
 #pragma unroll
       for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
@@ -766,7 +772,7 @@ cudaError_t tc_prepare() {
       result = cudaErrorNotSupported;
       return;
     }
-    const int lim = 200 * 1024;
+    const int lim = 227 * 1024;
     cudaError_t e = cudaSuccess;
     auto set = [&](const void* f) {
       if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
@@ -803,7 +809,7 @@ cudaError_t launch_conv_tc(int mode, int bf16, const void* in, int cin, int cout
   CUtensorMap m;
   const int KC = bf16 ? ConvCfg<1>::KC : ConvCfg<0>::KC;
   const int GE = bf16 ? 8 : 4;
-  cudaError_t e = make_map(&m, in, bf16, cin, H, W, kHaloX, 3, KC / GE);
+  cudaError_t e = make_map(&m, in, bf16, cin, H, W, kHaloX, kHaloY, KC / GE);
   if (e != cudaSuccess) return e;
   ConvTcParams p;
   p.w_hi = (const uint8_t*)w_hi;
@@ -818,7 +824,7 @@ cudaError_t launch_conv_tc(int mode, int bf16, const void* in, int cin, int cout
   p.tiles_x = (W + kTileM - 1) / kTileM;
   p.skip = skip;
   p.err = err;
-  dim3 grid((unsigned)(p.tiles_x * H), (unsigned)(cout / f.NT));
+  dim3 grid((unsigned)(p.tiles_x * ((H + kRowsM - 1) / kRowsM)), (unsigned)(cout / f.NT));
   const uint32_t smem = kConvStages * (bf16 ? ConvCfg<1>::stage_bytes(f.NT) : ConvCfg<0>::stage_bytes(f.NT));
   if (bf16)
     e = mode == 0 ? conv_tc_launch<1, 0>(m, p, grid, smem, st) : conv_tc_launch<1, 1>(m, p, grid, smem, st);
