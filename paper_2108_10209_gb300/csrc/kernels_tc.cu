@@ -772,10 +772,17 @@ cudaError_t tc_prepare() {
       result = cudaErrorNotSupported;
       return;
     }
-    const int lim = 227 * 1024;
-    cudaError_t e = cudaSuccess;
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    // dynamic limit = the per-block opt-in total minus the kernel's static shared memory
     auto set = [&](const void* f) {
-      if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+      if (e != cudaSuccess) return;
+      cudaFuncAttributes fa;
+      e = cudaFuncGetAttributes(&fa, f);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 optin - (int)fa.sharedSizeBytes);
     };
     set((const void*)k_conv_tc<1, 0>);
     set((const void*)k_conv_tc<1, 1>);
