@@ -672,55 +672,67 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc_f32(const __grid_constant__
   }
 }
 
-// gw[(o*C_in + c)*9 + tap] = sum_s part[s][tap][o][c] (ascending s)
-__global__ void k_reduce_wgrad_tc(const float* __restrict__ part, int S, int cin, int cout,
-                                  float* __restrict__ gw, const int* skip) {
+// gw[(o*C_in + c)*9 + tap] = sum_s part[s][tap][o][c]. A block owns 32 consecutive outputs;
+// warp w sums the splits s = w, w + 8, ... in order and the eight warp sums are added in warp
+// order, so the result is fixed for a given number of splits.
+__global__ void __launch_bounds__(256) k_reduce_wgrad_tc(const float* __restrict__ part, int S,
+                                                         int cin, int cout,
+                                                         float* __restrict__ gw, const int* skip) {
   if (skip && *skip) return;
+  __shared__ float sh[8][33];
   const size_t n = (size_t)cout * cin * 9;
   const size_t per = (size_t)9 * cout * cin;
-  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n;
-       q += (size_t)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const size_t q = (size_t)blockIdx.x * 32 + lane;
+  float s = 0.f;
+  size_t src = 0;
+  if (q < n) {
     const int tap = (int)(q % 9);
     const size_t oc = q / 9;
     const int c = (int)(oc % cin), o = (int)(oc / cin);
-    const size_t src = ((size_t)tap * cout + o) * cin + c;
-    float s = 0.f;
-    for (int k = 0; k < S; ++k) s += part[k * per + src];
-    gw[q] = s;
+    src = ((size_t)tap * cout + o) * cin + c;
+    for (int k = w; k < S; k += 8) s += part[k * per + src];
+  }
+  sh[w][lane] = s;
+  __syncthreads();
+  if (w == 0 && q < n) {
+    float t = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t += sh[k][lane];
+    gw[q] = t;
   }
 }
 
-// Bias gradient db[c] = sum_p d(p, c) of a CG map: block b sums its pixel range, then the
-// per-block sums are added in block order.
+// Bias gradient db[c] = sum_p d(p, c) of a CG map. Block b owns a pixel range; warp w takes
+// the channel groups w, w + 8, ...; its lanes read 32 consecutive pixels of a group (512
+// contiguous bytes) and a fixed shuffle tree adds the lanes. The per-block sums are then
+// added in block order, so the result is fixed for a given block count.
 template <typename T>
 __global__ void __launch_bounds__(256) k_colsum_cg(const T* __restrict__ d, int C, size_t npx,
                                                    size_t per_block, float* __restrict__ bpart,
                                                    const int* skip) {
   if (skip && *skip) return;
   constexpr int GE = CGTraits<T>::G;
-  __shared__ float sacc[256 * GE];
   const int ng = C / GE;
-  const int J = 256 / ng;
-  const int g = threadIdx.x % ng, j = threadIdx.x / ng;
-  float acc[GE];
-#pragma unroll
-  for (int k = 0; k < GE; ++k) acc[k] = 0.f;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const size_t pb = blockIdx.x * per_block, pe = min(npx, pb + per_block);
-  if (j < J)
-    for (size_t pix = pb + j; pix < pe; pix += J) {
+  for (int g = w; g < ng; g += 8) {
+    float acc[GE];
+#pragma unroll
+    for (int k = 0; k < GE; ++k) acc[k] = 0.f;
+    for (size_t pix = pb + lane; pix < pe; pix += 32) {
       float v[GE];
       load_group<T>(d, (size_t)g * npx + pix, v);
 #pragma unroll
       for (int k = 0; k < GE; ++k) acc[k] += v[k];
     }
-  if (j < J)
 #pragma unroll
-    for (int k = 0; k < GE; ++k) sacc[j * C + g * GE + k] = acc[k];
-  __syncthreads();
-  for (int c = threadIdx.x; c < C; c += 256) {
-    float s = 0.f;
-    for (int jj = 0; jj < J; ++jj) s += sacc[jj * C + c];
-    bpart[(size_t)blockIdx.x * C + c] = s;
+    for (int k = 0; k < GE; ++k)
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], off);
+    if (lane == 0)
+#pragma unroll
+      for (int k = 0; k < GE; ++k) bpart[(size_t)blockIdx.x * C + g * GE + k] = acc[k];
   }
 }
 
@@ -870,10 +882,10 @@ static cudaError_t launch_wgrad_grouped(int bf16, const void* dout, const void* 
   const int per_sm = (int)((227u * 1024u) / (smem + 2048u));
   const int ctas = otiles * tg.n;
   int S = (2 * 152 * (per_sm > 0 ? per_sm : 1)) / ctas;
+  if (S > p.total_chunks / 16) S = p.total_chunks / 16;  // at least 16 pixel chunks per split
   if (S < 1) S = 1;
-  if (S > p.total_chunks) S = p.total_chunks;
   const size_t npx = (size_t)H * W;
-  int SB = (int)((npx + 511) / 512);
+  int SB = (int)((npx + 255) / 256);
   if (SB > 1024) SB = 1024;
   while (S > 1 && (size_t)S * per_split_elems + 64 + (size_t)SB * cout > part_cap) --S;
   if ((size_t)S * per_split_elems + 64 + (size_t)SB * cout > part_cap) return cudaErrorInvalidValue;
@@ -889,9 +901,8 @@ static cudaError_t launch_wgrad_grouped(int bf16, const void* dout, const void* 
     k_wgrad_tc_f32<<<grid, 192, smem, st>>>(md, mx, p);
   count_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  unsigned g = (unsigned)((per_split_elems + 255) / 256);
-  if (g > 152u * 8) g = 152u * 8;
-  k_reduce_wgrad_tc<<<g, 256, 0, st>>>(part, S, cin, cout, gw, skip);
+  k_reduce_wgrad_tc<<<(unsigned)((per_split_elems + 31) / 32), 256, 0, st>>>(part, S, cin, cout,
+                                                                            gw, skip);
   count_launch();
   float* bpart = part + ((size_t)S * per_split_elems + 63) / 64 * 64;
   const size_t per_block = (npx + SB - 1) / SB;
