@@ -39,7 +39,7 @@ METRIC = "denoised images/s (p50/p99 latency per image)"
 UNIT = "images/s"
 WIDTH_NAMES = {0: "32-32-64-64-128-128-256-256", 1: "64x8"}
 CLASS_NAMES = {1: "conv3x3_fwd", 2: "conv3x3_dgrad", 3: "conv3x3_wgrad", 4: "conv1_fwd",
-               5: "head", 6: "adam"}
+               5: "head", 6: "adam", 7: "k_conv_tc (forward + dgrad)"}
 MIN_EPOCHS = 101  # shortest run the stopping rule allows: one best epoch + 100 without gain
 
 
@@ -177,7 +177,7 @@ def roofline(stats, kclass: int, precision: int, engine_tc: bool, workload: str)
     flops = stats["prof_flops"] / n
     bytes_ = stats["prof_bytes"] / n
     name = CLASS_NAMES.get(kclass, str(kclass))
-    if kclass in (1, 2, 3) and engine_tc:
+    if kclass in (1, 2, 3, 7) and engine_tc:
         if precision == 1:
             peak, note = pk["bf16_tflops_sustained"], f"bf16 dense sustained, {src}"
         elif kclass == 3:
@@ -187,7 +187,7 @@ def roofline(stats, kclass: int, precision: int, engine_tc: bool, workload: str)
             peak = pk["bf16_tflops_sustained"] * (1.1 / 2.25) / 3.0
             note = f"3xTF32: TF32 = bf16 sustained x 1.1/2.25 (nominal ratio), /3 products, {src}"
         rl = {"bound": "tensor", "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s"}
-    elif kclass in (1, 2, 3):
+    elif kclass in (1, 2, 3, 7):
         clk = pk.get("sm_max_mhz", 2070.0)
         peak = 152 * 128 * 2 * clk * 1e6 / 1e12
         note = f"FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x {clk:.0f} MHz (unit counts x max clock)"
@@ -469,8 +469,9 @@ def main():
     ap.add_argument("--precision", type=int, default=0, help="0 fp32, 1 bf16")
     ap.add_argument("--widths", type=int, default=0, help="0 literal widths, 1 constant 64")
     ap.add_argument("--engine", type=int, default=0, help="0 auto, 1 simt, 2 tcgen05")
-    ap.add_argument("--profile-kernel", type=int, default=1,
-                    help="kernel class timed for the roofline (1 fwd, 2 dgrad, 3 wgrad)")
+    ap.add_argument("--profile-kernel", type=int, default=7,
+                    help="kernel class timed for the roofline (7 conv forward+dgrad, 1 forward, "
+                         "2 dgrad, 3 wgrad)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--form", default="plain", choices=["plain", "batched", "serving"])
     ap.add_argument("--compare-batch", type=int, default=16,

@@ -80,7 +80,8 @@ enum n2f_kernel_class {
   N2F_K_CONV_WGRAD = 3, /* 3x3 weight-gradient layers with C_in >= 8 (incl. their reduce) */
   N2F_K_FIRST = 4,      /* the one-channel first layer, forward */
   N2F_K_HEAD = 5,       /* the 1x1 + sigmoid head, training and validation */
-  N2F_K_ADAM = 6        /* Adam + operand packing */
+  N2F_K_ADAM = 6,       /* Adam + operand packing */
+  N2F_K_CONV = 7        /* forward and dgrad 3x3 layers with C_in >= 8 (one kernel template) */
 };
 
 typedef struct {

@@ -100,7 +100,9 @@ struct Timed {
   cudaStream_t st;
   KTimer::Pair p;
   Timed(Trainer* t, int kind, double flops, double bytes, int val) : st(t->st) {
-    if (!t->kt || t->kt->kind != kind) return;
+    if (!t->kt) return;
+    const bool conv = t->kt->kind == N2F_K_CONV && (kind == N2F_K_CONV_FWD || kind == N2F_K_CONV_DGRAD);
+    if (t->kt->kind != kind && !conv) return;
     kt = t->kt;
     p.a = kt->get();
     p.b = nullptr;

@@ -26,7 +26,7 @@ N2F_QUEUED, N2F_RUNNING, N2F_DONE, N2F_FAILED, N2F_CANCELED = range(5)
 (N2F_X_THETA, N2F_X_GRAD, N2F_X_ADAM_M, N2F_X_ADAM_V, N2F_X_ACT, N2F_X_DELTA) = range(6)
 N2F_X_DZ, N2F_X_PAIR, N2F_X_VAL, N2F_X_SUM, N2F_X_OUT = 7, 8, 9, 10, 11
 (N2F_K_NONE, N2F_K_CONV_FWD, N2F_K_CONV_DGRAD, N2F_K_CONV_WGRAD, N2F_K_FIRST, N2F_K_HEAD,
- N2F_K_ADAM) = range(7)
+ N2F_K_ADAM, N2F_K_CONV) = range(8)
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
