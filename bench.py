@@ -252,15 +252,11 @@ def run_ours(args, ws, rank, local):
     clk = clocks.stop()
     st1 = ctx.stats()
     ctx.close()
-    tot_dev_s = sum(comp_ms) / 1e3
-    tot_wall_s = sum(wall_ms) / 1e3
-    if ws > 1:
-        t = torch.tensor([tot_dev_s, tot_wall_s], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot_dev_s, tot_wall_s = float(t[0]), float(t[1])
+    from paper_2108_10209_gb300 import dispatch
+    tot_dev_s, n_img = dispatch.aggregate(sum(comp_ms) / 1e3, args.steps)
+    tot_wall_s, _ = dispatch.aggregate(sum(wall_ms) / 1e3, args.steps)
     if rank != 0:
         return None
-    n_img = args.steps * ws
     stats = {k: st1[k] - st0[k] if isinstance(st1[k], (int, float)) else st1[k] for k in st1}
     workload = f"{size}x{size} cells fp{'32' if args.precision == 0 else 'bf16'} " \
                f"{WIDTH_NAMES[args.widths]} plain"

@@ -125,3 +125,52 @@ def test_trained_network_gains_over_the_untrained_path(n2f):
     assert st.stopped == 1 and st.epoch >= 101
     assert p_out > p_noisy + 3.0
     assert p_out > p_out0 + 5.0
+
+
+def test_graph_replay_matches_launch_by_launch(n2f):
+    # An epoch captured once as a CUDA graph and replayed computes exactly what launching its
+    # kernels one by one computes (every mutable scalar lives in device memory).
+    _, x = _img(40, 36, 31)
+    p = n2f.params(seed=3, patience=5, widths=1)
+    outs = []
+    for graphs in (False, True):
+        with n2f.Context(use_graphs=graphs) as ctx:
+            j = ctx.submit(x, p)
+            ctx.wait(j)
+            st = ctx.poll(j)
+            outs.append((ctx.result(j, x.shape), st.epoch, st.steps))
+    assert outs[0][1:] == outs[1][1:]
+    assert np.array_equal(outs[0][0], outs[1][0])
+
+
+def test_admission_by_hbm_budget(n2f):
+    # The budget admits jobs first-in first-out while their device state fits; a job that can
+    # never fit is refused at submission.
+    _, x = _img(64, 64, 41)
+    p = n2f.params(seed=1, fixed_steps=40)
+    with n2f.Context(hbm_budget_bytes=1 << 20) as ctx:
+        with pytest.raises(n2f.N2FError) as e:
+            ctx.submit(x, p)
+        assert e.value.code == n2f.N2F_ETOOBIG
+    probe_bytes = 0
+    with n2f.Context() as ctx:  # measure one job's resident bytes
+        j = ctx.submit(x, p)
+        while ctx.poll(j).state == n2f.N2F_QUEUED:
+            pass
+        probe_bytes = ctx.stats()["bytes_resident"]
+        ctx.wait(j)
+        ref = ctx.result(j, x.shape)
+    assert probe_bytes > 0
+    with n2f.Context(hbm_budget_bytes=int(probe_bytes * 1.5)) as ctx:  # one job at a time
+        ids = [ctx.submit(x, p) for _ in range(3)]
+        seen_queued = False
+        while True:
+            st = ctx.stats()
+            assert st["bytes_resident"] <= int(probe_bytes * 1.5)
+            seen_queued |= st["jobs_queued"] > 0 and st["jobs_running"] == 1
+            if st["jobs_done"] == 3:
+                break
+        outs = [ctx.result(j, x.shape) for j in ids]
+    assert seen_queued
+    for o in outs:
+        assert np.array_equal(o, ref)
