@@ -153,12 +153,10 @@ def test_admission_by_hbm_budget(n2f):
             ctx.submit(x, p)
         assert e.value.code == n2f.N2F_ETOOBIG
     probe_bytes = 0
-    with n2f.Context() as ctx:  # measure one job's resident bytes
+    with n2f.Context() as ctx:  # measure one job's resident bytes while it runs
         j = ctx.submit(x, p)
-        while ctx.poll(j).state == n2f.N2F_QUEUED:
-            pass
-        probe_bytes = ctx.stats()["bytes_resident"]
-        ctx.wait(j)
+        while ctx.poll(j).state < n2f.N2F_DONE:
+            probe_bytes = max(probe_bytes, ctx.stats()["bytes_resident"])
         ref = ctx.result(j, x.shape)
     assert probe_bytes > 0
     with n2f.Context(hbm_budget_bytes=int(probe_bytes * 1.5)) as ctx:  # one job at a time
