@@ -177,23 +177,37 @@ struct ConvCfg {
   }
 };
 
+// Persistent: the grid holds one CTA per resident slot and each CTA takes the tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ... (a fixed order). The producer streams the stages of
+// successive tiles without a break; the accumulators are double-buffered in TMEM when two sets
+// fit (2 x kRowsM x N <= 512 columns), so a tile's epilogue overlaps the next tile's MMAs.
+// Warp roles: 0 TMA producer, 1 MMA issuer, 2-5 epilogue, 6-9 (3xTF32 only) operand split.
+template <int BF16>
+struct ConvWarps {
+  static constexpr int kThreads = BF16 ? 192 : 320;
+};
+
 template <int BF16, int MODE>
-__global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUtensorMap tmA,
-                                                   ConvTcParams p) {
+__global__ void __launch_bounds__(ConvWarps<BF16>::kThreads, 1)
+    k_conv_tc(const __grid_constant__ CUtensorMap tmA, ConvTcParams p) {
   using C = ConvCfg<BF16>;
   using T = typename std::conditional<BF16, __nv_bfloat16, float>::type;
   extern __shared__ __align__(1024) uint8_t smem[];
-  __shared__ uint64_t full[kConvStages], empty[kConvStages], split[kConvStages], accf;
+  __shared__ uint64_t full[kConvStages], empty[kConvStages], split[kConvStages];
+  __shared__ uint64_t accf[2], acce[2];
   __shared__ uint32_t tslot;
   __shared__ int abort_flag;
   if (p.skip && *p.skip) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int NT = tc_cfg(p.cin, p.cout, BF16).NT;
   const uint32_t B_BYTES = C::b_bytes(NT), SB = C::stage_bytes(NT);
-  const int ty = (blockIdx.x / p.tiles_x) * kRowsM, x0 = (blockIdx.x % p.tiles_x) * kTileM;
-  const int nt = blockIdx.y;
   const int nk = p.cin / C::KC;
-  const uint32_t ncols = tmem_cols(kRowsM * NT);
+  const int ntn = p.cout / NT;
+  const int tiles_y = (p.H + kRowsM - 1) / kRowsM;
+  const int ntiles = p.tiles_x * tiles_y * ntn;
+  const int acc_cols = kRowsM * NT;
+  const int NB = 2 * acc_cols <= 512 ? 2 : 1;  // accumulator buffers
+  const uint32_t ncols = tmem_cols(NB * acc_cols);
   volatile int* abort = &abort_flag;
   if (threadIdx.x == 0) {
     for (int s = 0; s < kConvStages; ++s) {
@@ -201,7 +215,10 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
       mbar_init(&empty[s], 1);
       mbar_init(&split[s], 128);
     }
-    mbar_init(&accf, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accf[b], 1);
+      mbar_init(&acce[b], 128);
+    }
     abort_flag = 0;
     mbar_fence_init();
   }
@@ -210,66 +227,91 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = tslot;
+  // tile -> (n-tile, row pair, x segment); the n-tile varies fastest so CTAs running at the
+  // same time share the activation halo in L2
+  auto decode = [&](int tile, int& nt, int& ty, int& x0) {
+    nt = tile % ntn;
+    const int rest = tile / ntn;
+    ty = (rest / p.tiles_x) * kRowsM;
+    x0 = (rest % p.tiles_x) * kTileM;
+  };
 
   if (warp == 0) {
     if (lane == 0) {  // producer: halo tile by TMA, weight stage image by bulk copy
-      int issued = 0;
-      for (int i = 0; i < nk; ++i) {
-        const int s = i % kConvStages;
-        if (i >= kConvStages && !mbar_wait(&empty[s], ((i / kConvStages) - 1) & 1, abort, p.err))
-          break;
-        uint8_t* st = smem + s * SB;
-        mbar_expect_tx(&full[s], C::A_BYTES + B_BYTES * (BF16 ? 1 : 2));
-        tma_load_4d(st, &tmA, &full[s], 0, x0 - 1, ty - 1, i * C::NSLAB);
-        const size_t stage = (size_t)nt * nk + i;
-        bulk_load(st + C::b_off(), p.w_hi + stage * B_BYTES, B_BYTES, &full[s]);
-        if (!BF16) bulk_load(st + C::b_lo_off(NT), p.w_lo + stage * B_BYTES, B_BYTES, &full[s]);
-        issued = i + 1;
+      uint32_t it = 0, issued_lo = 0;
+      for (int tile = blockIdx.x; tile < ntiles && !*abort; tile += gridDim.x) {
+        int nt, ty, x0;
+        decode(tile, nt, ty, x0);
+        for (int i = 0; i < nk; ++i, ++it) {
+          const int s = it % kConvStages;
+          if (it >= kConvStages && !mbar_wait(&empty[s], ((it / kConvStages) - 1) & 1, abort, p.err))
+            break;
+          uint8_t* st = smem + s * SB;
+          mbar_expect_tx(&full[s], C::A_BYTES + B_BYTES * (BF16 ? 1 : 2));
+          tma_load_4d(st, &tmA, &full[s], 0, x0 - 1, ty - 1, i * C::NSLAB);
+          const size_t stage = (size_t)nt * nk + i;
+          bulk_load(st + C::b_off(), p.w_hi + stage * B_BYTES, B_BYTES, &full[s]);
+          if (!BF16) bulk_load(st + C::b_lo_off(NT), p.w_lo + stage * B_BYTES, B_BYTES, &full[s]);
+          issued_lo = it + 1;
+        }
       }
       if (*abort)
-        for (int i = issued > kConvStages ? issued - kConvStages : 0; i < issued; ++i)
+        for (uint32_t i = issued_lo > kConvStages ? issued_lo - kConvStages : 0; i < issued_lo; ++i)
           mbar_drain(&full[i % kConvStages], (i / kConvStages) & 1);
     }
   } else if (warp == 1) {
     if (lane == 0) {  // MMA issuer
       const uint32_t id = idesc(BF16 ? 1 : 2, kTileM, NT, 0, 0);
-      for (int i = 0; i < nk; ++i) {
-        const int s = i % kConvStages;
-        const uint32_t ph = (i / kConvStages) & 1;
-        if (!mbar_wait(BF16 ? &full[s] : &split[s], ph, abort, p.err)) break;
+      uint32_t it = 0, lt = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++lt) {
+        const int buf = (int)(lt % NB);
+        if (lt >= (uint32_t)NB && !mbar_wait(&acce[buf], ((lt / NB) - 1) & 1, abort, p.err)) break;
         tc_fence_after();
-        const uint32_t sa = smem_u32(smem + s * SB);
-        const uint32_t sal = sa + C::a_lo_off();
-        const uint32_t sb = sa + C::b_off(), sbl = sa + C::b_lo_off(NT);
+        const uint32_t dbase = tbase + (uint32_t)(buf * acc_cols);
+        for (int i = 0; i < nk; ++i, ++it) {
+          const int s = it % kConvStages;
+          const uint32_t ph = (it / kConvStages) & 1;
+          if (!mbar_wait(BF16 ? &full[s] : &split[s], ph, abort, p.err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(smem + s * SB);
+          const uint32_t sal = sa + C::a_lo_off();
+          const uint32_t sb = sa + C::b_off(), sbl = sa + C::b_lo_off(NT);
 #pragma unroll
-        for (int tap = 0; tap < 9; ++tap) {
-          const uint32_t bo = (uint32_t)tap * C::NSLAB * NT * 16u;
-          const uint64_t db = sdesc(sb + bo, NT * 16, 128);
-          const uint32_t acc = (i > 0 || tap > 0) ? 1u : 0u;
+          for (int tap = 0; tap < 9; ++tap) {
+            const uint32_t bo = (uint32_t)tap * C::NSLAB * NT * 16u;
+            const uint64_t db = sdesc(sb + bo, NT * 16, 128);
+            const uint32_t acc = (i > 0 || tap > 0) ? 1u : 0u;
 #pragma unroll
-          for (int r = 0; r < kRowsM; ++r) {  // output row r reads halo rows r .. r + 2
-            const uint32_t ao = (uint32_t)((r + tap / 3) * kHaloX + (tap % 3)) * 16u;
-            const uint64_t da = sdesc(sa + ao, C::A_SLAB, 128);
-            const uint32_t d = tbase + (uint32_t)(r * NT);
-            if (BF16) {
-              mma_f16(d, da, db, id, acc);
-            } else {
-              mma_tf32(d, da, db, id, acc);
-              mma_tf32(d, da, sdesc(sbl + bo, NT * 16, 128), id, 1u);
-              mma_tf32(d, sdesc(sal + ao, C::A_SLAB, 128), db, id, 1u);
+            for (int r = 0; r < kRowsM; ++r) {  // output row r reads halo rows r .. r + 2
+              const uint32_t ao = (uint32_t)((r + tap / 3) * kHaloX + (tap % 3)) * 16u;
+              const uint64_t da = sdesc(sa + ao, C::A_SLAB, 128);
+              const uint32_t d = dbase + (uint32_t)(r * NT);
+              if (BF16) {
+                mma_f16(d, da, db, id, acc);
+              } else {
+                mma_tf32(d, da, db, id, acc);
+                mma_tf32(d, da, sdesc(sbl + bo, NT * 16, 128), id, 1u);
+                mma_tf32(d, sdesc(sal + ao, C::A_SLAB, 128), db, id, 1u);
+              }
             }
           }
+          mma_commit(&empty[s]);
         }
-        mma_commit(&empty[s]);
+        mma_commit(&accf[buf]);
       }
-      mma_commit(&accf);
     }
-  } else {
-    const int et = threadIdx.x - 64;
-    if (!BF16) {  // 3xTF32: split the fp32 halo into TF32 hi and lo parts
-      for (int i = 0; i < nk; ++i) {
-        const int s = i % kConvStages;
-        if (!mbar_wait(&full[s], (i / kConvStages) & 1, abort, p.err)) break;
+  } else if (warp >= 6) {
+    // 3xTF32: split each fp32 halo stage into TF32 hi and lo parts, ahead of the MMAs
+    const int et = threadIdx.x - 192;
+    uint32_t it = 0;
+    for (int tile = blockIdx.x; tile < ntiles && !*abort; tile += gridDim.x) {
+      for (int i = 0; i < nk; ++i, ++it) {
+        const int s = it % kConvStages;
+        if (!mbar_wait(&full[s], (it / kConvStages) & 1, abort, p.err)) break;
         float4* A = reinterpret_cast<float4*>(smem + s * SB);
         float4* Al = reinterpret_cast<float4*>(smem + s * SB + C::a_lo_off());
         for (int q = et; q < (int)(C::A_BYTES / 16); q += 128) {
@@ -282,42 +324,56 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
         mbar_arrive(&split[s]);
       }
     }
-    if (!mbar_wait(&accf, 0, abort, p.err)) mbar_drain(&accf, 0);
-    tc_fence_after();
+  } else {
+    // epilogue: TMEM -> bias + ReLU (forward) or ReLU mask (dgrad) -> global
     const int wq = warp & 3;  // the TMEM lane quarter this warp may read
     const int row = wq * 32 + lane;
-    const int x = x0 + row;
     const size_t npx = (size_t)p.H * p.W;
     constexpr int GE = C::GE;
-    for (int c0 = 0; c0 < kRowsM * NT; c0 += 16) {
-      uint32_t r[16];
-      tmem_ld16(tbase + ((uint32_t)(wq * 32) << 16) + c0, r);
-      tmem_ld_wait();
-      const int yr = ty + c0 / NT;
-      if (x >= p.W || yr >= p.H || *abort) continue;
-      const size_t pix = (size_t)yr * p.W + x;
-      const int o0 = nt * NT + (c0 % NT);
-      float v[16];
-#pragma unroll
-      for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
-#pragma unroll
-      for (int q = 0; q < 16 / GE; ++q) {
-        const size_t gi = (size_t)((o0 + q * GE) / GE) * npx + pix;
-        float* vv = v + q * GE;
-        if (MODE == 0) {
-#pragma unroll
-          for (int j = 0; j < GE; ++j) {
-            const float t = vv[j] + __ldg(p.bias + o0 + q * GE + j);
-            vv[j] = t > 0.f ? t : 0.f;
-          }
-        } else {
-          float mk[GE];
-          load_group<T>((const T*)p.mask, gi, mk);
-#pragma unroll
-          for (int j = 0; j < GE; ++j) vv[j] = mk[j] > 0.f ? vv[j] : 0.f;
-        }
-        store_group<T>((T*)p.out, gi, vv);
+    uint32_t lt = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
+      const int buf = (int)(lt % NB);
+      if (!mbar_wait(&accf[buf], (lt / NB) & 1, abort, p.err)) {
+        mbar_drain(&accf[buf], (lt / NB) & 1);
+        break;
       }
+      tc_fence_after();
+      int nt, ty, x0;
+      decode(tile, nt, ty, x0);
+      const int x = x0 + row;
+      const uint32_t cbase = tbase + ((uint32_t)(wq * 32) << 16) + (uint32_t)(buf * acc_cols);
+      for (int c0 = 0; c0 < acc_cols; c0 += 16) {
+        uint32_t r[16];
+        tmem_ld16(cbase + c0, r);
+        tmem_ld_wait();
+        const int yr = ty + c0 / NT;
+        if (x >= p.W || yr >= p.H) continue;
+        const size_t pix = (size_t)yr * p.W + x;
+        const int o0 = nt * NT + (c0 % NT);
+        float v[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+#pragma unroll
+        for (int q = 0; q < 16 / GE; ++q) {
+          const size_t gi = (size_t)((o0 + q * GE) / GE) * npx + pix;
+          float* vv = v + q * GE;
+          if (MODE == 0) {
+#pragma unroll
+            for (int j = 0; j < GE; ++j) {
+              const float t = vv[j] + __ldg(p.bias + o0 + q * GE + j);
+              vv[j] = t > 0.f ? t : 0.f;
+            }
+          } else {
+            float mk[GE];
+            load_group<T>((const T*)p.mask, gi, mk);
+#pragma unroll
+            for (int j = 0; j < GE; ++j) vv[j] = mk[j] > 0.f ? vv[j] : 0.f;
+          }
+          store_group<T>((T*)p.out, gi, vv);
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&acce[buf]);
     }
   }
   tc_fence_before();
@@ -327,8 +383,6 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
     tmem_dealloc(tbase, ncols);
   }
 }
-
-// ---- weight gradient ------------------------------------------------------------------------
 
 // ---- bf16 weight gradient, several taps per CTA -----------------------------------------
 // A CTA covers a group of taps that share image rows: the x halo tile (R rows x (KP + 2)
@@ -768,7 +822,7 @@ namespace {
 template <int BF16, int MODE>
 cudaError_t conv_tc_launch(const CUtensorMap& m, const ConvTcParams& p, dim3 grid, uint32_t smem,
                            cudaStream_t st) {
-  k_conv_tc<BF16, MODE><<<grid, 192, smem, st>>>(m, p);
+  k_conv_tc<BF16, MODE><<<grid, ConvWarps<BF16>::kThreads, smem, st>>>(m, p);
   return cudaGetLastError();
 }
 
@@ -843,8 +897,20 @@ cudaError_t launch_conv_tc(int mode, int bf16, const void* in, int cin, int cout
   p.tiles_x = (W + kTileM - 1) / kTileM;
   p.skip = skip;
   p.err = err;
-  dim3 grid((unsigned)(p.tiles_x * ((H + kRowsM - 1) / kRowsM)), (unsigned)(cout / f.NT));
-  const uint32_t smem = kConvStages * (bf16 ? ConvCfg<1>::stage_bytes(f.NT) : ConvCfg<0>::stage_bytes(f.NT));
+  uint32_t smem = kConvStages * (bf16 ? ConvCfg<1>::stage_bytes(f.NT) : ConvCfg<0>::stage_bytes(f.NT));
+  // persistent grid: every resident slot once. The CTAs an SM may hold are capped by TMEM
+  // (512 columns): shared memory is padded so no more than 512 / ncols CTAs fit on one SM.
+  const long ntiles = (long)p.tiles_x * ((H + kRowsM - 1) / kRowsM) * (cout / f.NT);
+  const int acc_cols = kRowsM * f.NT;
+  const int ncols = (int)tmem_cols((2 * acc_cols <= 512 ? 2 : 1) * acc_cols);
+  const int max_res = 512 / ncols;
+  const uint32_t min_smem = (228u * 1024u) / (uint32_t)(max_res + 1) + 1024u;
+  if (smem < min_smem) smem = min_smem;
+  int per_sm = (int)((227u * 1024u) / (smem + 2048u));
+  if (per_sm > max_res) per_sm = max_res;
+  if (per_sm < 1) per_sm = 1;
+  const long slots = 152L * per_sm;
+  dim3 grid((unsigned)(ntiles < slots ? ntiles : slots), 1);
   if (bf16)
     e = mode == 0 ? conv_tc_launch<1, 0>(m, p, grid, smem, st) : conv_tc_launch<1, 1>(m, p, grid, smem, st);
   else
