@@ -415,6 +415,7 @@ TapGroups tap_groups(int cin) {
 struct WgBf16Params {
   float* part;  // [S][9][C_out][C_in]
   int cin, cout, H, W, chunks_x, total_chunks, per_split;
+  int stages;  // pipeline stages (float32 kernel)
   TapGroups tg;
   const int* skip;
   int* err;
@@ -541,10 +542,12 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc_bf16(const __grid_constant_
 // Each fp32 value x is split into x = b0 + b1 + b2 (bf16, each the rounded remainder of the
 // previous) and D = sum of the six products b_i c_j with i + j <= 2; the three dropped products
 // are below 2^-25 of the true one. bf16 operands can be read MN-major, so the tap-grouped halo
-// scheme of the bf16 kernel applies unchanged: TMA brings the fp32 tiles, the four epilogue
-// warps write the three bf16 images of each, one MMA warp issues six MMAs per tap and K step.
+// scheme of the bf16 kernel applies unchanged: TMA brings the fp32 tiles, eight split warps
+// write the three bf16 images of each, one MMA warp issues six MMAs per tap and K step.
 constexpr int kW3KP = 16;  // pixels per stage (one bf16 K step)
-constexpr int kW3Stages = 3;
+constexpr int kW3MaxStages = 4;
+constexpr int kW3SplitWarps = 8;
+constexpr int kW3Threads = 64 + 32 * kW3SplitWarps;
 
 struct W3Layout {
   uint32_t rawA, rawB, a[3], b[3], stage;
@@ -565,50 +568,85 @@ __host__ __device__ inline W3Layout w3_layout(int cin, int R) {
   return L;
 }
 
-// [G4][P][4] fp32 tile -> three [G4/2][P][8] bf16 tiles (rows of one 16-byte group each).
-__device__ __forceinline__ void split3_bf16(const float4* raw, uint4* b0, uint4* b1, uint4* b2,
-                                            int g8n, int P, int et) {
-  for (int u = et; u < g8n * P; u += 128) {
-    const int g8 = u / P, px = u % P;
-    const float4 lo4 = raw[(size_t)(2 * g8) * P + px], hi4 = raw[(size_t)(2 * g8 + 1) * P + px];
-    const float x[8] = {lo4.x, lo4.y, lo4.z, lo4.w, hi4.x, hi4.y, hi4.z, hi4.w};
-    unsigned w0[4], w1[4], w2[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      __nv_bfloat162 p0, p1, p2;
-      float r[2][3];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const float v = x[2 * q + h];
-        const float c0 = __bfloat162float(__float2bfloat16_rn(v));
-        const float c1 = __bfloat162float(__float2bfloat16_rn(v - c0));
-        const float c2 = __bfloat162float(__float2bfloat16_rn((v - c0) - c1));
-        r[h][0] = c0; r[h][1] = c1; r[h][2] = c2;
-      }
-      p0 = __floats2bfloat162_rn(r[0][0], r[1][0]);
-      p1 = __floats2bfloat162_rn(r[0][1], r[1][1]);
-      p2 = __floats2bfloat162_rn(r[0][2], r[1][2]);
-      w0[q] = *reinterpret_cast<unsigned*>(&p0);
-      w1[q] = *reinterpret_cast<unsigned*>(&p1);
-      w2[q] = *reinterpret_cast<unsigned*>(&p2);
+// Two fp32 values -> their three bf16 parts, packed in pairs (value a in the low half). The
+// remainders v - b0 and (v - b0) - b1 are exact in fp32.
+__device__ __forceinline__ void split3_pair(float a, float b, uint32_t& w0, uint32_t& w1,
+                                            uint32_t& w2) {
+  const __nv_bfloat162 p0 = __floats2bfloat162_rn(a, b);
+  const float2 f0 = __bfloat1622float2(p0);
+  const float ra = a - f0.x, rb = b - f0.y;
+  const __nv_bfloat162 p1 = __floats2bfloat162_rn(ra, rb);
+  const float2 f1 = __bfloat1622float2(p1);
+  const __nv_bfloat162 p2 = __floats2bfloat162_rn(ra - f1.x, rb - f1.y);
+  w0 = *reinterpret_cast<const uint32_t*>(&p0);
+  w1 = *reinterpret_cast<const uint32_t*>(&p1);
+  w2 = *reinterpret_cast<const uint32_t*>(&p2);
+}
+
+// One 16-byte group of 8 channels: the fp32 groups lo (channels 0-3) and hi (4-7) -> the three
+// bf16 images at element index u.
+__device__ __forceinline__ void split3_group(const float4 lo, const float4 hi, uint4* b0, uint4* b1,
+                                             uint4* b2, int u) {
+  uint4 o0, o1, o2;
+  split3_pair(lo.x, lo.y, o0.x, o1.x, o2.x);
+  split3_pair(lo.z, lo.w, o0.y, o1.y, o2.y);
+  split3_pair(hi.x, hi.y, o0.z, o1.z, o2.z);
+  split3_pair(hi.z, hi.w, o0.w, o1.w, o2.w);
+  b0[u] = o0;
+  b1[u] = o1;
+  b2[u] = o2;
+}
+
+// Splits one stage. Delta tile: raw [32 g4][16 px], parts [16 g8][16 px]. x tile: raw
+// [C/4][R][18 px], parts [C/8][R][18 px]. Each quarter-warp takes 8 consecutive pixels of one
+// row, so its eight 16-byte reads fall in distinct bank groups; the 2 halo pixels of each row
+// follow in a short second pass.
+template <int R>
+__device__ __forceinline__ void split3_stage(const uint8_t* st, uint8_t* stw, const W3Layout& L,
+                                             int g8n, int et) {
+  constexpr int kThr = 32 * kW3SplitWarps;
+  constexpr int PR = kW3KP + 2;
+  {
+    const float4* raw = reinterpret_cast<const float4*>(st + L.rawA);
+    for (int u = et; u < 16 * kW3KP; u += kThr) {
+      const int g8 = u / kW3KP, px = u % kW3KP;
+      split3_group(raw[(2 * g8) * kW3KP + px], raw[(2 * g8 + 1) * kW3KP + px],
+                   reinterpret_cast<uint4*>(stw + L.a[0]), reinterpret_cast<uint4*>(stw + L.a[1]),
+                   reinterpret_cast<uint4*>(stw + L.a[2]), u);
     }
-    b0[u] = make_uint4(w0[0], w0[1], w0[2], w0[3]);
-    b1[u] = make_uint4(w1[0], w1[1], w1[2], w1[3]);
-    b2[u] = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+  }
+  const float4* raw = reinterpret_cast<const float4*>(st + L.rawB);
+  uint4* b0 = reinterpret_cast<uint4*>(stw + L.b[0]);
+  uint4* b1 = reinterpret_cast<uint4*>(stw + L.b[1]);
+  uint4* b2 = reinterpret_cast<uint4*>(stw + L.b[2]);
+  const int nmain = g8n * R * kW3KP;
+  for (int u = et; u < nmain; u += kThr) {
+    const int q = u / kW3KP, px = u % kW3KP;  // q = g8 * R + r
+    const int g8 = q / R, r = q - g8 * R;
+    split3_group(raw[((2 * g8) * R + r) * PR + px], raw[((2 * g8 + 1) * R + r) * PR + px], b0, b1,
+                 b2, q * PR + px);
+  }
+  for (int u = et; u < g8n * R * 2; u += kThr) {
+    const int q = u >> 1, px = kW3KP + (u & 1);
+    const int g8 = q / R, r = q - g8 * R;
+    split3_group(raw[((2 * g8) * R + r) * PR + px], raw[((2 * g8 + 1) * R + r) * PR + px], b0, b1,
+                 b2, q * PR + px);
   }
 }
 
-__global__ void __launch_bounds__(192, 1) k_wgrad_tc_f32(const __grid_constant__ CUtensorMap tmD,
-                                                        const __grid_constant__ CUtensorMap tmX,
-                                                        WgBf16Params p) {
+template <int R>
+__global__ void __launch_bounds__(kW3Threads, 1) k_wgrad_tc_f32(const __grid_constant__ CUtensorMap tmD,
+                                                               const __grid_constant__ CUtensorMap tmX,
+                                                               WgBf16Params p) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  __shared__ uint64_t full[kW3Stages], empty[kW3Stages], split[kW3Stages], accf;
+  __shared__ uint64_t full[kW3MaxStages], empty[kW3MaxStages], split[kW3MaxStages], accf;
   __shared__ uint32_t tslot;
   __shared__ int abort_flag;
   if (p.skip && *p.skip) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int o0 = blockIdx.x * 128, grp = blockIdx.y, s_idx = blockIdx.z;
-  const int t0 = p.tg.first[grp], nt = p.tg.count[grp], r0 = p.tg.row0[grp], R = p.tg.R;
+  const int t0 = p.tg.first[grp], nt = p.tg.count[grp], r0 = p.tg.row0[grp];
+  const int ns = p.stages;
   const int cbeg = s_idx * p.per_split;
   const int cend = min(p.total_chunks, cbeg + p.per_split);
   const int nk = cend > cbeg ? cend - cbeg : 0;
@@ -617,10 +655,10 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc_f32(const __grid_constant__
   const uint32_t ncols = tmem_cols(nt * p.cin);
   volatile int* abort = &abort_flag;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kW3Stages; ++s) {
+    for (int s = 0; s < ns; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
-      mbar_init(&split[s], 128);
+      mbar_init(&split[s], kW3SplitWarps);
     }
     mbar_init(&accf, 1);
     abort_flag = 0;
@@ -636,9 +674,8 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc_f32(const __grid_constant__
     if (lane == 0) {
       int issued = 0;
       for (int i = 0; i < nk; ++i) {
-        const int s = i % kW3Stages;
-        if (i >= kW3Stages && !mbar_wait(&empty[s], ((i / kW3Stages) - 1) & 1, abort, p.err))
-          break;
+        const int s = i % ns;
+        if (i >= ns && !mbar_wait(&empty[s], ((i / ns) - 1) & 1, abort, p.err)) break;
         const int ch = cbeg + i;
         const int y = ch / p.chunks_x, x0 = (ch % p.chunks_x) * kW3KP;
         uint8_t* st = smem + s * L.stage;
@@ -648,8 +685,8 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc_f32(const __grid_constant__
         issued = i + 1;
       }
       if (*abort)
-        for (int i = issued > kW3Stages ? issued - kW3Stages : 0; i < issued; ++i)
-          mbar_drain(&full[i % kW3Stages], (i / kW3Stages) & 1);
+        for (int i = issued > ns ? issued - ns : 0; i < issued; ++i)
+          mbar_drain(&full[i % ns], (i / ns) & 1);
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -657,8 +694,8 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc_f32(const __grid_constant__
       const uint32_t a_sbo = kW3KP * 16;                     // next 8-channel group of delta
       const uint32_t b_sbo = (uint32_t)R * (kW3KP + 2) * 16;  // next 8-channel group of x
       for (int i = 0; i < nk; ++i) {
-        const int s = i % kW3Stages;
-        if (!mbar_wait(&split[s], (i / kW3Stages) & 1, abort, p.err)) break;
+        const int s = i % ns;
+        if (!mbar_wait(&split[s], (i / ns) & 1, abort, p.err)) break;
         tc_fence_after();
         const uint32_t st = smem_u32(smem + s * L.stage);
         uint64_t da[3];
@@ -685,27 +722,25 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc_f32(const __grid_constant__
   } else {
     const int et = threadIdx.x - 64;
     for (int i = 0; i < nk; ++i) {
-      const int s = i % kW3Stages;
-      if (!mbar_wait(&full[s], (i / kW3Stages) & 1, abort, p.err)) break;
+      const int s = i % ns;
+      if (!mbar_wait(&full[s], (i / ns) & 1, abort, p.err)) break;
       uint8_t* st = smem + s * L.stage;
-      split3_bf16(reinterpret_cast<const float4*>(st + L.rawA), reinterpret_cast<uint4*>(st + L.a[0]),
-                  reinterpret_cast<uint4*>(st + L.a[1]), reinterpret_cast<uint4*>(st + L.a[2]), 16,
-                  kW3KP, et);
-      split3_bf16(reinterpret_cast<const float4*>(st + L.rawB), reinterpret_cast<uint4*>(st + L.b[0]),
-                  reinterpret_cast<uint4*>(st + L.b[1]), reinterpret_cast<uint4*>(st + L.b[2]),
-                  p.cin / 8, R * (kW3KP + 2), et);
+      split3_stage<R>(st, st, L, p.cin / 8, et);
       fence_proxy_async();
-      mbar_arrive(&split[s]);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&split[s]);
     }
     if (!mbar_wait(&accf, 0, abort, p.err)) mbar_drain(&accf, 0);
     tc_fence_after();
-    const int wq = warp & 3;
+    // warps 2..9: TMEM lane quarter warp % 4, column half (warp - 2) / 4 (16-column blocks
+    // alternate between the two halves)
+    const int wq = warp & 3, half = (warp - 2) >> 2;
     const int o = o0 + wq * 32 + lane;
     const bool live = o < p.cout && !*abort;
     for (int j = 0; j < nt; ++j) {
       const int tap = t0 + j;
       float* dst = p.part + (((size_t)s_idx * 9 + tap) * p.cout + (live ? o : 0)) * p.cin;
-      for (int c0 = 0; c0 < p.cin; c0 += 16) {
+      for (int c0 = 16 * half; c0 < p.cin; c0 += 32) {
         uint32_t r[16];
         tmem_ld16(tbase + ((uint32_t)(wq * 32) << 16) + (uint32_t)(j * p.cin + c0), r);
         tmem_ld_wait();
@@ -855,7 +890,8 @@ cudaError_t tc_prepare() {
     set((const void*)k_conv_tc<0, 0>);
     set((const void*)k_conv_tc<0, 1>);
     set((const void*)k_wgrad_tc_bf16);
-    set((const void*)k_wgrad_tc_f32);
+    set((const void*)k_wgrad_tc_f32<1>);
+    set((const void*)k_wgrad_tc_f32<3>);
     result = e;
   });
   return result;
@@ -940,11 +976,21 @@ static cudaError_t launch_wgrad_grouped(int bf16, const void* dout, const void* 
   p.total_chunks = p.chunks_x * H;
   p.tg = tg;
   const size_t per_split_elems = (size_t)9 * cout * cin;
-  uint32_t smem = bf16 ? kWbStages * wb_stage(cin, tg.R) : kW3Stages * w3_layout(cin, tg.R).stage;
   int maxcols = 0;
   for (int g = 0; g < tg.n; ++g) maxcols = tg.count[g] * cin > maxcols ? tg.count[g] * cin : maxcols;
+  const int max_res = 512 / (int)tmem_cols(maxcols);  // CTAs per SM that TMEM allows
+  uint32_t smem;
+  if (bf16) {
+    smem = kWbStages * wb_stage(cin, tg.R);
+    p.stages = kWbStages;
+  } else {
+    // a fourth stage where it costs no resident CTA
+    const uint32_t sb = w3_layout(cin, tg.R).stage;
+    p.stages = (uint32_t)max_res * (4 * sb + 2048u) <= 227u * 1024u ? 4 : 3;
+    smem = (uint32_t)p.stages * sb;
+  }
   // a CTA holding more than half of TMEM keeps the SM to itself
-  if (tmem_cols(maxcols) > 256 && smem < 116u * 1024u) smem = 116u * 1024u;
+  if (max_res == 1 && smem < 116u * 1024u) smem = 116u * 1024u;
   const int per_sm = (int)((227u * 1024u) / (smem + 2048u));
   const int ctas = otiles * tg.n;
   int S = (2 * 152 * (per_sm > 0 ? per_sm : 1)) / ctas;
@@ -963,8 +1009,10 @@ static cudaError_t launch_wgrad_grouped(int bf16, const void* dout, const void* 
   const dim3 grid((unsigned)otiles, (unsigned)tg.n, (unsigned)S);
   if (bf16)
     k_wgrad_tc_bf16<<<grid, 192, smem, st>>>(md, mx, p);
+  else if (tg.R == 1)
+    k_wgrad_tc_f32<1><<<grid, kW3Threads, smem, st>>>(md, mx, p);
   else
-    k_wgrad_tc_f32<<<grid, 192, smem, st>>>(md, mx, p);
+    k_wgrad_tc_f32<3><<<grid, kW3Threads, smem, st>>>(md, mx, p);
   count_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_reduce_wgrad_tc<<<(unsigned)((per_split_elems + 31) / 32), 256, 0, st>>>(part, S, cin, cout,
