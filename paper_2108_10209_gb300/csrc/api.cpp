@@ -559,9 +559,8 @@ static bool progress(n2f_ctx* c, Job* j) {
     }
     const uint32_t la = std::max<uint32_t>(1, c->cfg.lookahead);
     while (!j->finishing && j->ep_enq - j->ep_seen < la) {
-      // epochs replay a captured graph unless a kernel class is being timed per launch
-      if ((rc = j->tr.kt || !c->cfg.use_graphs ? trainer_epoch(&j->tr)
-                                              : trainer_epoch_graph(&j->tr)))
+      // epochs replay a captured graph (timed launches keep event-record nodes in it)
+      if ((rc = !c->cfg.use_graphs ? trainer_epoch(&j->tr) : trainer_epoch_graph(&j->tr)))
         break;
       const int slot = (int)(j->ep_enq % j->ring);
       cudaError_t e = cudaMemcpyAsync(&j->hst[slot], j->tr.state, sizeof(DevState),

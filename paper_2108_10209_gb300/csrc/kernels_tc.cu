@@ -62,16 +62,21 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// A channel-grouped map act[g][y][x][GE] seen as a 4-D tensor (GE, W, H, C/GE), innermost
-// first, with a box of (GE, bx, by, bg) elements. Outside the tensor the box reads zeros.
+// A channel-grouped map act[g][y][x][GE] seen as a 4-D tensor (GE * pu, W / pu, H, C / GE),
+// innermost first: `pu` consecutive pixels form one unit, so a box row is pu * 16 bytes (TMA
+// moves whole 32-byte sectors: 16-byte rows would fetch every sector twice). The box is
+// (GE * pu, bx units, by rows, bg groups); outside the tensor it reads zeros. W must be a
+// multiple of pu.
 cudaError_t make_map(CUtensorMap* m, const void* base, int bf16, int C, int H, int W, int bx,
-                     int by, int bg) {
+                     int by, int bg, int pu = 1) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return cudaErrorNotSupported;
+  if (pu < 1 || W % pu) return cudaErrorInvalidValue;
   const int GE = bf16 ? 8 : 4;
-  cuuint64_t dims[4] = {(cuuint64_t)GE, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)(C / GE)};
-  cuuint64_t strides[3] = {16, (cuuint64_t)W * 16, (cuuint64_t)H * W * 16};
-  cuuint32_t box[4] = {(cuuint32_t)GE, (cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bg};
+  cuuint64_t dims[4] = {(cuuint64_t)(GE * pu), (cuuint64_t)(W / pu), (cuuint64_t)H,
+                        (cuuint64_t)(C / GE)};
+  cuuint64_t strides[3] = {(cuuint64_t)pu * 16, (cuuint64_t)W * 16, (cuuint64_t)H * W * 16};
+  cuuint32_t box[4] = {(cuuint32_t)(GE * pu), (cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bg};
   cuuint32_t es[4] = {1, 1, 1, 1};
   CUresult r = fn(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
                   const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -416,6 +421,7 @@ struct WgBf16Params {
   float* part;  // [S][9][C_out][C_in]
   int cin, cout, H, W, chunks_x, total_chunks, per_split;
   int stages;  // pipeline stages (float32 kernel)
+  int pu;      // pixels per TMA unit of both maps
   TapGroups tg;
   const int* skip;
   int* err;
@@ -425,11 +431,13 @@ constexpr int kWbKP = 64;       // pixels per stage
 constexpr int kWbStages = 3;
 constexpr uint32_t kWbA = 128u * kWbKP * 2;  // delta tile, 128 channels (zero-filled past C_out)
 
-__host__ __device__ inline uint32_t wb_b_bytes(int cin, int R) {
-  return (uint32_t)(cin / 8) * R * (kWbKP + 2) * 16;
+// x halo pitch: the chunk's KP pixels plus one TMA unit of pu pixels on each side
+__host__ __device__ inline int wb_pitch(int pu) { return kWbKP + 2 * pu; }
+__host__ __device__ inline uint32_t wb_b_bytes(int cin, int R, int pu) {
+  return (uint32_t)(cin / 8) * R * wb_pitch(pu) * 16;
 }
-__host__ __device__ inline uint32_t wb_stage(int cin, int R) {
-  return align_up(kWbA, 1024) + align_up(wb_b_bytes(cin, R), 1024);
+__host__ __device__ inline uint32_t wb_stage(int cin, int R, int pu) {
+  return align_up(kWbA, 1024) + align_up(wb_b_bytes(cin, R, pu), 1024);
 }
 
 __global__ void __launch_bounds__(192, 1) k_wgrad_tc_bf16(const __grid_constant__ CUtensorMap tmD,
@@ -446,7 +454,8 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc_bf16(const __grid_constant_
   const int cbeg = s_idx * p.per_split;
   const int cend = min(p.total_chunks, cbeg + p.per_split);
   const int nk = cend > cbeg ? cend - cbeg : 0;
-  const uint32_t BB = wb_b_bytes(p.cin, R), SB = wb_stage(p.cin, R);
+  const int pu = p.pu, HX = wb_pitch(pu);
+  const uint32_t BB = wb_b_bytes(p.cin, R, pu), SB = wb_stage(p.cin, R, pu);
   const uint32_t b_off = align_up(kWbA, 1024);
   const uint32_t ncols = tmem_cols(nt * p.cin);
   volatile int* abort = &abort_flag;
@@ -476,8 +485,8 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc_bf16(const __grid_constant_
         const int y = ch / p.chunks_x, x0 = (ch % p.chunks_x) * kWbKP;
         uint8_t* st = smem + s * SB;
         mbar_expect_tx(&full[s], kWbA + BB);
-        tma_load_4d(st, &tmD, &full[s], 0, x0, y, o0 / 8);
-        tma_load_4d(st + b_off, &tmX, &full[s], 0, x0 - 1, y + r0 - 1, 0);
+        tma_load_4d(st, &tmD, &full[s], 0, x0 / pu, y, o0 / 8);
+        tma_load_4d(st + b_off, &tmX, &full[s], 0, x0 / pu - 1, y + r0 - 1, 0);
         issued = i + 1;
       }
       if (*abort)
@@ -488,7 +497,7 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc_bf16(const __grid_constant_
     if (lane == 0) {
       const uint32_t id = idesc(1, 128, p.cin, 1, 1);
       const uint32_t a_sbo = kWbKP * 16;                    // next 8-channel group of delta
-      const uint32_t b_sbo = (uint32_t)R * (kWbKP + 2) * 16;  // next 8-channel group of x
+      const uint32_t b_sbo = (uint32_t)R * HX * 16;  // next 8-channel group of x
       for (int i = 0; i < nk; ++i) {
         const int s = i % kWbStages;
         if (!mbar_wait(&full[s], (i / kWbStages) & 1, abort, p.err)) break;
@@ -496,7 +505,8 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc_bf16(const __grid_constant_
         const uint32_t sa = smem_u32(smem + s * SB), sb = sa + b_off;
         for (int j = 0; j < nt; ++j) {
           const int tap = t0 + j;
-          const uint32_t boff = (uint32_t)(((tap / 3) - r0) * (kWbKP + 2) + (tap % 3)) * 16u;
+          // pixel p of the chunk, tap column dx, sits at halo column p + dx - 1 + pu
+          const uint32_t boff = (uint32_t)(((tap / 3) - r0) * HX + (tap % 3) + pu - 1) * 16u;
 #pragma unroll
           for (int k = 0; k < kWbKP / 16; ++k) {
             const uint32_t ko = (uint32_t)k * 16u * 16u;
@@ -553,10 +563,13 @@ struct W3Layout {
   uint32_t rawA, rawB, a[3], b[3], stage;
 };
 
-__host__ __device__ inline W3Layout w3_layout(int cin, int R) {
+// raw x tile pitch: the 16 chunk pixels plus one TMA unit of pu pixels on each side
+__host__ __device__ inline int w3_raw_pitch(int pu) { return kW3KP + 2 * pu; }
+
+__host__ __device__ inline W3Layout w3_layout(int cin, int R, int pu) {
   W3Layout L;
   const uint32_t ra = 128u * kW3KP * 4;                         // [32 g4][16 px][16 B]
-  const uint32_t rb = (uint32_t)cin * R * (kW3KP + 2) * 4;     // [C/4][R][18 px][16 B]
+  const uint32_t rb = (uint32_t)cin * R * w3_raw_pitch(pu) * 4;  // [C/4][R][16 + 2 pu][16 B]
   const uint32_t pa = 128u * kW3KP * 2;                         // [16 g8][16 px][16 B]
   const uint32_t pb = (uint32_t)cin * R * (kW3KP + 2) * 2;     // [C/8][R][18 px][16 B]
   uint32_t o = 0;
@@ -598,14 +611,15 @@ __device__ __forceinline__ void split3_group(const float4 lo, const float4 hi, u
 }
 
 // Splits one stage. Delta tile: raw [32 g4][16 px], parts [16 g8][16 px]. x tile: raw
-// [C/4][R][18 px], parts [C/8][R][18 px]. Each quarter-warp takes 8 consecutive pixels of one
-// row, so its eight 16-byte reads fall in distinct bank groups; the 2 halo pixels of each row
-// follow in a short second pass.
+// [C/4][R][16 + 2 pu px], parts [C/8][R][18 px] (raw column pu - 1 + i -> part column i). Each
+// quarter-warp takes 8 consecutive pixels of one row, so its eight 16-byte reads fall in
+// distinct bank groups; the 2 halo pixels of each row follow in a short second pass.
 template <int R>
 __device__ __forceinline__ void split3_stage(const uint8_t* st, uint8_t* stw, const W3Layout& L,
-                                             int g8n, int et) {
+                                             int g8n, int pu, int et) {
   constexpr int kThr = 32 * kW3SplitWarps;
-  constexpr int PR = kW3KP + 2;
+  constexpr int PP = kW3KP + 2;  // part pitch
+  const int PR = w3_raw_pitch(pu);
   {
     const float4* raw = reinterpret_cast<const float4*>(st + L.rawA);
     for (int u = et; u < 16 * kW3KP; u += kThr) {
@@ -621,16 +635,16 @@ __device__ __forceinline__ void split3_stage(const uint8_t* st, uint8_t* stw, co
   uint4* b2 = reinterpret_cast<uint4*>(stw + L.b[2]);
   const int nmain = g8n * R * kW3KP;
   for (int u = et; u < nmain; u += kThr) {
-    const int q = u / kW3KP, px = u % kW3KP;  // q = g8 * R + r
-    const int g8 = q / R, r = q - g8 * R;
+    const int q = u / kW3KP, i = 1 + u % kW3KP;  // q = g8 * R + r, part column i
+    const int g8 = q / R, r = q - g8 * R, px = pu - 1 + i;
     split3_group(raw[((2 * g8) * R + r) * PR + px], raw[((2 * g8 + 1) * R + r) * PR + px], b0, b1,
-                 b2, q * PR + px);
+                 b2, q * PP + i);
   }
   for (int u = et; u < g8n * R * 2; u += kThr) {
-    const int q = u >> 1, px = kW3KP + (u & 1);
-    const int g8 = q / R, r = q - g8 * R;
+    const int q = u >> 1, i = (u & 1) ? PP - 1 : 0;
+    const int g8 = q / R, r = q - g8 * R, px = pu - 1 + i;
     split3_group(raw[((2 * g8) * R + r) * PR + px], raw[((2 * g8 + 1) * R + r) * PR + px], b0, b1,
-                 b2, q * PR + px);
+                 b2, q * PP + i);
   }
 }
 
@@ -650,8 +664,9 @@ __global__ void __launch_bounds__(kW3Threads, 1) k_wgrad_tc_f32(const __grid_con
   const int cbeg = s_idx * p.per_split;
   const int cend = min(p.total_chunks, cbeg + p.per_split);
   const int nk = cend > cbeg ? cend - cbeg : 0;
-  const W3Layout L = w3_layout(p.cin, R);
-  const uint32_t RB = (uint32_t)p.cin * R * (kW3KP + 2) * 4;
+  const int pu = p.pu;
+  const W3Layout L = w3_layout(p.cin, R, pu);
+  const uint32_t RB = (uint32_t)p.cin * R * w3_raw_pitch(pu) * 4;
   const uint32_t ncols = tmem_cols(nt * p.cin);
   volatile int* abort = &abort_flag;
   if (threadIdx.x == 0) {
@@ -680,8 +695,8 @@ __global__ void __launch_bounds__(kW3Threads, 1) k_wgrad_tc_f32(const __grid_con
         const int y = ch / p.chunks_x, x0 = (ch % p.chunks_x) * kW3KP;
         uint8_t* st = smem + s * L.stage;
         mbar_expect_tx(&full[s], 128u * kW3KP * 4 + RB);
-        tma_load_4d(st + L.rawA, &tmD, &full[s], 0, x0, y, o0 / 4);
-        tma_load_4d(st + L.rawB, &tmX, &full[s], 0, x0 - 1, y + r0 - 1, 0);
+        tma_load_4d(st + L.rawA, &tmD, &full[s], 0, x0 / pu, y, o0 / 4);
+        tma_load_4d(st + L.rawB, &tmX, &full[s], 0, x0 / pu - 1, y + r0 - 1, 0);
         issued = i + 1;
       }
       if (*abort)
@@ -725,7 +740,7 @@ __global__ void __launch_bounds__(kW3Threads, 1) k_wgrad_tc_f32(const __grid_con
       const int s = i % ns;
       if (!mbar_wait(&full[s], (i / ns) & 1, abort, p.err)) break;
       uint8_t* st = smem + s * L.stage;
-      split3_stage<R>(st, st, L, p.cin / 8, et);
+      split3_stage<R>(st, st, L, p.cin / 8, pu, et);
       fence_proxy_async();
       __syncwarp();
       if (lane == 0) mbar_arrive(&split[s]);
@@ -962,9 +977,14 @@ static cudaError_t launch_wgrad_grouped(int bf16, const void* dout, const void* 
                                         cudaStream_t st) {
   const TapGroups tg = tap_groups(cin);
   const int KP = bf16 ? kWbKP : kW3KP, GE = bf16 ? 8 : 4;
+  // pixels per TMA unit: 128-byte box rows for bf16 (the halo grows by 14 pixels of 66),
+  // 64-byte rows for float32 (the raw tile of 16 pixels would grow too much with 8)
+  const int pu_max = bf16 ? 8 : 4;
+  int pu = 1;
+  while (pu < pu_max && W % (2 * pu) == 0) pu *= 2;
   CUtensorMap md, mx;
-  cudaError_t e = make_map(&md, dout, bf16, cout, H, W, KP, 1, 128 / GE);
-  if (e == cudaSuccess) e = make_map(&mx, in, bf16, cin, H, W, KP + 2, tg.R, cin / GE);
+  cudaError_t e = make_map(&md, dout, bf16, cout, H, W, KP / pu, 1, 128 / GE, pu);
+  if (e == cudaSuccess) e = make_map(&mx, in, bf16, cin, H, W, KP / pu + 2, tg.R, cin / GE, pu);
   if (e != cudaSuccess) return e;
   const int otiles = (cout + 127) / 128;
   WgBf16Params p;
@@ -975,17 +995,18 @@ static cudaError_t launch_wgrad_grouped(int bf16, const void* dout, const void* 
   p.chunks_x = (W + KP - 1) / KP;
   p.total_chunks = p.chunks_x * H;
   p.tg = tg;
+  p.pu = pu;
   const size_t per_split_elems = (size_t)9 * cout * cin;
   int maxcols = 0;
   for (int g = 0; g < tg.n; ++g) maxcols = tg.count[g] * cin > maxcols ? tg.count[g] * cin : maxcols;
   const int max_res = 512 / (int)tmem_cols(maxcols);  // CTAs per SM that TMEM allows
   uint32_t smem;
   if (bf16) {
-    smem = kWbStages * wb_stage(cin, tg.R);
+    smem = kWbStages * wb_stage(cin, tg.R, pu);
     p.stages = kWbStages;
   } else {
     // a fourth stage where it costs no resident CTA
-    const uint32_t sb = w3_layout(cin, tg.R).stage;
+    const uint32_t sb = w3_layout(cin, tg.R, pu).stage;
     p.stages = (uint32_t)max_res * (4 * sb + 2048u) <= 227u * 1024u ? 4 : 3;
     smem = (uint32_t)p.stages * sb;
   }

@@ -95,28 +95,46 @@ void KTimer::destroy() {
 namespace {
 
 // Brackets one launch of kernel class `kind` with events when the trainer times that class.
+// While an epoch is being captured the events become event-record nodes of the graph.
 struct Timed {
+  Trainer* t = nullptr;
   KTimer* kt = nullptr;
   cudaStream_t st;
   KTimer::Pair p;
-  Timed(Trainer* t, int kind, double flops, double bytes, int val) : st(t->st) {
-    if (!t->kt) return;
-    const bool conv = t->kt->kind == N2F_K_CONV && (kind == N2F_K_CONV_FWD || kind == N2F_K_CONV_DGRAD);
-    if (t->kt->kind != kind && !conv) return;
-    kt = t->kt;
+  Timed(Trainer* tr, int kind, double flops, double bytes, int val) : st(tr->st) {
+    if (!tr->kt) return;
+    const bool conv = tr->kt->kind == N2F_K_CONV && (kind == N2F_K_CONV_FWD || kind == N2F_K_CONV_DGRAD);
+    if (tr->kt->kind != kind && !conv) return;
+    t = tr;
+    kt = tr->kt;
     p.a = kt->get();
     p.b = nullptr;
     p.flops = flops;
     p.bytes = bytes;
     p.val = val;
     p.seq = val ? t->vals_enqueued : t->steps_enqueued;
-    cudaEventRecord(p.a, st);
+    if (t->capturing)
+      cudaEventRecordWithFlags(p.a, st, cudaEventRecordExternal);
+    else
+      cudaEventRecord(p.a, st);
   }
   ~Timed() {
     if (!kt) return;
     p.b = kt->get();
-    cudaEventRecord(p.b, st);
-    kt->pending.push_back(p);
+    if (t->capturing) {
+      cudaEventRecordWithFlags(p.b, st, cudaEventRecordExternal);
+      Trainer::TimedNode n;
+      n.a = p.a;
+      n.b = p.b;
+      n.flops = p.flops;
+      n.bytes = p.bytes;
+      n.val = p.val;
+      n.k = (int)(p.seq - (p.val ? t->cap_vals0 : t->cap_steps0));
+      t->tnodes.push_back(n);
+    } else {
+      cudaEventRecord(p.b, st);
+      kt->pending.push_back(p);
+    }
   }
 };
 
@@ -274,6 +292,15 @@ int trainer_init(Trainer* t, const Allocator& al, cudaStream_t st, int want_u16)
 void trainer_release(Trainer* t) {
   if (t->epoch_exec) cudaGraphExecDestroy(t->epoch_exec);
   t->epoch_exec = nullptr;
+  if (t->epoch_graph) cudaGraphDestroy(t->epoch_graph);
+  t->epoch_graph = nullptr;
+  for (Trainer::TimedNode& n : t->tnodes) {
+    if (t->kt) {
+      t->kt->pool.push_back(n.a);
+      t->kt->pool.push_back(n.b);
+    }
+  }
+  t->tnodes.clear();
   if (t->slab) dev_free(t->al, t->slab, t->slab_bytes);
   t->slab = nullptr;
 }
@@ -446,28 +473,85 @@ int trainer_epoch(Trainer* t) {
   return trainer_validate(t);
 }
 
+namespace {
+
+// Finds the event-record nodes of the captured epoch that belong to timed launches.
+int bind_timed_nodes(Trainer* t, cudaGraph_t g) {
+  if (t->tnodes.empty()) return N2F_OK;
+  size_t n = 0;
+  CK(cudaGraphGetNodes(g, nullptr, &n));
+  std::vector<cudaGraphNode_t> nodes(n);
+  CK(cudaGraphGetNodes(g, nodes.data(), &n));
+  for (cudaGraphNode_t nd : nodes) {
+    cudaGraphNodeType ty;
+    CK(cudaGraphNodeGetType(nd, &ty));
+    if (ty != cudaGraphNodeTypeEventRecord) continue;
+    cudaEvent_t ev = nullptr;
+    CK(cudaGraphEventRecordNodeGetEvent(nd, &ev));
+    for (Trainer::TimedNode& tn : t->tnodes) {
+      if (tn.a == ev) tn.na = nd;
+      if (tn.b == ev) tn.nb = nd;
+    }
+  }
+  for (const Trainer::TimedNode& tn : t->tnodes)
+    if (!tn.na || !tn.nb) return set_cuda_error(cudaErrorInvalidValue, "timed graph nodes");
+  return N2F_OK;
+}
+
+}  // namespace
+
 int trainer_epoch_graph(Trainer* t) {
   if (!t->epoch_exec) {
     uint64_t counted = 0;
     cudaGraph_t g = nullptr;
     {
       LaunchScope ls(&counted);
-      CK(cudaStreamBeginCapture(t->st, cudaStreamCaptureModeThreadLocal));
+      t->tnodes.clear();
+      t->cap_steps0 = t->steps_enqueued;
+      t->cap_vals0 = t->vals_enqueued;
+      t->capturing = true;
+      cudaError_t e = cudaStreamBeginCapture(t->st, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) {
+        t->capturing = false;
+        return set_cuda_error(e, "epoch graph capture");
+      }
       const int rc = trainer_epoch(t);
-      const cudaError_t e = cudaStreamEndCapture(t->st, &g);
+      e = cudaStreamEndCapture(t->st, &g);
+      t->capturing = false;
       if (rc) {
         if (g) cudaGraphDestroy(g);
         return rc;
       }
       if (e != cudaSuccess) return set_cuda_error(e, "epoch graph capture");
     }
+    int rc = bind_timed_nodes(t, g);
+    if (rc) {
+      cudaGraphDestroy(g);
+      return rc;
+    }
     const cudaError_t e = cudaGraphInstantiate(&t->epoch_exec, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) return set_cuda_error(e, "epoch graph instantiate");
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return set_cuda_error(e, "epoch graph instantiate");
+    }
+    t->epoch_graph = g;  // kept: the timed nodes are addressed through it
     t->epoch_kernels = counted;
     // the captured calls advanced the enqueue counters once; the launch below is the epoch
     t->steps_enqueued -= 4;
     t->vals_enqueued -= 1;
+  }
+  // every replay records into its own events, harvested when the job's steps are known
+  for (const Trainer::TimedNode& tn : t->tnodes) {
+    KTimer::Pair p;
+    p.a = t->kt->get();
+    p.b = t->kt->get();
+    p.flops = tn.flops;
+    p.bytes = tn.bytes;
+    p.val = tn.val;
+    p.seq = tn.val ? t->vals_enqueued + tn.k : t->steps_enqueued + tn.k;
+    CK(cudaGraphExecEventRecordNodeSetEvent(t->epoch_exec, tn.na, p.a));
+    CK(cudaGraphExecEventRecordNodeSetEvent(t->epoch_exec, tn.nb, p.b));
+    t->kt->pending.push_back(p);
   }
   CK(cudaGraphLaunch(t->epoch_exec, t->st));
   t->steps_enqueued += 4;

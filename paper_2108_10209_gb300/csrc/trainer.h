@@ -89,8 +89,21 @@ struct Trainer {
   uint64_t steps_enqueued = 0, vals_enqueued = 0;
   KTimer* kt = nullptr;  // optional kernel-class timer (owned by the caller)
   // one epoch captured as a CUDA graph (everything it mutates lives in device memory)
+  cudaGraph_t epoch_graph = nullptr;
   cudaGraphExec_t epoch_exec = nullptr;
   uint64_t epoch_kernels = 0;  // kernels in one captured epoch
+  // Timed launches inside the captured epoch: their event-record nodes get fresh events before
+  // every replay, so a profiled job still replays graphs. `k` is the step within the epoch
+  // (or 0 for the validation), `a`/`b` the nodes' events while capturing.
+  struct TimedNode {
+    cudaGraphNode_t na = nullptr, nb = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    double flops = 0, bytes = 0;
+    int val = 0, k = 0;
+  };
+  bool capturing = false;
+  uint64_t cap_steps0 = 0, cap_vals0 = 0;
+  std::vector<TimedNode> tnodes;
 };
 
 int trainer_configure(Trainer* t, int H, int W, const n2f_params* p, int keep_deltas);

@@ -143,6 +143,27 @@ def test_graph_replay_matches_launch_by_launch(n2f):
     assert np.array_equal(outs[0][0], outs[1][0])
 
 
+def test_profiled_graph_replay(n2f):
+    # A job that times a kernel class per launch still replays its epoch graph: the graph's
+    # event-record nodes get fresh events before each replay. Results are identical to the
+    # unprofiled job, and the launch count and FLOP total equal those of launch-by-launch timing.
+    _, x = _img(48, 40, 33)
+    p = n2f.params(seed=4, patience=4)
+    ref = n2f.denoise(x, p)
+    got = {}
+    for kind in (n2f.N2F_K_CONV, n2f.N2F_K_CONV_WGRAD):
+        for graphs in (False, True):
+            with n2f.Context(profile_kernel=kind, use_graphs=graphs) as ctx:
+                j = ctx.submit(x, p)
+                ctx.wait(j)
+                out = ctx.result(j, x.shape)
+                st = ctx.stats()
+            assert np.array_equal(out, ref)
+            assert st["prof_launches"] > 0 and st["prof_ms"] > 0
+            got[(kind, graphs)] = (st["prof_launches"], st["prof_flops"])
+        assert got[(kind, False)] == got[(kind, True)]
+
+
 def test_admission_by_hbm_budget(n2f):
     # The budget admits jobs first-in first-out while their device state fits; a job that can
     # never fit is refused at submission.
