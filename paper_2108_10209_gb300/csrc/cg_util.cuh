@@ -42,6 +42,24 @@ __device__ __forceinline__ void load_group<__nv_bfloat16>(const __nv_bfloat16* b
     v[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
   }
 }
+// The same conversion from a 16-byte group already in registers (e.g. loaded ahead of use).
+template <typename T>
+__device__ __forceinline__ void group_from_raw(uint4 q, float* v);
+template <>
+__device__ __forceinline__ void group_from_raw<float>(uint4 q, float* v) {
+  v[0] = __uint_as_float(q.x); v[1] = __uint_as_float(q.y);
+  v[2] = __uint_as_float(q.z); v[3] = __uint_as_float(q.w);
+}
+template <>
+__device__ __forceinline__ void group_from_raw<__nv_bfloat16>(uint4 q, float* v) {
+  const unsigned w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    v[2 * i] = __uint_as_float(w[i] << 16);
+    v[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ void store_group(T* base, size_t idx, const float* v);
 template <>

@@ -186,10 +186,12 @@ struct ConvCfg {
 // blockIdx.x, blockIdx.x + gridDim.x, ... (a fixed order). The producer streams the stages of
 // successive tiles without a break; the accumulators are double-buffered in TMEM when two sets
 // fit (2 x kRowsM x N <= 512 columns), so a tile's epilogue overlaps the next tile's MMAs.
-// Warp roles: 0 TMA producer, 1 MMA issuer, 2-5 epilogue, 6-9 (3xTF32 only) operand split.
+// Warp roles: 0 TMA producer, 1 MMA issuer; bf16: 2-9 epilogue (two warps per TMEM lane
+// quarter, alternate 16-column blocks); 3xTF32: 2-5 epilogue, 6-9 operand split.
 template <int BF16>
 struct ConvWarps {
-  static constexpr int kThreads = BF16 ? 192 : 320;
+  static constexpr int kThreads = 320;
+  static constexpr int kEpi = BF16 ? 8 : 4;  // epilogue warps
 };
 
 template <int BF16, int MODE>
@@ -222,7 +224,7 @@ __global__ void __launch_bounds__(ConvWarps<BF16>::kThreads, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&accf[b], 1);
-      mbar_init(&acce[b], 128);
+      mbar_init(&acce[b], 32 * ConvWarps<BF16>::kEpi);
     }
     abort_flag = 0;
     mbar_fence_init();
@@ -309,7 +311,7 @@ __global__ void __launch_bounds__(ConvWarps<BF16>::kThreads, 1)
         mma_commit(&accf[buf]);
       }
     }
-  } else if (warp >= 6) {
+  } else if (!BF16 && warp >= 6) {
     // 3xTF32: split each fp32 halo stage into TF32 hi and lo parts, ahead of the MMAs
     const int et = threadIdx.x - 192;
     uint32_t it = 0;
@@ -330,11 +332,17 @@ __global__ void __launch_bounds__(ConvWarps<BF16>::kThreads, 1)
       }
     }
   } else {
-    // epilogue: TMEM -> bias + ReLU (forward) or ReLU mask (dgrad) -> global
+    // epilogue: TMEM -> bias + ReLU (forward) or ReLU mask (dgrad) -> global. The dgrad's
+    // mask groups of the next 16-column block are loaded before this block's TMEM read.
+    constexpr int EW = ConvWarps<BF16>::kEpi;
+    constexpr int CSTEP = 16 * (EW / 4);
+    constexpr int GE = C::GE;
+    constexpr int NG = 16 / GE;  // 16-byte groups per 16 columns
     const int wq = warp & 3;  // the TMEM lane quarter this warp may read
+    const int cfirst = 16 * ((warp - 2) >> 2);
     const int row = wq * 32 + lane;
     const size_t npx = (size_t)p.H * p.W;
-    constexpr int GE = C::GE;
+    const uint4* mask = reinterpret_cast<const uint4*>(p.mask);
     uint32_t lt = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
       const int buf = (int)(lt % NB);
@@ -347,20 +355,34 @@ __global__ void __launch_bounds__(ConvWarps<BF16>::kThreads, 1)
       decode(tile, nt, ty, x0);
       const int x = x0 + row;
       const uint32_t cbase = tbase + ((uint32_t)(wq * 32) << 16) + (uint32_t)(buf * acc_cols);
-      for (int c0 = 0; c0 < acc_cols; c0 += 16) {
+      // group index of (16-column block c0, group q) and whether its pixel exists
+      auto gidx = [&](int c0, int q) {
+        const size_t pix = (size_t)(ty + c0 / NT) * p.W + x;
+        return (size_t)((nt * NT + (c0 % NT) + q * GE) / GE) * npx + pix;
+      };
+      auto live = [&](int c0) { return x < p.W && ty + c0 / NT < p.H; };
+      uint4 mnext[NG];
+      if (MODE == 1 && live(cfirst))
+#pragma unroll
+        for (int q = 0; q < NG; ++q) mnext[q] = __ldg(mask + gidx(cfirst, q));
+      for (int c0 = cfirst; c0 < acc_cols; c0 += CSTEP) {
+        uint4 mcur[NG];
+#pragma unroll
+        for (int q = 0; q < NG; ++q) mcur[q] = mnext[q];
+        const int c1 = c0 + CSTEP;
+        if (MODE == 1 && c1 < acc_cols && live(c1))
+#pragma unroll
+          for (int q = 0; q < NG; ++q) mnext[q] = __ldg(mask + gidx(c1, q));
         uint32_t r[16];
         tmem_ld16(cbase + c0, r);
         tmem_ld_wait();
-        const int yr = ty + c0 / NT;
-        if (x >= p.W || yr >= p.H) continue;
-        const size_t pix = (size_t)yr * p.W + x;
+        if (!live(c0)) continue;
         const int o0 = nt * NT + (c0 % NT);
         float v[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 #pragma unroll
-        for (int q = 0; q < 16 / GE; ++q) {
-          const size_t gi = (size_t)((o0 + q * GE) / GE) * npx + pix;
+        for (int q = 0; q < NG; ++q) {
           float* vv = v + q * GE;
           if (MODE == 0) {
 #pragma unroll
@@ -370,11 +392,11 @@ __global__ void __launch_bounds__(ConvWarps<BF16>::kThreads, 1)
             }
           } else {
             float mk[GE];
-            load_group<T>((const T*)p.mask, gi, mk);
+            group_from_raw<T>(mcur[q], mk);
 #pragma unroll
             for (int j = 0; j < GE; ++j) vv[j] = mk[j] > 0.f ? vv[j] : 0.f;
           }
-          store_group<T>((T*)p.out, gi, vv);
+          store_group<T>((T*)p.out, gidx(c0, q), vv);
         }
       }
       tc_fence_before();
@@ -390,37 +412,41 @@ __global__ void __launch_bounds__(ConvWarps<BF16>::kThreads, 1)
 }
 
 // ---- bf16 weight gradient, several taps per CTA -----------------------------------------
-// A CTA covers a group of taps that share image rows: the x halo tile (R rows x (KP + 2)
-// pixels x C_in, MN-major) is loaded once per pixel chunk and each tap's B operand is the
-// same tile at a descriptor offset of (row, dx) pixels (16 bytes per pixel). The group's
-// accumulators sit side by side in TMEM (taps x C_in <= 512 columns).
+// A CTA covers a group of taps that share image rows, for a slice of cn input channels: the x
+// halo tile (R rows x (KP + 2 pu) pixels x cn channels, MN-major) is loaded once per pixel
+// chunk and each tap's B operand is the same tile at a descriptor offset of (row, dx) pixels
+// (16 bytes per pixel). The group's accumulators sit side by side in TMEM (taps x cn <= 512
+// columns). Every group has the same number of taps, so all CTAs carry equal work.
 struct TapGroups {
   int n;                                  // groups
-  int first[9], count[9], row0[9];        // taps first..first+count-1, rows row0..row0+R-1
+  int first[9], count[9], row0[9], c0[9];  // taps first..first+count-1, rows row0..row0+R-1,
+                                          // input channels c0..c0+cn-1
   int R;                                  // halo rows (same for every group)
+  int cn;                                 // input channels per group
 };
 
 TapGroups tap_groups(int cin) {
   TapGroups g{};
   if (cin <= 32) {  // 9 x 32 = 288 columns: all taps, 3-row halo
-    g.n = 1; g.first[0] = 0; g.count[0] = 9; g.row0[0] = 0; g.R = 3;
+    g.n = 1; g.first[0] = 0; g.count[0] = 9; g.row0[0] = 0; g.c0[0] = 0; g.R = 3; g.cn = cin;
   } else if (cin <= 128) {  // one row of 3 taps per group
-    g.n = 3; g.R = 1;
-    for (int r = 0; r < 3; ++r) { g.first[r] = 3 * r; g.count[r] = 3; g.row0[r] = r; }
-  } else {  // C_in = 256: two taps fill TMEM, (dx 0-1) and (dx 2) per row
-    g.n = 6; g.R = 1;
-    for (int r = 0; r < 3; ++r) {
-      g.first[2 * r] = 3 * r; g.count[2 * r] = 2; g.row0[2 * r] = r;
-      g.first[2 * r + 1] = 3 * r + 2; g.count[2 * r + 1] = 1; g.row0[2 * r + 1] = r;
-    }
+    g.n = 3; g.R = 1; g.cn = cin;
+    for (int r = 0; r < 3; ++r) { g.first[r] = 3 * r; g.count[r] = 3; g.row0[r] = r; g.c0[r] = 0; }
+  } else {  // C_in = 256: one row of 3 taps for one half of the input channels
+    g.n = 6; g.R = 1; g.cn = 128;
+    for (int r = 0; r < 3; ++r)
+      for (int h = 0; h < 2; ++h) {
+        const int k = 2 * r + h;
+        g.first[k] = 3 * r; g.count[k] = 3; g.row0[k] = r; g.c0[k] = 128 * h;
+      }
   }
   return g;
 }
 
 struct WgBf16Params {
-  float* part;  // [S][9][C_out][C_in]
+  float* part;  // [S][9][C_in][C_out]
   int cin, cout, H, W, chunks_x, total_chunks, per_split;
-  int stages;  // pipeline stages (float32 kernel)
+  int stages;  // pipeline stages
   int pu;      // pixels per TMA unit of both maps
   TapGroups tg;
   const int* skip;
@@ -428,7 +454,7 @@ struct WgBf16Params {
 };
 
 constexpr int kWbKP = 64;       // pixels per stage
-constexpr int kWbStages = 3;
+constexpr int kWbMaxStages = 6;
 constexpr uint32_t kWbA = 128u * kWbKP * 2;  // delta tile, 128 channels (zero-filled past C_out)
 
 // x halo pitch: the chunk's KP pixels plus one TMA unit of pu pixels on each side
@@ -444,23 +470,25 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc_bf16(const __grid_constant_
                                                          const __grid_constant__ CUtensorMap tmX,
                                                          WgBf16Params p) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  __shared__ uint64_t full[kWbStages], empty[kWbStages], accf;
+  __shared__ uint64_t full[kWbMaxStages], empty[kWbMaxStages], accf;
   __shared__ uint32_t tslot;
   __shared__ int abort_flag;
   if (p.skip && *p.skip) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int o0 = blockIdx.x * 128, grp = blockIdx.y, s_idx = blockIdx.z;
   const int t0 = p.tg.first[grp], nt = p.tg.count[grp], r0 = p.tg.row0[grp], R = p.tg.R;
+  const int cn = p.tg.cn, c0g = p.tg.c0[grp];
+  const int ns = p.stages;
   const int cbeg = s_idx * p.per_split;
   const int cend = min(p.total_chunks, cbeg + p.per_split);
   const int nk = cend > cbeg ? cend - cbeg : 0;
   const int pu = p.pu, HX = wb_pitch(pu);
-  const uint32_t BB = wb_b_bytes(p.cin, R, pu), SB = wb_stage(p.cin, R, pu);
+  const uint32_t BB = wb_b_bytes(cn, R, pu), SB = wb_stage(cn, R, pu);
   const uint32_t b_off = align_up(kWbA, 1024);
-  const uint32_t ncols = tmem_cols(nt * p.cin);
+  const uint32_t ncols = tmem_cols(nt * cn);
   volatile int* abort = &abort_flag;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kWbStages; ++s) {
+    for (int s = 0; s < ns; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -478,29 +506,29 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc_bf16(const __grid_constant_
     if (lane == 0) {
       int issued = 0;
       for (int i = 0; i < nk; ++i) {
-        const int s = i % kWbStages;
-        if (i >= kWbStages && !mbar_wait(&empty[s], ((i / kWbStages) - 1) & 1, abort, p.err))
+        const int s = i % ns;
+        if (i >= ns && !mbar_wait(&empty[s], ((i / ns) - 1) & 1, abort, p.err))
           break;
         const int ch = cbeg + i;
         const int y = ch / p.chunks_x, x0 = (ch % p.chunks_x) * kWbKP;
         uint8_t* st = smem + s * SB;
         mbar_expect_tx(&full[s], kWbA + BB);
         tma_load_4d(st, &tmD, &full[s], 0, x0 / pu, y, o0 / 8);
-        tma_load_4d(st + b_off, &tmX, &full[s], 0, x0 / pu - 1, y + r0 - 1, 0);
+        tma_load_4d(st + b_off, &tmX, &full[s], 0, x0 / pu - 1, y + r0 - 1, c0g / 8);
         issued = i + 1;
       }
       if (*abort)
-        for (int i = issued > kWbStages ? issued - kWbStages : 0; i < issued; ++i)
-          mbar_drain(&full[i % kWbStages], (i / kWbStages) & 1);
+        for (int i = issued > ns ? issued - ns : 0; i < issued; ++i)
+          mbar_drain(&full[i % ns], (i / ns) & 1);
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t id = idesc(1, 128, p.cin, 1, 1);
+      const uint32_t id = idesc(1, 128, cn, 1, 1);
       const uint32_t a_sbo = kWbKP * 16;                    // next 8-channel group of delta
       const uint32_t b_sbo = (uint32_t)R * HX * 16;  // next 8-channel group of x
       for (int i = 0; i < nk; ++i) {
-        const int s = i % kWbStages;
-        if (!mbar_wait(&full[s], (i / kWbStages) & 1, abort, p.err)) break;
+        const int s = i % ns;
+        if (!mbar_wait(&full[s], (i / ns) & 1, abort, p.err)) break;
         tc_fence_after();
         const uint32_t sa = smem_u32(smem + s * SB), sb = sa + b_off;
         for (int j = 0; j < nt; ++j) {
@@ -510,7 +538,7 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc_bf16(const __grid_constant_
 #pragma unroll
           for (int k = 0; k < kWbKP / 16; ++k) {
             const uint32_t ko = (uint32_t)k * 16u * 16u;
-            mma_f16(tbase + (uint32_t)(j * p.cin), sdesc(sa + ko, 128, a_sbo),
+            mma_f16(tbase + (uint32_t)(j * cn), sdesc(sa + ko, 128, a_sbo),
                     sdesc(sb + boff + ko, 128, b_sbo), id, (i > 0 || k > 0) ? 1u : 0u);
           }
         }
@@ -526,17 +554,15 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc_bf16(const __grid_constant_
     const bool live = o < p.cout && !*abort;
     for (int j = 0; j < nt; ++j) {
       const int tap = t0 + j;
-      float* dst = p.part + (((size_t)s_idx * 9 + tap) * p.cout + (live ? o : 0)) * p.cin;
-      for (int c0 = 0; c0 < p.cin; c0 += 16) {
+      // part[s][tap][c][o]: the warp's 32 lanes are 32 consecutive o, one 128-byte row per c
+      float* dst = p.part + ((size_t)s_idx * 9 + tap) * p.cin * p.cout + (size_t)c0g * p.cout + o;
+      for (int c0 = 0; c0 < cn; c0 += 16) {
         uint32_t r[16];
-        tmem_ld16(tbase + ((uint32_t)(wq * 32) << 16) + (uint32_t)(j * p.cin + c0), r);
+        tmem_ld16(tbase + ((uint32_t)(wq * 32) << 16) + (uint32_t)(j * cn + c0), r);
         tmem_ld_wait();
         if (!live) continue;
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-          reinterpret_cast<float4*>(dst + c0)[q] = make_float4(
-              nk ? __uint_as_float(r[4 * q]) : 0.f, nk ? __uint_as_float(r[4 * q + 1]) : 0.f,
-              nk ? __uint_as_float(r[4 * q + 2]) : 0.f, nk ? __uint_as_float(r[4 * q + 3]) : 0.f);
+        for (int q = 0; q < 16; ++q) dst[(size_t)(c0 + q) * p.cout] = nk ? __uint_as_float(r[q]) : 0.f;
       }
     }
   }
@@ -660,14 +686,15 @@ __global__ void __launch_bounds__(kW3Threads, 1) k_wgrad_tc_f32(const __grid_con
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int o0 = blockIdx.x * 128, grp = blockIdx.y, s_idx = blockIdx.z;
   const int t0 = p.tg.first[grp], nt = p.tg.count[grp], r0 = p.tg.row0[grp];
+  const int cn = p.tg.cn, c0g = p.tg.c0[grp];
   const int ns = p.stages;
   const int cbeg = s_idx * p.per_split;
   const int cend = min(p.total_chunks, cbeg + p.per_split);
   const int nk = cend > cbeg ? cend - cbeg : 0;
   const int pu = p.pu;
-  const W3Layout L = w3_layout(p.cin, R, pu);
-  const uint32_t RB = (uint32_t)p.cin * R * w3_raw_pitch(pu) * 4;
-  const uint32_t ncols = tmem_cols(nt * p.cin);
+  const W3Layout L = w3_layout(cn, R, pu);
+  const uint32_t RB = (uint32_t)cn * R * w3_raw_pitch(pu) * 4;
+  const uint32_t ncols = tmem_cols(nt * cn);
   volatile int* abort = &abort_flag;
   if (threadIdx.x == 0) {
     for (int s = 0; s < ns; ++s) {
@@ -696,7 +723,7 @@ __global__ void __launch_bounds__(kW3Threads, 1) k_wgrad_tc_f32(const __grid_con
         uint8_t* st = smem + s * L.stage;
         mbar_expect_tx(&full[s], 128u * kW3KP * 4 + RB);
         tma_load_4d(st + L.rawA, &tmD, &full[s], 0, x0 / pu, y, o0 / 4);
-        tma_load_4d(st + L.rawB, &tmX, &full[s], 0, x0 / pu - 1, y + r0 - 1, 0);
+        tma_load_4d(st + L.rawB, &tmX, &full[s], 0, x0 / pu - 1, y + r0 - 1, c0g / 4);
         issued = i + 1;
       }
       if (*abort)
@@ -705,7 +732,7 @@ __global__ void __launch_bounds__(kW3Threads, 1) k_wgrad_tc_f32(const __grid_con
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t id = idesc(1, 128, p.cin, 1, 1);
+      const uint32_t id = idesc(1, 128, cn, 1, 1);
       const uint32_t a_sbo = kW3KP * 16;                     // next 8-channel group of delta
       const uint32_t b_sbo = (uint32_t)R * (kW3KP + 2) * 16;  // next 8-channel group of x
       for (int i = 0; i < nk; ++i) {
@@ -722,7 +749,7 @@ __global__ void __launch_bounds__(kW3Threads, 1) k_wgrad_tc_f32(const __grid_con
           uint64_t db[3];
 #pragma unroll
           for (int k = 0; k < 3; ++k) db[k] = sdesc(st + L.b[k] + boff, 128, b_sbo);
-          const uint32_t d = tbase + (uint32_t)(j * p.cin);
+          const uint32_t d = tbase + (uint32_t)(j * cn);
           mma_f16(d, da[0], db[0], id, i > 0 ? 1u : 0u);
           mma_f16(d, da[0], db[1], id, 1u);
           mma_f16(d, da[1], db[0], id, 1u);
@@ -740,7 +767,7 @@ __global__ void __launch_bounds__(kW3Threads, 1) k_wgrad_tc_f32(const __grid_con
       const int s = i % ns;
       if (!mbar_wait(&full[s], (i / ns) & 1, abort, p.err)) break;
       uint8_t* st = smem + s * L.stage;
-      split3_stage<R>(st, st, L, p.cin / 8, pu, et);
+      split3_stage<R>(st, st, L, cn / 8, pu, et);
       fence_proxy_async();
       __syncwarp();
       if (lane == 0) mbar_arrive(&split[s]);
@@ -754,17 +781,15 @@ __global__ void __launch_bounds__(kW3Threads, 1) k_wgrad_tc_f32(const __grid_con
     const bool live = o < p.cout && !*abort;
     for (int j = 0; j < nt; ++j) {
       const int tap = t0 + j;
-      float* dst = p.part + (((size_t)s_idx * 9 + tap) * p.cout + (live ? o : 0)) * p.cin;
-      for (int c0 = 16 * half; c0 < p.cin; c0 += 32) {
+      // part[s][tap][c][o]: the warp's 32 lanes are 32 consecutive o, one 128-byte row per c
+      float* dst = p.part + ((size_t)s_idx * 9 + tap) * p.cin * p.cout + (size_t)c0g * p.cout + o;
+      for (int c0 = 16 * half; c0 < cn; c0 += 32) {
         uint32_t r[16];
-        tmem_ld16(tbase + ((uint32_t)(wq * 32) << 16) + (uint32_t)(j * p.cin + c0), r);
+        tmem_ld16(tbase + ((uint32_t)(wq * 32) << 16) + (uint32_t)(j * cn + c0), r);
         tmem_ld_wait();
         if (!live) continue;
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-          reinterpret_cast<float4*>(dst + c0)[q] = make_float4(
-              nk ? __uint_as_float(r[4 * q]) : 0.f, nk ? __uint_as_float(r[4 * q + 1]) : 0.f,
-              nk ? __uint_as_float(r[4 * q + 2]) : 0.f, nk ? __uint_as_float(r[4 * q + 3]) : 0.f);
+        for (int q = 0; q < 16; ++q) dst[(size_t)(c0 + q) * p.cout] = nk ? __uint_as_float(r[q]) : 0.f;
       }
     }
   }
@@ -776,34 +801,40 @@ __global__ void __launch_bounds__(kW3Threads, 1) k_wgrad_tc_f32(const __grid_con
   }
 }
 
-// gw[(o*C_in + c)*9 + tap] = sum_s part[s][tap][o][c]. A block owns 32 consecutive outputs;
-// warp w sums the splits s = w, w + 8, ... in order and the eight warp sums are added in warp
-// order, so the result is fixed for a given number of splits.
+// gw[(o*C_in + c)*9 + tap] = sum over s of part[s][tap][c][o]. A block owns 32 consecutive o
+// (the lanes, so every read is one 128-byte row) of one input channel c and all 9 taps; warp w
+// sums the splits s = w, w + 8, ... in order and the eight warp sums are added in warp order,
+// so the result is fixed for a given number of splits.
+constexpr int kRwO = 32;
 __global__ void __launch_bounds__(256) k_reduce_wgrad_tc(const float* __restrict__ part, int S,
                                                          int cin, int cout,
                                                          float* __restrict__ gw, const int* skip) {
   if (skip && *skip) return;
-  __shared__ float sh[8][33];
-  const size_t n = (size_t)cout * cin * 9;
-  const size_t per = (size_t)9 * cout * cin;
+  __shared__ float sh[8][9][kRwO + 1];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const size_t q = (size_t)blockIdx.x * 32 + lane;
-  float s = 0.f;
-  size_t src = 0;
-  if (q < n) {
-    const int tap = (int)(q % 9);
-    const size_t oc = q / 9;
-    const int c = (int)(oc % cin), o = (int)(oc / cin);
-    src = ((size_t)tap * cout + o) * cin + c;
-    for (int k = w; k < S; k += 8) s += part[k * per + src];
-  }
-  sh[w][lane] = s;
-  __syncthreads();
-  if (w == 0 && q < n) {
-    float t = 0.f;
+  const int otiles = (cout + kRwO - 1) / kRwO;
+  const int o0 = (blockIdx.x % otiles) * kRwO, c = blockIdx.x / otiles;
+  const int o = o0 + lane;
+  const size_t per = (size_t)9 * cout * cin, tstride = (size_t)cin * cout;
+  float acc[9];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) t += sh[k][lane];
-    gw[q] = t;
+  for (int t = 0; t < 9; ++t) acc[t] = 0.f;
+  if (o < cout) {
+    const float* src = part + (size_t)c * cout + o;
+    for (int k = w; k < S; k += 8)
+#pragma unroll
+      for (int t = 0; t < 9; ++t) acc[t] += src[k * per + t * tstride];
+  }
+#pragma unroll
+  for (int t = 0; t < 9; ++t) sh[w][t][lane] = acc[t];
+  __syncthreads();
+  for (int i = threadIdx.x; i < kRwO * 9; i += 256) {
+    const int oo = i / 9, t = i % 9;
+    if (o0 + oo >= cout) continue;
+    float v = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v += sh[k][t][oo];
+    gw[((size_t)(o0 + oo) * cin + c) * 9 + t] = v;
   }
 }
 
@@ -984,7 +1015,7 @@ static cudaError_t launch_wgrad_grouped(int bf16, const void* dout, const void* 
   while (pu < pu_max && W % (2 * pu) == 0) pu *= 2;
   CUtensorMap md, mx;
   cudaError_t e = make_map(&md, dout, bf16, cout, H, W, KP / pu, 1, 128 / GE, pu);
-  if (e == cudaSuccess) e = make_map(&mx, in, bf16, cin, H, W, KP / pu + 2, tg.R, cin / GE, pu);
+  if (e == cudaSuccess) e = make_map(&mx, in, bf16, cin, H, W, KP / pu + 2, tg.R, tg.cn / GE, pu);
   if (e != cudaSuccess) return e;
   const int otiles = (cout + 127) / 128;
   WgBf16Params p;
@@ -998,23 +1029,24 @@ static cudaError_t launch_wgrad_grouped(int bf16, const void* dout, const void* 
   p.pu = pu;
   const size_t per_split_elems = (size_t)9 * cout * cin;
   int maxcols = 0;
-  for (int g = 0; g < tg.n; ++g) maxcols = tg.count[g] * cin > maxcols ? tg.count[g] * cin : maxcols;
+  for (int g = 0; g < tg.n; ++g) maxcols = tg.count[g] * tg.cn > maxcols ? tg.count[g] * tg.cn : maxcols;
   const int max_res = 512 / (int)tmem_cols(maxcols);  // CTAs per SM that TMEM allows
-  uint32_t smem;
-  if (bf16) {
-    smem = kWbStages * wb_stage(cin, tg.R, pu);
-    p.stages = kWbStages;
-  } else {
-    // a fourth stage where it costs no resident CTA
-    const uint32_t sb = w3_layout(cin, tg.R, pu).stage;
-    p.stages = (uint32_t)max_res * (4 * sb + 2048u) <= 227u * 1024u ? 4 : 3;
-    smem = (uint32_t)p.stages * sb;
-  }
+  // as many stages as fit beside the CTAs that TMEM allows on one SM
+  const uint32_t sb = bf16 ? wb_stage(tg.cn, tg.R, pu) : w3_layout(tg.cn, tg.R, pu).stage;
+  const int max_stages = bf16 ? kWbMaxStages : kW3MaxStages;
+  p.stages = (int)((227u * 1024u / (uint32_t)max_res - 2048u) / sb);
+  if (p.stages > max_stages) p.stages = max_stages;
+  if (p.stages < 2) p.stages = 2;
+  uint32_t smem = (uint32_t)p.stages * sb;
   // a CTA holding more than half of TMEM keeps the SM to itself
   if (max_res == 1 && smem < 116u * 1024u) smem = 116u * 1024u;
   const int per_sm = (int)((227u * 1024u) / (smem + 2048u));
   const int ctas = otiles * tg.n;
-  int S = (2 * 152 * (per_sm > 0 ? per_sm : 1)) / ctas;
+  // one wave of equal CTAs (every group carries the same work), unless it leaves more than a
+  // tenth of the slots idle; each extra wave costs a pipeline fill and a partial-sum epilogue
+  const int slots = 152 * (per_sm > 0 ? per_sm : 1);
+  int S = slots / ctas;
+  if (S * ctas * 10 < slots * 9) S = 2 * slots / ctas;
   if (S > p.total_chunks / 16) S = p.total_chunks / 16;  // at least 16 pixel chunks per split
   if (S < 1) S = 1;
   const size_t npx = (size_t)H * W;
@@ -1036,8 +1068,8 @@ static cudaError_t launch_wgrad_grouped(int bf16, const void* dout, const void* 
     k_wgrad_tc_f32<3><<<grid, kW3Threads, smem, st>>>(md, mx, p);
   count_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_reduce_wgrad_tc<<<(unsigned)((per_split_elems + 31) / 32), 256, 0, st>>>(part, S, cin, cout,
-                                                                            gw, skip);
+  k_reduce_wgrad_tc<<<(unsigned)(((cout + kRwO - 1) / kRwO) * cin), 256, 0, st>>>(part, S, cin,
+                                                                                 cout, gw, skip);
   count_launch();
   float* bpart = part + ((size_t)S * per_split_elems + 63) / 64 * 64;
   const size_t per_block = (npx + SB - 1) / SB;
