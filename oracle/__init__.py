@@ -69,6 +69,7 @@ def lib():
         L.orc_job_free.argtypes = [C.c_void_p]
         L.orc_net_forward.argtypes = [C.POINTER(C.c_int), _dp, _dp, C.c_int, C.c_int, C.c_void_p,
                                       C.c_void_p]
+        L.orc_max_project.argtypes = [_dp, C.c_int, C.c_int, C.c_int, _dp]
         _lib = L
     return _lib
 
@@ -298,3 +299,19 @@ def denoise(x, params: Params = Params()):
     j = Job(x, params)
     out = j.run()
     return out, j.info()
+
+
+def max_project(vol):
+    """Maximum projection along Z of a (Z, H, W) volume (Methods, fluorescence microscopy)."""
+    vol = _f64(vol)
+    Z, H, W = vol.shape
+    out = np.zeros((H, W))
+    lib().orc_max_project(vol, Z, H, W, out)
+    return out
+
+
+def denoise_stack(vol, params: Params = Params()):
+    """A Z-stack as the paper processes one: every slice denoised as its own image with the same
+    parameters, then max projected. Returns (denoised slices, projection)."""
+    outs = np.stack([denoise(np.asarray(s), params)[0] for s in vol])
+    return outs, max_project(outs)

@@ -524,3 +524,14 @@ void orc_job_free(orc_job* j) {
   free(j->z); free(j->dz); free(j->S); free(j->Vbest); free(j->V);
   free(j);
 }
+
+/* Maximum intensity projection along Z of the independently denoised slices. */
+void orc_max_project(const double* vol, int Z, int H, int W, double* out) {
+  const size_t n = (size_t)H * W;
+  for (size_t p = 0; p < n; ++p) {
+    double m = vol[p];
+    for (int z = 1; z < Z; ++z)
+      if (vol[(size_t)z * n + p] > m) m = vol[(size_t)z * n + p];
+    out[p] = m;
+  }
+}

@@ -141,6 +141,11 @@ void orc_job_free(orc_job* j);
 void orc_net_forward(const int widths[ORC_LAYERS], const double* theta, const double* img, int h,
                      int w, double* v, double* z);
 
+/* ---- Volumes (Methods, fluorescence microscopy: a Z-stack is denoised slice by slice, each
+ * slice an independent image, and the denoised slices are max projected along Z) ----------
+ * out[y][x] = max over z of vol[z][y][x]; vol is Z planes of H x W. */
+void orc_max_project(const double* vol, int Z, int H, int W, double* out);
+
 #ifdef __cplusplus
 }
 #endif

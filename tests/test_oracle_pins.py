@@ -400,3 +400,30 @@ def test_output_is_mean_of_last_patience_validations():
         outs.append(v)
     assert info["epoch"] == rule.epoch and info["stopped"]
     np.testing.assert_allclose(out, np.mean(outs[-P:], axis=0), rtol=1e-13, atol=1e-15)
+
+
+def test_max_projection():
+    # The projection of a Z-stack (Methods, fluorescence microscopy) against numpy's max along
+    # Z, plus its defining properties: never below a slice, equal to some slice at every pixel,
+    # the identity on a one-slice stack, and invariant under reordering the slices.
+    r = _rng(15)
+    vol = r.normal(size=(5, 7, 9))
+    out = oracle.max_project(vol)
+    assert np.array_equal(out, vol.max(axis=0))
+    assert np.all(out[None] >= vol)
+    assert np.all(np.any(vol == out[None], axis=0))
+    assert np.array_equal(oracle.max_project(vol[:1]), vol[0])
+    assert np.array_equal(oracle.max_project(vol[::-1]), out)
+
+
+def test_stack_is_slices_denoised_independently():
+    # Each slice of a stack is denoised as its own image: the stack result equals the per-slice
+    # results, and the projection is their maximum.
+    r = _rng(16)
+    vol = r.uniform(0, 1, size=(3, 6, 6))
+    p = oracle.Params(widths=(2,) * 8, seed=2, fixed_steps=3)
+    outs, proj = oracle.denoise_stack(vol, p)
+    for z in range(3):
+        ref, _ = oracle.denoise(vol[z], p)
+        assert np.array_equal(outs[z], ref)
+    assert np.array_equal(proj, outs.max(axis=0))
