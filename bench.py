@@ -421,6 +421,63 @@ def run_serving(args, n2f):
     }
 
 
+def run_zstack(args, n2f):
+    """A live-cell-like Z-stack (Methods, fluorescence microscopy: 1024x1024 slices, Z = 20 um at
+    0.5 um, denoised slice by slice and max projected): Poisson-Gaussian noise, every slice its
+    own job, all in flight, the denoised slices gathered on the device and max projected there.
+    Timed from the first submission to the projection back on the host."""
+    import numpy as np
+    import torch
+    from paper_2108_10209_gb300 import synth
+    Z, S = args.z, args.stack_side
+    clean, noisy = synth.volume_cells(Z, S, S, seed=5_000_000)
+    noisy32 = noisy.astype(np.float32)
+    p = n2f.params(seed=0, precision=args.precision, widths=args.widths, engine=args.engine)
+    with n2f.Context(max_slots=Z) as ctx:
+        warm = synth.image_cells(256, 256, seed=7)[1].astype(np.float32)
+        n2f.denoise(warm, p, ctx)
+        st0 = ctx.stats()
+        slices = torch.empty((Z, S, S), dtype=torch.float32, device="cuda")
+        t0 = time.perf_counter()
+        ids = [ctx.submit(noisy32[z], p) for z in range(Z)]
+        sts = []
+        for z, j in enumerate(ids):
+            ctx.wait(j)
+            sts.append(ctx.poll(j))
+            assert sts[-1].state == n2f.N2F_DONE, sts[-1].as_dict()
+            ctx.result_device(j, slices[z])
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        proj = n2f.max_project(slices)
+        ev1.record()
+        proj_host = proj.cpu().numpy()
+        host_s = time.perf_counter() - t0
+        st1 = ctx.stats()
+    proj_ms = ev0.elapsed_time(ev1)
+    dev_s = (max(s.t_done_ms for s in sts) - min(s.t_start_ms for s in sts) + proj_ms) / 1e3
+    lat = [s.latency_ms for s in sts]
+    ref = clean.max(axis=0)
+    return {
+        "metric": METRIC, "value": Z / dev_s, "unit": UNIT, "n_gpus": 1, "steps": 1,
+        "warmup": 1, "ms_per_step": dev_s * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16 (f32 accumulate)" if args.precision else "f32",
+        "data": "synthetic (ellipsoid cells, Poisson-Gaussian per slice, seeded)",
+        "config": {"workload": f"Z-stack of {Z} slices of {S}x{S}, Poisson-Gaussian (peak 30, "
+                               "read 0.02), stopping rule per slice, all slices in flight, "
+                               "max projection on the device",
+                   "widths": WIDTH_NAMES[args.widths],
+                   "precision": "bf16" if args.precision else "fp32"},
+        "latency_ms": {"p50": pct(lat, 0.5), "p99": pct(lat, 0.99), "max": max(lat)},
+        "projection_ms": proj_ms,
+        "psnr_projection_db": {"noisy": synth.psnr(noisy.max(axis=0), ref),
+                               "denoised": synth.psnr(proj_host.astype(np.float64), ref)},
+        "e2e": {"value": Z / host_s, "unit": UNIT, "h2d_bytes_per_step": Z * S * S * 4,
+                "d2h_bytes_per_step": S * S * 4},
+        "gpu_launches": int(st1["kernel_launches"] - st0["kernel_launches"]),
+        "epochs": [s.epoch for s in sts],
+    }
+
+
 # ---------------------------------------------------------------------------- reference arm -
 
 def run_reference(args, ws, rank):
@@ -469,13 +526,15 @@ def main():
                     help="kernel class timed for the roofline (7 conv forward+dgrad, 1 forward, "
                          "2 dgrad, 3 wgrad)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--form", default="plain", choices=["plain", "batched", "serving"])
+    ap.add_argument("--form", default="plain", choices=["plain", "batched", "serving", "zstack"])
     ap.add_argument("--compare-batch", type=int, default=16,
                     help="plain form: also run this many images in the bf16 form together (0 = off)")
     ap.add_argument("--jobs", type=int, default=64, help="batched / serving: number of images")
     ap.add_argument("--rate", type=float, default=5.0, help="serving: arrivals per second")
     ap.add_argument("--slots", type=int, default=64, help="serving: jobs resident at once")
     ap.add_argument("--max-side", type=int, default=2048, help="serving: largest image side")
+    ap.add_argument("--z", type=int, default=41, help="zstack: slices")
+    ap.add_argument("--stack-side", type=int, default=1024, help="zstack: slice side")
     args = ap.parse_args()
     os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
     ws, rank, local = dist_env()
@@ -494,7 +553,8 @@ def main():
             import __graft_entry__ as g
             g.build()
             from paper_2108_10209_gb300 import n2f
-            line = run_batched(args, n2f) if args.form == "batched" else run_serving(args, n2f)
+            run = {"batched": run_batched, "serving": run_serving, "zstack": run_zstack}[args.form]
+            line = run(args, n2f)
             if rank != 0:
                 line = None
         if ws > 1:

@@ -226,6 +226,14 @@ size_t n2f_param_count(int widths);
  * H*(W/2); lf_e/lf_o: (H/2)*W. Exact copies. */
 int n2f_checker_gather(const float* x, int H, int W, float* up_e, float* up_o, float* lf_e,
                        float* lf_o, void* stream);
+
+/* Maximum projection of a Z-stack (Methods, fluorescence microscopy: the slices of a volume are
+ * denoised as independent images and max projected along Z). vol: Z planes of H*W floats,
+ * contiguous, device memory; out: H*W floats, device memory, caller-owned; may not overlap vol.
+ * out[y*W + x] = max over z of vol[z*H*W + y*W + x], exact. Runs on `stream` (0: default) and
+ * returns without waiting. N2F_EINVAL for a NULL pointer or Z, H or W < 1; N2F_EDEVICE if the
+ * launch fails. */
+int n2f_max_project(const float* vol, int Z, int H, int W, float* out, void* stream);
 /* NCHW float32 <-> CG layout of the given precision (C a multiple of G). */
 int n2f_pack_cg(const float* nchw, int C, int H, int W, int precision, void* cg, void* stream);
 int n2f_unpack_cg(const void* cg, int C, int H, int W, int precision, float* nchw, void* stream);

@@ -288,6 +288,12 @@ extern "C" int n2f_checker_gather(const float* x, int H, int W, float* up_e, flo
   return N2F_OK;
 }
 
+extern "C" int n2f_max_project(const float* vol, int Z, int H, int W, float* out, void* stream) {
+  if (!vol || !out || Z < 1 || H < 1 || W < 1) return N2F_EINVAL;
+  CKR(launch_max_project(vol, Z, (size_t)H * W, out, (cudaStream_t)stream));
+  return N2F_OK;
+}
+
 extern "C" int n2f_pack_cg(const float* nchw, int C, int H, int W, int precision, void* cg,
                            void* stream) {
   const int G = precision == N2F_BF16 ? 8 : 4;

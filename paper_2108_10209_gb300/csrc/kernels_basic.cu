@@ -51,6 +51,50 @@ cudaError_t launch_gather(const float* x, int H, int W, float* ue, float* uo, fl
   N2F_LAUNCH_CHECK();
 }
 
+// Maximum projection along Z of independently denoised slices (Methods, fluorescence
+// microscopy). vol: Z planes of n floats; four pixels per thread when n and both pointers
+// allow 16-byte accesses. Exact (a comparison, no rounding).
+__global__ void k_max_project4(const float4* __restrict__ vol, int Z, size_t n4,
+                               float4* __restrict__ out) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4;
+       i += (size_t)gridDim.x * blockDim.x) {
+    float4 m = vol[i];
+    for (int z = 1; z < Z; ++z) {
+      const float4 v = vol[(size_t)z * n4 + i];
+      m.x = v.x > m.x ? v.x : m.x;
+      m.y = v.y > m.y ? v.y : m.y;
+      m.z = v.z > m.z ? v.z : m.z;
+      m.w = v.w > m.w ? v.w : m.w;
+    }
+    out[i] = m;
+  }
+}
+
+__global__ void k_max_project1(const float* __restrict__ vol, int Z, size_t n,
+                               float* __restrict__ out) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    float m = vol[i];
+    for (int z = 1; z < Z; ++z) {
+      const float v = vol[(size_t)z * n + i];
+      m = v > m ? v : m;
+    }
+    out[i] = m;
+  }
+}
+
+cudaError_t launch_max_project(const float* vol, int Z, size_t n, float* out, cudaStream_t st) {
+  const bool v4 = n % 4 == 0 && ((uintptr_t)vol % 16) == 0 && ((uintptr_t)out % 16) == 0;
+  const size_t m = v4 ? n / 4 : n;
+  unsigned g = nblocks(m, 256);
+  if (g > 152u * 8) g = 152u * 8;
+  if (v4)
+    k_max_project4<<<g, 256, 0, st>>>((const float4*)vol, Z, m, (float4*)out);
+  else
+    k_max_project1<<<g, 256, 0, st>>>(vol, Z, n, out);
+  N2F_LAUNCH_CHECK();
+}
+
 __global__ void k_u16(const uint16_t* __restrict__ in, float* __restrict__ out, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x)

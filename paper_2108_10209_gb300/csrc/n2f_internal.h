@@ -68,6 +68,7 @@ struct PackArgs {
 };
 
 // ---- kernel launchers (kernels_*.cu); all enqueue on `st` and return cudaError_t ----------
+cudaError_t launch_max_project(const float* vol, int Z, size_t n, float* out, cudaStream_t st);
 cudaError_t launch_gather(const float* x, int H, int W, float* ue, float* uo, float* le, float* lo,
                           cudaStream_t st);
 cudaError_t launch_u16_to_f32(const uint16_t* in, float* out, size_t n, cudaStream_t st);

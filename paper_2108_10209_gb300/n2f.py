@@ -97,6 +97,7 @@ SIGNATURES = {
     "n2f_trainer_launches": (_U64, [_P]),
     "n2f_param_count": (_Z, [_I]),
     "n2f_checker_gather": (_I, [_P, _I, _I, _P, _P, _P, _P, _P]),
+    "n2f_max_project": (_I, [_P, _I, _I, _I, _P, _P]),
     "n2f_pack_cg": (_I, [_P, _I, _I, _I, _I, _P, _P]),
     "n2f_unpack_cg": (_I, [_P, _I, _I, _I, _I, _P, _P]),
     "n2f_conv3x3": (_I, [_I, _I, _I, _P, _I, _I, _I, _I, _P, _P, _P, _P, _P]),
@@ -183,6 +184,7 @@ class Context:
             cfg.lookahead = lookahead
         cfg.profile_kernel = profile_kernel
         cfg.use_graphs = int(use_graphs)
+        self.device = device
         self._keep = []
         if torch_alloc:
             import torch
@@ -359,6 +361,41 @@ def checker_gather(x, stream=None):
     check(lib().n2f_checker_gather(_ptr(x), H, W, _ptr(ue), _ptr(uo), _ptr(le), _ptr(lo),
                                    _stream_ptr(stream)), "n2f_checker_gather")
     return ue, uo, le, lo
+
+
+def max_project(vol, stream=None):
+    """Maximum projection along Z of a contiguous float32 CUDA tensor (Z, H, W) (n2f_max_project)."""
+    import torch
+    Z, H, W = vol.shape
+    out = torch.empty((H, W), dtype=torch.float32, device=vol.device)
+    check(lib().n2f_max_project(_ptr(vol), Z, H, W, _ptr(out), _stream_ptr(stream)),
+          "n2f_max_project")
+    return out
+
+
+def denoise_stack(vol: np.ndarray, p: Params | None = None, ctx: Context | None = None):
+    """A Z-stack the way the paper processes one (Methods, fluorescence microscopy): every slice
+    is submitted as its own job (all in flight at once, admitted by the context's budget), the
+    denoised slices are gathered on the device and max projected there. Returns the slices
+    (Z, H, W) and the projection (H, W) as float32 CUDA tensors on the context's device."""
+    import torch
+    own = ctx is None
+    ctx = ctx or Context()
+    try:
+        Z, H, W = vol.shape
+        dev = torch.device("cuda", ctx.device)
+        jobs = [ctx.submit(np.ascontiguousarray(vol[z], dtype=np.float32), p) for z in range(Z)]
+        slices = torch.empty((Z, H, W), dtype=torch.float32, device=dev)
+        for z, j in enumerate(jobs):
+            ctx.wait(j)
+            ctx.result_device(j, slices[z])
+        with torch.cuda.device(dev):
+            proj = max_project(slices)
+            torch.cuda.current_stream(dev).synchronize()
+        return slices, proj
+    finally:
+        if own:
+            ctx.close()
 
 
 def pack_cg(nchw, precision=N2F_FP32, stream=None):

@@ -15,6 +15,10 @@ Recipes (the paper's datasets are not available; these mimic their shapes and no
             Poisson-Gaussian:  y = Poisson(peak * clean) / peak + N(0, read^2)  (FMD-Confocal-like
                                shot + read noise, renormalised by the photon peak).
   u16       quantisation of a noisy image to 16-bit integers, then /65535 (microscope output).
+  volume    a live-cell-like Z-stack: ellipsoid "cells" (xy semi-axes U(4, 20), z semi-axis
+            U(1.5, 6) slices, angle U(0, pi), intensity U(0.2, 1.0), painter's order) on 0.05,
+            each slice blurred like `ellipses`, Poisson-Gaussian noise per slice (seeded per
+            slice). 200 cells per 512x512 of slice area, times Z / 20.
 """
 from __future__ import annotations
 
@@ -125,6 +129,38 @@ def image_cells_pg(h: int = 512, w: int = 512, peak: float = 30.0, read: float =
     """Ellipse cells + Poisson-Gaussian noise (photon peak, read-noise sigma)."""
     clean = ellipses(h, w, seed=seed)
     noisy = poisson_gaussian(clean, peak, read, seed=seed + 2000003)
+    return clean, noisy.astype(np.float32).astype(np.float64)
+
+
+def volume_cells(Z: int = 41, h: int = 1024, w: int = 1024, seed: int = 0, peak: float = 30.0,
+                 read: float = 0.02, n: int | None = None):
+    """(clean, noisy) Z-stacks of shape (Z, h, w); noisy is float32-representable."""
+    r = rng(seed)
+    if n is None:
+        n = max(1, int(round(200 * h * w / (512 * 512) * Z / 20)))
+    vol = np.full((Z, h, w), 0.05)
+    for _ in range(n):
+        cz, cy, cx = r.uniform(0, Z), r.uniform(0, h), r.uniform(0, w)
+        a, b, c = r.uniform(4, 20), r.uniform(4, 20), r.uniform(1.5, 6)
+        th = r.uniform(0, np.pi)
+        inten = r.uniform(0.2, 1.0)
+        R = int(np.ceil(max(a, b))) + 1
+        y0, y1 = max(0, int(cy) - R), min(h, int(cy) + R + 1)
+        x0, x1 = max(0, int(cx) - R), min(w, int(cx) + R + 1)
+        if y0 >= y1 or x0 >= x1:
+            continue
+        yy, xx = np.mgrid[y0:y1, x0:x1].astype(np.float64)
+        dy, dx = yy - cy, xx - cx
+        u = (dx * np.cos(th) + dy * np.sin(th)) / a
+        v = (-dx * np.sin(th) + dy * np.cos(th)) / b
+        q = u * u + v * v
+        for z in range(max(0, int(np.floor(cz - c))), min(Z, int(np.ceil(cz + c)) + 1)):
+            t = 1.0 - ((z + 0.5 - cz) / c) ** 2
+            if t > 0:
+                vol[z, y0:y1, x0:x1][q <= t] = inten
+    clean = np.stack([np.clip(_blur(vol[z], 1.5), 0.0, 1.0) for z in range(Z)])
+    noisy = np.stack([poisson_gaussian(clean[z], peak, read, seed=seed + 7000003 + z)
+                      for z in range(Z)])
     return clean, noisy.astype(np.float32).astype(np.float64)
 
 
