@@ -38,6 +38,11 @@ def lib():
         L.orc_splitmix64_at.argtypes = [C.c_uint64, C.c_uint64]
         L.orc_param_count.restype = C.c_size_t
         L.orc_param_count.argtypes = [C.POINTER(C.c_int)]
+        L.orc_param_count_c.restype = C.c_size_t
+        L.orc_param_count_c.argtypes = [C.POINTER(C.c_int), C.c_int]
+        L.orc_init_params_c.argtypes = [C.POINTER(C.c_int), C.c_int, C.c_uint64, _dp]
+        L.orc_net_forward_c.argtypes = [C.POINTER(C.c_int), C.c_int, _dp, _dp, C.c_int, C.c_int,
+                                        C.c_void_p, C.c_void_p]
         L.orc_init_params.argtypes = [C.POINTER(C.c_int), C.c_uint64, _dp]
         L.orc_checker.argtypes = [_dp, C.c_int, C.c_int, _dp, _dp, _dp, _dp]
         L.orc_conv3x3_fwd.argtypes = [_dp, C.c_int, C.c_int, C.c_int, _dp, _dp, C.c_int, C.c_int, _dp]
@@ -88,19 +93,19 @@ def splitmix64_at(seed: int, k: int) -> int:
     return int(lib().orc_splitmix64_at(seed, k))
 
 
-def param_count(widths=WIDTHS_PLIT) -> int:
-    return int(lib().orc_param_count(_widths(widths)))
+def param_count(widths=WIDTHS_PLIT, channels: int = 1) -> int:
+    return int(lib().orc_param_count_c(_widths(widths), max(1, channels)))
 
 
-def init_params(widths=WIDTHS_PLIT, seed: int = 0) -> np.ndarray:
-    th = np.zeros(param_count(widths), np.float64)
-    lib().orc_init_params(_widths(widths), seed, th)
+def init_params(widths=WIDTHS_PLIT, seed: int = 0, channels: int = 1) -> np.ndarray:
+    th = np.zeros(param_count(widths, channels), np.float64)
+    lib().orc_init_params_c(_widths(widths), max(1, channels), seed, th)
     return th
 
 
-def unpack(widths, theta):
+def unpack(widths, theta, channels: int = 1):
     """Splits a flat parameter vector into [(W_l, b_l)] * 8 + [(w_head, b_head)] views."""
-    out, off, cin = [], 0, 1
+    out, off, cin = [], 0, max(1, channels)
     for cout in widths:
         n = cout * cin * 9
         out.append((theta[off:off + n].reshape(cout, cin, 3, 3), theta[off + n:off + n + cout]))
@@ -210,7 +215,8 @@ class _Params(C.Structure):
     _fields_ = [("widths", C.c_int * LAYERS), ("lr", C.c_double), ("beta1", C.c_double),
                 ("beta2", C.c_double), ("eps", C.c_double), ("patience", C.c_int),
                 ("max_epochs", C.c_int), ("fixed_steps", C.c_int), ("loss_kind", C.c_int),
-                ("incl_best", C.c_int), ("seed", C.c_uint64)]
+                ("incl_best", C.c_int), ("seed", C.c_uint64), ("channels", C.c_int),
+                ("target", C.c_int)]
 
 
 @dataclasses.dataclass
@@ -227,22 +233,30 @@ class Params:
     incl_best: bool = False
     seed: int = 0
 
+    channels: int = 1   # input channels C_0 (Fig. 2a caption: inputs may be multi-channel)
+    target: int = 0     # the predicted channel (one output channel per network)
+
     def _c(self):
         return _Params(_widths(self.widths), self.lr, self.beta1, self.beta2, self.eps,
                        self.patience, self.max_epochs, self.fixed_steps, self.loss_kind,
-                       int(self.incl_best), self.seed)
+                       int(self.incl_best), self.seed, self.channels, self.target)
 
 
 class Job:
     """One image's whole Noise2Fast run, stepped from Python."""
 
     def __init__(self, x, params: Params = Params()):
+        """x: (H, W), or (C_0, H, W) planes when params.channels = C_0 > 1."""
         x = _f64(x)
-        self.H, self.W = x.shape
+        if x.ndim == 2:
+            x = x[None]
+        assert x.shape[0] == max(1, params.channels) and 0 <= params.target < x.shape[0]
+        _, self.H, self.W = x.shape
+        x = np.ascontiguousarray(x)
         self.params = params
         self._p = params._c()
         self.h = lib().orc_job_new(x, self.H, self.W, C.byref(self._p))
-        self.np = param_count(params.widths)
+        self.np = param_count(params.widths, params.channels)
 
     def __del__(self):
         if getattr(self, "h", None):
@@ -287,11 +301,25 @@ class Job:
 
 
 def net_forward(widths, theta, img):
+    """img: (h, w), or (C_0, h, w) planes."""
     img = _f64(img)
-    h, w = img.shape
+    if img.ndim == 2:
+        img = img[None]
+    c0, h, w = img.shape
+    img = np.ascontiguousarray(img)
     v = np.zeros((h, w)); z = np.zeros((h, w))
-    lib().orc_net_forward(_widths(widths), _f64(theta), img, h, w, v.ctypes.data, z.ctypes.data)
+    lib().orc_net_forward_c(_widths(widths), c0, _f64(theta), img, h, w, v.ctypes.data,
+                            z.ctypes.data)
     return v, z
+
+
+def denoise_channels(x, params: Params = Params()):
+    """A multi-channel image (C, H, W) the way Fig. 2a's caption describes RGB: every channel
+    predicted by its own network that sees all C input channels. Returns (C, H, W)."""
+    x = _f64(x)
+    c0 = x.shape[0]
+    return np.stack([denoise(x, dataclasses.replace(params, channels=c0, target=t))[0]
+                     for t in range(c0)])
 
 
 def denoise(x, params: Params = Params()):

@@ -23,10 +23,11 @@ uint64_t orc_splitmix64_at(uint64_t seed, uint64_t k) {
 }
 
 /* Methods, first paragraph: two 32-channel 3x3 conv+ReLU, repeated three more times with the
- * width doubled each time, then 1x1 conv + sigmoid. Widths are a parameter (see oracle.h). */
-size_t orc_param_count(const int widths[ORC_LAYERS]) {
+ * width doubled each time, then 1x1 conv + sigmoid. Widths are a parameter (see oracle.h); the
+ * first layer sees c0 input channels (Fig. 2a caption: inputs may be multi-channel). */
+size_t orc_param_count_c(const int widths[ORC_LAYERS], int c0) {
   size_t n = 0;
-  int cin = 1;
+  int cin = c0;
   for (int l = 0; l < ORC_LAYERS; ++l) {
     n += (size_t)widths[l] * cin * 9 + widths[l];
     cin = widths[l];
@@ -34,11 +35,13 @@ size_t orc_param_count(const int widths[ORC_LAYERS]) {
   return n + (size_t)cin + 1;
 }
 
+size_t orc_param_count(const int widths[ORC_LAYERS]) { return orc_param_count_c(widths, 1); }
+
 /* Offsets of W_l and b_l (l = 0..7) and of the head (index 8) in the flat vector. */
-static void param_offsets(const int widths[ORC_LAYERS], size_t ow[ORC_LAYERS + 1],
+static void param_offsets(const int widths[ORC_LAYERS], int c0, size_t ow[ORC_LAYERS + 1],
                           size_t ob[ORC_LAYERS + 1]) {
   size_t n = 0;
-  int cin = 1;
+  int cin = c0;
   for (int l = 0; l < ORC_LAYERS; ++l) {
     ow[l] = n;
     n += (size_t)widths[l] * cin * 9;
@@ -50,9 +53,9 @@ static void param_offsets(const int widths[ORC_LAYERS], size_t ow[ORC_LAYERS + 1
   ob[ORC_LAYERS] = n + cin;
 }
 
-void orc_init_params(const int widths[ORC_LAYERS], uint64_t seed, double* theta) {
+void orc_init_params_c(const int widths[ORC_LAYERS], int c0, uint64_t seed, double* theta) {
   size_t k = 0;
-  int cin = 1;
+  int cin = c0;
   for (int l = 0; l <= ORC_LAYERS; ++l) {
     const int head = (l == ORC_LAYERS);
     const int cout = head ? 1 : widths[l];
@@ -65,6 +68,10 @@ void orc_init_params(const int widths[ORC_LAYERS], uint64_t seed, double* theta)
     }
     if (!head) cin = widths[l];
   }
+}
+
+void orc_init_params(const int widths[ORC_LAYERS], uint64_t seed, double* theta) {
+  orc_init_params_c(widths, 1, seed, theta);
 }
 
 /* ------------------------------------------------------------------------------------------ */
@@ -267,11 +274,12 @@ int orc_stop_update(orc_stop_state* s, double score, int patience, int incl_best
 struct orc_job {
   orc_params p;
   int H, W;
-  double* x;
+  int c0, tc; /* input channels, target channel */
+  double* x;  /* c0 planes of H*W */
   int ph[4], pw[4];
   double* pin[4]; /* pair inputs */
-  double* ptg[4]; /* pair targets (aliases of the inputs, table order) */
-  double* sub[4]; /* up_e, up_o, lf_e, lf_o */
+  double* ptg[4]; /* pair targets (channel tc of the paired sub-image, table order) */
+  double* sub[4]; /* up_e, up_o, lf_e, lf_o; c0 planes each */
   size_t np;
   double *theta, *grad, *m, *v;
   long t;
@@ -296,27 +304,39 @@ orc_job* orc_job_new(const double* x, int H, int W, const orc_params* p) {
   j->p = *p;
   j->H = H;
   j->W = W;
-  j->x = dalloc((size_t)H * W);
-  memcpy(j->x, x, sizeof(double) * H * W);
+  j->c0 = p->channels > 0 ? p->channels : 1;
+  j->tc = p->target;
+  const size_t N = (size_t)H * W;
+  j->x = dalloc((size_t)j->c0 * N);
+  memcpy(j->x, x, sizeof(double) * j->c0 * N);
   j->ph[0] = j->ph[1] = H;
   j->pw[0] = j->pw[1] = W / 2;
   j->ph[2] = j->ph[3] = H / 2;
   j->pw[2] = j->pw[3] = W;
-  for (int k = 0; k < 4; ++k) j->sub[k] = dalloc((size_t)j->ph[k] * j->pw[k]);
-  orc_checker(j->x, H, W, j->sub[0], j->sub[1], j->sub[2], j->sub[3]);
-  /* Methods table: (x_even -> x_odd), (x_odd -> x_even), (x'_even -> x'_odd), (x'_odd -> x'_even) */
-  j->pin[0] = j->sub[0]; j->ptg[0] = j->sub[1];
-  j->pin[1] = j->sub[1]; j->ptg[1] = j->sub[0];
-  j->pin[2] = j->sub[2]; j->ptg[2] = j->sub[3];
-  j->pin[3] = j->sub[3]; j->ptg[3] = j->sub[2];
-  j->np = orc_param_count(p->widths);
+  size_t P[4];
+  for (int k = 0; k < 4; ++k) {
+    P[k] = (size_t)j->ph[k] * j->pw[k];
+    j->sub[k] = dalloc((size_t)j->c0 * P[k]);
+  }
+  /* every input channel is downsampled the same way */
+  for (int c = 0; c < j->c0; ++c)
+    orc_checker(j->x + c * N, H, W, j->sub[0] + c * P[0], j->sub[1] + c * P[1],
+                j->sub[2] + c * P[2], j->sub[3] + c * P[3]);
+  /* Methods table: (x_even -> x_odd), (x_odd -> x_even), (x'_even -> x'_odd), (x'_odd -> x'_even);
+   * the target is the predicted channel of the paired sub-image (Fig. 2a caption: one output
+   * channel per network) */
+  for (int k = 0; k < 4; ++k) {
+    j->pin[k] = j->sub[k];
+    j->ptg[k] = j->sub[k ^ 1] + (size_t)j->tc * P[k ^ 1];
+  }
+  j->np = orc_param_count_c(p->widths, j->c0);
   j->theta = dalloc(j->np);
   j->grad = dalloc(j->np);
   j->m = dalloc(j->np);
   j->v = dalloc(j->np);
-  orc_init_params(p->widths, p->seed, j->theta);
-  param_offsets(p->widths, j->ow, j->ob);
-  int cin = 1;
+  orc_init_params_c(p->widths, j->c0, p->seed, j->theta);
+  param_offsets(p->widths, j->c0, j->ow, j->ob);
+  int cin = j->c0;
   size_t maxpx = 0;
   for (int k = 0; k < 4; ++k)
     if ((size_t)j->ph[k] * j->pw[k] > maxpx) maxpx = (size_t)j->ph[k] * j->pw[k];
@@ -340,10 +360,11 @@ void orc_job_set_theta(orc_job* j, const double* theta) {
 }
 
 /* Forward through the eight conv layers, keeping every post-ReLU map in act[]. */
-static void forward_layers(const int widths[ORC_LAYERS], const double* theta, const size_t* ow,
-                           const size_t* ob, const double* img, int h, int w, double** act) {
+static void forward_layers(const int widths[ORC_LAYERS], int c0, const double* theta,
+                           const size_t* ow, const size_t* ob, const double* img, int h, int w,
+                           double** act) {
   const double* in = img;
-  int cin = 1;
+  int cin = c0;
   for (int l = 0; l < ORC_LAYERS; ++l) {
     orc_conv3x3_fwd(in, cin, h, w, theta + ow[l], theta + ob[l], widths[l], 1, act[l]);
     in = act[l];
@@ -357,7 +378,7 @@ double orc_job_step(orc_job* j, int pair) {
   const int* wd = j->p.widths;
   j->lh = h;
   j->lw = w;
-  forward_layers(wd, j->theta, j->ow, j->ob, j->pin[pair], h, w, j->act);
+  forward_layers(wd, j->c0, j->theta, j->ow, j->ob, j->pin[pair], h, w, j->act);
   const int c8 = wd[ORC_LAYERS - 1];
   const double* w9 = j->theta + j->ow[ORC_LAYERS];
   orc_head_fwd(j->act[ORC_LAYERS - 1], c8, npx, w9, j->theta[j->ob[ORC_LAYERS]], j->z);
@@ -403,14 +424,14 @@ double orc_job_step(orc_job* j, int pair) {
   return j->last_loss;
 }
 
-void orc_net_forward(const int widths[ORC_LAYERS], const double* theta, const double* img, int h,
-                     int w, double* v, double* z) {
+void orc_net_forward_c(const int widths[ORC_LAYERS], int c0, const double* theta,
+                       const double* img, int h, int w, double* v, double* z) {
   size_t ow[ORC_LAYERS + 1], ob[ORC_LAYERS + 1];
-  param_offsets(widths, ow, ob);
+  param_offsets(widths, c0, ow, ob);
   const size_t npx = (size_t)h * w;
   double* act[ORC_LAYERS];
   for (int l = 0; l < ORC_LAYERS; ++l) act[l] = dalloc((size_t)widths[l] * npx);
-  forward_layers(widths, theta, ow, ob, img, h, w, act);
+  forward_layers(widths, c0, theta, ow, ob, img, h, w, act);
   double* zz = dalloc(npx);
   orc_head_fwd(act[ORC_LAYERS - 1], widths[ORC_LAYERS - 1], (int)npx, theta + ow[ORC_LAYERS],
                theta[ob[ORC_LAYERS]], zz);
@@ -422,13 +443,19 @@ void orc_net_forward(const int widths[ORC_LAYERS], const double* theta, const do
   for (int l = 0; l < ORC_LAYERS; ++l) free(act[l]);
 }
 
+void orc_net_forward(const int widths[ORC_LAYERS], const double* theta, const double* img, int h,
+                     int w, double* v, double* z) {
+  orc_net_forward_c(widths, 1, theta, img, h, w, v, z);
+}
+
 /* Methods: after each epoch, run the full noisy image through the network and take the MSE
- * between that output and the noisy image itself. */
+ * between that output and the noisy image itself (its predicted channel). */
 double orc_job_validate(orc_job* j, double* v) {
   const size_t n = (size_t)j->H * j->W;
-  orc_net_forward(j->p.widths, j->theta, j->x, j->H, j->W, j->V, NULL);
+  orc_net_forward_c(j->p.widths, j->c0, j->theta, j->x, j->H, j->W, j->V, NULL);
+  const double* y = j->x + (size_t)j->tc * n;
   double s = 0.0;
-  for (size_t i = 0; i < n; ++i) s += (j->V[i] - j->x[i]) * (j->V[i] - j->x[i]);
+  for (size_t i = 0; i < n; ++i) s += (j->V[i] - y[i]) * (j->V[i] - y[i]);
   if (v) memcpy(v, j->V, sizeof(double) * n);
   return s / (double)n;
 }
@@ -489,7 +516,7 @@ size_t orc_job_get(const orc_job* j, int what, int layer, double* out) {
     case ORC_DZ: src = j->dz; n = lpx; break;
     case ORC_PAIR_IN:
       if (layer < 0 || layer > 3) return 0;
-      src = j->pin[layer]; n = (size_t)j->ph[layer] * j->pw[layer]; break;
+      src = j->pin[layer]; n = (size_t)j->c0 * j->ph[layer] * j->pw[layer]; break;
     case ORC_PAIR_TGT:
       if (layer < 0 || layer > 3) return 0;
       src = j->ptg[layer]; n = (size_t)j->ph[layer] * j->pw[layer]; break;

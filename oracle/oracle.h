@@ -38,12 +38,16 @@ extern "C" {
  * `seed` is mix(seed + (k+1) * 0x9E3779B97F4A7C15). */
 uint64_t orc_splitmix64_at(uint64_t seed, uint64_t k);
 
-/* Number of parameters of the network with the given eight layer widths.
- * Flat order: for l = 1..8: W_l[C_l][C_{l-1}][3][3], b_l[C_l]; then head w[C_8], b (C_0 = 1). */
+/* Number of parameters of the network with the given eight layer widths and C_0 input channels
+ * (Fig. 2a caption: inputs can be multi-channel; the output is always one channel).
+ * Flat order: for l = 1..8: W_l[C_l][C_{l-1}][3][3], b_l[C_l]; then head w[C_8], b.
+ * orc_param_count is the one-channel case. */
+size_t orc_param_count_c(const int widths[ORC_LAYERS], int c0);
 size_t orc_param_count(const int widths[ORC_LAYERS]);
 
 /* theta[i] = float( (2u_i - 1) / sqrt(fan_in) ), u_i = (splitmix64_at(seed, i) >> 11) * 2^-53,
  * fan_in = 9 C_in for the 3x3 layers and C_8 for the head (weights and biases alike). */
+void orc_init_params_c(const int widths[ORC_LAYERS], int c0, uint64_t seed, double* theta);
 void orc_init_params(const int widths[ORC_LAYERS], uint64_t seed, double* theta);
 
 /* ---- Checkerboard downsampling (Theoretical Background Eq. 6-7; Methods, "up" and "left") --
@@ -101,11 +105,16 @@ typedef struct {
   int loss_kind;                /* 0 = BCE, 1 = MSE */
   int incl_best;                /* 0 = window is the 100 epochs after the best */
   uint64_t seed;
+  int channels;                 /* input channels C_0 (0 or 1: a grayscale image) */
+  int target;                   /* the predicted channel, 0 .. C_0 - 1 (Fig. 2a caption: an RGB
+                                   image is denoised one output channel per network) */
 } orc_params;
 
 typedef struct orc_job orc_job;
 
-/* A job owns the image, the four training pairs, theta, Adam moments and the stop state. */
+/* A job owns the image (C_0 planes of H x W), the four training pairs, theta, Adam moments and
+ * the stop state. Each pair's input is all C_0 channels of one sub-image, its target the
+ * predicted channel of the paired sub-image; validation compares with that channel of x. */
 orc_job* orc_job_new(const double* x, int H, int W, const orc_params* p);
 /* Replace theta (n = orc_param_count values). */
 void orc_job_set_theta(orc_job* j, const double* theta);
@@ -136,8 +145,10 @@ void orc_job_info(const orc_job* j, long* t, int* epoch, int* since, int* stoppe
                   double* best, double* last_loss, int dims[4]);
 void orc_job_free(orc_job* j);
 
-/* Forward pass of the whole network on an arbitrary h x w one-channel image:
- * writes V = sigmoid(z) (h*w) and z if non-NULL. */
+/* Forward pass of the whole network on an arbitrary h x w image of C_0 channels (planes):
+ * writes V = sigmoid(z) (h*w) and z if non-NULL. orc_net_forward is the one-channel case. */
+void orc_net_forward_c(const int widths[ORC_LAYERS], int c0, const double* theta,
+                       const double* img, int h, int w, double* v, double* z);
 void orc_net_forward(const int widths[ORC_LAYERS], const double* theta, const double* img, int h,
                      int w, double* v, double* z);
 

@@ -427,3 +427,74 @@ def test_stack_is_slices_denoised_independently():
         ref, _ = oracle.denoise(vol[z], p)
         assert np.array_equal(outs[z], ref)
     assert np.array_equal(proj, outs.max(axis=0))
+
+
+def _torch_net_c(widths, theta, c0):
+    parts = [(torch.tensor(w.copy(), requires_grad=True), torch.tensor(b.copy(), requires_grad=True))
+             for w, b in oracle.unpack(widths, theta, c0)]
+
+    def fwd(img):
+        a = torch.tensor(img)[None]
+        for l in range(8):
+            a = torch.relu(F.conv2d(a, parts[l][0], parts[l][1], padding=1))
+        wh, bh = parts[8]
+        return (F.conv2d(a, wh.reshape(1, -1, 1, 1), bh))[0, 0]
+    return parts, fwd
+
+
+def test_multichannel_step_matches_torch_float64():
+    # Fig. 2a caption: a multi-channel input, one predicted channel per network. Each pair's
+    # input is all channels of one sub-image and its target the predicted channel of the paired
+    # sub-image; replayed with a float64 torch model whose first convolution has three inputs.
+    r = _rng(17)
+    x = r.uniform(0, 1, size=(3, 9, 8))
+    p = oracle.Params(widths=TINY, seed=5, channels=3, target=1)
+    job = oracle.Job(x, p)
+    assert job.np == oracle.param_count(TINY, 3) == oracle.param_count(TINY) + TINY[0] * 2 * 9
+    parts, fwd = _torch_net_c(TINY, job.get(oracle.THETA), 3)
+    params = [t for wb in parts for t in wb]
+    opt = torch.optim.Adam(params, lr=1e-3, betas=(0.9, 0.999), eps=1e-8)
+    subs = [oracle.checker(x[c]) for c in range(3)]
+    for pair in (0, 3, 1, 2):
+        h, w = (9, 4) if pair < 2 else (4, 8)
+        inp = job.get(oracle.PAIR_IN, pair).reshape(3, h, w)
+        tgt = job.get(oracle.PAIR_TGT, pair).reshape(h, w)
+        for c in range(3):
+            assert np.array_equal(inp[c], subs[c][pair])
+        assert np.array_equal(tgt, subs[1][pair ^ 1])
+        opt.zero_grad()
+        z = fwd(inp)
+        L = F.binary_cross_entropy_with_logits(z, torch.tensor(tgt))
+        L.backward()
+        loss = job.step(pair)
+        assert abs(loss - L.item()) < 1e-12
+        g = np.concatenate([t.grad.numpy().ravel() for t in params])
+        np.testing.assert_allclose(job.get(oracle.GRAD), g, rtol=1e-9, atol=1e-14)
+        opt.step()
+        th = np.concatenate([t.detach().numpy().ravel() for t in params])
+        np.testing.assert_allclose(job.get(oracle.THETA), th, rtol=1e-12, atol=1e-15)
+    # validation: the predicted channel of the noisy image is the reference
+    s, v = job.validate()
+    v_ref, _ = oracle.net_forward(TINY, job.get(oracle.THETA), x)
+    np.testing.assert_array_equal(v, v_ref)
+    assert abs(s - np.mean((v_ref - x[1]) ** 2)) < 1e-15
+
+
+def test_multichannel_reduces_to_one_channel():
+    # With the extra input channels identically zero, the three-channel network computes what
+    # the one-channel network with the first layer's channel-0 weights computes, and the
+    # gradient of the zero channels' first-layer weights vanishes.
+    r = _rng(18)
+    x1 = r.uniform(0, 1, size=(8, 8))
+    x3 = np.stack([x1, np.zeros_like(x1), np.zeros_like(x1)])
+    th3 = oracle.init_params(TINY, seed=6, channels=3)
+    parts3 = oracle.unpack(TINY, th3, 3)
+    th1 = np.concatenate([parts3[0][0][:, :1].ravel(), parts3[0][1]] +
+                         [np.concatenate([w.ravel(), b.ravel()]) for w, b in parts3[1:]])
+    v3, z3 = oracle.net_forward(TINY, th3, x3)
+    v1, z1 = oracle.net_forward(TINY, th1, x1)
+    np.testing.assert_array_equal(z3, z1)
+    job = oracle.Job(x3, oracle.Params(widths=TINY, seed=6, channels=3, target=0))
+    job.step(0)
+    gw1 = oracle.unpack(TINY, job.get(oracle.GRAD), 3)[0][0]
+    assert np.all(gw1[:, 1:] == 0.0) and np.any(gw1[:, 0] != 0.0)
