@@ -115,6 +115,14 @@ typedef struct {
   int32_t widths;       /* enum n2f_widths */
   int32_t incl_best;    /* 0: the window is the 100 epochs after the best (the reading used) */
   int32_t engine;       /* enum n2f_engine */
+  /* Input channels C_0 (1..4; 0 means 1) and the predicted channel 0..C_0-1. Fig. 2a's caption:
+   * the network input may be multi-channel, its output is always one channel, and an RGB
+   * image is denoised one channel per network. With C_0 > 1 the submitted image is C_0 planes
+   * of H*W floats; every plane is downsampled alike, each pair's input is all C_0 planes of one
+   * sub-image and its target the predicted plane of the paired sub-image, and validation
+   * compares with that plane of the image. The result is one H*W plane. */
+  int32_t channels;
+  int32_t target_channel;
 } n2f_params;
 
 typedef struct {
@@ -148,14 +156,16 @@ const char* n2f_strerror(int code);
 int n2f_create(n2f_ctx** out, const n2f_config* cfg);
 /* Stops the scheduler, cancels unfinished jobs and frees everything. */
 void n2f_destroy(n2f_ctx* ctx);
-/* Queues one H x W image (host memory, copied before return). p may be NULL (defaults).
+/* Queues one H x W image (host memory, copied before return); with p->channels = C_0 > 1, C_0
+ * planes of H x W. p may be NULL (defaults).
  * Errors: EINVAL (NULL, H or W < 2, non-finite pixel, bad params), ETOOBIG. */
 int n2f_submit(n2f_ctx* ctx, const float* image, int H, int W, const n2f_params* p, n2f_job* out);
 /* Same, for an image already in device memory (copied on the device before the job runs;
  * the caller must keep it valid until n2f_poll reports RUNNING or later). */
 int n2f_submit_device(n2f_ctx* ctx, const float* dimage, int H, int W, const n2f_params* p,
                       n2f_job* out);
-/* Same, for a 16-bit microscope image, normalised on the device as value / 65535. */
+/* Same, for a 16-bit microscope image, normalised on the device as value / 65535 (one plane:
+ * EINVAL when p->channels > 1). */
 int n2f_submit_u16(n2f_ctx* ctx, const uint16_t* image, int H, int W, const n2f_params* p,
                    n2f_job* out);
 /* Status snapshot; never blocks. */
@@ -190,7 +200,7 @@ int n2f_stats(n2f_ctx* ctx, n2f_ctx_stats* st);
  * NCHW maps, weights [C_out][C_in][3][3], the flat parameter order of n2f_param_count. */
 typedef struct n2f_trainer n2f_trainer;
 int n2f_trainer_create(n2f_trainer** out, const float* image, int H, int W, const n2f_params* p,
-                       void* stream);          /* image: host memory */
+                       void* stream);          /* image: host memory, p->channels planes */
 void n2f_trainer_destroy(n2f_trainer* tr);
 int n2f_trainer_step(n2f_trainer* tr, int pair); /* one Adam step on pair 0..3 (Methods table) */
 int n2f_trainer_validate(n2f_trainer* tr);       /* full-image forward + MSE + stop rule */
@@ -203,7 +213,7 @@ enum n2f_export {
   N2F_X_ACT = 4,    /* post-ReLU map of layer 1..8 from the last step, C*h*w */
   N2F_X_DELTA = 5,  /* dL/d(pre-activation) of layer 1..8 from the last step, C*h*w */
   N2F_X_DZ = 7,     /* dL/dz of the last step, h*w */
-  N2F_X_PAIR = 8,   /* sub-image 0..3 = up_e, up_o, lf_e, lf_o */
+  N2F_X_PAIR = 8,   /* sub-image 0..3 = up_e, up_o, lf_e, lf_o (all input planes) */
   N2F_X_VAL = 9,    /* last validation output, H*W */
   N2F_X_SUM = 10,   /* running output sum, H*W */
   N2F_X_OUT = 11    /* output image (after n2f_trainer_finish), H*W */

@@ -52,6 +52,8 @@ void n2f_params_default(n2f_params* p) {
   p->widths = N2F_WIDTHS_PLIT;
   p->incl_best = 0;
   p->engine = N2F_ENGINE_AUTO;
+  p->channels = 1;
+  p->target_channel = 0;
 }
 
 const char* n2f_strerror(int code) {
@@ -90,8 +92,14 @@ static int check_params(const n2f_params* p) {
     return N2F_EINVAL;
   if (p->fixed_steps < 0 && p->patience < 1) return N2F_EINVAL;
   if (p->incl_best && p->patience < 2) return N2F_EINVAL;
+  if (p->channels < 0 || p->channels > kMaxC0) return N2F_EINVAL;
+  if (p->target_channel < 0 || p->target_channel >= std::max(1, (int)p->channels))
+    return N2F_EINVAL;
   return N2F_OK;
 }
+
+// input planes of a job
+static size_t planes(const n2f_params* p) { return (size_t)std::max(1, (int)p->channels); }
 
 static int check_image(int H, int W) {
   if (H < 2 || W < 2) return N2F_EINVAL;
@@ -115,7 +123,7 @@ extern "C" int n2f_trainer_create(n2f_trainer** out, const float* image, int H, 
   int rc = check_params(p);
   if (rc) return rc;
   if ((rc = check_image(H, W))) return rc;
-  for (size_t i = 0; i < (size_t)H * W; ++i)
+  for (size_t i = 0; i < planes(p) * H * W; ++i)
     if (!isfinite(image[i])) return N2F_EINVAL;
   n2f_trainer* tr = new n2f_trainer();
   tr->own_stream = false;
@@ -128,8 +136,8 @@ extern "C" int n2f_trainer_create(n2f_trainer** out, const float* image, int H, 
     delete tr;
     return rc;
   }
-  cudaError_t e = cudaMemcpyAsync(tr->t.x, image, sizeof(float) * H * W, cudaMemcpyHostToDevice,
-                                  tr->t.st);
+  cudaError_t e = cudaMemcpyAsync(tr->t.x, image, sizeof(float) * planes(p) * H * W,
+                                  cudaMemcpyHostToDevice, tr->t.st);
   if (e != cudaSuccess) {
     trainer_release(&tr->t);
     delete tr;
@@ -241,7 +249,7 @@ extern "C" int n2f_trainer_export(n2f_trainer* tr, int what, int index, double* 
     case N2F_X_DZ: n = (size_t)h * w; break;
     case N2F_X_PAIR:
       if (index < 0 || index > 3) return N2F_EINVAL;
-      n = (size_t)t->ph[index] * t->pw[index];
+      n = (size_t)t->net.c0 * t->ph[index] * t->pw[index];
       break;
     case N2F_X_VAL: case N2F_X_SUM: case N2F_X_OUT: n = t->N; break;
     default: return N2F_EINVAL;
@@ -508,11 +516,11 @@ static int admit(n2f_ctx* c, Job* j) {
   int rc = trainer_init(&j->tr, c->al, j->st, j->src_kind == 2);
   if (rc) return rc;
   CKR(cudaEventRecord(j->ev_start, j->st));
-  const size_t n = (size_t)j->H * j->W;
+  const size_t n = (size_t)j->H * j->W, nin = planes(&j->prm) * n;
   if (j->src_kind == 0)
-    CKR(cudaMemcpyAsync(j->tr.x, j->pin_in, n * sizeof(float), cudaMemcpyHostToDevice, j->st));
+    CKR(cudaMemcpyAsync(j->tr.x, j->pin_in, nin * sizeof(float), cudaMemcpyHostToDevice, j->st));
   else if (j->src_kind == 1)
-    CKR(cudaMemcpyAsync(j->tr.x, j->dev_in, n * sizeof(float), cudaMemcpyDeviceToDevice, j->st));
+    CKR(cudaMemcpyAsync(j->tr.x, j->dev_in, nin * sizeof(float), cudaMemcpyDeviceToDevice, j->st));
   else
     CKR(cudaMemcpyAsync(j->tr.in_u16, j->pin_u16, n * sizeof(uint16_t), cudaMemcpyHostToDevice,
                         j->st));
@@ -747,7 +755,8 @@ static int submit_common(n2f_ctx* c, int kind, const void* image, int H, int W,
   int rc = check_params(p);
   if (rc) return rc;
   if ((rc = check_image(H, W))) return rc;
-  const size_t n = (size_t)H * W;
+  if (kind == 2 && planes(p) != 1) return N2F_EINVAL;  // 16-bit input: one plane
+  const size_t n = (size_t)H * W * planes(p);
   if (kind == 0) {
     const float* f = (const float*)image;
     for (size_t i = 0; i < n; ++i)

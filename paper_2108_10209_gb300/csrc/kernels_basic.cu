@@ -139,7 +139,7 @@ __global__ void k_init(float* __restrict__ theta, InitArgs a) {
 
 cudaError_t launch_init_params(float* theta, const NetShape& net, uint64_t seed, cudaStream_t st) {
   InitArgs a;
-  int cin = 1;
+  int cin = net.c0;
   for (int l = 0; l <= kLayers; ++l) {
     const int fan = l < kLayers ? cin * 9 : cin;
     a.bound[l] = 1.0 / sqrt((double)fan);
@@ -156,15 +156,15 @@ cudaError_t launch_init_params(float* theta, const NetShape& net, uint64_t seed,
 
 // ---------------------------------------------------------------------------------------------
 // Writes weight W[o][c][tap] of one layer into every operand copy that is present:
-//   SIMT forward  [C_in/8][tap][8][C_out]   (first layer: [C_out][9])
+//   SIMT forward  [C_in/8][tap][8][C_out]   (first layer: canonical [C_out][C_0][9])
 //   SIMT dgrad    [C_out/8][8 - tap][8][C_in]
 //   tensor core   tc_layout.cuh order, forward (rows o, k = tap*C_in + c) and dgrad
 //                 (rows c, k = (8 - tap)*C_out + o); bf16, or a TF32 hi part + residual.
 __device__ __forceinline__ void pack_one(float* fwd, float* dgr, void* tcf, void* tcd,
-                                         float* tcf_lo, float* tcd_lo, int tc_bf16, int cin,
-                                         int cout, int o, int c, int tap, float th) {
-  if (cin == 1) {
-    if (fwd) fwd[(size_t)o * 9 + tap] = th;
+                                         float* tcf_lo, float* tcd_lo, int tc_bf16, int first,
+                                         int cin, int cout, int o, int c, int tap, float th) {
+  if (first) {
+    if (fwd) fwd[((size_t)o * cin + c) * 9 + tap] = th;
     return;
   }
   if (fwd) fwd[(((size_t)(c >> 3) * 9 + tap) * 8 + (c & 7)) * cout + o] = th;
@@ -213,12 +213,12 @@ __global__ void k_adam(PackArgs pa, const float* __restrict__ grad, float* __res
     int l = 0;
     while (l < kLayers && i >= pa.w_off[l + 1]) ++l;
     if (l == kLayers || i >= pa.b_off[l]) continue;  // head or a bias: read from theta
-    const int cin = l == 0 ? 1 : pa.widths[l - 1], cout = pa.widths[l];
+    const int cin = l == 0 ? pa.c0 : pa.widths[l - 1], cout = pa.widths[l];
     const size_t j = i - pa.w_off[l];
     const int o = (int)(j / ((size_t)cin * 9));
     const int rem = (int)(j % ((size_t)cin * 9));
     pack_one(pa.fwd[l], pa.dgr[l], pa.tcf[l], pa.tcd[l], pa.tcf_lo[l], pa.tcd_lo[l], pa.tc_bf16,
-             cin, cout, o, rem / 9, rem % 9, th);
+             l == 0, cin, cout, o, rem / 9, rem % 9, th);
   }
 }
 
@@ -231,7 +231,8 @@ __global__ void k_pack_layer(const float* __restrict__ w, int cin, int cout, flo
        j += (size_t)gridDim.x * blockDim.x) {
     const int o = (int)(j / ((size_t)cin * 9));
     const int rem = (int)(j % ((size_t)cin * 9));
-    pack_one(fwd, dgr, tcf, tcd, tcf_lo, tcd_lo, tc_bf16, cin, cout, o, rem / 9, rem % 9, w[j]);
+    pack_one(fwd, dgr, tcf, tcd, tcf_lo, tcd_lo, tc_bf16, cin == 1, cin, cout, o, rem / 9,
+             rem % 9, w[j]);
   }
 }
 
@@ -316,72 +317,84 @@ cudaError_t launch_unpack_cg_f64(const void* cg, int C, int H, int W, int bf16, 
 }
 
 // ---------------------------------------------------------------------------------------------
-// First layer, C_in = 1 (Methods: the first 3x3 convolution sees the one-channel image).
-// One thread per pixel: nine taps from the image (zero outside), C outputs + bias, ReLU.
+// First layer, C_0 <= 4 input planes (Methods: the first 3x3 convolution sees the image; Fig.
+// 2a caption: the input may be multi-channel). One thread per pixel: 9 C_0 taps from the
+// planes (zero outside), C outputs + bias, ReLU.
 template <typename T>
-__global__ void __launch_bounds__(256) k_conv1_fwd(const float* __restrict__ img, int H, int W,
-                                                   const float* __restrict__ w,
+__global__ void __launch_bounds__(256) k_conv1_fwd(const float* __restrict__ img, int C0, int H,
+                                                   int W, const float* __restrict__ w,
                                                    const float* __restrict__ b, int C,
                                                    T* __restrict__ out, const int* skip) {
   if (skip && *skip) return;
   constexpr int G = CGTraits<T>::G;
-  __shared__ float sw[64 * 9], sb[64];
-  for (int i = threadIdx.x; i < C * 9; i += blockDim.x) sw[i] = w[i];
+  __shared__ float sw[64 * kMaxC0 * 9], sb[64];
+  for (int i = threadIdx.x; i < C * C0 * 9; i += blockDim.x) sw[i] = w[i];
   for (int i = threadIdx.x; i < C; i += blockDim.x) sb[i] = b[i];
   __syncthreads();
   const size_t npx = (size_t)H * W;
   const size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (p >= npx) return;
   const int y = (int)(p / W), x = (int)(p % W);
-  float t[9];
+  float t[kMaxC0][9];
 #pragma unroll
-  for (int ky = 0; ky < 3; ++ky)
+  for (int c = 0; c < kMaxC0; ++c)
 #pragma unroll
-    for (int kx = 0; kx < 3; ++kx) {
-      const int yy = y + ky - 1, xx = x + kx - 1;
-      t[ky * 3 + kx] = (yy >= 0 && yy < H && xx >= 0 && xx < W) ? img[(size_t)yy * W + xx] : 0.f;
-    }
+    for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+      for (int kx = 0; kx < 3; ++kx) {
+        const int yy = y + ky - 1, xx = x + kx - 1;
+        t[c][ky * 3 + kx] = (c < C0 && yy >= 0 && yy < H && xx >= 0 && xx < W)
+                                ? img[(size_t)c * npx + (size_t)yy * W + xx]
+                                : 0.f;
+      }
   for (int g = 0; g < C / G; ++g) {
     float v[G];
 #pragma unroll
     for (int k = 0; k < G; ++k) {
       const int o = g * G + k;
       float s = sb[o];
+      for (int c = 0; c < C0; ++c)
 #pragma unroll
-      for (int q = 0; q < 9; ++q) s += sw[o * 9 + q] * t[q];
+        for (int q = 0; q < 9; ++q) s += sw[(o * C0 + c) * 9 + q] * t[c][q];
       v[k] = s > 0.f ? s : 0.f;
     }
     store_group<T>(out, (size_t)g * npx + p, v);
   }
 }
 
-cudaError_t launch_conv1_fwd(const float* img, int H, int W, const float* w, const float* b, int C,
-                             int bf16, void* out, const int* skip, cudaStream_t st) {
-  if (C > 64) return cudaErrorInvalidValue;
+cudaError_t launch_conv1_fwd(const float* img, int C0, int H, int W, const float* w,
+                             const float* b, int C, int bf16, void* out, const int* skip,
+                             cudaStream_t st) {
+  if (C > 64 || C0 < 1 || C0 > kMaxC0) return cudaErrorInvalidValue;
   const size_t npx = (size_t)H * W;
   if (bf16)
-    k_conv1_fwd<__nv_bfloat16><<<nblocks(npx, 256), 256, 0, st>>>(img, H, W, w, b, C,
+    k_conv1_fwd<__nv_bfloat16><<<nblocks(npx, 256), 256, 0, st>>>(img, C0, H, W, w, b, C,
                                                                   (__nv_bfloat16*)out, skip);
   else
-    k_conv1_fwd<float><<<nblocks(npx, 256), 256, 0, st>>>(img, H, W, w, b, C, (float*)out, skip);
+    k_conv1_fwd<float><<<nblocks(npx, 256), 256, 0, st>>>(img, C0, H, W, w, b, C, (float*)out,
+                                                          skip);
   N2F_LAUNCH_CHECK();
 }
 
-// First-layer weight gradient: dW[o][tap] = sum_p d(p,o) x(p + tap), db[o] = sum_p d(p,o).
+// First-layer weight gradient: dW[o][c][tap] = sum_p d(p,o) x_c(p + tap), db[o] = sum_p d(p,o).
 // Block s sums pixel tiles s, s+S, ... in order; the partials are reduced in block order.
+constexpr int kConv1Acc = (64 * (kMaxC0 * 9 + 1) + 255) / 256;  // (o, c, tap) + biases per thread
 template <typename T>
 __global__ void __launch_bounds__(256) k_conv1_wgrad(const T* __restrict__ dout,
-                                                     const float* __restrict__ img, int H, int W,
-                                                     int C, float* __restrict__ part,
+                                                     const float* __restrict__ img, int C0, int H,
+                                                     int W, int C, float* __restrict__ part,
                                                      const int* skip) {
   if (skip && *skip) return;
   constexpr int G = CGTraits<T>::G;
-  constexpr int TP = 128;
+  constexpr int TP = 64;
   __shared__ float sD[TP][64 + 1];
-  __shared__ float sX[TP][9];
+  __shared__ float sX[TP][kMaxC0 * 9 + 1];
   const size_t npx = (size_t)H * W;
-  const int Q = C * 10;  // (o, tap) pairs then the C biases
-  float acc[3] = {0.f, 0.f, 0.f};
+  const int K = C0 * 9;
+  const int Q = C * (K + 1);  // (o, c, tap) triples then the C biases
+  float acc[kConv1Acc];
+#pragma unroll
+  for (int r = 0; r < kConv1Acc; ++r) acc[r] = 0.f;
   const size_t ntiles = (npx + TP - 1) / TP;
   for (size_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const size_t p0 = tile * TP;
@@ -399,71 +412,71 @@ __global__ void __launch_bounds__(256) k_conv1_wgrad(const T* __restrict__ dout,
 #pragma unroll
       for (int k = 0; k < G; ++k) sD[pp][g * G + k] = v[k];
     }
-    for (int i = threadIdx.x; i < TP * 9; i += blockDim.x) {
-      const int pp = i / 9, q = i % 9;
+    for (int i = threadIdx.x; i < TP * K; i += blockDim.x) {
+      const int pp = i / K, cq = i % K, c = cq / 9, q = cq % 9;
       const size_t p = p0 + pp;
       float v = 0.f;
       if (p < npx) {
         const int y = (int)(p / W) + q / 3 - 1, x = (int)(p % W) + q % 3 - 1;
-        if (y >= 0 && y < H && x >= 0 && x < W) v = img[(size_t)y * W + x];
+        if (y >= 0 && y < H && x >= 0 && x < W) v = img[(size_t)c * npx + (size_t)y * W + x];
       }
-      sX[pp][q] = v;
+      sX[pp][cq] = v;
     }
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < 3; ++r) {
+    for (int r = 0; r < kConv1Acc; ++r) {
       const int qi = threadIdx.x + r * 256;
       if (qi >= Q) break;
       float s = acc[r];
-      if (qi < C * 9) {
-        const int o = qi / 9, q = qi % 9;
-        for (int pp = 0; pp < TP; ++pp) s += sD[pp][o] * sX[pp][q];
+      if (qi < C * K) {
+        const int o = qi / K, cq = qi % K;
+        for (int pp = 0; pp < TP; ++pp) s += sD[pp][o] * sX[pp][cq];
       } else {
-        const int o = qi - C * 9;
+        const int o = qi - C * K;
         for (int pp = 0; pp < TP; ++pp) s += sD[pp][o];
       }
       acc[r] = s;
     }
   }
 #pragma unroll
-  for (int r = 0; r < 3; ++r) {
+  for (int r = 0; r < kConv1Acc; ++r) {
     const int qi = threadIdx.x + r * 256;
     if (qi < Q) part[(size_t)blockIdx.x * Q + qi] = acc[r];
   }
 }
 
 // out[q] = sum_{s < S} part[s * Q + q] (ascending s). Canonical placement of dW and db.
-__global__ void k_reduce_conv1(const float* __restrict__ part, int S, int C, float* __restrict__ gw,
-                               float* __restrict__ gb, const int* skip) {
+__global__ void k_reduce_conv1(const float* __restrict__ part, int S, int C, int K,
+                               float* __restrict__ gw, float* __restrict__ gb, const int* skip) {
   if (skip && *skip) return;
-  const int Q = C * 10;
+  const int Q = C * (K + 1);
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < Q; q += gridDim.x * blockDim.x) {
     float s = 0.f;
     for (int k = 0; k < S; ++k) s += part[(size_t)k * Q + q];
-    if (q < C * 9)
-      gw[q] = s;  // [o][0][ky][kx] == o * 9 + tap
+    if (q < C * K)
+      gw[q] = s;  // [o][c][ky][kx] == (o * C0 + c) * 9 + tap
     else
-      gb[q - C * 9] = s;
+      gb[q - C * K] = s;
   }
 }
 
-cudaError_t launch_conv1_wgrad(const void* dout, const float* img, int H, int W, int C, int bf16,
-                               float* part, size_t part_cap, float* gw, float* gb,
+cudaError_t launch_conv1_wgrad(const void* dout, const float* img, int C0, int H, int W, int C,
+                               int bf16, float* part, size_t part_cap, float* gw, float* gb,
                                const int* skip, cudaStream_t st) {
-  if (C > 64) return cudaErrorInvalidValue;
+  if (C > 64 || C0 < 1 || C0 > kMaxC0) return cudaErrorInvalidValue;
   const size_t npx = (size_t)H * W;
-  const int Q = C * 10;
+  const int K = C0 * 9, Q = C * (K + 1);
   int S = (int)((npx + 127) / 128);
   if (S > 304) S = 304;
   if ((size_t)S * Q > part_cap) S = (int)(part_cap / Q);
   if (S < 1) return cudaErrorInvalidValue;
   if (bf16)
-    k_conv1_wgrad<__nv_bfloat16><<<S, 256, 0, st>>>((const __nv_bfloat16*)dout, img, H, W, C,
-                                                    part, skip);
+    k_conv1_wgrad<__nv_bfloat16><<<S, 256, 0, st>>>((const __nv_bfloat16*)dout, img, C0, H, W,
+                                                    C, part, skip);
   else
-    k_conv1_wgrad<float><<<S, 256, 0, st>>>((const float*)dout, img, H, W, C, part, skip);
+    k_conv1_wgrad<float><<<S, 256, 0, st>>>((const float*)dout, img, C0, H, W, C, part, skip);
   count_launch();
-  k_reduce_conv1<<<nblocks(Q, 128), 128, 0, st>>>(part, S, C, gw, gb, skip);
+  k_reduce_conv1<<<nblocks(Q, 128), 128, 0, st>>>(part, S, C, K, gw, gb, skip);
   N2F_LAUNCH_CHECK();
 }
 

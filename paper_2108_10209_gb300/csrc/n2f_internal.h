@@ -16,8 +16,9 @@ constexpr int kLayers = 8;  // eight 3x3 conv + ReLU layers, then the 1x1 + sigm
 // then head w[C_8], b. Kernels read weights from packed copies (see Packing), never from it.
 struct NetShape {
   int widths[kLayers];
+  int c0 = 1;  // input channels of the first layer
   size_t w_off[kLayers + 1], b_off[kLayers + 1], count;
-  int cin(int l) const { return l == 0 ? 1 : widths[l - 1]; }
+  int cin(int l) const { return l == 0 ? c0 : widths[l - 1]; }
   int cmax() const {
     int m = 0;
     for (int l = 0; l < kLayers; ++l) m = widths[l] > m ? widths[l] : m;
@@ -28,7 +29,7 @@ struct NetShape {
     for (int l = 0; l < kLayers; ++l) s += widths[l];
     return s;
   }
-  void init(int which);
+  void init(int which, int channels = 1);
 };
 
 // Device-resident per-job scalars (updated only by kernels, so CUDA graphs can replay epochs).
@@ -62,6 +63,7 @@ struct PackArgs {
   float* tcf_lo[kLayers];
   float* tcd_lo[kLayers];
   int widths[kLayers];
+  int c0;       // input channels of the first layer
   unsigned long long w_off[kLayers + 1], b_off[kLayers + 1];
   unsigned long long count;
   int tc_bf16;  // tensor-core copies in bf16 (1) or f32 (0); tcf[l] == nullptr: none
@@ -87,12 +89,13 @@ cudaError_t launch_unpack_cg_f64(const void* cg, int C, int H, int W, int bf16, 
                                  cudaStream_t st);
 
 // First layer (C_in = 1): image plane -> CG map with bias + ReLU.
-cudaError_t launch_conv1_fwd(const float* img, int H, int W, const float* w /*[C][9]*/,
-                             const float* b, int C, int bf16, void* out, const int* skip,
-                             cudaStream_t st);
+constexpr int kMaxC0 = 4;  // input channels the first-layer kernels take
+cudaError_t launch_conv1_fwd(const float* img /*[C0][H][W]*/, int C0, int H, int W,
+                             const float* w /*[C][C0][9]*/, const float* b, int C, int bf16,
+                             void* out, const int* skip, cudaStream_t st);
 // First layer weight gradient: partials then ordered reduce into grad (canonical order).
-cudaError_t launch_conv1_wgrad(const void* dout, const float* img, int H, int W, int C, int bf16,
-                               float* part, size_t part_cap, float* gw, float* gb,
+cudaError_t launch_conv1_wgrad(const void* dout, const float* img, int C0, int H, int W, int C,
+                               int bf16, float* part, size_t part_cap, float* gw, float* gb,
                                const int* skip, cudaStream_t st);
 
 // SIMT implicit-GEMM 3x3 layers (C_in, C_out multiples of 8).

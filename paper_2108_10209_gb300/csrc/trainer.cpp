@@ -17,13 +17,14 @@ int set_cuda_error(cudaError_t e, const char* where) {
   return N2F_EDEVICE;
 }
 
-void NetShape::init(int which) {
+void NetShape::init(int which, int channels) {
   for (int l = 0; l < kLayers; ++l) {
     static const int plit[kLayers] = {32, 32, 64, 64, 128, 128, 256, 256};
     widths[l] = which == N2F_WIDTHS_W64 ? 64 : plit[l];
   }
+  c0 = channels > 0 ? channels : 1;
   size_t n = 0;
-  int cin = 1;
+  int cin = c0;
   for (int l = 0; l < kLayers; ++l) {
     w_off[l] = n;
     n += (size_t)widths[l] * cin * 9;
@@ -169,8 +170,9 @@ static size_t layout(Trainer* t, char* base) {
   c.base = base;
   const NetShape& net = t->net;
   const size_t es = t->bf16 ? 2 : 4;
-  t->x = c.take<float>(t->N);
-  for (int k = 0; k < 4; ++k) t->sub[k] = c.take<float>((size_t)t->ph[k] * t->pw[k]);
+  const size_t c0 = (size_t)net.c0;
+  t->x = c.take<float>(c0 * t->N);
+  for (int k = 0; k < 4; ++k) t->sub[k] = c.take<float>(c0 * t->ph[k] * t->pw[k]);
   t->theta = c.take<float>(net.count);
   t->grad = c.take<float>(net.count);
   t->m = c.take<float>(net.count);
@@ -245,7 +247,7 @@ int trainer_configure(Trainer* t, int H, int W, const n2f_params* p, int keep_de
   t->ph[2] = t->ph[3] = H / 2;
   t->pw[2] = t->pw[3] = W;
   t->maxP = std::max((size_t)H * (W / 2), (size_t)(H / 2) * W);
-  t->net.init(p->widths);
+  t->net.init(p->widths, p->channels);
   t->bf16 = p->precision == N2F_BF16;
   t->keep_deltas = keep_deltas;
   t->fixed_mode = p->fixed_steps >= 0;
@@ -280,6 +282,7 @@ int trainer_init(Trainer* t, const Allocator& al, cudaStream_t st, int want_u16)
   PackArgs& pa = t->pa;
   pa.theta = t->theta;
   for (int l = 0; l < kLayers; ++l) pa.widths[l] = t->net.widths[l];
+  pa.c0 = t->net.c0;
   for (int l = 0; l <= kLayers; ++l) {
     pa.w_off[l] = t->net.w_off[l];
     pa.b_off[l] = t->net.b_off[l];
@@ -316,7 +319,13 @@ int trainer_start(Trainer* t, int from_u16) {
   LaunchScope ls(&t->launches);
   cudaStream_t st = t->st;
   if (from_u16) CK(launch_u16_to_f32(t->in_u16, t->x, t->N, st));
-  CK(launch_gather(t->x, t->H, t->W, t->sub[0], t->sub[1], t->sub[2], t->sub[3], st));
+  // every input channel is downsampled the same way
+  for (int c = 0; c < t->net.c0; ++c) {
+    size_t P[4];
+    for (int k = 0; k < 4; ++k) P[k] = (size_t)c * t->ph[k] * t->pw[k];
+    CK(launch_gather(t->x + (size_t)c * t->N, t->H, t->W, t->sub[0] + P[0], t->sub[1] + P[1],
+                     t->sub[2] + P[2], t->sub[3] + P[3], st));
+  }
   CK(launch_init_params(t->theta, t->net, t->prm.seed, st));
   CK(cudaMemsetAsync(t->m, 0, t->net.count * sizeof(float), st));
   CK(cudaMemsetAsync(t->v, 0, t->net.count * sizeof(float), st));
@@ -354,7 +363,8 @@ static int conv_layer(Trainer* t, int l, const void* in, void* out, int H, int W
   Timed tm(t, l == 0 ? N2F_K_FIRST : N2F_K_CONV_FWD, 2.0 * P * 9 * cin * cout,
            l == 0 ? P * 4.0 + P * cout * es : P * (cin + cout) * es, val);
   if (l == 0) {
-    CK(launch_conv1_fwd((const float*)in, H, W, t->pa.fwd[0], b, cout, t->bf16, out, skip, t->st));
+    CK(launch_conv1_fwd((const float*)in, cin, H, W, t->pa.fwd[0], b, cout, t->bf16, out, skip,
+                        t->st));
   } else if (t->engine[l] == N2F_ENGINE_TC) {
     CK(launch_conv_tc(0, t->bf16, in, cin, cout, H, W, t->pa.tcf[l], t->pa.tcf_lo[l], b, nullptr,
                       out, skip, &t->state->kerr, t->st));
@@ -372,7 +382,9 @@ int trainer_step(Trainer* t, int pair) {
   const NetShape& net = t->net;
   const int* skip = t->fixed_mode ? nullptr : &t->state->stopped;
   const float* in = t->sub[pair];
-  const float* tgt = t->sub[pair ^ 1];  // Methods table: even <-> odd of the same kind
+  // Methods table: even <-> odd of the same kind; the target is the predicted channel
+  const float* tgt =
+      t->sub[pair ^ 1] + (size_t)t->prm.target_channel * t->ph[pair ^ 1] * t->pw[pair ^ 1];
   t->last_pair = pair;
   // forward, keeping every post-ReLU map
   const void* cur = in;
@@ -404,8 +416,8 @@ int trainer_step(Trainer* t, int pair) {
     float* gb = t->grad + net.b_off[l];
     const double fl = 2.0 * npx * 9 * cin * cout;
     if (l == 0) {
-      CK(launch_conv1_wgrad(dcur, in, h, w, cout, t->bf16, t->wpart, t->wpart_cap, gw, gb, skip,
-                            t->st));
+      CK(launch_conv1_wgrad(dcur, in, cin, h, w, cout, t->bf16, t->wpart, t->wpart_cap, gw, gb,
+                            skip, t->st));
       break;
     }
     {
@@ -456,7 +468,8 @@ int trainer_validate(Trainer* t) {
     const double es = t->bf16 ? 2.0 : 4.0, C8 = net.widths[kLayers - 1];
     Timed tm(t, N2F_K_HEAD, 2.0 * t->N * C8, (double)t->N * (C8 * es + 8.0), 1);
   CK(launch_head_val(cur, net.widths[kLayers - 1], (int)t->N, t->theta + net.w_off[kLayers],
-                     t->theta + net.b_off[kLayers], t->x, t->bf16, t->V, t->mpart, &nblk, skip,
+                     t->theta + net.b_off[kLayers], t->x + (size_t)t->prm.target_channel * t->N,
+                     t->bf16, t->V, t->mpart, &nblk, skip,
                      t->st));
   }
   CK(launch_val_decide(t->mpart, nblk, t->N, t->state, t->fixed_mode, t->st));

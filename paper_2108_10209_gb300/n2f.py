@@ -44,7 +44,8 @@ class Params(C.Structure):
                 ("beta2", C.c_float), ("eps", C.c_float), ("patience", C.c_uint32),
                 ("max_epochs", C.c_uint32), ("fixed_steps", C.c_int32), ("seed", C.c_uint64),
                 ("precision", C.c_int32), ("loss", C.c_int32), ("widths", C.c_int32),
-                ("incl_best", C.c_int32), ("engine", C.c_int32)]
+                ("incl_best", C.c_int32), ("engine", C.c_int32), ("channels", C.c_int32),
+                ("target_channel", C.c_int32)]
 
 
 class Status(C.Structure):
@@ -222,8 +223,9 @@ class Context:
         self.close()
 
     def submit(self, image: np.ndarray, p: Params | None = None) -> int:
+        """image: (H, W), or (C_0, H, W) planes with p.channels = C_0."""
         img = np.ascontiguousarray(image, dtype=np.float32)
-        H, W = img.shape
+        H, W = img.shape[-2:]
         job = C.c_uint64()
         check(lib().n2f_submit(self.h, img.ctypes.data_as(C.c_void_p), H, W,
                                C.byref(p) if p else None, C.byref(job)), "n2f_submit")
@@ -274,13 +276,39 @@ class Context:
 
 
 def denoise(image: np.ndarray, p: Params | None = None, ctx: Context | None = None) -> np.ndarray:
-    """One image through the whole path (submit, wait, result)."""
+    """One image through the whole path (submit, wait, result); (H, W), or (C_0, H, W) planes
+    with p.channels = C_0 (the result is the predicted plane, (H, W))."""
     own = ctx is None
     ctx = ctx or Context()
     try:
         j = ctx.submit(image, p)
         ctx.wait(j)
-        return ctx.result(j, image.shape)
+        return ctx.result(j, image.shape[-2:])
+    finally:
+        if own:
+            ctx.close()
+
+
+def denoise_channels(image: np.ndarray, p: Params | None = None,
+                     ctx: Context | None = None) -> np.ndarray:
+    """A multi-channel image (C, H, W), e.g. RGB, the way Fig. 2a's caption describes it: one
+    network per output channel, each seeing all C input channels. The C jobs run concurrently.
+    Returns (C, H, W)."""
+    own = ctx is None
+    ctx = ctx or Context()
+    try:
+        c0 = image.shape[0]
+        base = p if p is not None else params()
+        jobs = []
+        for t in range(c0):
+            q = Params.from_buffer_copy(base)
+            q.channels, q.target_channel = c0, t
+            jobs.append(ctx.submit(image, q))
+        outs = []
+        for j in jobs:
+            ctx.wait(j)
+            outs.append(ctx.result(j, image.shape[-2:]))
+        return np.stack(outs)
     finally:
         if own:
             ctx.close()
@@ -293,7 +321,7 @@ class Trainer:
 
     def __init__(self, image: np.ndarray, p: Params | None = None, stream=None):
         img = np.ascontiguousarray(image, dtype=np.float32)
-        self.H, self.W = img.shape
+        self.H, self.W = img.shape[-2:]
         self.h = C.c_void_p()
         check(lib().n2f_trainer_create(C.byref(self.h), img.ctypes.data_as(C.c_void_p), self.H,
                                        self.W, C.byref(p) if p else None,
