@@ -75,6 +75,7 @@ def lib():
         L.orc_net_forward.argtypes = [C.POINTER(C.c_int), _dp, _dp, C.c_int, C.c_int, C.c_void_p,
                                       C.c_void_p]
         L.orc_max_project.argtypes = [_dp, C.c_int, C.c_int, C.c_int, _dp]
+        L.orc_quad.argtypes = [_dp, C.c_int, C.c_int, _dp, _dp, _dp, _dp]
         _lib = L
     return _lib
 
@@ -123,6 +124,15 @@ def checker(x):
     lf_e = np.zeros((H // 2, W)); lf_o = np.zeros((H // 2, W))
     lib().orc_checker(x, H, W, up_e, up_o, lf_e, lf_o)
     return up_e, up_o, lf_e, lf_o
+
+
+def quad(x):
+    """Ablation Study's Quad downsampling: (TL, TR, BL, BR), each floor(H/2) x floor(W/2)."""
+    x = _f64(x)
+    H, W = x.shape
+    outs = [np.zeros((H // 2, W // 2)) for _ in range(4)]
+    lib().orc_quad(x, H, W, *outs)
+    return tuple(outs)
 
 
 def conv3x3_fwd(inp, wt, b, relu=True):
@@ -216,7 +226,7 @@ class _Params(C.Structure):
                 ("beta2", C.c_double), ("eps", C.c_double), ("patience", C.c_int),
                 ("max_epochs", C.c_int), ("fixed_steps", C.c_int), ("loss_kind", C.c_int),
                 ("incl_best", C.c_int), ("seed", C.c_uint64), ("channels", C.c_int),
-                ("target", C.c_int)]
+                ("target", C.c_int), ("downsample", C.c_int), ("exact", C.c_int)]
 
 
 @dataclasses.dataclass
@@ -235,11 +245,14 @@ class Params:
 
     channels: int = 1   # input channels C_0 (Fig. 2a caption: inputs may be multi-channel)
     target: int = 0     # the predicted channel (one output channel per network)
+    downsample: int = 0  # 0 checkerboard, 1 Quad (Ablation Study)
+    exact: bool = False  # Exact (Ablation Study): x carries the clean target plane last
 
     def _c(self):
         return _Params(_widths(self.widths), self.lr, self.beta1, self.beta2, self.eps,
                        self.patience, self.max_epochs, self.fixed_steps, self.loss_kind,
-                       int(self.incl_best), self.seed, self.channels, self.target)
+                       int(self.incl_best), self.seed, self.channels, self.target,
+                       self.downsample, int(self.exact))
 
 
 class Job:
@@ -250,7 +263,8 @@ class Job:
         x = _f64(x)
         if x.ndim == 2:
             x = x[None]
-        assert x.shape[0] == max(1, params.channels) and 0 <= params.target < x.shape[0]
+        c0 = max(1, params.channels)
+        assert x.shape[0] == c0 + int(params.exact) and 0 <= params.target < c0
         _, self.H, self.W = x.shape
         x = np.ascontiguousarray(x)
         self.params = params

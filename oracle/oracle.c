@@ -91,6 +91,19 @@ void orc_checker(const double* x, int H, int W, double* up_e, double* up_o, doub
     }
 }
 
+/* Ablation Study, "Quad": the image cut into 2x2 blocks and four images made of the blocks'
+ * top-left, top-right, bottom-left and bottom-right pixels, floor(H/2) x floor(W/2) each.    */
+void orc_quad(const double* x, int H, int W, double* tl, double* tr, double* bl, double* br) {
+  const int hh = H / 2, hw = W / 2;
+  for (int i = 0; i < hh; ++i)
+    for (int j = 0; j < hw; ++j) {
+      tl[i * hw + j] = x[(2 * i) * W + 2 * j];
+      tr[i * hw + j] = x[(2 * i) * W + 2 * j + 1];
+      bl[i * hw + j] = x[(2 * i + 1) * W + 2 * j];
+      br[i * hw + j] = x[(2 * i + 1) * W + 2 * j + 1];
+    }
+}
+
 /* ------------------------------------------------------------------------------------------ */
 /* 3x3 convolution with zero "same" padding, forward.                                         */
 void orc_conv3x3_fwd(const double* in, int cin, int h, int w, const double* wt, const double* b,
@@ -279,6 +292,7 @@ struct orc_job {
   int ph[4], pw[4];
   double* pin[4]; /* pair inputs */
   double* ptg[4]; /* pair targets (channel tc of the paired sub-image, table order) */
+  double* ptx[4]; /* Exact ablation: the adjusted targets (owned) */
   double* sub[4]; /* up_e, up_o, lf_e, lf_o; c0 planes each */
   size_t np;
   double *theta, *grad, *m, *v;
@@ -307,27 +321,50 @@ orc_job* orc_job_new(const double* x, int H, int W, const orc_params* p) {
   j->c0 = p->channels > 0 ? p->channels : 1;
   j->tc = p->target;
   const size_t N = (size_t)H * W;
-  j->x = dalloc((size_t)j->c0 * N);
-  memcpy(j->x, x, sizeof(double) * j->c0 * N);
-  j->ph[0] = j->ph[1] = H;
-  j->pw[0] = j->pw[1] = W / 2;
-  j->ph[2] = j->ph[3] = H / 2;
-  j->pw[2] = j->pw[3] = W;
+  /* x holds the C_0 input planes and, for the Exact ablation, the clean target plane after them */
+  const int nplanes = j->c0 + (p->exact ? 1 : 0);
+  j->x = dalloc((size_t)nplanes * N);
+  memcpy(j->x, x, sizeof(double) * nplanes * N);
+  const int quad = p->downsample == 1;
+  for (int k = 0; k < 4; ++k) {
+    j->ph[k] = quad ? H / 2 : (k < 2 ? H : H / 2);
+    j->pw[k] = quad ? W / 2 : (k < 2 ? W / 2 : W);
+  }
   size_t P[4];
   for (int k = 0; k < 4; ++k) {
     P[k] = (size_t)j->ph[k] * j->pw[k];
-    j->sub[k] = dalloc((size_t)j->c0 * P[k]);
+    j->sub[k] = dalloc((size_t)nplanes * P[k]);
   }
-  /* every input channel is downsampled the same way */
-  for (int c = 0; c < j->c0; ++c)
-    orc_checker(j->x + c * N, H, W, j->sub[0] + c * P[0], j->sub[1] + c * P[1],
-                j->sub[2] + c * P[2], j->sub[3] + c * P[3]);
-  /* Methods table: (x_even -> x_odd), (x_odd -> x_even), (x'_even -> x'_odd), (x'_odd -> x'_even);
-   * the target is the predicted channel of the paired sub-image (Fig. 2a caption: one output
-   * channel per network) */
+  /* every plane is downsampled the same way. Checkerboard: sub = up_e, up_o, lf_e, lf_o and the
+   * Methods table's pairs k -> k^1. Quad (the reading taken: the pairs go once round the 2x2
+   * block through horizontally and vertically adjacent pixels): sub = TL, TR, BR, BL and the
+   * pairs k -> k+1 mod 4, i.e. TL->TR, TR->BR, BR->BL, BL->TL. */
+  int tgt_of[4];
+  for (int c = 0; c < nplanes; ++c) {
+    const double* xc = j->x + c * N;
+    if (quad)
+      orc_quad(xc, H, W, j->sub[0] + c * P[0], j->sub[1] + c * P[1], j->sub[3] + c * P[3],
+               j->sub[2] + c * P[2]);
+    else
+      orc_checker(xc, H, W, j->sub[0] + c * P[0], j->sub[1] + c * P[1], j->sub[2] + c * P[2],
+                  j->sub[3] + c * P[3]);
+  }
+  for (int k = 0; k < 4; ++k) tgt_of[k] = quad ? (k + 1) % 4 : k ^ 1;
+  /* the target is the predicted channel of the paired sub-image (Fig. 2a caption: one output
+   * channel per network). Exact ablation: the signal difference s_tgt - s_in (the s_odd - s_even
+   * term of the Theoretical Background) is subtracted using the clean plane,
+   * target = x_tgt - (s_tgt - s_in). */
   for (int k = 0; k < 4; ++k) {
+    const int g = tgt_of[k];
     j->pin[k] = j->sub[k];
-    j->ptg[k] = j->sub[k ^ 1] + (size_t)j->tc * P[k ^ 1];
+    j->ptg[k] = j->sub[g] + (size_t)j->tc * P[g];
+    if (p->exact) {
+      j->ptx[k] = dalloc(P[k]);
+      const double* sg = j->sub[g] + (size_t)j->c0 * P[g];
+      const double* sk = j->sub[k] + (size_t)j->c0 * P[k];
+      for (size_t i = 0; i < P[k]; ++i) j->ptx[k][i] = j->ptg[k][i] - (sg[i] - sk[i]);
+      j->ptg[k] = j->ptx[k];
+    }
   }
   j->np = orc_param_count_c(p->widths, j->c0);
   j->theta = dalloc(j->np);
@@ -545,7 +582,10 @@ void orc_job_info(const orc_job* j, long* t, int* epoch, int* since, int* stoppe
 void orc_job_free(orc_job* j) {
   if (!j) return;
   free(j->x);
-  for (int k = 0; k < 4; ++k) free(j->sub[k]);
+  for (int k = 0; k < 4; ++k) {
+    free(j->sub[k]);
+    free(j->ptx[k]);
+  }
   free(j->theta); free(j->grad); free(j->m); free(j->v);
   for (int l = 0; l < ORC_LAYERS; ++l) { free(j->act[l]); free(j->delta[l]); }
   free(j->z); free(j->dz); free(j->S); free(j->Vbest); free(j->V);

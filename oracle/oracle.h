@@ -57,6 +57,11 @@ void orc_init_params(const int widths[ORC_LAYERS], uint64_t seed, double* theta)
 void orc_checker(const double* x, int H, int W, double* up_e, double* up_o, double* lf_e,
                  double* lf_o);
 
+/* Ablation Study, "Quad": 2x2 blocks -> the images of their top-left, top-right, bottom-left
+ * and bottom-right pixels, floor(H/2) x floor(W/2) each:
+ *   tl(i,j) = x(2i, 2j), tr(i,j) = x(2i, 2j+1), bl(i,j) = x(2i+1, 2j), br(i,j) = x(2i+1, 2j+1) */
+void orc_quad(const double* x, int H, int W, double* tl, double* tr, double* bl, double* br);
+
 /* ---- Network pieces (Methods, first paragraph; Fig. 2a) ---------------------------------- */
 /* out[o] = b[o] + sum_c sum_ky sum_kx w[o][c][ky][kx] * in[c](y+ky-1, x+kx-1), then ReLU if relu. */
 void orc_conv3x3_fwd(const double* in, int cin, int h, int w, const double* wt, const double* b,
@@ -108,17 +113,24 @@ typedef struct {
   int channels;                 /* input channels C_0 (0 or 1: a grayscale image) */
   int target;                   /* the predicted channel, 0 .. C_0 - 1 (Fig. 2a caption: an RGB
                                    image is denoised one output channel per network) */
+  int downsample;               /* 0 = checkerboard (the method); 1 = the Ablation Study's Quad */
+  int exact;                    /* 1 = the Ablation Study's Exact: the job's image carries the
+                                   clean target plane after the C_0 input planes, and each
+                                   target becomes x_tgt - (s_tgt - s_in) */
 } orc_params;
 
 typedef struct orc_job orc_job;
 
-/* A job owns the image (C_0 planes of H x W), the four training pairs, theta, Adam moments and
- * the stop state. Each pair's input is all C_0 channels of one sub-image, its target the
- * predicted channel of the paired sub-image; validation compares with that channel of x. */
+/* A job owns the image (C_0 planes of H x W, plus the clean plane for Exact), the four training
+ * pairs, theta, Adam moments and the stop state. Each pair's input is all C_0 channels of one
+ * sub-image, its target the predicted channel of the paired sub-image; validation compares
+ * with that channel of x. Pairs: checkerboard up_e->up_o, up_o->up_e, lf_e->lf_o, lf_o->lf_e
+ * (Methods table); Quad TL->TR, TR->BR, BR->BL, BL->TL (the reading taken: once round the
+ * 2x2 block through adjacent pixels). */
 orc_job* orc_job_new(const double* x, int H, int W, const orc_params* p);
 /* Replace theta (n = orc_param_count values). */
 void orc_job_set_theta(orc_job* j, const double* theta);
-/* One Adam step on pair k (0..3, table order: up_e->up_o, up_o->up_e, lf_e->lf_o, lf_o->lf_e).
+/* One Adam step on pair k (0..3, in the pair order above).
  * Returns the training loss before the update. Keeps activations, deltas and grads for inspection. */
 double orc_job_step(orc_job* j, int pair);
 /* Full-image validation forward; writes V (H*W) if v != NULL; returns mean((V - x)^2). */

@@ -498,3 +498,84 @@ def test_multichannel_reduces_to_one_channel():
     job.step(0)
     gw1 = oracle.unpack(TINY, job.get(oracle.GRAD), 3)[0][0]
     assert np.all(gw1[:, 1:] == 0.0) and np.any(gw1[:, 0] != 0.0)
+
+
+# ---------------------------------------------------------------- ablations (Quad, Exact) --
+
+def _load_golden(name):
+    out = {}
+    for line in open(os.path.join(GOLD, name)):
+        if line.startswith("#") or not line.strip():
+            continue
+        k, rows = line.split(":")
+        out[k.strip()] = np.array([[float(v) for v in r.split(",")] for r in rows.split("|")])
+    return out
+
+
+def test_quad_hand_example():
+    g = _load_golden("quad_4x4.txt")
+    got = dict(zip(("tl", "tr", "bl", "br"), oracle.quad(np.arange(16.0).reshape(4, 4))))
+    for k in g:
+        assert np.array_equal(got[k], g[k]), k
+    assert sum(v.sum() for v in got.values()) == 120
+
+
+@pytest.mark.parametrize("H,W", [(2, 2), (4, 6), (7, 9), (5, 4), (2, 130)])
+def test_quad_partition_and_slices(H, W):
+    # The four images are the strided slices of the even crop and partition its pixels.
+    x = np.arange(H * W, dtype=np.float64).reshape(H, W)
+    tl, tr, bl, br = oracle.quad(x)
+    crop = x[: H // 2 * 2, : W // 2 * 2]
+    assert np.array_equal(tl, crop[0::2, 0::2]) and np.array_equal(tr, crop[0::2, 1::2])
+    assert np.array_equal(bl, crop[1::2, 0::2]) and np.array_equal(br, crop[1::2, 1::2])
+    vals = np.sort(np.concatenate([a.ravel() for a in (tl, tr, bl, br)]))
+    assert np.array_equal(vals, np.sort(crop.ravel()))
+
+
+def test_quad_pairs_go_round_the_block():
+    # The reading taken for Quad's training pairs: TL->TR, TR->BR, BR->BL, BL->TL (every image
+    # once as input and once as target, each pair of horizontally or vertically adjacent
+    # pixels); one step against the float64 torch model on each pair.
+    r = _rng(19)
+    x = r.uniform(0, 1, size=(8, 10))
+    tl, tr, bl, br = oracle.quad(x)
+    want = [(tl, tr), (tr, br), (br, bl), (bl, tl)]
+    job = oracle.Job(x, oracle.Params(widths=TINY, seed=2, downsample=1))
+    parts, fwd = _torch_net(TINY, job.get(oracle.THETA))
+    params = [t for wb in parts for t in wb]
+    opt = torch.optim.Adam(params, lr=1e-3, betas=(0.9, 0.999), eps=1e-8)
+    for pair in range(4):
+        inp = job.get(oracle.PAIR_IN, pair).reshape(4, 5)
+        tgt = job.get(oracle.PAIR_TGT, pair).reshape(4, 5)
+        assert np.array_equal(inp, want[pair][0]) and np.array_equal(tgt, want[pair][1])
+        opt.zero_grad()
+        L = F.binary_cross_entropy_with_logits(fwd(inp), torch.tensor(tgt))
+        L.backward()
+        assert abs(job.step(pair) - L.item()) < 1e-12
+        g = np.concatenate([t.grad.numpy().ravel() for t in params])
+        np.testing.assert_allclose(job.get(oracle.GRAD), g, rtol=1e-9, atol=1e-14)
+        opt.step()
+
+
+@pytest.mark.parametrize("downsample", [0, 1])
+def test_exact_targets(downsample):
+    # Ablation Study, Exact: the target x_tgt minus the signal difference s_tgt - s_in, taken
+    # from the clean image downsampled the same way. A zero or constant clean image leaves the
+    # targets unchanged; otherwise they equal the difference computed here from the sub-images.
+    r = _rng(20)
+    x = r.uniform(0, 1, size=(8, 8))
+    s = r.uniform(0, 1, size=(8, 8))
+    split = oracle.checker if downsample == 0 else (lambda a: (lambda q: (q[0], q[1], q[3], q[2]))(oracle.quad(a)))
+    order = [1, 0, 3, 2] if downsample == 0 else [1, 2, 3, 0]
+    base = oracle.Job(x, oracle.Params(widths=TINY, downsample=downsample))
+    for clean in (np.zeros_like(x), np.full_like(x, 0.375)):
+        j = oracle.Job(np.stack([x, clean]), oracle.Params(widths=TINY, downsample=downsample,
+                                                            exact=True))
+        for k in range(4):
+            assert np.array_equal(j.get(oracle.PAIR_TGT, k), base.get(oracle.PAIR_TGT, k))
+            assert np.array_equal(j.get(oracle.PAIR_IN, k), base.get(oracle.PAIR_IN, k))
+    j = oracle.Job(np.stack([x, s]), oracle.Params(widths=TINY, downsample=downsample, exact=True))
+    xs, ss = split(x), split(s)
+    for k in range(4):
+        g = order[k]
+        np.testing.assert_array_equal(j.get(oracle.PAIR_TGT, k), (xs[g] - (ss[g] - ss[k])).ravel())
