@@ -99,6 +99,8 @@ typedef struct {
                                 Per-launch kernel timing always launches one by one. */
 } n2f_config;
 
+enum n2f_downsample { N2F_DOWN_CHECKER = 0, N2F_DOWN_QUAD = 1 };
+
 /* Per-image parameters. Defaults (n2f_params_default) follow the Methods section; the Adam
  * moments and epsilon are Kingma & Ba's defaults (the paper cites Adam without them). */
 typedef struct {
@@ -123,6 +125,15 @@ typedef struct {
    * compares with that plane of the image. The result is one H*W plane. */
   int32_t channels;
   int32_t target_channel;
+  /* Ablation Study variants (not the method; for comparisons on synthetic data):
+   * downsample = N2F_DOWN_QUAD replaces the checkerboard sub-images by the four images of the
+   * 2x2 blocks' top-left, top-right, bottom-right and bottom-left pixels (floor(H/2) x
+   * floor(W/2)), trained on the pairs TL->TR, TR->BR, BR->BL, BL->TL (a reading: the paper
+   * names the four images, not the pairs). exact = 1 takes the clean (ground-truth) plane of the
+   * predicted channel as one more plane after the input planes and trains on the targets
+   * x_tgt - (s_tgt - s_in), removing the signal-difference term of the Theoretical Background. */
+  int32_t downsample;   /* enum n2f_downsample */
+  int32_t exact;
 } n2f_params;
 
 typedef struct {

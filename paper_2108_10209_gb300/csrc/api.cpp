@@ -54,6 +54,8 @@ void n2f_params_default(n2f_params* p) {
   p->engine = N2F_ENGINE_AUTO;
   p->channels = 1;
   p->target_channel = 0;
+  p->downsample = N2F_DOWN_CHECKER;
+  p->exact = 0;
 }
 
 const char* n2f_strerror(int code) {
@@ -95,11 +97,15 @@ static int check_params(const n2f_params* p) {
   if (p->channels < 0 || p->channels > kMaxC0) return N2F_EINVAL;
   if (p->target_channel < 0 || p->target_channel >= std::max(1, (int)p->channels))
     return N2F_EINVAL;
+  if (p->downsample != N2F_DOWN_CHECKER && p->downsample != N2F_DOWN_QUAD) return N2F_EINVAL;
+  if (p->exact != 0 && p->exact != 1) return N2F_EINVAL;
   return N2F_OK;
 }
 
-// input planes of a job
-static size_t planes(const n2f_params* p) { return (size_t)std::max(1, (int)p->channels); }
+// planes of a job's image: the input channels, then the clean plane for the Exact ablation
+static size_t planes(const n2f_params* p) {
+  return (size_t)std::max(1, (int)p->channels) + (p->exact ? 1 : 0);
+}
 
 static int check_image(int H, int W) {
   if (H < 2 || W < 2) return N2F_EINVAL;
@@ -755,7 +761,7 @@ static int submit_common(n2f_ctx* c, int kind, const void* image, int H, int W,
   int rc = check_params(p);
   if (rc) return rc;
   if ((rc = check_image(H, W))) return rc;
-  if (kind == 2 && planes(p) != 1) return N2F_EINVAL;  // 16-bit input: one plane
+  if (kind == 2 && planes(p) != 1) return N2F_EINVAL;  // 16-bit input: one plane, no clean plane
   const size_t n = (size_t)H * W * planes(p);
   if (kind == 0) {
     const float* f = (const float*)image;

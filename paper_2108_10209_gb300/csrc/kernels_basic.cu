@@ -51,6 +51,52 @@ cudaError_t launch_gather(const float* x, int H, int W, float* ue, float* uo, fl
   N2F_LAUNCH_CHECK();
 }
 
+// Ablation Study, "Quad": 2x2 blocks -> the images of their top-left, top-right, bottom-right
+// and bottom-left pixels (stored in that order: the training pairs go k -> k+1 mod 4), each
+// floor(H/2) x floor(W/2). Pure copies, bit-exact.
+__global__ void k_gather_quad(const float* __restrict__ x, int H, int W, float* __restrict__ tl,
+                              float* __restrict__ tr, float* __restrict__ br,
+                              float* __restrict__ bl) {
+  const int hh = H >> 1, hw = W >> 1;
+  const size_t n = (size_t)hh * hw;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / hw), j = (int)(t % hw);
+    const float* r0 = x + (size_t)(2 * i) * W + 2 * j;
+    const float* r1 = r0 + W;
+    tl[t] = r0[0];
+    tr[t] = r0[1];
+    bl[t] = r1[0];
+    br[t] = r1[1];
+  }
+}
+
+cudaError_t launch_gather_quad(const float* x, int H, int W, float* tl, float* tr, float* br,
+                               float* bl, cudaStream_t st) {
+  const size_t n = (size_t)(H / 2) * (W / 2);
+  unsigned g = nblocks(n, 256);
+  if (g > 152u * 16) g = 152u * 16;
+  k_gather_quad<<<g, 256, 0, st>>>(x, H, W, tl, tr, br, bl);
+  N2F_LAUNCH_CHECK();
+}
+
+// Ablation Study, "Exact": target = x_tgt - (s_tgt - s_in), the signal difference taken from
+// the clean image's sub-images (the s_odd - s_even term of the Theoretical Background).
+__global__ void k_exact_target(const float* __restrict__ xt, const float* __restrict__ st_,
+                               const float* __restrict__ si, size_t n, float* __restrict__ out) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    out[i] = xt[i] - (st_[i] - si[i]);
+}
+
+cudaError_t launch_exact_target(const float* xt, const float* s_tgt, const float* s_in, size_t n,
+                                float* out, cudaStream_t st) {
+  unsigned g = nblocks(n, 256);
+  if (g > 152u * 16) g = 152u * 16;
+  k_exact_target<<<g, 256, 0, st>>>(xt, s_tgt, s_in, n, out);
+  N2F_LAUNCH_CHECK();
+}
+
 // Maximum projection along Z of independently denoised slices (Methods, fluorescence
 // microscopy). vol: Z planes of n floats; four pixels per thread when n and both pointers
 // allow 16-byte accesses. Exact (a comparison, no rounding).

@@ -70,6 +70,10 @@ struct PackArgs {
 };
 
 // ---- kernel launchers (kernels_*.cu); all enqueue on `st` and return cudaError_t ----------
+cudaError_t launch_gather_quad(const float* x, int H, int W, float* tl, float* tr, float* br,
+                               float* bl, cudaStream_t st);
+cudaError_t launch_exact_target(const float* xt, const float* s_tgt, const float* s_in, size_t n,
+                                float* out, cudaStream_t st);
 cudaError_t launch_max_project(const float* vol, int Z, size_t n, float* out, cudaStream_t st);
 cudaError_t launch_gather(const float* x, int H, int W, float* ue, float* uo, float* le, float* lo,
                           cudaStream_t st);

@@ -170,9 +170,10 @@ static size_t layout(Trainer* t, char* base) {
   c.base = base;
   const NetShape& net = t->net;
   const size_t es = t->bf16 ? 2 : 4;
-  const size_t c0 = (size_t)net.c0;
-  t->x = c.take<float>(c0 * t->N);
-  for (int k = 0; k < 4; ++k) t->sub[k] = c.take<float>(c0 * t->ph[k] * t->pw[k]);
+  const size_t np = (size_t)t->nplanes;
+  t->x = c.take<float>(np * t->N);
+  for (int k = 0; k < 4; ++k) t->sub[k] = c.take<float>(np * t->ph[k] * t->pw[k]);
+  for (int k = 0; k < 4; ++k) t->tx[k] = c.take<float>(t->prm.exact ? (size_t)t->ph[k] * t->pw[k] : 0);
   t->theta = c.take<float>(net.count);
   t->grad = c.take<float>(net.count);
   t->m = c.take<float>(net.count);
@@ -242,12 +243,17 @@ int trainer_configure(Trainer* t, int H, int W, const n2f_params* p, int keep_de
   t->H = H;
   t->W = W;
   t->N = (size_t)H * W;
-  t->ph[0] = t->ph[1] = H;
-  t->pw[0] = t->pw[1] = W / 2;
-  t->ph[2] = t->ph[3] = H / 2;
-  t->pw[2] = t->pw[3] = W;
-  t->maxP = std::max((size_t)H * (W / 2), (size_t)(H / 2) * W);
+  const bool quad = p->downsample == N2F_DOWN_QUAD;
+  for (int k = 0; k < 4; ++k) {
+    t->ph[k] = quad ? H / 2 : (k < 2 ? H : H / 2);
+    t->pw[k] = quad ? W / 2 : (k < 2 ? W / 2 : W);
+    // checkerboard: the Methods table's pairs k -> k^1; Quad: once round the 2x2 block
+    t->tgt_of[k] = quad ? (k + 1) % 4 : k ^ 1;
+  }
+  t->maxP = 0;
+  for (int k = 0; k < 4; ++k) t->maxP = std::max(t->maxP, (size_t)t->ph[k] * t->pw[k]);
   t->net.init(p->widths, p->channels);
+  t->nplanes = t->net.c0 + (p->exact ? 1 : 0);
   t->bf16 = p->precision == N2F_BF16;
   t->keep_deltas = keep_deltas;
   t->fixed_mode = p->fixed_steps >= 0;
@@ -319,12 +325,27 @@ int trainer_start(Trainer* t, int from_u16) {
   LaunchScope ls(&t->launches);
   cudaStream_t st = t->st;
   if (from_u16) CK(launch_u16_to_f32(t->in_u16, t->x, t->N, st));
-  // every input channel is downsampled the same way
-  for (int c = 0; c < t->net.c0; ++c) {
+  // every plane is downsampled the same way
+  for (int c = 0; c < t->nplanes; ++c) {
     size_t P[4];
     for (int k = 0; k < 4; ++k) P[k] = (size_t)c * t->ph[k] * t->pw[k];
-    CK(launch_gather(t->x + (size_t)c * t->N, t->H, t->W, t->sub[0] + P[0], t->sub[1] + P[1],
-                     t->sub[2] + P[2], t->sub[3] + P[3], st));
+    const float* xc = t->x + (size_t)c * t->N;
+    if (t->prm.downsample == N2F_DOWN_QUAD)
+      CK(launch_gather_quad(xc, t->H, t->W, t->sub[0] + P[0], t->sub[1] + P[1], t->sub[2] + P[2],
+                            t->sub[3] + P[3], st));
+    else
+      CK(launch_gather(xc, t->H, t->W, t->sub[0] + P[0], t->sub[1] + P[1], t->sub[2] + P[2],
+                       t->sub[3] + P[3], st));
+  }
+  if (t->prm.exact) {
+    // targets x_tgt - (s_tgt - s_in): the clean plane is the last plane of every sub-image
+    for (int k = 0; k < 4; ++k) {
+      const int g = t->tgt_of[k];
+      const size_t Pg = (size_t)t->ph[g] * t->pw[g], Pk = (size_t)t->ph[k] * t->pw[k];
+      CK(launch_exact_target(t->sub[g] + (size_t)t->prm.target_channel * Pg,
+                             t->sub[g] + (size_t)t->net.c0 * Pg, t->sub[k] + (size_t)t->net.c0 * Pk,
+                             Pk, t->tx[k], st));
+    }
   }
   CK(launch_init_params(t->theta, t->net, t->prm.seed, st));
   CK(cudaMemsetAsync(t->m, 0, t->net.count * sizeof(float), st));
@@ -382,9 +403,11 @@ int trainer_step(Trainer* t, int pair) {
   const NetShape& net = t->net;
   const int* skip = t->fixed_mode ? nullptr : &t->state->stopped;
   const float* in = t->sub[pair];
-  // Methods table: even <-> odd of the same kind; the target is the predicted channel
-  const float* tgt =
-      t->sub[pair ^ 1] + (size_t)t->prm.target_channel * t->ph[pair ^ 1] * t->pw[pair ^ 1];
+  // Methods table: even <-> odd of the same kind (Quad: the next image round the block); the
+  // target is the predicted channel (Exact: with the signal difference removed)
+  const int g = t->tgt_of[pair];
+  const float* tgt = t->prm.exact ? t->tx[pair]
+                                  : t->sub[g] + (size_t)t->prm.target_channel * t->ph[g] * t->pw[g];
   t->last_pair = pair;
   // forward, keeping every post-ReLU map
   const void* cur = in;

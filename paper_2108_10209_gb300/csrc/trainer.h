@@ -58,7 +58,10 @@ struct Trainer {
   n2f_params prm;
   int H = 0, W = 0;
   size_t N = 0;
-  int ph[4], pw[4];  // pair sizes: up (H x W/2) twice, left (H/2 x W) twice
+  int ph[4], pw[4];  // sub-image sizes: up (H x W/2) twice, left (H/2 x W) twice; Quad H/2 x W/2
+  int tgt_of[4];     // pair k trains sub-image k -> sub-image tgt_of[k]
+  int nplanes = 1;   // planes of x and of every sub-image: input channels (+ the clean plane)
+  float* tx[4] = {nullptr, nullptr, nullptr, nullptr};  // Exact: the adjusted targets
   size_t maxP = 0;
   int bf16 = 0, keep_deltas = 0, fixed_mode = 0, want_u16 = 0;
   int engine[kLayers];     // forward / dgrad kernels of layer l

@@ -22,6 +22,7 @@ N2F_FP32, N2F_BF16 = 0, 1
 N2F_LOSS_BCE, N2F_LOSS_MSE = 0, 1
 N2F_WIDTHS_PLIT, N2F_WIDTHS_W64 = 0, 1
 N2F_ENGINE_AUTO, N2F_ENGINE_SIMT, N2F_ENGINE_TC = 0, 1, 2
+N2F_DOWN_CHECKER, N2F_DOWN_QUAD = 0, 1
 N2F_QUEUED, N2F_RUNNING, N2F_DONE, N2F_FAILED, N2F_CANCELED = range(5)
 (N2F_X_THETA, N2F_X_GRAD, N2F_X_ADAM_M, N2F_X_ADAM_V, N2F_X_ACT, N2F_X_DELTA) = range(6)
 N2F_X_DZ, N2F_X_PAIR, N2F_X_VAL, N2F_X_SUM, N2F_X_OUT = 7, 8, 9, 10, 11
@@ -45,7 +46,7 @@ class Params(C.Structure):
                 ("max_epochs", C.c_uint32), ("fixed_steps", C.c_int32), ("seed", C.c_uint64),
                 ("precision", C.c_int32), ("loss", C.c_int32), ("widths", C.c_int32),
                 ("incl_best", C.c_int32), ("engine", C.c_int32), ("channels", C.c_int32),
-                ("target_channel", C.c_int32)]
+                ("target_channel", C.c_int32), ("downsample", C.c_int32), ("exact", C.c_int32)]
 
 
 class Status(C.Structure):
@@ -223,7 +224,8 @@ class Context:
         self.close()
 
     def submit(self, image: np.ndarray, p: Params | None = None) -> int:
-        """image: (H, W), or (C_0, H, W) planes with p.channels = C_0."""
+        """image: (H, W), or (planes, H, W): the p.channels input planes, then the clean plane
+        when p.exact (Ablation Study)."""
         img = np.ascontiguousarray(image, dtype=np.float32)
         H, W = img.shape[-2:]
         job = C.c_uint64()
