@@ -478,6 +478,57 @@ def run_zstack(args, n2f):
     }
 
 
+def run_variants(args, n2f):
+    """The Ablation Study's comparison on synthetic data (Table 1's Normal / Quad / Exact
+    columns; the U-net column is out of scope) plus an RGB image denoised one channel per
+    network (Fig. 2a caption). Every variant runs the same images (512x512 ellipse cells,
+    Gaussian sigma 25/255 and 50/255) under the stopping rule; reported: images/s and PSNR."""
+    import numpy as np
+    from paper_2108_10209_gb300 import synth
+    S = args.size
+    imgs = [synth.image_cells(S, S, sigma=sg / 255.0, seed=6_000_000 + i)
+            for i, sg in enumerate((25, 50))]
+    base = dict(seed=0, precision=args.precision, widths=args.widths, engine=args.engine)
+    rows = {}
+    with n2f.Context() as ctx:
+        n2f.denoise(synth.image_cells(256, 256, seed=7)[1].astype(np.float32), n2f.params(**base),
+                    ctx)
+        for name, kw, extra in (("normal", {}, False), ("quad", {"downsample": 1}, False),
+                                ("exact", {"exact": 1}, True)):
+            t0 = time.perf_counter()
+            ps = []
+            for clean, noisy in imgs:
+                img = noisy.astype(np.float32)
+                if extra:
+                    img = np.stack([img, clean.astype(np.float32)])
+                out = n2f.denoise(img, n2f.params(**base, **kw), ctx)
+                ps.append(synth.psnr(out.astype(np.float64), clean))
+            dt = time.perf_counter() - t0
+            rows[name] = {"images_per_s": len(imgs) / dt, "psnr_db": ps}
+        # RGB: three channels of independent cell images, one network per output channel
+        cl = np.stack([synth.ellipses(S, S, seed=6_100_000 + c) for c in range(3)])
+        no = (cl + synth.rng(6_200_000).normal(0, 25 / 255.0, cl.shape)).astype(np.float32)
+        t0 = time.perf_counter()
+        out = n2f.denoise_channels(no, n2f.params(**base), ctx)
+        dt = time.perf_counter() - t0
+        rows["rgb"] = {"images_per_s": 1.0 / dt,
+                       "psnr_db": [synth.psnr(out[c].astype(np.float64), cl[c]) for c in range(3)],
+                       "noisy_psnr_db": [synth.psnr(no[c].astype(np.float64), cl[c])
+                                         for c in range(3)]}
+    return {
+        "metric": METRIC, "value": rows["normal"]["images_per_s"], "unit": UNIT, "n_gpus": 1,
+        "steps": len(imgs), "warmup": 1, "ms_per_step": 1e3 / rows["normal"]["images_per_s"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16 (f32 accumulate)" if args.precision else "f32",
+        "data": "synthetic (ellipse cells + Gaussian noise, seeded)",
+        "config": {"workload": f"{S}x{S} cells, sigma 25/255 and 50/255: the method, Quad and "
+                               "Exact ablations, and an RGB image (three networks)",
+                   "widths": WIDTH_NAMES[args.widths],
+                   "precision": "bf16" if args.precision else "fp32"},
+        "variants": rows,
+    }
+
+
 # ---------------------------------------------------------------------------- reference arm -
 
 def run_reference(args, ws, rank):
@@ -526,7 +577,8 @@ def main():
                     help="kernel class timed for the roofline (7 conv forward+dgrad, 1 forward, "
                          "2 dgrad, 3 wgrad)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--form", default="plain", choices=["plain", "batched", "serving", "zstack"])
+    ap.add_argument("--form", default="plain",
+                    choices=["plain", "batched", "serving", "zstack", "variants"])
     ap.add_argument("--compare-batch", type=int, default=16,
                     help="plain form: also run this many images in the bf16 form together (0 = off)")
     ap.add_argument("--jobs", type=int, default=64, help="batched / serving: number of images")
@@ -553,7 +605,8 @@ def main():
             import __graft_entry__ as g
             g.build()
             from paper_2108_10209_gb300 import n2f
-            run = {"batched": run_batched, "serving": run_serving, "zstack": run_zstack}[args.form]
+            run = {"batched": run_batched, "serving": run_serving, "zstack": run_zstack,
+                   "variants": run_variants}[args.form]
             line = run(args, n2f)
             if rank != 0:
                 line = None
