@@ -366,9 +366,12 @@ def run_batched(args, n2f):
     U[15, 50]/255, all submitted at once; stopping rule each."""
     from paper_2108_10209_gb300 import synth
     jobs = synth.batch_jobs(args.jobs)
+    if args.side:  # every job args.side x args.side instead of the size mix
+        for j in jobs:
+            j["h"] = j["w"] = args.side
     imgs = [synth.image_cells(j["h"], j["w"], sigma=j["sigma"], seed=j["seed"]) for j in jobs]
     p = n2f.params(seed=0, precision=args.precision, widths=args.widths, engine=args.engine)
-    with n2f.Context(max_slots=args.jobs) as ctx:
+    with n2f.Context(max_slots=args.jobs, group_size=args.group) as ctx:
         warm = synth.image_cells(256, 256, seed=7)
         run_jobs(ctx, n2f, [warm[1].astype("float32")], lambda _: p)
         st0 = ctx.stats()
@@ -382,10 +385,15 @@ def run_batched(args, n2f):
         "warmup": 1, "ms_per_step": dev_s * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16 (f32 accumulate)" if args.precision else "f32",
         "data": "synthetic (ellipse cells + Gaussian noise, seeded)",
-        "config": {"workload": f"{args.jobs} jobs, sizes uniform over 256x256, 512x512, 768x512, "
-                               "1024x768, sigma U[15,50]/255, stopping rule, all in flight",
+        "config": {"workload": (f"{args.jobs} jobs of {args.side}x{args.side}" if args.side else
+                                f"{args.jobs} jobs, sizes uniform over 256x256, 512x512, "
+                                "768x512, 1024x768") +
+                               ", sigma U[15,50]/255, stopping rule, all in flight",
                    "widths": WIDTH_NAMES[args.widths],
-                   "precision": "bf16" if args.precision else "fp32", "jobs_in_flight": args.jobs},
+                   "precision": "bf16" if args.precision else "fp32", "jobs_in_flight": args.jobs,
+                   "grouping": (f"lockstep groups of up to {args.group}: one grouped tensor-core "
+                                "launch per conv phase, one epoch graph per group")
+                   if args.group > 1 else "one stream and one epoch graph per job"},
         "latency_ms": {"p50": pct(lat, 0.5), "p99": pct(lat, 0.99)},
         "megapixels": mpx, "mpx_per_s": mpx / dev_s,
         "e2e": {"value": len(res) / host_s, "unit": UNIT,
@@ -433,7 +441,7 @@ def run_zstack(args, n2f):
     clean, noisy = synth.volume_cells(Z, S, S, seed=5_000_000)
     noisy32 = noisy.astype(np.float32)
     p = n2f.params(seed=0, precision=args.precision, widths=args.widths, engine=args.engine)
-    with n2f.Context(max_slots=Z) as ctx:
+    with n2f.Context(max_slots=Z, group_size=args.group) as ctx:
         warm = synth.image_cells(256, 256, seed=7)[1].astype(np.float32)
         n2f.denoise(warm, p, ctx)
         st0 = ctx.stats()
@@ -586,6 +594,10 @@ def main():
     ap.add_argument("--slots", type=int, default=64, help="serving: jobs resident at once")
     ap.add_argument("--max-side", type=int, default=2048, help="serving: largest image side")
     ap.add_argument("--z", type=int, default=41, help="zstack: slices")
+    ap.add_argument("--side", type=int, default=0,
+                    help="batched: every job side x side instead of the size mix")
+    ap.add_argument("--group", type=int, default=0,
+                    help="batched / zstack: lockstep group size (n2f_config.group_size), 0 = off")
     ap.add_argument("--stack-side", type=int, default=1024, help="zstack: slice side")
     args = ap.parse_args()
     os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))

@@ -95,8 +95,15 @@ typedef struct {
   void* alloc_user;
   int32_t profile_kernel;    /* enum n2f_kernel_class timed per launch (events), 0 = off */
   int32_t use_graphs;        /* 1: each job's epoch is captured once as a CUDA graph and
-                                replayed (default); 0: kernels are launched one by one.
-                                Per-launch kernel timing always launches one by one. */
+                                replayed (default); 0: kernels are launched one by one. */
+  uint32_t group_size;       /* > 1: jobs admitted together with identical parameters (stopping
+                                rule, not fixed steps) run in lockstep groups of up to this many
+                                on one stream, the tensor-core forward and dgrad of each layer
+                                as ONE persistent launch over all members' tiles, each member
+                                with its own weights, size and stop flag; the group's epoch is
+                                one CUDA graph. A member's result is ready when every member of
+                                its group has stopped. Grouped jobs are not kernel-timed.
+                                0 or 1: every job alone (default). */
 } n2f_config;
 
 enum n2f_downsample { N2F_DOWN_CHECKER = 0, N2F_DOWN_QUAD = 1 };

@@ -420,8 +420,11 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+struct Group;
+
 struct Job {
   n2f_job id = 0;
+  Group* grp = nullptr;  // lockstep group (nullptr: the job runs alone)
   int H = 0, W = 0;
   n2f_params prm;
   int src_kind = 0;  // 0 host f32, 1 device f32, 2 host u16
@@ -447,6 +450,39 @@ struct Job {
   Clock::time_point t_submit, t_done;
   double device_ms = 0, compute_ms = 0, t0_ms = 0, t1_ms = 0;
 };
+
+// Jobs stepped in lockstep (n2f_config.group_size): one stream, one epoch graph, the grouped
+// tensor-core launches; each member keeps its own state ring for the host's epoch reads.
+struct Group {
+  std::vector<Job*> m;
+  TrainerGroup tg;
+  cudaStream_t st = nullptr;
+  cudaEvent_t ev_ep[8] = {};
+  int ring = 0;
+  uint64_t ep_enq = 0, ep_seen = 0;
+  bool finishing = false, results = false;
+  int fail_rc = 0;    // set when the group failed: every member then finishes with it
+  int remaining = 0;  // references: unfinished members (+ one while the worker sets it up)
+};
+
+void group_unref(Group* g) {
+  if (--g->remaining > 0) return;
+  if (g->st) cudaStreamSynchronize(g->st);
+  group_release(&g->tg);
+  for (int k = 0; k < 8; ++k)
+    if (g->ev_ep[k]) cudaEventDestroy(g->ev_ep[k]);
+  if (g->st) cudaStreamDestroy(g->st);
+  delete g;
+}
+
+// Jobs that may share a group: everything that shapes the kernels and the schedule is equal.
+bool same_group_key(const Job* a, const Job* b) {
+  const n2f_params &p = a->prm, &q = b->prm;
+  return p.precision == q.precision && p.widths == q.widths && p.engine == q.engine &&
+         p.loss == q.loss && p.channels == q.channels && p.downsample == q.downsample &&
+         p.exact == q.exact && p.fixed_steps < 0 && q.fixed_steps < 0 &&
+         a->src_kind != 2 && b->src_kind != 2;
+}
 
 }  // namespace
 
@@ -487,6 +523,11 @@ static void release_device(n2f_ctx* c, Job* j) {
     if (j->ev_ep[k]) cudaEventDestroy(j->ev_ep[k]), j->ev_ep[k] = nullptr;
   for (cudaEvent_t* e : {&j->ev_start, &j->ev_in, &j->ev_out, &j->ev_done})
     if (*e) cudaEventDestroy(*e), *e = nullptr;
+  if (Group* g = j->grp) {
+    j->st = nullptr;  // the group's stream
+    j->grp = nullptr;
+    group_unref(g);
+  }
   if (j->st) cudaStreamDestroy(j->st), j->st = nullptr;
   std::lock_guard<std::mutex> g(c->mu);
   c->bytes_resident -= j->bytes;
@@ -508,12 +549,15 @@ static void finish_job(n2f_ctx* c, Job* j, int state, int err) {
 // Creates the device state of a job and enqueues upload, gather and initialisation.
 static int admit(n2f_ctx* c, Job* j) {
   LaunchScope ls(&c->launches);
-  CKR(cudaStreamCreateWithFlags(&j->st, cudaStreamNonBlocking));
+  if (j->grp)
+    j->st = j->grp->st;
+  else
+    CKR(cudaStreamCreateWithFlags(&j->st, cudaStreamNonBlocking));
   CKR(cudaEventCreate(&j->ev_start));
   CKR(cudaEventCreate(&j->ev_in));
   CKR(cudaEventCreate(&j->ev_out));
   CKR(cudaEventCreate(&j->ev_done));
-  j->kt.kind = c->cfg.profile_kernel;
+  j->kt.kind = j->grp ? N2F_K_NONE : c->cfg.profile_kernel;
   if (j->kt.kind != N2F_K_NONE) j->tr.kt = &j->kt;
   j->ring = (int)std::min<uint32_t>(8, std::max<uint32_t>(2, c->cfg.lookahead + 1));
   for (int k = 0; k < j->ring; ++k) CKR(cudaEventCreateWithFlags(&j->ev_ep[k], cudaEventDisableTiming));
@@ -542,12 +586,91 @@ static int admit(n2f_ctx* c, Job* j) {
   return N2F_OK;
 }
 
+// Advances a lockstep group without blocking (called through its first member).
+static bool group_progress(n2f_ctx* c, Group* g) {
+  bool did = false;
+  int rc = 0;
+  // members finish themselves (in their own progress calls) once the group has failed
+  auto fail_all = [&](int err) { g->fail_rc = err; };
+  while (!g->finishing && g->ep_seen < g->ep_enq) {
+    const int slot = (int)(g->ep_seen % g->ring);
+    const cudaError_t q = cudaEventQuery(g->ev_ep[slot]);
+    if (q == cudaErrorNotReady) break;
+    if (q != cudaSuccess) {
+      set_cuda_error(q, "group epoch");
+      fail_all(N2F_EDEVICE);
+      return true;
+    }
+    int stopped = 0, kerr = 0;
+    for (Job* j : g->m) {
+      {
+        std::lock_guard<std::mutex> lk(c->mu);
+        j->last = j->hst[slot];
+      }
+      stopped += j->last.stopped != 0;
+      kerr |= j->last.kerr;
+    }
+    g->ep_seen += 1;
+    did = true;
+    if (kerr) {
+      tl_error = "a device wait ran out of time";
+      fail_all(N2F_ETIMEDOUT);
+      return true;
+    }
+    if (stopped == (int)g->m.size()) g->finishing = true;
+  }
+  const uint32_t la = std::max<uint32_t>(1, c->cfg.lookahead);
+  while (!g->finishing && g->ep_enq - g->ep_seen < la) {
+    if ((rc = !c->cfg.use_graphs ? group_epoch(&g->tg) : group_epoch_graph(&g->tg))) break;
+    const int slot = (int)(g->ep_enq % g->ring);
+    cudaError_t e = cudaSuccess;
+    for (Job* j : g->m)
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&j->hst[slot], j->tr.state, sizeof(DevState), cudaMemcpyDeviceToHost,
+                            g->st);
+    if (e == cudaSuccess) e = cudaEventRecord(g->ev_ep[slot], g->st);
+    if (e != cudaSuccess) {
+      rc = set_cuda_error(e, "group epoch enqueue");
+      break;
+    }
+    g->ep_enq += 1;
+    did = true;
+  }
+  if (rc) {
+    fail_all(rc);
+    return true;
+  }
+  if (g->finishing && !g->results) {
+    // each member enqueues its result on its own stream, after the group's last epoch
+    cudaError_t e = cudaEventRecord(g->tg.ev_fork, g->st);
+    for (Job* j : g->m)
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(j->st, g->tg.ev_fork, 0);
+    if (e != cudaSuccess) {
+      fail_all(set_cuda_error(e, "group results"));
+      return true;
+    }
+    for (Job* j : g->m) j->finishing = true;
+    g->results = true;
+    did = true;
+  }
+  return did;
+}
+
 // Advances one running job without blocking. Returns true if it enqueued or finished work.
 static bool progress(n2f_ctx* c, Job* j) {
   LaunchScope ls(&c->launches);
   bool did = false;
   int rc = 0;
-  if (j->cancel) {
+  if (j->grp && j->grp->fail_rc) {
+    finish_job(c, j, N2F_FAILED, j->grp->fail_rc);
+    return true;
+  }
+  if (j->grp && !j->result_enq) {
+    // a group member: epochs are the group's; a cancelled member finishes with its group
+    if (j == j->grp->m[0] && group_progress(c, j->grp)) return true;
+    if (!j->finishing) return false;
+  }
+  if (j->cancel && !j->grp) {
     finish_job(c, j, N2F_CANCELED, N2F_ECANCELED);
     return true;
   }
@@ -650,8 +773,11 @@ static bool progress(n2f_ctx* c, Job* j) {
     j->t0_ms = a;
     j->t1_ms = b;
     const bool bad = j->last.stopped == 3 || j->last.kerr;
-    finish_job(c, j, bad ? N2F_FAILED : N2F_DONE,
-               j->last.kerr ? N2F_ETIMEDOUT : (bad ? N2F_ENONFINITE : N2F_OK));
+    if (j->cancel)
+      finish_job(c, j, N2F_CANCELED, N2F_ECANCELED);
+    else
+      finish_job(c, j, bad ? N2F_FAILED : N2F_DONE,
+                 j->last.kerr ? N2F_ETIMEDOUT : (bad ? N2F_ENONFINITE : N2F_OK));
     return true;
   }
   return did;
@@ -681,6 +807,41 @@ static void worker_main(n2f_ctx* c) {
         to_admit.push_back(j);
       }
     }
+    // lockstep groups of jobs admitted together with the same key
+    std::vector<Group*> groups;
+    if (c->cfg.group_size > 1) {
+      std::vector<bool> used(to_admit.size(), false);
+      for (size_t a = 0; a < to_admit.size(); ++a) {
+        if (used[a] || !same_group_key(to_admit[a], to_admit[a])) continue;
+        std::vector<Job*> mem{to_admit[a]};
+        for (size_t b = a + 1; b < to_admit.size() && mem.size() < c->cfg.group_size; ++b)
+          if (!used[b] && same_group_key(to_admit[a], to_admit[b])) {
+            mem.push_back(to_admit[b]);
+            used[b] = true;
+          }
+        if (mem.size() < 2) continue;
+        used[a] = true;
+        Group* g = new Group();
+        g->m = mem;
+        g->remaining = (int)mem.size() + 1;  // + the set-up reference
+        g->ring = (int)std::min<uint32_t>(8, std::max<uint32_t>(2, c->cfg.lookahead + 1));
+        for (Job* j : mem) j->grp = g;
+        groups.push_back(g);
+      }
+    }
+    for (Group* g : groups) {
+      cudaError_t e = cudaStreamCreateWithFlags(&g->st, cudaStreamNonBlocking);
+      for (int k = 0; k < g->ring && e == cudaSuccess; ++k)
+        e = cudaEventCreateWithFlags(&g->ev_ep[k], cudaEventDisableTiming);
+      if (e != cudaSuccess) {  // run the members alone instead
+        for (Job* j : g->m) j->grp = nullptr;
+        g->remaining = 1;
+        group_unref(g);
+      }
+    }
+    groups.erase(std::remove_if(groups.begin(), groups.end(),
+                                [](Group* g) { return g->m.empty() || g->m[0]->grp != g; }),
+                 groups.end());
     for (Job* j : to_admit) {
       {
         std::lock_guard<std::mutex> g(c->mu);
@@ -689,6 +850,21 @@ static void worker_main(n2f_ctx* c) {
       j->state.store(N2F_RUNNING);
       int rc = admit(c, j);
       if (rc) finish_job(c, j, N2F_FAILED, rc);
+    }
+    for (Group* g : groups) {
+      // members that failed at admission left the group; the rest get the grouped tables
+      std::vector<Job*> ok;
+      for (Job* j : g->m)
+        if (j->grp == g) ok.push_back(j);
+      g->m = ok;
+      if (!ok.empty()) {
+        for (Job* j : ok) g->tg.ts.push_back(&j->tr);
+        const int rc = group_init(&g->tg, c->al, g->st);
+        if (rc) g->fail_rc = rc;
+        else
+          for (Job* j : ok) j->st = j->tr.st;  // the member's own stream (owned by the group)
+      }
+      group_unref(g);  // the set-up reference
     }
     std::vector<Job*> act;
     {

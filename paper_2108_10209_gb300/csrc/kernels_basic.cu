@@ -366,14 +366,14 @@ cudaError_t launch_unpack_cg_f64(const void* cg, int C, int H, int W, int bf16, 
 // First layer, C_0 <= 4 input planes (Methods: the first 3x3 convolution sees the image; Fig.
 // 2a caption: the input may be multi-channel). One thread per pixel: 9 C_0 taps from the
 // planes (zero outside), C outputs + bias, ReLU.
-template <typename T>
-__global__ void __launch_bounds__(256) k_conv1_fwd(const float* __restrict__ img, int C0, int H,
-                                                   int W, const float* __restrict__ w,
+template <typename T, int C0>
+__global__ void __launch_bounds__(256) k_conv1_fwd(const float* __restrict__ img, int H, int W,
+                                                   const float* __restrict__ w,
                                                    const float* __restrict__ b, int C,
                                                    T* __restrict__ out, const int* skip) {
   if (skip && *skip) return;
   constexpr int G = CGTraits<T>::G;
-  __shared__ float sw[64 * kMaxC0 * 9], sb[64];
+  __shared__ float sw[64 * C0 * 9], sb[64];
   for (int i = threadIdx.x; i < C * C0 * 9; i += blockDim.x) sw[i] = w[i];
   for (int i = threadIdx.x; i < C; i += blockDim.x) sb[i] = b[i];
   __syncthreads();
@@ -381,15 +381,15 @@ __global__ void __launch_bounds__(256) k_conv1_fwd(const float* __restrict__ img
   const size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (p >= npx) return;
   const int y = (int)(p / W), x = (int)(p % W);
-  float t[kMaxC0][9];
+  float t[C0][9];
 #pragma unroll
-  for (int c = 0; c < kMaxC0; ++c)
+  for (int c = 0; c < C0; ++c)
 #pragma unroll
     for (int ky = 0; ky < 3; ++ky)
 #pragma unroll
       for (int kx = 0; kx < 3; ++kx) {
         const int yy = y + ky - 1, xx = x + kx - 1;
-        t[c][ky * 3 + kx] = (c < C0 && yy >= 0 && yy < H && xx >= 0 && xx < W)
+        t[c][ky * 3 + kx] = (yy >= 0 && yy < H && xx >= 0 && xx < W)
                                 ? img[(size_t)c * npx + (size_t)yy * W + xx]
                                 : 0.f;
       }
@@ -399,6 +399,7 @@ __global__ void __launch_bounds__(256) k_conv1_fwd(const float* __restrict__ img
     for (int k = 0; k < G; ++k) {
       const int o = g * G + k;
       float s = sb[o];
+#pragma unroll
       for (int c = 0; c < C0; ++c)
 #pragma unroll
         for (int q = 0; q < 9; ++q) s += sw[(o * C0 + c) * 9 + q] * t[c][q];
@@ -408,17 +409,27 @@ __global__ void __launch_bounds__(256) k_conv1_fwd(const float* __restrict__ img
   }
 }
 
+template <typename T>
+static void conv1_fwd_c0(int C0, unsigned g, const float* img, int H, int W, const float* w,
+                         const float* b, int C, T* out, const int* skip, cudaStream_t st) {
+  switch (C0) {
+    case 1: k_conv1_fwd<T, 1><<<g, 256, 0, st>>>(img, H, W, w, b, C, out, skip); break;
+    case 2: k_conv1_fwd<T, 2><<<g, 256, 0, st>>>(img, H, W, w, b, C, out, skip); break;
+    case 3: k_conv1_fwd<T, 3><<<g, 256, 0, st>>>(img, H, W, w, b, C, out, skip); break;
+    default: k_conv1_fwd<T, 4><<<g, 256, 0, st>>>(img, H, W, w, b, C, out, skip); break;
+  }
+}
+
 cudaError_t launch_conv1_fwd(const float* img, int C0, int H, int W, const float* w,
                              const float* b, int C, int bf16, void* out, const int* skip,
                              cudaStream_t st) {
   if (C > 64 || C0 < 1 || C0 > kMaxC0) return cudaErrorInvalidValue;
   const size_t npx = (size_t)H * W;
   if (bf16)
-    k_conv1_fwd<__nv_bfloat16><<<nblocks(npx, 256), 256, 0, st>>>(img, C0, H, W, w, b, C,
-                                                                  (__nv_bfloat16*)out, skip);
+    conv1_fwd_c0<__nv_bfloat16>(C0, nblocks(npx, 256), img, H, W, w, b, C, (__nv_bfloat16*)out,
+                                skip, st);
   else
-    k_conv1_fwd<float><<<nblocks(npx, 256), 256, 0, st>>>(img, C0, H, W, w, b, C, (float*)out,
-                                                          skip);
+    conv1_fwd_c0<float>(C0, nblocks(npx, 256), img, H, W, w, b, C, (float*)out, skip, st);
   N2F_LAUNCH_CHECK();
 }
 
@@ -491,18 +502,30 @@ __global__ void __launch_bounds__(256) k_conv1_wgrad(const T* __restrict__ dout,
   }
 }
 
-// out[q] = sum_{s < S} part[s * Q + q] (ascending s). Canonical placement of dW and db.
-__global__ void k_reduce_conv1(const float* __restrict__ part, int S, int C, int K,
-                               float* __restrict__ gw, float* __restrict__ gb, const int* skip) {
+// out[q] = sum over s of part[s * Q + q], canonical placement of dW and db. A block owns 32
+// consecutive q (the lanes); warp w sums s = w, w + 8, ... in order and the eight warp sums
+// are added in warp order, so the result is fixed for a given S.
+__global__ void __launch_bounds__(256) k_reduce_conv1(const float* __restrict__ part, int S,
+                                                      int C, int K, float* __restrict__ gw,
+                                                      float* __restrict__ gb, const int* skip) {
   if (skip && *skip) return;
+  __shared__ float sh[8][33];
   const int Q = C * (K + 1);
-  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < Q; q += gridDim.x * blockDim.x) {
-    float s = 0.f;
-    for (int k = 0; k < S; ++k) s += part[(size_t)k * Q + q];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int q = blockIdx.x * 32 + lane;
+  float s = 0.f;
+  if (q < Q)
+    for (int k = w; k < S; k += 8) s += part[(size_t)k * Q + q];
+  sh[w][lane] = s;
+  __syncthreads();
+  if (w == 0 && q < Q) {
+    float t = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t += sh[k][lane];
     if (q < C * K)
-      gw[q] = s;  // [o][c][ky][kx] == (o * C0 + c) * 9 + tap
+      gw[q] = t;  // [o][c][ky][kx] == (o * C0 + c) * 9 + tap
     else
-      gb[q - C * K] = s;
+      gb[q - C * K] = t;
   }
 }
 
@@ -522,7 +545,7 @@ cudaError_t launch_conv1_wgrad(const void* dout, const float* img, int C0, int H
   else
     k_conv1_wgrad<float><<<S, 256, 0, st>>>((const float*)dout, img, C0, H, W, C, part, skip);
   count_launch();
-  k_reduce_conv1<<<nblocks(Q, 128), 128, 0, st>>>(part, S, C, K, gw, gb, skip);
+  k_reduce_conv1<<<nblocks(Q, 32), 256, 0, st>>>(part, S, C, K, gw, gb, skip);
   N2F_LAUNCH_CHECK();
 }
 

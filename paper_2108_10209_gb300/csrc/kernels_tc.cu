@@ -159,6 +159,20 @@ struct ConvTcParams {
   int* err;
 };
 
+// One job of a grouped launch: the same layer of several independent images (each with its
+// own weights), their tiles numbered one after the other. The tensor map lives in global
+// memory (written by the host before the launch, never by the device).
+struct alignas(128) ConvJob {
+  CUtensorMap map;
+  const uint8_t* w_hi;
+  const uint8_t* w_lo;
+  const float* bias;
+  const void* mask;
+  void* out;
+  const int* skip;  // the job's stop flag: its tiles are skipped once set
+  int H, W, tiles_x, tile0;
+};
+
 constexpr int kTileM = 128;   // pixels per accumulator (one image row segment)
 constexpr int kRowsM = 2;     // image rows per CTA: each weight stage feeds two accumulators
 constexpr int kHaloX = kTileM + 2;
@@ -194,9 +208,25 @@ struct ConvWarps {
   static constexpr int kEpi = BF16 ? 8 : 4;  // epilogue warps
 };
 
-template <int BF16, int MODE>
+// What a role needs of the job a tile belongs to.
+struct TileJob {
+  const CUtensorMap* map;
+  const uint8_t* w_hi;
+  const uint8_t* w_lo;
+  const float* bias;
+  const void* mask;
+  void* out;
+  int H, W, tiles_x, local;
+  bool skip;
+};
+
+// GROUPED = 0: one image, the tensor map a kernel parameter. GROUPED = 1: the tiles of
+// `njobs` images of the same layer shape (p.cin, p.cout), ntiles = p.tiles_x in total; every
+// role walks the same tile sequence and skips the tiles of stopped jobs.
+template <int BF16, int MODE, int GROUPED>
 __global__ void __launch_bounds__(ConvWarps<BF16>::kThreads, 1)
-    k_conv_tc(const __grid_constant__ CUtensorMap tmA, ConvTcParams p) {
+    k_conv_tc(const __grid_constant__ CUtensorMap tmA, ConvTcParams p,
+              const ConvJob* __restrict__ jobs, int njobs) {
   using C = ConvCfg<BF16>;
   using T = typename std::conditional<BF16, __nv_bfloat16, float>::type;
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -204,14 +234,30 @@ __global__ void __launch_bounds__(ConvWarps<BF16>::kThreads, 1)
   __shared__ uint64_t accf[2], acce[2];
   __shared__ uint32_t tslot;
   __shared__ int abort_flag;
-  if (p.skip && *p.skip) return;
+  if (!GROUPED && p.skip && *p.skip) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int NT = tc_cfg(p.cin, p.cout, BF16).NT;
   const uint32_t B_BYTES = C::b_bytes(NT), SB = C::stage_bytes(NT);
   const int nk = p.cin / C::KC;
   const int ntn = p.cout / NT;
-  const int tiles_y = (p.H + kRowsM - 1) / kRowsM;
-  const int ntiles = p.tiles_x * tiles_y * ntn;
+  const int ntiles = GROUPED ? p.tiles_x : p.tiles_x * ((p.H + kRowsM - 1) / kRowsM) * ntn;
+  // tile -> its job; `cur` is the role's cursor (tiles only grow along a role's sequence)
+  auto locate = [&](int tile, int& cur) {
+    TileJob t;
+    if constexpr (!GROUPED) {
+      t.map = &tmA;
+      t.w_hi = p.w_hi; t.w_lo = p.w_lo; t.bias = p.bias; t.mask = p.mask; t.out = p.out;
+      t.H = p.H; t.W = p.W; t.tiles_x = p.tiles_x; t.local = tile; t.skip = false;
+    } else {
+      while (cur + 1 < njobs && tile >= jobs[cur + 1].tile0) ++cur;
+      const ConvJob& J = jobs[cur];
+      t.map = &J.map;
+      t.w_hi = J.w_hi; t.w_lo = J.w_lo; t.bias = J.bias; t.mask = J.mask; t.out = J.out;
+      t.H = J.H; t.W = J.W; t.tiles_x = J.tiles_x; t.local = tile - J.tile0;
+      t.skip = J.skip && *J.skip;
+    }
+    return t;
+  };
   const int acc_cols = kRowsM * NT;
   const int NB = 2 * acc_cols <= 512 ? 2 : 1;  // accumulator buffers
   const uint32_t ncols = tmem_cols(NB * acc_cols);
@@ -236,29 +282,32 @@ __global__ void __launch_bounds__(ConvWarps<BF16>::kThreads, 1)
   const uint32_t tbase = tslot;
   // tile -> (n-tile, row pair, x segment); the n-tile varies fastest so CTAs running at the
   // same time share the activation halo in L2
-  auto decode = [&](int tile, int& nt, int& ty, int& x0) {
-    nt = tile % ntn;
-    const int rest = tile / ntn;
-    ty = (rest / p.tiles_x) * kRowsM;
-    x0 = (rest % p.tiles_x) * kTileM;
+  auto decode = [&](const TileJob& t, int& nt, int& ty, int& x0) {
+    nt = t.local % ntn;
+    const int rest = t.local / ntn;
+    ty = (rest / t.tiles_x) * kRowsM;
+    x0 = (rest % t.tiles_x) * kTileM;
   };
 
   if (warp == 0) {
     if (lane == 0) {  // producer: halo tile by TMA, weight stage image by bulk copy
       uint32_t it = 0, issued_lo = 0;
+      int cur = 0;
       for (int tile = blockIdx.x; tile < ntiles && !*abort; tile += gridDim.x) {
+        const TileJob tj = locate(tile, cur);
+        if (tj.skip) continue;
         int nt, ty, x0;
-        decode(tile, nt, ty, x0);
+        decode(tj, nt, ty, x0);
         for (int i = 0; i < nk; ++i, ++it) {
           const int s = it % kConvStages;
           if (it >= kConvStages && !mbar_wait(&empty[s], ((it / kConvStages) - 1) & 1, abort, p.err))
             break;
           uint8_t* st = smem + s * SB;
           mbar_expect_tx(&full[s], C::A_BYTES + B_BYTES * (BF16 ? 1 : 2));
-          tma_load_4d(st, &tmA, &full[s], 0, x0 - 1, ty - 1, i * C::NSLAB);
+          tma_load_4d(st, tj.map, &full[s], 0, x0 - 1, ty - 1, i * C::NSLAB);
           const size_t stage = (size_t)nt * nk + i;
-          bulk_load(st + C::b_off(), p.w_hi + stage * B_BYTES, B_BYTES, &full[s]);
-          if (!BF16) bulk_load(st + C::b_lo_off(NT), p.w_lo + stage * B_BYTES, B_BYTES, &full[s]);
+          bulk_load(st + C::b_off(), tj.w_hi + stage * B_BYTES, B_BYTES, &full[s]);
+          if (!BF16) bulk_load(st + C::b_lo_off(NT), tj.w_lo + stage * B_BYTES, B_BYTES, &full[s]);
           issued_lo = it + 1;
         }
       }
@@ -271,7 +320,9 @@ __global__ void __launch_bounds__(ConvWarps<BF16>::kThreads, 1)
       const uint32_t id = idesc(BF16 ? 1 : 2, kTileM, NT, 0, 0);
       uint32_t it = 0, lt = 0;
       bool ok = true;
-      for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++lt) {
+      int cur = 0;
+      for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        if (locate(tile, cur).skip) continue;
         const int buf = (int)(lt % NB);
         if (lt >= (uint32_t)NB && !mbar_wait(&acce[buf], ((lt / NB) - 1) & 1, abort, p.err)) break;
         tc_fence_after();
@@ -309,13 +360,16 @@ __global__ void __launch_bounds__(ConvWarps<BF16>::kThreads, 1)
           mma_commit(&empty[s]);
         }
         mma_commit(&accf[buf]);
+        ++lt;
       }
     }
   } else if (!BF16 && warp >= 6) {
     // 3xTF32: split each fp32 halo stage into TF32 hi and lo parts, ahead of the MMAs
     const int et = threadIdx.x - 192;
     uint32_t it = 0;
+    int cur = 0;
     for (int tile = blockIdx.x; tile < ntiles && !*abort; tile += gridDim.x) {
+      if (locate(tile, cur).skip) continue;
       for (int i = 0; i < nk; ++i, ++it) {
         const int s = it % kConvStages;
         if (!mbar_wait(&full[s], (it / kConvStages) & 1, abort, p.err)) break;
@@ -341,10 +395,30 @@ __global__ void __launch_bounds__(ConvWarps<BF16>::kThreads, 1)
     const int wq = warp & 3;  // the TMEM lane quarter this warp may read
     const int cfirst = 16 * ((warp - 2) >> 2);
     const int row = wq * 32 + lane;
-    const size_t npx = (size_t)p.H * p.W;
-    const uint4* mask = reinterpret_cast<const uint4*>(p.mask);
+    // dgrad: the mask (the layer's forward activation, long evicted from L2) of a CTA's next
+    // tile is requested into L2 one tile ahead, while that tile's MMAs run
+    int pcur = 0;
+    auto prefetch_mask = [&](int tile) {
+      if (MODE != 1 || tile >= ntiles || warp != 2 || lane != 0) return;
+      const TileJob tj = locate(tile, pcur);
+      if (tj.skip) return;
+      int nt, ty, x0;
+      decode(tj, nt, ty, x0);
+      const size_t npx = (size_t)tj.H * tj.W;
+      const int npx_row = min(kTileM, tj.W - x0);
+      const char* m = static_cast<const char*>(tj.mask);
+      for (int r = 0; r < kRowsM && ty + r < tj.H; ++r)
+        for (int g = nt * NT / GE; g < (nt + 1) * NT / GE; ++g)
+          bulk_prefetch_l2(m + ((size_t)g * npx + (size_t)(ty + r) * tj.W + x0) * 16,
+                           (uint32_t)npx_row * 16u);
+    };
+    prefetch_mask(blockIdx.x);
     uint32_t lt = 0;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
+    int cur = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+      prefetch_mask(tile + gridDim.x);
+      const TileJob tj = locate(tile, cur);
+      if (tj.skip) continue;
       const int buf = (int)(lt % NB);
       if (!mbar_wait(&accf[buf], (lt / NB) & 1, abort, p.err)) {
         mbar_drain(&accf[buf], (lt / NB) & 1);
@@ -352,15 +426,17 @@ __global__ void __launch_bounds__(ConvWarps<BF16>::kThreads, 1)
       }
       tc_fence_after();
       int nt, ty, x0;
-      decode(tile, nt, ty, x0);
+      decode(tj, nt, ty, x0);
       const int x = x0 + row;
+      const size_t npx = (size_t)tj.H * tj.W;
+      const uint4* mask = reinterpret_cast<const uint4*>(tj.mask);
       const uint32_t cbase = tbase + ((uint32_t)(wq * 32) << 16) + (uint32_t)(buf * acc_cols);
       // group index of (16-column block c0, group q) and whether its pixel exists
       auto gidx = [&](int c0, int q) {
-        const size_t pix = (size_t)(ty + c0 / NT) * p.W + x;
+        const size_t pix = (size_t)(ty + c0 / NT) * tj.W + x;
         return (size_t)((nt * NT + (c0 % NT) + q * GE) / GE) * npx + pix;
       };
-      auto live = [&](int c0) { return x < p.W && ty + c0 / NT < p.H; };
+      auto live = [&](int c0) { return x < tj.W && ty + c0 / NT < tj.H; };
       uint4 mnext[NG];
       if (MODE == 1 && live(cfirst))
 #pragma unroll
@@ -387,7 +463,7 @@ __global__ void __launch_bounds__(ConvWarps<BF16>::kThreads, 1)
           if (MODE == 0) {
 #pragma unroll
             for (int j = 0; j < GE; ++j) {
-              const float t = vv[j] + __ldg(p.bias + o0 + q * GE + j);
+              const float t = vv[j] + __ldg(tj.bias + o0 + q * GE + j);
               vv[j] = t > 0.f ? t : 0.f;
             }
           } else {
@@ -396,11 +472,12 @@ __global__ void __launch_bounds__(ConvWarps<BF16>::kThreads, 1)
 #pragma unroll
             for (int j = 0; j < GE; ++j) vv[j] = mk[j] > 0.f ? vv[j] : 0.f;
           }
-          store_group<T>((T*)p.out, gidx(c0, q), vv);
+          store_group<T>((T*)tj.out, gidx(c0, q), vv);
         }
       }
       tc_fence_before();
       mbar_arrive(&acce[buf]);
+      ++lt;
     }
   }
   tc_fence_before();
@@ -820,8 +897,19 @@ __global__ void __launch_bounds__(256) k_reduce_wgrad_tc(const float* __restrict
 #pragma unroll
   for (int t = 0; t < 9; ++t) acc[t] = 0.f;
   if (o < cout) {
+    // splits w, w + 8, ... in order, four loads of each tap in flight (a, b, c, d hold the
+    // splits w + 32 i, w + 32 i + 8, ... and are added in that order)
     const float* src = part + (size_t)c * cout + o;
-    for (int k = w; k < S; k += 8)
+    int k = w;
+    for (; k + 24 < S; k += 32)
+#pragma unroll
+      for (int t = 0; t < 9; ++t) {
+        const float* q = src + (size_t)t * tstride;
+        const float a = q[k * per], b = q[(k + 8) * per], cc = q[(k + 16) * per],
+                    d = q[(k + 24) * per];
+        acc[t] = (((acc[t] + a) + b) + cc) + d;
+      }
+    for (; k < S; k += 8)
 #pragma unroll
       for (int t = 0; t < 9; ++t) acc[t] += src[k * per + t * tstride];
   }
@@ -900,10 +988,10 @@ cudaError_t launch_reduce_cols(const float* part, int R, int C, float* out, cons
 
 namespace {
 
-template <int BF16, int MODE>
-cudaError_t conv_tc_launch(const CUtensorMap& m, const ConvTcParams& p, dim3 grid, uint32_t smem,
-                           cudaStream_t st) {
-  k_conv_tc<BF16, MODE><<<grid, ConvWarps<BF16>::kThreads, smem, st>>>(m, p);
+template <int BF16, int MODE, int GROUPED>
+cudaError_t conv_tc_launch(const CUtensorMap& m, const ConvTcParams& p, const ConvJob* jobs,
+                           int njobs, dim3 grid, uint32_t smem, cudaStream_t st) {
+  k_conv_tc<BF16, MODE, GROUPED><<<grid, ConvWarps<BF16>::kThreads, smem, st>>>(m, p, jobs, njobs);
   return cudaGetLastError();
 }
 
@@ -931,10 +1019,14 @@ cudaError_t tc_prepare() {
         e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  optin - (int)fa.sharedSizeBytes);
     };
-    set((const void*)k_conv_tc<1, 0>);
-    set((const void*)k_conv_tc<1, 1>);
-    set((const void*)k_conv_tc<0, 0>);
-    set((const void*)k_conv_tc<0, 1>);
+    set((const void*)k_conv_tc<1, 0, 0>);
+    set((const void*)k_conv_tc<1, 1, 0>);
+    set((const void*)k_conv_tc<0, 0, 0>);
+    set((const void*)k_conv_tc<0, 1, 0>);
+    set((const void*)k_conv_tc<1, 0, 1>);
+    set((const void*)k_conv_tc<1, 1, 1>);
+    set((const void*)k_conv_tc<0, 0, 1>);
+    set((const void*)k_conv_tc<0, 1, 1>);
     set((const void*)k_wgrad_tc_bf16);
     set((const void*)k_wgrad_tc_f32<1>);
     set((const void*)k_wgrad_tc_f32<3>);
@@ -954,6 +1046,38 @@ bool tc_wgrad_supported(int cin, int cout, int bf16) {
 }
 
 size_t tc_weight_elems(int cin, int cout) { return (size_t)cin * cout * 9; }
+
+// Persistent grid: every resident slot once. The CTAs an SM may hold are capped by TMEM (512
+// columns): shared memory is padded so no more than 512 / ncols CTAs fit on one SM.
+static cudaError_t conv_tc_dispatch(int mode, int bf16, const CUtensorMap& m, const ConvTcParams& p,
+                                    const ConvJob* jobs, int njobs, long ntiles, cudaStream_t st) {
+  const TcCfg f = tc_cfg(p.cin, p.cout, bf16);
+  uint32_t smem = kConvStages * (bf16 ? ConvCfg<1>::stage_bytes(f.NT) : ConvCfg<0>::stage_bytes(f.NT));
+  const int acc_cols = kRowsM * f.NT;
+  const int ncols = (int)tmem_cols((2 * acc_cols <= 512 ? 2 : 1) * acc_cols);
+  const int max_res = 512 / ncols;
+  const uint32_t min_smem = (228u * 1024u) / (uint32_t)(max_res + 1) + 1024u;
+  if (smem < min_smem) smem = min_smem;
+  int per_sm = (int)((227u * 1024u) / (smem + 2048u));
+  if (per_sm > max_res) per_sm = max_res;
+  if (per_sm < 1) per_sm = 1;
+  const long slots = 152L * per_sm;
+  dim3 grid((unsigned)(ntiles < slots ? ntiles : slots), 1);
+  if (grid.x == 0) return cudaSuccess;
+  const int g = jobs != nullptr;
+  if (bf16) {
+    if (mode == 0)
+      return g ? conv_tc_launch<1, 0, 1>(m, p, jobs, njobs, grid, smem, st)
+               : conv_tc_launch<1, 0, 0>(m, p, jobs, njobs, grid, smem, st);
+    return g ? conv_tc_launch<1, 1, 1>(m, p, jobs, njobs, grid, smem, st)
+             : conv_tc_launch<1, 1, 0>(m, p, jobs, njobs, grid, smem, st);
+  }
+  if (mode == 0)
+    return g ? conv_tc_launch<0, 0, 1>(m, p, jobs, njobs, grid, smem, st)
+             : conv_tc_launch<0, 0, 0>(m, p, jobs, njobs, grid, smem, st);
+  return g ? conv_tc_launch<0, 1, 1>(m, p, jobs, njobs, grid, smem, st)
+           : conv_tc_launch<0, 1, 0>(m, p, jobs, njobs, grid, smem, st);
+}
 
 cudaError_t launch_conv_tc(int mode, int bf16, const void* in, int cin, int cout, int H, int W,
                            const void* w_hi, const void* w_lo, const float* b, const void* mask,
@@ -979,27 +1103,61 @@ cudaError_t launch_conv_tc(int mode, int bf16, const void* in, int cin, int cout
   p.tiles_x = (W + kTileM - 1) / kTileM;
   p.skip = skip;
   p.err = err;
-  uint32_t smem = kConvStages * (bf16 ? ConvCfg<1>::stage_bytes(f.NT) : ConvCfg<0>::stage_bytes(f.NT));
-  // persistent grid: every resident slot once. The CTAs an SM may hold are capped by TMEM
-  // (512 columns): shared memory is padded so no more than 512 / ncols CTAs fit on one SM.
   const long ntiles = (long)p.tiles_x * ((H + kRowsM - 1) / kRowsM) * (cout / f.NT);
-  const int acc_cols = kRowsM * f.NT;
-  const int ncols = (int)tmem_cols((2 * acc_cols <= 512 ? 2 : 1) * acc_cols);
-  const int max_res = 512 / ncols;
-  const uint32_t min_smem = (228u * 1024u) / (uint32_t)(max_res + 1) + 1024u;
-  if (smem < min_smem) smem = min_smem;
-  int per_sm = (int)((227u * 1024u) / (smem + 2048u));
-  if (per_sm > max_res) per_sm = max_res;
-  if (per_sm < 1) per_sm = 1;
-  const long slots = 152L * per_sm;
-  dim3 grid((unsigned)(ntiles < slots ? ntiles : slots), 1);
-  if (bf16)
-    e = mode == 0 ? conv_tc_launch<1, 0>(m, p, grid, smem, st) : conv_tc_launch<1, 1>(m, p, grid, smem, st);
-  else
-    e = mode == 0 ? conv_tc_launch<0, 0>(m, p, grid, smem, st) : conv_tc_launch<0, 1>(m, p, grid, smem, st);
+  e = conv_tc_dispatch(mode, bf16, m, p, nullptr, 0, ntiles, st);
   count_launch();
   return e;
 }
+
+size_t conv_job_size() { return sizeof(ConvJob); }
+
+cudaError_t conv_group_table(int mode, int bf16, int cin, int cout, const ConvGroupEntry* e,
+                             int n, void* table, long* ntiles) {
+  (void)mode;
+  if (!tc_supported(cin, cout)) return cudaErrorNotSupported;
+  const TcCfg f = tc_cfg(cin, cout, bf16);
+  const int KC = bf16 ? ConvCfg<1>::KC : ConvCfg<0>::KC;
+  const int GE = bf16 ? 8 : 4;
+  ConvJob* t = static_cast<ConvJob*>(table);
+  long tiles = 0;
+  for (int k = 0; k < n; ++k) {
+    memset(&t[k], 0, sizeof(ConvJob));
+    cudaError_t r = make_map(&t[k].map, e[k].in, bf16, cin, e[k].H, e[k].W, kHaloX, kHaloY, KC / GE);
+    if (r != cudaSuccess) return r;
+    t[k].w_hi = (const uint8_t*)e[k].w_hi;
+    t[k].w_lo = (const uint8_t*)e[k].w_lo;
+    t[k].bias = e[k].bias;
+    t[k].mask = e[k].mask;
+    t[k].out = e[k].out;
+    t[k].skip = e[k].skip;
+    t[k].H = e[k].H;
+    t[k].W = e[k].W;
+    t[k].tiles_x = (e[k].W + kTileM - 1) / kTileM;
+    t[k].tile0 = (int)tiles;
+    tiles += (long)t[k].tiles_x * ((e[k].H + kRowsM - 1) / kRowsM) * (cout / f.NT);
+  }
+  *ntiles = tiles;
+  return cudaSuccess;
+}
+
+cudaError_t launch_conv_tc_grouped(int mode, int bf16, int cin, int cout, const void* dtable,
+                                   int n, long ntiles, int* err, cudaStream_t st) {
+  if (!tc_supported(cin, cout)) return cudaErrorNotSupported;
+  if (const cudaError_t pe = tc_prepare()) return pe;
+  if (ntiles > 0x7fffffffL) return cudaErrorInvalidValue;
+  ConvTcParams p;
+  memset(&p, 0, sizeof(p));
+  p.cin = cin;
+  p.cout = cout;
+  p.tiles_x = (int)ntiles;  // the grouped kernel's total tile count
+  p.err = err;
+  CUtensorMap unused;
+  memset(&unused, 0, sizeof(unused));
+  const cudaError_t e = conv_tc_dispatch(mode, bf16, unused, p, (const ConvJob*)dtable, n, ntiles, st);
+  count_launch();
+  return e;
+}
+
 
 // bf16 = 1: bf16 maps, k_wgrad_tc_bf16; bf16 = 0: float32 maps, k_wgrad_tc_f32 (three bf16 parts)
 static cudaError_t launch_wgrad_grouped(int bf16, const void* dout, const void* in, int cin,

@@ -119,6 +119,25 @@ bool tc_supported(int cin, int cout);
 bool tc_wgrad_supported(int cin, int cout, int bf16);
 // mode 0 forward (bias + ReLU), 1 dgrad (ReLU mask); w_hi/w_lo: packed operand copies
 // (tc_layout.cuh), w_lo only in the float32 (3xTF32) form. err: device error word.
+// Grouped forward / dgrad: one persistent launch over the tiles of n images of the same layer
+// shape, each with its own input, weights, bias or mask and output. The table (conv_job_size()
+// bytes per image, 128-byte aligned) is filled on the host by conv_group_table and copied to
+// device memory before the launch.
+struct ConvGroupEntry {
+  const void* in;
+  int H, W;
+  const void* w_hi;
+  const void* w_lo;
+  const float* bias;
+  const void* mask;
+  void* out;
+  const int* skip;
+};
+size_t conv_job_size();
+cudaError_t conv_group_table(int mode, int bf16, int cin, int cout, const ConvGroupEntry* e,
+                             int n, void* table, long* ntiles);
+cudaError_t launch_conv_tc_grouped(int mode, int bf16, int cin, int cout, const void* dtable,
+                                   int n, long ntiles, int* err, cudaStream_t st);
 cudaError_t launch_conv_tc(int mode, int bf16, const void* in, int cin, int cout, int H, int W,
                            const void* w_hi, const void* w_lo, const float* b, const void* mask,
                            void* out, const int* skip, int* err, cudaStream_t st);

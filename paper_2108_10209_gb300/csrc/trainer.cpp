@@ -396,110 +396,369 @@ static int conv_layer(Trainer* t, int l, const void* in, void* out, int H, int W
   return N2F_OK;
 }
 
-int trainer_step(Trainer* t, int pair) {
-  LaunchScope ls(&t->launches);
+// ---- one training step, in pieces (the grouped executor replaces the tensor-core forward and
+// dgrad launches by one launch over all its jobs and calls the rest per job) ----------------
+
+static const int* step_skip(const Trainer* t) { return t->fixed_mode ? nullptr : &t->state->stopped; }
+
+// delta (dL/d pre-activation) of layer m (0-based) in the training step
+static void* delta_of(const Trainer* t, int m) {
+  return t->keep_deltas ? t->dkeep[m] : t->dl[(kLayers - 1 - m) & 1];
+}
+
+static int step_forward(Trainer* t, int pair, int l) {
+  const void* in = l == 0 ? (const void*)t->sub[pair] : t->act[l - 1];
+  return conv_layer(t, l, in, t->act[l], t->ph[pair], t->pw[pair], step_skip(t), 0);
+}
+
+static int step_head(Trainer* t, int pair) {
   const int h = t->ph[pair], w = t->pw[pair];
   const int npx = h * w;
   const NetShape& net = t->net;
-  const int* skip = t->fixed_mode ? nullptr : &t->state->stopped;
-  const float* in = t->sub[pair];
+  const int* skip = step_skip(t);
   // Methods table: even <-> odd of the same kind (Quad: the next image round the block); the
   // target is the predicted channel (Exact: with the signal difference removed)
   const int g = t->tgt_of[pair];
   const float* tgt = t->prm.exact ? t->tx[pair]
                                   : t->sub[g] + (size_t)t->prm.target_channel * t->ph[g] * t->pw[g];
   t->last_pair = pair;
-  // forward, keeping every post-ReLU map
-  const void* cur = in;
-  for (int l = 0; l < kLayers; ++l) {
-    int rc = conv_layer(t, l, cur, t->act[l], h, w, skip, 0);
-    if (rc) return rc;
-    cur = t->act[l];
-  }
-  // head: loss, dL/dz, delta_8, head-grad partials
   const int C8 = net.widths[kLayers - 1];
-  void* d8 = t->keep_deltas ? t->dkeep[kLayers - 1] : t->dl[0];
   int nblk = 0;
   const double es = t->bf16 ? 2.0 : 4.0;
   {
     Timed tm(t, N2F_K_HEAD, 2.0 * npx * C8, (double)npx * C8 * 2 * es + npx * 8.0, 0);
-  CK(launch_head_train(t->act[kLayers - 1], C8, npx, t->theta + net.w_off[kLayers],
-                       t->theta + net.b_off[kLayers], tgt, t->prm.loss, t->bf16, t->dz, d8,
-                       t->lpart, t->hpart, &nblk, skip, t->st));
+    CK(launch_head_train(t->act[kLayers - 1], C8, npx, t->theta + net.w_off[kLayers],
+                         t->theta + net.b_off[kLayers], tgt, t->prm.loss, t->bf16, t->dz,
+                         delta_of(t, kLayers - 1), t->lpart, t->hpart, &nblk, skip, t->st));
   }
   CK(launch_step_finish(t->hpart, t->lpart, nblk, C8, npx, t->grad + net.w_off[kLayers],
                         t->grad + net.b_off[kLayers], t->state, t->prm.beta1, t->prm.beta2,
                         t->st));
-  // backward through the 3x3 layers
-  void* dcur = d8;
-  int pp = 0;
+  return N2F_OK;
+}
+
+static int step_wgrad(Trainer* t, int pair, int l) {
+  const int h = t->ph[pair], w = t->pw[pair];
+  const int npx = h * w;
+  const NetShape& net = t->net;
+  const int* skip = step_skip(t);
+  const int cin = net.cin(l), cout = net.widths[l];
+  float* gw = t->grad + net.w_off[l];
+  float* gb = t->grad + net.b_off[l];
+  const void* dcur = delta_of(t, l);
+  if (l == 0) {
+    CK(launch_conv1_wgrad(dcur, t->sub[pair], cin, h, w, cout, t->bf16, t->wpart, t->wpart_cap,
+                          gw, gb, skip, t->st));
+    return N2F_OK;
+  }
+  const double es = t->bf16 ? 2.0 : 4.0;
+  Timed tm(t, N2F_K_CONV_WGRAD, 2.0 * npx * 9 * cin * cout, (double)npx * (cin + cout) * es, 0);
+  if (t->wg_engine[l] == N2F_ENGINE_TC)
+    CK(launch_wgrad_tc(t->bf16, dcur, t->act[l - 1], cin, cout, h, w, t->wpart, t->wpart_cap, gw,
+                       gb, skip, &t->state->kerr, t->st));
+  else
+    CK(launch_wgrad_simt(t->bf16, dcur, t->act[l - 1], cin, cout, h, w, t->wpart, t->wpart_cap,
+                         gw, gb, skip, t->st));
+  return N2F_OK;
+}
+
+static int step_dgrad(Trainer* t, int pair, int l) {
+  const int h = t->ph[pair], w = t->pw[pair];
+  const NetShape& net = t->net;
+  const int cin = net.cin(l), cout = net.widths[l];
+  const double es = t->bf16 ? 2.0 : 4.0;
+  Timed tm(t, N2F_K_CONV_DGRAD, 2.0 * h * w * 9 * cin * cout, (double)h * w * (cin * 2 + cout) * es,
+           0);
+  if (t->engine[l] == N2F_ENGINE_TC)
+    CK(launch_conv_tc(1, t->bf16, delta_of(t, l), cout, cin, h, w, t->pa.tcd[l], t->pa.tcd_lo[l],
+                      nullptr, t->act[l - 1], delta_of(t, l - 1), step_skip(t), &t->state->kerr,
+                      t->st));
+  else
+    CK(launch_conv_simt(1, t->bf16, delta_of(t, l), cout, cin, h, w, t->pa.dgr[l], nullptr,
+                        t->act[l - 1], delta_of(t, l - 1), step_skip(t), t->st));
+  return N2F_OK;
+}
+
+static int step_adam(Trainer* t) {
+  Timed tm(t, N2F_K_ADAM, 0.0, (double)t->net.count * 4.0 * 9, 0);
+  CK(launch_adam(t->pa, t->grad, t->m, t->v, t->prm.lr, t->prm.beta1, t->prm.beta2, t->prm.eps,
+                 t->state, 1, t->st));
+  return N2F_OK;
+}
+
+int trainer_step(Trainer* t, int pair) {
+  LaunchScope ls(&t->launches);
+  int rc;
+  for (int l = 0; l < kLayers; ++l)
+    if ((rc = step_forward(t, pair, l))) return rc;
+  if ((rc = step_head(t, pair))) return rc;
   for (int l = kLayers - 1; l >= 0; --l) {
-    const int cin = net.cin(l), cout = net.widths[l];
-    float* gw = t->grad + net.w_off[l];
-    float* gb = t->grad + net.b_off[l];
-    const double fl = 2.0 * npx * 9 * cin * cout;
-    if (l == 0) {
-      CK(launch_conv1_wgrad(dcur, in, cin, h, w, cout, t->bf16, t->wpart, t->wpart_cap, gw, gb,
-                            skip, t->st));
-      break;
-    }
-    {
-      Timed tm(t, N2F_K_CONV_WGRAD, fl, (double)npx * (cin + cout) * es, 0);
-    if (t->wg_engine[l] == N2F_ENGINE_TC) {
-      CK(launch_wgrad_tc(t->bf16, dcur, t->act[l - 1], cin, cout, h, w, t->wpart, t->wpart_cap,
-                         gw, gb, skip, &t->state->kerr, t->st));
-    } else {
-      CK(launch_wgrad_simt(t->bf16, dcur, t->act[l - 1], cin, cout, h, w, t->wpart,
-                           t->wpart_cap, gw, gb, skip, t->st));
-    }
-    }
-    void* dnext = t->keep_deltas ? t->dkeep[l - 1] : t->dl[pp ^ 1];
-    Timed tm(t, N2F_K_CONV_DGRAD, fl, (double)npx * (cin * 2 + cout) * es, 0);
-    if (t->engine[l] == N2F_ENGINE_TC) {
-      CK(launch_conv_tc(1, t->bf16, dcur, cout, cin, h, w, t->pa.tcd[l], t->pa.tcd_lo[l], nullptr,
-                        t->act[l - 1], dnext, skip, &t->state->kerr, t->st));
-    } else {
-      CK(launch_conv_simt(1, t->bf16, dcur, cout, cin, h, w, t->pa.dgr[l], nullptr,
-                          t->act[l - 1], dnext, skip, t->st));
-    }
-    dcur = dnext;
-    pp ^= 1;
+    if ((rc = step_wgrad(t, pair, l))) return rc;
+    if (l > 0 && (rc = step_dgrad(t, pair, l))) return rc;
   }
-  {
-    Timed tm(t, N2F_K_ADAM, 0.0, (double)net.count * 4.0 * 9, 0);
-    CK(launch_adam(t->pa, t->grad, t->m, t->v, t->prm.lr, t->prm.beta1, t->prm.beta2,
-                   t->prm.eps, t->state, 1, t->st));
-  }
+  if ((rc = step_adam(t))) return rc;
   t->steps_enqueued += 1;
   return N2F_OK;
 }
 
-int trainer_validate(Trainer* t) {
-  LaunchScope ls(&t->launches);
+// validation forward of layer l: x -> vb[0] -> vb[1] -> ...
+static int val_forward(Trainer* t, int l) {
+  const void* in = l == 0 ? (const void*)t->x : t->vb[(l - 1) & 1];
+  return conv_layer(t, l, in, t->vb[l & 1], t->H, t->W, step_skip(t), 1);
+}
+
+static int val_finish(Trainer* t) {
   const NetShape& net = t->net;
-  const int* skip = t->fixed_mode ? nullptr : &t->state->stopped;
-  const void* cur = t->x;
-  int pp = 0;
-  for (int l = 0; l < kLayers; ++l) {
-    int rc = conv_layer(t, l, cur, t->vb[pp], t->H, t->W, skip, 1);
-    if (rc) return rc;
-    cur = t->vb[pp];
-    pp ^= 1;
-  }
+  const int* skip = step_skip(t);
   int nblk = 0;
   {
     const double es = t->bf16 ? 2.0 : 4.0, C8 = net.widths[kLayers - 1];
     Timed tm(t, N2F_K_HEAD, 2.0 * t->N * C8, (double)t->N * (C8 * es + 8.0), 1);
-  CK(launch_head_val(cur, net.widths[kLayers - 1], (int)t->N, t->theta + net.w_off[kLayers],
-                     t->theta + net.b_off[kLayers], t->x + (size_t)t->prm.target_channel * t->N,
-                     t->bf16, t->V, t->mpart, &nblk, skip,
-                     t->st));
+    CK(launch_head_val(t->vb[(kLayers - 1) & 1], net.widths[kLayers - 1], (int)t->N,
+                       t->theta + net.w_off[kLayers], t->theta + net.b_off[kLayers],
+                       t->x + (size_t)t->prm.target_channel * t->N, t->bf16, t->V, t->mpart,
+                       &nblk, skip, t->st));
   }
   CK(launch_val_decide(t->mpart, nblk, t->N, t->state, t->fixed_mode, t->st));
   if (!t->fixed_mode) CK(launch_val_accum(t->V, t->S, t->Vbest, t->N, t->state, t->st));
   t->vals_enqueued += 1;
   return N2F_OK;
 }
+
+int trainer_validate(Trainer* t) {
+  LaunchScope ls(&t->launches);
+  int rc;
+  for (int l = 0; l < kLayers; ++l)
+    if ((rc = val_forward(t, l))) return rc;
+  return val_finish(t);
+}
+
+// ---- lockstep group -----------------------------------------------------------------------
+
+int group_init(TrainerGroup* g, const Allocator& al, cudaStream_t st) {
+  g->al = al;
+  g->st = st;
+  const int n = (int)g->ts.size();
+  if (n < 1) return N2F_EINVAL;
+  const Trainer* t0 = g->ts[0];
+  const size_t js = conv_job_size();
+  // table layout: [layer][kind][mode] blocks of n entries; kinds 0/1 the pairs' two shapes,
+  // kind 2 the validation; mode 1 (dgrad) only for the training kinds
+  size_t off = 0;
+  for (int l = 0; l < kLayers; ++l) {
+    g->grouped[l] = l > 0 && t0->engine[l] == N2F_ENGINE_TC;
+    for (int k = 0; k < 3; ++k)
+      for (int m = 0; m < 2; ++m) {
+        g->toff[l][k][m] = off;
+        g->ntiles[l][k][m] = 0;
+        if (g->grouped[l] && !(m == 1 && k == 2)) off += (size_t)n * js;
+      }
+  }
+  g->tbl_bytes = off ? off : js;
+  g->tbl = (char*)dev_alloc(al, g->tbl_bytes);
+  if (!g->tbl) {
+    tl_error = "device allocation of the group tables failed";
+    return N2F_ENOMEM;
+  }
+  std::vector<char> host(g->tbl_bytes);
+  std::vector<ConvGroupEntry> e(n);
+  for (int l = 1; l < kLayers; ++l) {
+    if (!g->grouped[l]) continue;
+    const int cin = t0->net.cin(l), cout = t0->net.widths[l];
+    for (int k = 0; k < 3; ++k)
+      for (int m = 0; m < 2; ++m) {
+        if (m == 1 && k == 2) continue;
+        for (int i = 0; i < n; ++i) {
+          Trainer* t = g->ts[i];
+          const int pk = k == 0 ? 0 : 2;  // a pair of this kind
+          ConvGroupEntry& q = e[i];
+          q.H = k == 2 ? t->H : t->ph[pk];
+          q.W = k == 2 ? t->W : t->pw[pk];
+          q.skip = step_skip(t);
+          if (m == 0) {
+            q.in = k == 2 ? t->vb[(l - 1) & 1] : t->act[l - 1];
+            q.out = k == 2 ? t->vb[l & 1] : t->act[l];
+            q.w_hi = t->pa.tcf[l];
+            q.w_lo = t->pa.tcf_lo[l];
+            q.bias = t->theta + t->net.b_off[l];
+            q.mask = nullptr;
+          } else {
+            q.in = delta_of(t, l);
+            q.out = delta_of(t, l - 1);
+            q.w_hi = t->pa.tcd[l];
+            q.w_lo = t->pa.tcd_lo[l];
+            q.bias = nullptr;
+            q.mask = t->act[l - 1];
+          }
+        }
+        long nt = 0;
+        const cudaError_t r = m == 0 ? conv_group_table(0, t0->bf16, cin, cout, e.data(), n,
+                                                        host.data() + g->toff[l][k][m], &nt)
+                                     : conv_group_table(1, t0->bf16, cout, cin, e.data(), n,
+                                                        host.data() + g->toff[l][k][m], &nt);
+        if (r != cudaSuccess) return set_cuda_error(r, "group table");
+        g->ntiles[l][k][m] = nt;
+      }
+  }
+  CK(cudaMemcpyAsync(g->tbl, host.data(), g->tbl_bytes, cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  CK(cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming));
+  g->mst.assign(n, nullptr);
+  g->ev_join.assign(n, nullptr);
+  for (int i = 0; i < n; ++i) {
+    CK(cudaStreamCreateWithFlags(&g->mst[i], cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&g->ev_join[i], cudaEventDisableTiming));
+    g->ts[i]->st = g->mst[i];
+  }
+  return N2F_OK;
+}
+
+// per-member phases: the member streams start after everything enqueued on the group stream
+static int fork(TrainerGroup* g) {
+  CK(cudaEventRecord(g->ev_fork, g->st));
+  for (cudaStream_t s : g->mst) CK(cudaStreamWaitEvent(s, g->ev_fork, 0));
+  return N2F_OK;
+}
+
+// ... and the group stream continues after everything enqueued on the member streams
+static int join(TrainerGroup* g) {
+  for (size_t i = 0; i < g->mst.size(); ++i) {
+    CK(cudaEventRecord(g->ev_join[i], g->mst[i]));
+    CK(cudaStreamWaitEvent(g->st, g->ev_join[i], 0));
+  }
+  return N2F_OK;
+}
+
+void group_release(TrainerGroup* g) {
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  g->exec = nullptr;
+  g->graph = nullptr;
+  if (g->tbl) dev_free(g->al, g->tbl, g->tbl_bytes);
+  g->tbl = nullptr;
+  for (cudaStream_t s : g->mst)
+    if (s) cudaStreamSynchronize(s), cudaStreamDestroy(s);
+  for (cudaEvent_t e : g->ev_join)
+    if (e) cudaEventDestroy(e);
+  if (g->ev_fork) cudaEventDestroy(g->ev_fork);
+  g->mst.clear();
+  g->ev_join.clear();
+  g->ev_fork = nullptr;
+}
+
+static int group_conv(TrainerGroup* g, int l, int k, int m) {
+  const Trainer* t0 = g->ts[0];
+  const int cin = t0->net.cin(l), cout = t0->net.widths[l];
+  CK(launch_conv_tc_grouped(m, t0->bf16, m == 0 ? cin : cout, m == 0 ? cout : cin,
+                            g->tbl + g->toff[l][k][m], (int)g->ts.size(), g->ntiles[l][k][m],
+                            &g->ts[0]->state->kerr, g->st));
+  return N2F_OK;
+}
+
+int group_step(TrainerGroup* g, int pair) {
+  LaunchScope ls(&g->launches);
+  const int kind = pair < 2 ? 0 : 1;
+  int rc;
+  for (int l = 0; l < kLayers; ++l) {
+    if (g->grouped[l]) {
+      if ((rc = group_conv(g, l, kind, 0))) return rc;
+    } else {
+      if ((rc = fork(g))) return rc;
+      for (Trainer* t : g->ts)
+        if ((rc = step_forward(t, pair, l))) return rc;
+      if ((rc = join(g))) return rc;
+    }
+  }
+  if ((rc = fork(g))) return rc;
+  for (Trainer* t : g->ts)
+    if ((rc = step_head(t, pair))) return rc;
+  if ((rc = join(g))) return rc;
+  // layer l's weight gradients (member streams) overlap its grouped dgrad (group stream); they
+  // are joined before the next dgrad overwrites the delta buffer they read
+  for (int l = kLayers - 1; l >= 0; --l) {
+    if ((rc = fork(g))) return rc;
+    for (Trainer* t : g->ts)
+      if ((rc = step_wgrad(t, pair, l))) return rc;
+    if (l > 0 && g->grouped[l]) {
+      if ((rc = group_conv(g, l, kind, 1))) return rc;
+    } else if (l > 0) {
+      for (Trainer* t : g->ts)
+        if ((rc = step_dgrad(t, pair, l))) return rc;
+    }
+    if ((rc = join(g))) return rc;
+  }
+  if ((rc = fork(g))) return rc;
+  for (Trainer* t : g->ts) {
+    if ((rc = step_adam(t))) return rc;
+    t->steps_enqueued += 1;
+  }
+  return join(g);
+}
+
+int group_validate(TrainerGroup* g) {
+  LaunchScope ls(&g->launches);
+  int rc;
+  for (int l = 0; l < kLayers; ++l) {
+    if (g->grouped[l]) {
+      if ((rc = group_conv(g, l, 2, 0))) return rc;
+    } else {
+      if ((rc = fork(g))) return rc;
+      for (Trainer* t : g->ts)
+        if ((rc = val_forward(t, l))) return rc;
+      if ((rc = join(g))) return rc;
+    }
+  }
+  if ((rc = fork(g))) return rc;
+  for (Trainer* t : g->ts)
+    if ((rc = val_finish(t))) return rc;
+  return join(g);
+}
+
+int group_epoch(TrainerGroup* g) {
+  int rc;
+  for (int k = 0; k < 4; ++k)
+    if ((rc = group_step(g, k))) return rc;
+  return group_validate(g);
+}
+
+int group_epoch_graph(TrainerGroup* g) {
+  if (!g->exec) {
+    uint64_t counted = 0;
+    cudaGraph_t gr = nullptr;
+    {
+      LaunchScope ls(&counted);
+      cudaError_t e = cudaStreamBeginCapture(g->st, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) return set_cuda_error(e, "group graph capture");
+      const int rc = group_epoch(g);
+      e = cudaStreamEndCapture(g->st, &gr);
+      if (rc) {
+        if (gr) cudaGraphDestroy(gr);
+        return rc;
+      }
+      if (e != cudaSuccess) return set_cuda_error(e, "group graph capture");
+    }
+    const cudaError_t e = cudaGraphInstantiate(&g->exec, gr, 0);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(gr);
+      return set_cuda_error(e, "group graph instantiate");
+    }
+    g->graph = gr;
+    g->epoch_kernels = counted;
+    for (Trainer* t : g->ts) {  // the capture advanced the counters once
+      t->steps_enqueued -= 4;
+      t->vals_enqueued -= 1;
+    }
+  }
+  CK(cudaGraphLaunch(g->exec, g->st));
+  for (Trainer* t : g->ts) {
+    t->steps_enqueued += 4;
+    t->vals_enqueued += 1;
+  }
+  g->launches += g->epoch_kernels;
+  count_launch((int)g->epoch_kernels);
+  return N2F_OK;
+}
+
 
 int trainer_epoch(Trainer* t) {
   for (int k = 0; k < 4; ++k) {

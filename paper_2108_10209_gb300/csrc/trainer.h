@@ -121,6 +121,36 @@ int trainer_epoch(Trainer* t);
 // Same as trainer_epoch, replaying a CUDA graph of the epoch captured on first use.
 int trainer_epoch_graph(Trainer* t);
 int trainer_finish(Trainer* t);
+
+// Jobs of identical parameters stepped in lockstep on one stream: the tensor-core forward and
+// dgrad of every layer run as one grouped launch over all members' tiles (each member with its
+// own weights, image size and stop flag); the other kernels run per member on the member's
+// own stream. Members must be trainer_init'ed on the group's stream without kept deltas;
+// group_init moves each member to its own stream.
+struct TrainerGroup {
+  std::vector<Trainer*> ts;
+  cudaStream_t st = nullptr;
+  Allocator al;
+  char* tbl = nullptr;  // grouped-launch tables, device memory
+  size_t tbl_bytes = 0;
+  size_t toff[kLayers][3][2];  // [layer][pair shape 0/1, validation 2][forward, dgrad]
+  long ntiles[kLayers][3][2];
+  bool grouped[kLayers];
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  uint64_t epoch_kernels = 0, launches = 0;
+  // per-member work forks from the group stream onto one stream per member and joins back,
+  // so members' kernels overlap each other (and a layer's weight gradients its grouped dgrad)
+  std::vector<cudaStream_t> mst;
+  std::vector<cudaEvent_t> ev_join;
+  cudaEvent_t ev_fork = nullptr;
+};
+int group_init(TrainerGroup* g, const Allocator& al, cudaStream_t st);
+void group_release(TrainerGroup* g);
+int group_step(TrainerGroup* g, int pair);
+int group_validate(TrainerGroup* g);
+int group_epoch(TrainerGroup* g);
+int group_epoch_graph(TrainerGroup* g);
 int trainer_read_state(Trainer* t, DevState* s);
 void fill_status(const Trainer* t, const DevState& s, n2f_status* st);
 
