@@ -219,7 +219,8 @@ def run_ours(args, ws, rank, local):
     p = n2f.params(seed=0, precision=args.precision, widths=args.widths, engine=args.engine)
     work = [image_for(i, rank, size) for i in range(args.warmup + args.steps)]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
-    ctx = n2f.Context(device=local, max_slots=1, profile_kernel=args.profile_kernel)
+    ctx = n2f.Context(device=local, max_slots=1, profile_kernel=args.profile_kernel,
+                      autotune=bool(args.autotune))
     for i in range(args.warmup):
         j = ctx.submit(work[i][1].astype(np.float32), p)
         ctx.wait(j)
@@ -348,7 +349,7 @@ def bf16_batched_compare(n2f, noisy_clean, fp32_outs, widths, batch):
         imgs.append(image_for(100 + i, 0, imgs[0][1].shape[0]))
         i += 1
     p = n2f.params(seed=0, precision=1, widths=widths)
-    with n2f.Context(max_slots=batch) as ctx:
+    with n2f.Context(max_slots=batch, autotune=True) as ctx:
         res, host_s, dev_s = run_jobs(ctx, n2f, [nc[1].astype("float32") for nc in imgs],
                                       lambda _: p)
     dps = [synth.psnr(res[j]["out"], imgs[j][0]) - synth.psnr(fp32_outs[j], imgs[j][0])
@@ -371,7 +372,8 @@ def run_batched(args, n2f):
             j["h"] = j["w"] = args.side
     imgs = [synth.image_cells(j["h"], j["w"], sigma=j["sigma"], seed=j["seed"]) for j in jobs]
     p = n2f.params(seed=0, precision=args.precision, widths=args.widths, engine=args.engine)
-    with n2f.Context(max_slots=args.jobs, group_size=args.group) as ctx:
+    with n2f.Context(max_slots=args.jobs, group_size=args.group,
+                     autotune=bool(args.autotune)) as ctx:
         warm = synth.image_cells(256, 256, seed=7)
         run_jobs(ctx, n2f, [warm[1].astype("float32")], lambda _: p)
         st0 = ctx.stats()
@@ -412,7 +414,7 @@ def run_serving(args, n2f):
     imgs = [synth.make_serving_image(r)[0].astype(np.float32) for r in reqs]
     t_arr = [r["t"] for r in reqs]
     p = n2f.params(seed=0, precision=args.precision, widths=args.widths, engine=args.engine)
-    with n2f.Context(max_slots=args.slots) as ctx:
+    with n2f.Context(max_slots=args.slots, autotune=bool(args.autotune)) as ctx:
         res, host_s, dev_s = run_jobs(ctx, n2f, imgs, lambda _: p, submit_times=t_arr)
     lat = [r["latency_ms"] for r in res]
     return {
@@ -441,7 +443,7 @@ def run_zstack(args, n2f):
     clean, noisy = synth.volume_cells(Z, S, S, seed=5_000_000)
     noisy32 = noisy.astype(np.float32)
     p = n2f.params(seed=0, precision=args.precision, widths=args.widths, engine=args.engine)
-    with n2f.Context(max_slots=Z, group_size=args.group) as ctx:
+    with n2f.Context(max_slots=Z, group_size=args.group, autotune=bool(args.autotune)) as ctx:
         warm = synth.image_cells(256, 256, seed=7)[1].astype(np.float32)
         n2f.denoise(warm, p, ctx)
         st0 = ctx.stats()
@@ -594,6 +596,9 @@ def main():
     ap.add_argument("--slots", type=int, default=64, help="serving: jobs resident at once")
     ap.add_argument("--max-side", type=int, default=2048, help="serving: largest image side")
     ap.add_argument("--z", type=int, default=41, help="zstack: slices")
+    ap.add_argument("--autotune", type=int, default=1,
+                    help="1: tune each conv shape's launch choices (stages, CTAs per SM) once, "
+                         "during warm-up; results are unchanged by them")
     ap.add_argument("--side", type=int, default=0,
                     help="batched: every job side x side instead of the size mix")
     ap.add_argument("--group", type=int, default=0,

@@ -104,6 +104,10 @@ typedef struct {
                                 one CUDA graph. A member's result is ready when every member of
                                 its group has stopped. Grouped jobs are not kernel-timed.
                                 0 or 1: every job alone (default). */
+  int32_t autotune;          /* 1: before a job's first epoch, the launch choices that leave
+                                results unchanged (pipeline stages, CTAs per SM) are timed for
+                                each of its conv shapes not seen before in this process and the
+                                fastest kept; 0: fixed choices (default). */
 } n2f_config;
 
 enum n2f_downsample { N2F_DOWN_CHECKER = 0, N2F_DOWN_QUAD = 1 };

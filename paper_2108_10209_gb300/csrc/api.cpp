@@ -577,6 +577,7 @@ static int admit(n2f_ctx* c, Job* j) {
   CKR(cudaEventRecord(j->ev_in, j->st));
   rc = trainer_start(&j->tr, j->src_kind == 2);
   if (rc) return rc;
+  if (c->cfg.autotune && (rc = trainer_autotune(&j->tr))) return rc;
   if (j->tr.fixed_mode) {
     for (int k = 0; k < j->prm.fixed_steps; ++k)
       if ((rc = trainer_step(&j->tr, k % 4))) return rc;

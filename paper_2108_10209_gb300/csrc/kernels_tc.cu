@@ -11,7 +11,9 @@
 // Weight gradient: D[o][c] = sum_px delta[px][o] x[px + tap][c] per tap: M = 128 output
 //   channels, N = C_in, K = pixels; both operands are read MN-major straight from the
 //   channel-grouped maps, split over pixel chunks and reduced in a fixed order.
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <type_traits>
 
 #include "cg_util.cuh"
@@ -155,6 +157,7 @@ struct ConvTcParams {
   const void* mask;     // dgrad: the layer's input activation (ReLU mask)
   void* out;
   int cin, cout, H, W, tiles_x;
+  int stages;  // pipeline stages, 2 .. kConvMaxStages (a tuning choice; no effect on results)
   const int* skip;
   int* err;
 };
@@ -177,7 +180,7 @@ constexpr int kTileM = 128;   // pixels per accumulator (one image row segment)
 constexpr int kRowsM = 2;     // image rows per CTA: each weight stage feeds two accumulators
 constexpr int kHaloX = kTileM + 2;
 constexpr int kHaloY = kRowsM + 2;
-constexpr int kConvStages = 2;
+constexpr int kConvMaxStages = 4;
 
 template <int BF16>
 struct ConvCfg {
@@ -230,7 +233,7 @@ __global__ void __launch_bounds__(ConvWarps<BF16>::kThreads, 1)
   using C = ConvCfg<BF16>;
   using T = typename std::conditional<BF16, __nv_bfloat16, float>::type;
   extern __shared__ __align__(1024) uint8_t smem[];
-  __shared__ uint64_t full[kConvStages], empty[kConvStages], split[kConvStages];
+  __shared__ uint64_t full[kConvMaxStages], empty[kConvMaxStages], split[kConvMaxStages];
   __shared__ uint64_t accf[2], acce[2];
   __shared__ uint32_t tslot;
   __shared__ int abort_flag;
@@ -238,6 +241,7 @@ __global__ void __launch_bounds__(ConvWarps<BF16>::kThreads, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int NT = tc_cfg(p.cin, p.cout, BF16).NT;
   const uint32_t B_BYTES = C::b_bytes(NT), SB = C::stage_bytes(NT);
+  const int NS = p.stages;
   const int nk = p.cin / C::KC;
   const int ntn = p.cout / NT;
   const int ntiles = GROUPED ? p.tiles_x : p.tiles_x * ((p.H + kRowsM - 1) / kRowsM) * ntn;
@@ -263,7 +267,7 @@ __global__ void __launch_bounds__(ConvWarps<BF16>::kThreads, 1)
   const uint32_t ncols = tmem_cols(NB * acc_cols);
   volatile int* abort = &abort_flag;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kConvStages; ++s) {
+    for (int s = 0; s < NS; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
       mbar_init(&split[s], 128);
@@ -299,8 +303,8 @@ __global__ void __launch_bounds__(ConvWarps<BF16>::kThreads, 1)
         int nt, ty, x0;
         decode(tj, nt, ty, x0);
         for (int i = 0; i < nk; ++i, ++it) {
-          const int s = it % kConvStages;
-          if (it >= kConvStages && !mbar_wait(&empty[s], ((it / kConvStages) - 1) & 1, abort, p.err))
+          const int s = it % NS;
+          if (it >= (uint32_t)NS && !mbar_wait(&empty[s], ((it / NS) - 1) & 1, abort, p.err))
             break;
           uint8_t* st = smem + s * SB;
           mbar_expect_tx(&full[s], C::A_BYTES + B_BYTES * (BF16 ? 1 : 2));
@@ -312,8 +316,8 @@ __global__ void __launch_bounds__(ConvWarps<BF16>::kThreads, 1)
         }
       }
       if (*abort)
-        for (uint32_t i = issued_lo > kConvStages ? issued_lo - kConvStages : 0; i < issued_lo; ++i)
-          mbar_drain(&full[i % kConvStages], (i / kConvStages) & 1);
+        for (uint32_t i = issued_lo > (uint32_t)NS ? issued_lo - NS : 0; i < issued_lo; ++i)
+          mbar_drain(&full[i % NS], (i / NS) & 1);
     }
   } else if (warp == 1) {
     if (lane == 0) {  // MMA issuer
@@ -328,8 +332,8 @@ __global__ void __launch_bounds__(ConvWarps<BF16>::kThreads, 1)
         tc_fence_after();
         const uint32_t dbase = tbase + (uint32_t)(buf * acc_cols);
         for (int i = 0; i < nk; ++i, ++it) {
-          const int s = it % kConvStages;
-          const uint32_t ph = (it / kConvStages) & 1;
+          const int s = it % NS;
+          const uint32_t ph = (it / NS) & 1;
           if (!mbar_wait(BF16 ? &full[s] : &split[s], ph, abort, p.err)) {
             ok = false;
             break;
@@ -371,8 +375,8 @@ __global__ void __launch_bounds__(ConvWarps<BF16>::kThreads, 1)
     for (int tile = blockIdx.x; tile < ntiles && !*abort; tile += gridDim.x) {
       if (locate(tile, cur).skip) continue;
       for (int i = 0; i < nk; ++i, ++it) {
-        const int s = it % kConvStages;
-        if (!mbar_wait(&full[s], (it / kConvStages) & 1, abort, p.err)) break;
+        const int s = it % NS;
+        if (!mbar_wait(&full[s], (it / NS) & 1, abort, p.err)) break;
         float4* A = reinterpret_cast<float4*>(smem + s * SB);
         float4* Al = reinterpret_cast<float4*>(smem + s * SB + C::a_lo_off());
         for (int q = et; q < (int)(C::A_BYTES / 16); q += 128) {
@@ -1047,20 +1051,55 @@ bool tc_wgrad_supported(int cin, int cout, int bf16) {
 
 size_t tc_weight_elems(int cin, int cout) { return (size_t)cin * cout * 9; }
 
-// Persistent grid: every resident slot once. The CTAs an SM may hold are capped by TMEM (512
-// columns): shared memory is padded so no more than 512 / ncols CTAs fit on one SM.
-static cudaError_t conv_tc_dispatch(int mode, int bf16, const CUtensorMap& m, const ConvTcParams& p,
-                                    const ConvJob* jobs, int njobs, long ntiles, cudaStream_t st) {
+// ---- launch configuration and its tuner ---------------------------------------------------
+// A conv launch is persistent: grid = 152 x (CTAs per SM). Two choices change only the speed,
+// never a result (every tile is computed the same way by whichever CTA takes it): the number of
+// pipeline stages and the CTAs resident per SM (capped by TMEM, 512 columns, and by shared
+// memory; shared memory is padded so that exactly the chosen number fit).
+struct ConvTune {
+  int stages = 2, per_sm = 0;  // per_sm 0: as many as fit
+};
+
+static uint32_t conv_stage_bytes(int bf16, int NT) {
+  return bf16 ? ConvCfg<1>::stage_bytes(NT) : ConvCfg<0>::stage_bytes(NT);
+}
+
+static int conv_max_res(int NT) {
+  const int acc_cols = kRowsM * NT;
+  return 512 / (int)tmem_cols((2 * acc_cols <= 512 ? 2 : 1) * acc_cols);
+}
+
+struct ConvKey {
+  int mode, bf16, cin, cout, H, W;
+  bool operator<(const ConvKey& o) const {
+    return std::tie(mode, bf16, cin, cout, H, W) < std::tie(o.mode, o.bf16, o.cin, o.cout, o.H, o.W);
+  }
+};
+static std::mutex g_tune_mu;
+static std::map<ConvKey, ConvTune> g_tune;
+
+static ConvTune conv_tune_for(const ConvKey& k) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find(k);
+  return it == g_tune.end() ? ConvTune() : it->second;
+}
+
+static cudaError_t conv_tc_dispatch(int mode, int bf16, const CUtensorMap& m, ConvTcParams p,
+                                    const ConvJob* jobs, int njobs, long ntiles, ConvTune tune,
+                                    cudaStream_t st) {
   const TcCfg f = tc_cfg(p.cin, p.cout, bf16);
-  uint32_t smem = kConvStages * (bf16 ? ConvCfg<1>::stage_bytes(f.NT) : ConvCfg<0>::stage_bytes(f.NT));
-  const int acc_cols = kRowsM * f.NT;
-  const int ncols = (int)tmem_cols((2 * acc_cols <= 512 ? 2 : 1) * acc_cols);
-  const int max_res = 512 / ncols;
-  const uint32_t min_smem = (228u * 1024u) / (uint32_t)(max_res + 1) + 1024u;
-  if (smem < min_smem) smem = min_smem;
+  const uint32_t sb = conv_stage_bytes(bf16, f.NT);
+  const int max_res = conv_max_res(f.NT);
+  int stages = tune.stages;
+  while (stages > 2 && (uint32_t)stages * sb > 227u * 1024u - 2048u) --stages;
+  uint32_t smem = (uint32_t)stages * sb;
   int per_sm = (int)((227u * 1024u) / (smem + 2048u));
   if (per_sm > max_res) per_sm = max_res;
+  if (tune.per_sm > 0 && tune.per_sm < per_sm) per_sm = tune.per_sm;
   if (per_sm < 1) per_sm = 1;
+  const uint32_t min_smem = (228u * 1024u) / (uint32_t)(per_sm + 1) + 1024u;
+  if (smem < min_smem) smem = min_smem;
+  p.stages = stages;
   const long slots = 152L * per_sm;
   dim3 grid((unsigned)(ntiles < slots ? ntiles : slots), 1);
   if (grid.x == 0) return cudaSuccess;
@@ -1079,6 +1118,80 @@ static cudaError_t conv_tc_dispatch(int mode, int bf16, const CUtensorMap& m, co
            : conv_tc_launch<0, 1, 0>(m, p, jobs, njobs, grid, smem, st);
 }
 
+static cudaError_t conv_params(int bf16, const void* in, int cin, int cout, int H, int W,
+                               const void* w_hi, const void* w_lo, const float* b,
+                               const void* mask, void* out, const int* skip, int* err,
+                               CUtensorMap* m, ConvTcParams* p) {
+  const int KC = bf16 ? ConvCfg<1>::KC : ConvCfg<0>::KC;
+  const int GE = bf16 ? 8 : 4;
+  cudaError_t e = make_map(m, in, bf16, cin, H, W, kHaloX, kHaloY, KC / GE);
+  if (e != cudaSuccess) return e;
+  p->w_hi = (const uint8_t*)w_hi;
+  p->w_lo = (const uint8_t*)w_lo;
+  p->bias = b;
+  p->mask = mask;
+  p->out = out;
+  p->cin = cin;
+  p->cout = cout;
+  p->H = H;
+  p->W = W;
+  p->tiles_x = (W + kTileM - 1) / kTileM;
+  p->stages = 2;
+  p->skip = skip;
+  p->err = err;
+  return cudaSuccess;
+}
+
+cudaError_t conv_tc_autotune(int mode, int bf16, const void* in, int cin, int cout, int H, int W,
+                             const void* w_hi, const void* w_lo, const float* b, const void* mask,
+                             void* out, int* err, cudaStream_t st) {
+  if (!tc_supported(cin, cout)) return cudaErrorNotSupported;
+  if (const cudaError_t pe = tc_prepare()) return pe;
+  const ConvKey key{mode, bf16, cin, cout, H, W};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (g_tune.count(key)) return cudaSuccess;
+  }
+  CUtensorMap m;
+  ConvTcParams p;
+  cudaError_t e = conv_params(bf16, in, cin, cout, H, W, w_hi, w_lo, b, mask, out, nullptr, err,
+                              &m, &p);
+  if (e != cudaSuccess) return e;
+  const TcCfg f = tc_cfg(cin, cout, bf16);
+  const long ntiles = (long)p.tiles_x * ((H + kRowsM - 1) / kRowsM) * (cout / f.NT);
+  const uint32_t sb = conv_stage_bytes(bf16, f.NT);
+  cudaEvent_t a = nullptr, z = nullptr;
+  e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&z);
+  ConvTune best;
+  float best_ms = 1e30f;
+  for (int stages = 2; stages <= kConvMaxStages && e == cudaSuccess; ++stages) {
+    if ((uint32_t)stages * sb > 227u * 1024u - 2048u) break;
+    for (int per_sm = 1; per_sm <= conv_max_res(f.NT) && e == cudaSuccess; ++per_sm) {
+      if (per_sm * ((uint32_t)stages * sb + 2048u) > 227u * 1024u) break;
+      const ConvTune t{stages, per_sm};
+      float ms = 0.f;
+      e = conv_tc_dispatch(mode, bf16, m, p, nullptr, 0, ntiles, t, st);  // warm-up
+      if (e == cudaSuccess) e = cudaEventRecord(a, st);
+      for (int r = 0; r < 3 && e == cudaSuccess; ++r)
+        e = conv_tc_dispatch(mode, bf16, m, p, nullptr, 0, ntiles, t, st);
+      if (e == cudaSuccess) e = cudaEventRecord(z, st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(z);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, z);
+      if (e == cudaSuccess && ms < best_ms) {
+        best_ms = ms;
+        best = t;
+      }
+    }
+  }
+  if (a) cudaEventDestroy(a);
+  if (z) cudaEventDestroy(z);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = best;
+  return cudaSuccess;
+}
+
 cudaError_t launch_conv_tc(int mode, int bf16, const void* in, int cin, int cout, int H, int W,
                            const void* w_hi, const void* w_lo, const float* b, const void* mask,
                            void* out, const int* skip, int* err, cudaStream_t st) {
@@ -1086,25 +1199,13 @@ cudaError_t launch_conv_tc(int mode, int bf16, const void* in, int cin, int cout
   if (const cudaError_t pe = tc_prepare()) return pe;
   const TcCfg f = tc_cfg(cin, cout, bf16);
   CUtensorMap m;
-  const int KC = bf16 ? ConvCfg<1>::KC : ConvCfg<0>::KC;
-  const int GE = bf16 ? 8 : 4;
-  cudaError_t e = make_map(&m, in, bf16, cin, H, W, kHaloX, kHaloY, KC / GE);
-  if (e != cudaSuccess) return e;
   ConvTcParams p;
-  p.w_hi = (const uint8_t*)w_hi;
-  p.w_lo = (const uint8_t*)w_lo;
-  p.bias = b;
-  p.mask = mask;
-  p.out = out;
-  p.cin = cin;
-  p.cout = cout;
-  p.H = H;
-  p.W = W;
-  p.tiles_x = (W + kTileM - 1) / kTileM;
-  p.skip = skip;
-  p.err = err;
+  cudaError_t e = conv_params(bf16, in, cin, cout, H, W, w_hi, w_lo, b, mask, out, skip, err, &m,
+                              &p);
+  if (e != cudaSuccess) return e;
   const long ntiles = (long)p.tiles_x * ((H + kRowsM - 1) / kRowsM) * (cout / f.NT);
-  e = conv_tc_dispatch(mode, bf16, m, p, nullptr, 0, ntiles, st);
+  e = conv_tc_dispatch(mode, bf16, m, p, nullptr, 0, ntiles,
+                       conv_tune_for(ConvKey{mode, bf16, cin, cout, H, W}), st);
   count_launch();
   return e;
 }
@@ -1150,10 +1251,12 @@ cudaError_t launch_conv_tc_grouped(int mode, int bf16, int cin, int cout, const 
   p.cin = cin;
   p.cout = cout;
   p.tiles_x = (int)ntiles;  // the grouped kernel's total tile count
+  p.stages = 2;
   p.err = err;
   CUtensorMap unused;
   memset(&unused, 0, sizeof(unused));
-  const cudaError_t e = conv_tc_dispatch(mode, bf16, unused, p, (const ConvJob*)dtable, n, ntiles, st);
+  const cudaError_t e =
+      conv_tc_dispatch(mode, bf16, unused, p, (const ConvJob*)dtable, n, ntiles, ConvTune(), st);
   count_launch();
   return e;
 }

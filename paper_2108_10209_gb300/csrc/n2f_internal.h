@@ -119,6 +119,12 @@ bool tc_supported(int cin, int cout);
 bool tc_wgrad_supported(int cin, int cout, int bf16);
 // mode 0 forward (bias + ReLU), 1 dgrad (ReLU mask); w_hi/w_lo: packed operand copies
 // (tc_layout.cuh), w_lo only in the float32 (3xTF32) form. err: device error word.
+// Times the launch choices that leave results unchanged (pipeline stages, CTAs per SM) for one
+// conv shape on the given buffers (their contents are overwritten) and caches the fastest for
+// every later launch of that (mode, precision, C_in, C_out, H, W) in this process.
+cudaError_t conv_tc_autotune(int mode, int bf16, const void* in, int cin, int cout, int H, int W,
+                             const void* w_hi, const void* w_lo, const float* b, const void* mask,
+                             void* out, int* err, cudaStream_t st);
 // Grouped forward / dgrad: one persistent launch over the tiles of n images of the same layer
 // shape, each with its own input, weights, bias or mask and output. The table (conv_job_size()
 // bytes per image, 128-byte aligned) is filled on the host by conv_group_table and copied to

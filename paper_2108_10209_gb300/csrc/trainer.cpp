@@ -760,6 +760,30 @@ int group_epoch_graph(TrainerGroup* g) {
 }
 
 
+// Tunes every tensor-core conv shape of the job (training pairs' two shapes and the full image,
+// forward and dgrad) on its own buffers, before its first epoch: the buffers written here are
+// all rewritten by the epochs.
+int trainer_autotune(Trainer* t) {
+  for (int l = 1; l < kLayers; ++l) {
+    if (t->engine[l] != N2F_ENGINE_TC) continue;
+    const int cin = t->net.cin(l), cout = t->net.widths[l];
+    const float* b = t->theta + t->net.b_off[l];
+    for (int k = 0; k < 3; ++k) {
+      const int h = k == 2 ? t->H : t->ph[k == 0 ? 0 : 2];
+      const int w = k == 2 ? t->W : t->pw[k == 0 ? 0 : 2];
+      const void* in = k == 2 ? t->vb[(l - 1) & 1] : t->act[l - 1];
+      void* out = k == 2 ? t->vb[l & 1] : t->act[l];
+      CK(conv_tc_autotune(0, t->bf16, in, cin, cout, h, w, t->pa.tcf[l], t->pa.tcf_lo[l], b,
+                          nullptr, out, &t->state->kerr, t->st));
+      if (k == 2) continue;
+      CK(conv_tc_autotune(1, t->bf16, delta_of(t, l), cout, cin, h, w, t->pa.tcd[l],
+                          t->pa.tcd_lo[l], nullptr, t->act[l - 1], delta_of(t, l - 1),
+                          &t->state->kerr, t->st));
+    }
+  }
+  return N2F_OK;
+}
+
 int trainer_epoch(Trainer* t) {
   for (int k = 0; k < 4; ++k) {
     int rc = trainer_step(t, k);

@@ -118,6 +118,8 @@ int trainer_repack(Trainer* t);
 int trainer_step(Trainer* t, int pair);
 int trainer_validate(Trainer* t);
 int trainer_epoch(Trainer* t);
+// Tunes the job's conv launch choices (see conv_tc_autotune) before its first epoch.
+int trainer_autotune(Trainer* t);
 // Same as trainer_epoch, replaying a CUDA graph of the epoch captured on first use.
 int trainer_epoch_graph(Trainer* t);
 int trainer_finish(Trainer* t);

@@ -164,6 +164,23 @@ def test_profiled_graph_replay(n2f):
         assert got[(kind, False)] == got[(kind, True)]
 
 
+def test_autotuned_launches_give_identical_results(n2f):
+    # The tuner only picks among launch choices that leave every result unchanged (pipeline
+    # stages, CTAs per SM): tuned and untuned jobs agree bit for bit, in both forms.
+    imgs = [_img(48, 40, 51)[1], _img(64, 96, 52)[1]]
+    for prec in (0, 1):
+        p = n2f.params(seed=6, patience=3, precision=prec)
+        outs = []
+        for tune in (False, True):
+            with n2f.Context(autotune=tune) as ctx:
+                ids = [ctx.submit(x, p) for x in imgs]
+                for x, j in zip(imgs, ids):
+                    assert ctx.wait(j) == 0
+                outs.append([ctx.result(j, x.shape) for x, j in zip(imgs, ids)])
+        for a, b in zip(*outs):
+            assert np.array_equal(a, b)
+
+
 def test_admission_by_hbm_budget(n2f):
     # The budget admits jobs first-in first-out while their device state fits; a job that can
     # never fit is refused at submission.
