@@ -524,11 +524,27 @@ TapGroups tap_groups(int cin) {
   return g;
 }
 
+// The bias gradient db[o] = sum_px delta[px][o] comes out of the same GEMM: the CTAs of tap
+// group 0 multiply their delta tile by a constant tile of ones (N = 16, bf16 1.0, exact) into 16
+// more TMEM columns, one extra MMA per K step (three in the float32 form, one per bf16 part).
+constexpr uint32_t kOnesBytes = 512;  // [2 groups of 8 columns][16 px][16 B]
+
+__device__ __forceinline__ void write_ones(uint8_t* ones) {
+  for (int i = threadIdx.x; i < (int)(kOnesBytes / 4); i += blockDim.x)
+    reinterpret_cast<uint32_t*>(ones)[i] = 0x3F803F80u;  // two bf16 1.0
+  fence_proxy_async();
+}
+
+__device__ __forceinline__ uint64_t ones_desc(const uint8_t* ones) {
+  return sdesc(smem_u32(ones), 128, 256);
+}
+
 struct WgBf16Params {
   float* part;  // [S][9][C_in][C_out]
   int cin, cout, H, W, chunks_x, total_chunks, per_split;
   int stages;  // pipeline stages
   int pu;      // pixels per TMA unit of both maps
+  float* bpart;  // [S][C_out] bias-gradient partials, written by the tap group 0 CTAs
   TapGroups tg;
   const int* skip;
   int* err;
@@ -566,7 +582,9 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc_bf16(const __grid_constant_
   const int pu = p.pu, HX = wb_pitch(pu);
   const uint32_t BB = wb_b_bytes(cn, R, pu), SB = wb_stage(cn, R, pu);
   const uint32_t b_off = align_up(kWbA, 1024);
-  const uint32_t ncols = tmem_cols(nt * cn);
+  const bool bias = grp == 0;
+  const uint32_t ncols = tmem_cols(nt * cn + (bias ? 16 : 0));
+  uint8_t* ones = smem + (size_t)ns * SB;
   volatile int* abort = &abort_flag;
   if (threadIdx.x == 0) {
     for (int s = 0; s < ns; ++s) {
@@ -578,6 +596,7 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc_bf16(const __grid_constant_
     mbar_fence_init();
   }
   if (warp == 1) tmem_alloc(&tslot, ncols);
+  if (bias) write_ones(ones);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -604,7 +623,8 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc_bf16(const __grid_constant_
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t id = idesc(1, 128, cn, 1, 1);
+      const uint32_t id = idesc(1, 128, cn, 1, 1), id16 = idesc(1, 128, 16, 1, 1);
+      const uint64_t od = ones_desc(ones);
       const uint32_t a_sbo = kWbKP * 16;                    // next 8-channel group of delta
       const uint32_t b_sbo = (uint32_t)R * HX * 16;  // next 8-channel group of x
       for (int i = 0; i < nk; ++i) {
@@ -623,6 +643,11 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc_bf16(const __grid_constant_
                     sdesc(sb + boff + ko, 128, b_sbo), id, (i > 0 || k > 0) ? 1u : 0u);
           }
         }
+        if (bias)
+#pragma unroll
+          for (int k = 0; k < kWbKP / 16; ++k)
+            mma_f16(tbase + (uint32_t)(nt * cn), sdesc(sa + (uint32_t)k * 256u, 128, a_sbo), od,
+                    id16, (i > 0 || k > 0) ? 1u : 0u);
         mma_commit(&empty[s]);
       }
       mma_commit(&accf);
@@ -645,6 +670,12 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc_bf16(const __grid_constant_
 #pragma unroll
         for (int q = 0; q < 16; ++q) dst[(size_t)(c0 + q) * p.cout] = nk ? __uint_as_float(r[q]) : 0.f;
       }
+    }
+    if (bias) {
+      uint32_t r[16];
+      tmem_ld16(tbase + ((uint32_t)(wq * 32) << 16) + (uint32_t)(nt * cn), r);
+      tmem_ld_wait();
+      if (live) p.bpart[(size_t)s_idx * p.cout + o] = nk ? __uint_as_float(r[0]) : 0.f;
     }
   }
   tc_fence_before();
@@ -775,7 +806,9 @@ __global__ void __launch_bounds__(kW3Threads, 1) k_wgrad_tc_f32(const __grid_con
   const int pu = p.pu;
   const W3Layout L = w3_layout(cn, R, pu);
   const uint32_t RB = (uint32_t)cn * R * w3_raw_pitch(pu) * 4;
-  const uint32_t ncols = tmem_cols(nt * cn);
+  const bool bias = grp == 0;
+  const uint32_t ncols = tmem_cols(nt * cn + (bias ? 16 : 0));
+  uint8_t* ones = smem + (size_t)ns * L.stage;
   volatile int* abort = &abort_flag;
   if (threadIdx.x == 0) {
     for (int s = 0; s < ns; ++s) {
@@ -788,6 +821,7 @@ __global__ void __launch_bounds__(kW3Threads, 1) k_wgrad_tc_f32(const __grid_con
     mbar_fence_init();
   }
   if (warp == 1) tmem_alloc(&tslot, ncols);
+  if (bias) write_ones(ones);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -813,7 +847,8 @@ __global__ void __launch_bounds__(kW3Threads, 1) k_wgrad_tc_f32(const __grid_con
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t id = idesc(1, 128, cn, 1, 1);
+      const uint32_t id = idesc(1, 128, cn, 1, 1), id16 = idesc(1, 128, 16, 1, 1);
+      const uint64_t od = ones_desc(ones);
       const uint32_t a_sbo = kW3KP * 16;                     // next 8-channel group of delta
       const uint32_t b_sbo = (uint32_t)R * (kW3KP + 2) * 16;  // next 8-channel group of x
       for (int i = 0; i < nk; ++i) {
@@ -837,6 +872,12 @@ __global__ void __launch_bounds__(kW3Threads, 1) k_wgrad_tc_f32(const __grid_con
           mma_f16(d, da[0], db[2], id, 1u);
           mma_f16(d, da[1], db[1], id, 1u);
           mma_f16(d, da[2], db[0], id, 1u);
+        }
+        if (bias) {  // delta = a0 + a1 + a2, times ones
+          const uint32_t d = tbase + (uint32_t)(nt * cn);
+          mma_f16(d, da[0], od, id16, i > 0 ? 1u : 0u);
+          mma_f16(d, da[1], od, id16, 1u);
+          mma_f16(d, da[2], od, id16, 1u);
         }
         mma_commit(&empty[s]);
       }
@@ -872,6 +913,12 @@ __global__ void __launch_bounds__(kW3Threads, 1) k_wgrad_tc_f32(const __grid_con
 #pragma unroll
         for (int q = 0; q < 16; ++q) dst[(size_t)(c0 + q) * p.cout] = nk ? __uint_as_float(r[q]) : 0.f;
       }
+    }
+    if (bias && half == 0) {
+      uint32_t r[16];
+      tmem_ld16(tbase + ((uint32_t)(wq * 32) << 16) + (uint32_t)(nt * cn), r);
+      tmem_ld_wait();
+      if (live) p.bpart[(size_t)s_idx * p.cout + o] = nk ? __uint_as_float(r[0]) : 0.f;
     }
   }
   tc_fence_before();
@@ -927,39 +974,6 @@ __global__ void __launch_bounds__(256) k_reduce_wgrad_tc(const float* __restrict
 #pragma unroll
     for (int k = 0; k < 8; ++k) v += sh[k][t][oo];
     gw[((size_t)(o0 + oo) * cin + c) * 9 + t] = v;
-  }
-}
-
-// Bias gradient db[c] = sum_p d(p, c) of a CG map. Block b owns a pixel range; warp w takes
-// the channel groups w, w + 8, ...; its lanes read 32 consecutive pixels of a group (512
-// contiguous bytes) and a fixed shuffle tree adds the lanes. The per-block sums are then
-// added in block order, so the result is fixed for a given block count.
-template <typename T>
-__global__ void __launch_bounds__(256) k_colsum_cg(const T* __restrict__ d, int C, size_t npx,
-                                                   size_t per_block, float* __restrict__ bpart,
-                                                   const int* skip) {
-  if (skip && *skip) return;
-  constexpr int GE = CGTraits<T>::G;
-  const int ng = C / GE;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const size_t pb = blockIdx.x * per_block, pe = min(npx, pb + per_block);
-  for (int g = w; g < ng; g += 8) {
-    float acc[GE];
-#pragma unroll
-    for (int k = 0; k < GE; ++k) acc[k] = 0.f;
-    for (size_t pix = pb + lane; pix < pe; pix += 32) {
-      float v[GE];
-      load_group<T>(d, (size_t)g * npx + pix, v);
-#pragma unroll
-      for (int k = 0; k < GE; ++k) acc[k] += v[k];
-    }
-#pragma unroll
-    for (int k = 0; k < GE; ++k)
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], off);
-    if (lane == 0)
-#pragma unroll
-      for (int k = 0; k < GE; ++k) bpart[(size_t)blockIdx.x * C + g * GE + k] = acc[k];
   }
 }
 
@@ -1289,16 +1303,19 @@ static cudaError_t launch_wgrad_grouped(int bf16, const void* dout, const void* 
   p.tg = tg;
   p.pu = pu;
   const size_t per_split_elems = (size_t)9 * cout * cin;
-  int maxcols = 0;
-  for (int g = 0; g < tg.n; ++g) maxcols = tg.count[g] * tg.cn > maxcols ? tg.count[g] * tg.cn : maxcols;
+  int maxcols = 0;  // group 0 also holds the 16 bias columns
+  for (int g = 0; g < tg.n; ++g) {
+    const int cols = tg.count[g] * tg.cn + (g == 0 ? 16 : 0);
+    maxcols = cols > maxcols ? cols : maxcols;
+  }
   const int max_res = 512 / (int)tmem_cols(maxcols);  // CTAs per SM that TMEM allows
   // as many stages as fit beside the CTAs that TMEM allows on one SM
   const uint32_t sb = bf16 ? wb_stage(tg.cn, tg.R, pu) : w3_layout(tg.cn, tg.R, pu).stage;
   const int max_stages = bf16 ? kWbMaxStages : kW3MaxStages;
-  p.stages = (int)((227u * 1024u / (uint32_t)max_res - 2048u) / sb);
+  p.stages = (int)((227u * 1024u / (uint32_t)max_res - 2048u - 1024u) / sb);
   if (p.stages > max_stages) p.stages = max_stages;
   if (p.stages < 2) p.stages = 2;
-  uint32_t smem = (uint32_t)p.stages * sb;
+  uint32_t smem = (uint32_t)p.stages * sb + 1024u;  // + the tile of ones (1 KB aligned)
   // a CTA holding more than half of TMEM keeps the SM to itself
   if (max_res == 1 && smem < 116u * 1024u) smem = 116u * 1024u;
   const int per_sm = (int)((227u * 1024u) / (smem + 2048u));
@@ -1310,14 +1327,12 @@ static cudaError_t launch_wgrad_grouped(int bf16, const void* dout, const void* 
   if (S * ctas * 10 < slots * 9) S = 2 * slots / ctas;
   if (S > p.total_chunks / 16) S = p.total_chunks / 16;  // at least 16 pixel chunks per split
   if (S < 1) S = 1;
-  const size_t npx = (size_t)H * W;
-  int SB = (int)((npx + 255) / 256);
-  if (SB > 1024) SB = 1024;
-  while (S > 1 && (size_t)S * per_split_elems + 64 + (size_t)SB * cout > part_cap) --S;
-  if ((size_t)S * per_split_elems + 64 + (size_t)SB * cout > part_cap) return cudaErrorInvalidValue;
+  while (S > 1 && (size_t)S * (per_split_elems + cout) + 64 > part_cap) --S;
+  if ((size_t)S * (per_split_elems + cout) + 64 > part_cap) return cudaErrorInvalidValue;
   p.per_split = (p.total_chunks + S - 1) / S;
   S = (p.total_chunks + p.per_split - 1) / p.per_split;
   p.part = part;
+  p.bpart = part + ((size_t)S * per_split_elems + 63) / 64 * 64;
   p.skip = skip;
   p.err = err;
   const dim3 grid((unsigned)otiles, (unsigned)tg.n, (unsigned)S);
@@ -1332,15 +1347,8 @@ static cudaError_t launch_wgrad_grouped(int bf16, const void* dout, const void* 
   k_reduce_wgrad_tc<<<(unsigned)(((cout + kRwO - 1) / kRwO) * cin), 256, 0, st>>>(part, S, cin,
                                                                                  cout, gw, skip);
   count_launch();
-  float* bpart = part + ((size_t)S * per_split_elems + 63) / 64 * 64;
-  const size_t per_block = (npx + SB - 1) / SB;
-  if (bf16)
-    k_colsum_cg<__nv_bfloat16><<<SB, 256, 0, st>>>((const __nv_bfloat16*)dout, cout, npx,
-                                                   per_block, bpart, skip);
-  else
-    k_colsum_cg<float><<<SB, 256, 0, st>>>((const float*)dout, cout, npx, per_block, bpart, skip);
-  count_launch();
-  return launch_reduce_cols(bpart, SB, cout, gb, skip, st);
+  // bias: the S per-split sums of tap group 0, added in split order
+  return launch_reduce_cols(p.bpart, S, cout, gb, skip, st);
 }
 
 cudaError_t launch_wgrad_tc(int bf16, const void* dout, const void* in, int cin, int cout, int H,
