@@ -524,20 +524,15 @@ TapGroups tap_groups(int cin) {
   return g;
 }
 
-// The bias gradient db[o] = sum_px delta[px][o] comes out of the same GEMM: the CTAs of tap
-// group 0 multiply their delta tile by a constant tile of ones (N = 16, bf16 1.0, exact) into 16
-// more TMEM columns, one extra MMA per K step (three in the float32 form, one per bf16 part).
-constexpr uint32_t kOnesBytes = 512;  // [2 groups of 8 columns][16 px][16 B]
-
-__device__ __forceinline__ void write_ones(uint8_t* ones) {
-  for (int i = threadIdx.x; i < (int)(kOnesBytes / 4); i += blockDim.x)
-    reinterpret_cast<uint32_t*>(ones)[i] = 0x3F803F80u;  // two bf16 1.0
-  fence_proxy_async();
+// The bias gradient db[o] = sum_px delta[px][o] comes out of the same GEMM: in the CTAs of tap
+// group 0 the B operand of the group's last tap carries two more 8-channel groups, constant bf16
+// ones (zeros in the float32 form's second and third parts), so that tap's MMAs (N = C + 16)
+// also accumulate sum_px delta into 16 more TMEM columns, at no extra instruction.
+__device__ __forceinline__ void fill_ext(uint8_t* ext, uint32_t bytes, uint32_t value) {
+  for (uint32_t i = threadIdx.x; i < bytes / 4; i += blockDim.x)
+    reinterpret_cast<uint32_t*>(ext)[i] = value;
 }
-
-__device__ __forceinline__ uint64_t ones_desc(const uint8_t* ones) {
-  return sdesc(smem_u32(ones), 128, 256);
-}
+constexpr uint32_t kBf16PairOne = 0x3F803F80u;  // two bf16 1.0
 
 struct WgBf16Params {
   float* part;  // [S][9][C_in][C_out]
@@ -559,8 +554,10 @@ __host__ __device__ inline int wb_pitch(int pu) { return kWbKP + 2 * pu; }
 __host__ __device__ inline uint32_t wb_b_bytes(int cin, int R, int pu) {
   return (uint32_t)(cin / 8) * R * wb_pitch(pu) * 16;
 }
+// the two extra 8-channel groups (ones) after the x tile
+__host__ __device__ inline uint32_t wb_ext_bytes(int R, int pu) { return 2u * R * wb_pitch(pu) * 16; }
 __host__ __device__ inline uint32_t wb_stage(int cin, int R, int pu) {
-  return align_up(kWbA, 1024) + align_up(wb_b_bytes(cin, R, pu), 1024);
+  return align_up(kWbA, 1024) + align_up(wb_b_bytes(cin, R, pu) + wb_ext_bytes(R, pu), 1024);
 }
 
 __global__ void __launch_bounds__(192, 1) k_wgrad_tc_bf16(const __grid_constant__ CUtensorMap tmD,
@@ -584,7 +581,6 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc_bf16(const __grid_constant_
   const uint32_t b_off = align_up(kWbA, 1024);
   const bool bias = grp == 0;
   const uint32_t ncols = tmem_cols(nt * cn + (bias ? 16 : 0));
-  uint8_t* ones = smem + (size_t)ns * SB;
   volatile int* abort = &abort_flag;
   if (threadIdx.x == 0) {
     for (int s = 0; s < ns; ++s) {
@@ -596,7 +592,10 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc_bf16(const __grid_constant_
     mbar_fence_init();
   }
   if (warp == 1) tmem_alloc(&tslot, ncols);
-  if (bias) write_ones(ones);
+  if (bias) {
+    for (int s = 0; s < ns; ++s) fill_ext(smem + s * SB + b_off + BB, wb_ext_bytes(R, pu), kBf16PairOne);
+    fence_proxy_async();
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -623,8 +622,7 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc_bf16(const __grid_constant_
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t id = idesc(1, 128, cn, 1, 1), id16 = idesc(1, 128, 16, 1, 1);
-      const uint64_t od = ones_desc(ones);
+      const uint32_t id = idesc(1, 128, cn, 1, 1), idx = idesc(1, 128, cn + 16, 1, 1);
       const uint32_t a_sbo = kWbKP * 16;                    // next 8-channel group of delta
       const uint32_t b_sbo = (uint32_t)R * HX * 16;  // next 8-channel group of x
       for (int i = 0; i < nk; ++i) {
@@ -640,14 +638,10 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc_bf16(const __grid_constant_
           for (int k = 0; k < kWbKP / 16; ++k) {
             const uint32_t ko = (uint32_t)k * 16u * 16u;
             mma_f16(tbase + (uint32_t)(j * cn), sdesc(sa + ko, 128, a_sbo),
-                    sdesc(sb + boff + ko, 128, b_sbo), id, (i > 0 || k > 0) ? 1u : 0u);
+                    sdesc(sb + boff + ko, 128, b_sbo), (bias && j == nt - 1) ? idx : id,
+                    (i > 0 || k > 0) ? 1u : 0u);
           }
         }
-        if (bias)
-#pragma unroll
-          for (int k = 0; k < kWbKP / 16; ++k)
-            mma_f16(tbase + (uint32_t)(nt * cn), sdesc(sa + (uint32_t)k * 256u, 128, a_sbo), od,
-                    id16, (i > 0 || k > 0) ? 1u : 0u);
         mma_commit(&empty[s]);
       }
       mma_commit(&accf);
@@ -709,7 +703,8 @@ __host__ __device__ inline W3Layout w3_layout(int cin, int R, int pu) {
   const uint32_t ra = 128u * kW3KP * 4;                         // [32 g4][16 px][16 B]
   const uint32_t rb = (uint32_t)cin * R * w3_raw_pitch(pu) * 4;  // [C/4][R][16 + 2 pu][16 B]
   const uint32_t pa = 128u * kW3KP * 2;                         // [16 g8][16 px][16 B]
-  const uint32_t pb = (uint32_t)cin * R * (kW3KP + 2) * 2;     // [C/8][R][18 px][16 B]
+  const uint32_t pb = (uint32_t)cin * R * (kW3KP + 2) * 2      // [C/8][R][18 px][16 B]
+                      + 2u * R * (kW3KP + 2) * 16;              // + 2 bias groups
   uint32_t o = 0;
   L.rawA = o; o += align_up(ra, 1024);
   L.rawB = o; o += align_up(rb, 1024);
@@ -808,7 +803,6 @@ __global__ void __launch_bounds__(kW3Threads, 1) k_wgrad_tc_f32(const __grid_con
   const uint32_t RB = (uint32_t)cn * R * w3_raw_pitch(pu) * 4;
   const bool bias = grp == 0;
   const uint32_t ncols = tmem_cols(nt * cn + (bias ? 16 : 0));
-  uint8_t* ones = smem + (size_t)ns * L.stage;
   volatile int* abort = &abort_flag;
   if (threadIdx.x == 0) {
     for (int s = 0; s < ns; ++s) {
@@ -821,7 +815,13 @@ __global__ void __launch_bounds__(kW3Threads, 1) k_wgrad_tc_f32(const __grid_con
     mbar_fence_init();
   }
   if (warp == 1) tmem_alloc(&tslot, ncols);
-  if (bias) write_ones(ones);
+  if (bias) {  // part 0: ones, parts 1 and 2: zeros, so the bias columns sum a0 + a1 + a2
+    const uint32_t eo = (uint32_t)cn * R * (kW3KP + 2) * 2, eb = 2u * R * (kW3KP + 2) * 16;
+    for (int s = 0; s < ns; ++s)
+      for (int q = 0; q < 3; ++q)
+        fill_ext(smem + s * L.stage + L.b[q] + eo, eb, q == 0 ? kBf16PairOne : 0u);
+    fence_proxy_async();
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -847,8 +847,7 @@ __global__ void __launch_bounds__(kW3Threads, 1) k_wgrad_tc_f32(const __grid_con
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t id = idesc(1, 128, cn, 1, 1), id16 = idesc(1, 128, 16, 1, 1);
-      const uint64_t od = ones_desc(ones);
+      const uint32_t idn = idesc(1, 128, cn, 1, 1), idx = idesc(1, 128, cn + 16, 1, 1);
       const uint32_t a_sbo = kW3KP * 16;                     // next 8-channel group of delta
       const uint32_t b_sbo = (uint32_t)R * (kW3KP + 2) * 16;  // next 8-channel group of x
       for (int i = 0; i < nk; ++i) {
@@ -866,18 +865,13 @@ __global__ void __launch_bounds__(kW3Threads, 1) k_wgrad_tc_f32(const __grid_con
 #pragma unroll
           for (int k = 0; k < 3; ++k) db[k] = sdesc(st + L.b[k] + boff, 128, b_sbo);
           const uint32_t d = tbase + (uint32_t)(j * cn);
+          const uint32_t id = (bias && j == nt - 1) ? idx : idn;
           mma_f16(d, da[0], db[0], id, i > 0 ? 1u : 0u);
           mma_f16(d, da[0], db[1], id, 1u);
           mma_f16(d, da[1], db[0], id, 1u);
           mma_f16(d, da[0], db[2], id, 1u);
           mma_f16(d, da[1], db[1], id, 1u);
           mma_f16(d, da[2], db[0], id, 1u);
-        }
-        if (bias) {  // delta = a0 + a1 + a2, times ones
-          const uint32_t d = tbase + (uint32_t)(nt * cn);
-          mma_f16(d, da[0], od, id16, i > 0 ? 1u : 0u);
-          mma_f16(d, da[1], od, id16, 1u);
-          mma_f16(d, da[2], od, id16, 1u);
         }
         mma_commit(&empty[s]);
       }
@@ -1312,10 +1306,10 @@ static cudaError_t launch_wgrad_grouped(int bf16, const void* dout, const void* 
   // as many stages as fit beside the CTAs that TMEM allows on one SM
   const uint32_t sb = bf16 ? wb_stage(tg.cn, tg.R, pu) : w3_layout(tg.cn, tg.R, pu).stage;
   const int max_stages = bf16 ? kWbMaxStages : kW3MaxStages;
-  p.stages = (int)((227u * 1024u / (uint32_t)max_res - 2048u - 1024u) / sb);
+  p.stages = (int)((227u * 1024u / (uint32_t)max_res - 2048u) / sb);
   if (p.stages > max_stages) p.stages = max_stages;
   if (p.stages < 2) p.stages = 2;
-  uint32_t smem = (uint32_t)p.stages * sb + 1024u;  // + the tile of ones (1 KB aligned)
+  uint32_t smem = (uint32_t)p.stages * sb;
   // a CTA holding more than half of TMEM keeps the SM to itself
   if (max_res == 1 && smem < 116u * 1024u) smem = 116u * 1024u;
   const int per_sm = (int)((227u * 1024u) / (smem + 2048u));
