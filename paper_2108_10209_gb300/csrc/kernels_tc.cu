@@ -698,13 +698,18 @@ struct W3Layout {
 // raw x tile pitch: the 16 chunk pixels plus one TMA unit of pu pixels on each side
 __host__ __device__ inline int w3_raw_pitch(int pu) { return kW3KP + 2 * pu; }
 
-__host__ __device__ inline W3Layout w3_layout(int cin, int R, int pu) {
+// exp: the x parts are written tap-expanded, [taps x C/8][16 px][16 B] + 2 bias groups, so one
+// MMA covers several taps (N = taps x C): used when C is small (N = C alone would leave the
+// tensor pipe idle between MMAs, each of which costs at least ~48 cycles)
+__host__ __device__ inline W3Layout w3_layout(int cin, int R, int pu, bool exp = false,
+                                              int taps = 0) {
   W3Layout L;
   const uint32_t ra = 128u * kW3KP * 4;                         // [32 g4][16 px][16 B]
   const uint32_t rb = (uint32_t)cin * R * w3_raw_pitch(pu) * 4;  // [C/4][R][16 + 2 pu][16 B]
   const uint32_t pa = 128u * kW3KP * 2;                         // [16 g8][16 px][16 B]
-  const uint32_t pb = (uint32_t)cin * R * (kW3KP + 2) * 2      // [C/8][R][18 px][16 B]
-                      + 2u * R * (kW3KP + 2) * 16;              // + 2 bias groups
+  const uint32_t pb = exp ? ((uint32_t)taps * cin / 8 + 2) * kW3KP * 16
+                          : (uint32_t)cin * R * (kW3KP + 2) * 2  // [C/8][R][18 px][16 B]
+                                + 2u * R * (kW3KP + 2) * 16;     // + 2 bias groups
   uint32_t o = 0;
   L.rawA = o; o += align_up(ra, 1024);
   L.rawB = o; o += align_up(rb, 1024);
@@ -747,9 +752,9 @@ __device__ __forceinline__ void split3_group(const float4 lo, const float4 hi, u
 // [C/4][R][16 + 2 pu px], parts [C/8][R][18 px] (raw column pu - 1 + i -> part column i). Each
 // quarter-warp takes 8 consecutive pixels of one row, so its eight 16-byte reads fall in
 // distinct bank groups; the 2 halo pixels of each row follow in a short second pass.
-template <int R>
+template <int R, int EXP>
 __device__ __forceinline__ void split3_stage(const uint8_t* st, uint8_t* stw, const W3Layout& L,
-                                             int g8n, int pu, int et) {
+                                             int g8n, int pu, int et, int nt, int t0, int r0) {
   constexpr int kThr = 32 * kW3SplitWarps;
   constexpr int PP = kW3KP + 2;  // part pitch
   const int PR = w3_raw_pitch(pu);
@@ -766,6 +771,18 @@ __device__ __forceinline__ void split3_stage(const uint8_t* st, uint8_t* stw, co
   uint4* b0 = reinterpret_cast<uint4*>(stw + L.b[0]);
   uint4* b1 = reinterpret_cast<uint4*>(stw + L.b[1]);
   uint4* b2 = reinterpret_cast<uint4*>(stw + L.b[2]);
+  if constexpr (EXP) {
+    // group gq = j * g8n + g8 holds tap j's view of channel group g8: pixel px of the chunk at
+    // raw row (tap / 3 - r0), raw column pu - 1 + px + tap % 3
+    for (int u = et; u < nt * g8n * kW3KP; u += kThr) {
+      const int gq = u / kW3KP, px = u % kW3KP;
+      const int j = gq / g8n, g8 = gq - j * g8n, tap = t0 + j;
+      const int r = tap / 3 - r0, col = pu - 1 + px + tap % 3;
+      split3_group(raw[((2 * g8) * R + r) * PR + col], raw[((2 * g8 + 1) * R + r) * PR + col], b0,
+                   b1, b2, u);
+    }
+    return;
+  }
   const int nmain = g8n * R * kW3KP;
   for (int u = et; u < nmain; u += kThr) {
     const int q = u / kW3KP, i = 1 + u % kW3KP;  // q = g8 * R + r, part column i
@@ -781,8 +798,8 @@ __device__ __forceinline__ void split3_stage(const uint8_t* st, uint8_t* stw, co
   }
 }
 
-template <int R>
-__global__ void __launch_bounds__(kW3Threads, 1) k_wgrad_tc_f32(const __grid_constant__ CUtensorMap tmD,
+template <int R, int EXP>
+__global__ void __launch_bounds__(kW3Threads, 2) k_wgrad_tc_f32(const __grid_constant__ CUtensorMap tmD,
                                                                const __grid_constant__ CUtensorMap tmX,
                                                                WgBf16Params p) {
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -799,7 +816,7 @@ __global__ void __launch_bounds__(kW3Threads, 1) k_wgrad_tc_f32(const __grid_con
   const int cend = min(p.total_chunks, cbeg + p.per_split);
   const int nk = cend > cbeg ? cend - cbeg : 0;
   const int pu = p.pu;
-  const W3Layout L = w3_layout(cn, R, pu);
+  const W3Layout L = w3_layout(cn, R, pu, EXP, nt);
   const uint32_t RB = (uint32_t)cn * R * w3_raw_pitch(pu) * 4;
   const bool bias = grp == 0;
   const uint32_t ncols = tmem_cols(nt * cn + (bias ? 16 : 0));
@@ -816,7 +833,8 @@ __global__ void __launch_bounds__(kW3Threads, 1) k_wgrad_tc_f32(const __grid_con
   }
   if (warp == 1) tmem_alloc(&tslot, ncols);
   if (bias) {  // part 0: ones, parts 1 and 2: zeros, so the bias columns sum a0 + a1 + a2
-    const uint32_t eo = (uint32_t)cn * R * (kW3KP + 2) * 2, eb = 2u * R * (kW3KP + 2) * 16;
+    const uint32_t eo = EXP ? (uint32_t)nt * cn / 8 * kW3KP * 16 : (uint32_t)cn * R * (kW3KP + 2) * 2;
+    const uint32_t eb = EXP ? 2u * kW3KP * 16 : 2u * R * (kW3KP + 2) * 16;
     for (int s = 0; s < ns; ++s)
       for (int q = 0; q < 3; ++q)
         fill_ext(smem + s * L.stage + L.b[q] + eo, eb, q == 0 ? kBf16PairOne : 0u);
@@ -858,20 +876,40 @@ __global__ void __launch_bounds__(kW3Threads, 1) k_wgrad_tc_f32(const __grid_con
         uint64_t da[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) da[k] = sdesc(st + L.a[k], 128, a_sbo);
-        for (int j = 0; j < nt; ++j) {
-          const int tap = t0 + j;
-          const uint32_t boff = (uint32_t)(((tap / 3) - r0) * (kW3KP + 2) + (tap % 3)) * 16u;
-          uint64_t db[3];
+        if constexpr (EXP) {
+          // the taps side by side along N, in chunks of at most 256 columns (multiples of 16)
+          const int ntot = nt * cn, nch = (ntot + 255) / 256;
+          const int csz = (ntot / nch + 15) / 16 * 16;
+          for (int c0 = 0; c0 < ntot; c0 += csz) {
+            const int n = min(csz, ntot - c0) + ((bias && c0 + csz >= ntot) ? 16 : 0);
+            const uint32_t id = idesc(1, 128, n, 1, 1);
+            uint64_t db[3];
 #pragma unroll
-          for (int k = 0; k < 3; ++k) db[k] = sdesc(st + L.b[k] + boff, 128, b_sbo);
-          const uint32_t d = tbase + (uint32_t)(j * cn);
-          const uint32_t id = (bias && j == nt - 1) ? idx : idn;
-          mma_f16(d, da[0], db[0], id, i > 0 ? 1u : 0u);
-          mma_f16(d, da[0], db[1], id, 1u);
-          mma_f16(d, da[1], db[0], id, 1u);
-          mma_f16(d, da[0], db[2], id, 1u);
-          mma_f16(d, da[1], db[1], id, 1u);
-          mma_f16(d, da[2], db[0], id, 1u);
+            for (int q = 0; q < 3; ++q) db[q] = sdesc(st + L.b[q] + (uint32_t)(c0 / 8) * kW3KP * 16u, 128, kW3KP * 16);
+            const uint32_t d = tbase + (uint32_t)c0;
+            mma_f16(d, da[0], db[0], id, i > 0 ? 1u : 0u);
+            mma_f16(d, da[0], db[1], id, 1u);
+            mma_f16(d, da[1], db[0], id, 1u);
+            mma_f16(d, da[0], db[2], id, 1u);
+            mma_f16(d, da[1], db[1], id, 1u);
+            mma_f16(d, da[2], db[0], id, 1u);
+          }
+        } else {
+        for (int j = 0; j < nt; ++j) {
+            const int tap = t0 + j;
+            const uint32_t boff = (uint32_t)(((tap / 3) - r0) * (kW3KP + 2) + (tap % 3)) * 16u;
+            uint64_t db[3];
+  #pragma unroll
+            for (int k = 0; k < 3; ++k) db[k] = sdesc(st + L.b[k] + boff, 128, b_sbo);
+            const uint32_t d = tbase + (uint32_t)(j * cn);
+            const uint32_t id = (bias && j == nt - 1) ? idx : idn;
+            mma_f16(d, da[0], db[0], id, i > 0 ? 1u : 0u);
+            mma_f16(d, da[0], db[1], id, 1u);
+            mma_f16(d, da[1], db[0], id, 1u);
+            mma_f16(d, da[0], db[2], id, 1u);
+            mma_f16(d, da[1], db[1], id, 1u);
+            mma_f16(d, da[2], db[0], id, 1u);
+          }
         }
         mma_commit(&empty[s]);
       }
@@ -883,7 +921,7 @@ __global__ void __launch_bounds__(kW3Threads, 1) k_wgrad_tc_f32(const __grid_con
       const int s = i % ns;
       if (!mbar_wait(&full[s], (i / ns) & 1, abort, p.err)) break;
       uint8_t* st = smem + s * L.stage;
-      split3_stage<R>(st, st, L, cn / 8, pu, et);
+      split3_stage<R, EXP>(st, st, L, cn / 8, pu, et, nt, t0, r0);
       fence_proxy_async();
       __syncwarp();
       if (lane == 0) mbar_arrive(&split[s]);
@@ -1040,8 +1078,9 @@ cudaError_t tc_prepare() {
     set((const void*)k_conv_tc<0, 0, 1>);
     set((const void*)k_conv_tc<0, 1, 1>);
     set((const void*)k_wgrad_tc_bf16);
-    set((const void*)k_wgrad_tc_f32<1>);
-    set((const void*)k_wgrad_tc_f32<3>);
+    set((const void*)k_wgrad_tc_f32<1, 0>);
+    set((const void*)k_wgrad_tc_f32<1, 1>);
+    set((const void*)k_wgrad_tc_f32<3, 1>);
     result = e;
   });
   return result;
@@ -1304,7 +1343,9 @@ static cudaError_t launch_wgrad_grouped(int bf16, const void* dout, const void* 
   }
   const int max_res = 512 / (int)tmem_cols(maxcols);  // CTAs per SM that TMEM allows
   // as many stages as fit beside the CTAs that TMEM allows on one SM
-  const uint32_t sb = bf16 ? wb_stage(tg.cn, tg.R, pu) : w3_layout(tg.cn, tg.R, pu).stage;
+  // float32 form: tap-expanded x parts when a tap alone would give MMAs of N <= 64
+  const bool exp = !bf16 && tg.cn <= 64;
+  const uint32_t sb = bf16 ? wb_stage(tg.cn, tg.R, pu) : w3_layout(tg.cn, tg.R, pu, exp, tg.count[0]).stage;
   const int max_stages = bf16 ? kWbMaxStages : kW3MaxStages;
   p.stages = (int)((227u * 1024u / (uint32_t)max_res - 2048u) / sb);
   if (p.stages > max_stages) p.stages = max_stages;
@@ -1332,10 +1373,12 @@ static cudaError_t launch_wgrad_grouped(int bf16, const void* dout, const void* 
   const dim3 grid((unsigned)otiles, (unsigned)tg.n, (unsigned)S);
   if (bf16)
     k_wgrad_tc_bf16<<<grid, 192, smem, st>>>(md, mx, p);
-  else if (tg.R == 1)
-    k_wgrad_tc_f32<1><<<grid, kW3Threads, smem, st>>>(md, mx, p);
+  else if (tg.R == 3)
+    k_wgrad_tc_f32<3, 1><<<grid, kW3Threads, smem, st>>>(md, mx, p);
+  else if (exp)
+    k_wgrad_tc_f32<1, 1><<<grid, kW3Threads, smem, st>>>(md, mx, p);
   else
-    k_wgrad_tc_f32<3><<<grid, kW3Threads, smem, st>>>(md, mx, p);
+    k_wgrad_tc_f32<1, 0><<<grid, kW3Threads, smem, st>>>(md, mx, p);
   count_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_reduce_wgrad_tc<<<(unsigned)(((cout + kRwO - 1) / kRwO) * cin), 256, 0, st>>>(part, S, cin,
