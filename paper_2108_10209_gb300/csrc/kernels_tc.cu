@@ -559,12 +559,23 @@ __host__ __device__ inline uint32_t wb_ext_bytes(int R, int pu) { return 2u * R 
 __host__ __device__ inline uint32_t wb_stage(int cin, int R, int pu) {
   return align_up(kWbA, 1024) + align_up(wb_b_bytes(cin, R, pu) + wb_ext_bytes(R, pu), 1024);
 }
+// tap-expanded stage (small C_in): after the raw x tile, [taps x C/8 + 2][KP px][16 B] with the
+// two bias groups (ones) last, so one MMA spans every tap of the group
+__host__ __device__ inline uint32_t wb_exp_off(int cin, int R, int pu) {
+  return align_up(kWbA, 1024) + align_up(wb_b_bytes(cin, R, pu), 1024);
+}
+__host__ __device__ inline uint32_t wb_stage_exp(int cin, int R, int pu, int taps) {
+  return wb_exp_off(cin, R, pu) + align_up(((uint32_t)taps * cin / 8 + 2) * kWbKP * 16, 1024);
+}
 
+// EXP = 1 (small C_in): warps 2-5 first copy each stage's x tile into the tap-expanded layout
+// (pure 16-byte copies), then serve as the epilogue.
+template <int EXP>
 __global__ void __launch_bounds__(192, 1) k_wgrad_tc_bf16(const __grid_constant__ CUtensorMap tmD,
                                                          const __grid_constant__ CUtensorMap tmX,
                                                          WgBf16Params p) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  __shared__ uint64_t full[kWbMaxStages], empty[kWbMaxStages], accf;
+  __shared__ uint64_t full[kWbMaxStages], empty[kWbMaxStages], split[kWbMaxStages], accf;
   __shared__ uint32_t tslot;
   __shared__ int abort_flag;
   if (p.skip && *p.skip) return;
@@ -577,7 +588,9 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc_bf16(const __grid_constant_
   const int cend = min(p.total_chunks, cbeg + p.per_split);
   const int nk = cend > cbeg ? cend - cbeg : 0;
   const int pu = p.pu, HX = wb_pitch(pu);
-  const uint32_t BB = wb_b_bytes(cn, R, pu), SB = wb_stage(cn, R, pu);
+  const uint32_t BB = wb_b_bytes(cn, R, pu);
+  const uint32_t SB = EXP ? wb_stage_exp(cn, R, pu, nt) : wb_stage(cn, R, pu);
+  const uint32_t e_off = wb_exp_off(cn, R, pu);
   const uint32_t b_off = align_up(kWbA, 1024);
   const bool bias = grp == 0;
   const uint32_t ncols = tmem_cols(nt * cn + (bias ? 16 : 0));
@@ -586,6 +599,7 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc_bf16(const __grid_constant_
     for (int s = 0; s < ns; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
+      mbar_init(&split[s], 4);
     }
     mbar_init(&accf, 1);
     abort_flag = 0;
@@ -593,7 +607,12 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc_bf16(const __grid_constant_
   }
   if (warp == 1) tmem_alloc(&tslot, ncols);
   if (bias) {
-    for (int s = 0; s < ns; ++s) fill_ext(smem + s * SB + b_off + BB, wb_ext_bytes(R, pu), kBf16PairOne);
+    for (int s = 0; s < ns; ++s)
+      if (EXP)
+        fill_ext(smem + s * SB + e_off + (uint32_t)nt * cn / 8 * kWbKP * 16, 2u * kWbKP * 16,
+                 kBf16PairOne);
+      else
+        fill_ext(smem + s * SB + b_off + BB, wb_ext_bytes(R, pu), kBf16PairOne);
     fence_proxy_async();
   }
   tc_fence_before();
@@ -627,19 +646,35 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc_bf16(const __grid_constant_
       const uint32_t b_sbo = (uint32_t)R * HX * 16;  // next 8-channel group of x
       for (int i = 0; i < nk; ++i) {
         const int s = i % ns;
-        if (!mbar_wait(&full[s], (i / ns) & 1, abort, p.err)) break;
+        if (!mbar_wait(EXP ? &split[s] : &full[s], (i / ns) & 1, abort, p.err)) break;
         tc_fence_after();
         const uint32_t sa = smem_u32(smem + s * SB), sb = sa + b_off;
-        for (int j = 0; j < nt; ++j) {
-          const int tap = t0 + j;
-          // pixel p of the chunk, tap column dx, sits at halo column p + dx - 1 + pu
-          const uint32_t boff = (uint32_t)(((tap / 3) - r0) * HX + (tap % 3) + pu - 1) * 16u;
+        if constexpr (EXP) {
+          // taps side by side along N, in chunks of at most 256 columns (multiples of 16)
+          const int ntot = nt * cn, nch = (ntot + 255) / 256;
+          const int csz = (ntot / nch + 15) / 16 * 16;
+          for (int c0 = 0; c0 < ntot; c0 += csz) {
+            const int n = min(csz, ntot - c0) + ((bias && c0 + csz >= ntot) ? 16 : 0);
+            const uint32_t idc = idesc(1, 128, n, 1, 1);
+            const uint32_t eb = sa + e_off + (uint32_t)(c0 / 8) * kWbKP * 16u;
 #pragma unroll
-          for (int k = 0; k < kWbKP / 16; ++k) {
-            const uint32_t ko = (uint32_t)k * 16u * 16u;
-            mma_f16(tbase + (uint32_t)(j * cn), sdesc(sa + ko, 128, a_sbo),
-                    sdesc(sb + boff + ko, 128, b_sbo), (bias && j == nt - 1) ? idx : id,
-                    (i > 0 || k > 0) ? 1u : 0u);
+            for (int k = 0; k < kWbKP / 16; ++k)
+              mma_f16(tbase + (uint32_t)c0, sdesc(sa + (uint32_t)k * 256u, 128, a_sbo),
+                      sdesc(eb + (uint32_t)k * 256u, 128, kWbKP * 16), idc,
+                      (i > 0 || k > 0) ? 1u : 0u);
+          }
+        } else {
+          for (int j = 0; j < nt; ++j) {
+            const int tap = t0 + j;
+            // pixel p of the chunk, tap column dx, sits at halo column p + dx - 1 + pu
+            const uint32_t boff = (uint32_t)(((tap / 3) - r0) * HX + (tap % 3) + pu - 1) * 16u;
+#pragma unroll
+            for (int k = 0; k < kWbKP / 16; ++k) {
+              const uint32_t ko = (uint32_t)k * 16u * 16u;
+              mma_f16(tbase + (uint32_t)(j * cn), sdesc(sa + ko, 128, a_sbo),
+                      sdesc(sb + boff + ko, 128, b_sbo), (bias && j == nt - 1) ? idx : id,
+                      (i > 0 || k > 0) ? 1u : 0u);
+            }
           }
         }
         mma_commit(&empty[s]);
@@ -647,6 +682,25 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc_bf16(const __grid_constant_
       mma_commit(&accf);
     }
   } else {
+    if constexpr (EXP) {
+      // group gq = j * g8n + g8 holds tap j's view of channel group g8: pixel px of the chunk
+      // at raw row (tap / 3 - r0), raw column pu - 1 + px + tap % 3
+      const int g8n = cn / 8, et = threadIdx.x - 64;
+      for (int i = 0; i < nk; ++i) {
+        const int s = i % ns;
+        if (!mbar_wait(&full[s], (i / ns) & 1, abort, p.err)) break;
+        const uint4* raw = reinterpret_cast<const uint4*>(smem + s * SB + b_off);
+        uint4* ex = reinterpret_cast<uint4*>(smem + s * SB + e_off);
+        for (int u = et; u < nt * g8n * kWbKP; u += 128) {
+          const int gq = u / kWbKP, px = u % kWbKP;
+          const int j = gq / g8n, g8 = gq - j * g8n, tap = t0 + j;
+          ex[u] = raw[(g8 * R + (tap / 3 - r0)) * HX + pu - 1 + px + tap % 3];
+        }
+        fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&split[s]);
+      }
+    }
     if (!mbar_wait(&accf, 0, abort, p.err)) mbar_drain(&accf, 0);
     tc_fence_after();
     const int wq = warp & 3;
@@ -899,7 +953,7 @@ __global__ void __launch_bounds__(kW3Threads, 2) k_wgrad_tc_f32(const __grid_con
             const int tap = t0 + j;
             const uint32_t boff = (uint32_t)(((tap / 3) - r0) * (kW3KP + 2) + (tap % 3)) * 16u;
             uint64_t db[3];
-  #pragma unroll
+#pragma unroll
             for (int k = 0; k < 3; ++k) db[k] = sdesc(st + L.b[k] + boff, 128, b_sbo);
             const uint32_t d = tbase + (uint32_t)(j * cn);
             const uint32_t id = (bias && j == nt - 1) ? idx : idn;
@@ -1077,7 +1131,8 @@ cudaError_t tc_prepare() {
     set((const void*)k_conv_tc<1, 1, 1>);
     set((const void*)k_conv_tc<0, 0, 1>);
     set((const void*)k_conv_tc<0, 1, 1>);
-    set((const void*)k_wgrad_tc_bf16);
+    set((const void*)k_wgrad_tc_bf16<0>);
+    set((const void*)k_wgrad_tc_bf16<1>);
     set((const void*)k_wgrad_tc_f32<1, 0>);
     set((const void*)k_wgrad_tc_f32<1, 1>);
     set((const void*)k_wgrad_tc_f32<3, 1>);
@@ -1343,9 +1398,11 @@ static cudaError_t launch_wgrad_grouped(int bf16, const void* dout, const void* 
   }
   const int max_res = 512 / (int)tmem_cols(maxcols);  // CTAs per SM that TMEM allows
   // as many stages as fit beside the CTAs that TMEM allows on one SM
-  // float32 form: tap-expanded x parts when a tap alone would give MMAs of N <= 64
-  const bool exp = !bf16 && tg.cn <= 64;
-  const uint32_t sb = bf16 ? wb_stage(tg.cn, tg.R, pu) : w3_layout(tg.cn, tg.R, pu, exp, tg.count[0]).stage;
+  // tap-expanded x operand when a tap alone would give MMAs of small N: float32 form for
+  // C_in <= 64, bf16 form for C_in = 32 (its expansion is a copy pass)
+  const bool exp = bf16 ? tg.cn <= 32 : tg.cn <= 64;
+  const uint32_t sb = bf16 ? (exp ? wb_stage_exp(tg.cn, tg.R, pu, tg.count[0]) : wb_stage(tg.cn, tg.R, pu))
+                           : w3_layout(tg.cn, tg.R, pu, exp, tg.count[0]).stage;
   const int max_stages = bf16 ? kWbMaxStages : kW3MaxStages;
   p.stages = (int)((227u * 1024u / (uint32_t)max_res - 2048u) / sb);
   if (p.stages > max_stages) p.stages = max_stages;
@@ -1371,8 +1428,10 @@ static cudaError_t launch_wgrad_grouped(int bf16, const void* dout, const void* 
   p.skip = skip;
   p.err = err;
   const dim3 grid((unsigned)otiles, (unsigned)tg.n, (unsigned)S);
-  if (bf16)
-    k_wgrad_tc_bf16<<<grid, 192, smem, st>>>(md, mx, p);
+  if (bf16 && exp)
+    k_wgrad_tc_bf16<1><<<grid, 192, smem, st>>>(md, mx, p);
+  else if (bf16)
+    k_wgrad_tc_bf16<0><<<grid, 192, smem, st>>>(md, mx, p);
   else if (tg.R == 3)
     k_wgrad_tc_f32<3, 1><<<grid, kW3Threads, smem, st>>>(md, mx, p);
   else if (exp)
