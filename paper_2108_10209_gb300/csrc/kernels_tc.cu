@@ -177,18 +177,20 @@ struct alignas(128) ConvJob {
 };
 
 constexpr int kTileM = 128;   // pixels per accumulator (one image row segment)
-constexpr int kRowsM = 2;     // image rows per CTA: each weight stage feeds two accumulators
+constexpr int kRowsM = 2;     // image rows per tile by default: each weight stage feeds two
+                              // accumulators (1 is a tuning choice: twice the tiles, half the
+                              // accumulator columns, so TMEM double-buffers at N = 256)
 constexpr int kHaloX = kTileM + 2;
-constexpr int kHaloY = kRowsM + 2;
 constexpr int kConvMaxStages = 4;
 
-template <int BF16>
+template <int BF16, int ROWS = kRowsM>
 struct ConvCfg {
   static constexpr int GE = BF16 ? 8 : 4;     // channels per 16-byte group
   static constexpr int KC = BF16 ? 16 : 8;    // channels per stage (= one K step of 32 bytes)
   static constexpr int NSLAB = KC / GE;       // 16-byte K slabs per stage (2)
-  static constexpr uint32_t A_BYTES = NSLAB * kHaloY * kHaloX * 16;
-  static constexpr uint32_t A_SLAB = kHaloY * kHaloX * 16;  // K distance between halo slabs
+  static constexpr int HALO_Y = ROWS + 2;
+  static constexpr uint32_t A_BYTES = NSLAB * HALO_Y * kHaloX * 16;
+  static constexpr uint32_t A_SLAB = HALO_Y * kHaloX * 16;  // K distance between halo slabs
   static __host__ __device__ uint32_t b_bytes(int NT) { return 9u * NSLAB * NT * 16; }
   // stage layout: A | A_lo (tf32) | B | B_lo (tf32)
   static __host__ __device__ uint32_t a_lo_off() { return align_up(A_BYTES, 1024); }
@@ -226,11 +228,11 @@ struct TileJob {
 // GROUPED = 0: one image, the tensor map a kernel parameter. GROUPED = 1: the tiles of
 // `njobs` images of the same layer shape (p.cin, p.cout), ntiles = p.tiles_x in total; every
 // role walks the same tile sequence and skips the tiles of stopped jobs.
-template <int BF16, int MODE, int GROUPED>
+template <int BF16, int MODE, int GROUPED, int ROWS>
 __global__ void __launch_bounds__(ConvWarps<BF16>::kThreads, 1)
     k_conv_tc(const __grid_constant__ CUtensorMap tmA, ConvTcParams p,
               const ConvJob* __restrict__ jobs, int njobs) {
-  using C = ConvCfg<BF16>;
+  using C = ConvCfg<BF16, ROWS>;
   using T = typename std::conditional<BF16, __nv_bfloat16, float>::type;
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ uint64_t full[kConvMaxStages], empty[kConvMaxStages], split[kConvMaxStages];
@@ -244,7 +246,7 @@ __global__ void __launch_bounds__(ConvWarps<BF16>::kThreads, 1)
   const int NS = p.stages;
   const int nk = p.cin / C::KC;
   const int ntn = p.cout / NT;
-  const int ntiles = GROUPED ? p.tiles_x : p.tiles_x * ((p.H + kRowsM - 1) / kRowsM) * ntn;
+  const int ntiles = GROUPED ? p.tiles_x : p.tiles_x * ((p.H + ROWS - 1) / ROWS) * ntn;
   // tile -> its job; `cur` is the role's cursor (tiles only grow along a role's sequence)
   auto locate = [&](int tile, int& cur) {
     TileJob t;
@@ -262,7 +264,7 @@ __global__ void __launch_bounds__(ConvWarps<BF16>::kThreads, 1)
     }
     return t;
   };
-  const int acc_cols = kRowsM * NT;
+  const int acc_cols = ROWS * NT;
   const int NB = 2 * acc_cols <= 512 ? 2 : 1;  // accumulator buffers
   const uint32_t ncols = tmem_cols(NB * acc_cols);
   volatile int* abort = &abort_flag;
@@ -289,7 +291,7 @@ __global__ void __launch_bounds__(ConvWarps<BF16>::kThreads, 1)
   auto decode = [&](const TileJob& t, int& nt, int& ty, int& x0) {
     nt = t.local % ntn;
     const int rest = t.local / ntn;
-    ty = (rest / t.tiles_x) * kRowsM;
+    ty = (rest / t.tiles_x) * ROWS;
     x0 = (rest % t.tiles_x) * kTileM;
   };
 
@@ -348,7 +350,7 @@ __global__ void __launch_bounds__(ConvWarps<BF16>::kThreads, 1)
             const uint64_t db = sdesc(sb + bo, NT * 16, 128);
             const uint32_t acc = (i > 0 || tap > 0) ? 1u : 0u;
 #pragma unroll
-            for (int r = 0; r < kRowsM; ++r) {  // output row r reads halo rows r .. r + 2
+            for (int r = 0; r < ROWS; ++r) {  // output row r reads halo rows r .. r + 2
               const uint32_t ao = (uint32_t)((r + tap / 3) * kHaloX + (tap % 3)) * 16u;
               const uint64_t da = sdesc(sa + ao, C::A_SLAB, 128);
               const uint32_t d = dbase + (uint32_t)(r * NT);
@@ -411,7 +413,7 @@ __global__ void __launch_bounds__(ConvWarps<BF16>::kThreads, 1)
       const size_t npx = (size_t)tj.H * tj.W;
       const int npx_row = min(kTileM, tj.W - x0);
       const char* m = static_cast<const char*>(tj.mask);
-      for (int r = 0; r < kRowsM && ty + r < tj.H; ++r)
+      for (int r = 0; r < ROWS && ty + r < tj.H; ++r)
         for (int g = nt * NT / GE; g < (nt + 1) * NT / GE; ++g)
           bulk_prefetch_l2(m + ((size_t)g * npx + (size_t)(ty + r) * tj.W + x0) * 16,
                            (uint32_t)npx_row * 16u);
@@ -1092,10 +1094,11 @@ cudaError_t launch_reduce_cols(const float* part, int R, int C, float* out, cons
 
 namespace {
 
-template <int BF16, int MODE, int GROUPED>
+template <int BF16, int MODE, int GROUPED, int ROWS>
 cudaError_t conv_tc_launch(const CUtensorMap& m, const ConvTcParams& p, const ConvJob* jobs,
                            int njobs, dim3 grid, uint32_t smem, cudaStream_t st) {
-  k_conv_tc<BF16, MODE, GROUPED><<<grid, ConvWarps<BF16>::kThreads, smem, st>>>(m, p, jobs, njobs);
+  k_conv_tc<BF16, MODE, GROUPED, ROWS><<<grid, ConvWarps<BF16>::kThreads, smem, st>>>(m, p, jobs,
+                                                                                    njobs);
   return cudaGetLastError();
 }
 
@@ -1123,14 +1126,18 @@ cudaError_t tc_prepare() {
         e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  optin - (int)fa.sharedSizeBytes);
     };
-    set((const void*)k_conv_tc<1, 0, 0>);
-    set((const void*)k_conv_tc<1, 1, 0>);
-    set((const void*)k_conv_tc<0, 0, 0>);
-    set((const void*)k_conv_tc<0, 1, 0>);
-    set((const void*)k_conv_tc<1, 0, 1>);
-    set((const void*)k_conv_tc<1, 1, 1>);
-    set((const void*)k_conv_tc<0, 0, 1>);
-    set((const void*)k_conv_tc<0, 1, 1>);
+    set((const void*)k_conv_tc<1, 0, 0, 2>);
+    set((const void*)k_conv_tc<1, 0, 0, 1>);
+    set((const void*)k_conv_tc<1, 1, 0, 2>);
+    set((const void*)k_conv_tc<1, 1, 0, 1>);
+    set((const void*)k_conv_tc<0, 0, 0, 2>);
+    set((const void*)k_conv_tc<0, 0, 0, 1>);
+    set((const void*)k_conv_tc<0, 1, 0, 2>);
+    set((const void*)k_conv_tc<0, 1, 0, 1>);
+    set((const void*)k_conv_tc<1, 0, 1, 2>);
+    set((const void*)k_conv_tc<1, 1, 1, 2>);
+    set((const void*)k_conv_tc<0, 0, 1, 2>);
+    set((const void*)k_conv_tc<0, 1, 1, 2>);
     set((const void*)k_wgrad_tc_bf16<0>);
     set((const void*)k_wgrad_tc_bf16<1>);
     set((const void*)k_wgrad_tc_f32<1, 0>);
@@ -1159,15 +1166,16 @@ size_t tc_weight_elems(int cin, int cout) { return (size_t)cin * cout * 9; }
 // pipeline stages and the CTAs resident per SM (capped by TMEM, 512 columns, and by shared
 // memory; shared memory is padded so that exactly the chosen number fit).
 struct ConvTune {
-  int stages = 2, per_sm = 0;  // per_sm 0: as many as fit
+  int stages = 2, per_sm = 0, rows = kRowsM;  // per_sm 0: as many as fit
 };
 
-static uint32_t conv_stage_bytes(int bf16, int NT) {
-  return bf16 ? ConvCfg<1>::stage_bytes(NT) : ConvCfg<0>::stage_bytes(NT);
+static uint32_t conv_stage_bytes(int bf16, int NT, int rows) {
+  if (rows == 1) return bf16 ? ConvCfg<1, 1>::stage_bytes(NT) : ConvCfg<0, 1>::stage_bytes(NT);
+  return bf16 ? ConvCfg<1, 2>::stage_bytes(NT) : ConvCfg<0, 2>::stage_bytes(NT);
 }
 
-static int conv_max_res(int NT) {
-  const int acc_cols = kRowsM * NT;
+static int conv_max_res(int NT, int rows) {
+  const int acc_cols = rows * NT;
   return 512 / (int)tmem_cols((2 * acc_cols <= 512 ? 2 : 1) * acc_cols);
 }
 
@@ -1190,8 +1198,9 @@ static cudaError_t conv_tc_dispatch(int mode, int bf16, const CUtensorMap& m, Co
                                     const ConvJob* jobs, int njobs, long ntiles, ConvTune tune,
                                     cudaStream_t st) {
   const TcCfg f = tc_cfg(p.cin, p.cout, bf16);
-  const uint32_t sb = conv_stage_bytes(bf16, f.NT);
-  const int max_res = conv_max_res(f.NT);
+  const int rows = jobs ? kRowsM : tune.rows;  // grouped launches keep the default tiles
+  const uint32_t sb = conv_stage_bytes(bf16, f.NT, rows);
+  const int max_res = conv_max_res(f.NT, rows);
   int stages = tune.stages;
   while (stages > 2 && (uint32_t)stages * sb > 227u * 1024u - 2048u) --stages;
   uint32_t smem = (uint32_t)stages * sb;
@@ -1205,28 +1214,34 @@ static cudaError_t conv_tc_dispatch(int mode, int bf16, const CUtensorMap& m, Co
   const long slots = 152L * per_sm;
   dim3 grid((unsigned)(ntiles < slots ? ntiles : slots), 1);
   if (grid.x == 0) return cudaSuccess;
-  const int g = jobs != nullptr;
-  if (bf16) {
-    if (mode == 0)
-      return g ? conv_tc_launch<1, 0, 1>(m, p, jobs, njobs, grid, smem, st)
-               : conv_tc_launch<1, 0, 0>(m, p, jobs, njobs, grid, smem, st);
-    return g ? conv_tc_launch<1, 1, 1>(m, p, jobs, njobs, grid, smem, st)
-             : conv_tc_launch<1, 1, 0>(m, p, jobs, njobs, grid, smem, st);
+  if (jobs) {
+    if (bf16)
+      return mode == 0 ? conv_tc_launch<1, 0, 1, 2>(m, p, jobs, njobs, grid, smem, st)
+                       : conv_tc_launch<1, 1, 1, 2>(m, p, jobs, njobs, grid, smem, st);
+    return mode == 0 ? conv_tc_launch<0, 0, 1, 2>(m, p, jobs, njobs, grid, smem, st)
+                     : conv_tc_launch<0, 1, 1, 2>(m, p, jobs, njobs, grid, smem, st);
   }
-  if (mode == 0)
-    return g ? conv_tc_launch<0, 0, 1>(m, p, jobs, njobs, grid, smem, st)
-             : conv_tc_launch<0, 0, 0>(m, p, jobs, njobs, grid, smem, st);
-  return g ? conv_tc_launch<0, 1, 1>(m, p, jobs, njobs, grid, smem, st)
-           : conv_tc_launch<0, 1, 0>(m, p, jobs, njobs, grid, smem, st);
+  if (rows == 1) {
+    if (bf16)
+      return mode == 0 ? conv_tc_launch<1, 0, 0, 1>(m, p, jobs, njobs, grid, smem, st)
+                       : conv_tc_launch<1, 1, 0, 1>(m, p, jobs, njobs, grid, smem, st);
+    return mode == 0 ? conv_tc_launch<0, 0, 0, 1>(m, p, jobs, njobs, grid, smem, st)
+                     : conv_tc_launch<0, 1, 0, 1>(m, p, jobs, njobs, grid, smem, st);
+  }
+  if (bf16)
+    return mode == 0 ? conv_tc_launch<1, 0, 0, 2>(m, p, jobs, njobs, grid, smem, st)
+                     : conv_tc_launch<1, 1, 0, 2>(m, p, jobs, njobs, grid, smem, st);
+  return mode == 0 ? conv_tc_launch<0, 0, 0, 2>(m, p, jobs, njobs, grid, smem, st)
+                   : conv_tc_launch<0, 1, 0, 2>(m, p, jobs, njobs, grid, smem, st);
 }
 
 static cudaError_t conv_params(int bf16, const void* in, int cin, int cout, int H, int W,
                                const void* w_hi, const void* w_lo, const float* b,
-                               const void* mask, void* out, const int* skip, int* err,
+                               const void* mask, void* out, const int* skip, int* err, int rows,
                                CUtensorMap* m, ConvTcParams* p) {
   const int KC = bf16 ? ConvCfg<1>::KC : ConvCfg<0>::KC;
   const int GE = bf16 ? 8 : 4;
-  cudaError_t e = make_map(m, in, bf16, cin, H, W, kHaloX, kHaloY, KC / GE);
+  cudaError_t e = make_map(m, in, bf16, cin, H, W, kHaloX, rows + 2, KC / GE);
   if (e != cudaSuccess) return e;
   p->w_hi = (const uint8_t*)w_hi;
   p->w_lo = (const uint8_t*)w_lo;
@@ -1254,35 +1269,36 @@ cudaError_t conv_tc_autotune(int mode, int bf16, const void* in, int cin, int co
     std::lock_guard<std::mutex> lk(g_tune_mu);
     if (g_tune.count(key)) return cudaSuccess;
   }
-  CUtensorMap m;
-  ConvTcParams p;
-  cudaError_t e = conv_params(bf16, in, cin, cout, H, W, w_hi, w_lo, b, mask, out, nullptr, err,
-                              &m, &p);
-  if (e != cudaSuccess) return e;
   const TcCfg f = tc_cfg(cin, cout, bf16);
-  const long ntiles = (long)p.tiles_x * ((H + kRowsM - 1) / kRowsM) * (cout / f.NT);
-  const uint32_t sb = conv_stage_bytes(bf16, f.NT);
   cudaEvent_t a = nullptr, z = nullptr;
-  e = cudaEventCreate(&a);
+  cudaError_t e = cudaEventCreate(&a);
   if (e == cudaSuccess) e = cudaEventCreate(&z);
   ConvTune best;
   float best_ms = 1e30f;
-  for (int stages = 2; stages <= kConvMaxStages && e == cudaSuccess; ++stages) {
-    if ((uint32_t)stages * sb > 227u * 1024u - 2048u) break;
-    for (int per_sm = 1; per_sm <= conv_max_res(f.NT) && e == cudaSuccess; ++per_sm) {
-      if (per_sm * ((uint32_t)stages * sb + 2048u) > 227u * 1024u) break;
-      const ConvTune t{stages, per_sm};
-      float ms = 0.f;
-      e = conv_tc_dispatch(mode, bf16, m, p, nullptr, 0, ntiles, t, st);  // warm-up
-      if (e == cudaSuccess) e = cudaEventRecord(a, st);
-      for (int r = 0; r < 3 && e == cudaSuccess; ++r)
-        e = conv_tc_dispatch(mode, bf16, m, p, nullptr, 0, ntiles, t, st);
-      if (e == cudaSuccess) e = cudaEventRecord(z, st);
-      if (e == cudaSuccess) e = cudaEventSynchronize(z);
-      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, z);
-      if (e == cudaSuccess && ms < best_ms) {
-        best_ms = ms;
-        best = t;
+  for (int rows = 1; rows <= 2 && e == cudaSuccess; ++rows) {
+    CUtensorMap m;
+    ConvTcParams p;
+    e = conv_params(bf16, in, cin, cout, H, W, w_hi, w_lo, b, mask, out, nullptr, err, rows, &m, &p);
+    if (e != cudaSuccess) break;
+    const long ntiles = (long)p.tiles_x * ((H + rows - 1) / rows) * (cout / f.NT);
+    const uint32_t sb = conv_stage_bytes(bf16, f.NT, rows);
+    for (int stages = 2; stages <= kConvMaxStages && e == cudaSuccess; ++stages) {
+      if ((uint32_t)stages * sb > 227u * 1024u - 2048u) break;
+      for (int per_sm = 1; per_sm <= conv_max_res(f.NT, rows) && e == cudaSuccess; ++per_sm) {
+        if (per_sm * ((uint32_t)stages * sb + 2048u) > 227u * 1024u) break;
+        const ConvTune t{stages, per_sm, rows};
+        float ms = 0.f;
+        e = conv_tc_dispatch(mode, bf16, m, p, nullptr, 0, ntiles, t, st);  // warm-up
+        if (e == cudaSuccess) e = cudaEventRecord(a, st);
+        for (int r = 0; r < 3 && e == cudaSuccess; ++r)
+          e = conv_tc_dispatch(mode, bf16, m, p, nullptr, 0, ntiles, t, st);
+        if (e == cudaSuccess) e = cudaEventRecord(z, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(z);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, z);
+        if (e == cudaSuccess && ms < best_ms) {
+          best_ms = ms;
+          best = t;
+        }
       }
     }
   }
@@ -1300,14 +1316,14 @@ cudaError_t launch_conv_tc(int mode, int bf16, const void* in, int cin, int cout
   if (!tc_supported(cin, cout)) return cudaErrorNotSupported;
   if (const cudaError_t pe = tc_prepare()) return pe;
   const TcCfg f = tc_cfg(cin, cout, bf16);
+  const ConvTune t = conv_tune_for(ConvKey{mode, bf16, cin, cout, H, W});
   CUtensorMap m;
   ConvTcParams p;
-  cudaError_t e = conv_params(bf16, in, cin, cout, H, W, w_hi, w_lo, b, mask, out, skip, err, &m,
-                              &p);
+  cudaError_t e = conv_params(bf16, in, cin, cout, H, W, w_hi, w_lo, b, mask, out, skip, err,
+                              t.rows, &m, &p);
   if (e != cudaSuccess) return e;
-  const long ntiles = (long)p.tiles_x * ((H + kRowsM - 1) / kRowsM) * (cout / f.NT);
-  e = conv_tc_dispatch(mode, bf16, m, p, nullptr, 0, ntiles,
-                       conv_tune_for(ConvKey{mode, bf16, cin, cout, H, W}), st);
+  const long ntiles = (long)p.tiles_x * ((H + t.rows - 1) / t.rows) * (cout / f.NT);
+  e = conv_tc_dispatch(mode, bf16, m, p, nullptr, 0, ntiles, t, st);
   count_launch();
   return e;
 }
@@ -1325,7 +1341,8 @@ cudaError_t conv_group_table(int mode, int bf16, int cin, int cout, const ConvGr
   long tiles = 0;
   for (int k = 0; k < n; ++k) {
     memset(&t[k], 0, sizeof(ConvJob));
-    cudaError_t r = make_map(&t[k].map, e[k].in, bf16, cin, e[k].H, e[k].W, kHaloX, kHaloY, KC / GE);
+    cudaError_t r = make_map(&t[k].map, e[k].in, bf16, cin, e[k].H, e[k].W, kHaloX, kRowsM + 2,
+                             KC / GE);
     if (r != cudaSuccess) return r;
     t[k].w_hi = (const uint8_t*)e[k].w_hi;
     t[k].w_lo = (const uint8_t*)e[k].w_lo;
