@@ -147,10 +147,14 @@ def peaks():
                 "sm_max_mhz": 2070.0}, "fallback"
 
 
-def kernel_source_hash():
+# the sources of the conv kernel whose DRAM traffic profiles/traffic.json records
+CONV_SOURCES = ("conv_tc.cu", "tc_common.cuh", "tc_ptx.cuh", "tc_layout.cuh", "cg_util.cuh")
+
+
+def kernel_source_hash(files=CONV_SOURCES):
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2108_10209_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in files:
         h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 

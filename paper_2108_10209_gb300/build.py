@@ -17,8 +17,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libn2f.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
-SOURCES = ["kernels_basic.cu", "kernels_simt.cu", "kernels_tc.cu", "trainer.cpp", "api.cpp",
-           "noalloc.cu"]
+SOURCES = ["kernels_basic.cu", "kernels_simt.cu", "conv_tc.cu", "wgrad_tc.cu", "tc_probe.cu",
+           "trainer.cpp", "api.cpp", "noalloc.cu"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2,-pthread",
          "-I" + os.path.join(ROOT, "include")]
 

@@ -115,6 +115,8 @@ cudaError_t launch_wgrad_simt(int bf16, const void* dout, const void* in, int ci
 
 // Tensor-core (tcgen05) kernels; return cudaErrorNotSupported when a shape is not covered.
 cudaError_t tc_prepare();  // once per process, before any launch or capture
+cudaError_t conv_tc_prepare();   // the forward / dgrad kernels' part of tc_prepare
+cudaError_t wgrad_tc_prepare();  // the weight-gradient kernels' part
 bool tc_supported(int cin, int cout);
 bool tc_wgrad_supported(int cin, int cout, int bf16);
 // mode 0 forward (bias + ReLU), 1 dgrad (ReLU mask); w_hi/w_lo: packed operand copies

@@ -1,0 +1,745 @@
+// tcgen05 / TMEM weight-gradient kernels for the 3x3 layers (sm_103a) and their fixed-order
+// reductions.
+//
+// D[o][c] = sum_px delta[px][o] x[px + tap][c] per tap: M = 128 output channels, N = C_in (per
+// tap, or several taps side by side), K = pixels; the operands are read MN-major from the
+// channel-grouped maps, the pixel sum is split over pixel chunks and the partial sums are
+// reduced in a fixed order. The bias gradient comes out of the same GEMM (a B operand extended
+// by 16 columns of ones).
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <type_traits>
+
+#include "cg_util.cuh"
+#include "n2f_internal.h"
+#include "tc_common.cuh"
+#include "tc_layout.cuh"
+#include "tc_ptx.cuh"
+#include "trainer.h"
+
+namespace n2f {
+
+using namespace tc;
+
+namespace {
+
+// ---- bf16 weight gradient, several taps per CTA -----------------------------------------
+// A CTA covers a group of taps that share image rows, for a slice of cn input channels: the x
+// halo tile (R rows x (KP + 2 pu) pixels x cn channels, MN-major) is loaded once per pixel
+// chunk and each tap's B operand is the same tile at a descriptor offset of (row, dx) pixels
+// (16 bytes per pixel). The group's accumulators sit side by side in TMEM (taps x cn <= 512
+// columns). Every group has the same number of taps, so all CTAs carry equal work.
+struct TapGroups {
+  int n;                                  // groups
+  int first[9], count[9], row0[9], c0[9];  // taps first..first+count-1, rows row0..row0+R-1,
+                                          // input channels c0..c0+cn-1
+  int R;                                  // halo rows (same for every group)
+  int cn;                                 // input channels per group
+};
+
+TapGroups tap_groups(int cin) {
+  TapGroups g{};
+  if (cin <= 32) {  // 9 x 32 = 288 columns: all taps, 3-row halo
+    g.n = 1; g.first[0] = 0; g.count[0] = 9; g.row0[0] = 0; g.c0[0] = 0; g.R = 3; g.cn = cin;
+  } else if (cin <= 128) {  // one row of 3 taps per group
+    g.n = 3; g.R = 1; g.cn = cin;
+    for (int r = 0; r < 3; ++r) { g.first[r] = 3 * r; g.count[r] = 3; g.row0[r] = r; g.c0[r] = 0; }
+  } else {  // C_in = 256: one row of 3 taps for one half of the input channels
+    g.n = 6; g.R = 1; g.cn = 128;
+    for (int r = 0; r < 3; ++r)
+      for (int h = 0; h < 2; ++h) {
+        const int k = 2 * r + h;
+        g.first[k] = 3 * r; g.count[k] = 3; g.row0[k] = r; g.c0[k] = 128 * h;
+      }
+  }
+  return g;
+}
+
+// The bias gradient db[o] = sum_px delta[px][o] comes out of the same GEMM: in the CTAs of tap
+// group 0 the B operand of the group's last tap carries two more 8-channel groups, constant bf16
+// ones (zeros in the float32 form's second and third parts), so that tap's MMAs (N = C + 16)
+// also accumulate sum_px delta into 16 more TMEM columns, at no extra instruction.
+__device__ __forceinline__ void fill_ext(uint8_t* ext, uint32_t bytes, uint32_t value) {
+  for (uint32_t i = threadIdx.x; i < bytes / 4; i += blockDim.x)
+    reinterpret_cast<uint32_t*>(ext)[i] = value;
+}
+constexpr uint32_t kBf16PairOne = 0x3F803F80u;  // two bf16 1.0
+
+struct WgBf16Params {
+  float* part;  // [S][9][C_in][C_out]
+  int cin, cout, H, W, chunks_x, total_chunks, per_split;
+  int stages;  // pipeline stages
+  int pu;      // pixels per TMA unit of both maps
+  float* bpart;  // [S][C_out] bias-gradient partials, written by the tap group 0 CTAs
+  TapGroups tg;
+  const int* skip;
+  int* err;
+};
+
+constexpr int kWbKP = 64;       // pixels per stage
+constexpr int kWbMaxStages = 6;
+constexpr uint32_t kWbA = 128u * kWbKP * 2;  // delta tile, 128 channels (zero-filled past C_out)
+
+// x halo pitch: the chunk's KP pixels plus one TMA unit of pu pixels on each side
+__host__ __device__ inline int wb_pitch(int pu) { return kWbKP + 2 * pu; }
+__host__ __device__ inline uint32_t wb_b_bytes(int cin, int R, int pu) {
+  return (uint32_t)(cin / 8) * R * wb_pitch(pu) * 16;
+}
+// the two extra 8-channel groups (ones) after the x tile
+__host__ __device__ inline uint32_t wb_ext_bytes(int R, int pu) { return 2u * R * wb_pitch(pu) * 16; }
+__host__ __device__ inline uint32_t wb_stage(int cin, int R, int pu) {
+  return align_up(kWbA, 1024) + align_up(wb_b_bytes(cin, R, pu) + wb_ext_bytes(R, pu), 1024);
+}
+// tap-expanded stage (small C_in): after the raw x tile, [taps x C/8 + 2][KP px][16 B] with the
+// two bias groups (ones) last, so one MMA spans every tap of the group
+__host__ __device__ inline uint32_t wb_exp_off(int cin, int R, int pu) {
+  return align_up(kWbA, 1024) + align_up(wb_b_bytes(cin, R, pu), 1024);
+}
+__host__ __device__ inline uint32_t wb_stage_exp(int cin, int R, int pu, int taps) {
+  return wb_exp_off(cin, R, pu) + align_up(((uint32_t)taps * cin / 8 + 2) * kWbKP * 16, 1024);
+}
+
+// EXP = 1 (small C_in): warps 2-5 first copy each stage's x tile into the tap-expanded layout
+// (pure 16-byte copies), then serve as the epilogue.
+template <int EXP>
+__global__ void __launch_bounds__(192, 1) k_wgrad_tc_bf16(const __grid_constant__ CUtensorMap tmD,
+                                                         const __grid_constant__ CUtensorMap tmX,
+                                                         WgBf16Params p) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ uint64_t full[kWbMaxStages], empty[kWbMaxStages], split[kWbMaxStages], accf;
+  __shared__ uint32_t tslot;
+  __shared__ int abort_flag;
+  if (p.skip && *p.skip) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int o0 = blockIdx.x * 128, grp = blockIdx.y, s_idx = blockIdx.z;
+  const int t0 = p.tg.first[grp], nt = p.tg.count[grp], r0 = p.tg.row0[grp], R = p.tg.R;
+  const int cn = p.tg.cn, c0g = p.tg.c0[grp];
+  const int ns = p.stages;
+  const int cbeg = s_idx * p.per_split;
+  const int cend = min(p.total_chunks, cbeg + p.per_split);
+  const int nk = cend > cbeg ? cend - cbeg : 0;
+  const int pu = p.pu, HX = wb_pitch(pu);
+  const uint32_t BB = wb_b_bytes(cn, R, pu);
+  const uint32_t SB = EXP ? wb_stage_exp(cn, R, pu, nt) : wb_stage(cn, R, pu);
+  const uint32_t e_off = wb_exp_off(cn, R, pu);
+  const uint32_t b_off = align_up(kWbA, 1024);
+  const bool bias = grp == 0;
+  const uint32_t ncols = tmem_cols(nt * cn + (bias ? 16 : 0));
+  volatile int* abort = &abort_flag;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < ns; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+      mbar_init(&split[s], 4);
+    }
+    mbar_init(&accf, 1);
+    abort_flag = 0;
+    mbar_fence_init();
+  }
+  if (warp == 1) tmem_alloc(&tslot, ncols);
+  if (bias) {
+    for (int s = 0; s < ns; ++s)
+      if (EXP)
+        fill_ext(smem + s * SB + e_off + (uint32_t)nt * cn / 8 * kWbKP * 16, 2u * kWbKP * 16,
+                 kBf16PairOne);
+      else
+        fill_ext(smem + s * SB + b_off + BB, wb_ext_bytes(R, pu), kBf16PairOne);
+    fence_proxy_async();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = tslot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int issued = 0;
+      for (int i = 0; i < nk; ++i) {
+        const int s = i % ns;
+        if (i >= ns && !mbar_wait(&empty[s], ((i / ns) - 1) & 1, abort, p.err))
+          break;
+        const int ch = cbeg + i;
+        const int y = ch / p.chunks_x, x0 = (ch % p.chunks_x) * kWbKP;
+        uint8_t* st = smem + s * SB;
+        mbar_expect_tx(&full[s], kWbA + BB);
+        tma_load_4d(st, &tmD, &full[s], 0, x0 / pu, y, o0 / 8);
+        tma_load_4d(st + b_off, &tmX, &full[s], 0, x0 / pu - 1, y + r0 - 1, c0g / 8);
+        issued = i + 1;
+      }
+      if (*abort)
+        for (int i = issued > ns ? issued - ns : 0; i < issued; ++i)
+          mbar_drain(&full[i % ns], (i / ns) & 1);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t id = idesc(1, 128, cn, 1, 1), idx = idesc(1, 128, cn + 16, 1, 1);
+      const uint32_t a_sbo = kWbKP * 16;                    // next 8-channel group of delta
+      const uint32_t b_sbo = (uint32_t)R * HX * 16;  // next 8-channel group of x
+      for (int i = 0; i < nk; ++i) {
+        const int s = i % ns;
+        if (!mbar_wait(EXP ? &split[s] : &full[s], (i / ns) & 1, abort, p.err)) break;
+        tc_fence_after();
+        const uint32_t sa = smem_u32(smem + s * SB), sb = sa + b_off;
+        if constexpr (EXP) {
+          // taps side by side along N, in chunks of at most 256 columns (multiples of 16)
+          const int ntot = nt * cn, nch = (ntot + 255) / 256;
+          const int csz = (ntot / nch + 15) / 16 * 16;
+          for (int c0 = 0; c0 < ntot; c0 += csz) {
+            const int n = min(csz, ntot - c0) + ((bias && c0 + csz >= ntot) ? 16 : 0);
+            const uint32_t idc = idesc(1, 128, n, 1, 1);
+            const uint32_t eb = sa + e_off + (uint32_t)(c0 / 8) * kWbKP * 16u;
+#pragma unroll
+            for (int k = 0; k < kWbKP / 16; ++k)
+              mma_f16(tbase + (uint32_t)c0, sdesc(sa + (uint32_t)k * 256u, 128, a_sbo),
+                      sdesc(eb + (uint32_t)k * 256u, 128, kWbKP * 16), idc,
+                      (i > 0 || k > 0) ? 1u : 0u);
+          }
+        } else {
+          for (int j = 0; j < nt; ++j) {
+            const int tap = t0 + j;
+            // pixel p of the chunk, tap column dx, sits at halo column p + dx - 1 + pu
+            const uint32_t boff = (uint32_t)(((tap / 3) - r0) * HX + (tap % 3) + pu - 1) * 16u;
+#pragma unroll
+            for (int k = 0; k < kWbKP / 16; ++k) {
+              const uint32_t ko = (uint32_t)k * 16u * 16u;
+              mma_f16(tbase + (uint32_t)(j * cn), sdesc(sa + ko, 128, a_sbo),
+                      sdesc(sb + boff + ko, 128, b_sbo), (bias && j == nt - 1) ? idx : id,
+                      (i > 0 || k > 0) ? 1u : 0u);
+            }
+          }
+        }
+        mma_commit(&empty[s]);
+      }
+      mma_commit(&accf);
+    }
+  } else {
+    if constexpr (EXP) {
+      // group gq = j * g8n + g8 holds tap j's view of channel group g8: pixel px of the chunk
+      // at raw row (tap / 3 - r0), raw column pu - 1 + px + tap % 3
+      const int g8n = cn / 8, et = threadIdx.x - 64;
+      for (int i = 0; i < nk; ++i) {
+        const int s = i % ns;
+        if (!mbar_wait(&full[s], (i / ns) & 1, abort, p.err)) break;
+        const uint4* raw = reinterpret_cast<const uint4*>(smem + s * SB + b_off);
+        uint4* ex = reinterpret_cast<uint4*>(smem + s * SB + e_off);
+        for (int u = et; u < nt * g8n * kWbKP; u += 128) {
+          const int gq = u / kWbKP, px = u % kWbKP;
+          const int j = gq / g8n, g8 = gq - j * g8n, tap = t0 + j;
+          ex[u] = raw[(g8 * R + (tap / 3 - r0)) * HX + pu - 1 + px + tap % 3];
+        }
+        fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&split[s]);
+      }
+    }
+    if (!mbar_wait(&accf, 0, abort, p.err)) mbar_drain(&accf, 0);
+    tc_fence_after();
+    const int wq = warp & 3;
+    const int o = o0 + wq * 32 + lane;
+    const bool live = o < p.cout && !*abort;
+    for (int j = 0; j < nt; ++j) {
+      const int tap = t0 + j;
+      // part[s][tap][c][o]: the warp's 32 lanes are 32 consecutive o, one 128-byte row per c
+      float* dst = p.part + ((size_t)s_idx * 9 + tap) * p.cin * p.cout + (size_t)c0g * p.cout + o;
+      for (int c0 = 0; c0 < cn; c0 += 16) {
+        uint32_t r[16];
+        tmem_ld16(tbase + ((uint32_t)(wq * 32) << 16) + (uint32_t)(j * cn + c0), r);
+        tmem_ld_wait();
+        if (!live) continue;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) dst[(size_t)(c0 + q) * p.cout] = nk ? __uint_as_float(r[q]) : 0.f;
+      }
+    }
+    if (bias) {
+      uint32_t r[16];
+      tmem_ld16(tbase + ((uint32_t)(wq * 32) << 16) + (uint32_t)(nt * cn), r);
+      tmem_ld_wait();
+      if (live) p.bpart[(size_t)s_idx * p.cout + o] = nk ? __uint_as_float(r[0]) : 0.f;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tbase, ncols);
+  }
+}
+
+// ---- float32 weight gradient as three bf16 parts per operand --------------------------------
+// Each fp32 value x is split into x = b0 + b1 + b2 (bf16, each the rounded remainder of the
+// previous) and D = sum of the six products b_i c_j with i + j <= 2; the three dropped products
+// are below 2^-25 of the true one. bf16 operands can be read MN-major, so the tap-grouped halo
+// scheme of the bf16 kernel applies unchanged: TMA brings the fp32 tiles, eight split warps
+// write the three bf16 images of each, one MMA warp issues six MMAs per tap and K step.
+constexpr int kW3KP = 16;  // pixels per stage (one bf16 K step)
+constexpr int kW3MaxStages = 4;
+constexpr int kW3SplitWarps = 8;
+constexpr int kW3Threads = 64 + 32 * kW3SplitWarps;
+
+struct W3Layout {
+  uint32_t rawA, rawB, a[3], b[3], stage;
+};
+
+// raw x tile pitch: the 16 chunk pixels plus one TMA unit of pu pixels on each side
+__host__ __device__ inline int w3_raw_pitch(int pu) { return kW3KP + 2 * pu; }
+
+// exp: the x parts are written tap-expanded, [taps x C/8][16 px][16 B] + 2 bias groups, so one
+// MMA covers several taps (N = taps x C): used when C is small (N = C alone would leave the
+// tensor pipe idle between MMAs, each of which costs at least ~48 cycles)
+__host__ __device__ inline W3Layout w3_layout(int cin, int R, int pu, bool exp = false,
+                                              int taps = 0) {
+  W3Layout L;
+  const uint32_t ra = 128u * kW3KP * 4;                         // [32 g4][16 px][16 B]
+  const uint32_t rb = (uint32_t)cin * R * w3_raw_pitch(pu) * 4;  // [C/4][R][16 + 2 pu][16 B]
+  const uint32_t pa = 128u * kW3KP * 2;                         // [16 g8][16 px][16 B]
+  const uint32_t pb = exp ? ((uint32_t)taps * cin / 8 + 2) * kW3KP * 16
+                          : (uint32_t)cin * R * (kW3KP + 2) * 2  // [C/8][R][18 px][16 B]
+                                + 2u * R * (kW3KP + 2) * 16;     // + 2 bias groups
+  uint32_t o = 0;
+  L.rawA = o; o += align_up(ra, 1024);
+  L.rawB = o; o += align_up(rb, 1024);
+  for (int k = 0; k < 3; ++k) { L.a[k] = o; o += align_up(pa, 1024); }
+  for (int k = 0; k < 3; ++k) { L.b[k] = o; o += align_up(pb, 1024); }
+  L.stage = o;
+  return L;
+}
+
+// Two fp32 values -> their three bf16 parts, packed in pairs (value a in the low half). The
+// remainders v - b0 and (v - b0) - b1 are exact in fp32.
+__device__ __forceinline__ void split3_pair(float a, float b, uint32_t& w0, uint32_t& w1,
+                                            uint32_t& w2) {
+  const __nv_bfloat162 p0 = __floats2bfloat162_rn(a, b);
+  const float2 f0 = __bfloat1622float2(p0);
+  const float ra = a - f0.x, rb = b - f0.y;
+  const __nv_bfloat162 p1 = __floats2bfloat162_rn(ra, rb);
+  const float2 f1 = __bfloat1622float2(p1);
+  const __nv_bfloat162 p2 = __floats2bfloat162_rn(ra - f1.x, rb - f1.y);
+  w0 = *reinterpret_cast<const uint32_t*>(&p0);
+  w1 = *reinterpret_cast<const uint32_t*>(&p1);
+  w2 = *reinterpret_cast<const uint32_t*>(&p2);
+}
+
+// One 16-byte group of 8 channels: the fp32 groups lo (channels 0-3) and hi (4-7) -> the three
+// bf16 images at element index u.
+__device__ __forceinline__ void split3_group(const float4 lo, const float4 hi, uint4* b0, uint4* b1,
+                                             uint4* b2, int u) {
+  uint4 o0, o1, o2;
+  split3_pair(lo.x, lo.y, o0.x, o1.x, o2.x);
+  split3_pair(lo.z, lo.w, o0.y, o1.y, o2.y);
+  split3_pair(hi.x, hi.y, o0.z, o1.z, o2.z);
+  split3_pair(hi.z, hi.w, o0.w, o1.w, o2.w);
+  b0[u] = o0;
+  b1[u] = o1;
+  b2[u] = o2;
+}
+
+// Splits one stage. Delta tile: raw [32 g4][16 px], parts [16 g8][16 px]. x tile: raw
+// [C/4][R][16 + 2 pu px], parts [C/8][R][18 px] (raw column pu - 1 + i -> part column i). Each
+// quarter-warp takes 8 consecutive pixels of one row, so its eight 16-byte reads fall in
+// distinct bank groups; the 2 halo pixels of each row follow in a short second pass.
+template <int R, int EXP>
+__device__ __forceinline__ void split3_stage(const uint8_t* st, uint8_t* stw, const W3Layout& L,
+                                             int g8n, int pu, int et, int nt, int t0, int r0) {
+  constexpr int kThr = 32 * kW3SplitWarps;
+  constexpr int PP = kW3KP + 2;  // part pitch
+  const int PR = w3_raw_pitch(pu);
+  {
+    const float4* raw = reinterpret_cast<const float4*>(st + L.rawA);
+    for (int u = et; u < 16 * kW3KP; u += kThr) {
+      const int g8 = u / kW3KP, px = u % kW3KP;
+      split3_group(raw[(2 * g8) * kW3KP + px], raw[(2 * g8 + 1) * kW3KP + px],
+                   reinterpret_cast<uint4*>(stw + L.a[0]), reinterpret_cast<uint4*>(stw + L.a[1]),
+                   reinterpret_cast<uint4*>(stw + L.a[2]), u);
+    }
+  }
+  const float4* raw = reinterpret_cast<const float4*>(st + L.rawB);
+  uint4* b0 = reinterpret_cast<uint4*>(stw + L.b[0]);
+  uint4* b1 = reinterpret_cast<uint4*>(stw + L.b[1]);
+  uint4* b2 = reinterpret_cast<uint4*>(stw + L.b[2]);
+  if constexpr (EXP) {
+    // group gq = j * g8n + g8 holds tap j's view of channel group g8: pixel px of the chunk at
+    // raw row (tap / 3 - r0), raw column pu - 1 + px + tap % 3
+    for (int u = et; u < nt * g8n * kW3KP; u += kThr) {
+      const int gq = u / kW3KP, px = u % kW3KP;
+      const int j = gq / g8n, g8 = gq - j * g8n, tap = t0 + j;
+      const int r = tap / 3 - r0, col = pu - 1 + px + tap % 3;
+      split3_group(raw[((2 * g8) * R + r) * PR + col], raw[((2 * g8 + 1) * R + r) * PR + col], b0,
+                   b1, b2, u);
+    }
+    return;
+  }
+  const int nmain = g8n * R * kW3KP;
+  for (int u = et; u < nmain; u += kThr) {
+    const int q = u / kW3KP, i = 1 + u % kW3KP;  // q = g8 * R + r, part column i
+    const int g8 = q / R, r = q - g8 * R, px = pu - 1 + i;
+    split3_group(raw[((2 * g8) * R + r) * PR + px], raw[((2 * g8 + 1) * R + r) * PR + px], b0, b1,
+                 b2, q * PP + i);
+  }
+  for (int u = et; u < g8n * R * 2; u += kThr) {
+    const int q = u >> 1, i = (u & 1) ? PP - 1 : 0;
+    const int g8 = q / R, r = q - g8 * R, px = pu - 1 + i;
+    split3_group(raw[((2 * g8) * R + r) * PR + px], raw[((2 * g8 + 1) * R + r) * PR + px], b0, b1,
+                 b2, q * PP + i);
+  }
+}
+
+template <int R, int EXP>
+__global__ void __launch_bounds__(kW3Threads, 2) k_wgrad_tc_f32(const __grid_constant__ CUtensorMap tmD,
+                                                               const __grid_constant__ CUtensorMap tmX,
+                                                               WgBf16Params p) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ uint64_t full[kW3MaxStages], empty[kW3MaxStages], split[kW3MaxStages], accf;
+  __shared__ uint32_t tslot;
+  __shared__ int abort_flag;
+  if (p.skip && *p.skip) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int o0 = blockIdx.x * 128, grp = blockIdx.y, s_idx = blockIdx.z;
+  const int t0 = p.tg.first[grp], nt = p.tg.count[grp], r0 = p.tg.row0[grp];
+  const int cn = p.tg.cn, c0g = p.tg.c0[grp];
+  const int ns = p.stages;
+  const int cbeg = s_idx * p.per_split;
+  const int cend = min(p.total_chunks, cbeg + p.per_split);
+  const int nk = cend > cbeg ? cend - cbeg : 0;
+  const int pu = p.pu;
+  const W3Layout L = w3_layout(cn, R, pu, EXP, nt);
+  const uint32_t RB = (uint32_t)cn * R * w3_raw_pitch(pu) * 4;
+  const bool bias = grp == 0;
+  const uint32_t ncols = tmem_cols(nt * cn + (bias ? 16 : 0));
+  volatile int* abort = &abort_flag;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < ns; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+      mbar_init(&split[s], kW3SplitWarps);
+    }
+    mbar_init(&accf, 1);
+    abort_flag = 0;
+    mbar_fence_init();
+  }
+  if (warp == 1) tmem_alloc(&tslot, ncols);
+  if (bias) {  // part 0: ones, parts 1 and 2: zeros, so the bias columns sum a0 + a1 + a2
+    const uint32_t eo = EXP ? (uint32_t)nt * cn / 8 * kW3KP * 16 : (uint32_t)cn * R * (kW3KP + 2) * 2;
+    const uint32_t eb = EXP ? 2u * kW3KP * 16 : 2u * R * (kW3KP + 2) * 16;
+    for (int s = 0; s < ns; ++s)
+      for (int q = 0; q < 3; ++q)
+        fill_ext(smem + s * L.stage + L.b[q] + eo, eb, q == 0 ? kBf16PairOne : 0u);
+    fence_proxy_async();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = tslot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int issued = 0;
+      for (int i = 0; i < nk; ++i) {
+        const int s = i % ns;
+        if (i >= ns && !mbar_wait(&empty[s], ((i / ns) - 1) & 1, abort, p.err)) break;
+        const int ch = cbeg + i;
+        const int y = ch / p.chunks_x, x0 = (ch % p.chunks_x) * kW3KP;
+        uint8_t* st = smem + s * L.stage;
+        mbar_expect_tx(&full[s], 128u * kW3KP * 4 + RB);
+        tma_load_4d(st + L.rawA, &tmD, &full[s], 0, x0 / pu, y, o0 / 4);
+        tma_load_4d(st + L.rawB, &tmX, &full[s], 0, x0 / pu - 1, y + r0 - 1, c0g / 4);
+        issued = i + 1;
+      }
+      if (*abort)
+        for (int i = issued > ns ? issued - ns : 0; i < issued; ++i)
+          mbar_drain(&full[i % ns], (i / ns) & 1);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idn = idesc(1, 128, cn, 1, 1), idx = idesc(1, 128, cn + 16, 1, 1);
+      const uint32_t a_sbo = kW3KP * 16;                     // next 8-channel group of delta
+      const uint32_t b_sbo = (uint32_t)R * (kW3KP + 2) * 16;  // next 8-channel group of x
+      for (int i = 0; i < nk; ++i) {
+        const int s = i % ns;
+        if (!mbar_wait(&split[s], (i / ns) & 1, abort, p.err)) break;
+        tc_fence_after();
+        const uint32_t st = smem_u32(smem + s * L.stage);
+        uint64_t da[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) da[k] = sdesc(st + L.a[k], 128, a_sbo);
+        if constexpr (EXP) {
+          // the taps side by side along N, in chunks of at most 256 columns (multiples of 16)
+          const int ntot = nt * cn, nch = (ntot + 255) / 256;
+          const int csz = (ntot / nch + 15) / 16 * 16;
+          for (int c0 = 0; c0 < ntot; c0 += csz) {
+            const int n = min(csz, ntot - c0) + ((bias && c0 + csz >= ntot) ? 16 : 0);
+            const uint32_t id = idesc(1, 128, n, 1, 1);
+            uint64_t db[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) db[q] = sdesc(st + L.b[q] + (uint32_t)(c0 / 8) * kW3KP * 16u, 128, kW3KP * 16);
+            const uint32_t d = tbase + (uint32_t)c0;
+            mma_f16(d, da[0], db[0], id, i > 0 ? 1u : 0u);
+            mma_f16(d, da[0], db[1], id, 1u);
+            mma_f16(d, da[1], db[0], id, 1u);
+            mma_f16(d, da[0], db[2], id, 1u);
+            mma_f16(d, da[1], db[1], id, 1u);
+            mma_f16(d, da[2], db[0], id, 1u);
+          }
+        } else {
+        for (int j = 0; j < nt; ++j) {
+            const int tap = t0 + j;
+            const uint32_t boff = (uint32_t)(((tap / 3) - r0) * (kW3KP + 2) + (tap % 3)) * 16u;
+            uint64_t db[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) db[k] = sdesc(st + L.b[k] + boff, 128, b_sbo);
+            const uint32_t d = tbase + (uint32_t)(j * cn);
+            const uint32_t id = (bias && j == nt - 1) ? idx : idn;
+            mma_f16(d, da[0], db[0], id, i > 0 ? 1u : 0u);
+            mma_f16(d, da[0], db[1], id, 1u);
+            mma_f16(d, da[1], db[0], id, 1u);
+            mma_f16(d, da[0], db[2], id, 1u);
+            mma_f16(d, da[1], db[1], id, 1u);
+            mma_f16(d, da[2], db[0], id, 1u);
+          }
+        }
+        mma_commit(&empty[s]);
+      }
+      mma_commit(&accf);
+    }
+  } else {
+    const int et = threadIdx.x - 64;
+    for (int i = 0; i < nk; ++i) {
+      const int s = i % ns;
+      if (!mbar_wait(&full[s], (i / ns) & 1, abort, p.err)) break;
+      uint8_t* st = smem + s * L.stage;
+      split3_stage<R, EXP>(st, st, L, cn / 8, pu, et, nt, t0, r0);
+      fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&split[s]);
+    }
+    if (!mbar_wait(&accf, 0, abort, p.err)) mbar_drain(&accf, 0);
+    tc_fence_after();
+    // warps 2..9: TMEM lane quarter warp % 4, column half (warp - 2) / 4 (16-column blocks
+    // alternate between the two halves)
+    const int wq = warp & 3, half = (warp - 2) >> 2;
+    const int o = o0 + wq * 32 + lane;
+    const bool live = o < p.cout && !*abort;
+    for (int j = 0; j < nt; ++j) {
+      const int tap = t0 + j;
+      // part[s][tap][c][o]: the warp's 32 lanes are 32 consecutive o, one 128-byte row per c
+      float* dst = p.part + ((size_t)s_idx * 9 + tap) * p.cin * p.cout + (size_t)c0g * p.cout + o;
+      for (int c0 = 16 * half; c0 < cn; c0 += 32) {
+        uint32_t r[16];
+        tmem_ld16(tbase + ((uint32_t)(wq * 32) << 16) + (uint32_t)(j * cn + c0), r);
+        tmem_ld_wait();
+        if (!live) continue;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) dst[(size_t)(c0 + q) * p.cout] = nk ? __uint_as_float(r[q]) : 0.f;
+      }
+    }
+    if (bias && half == 0) {
+      uint32_t r[16];
+      tmem_ld16(tbase + ((uint32_t)(wq * 32) << 16) + (uint32_t)(nt * cn), r);
+      tmem_ld_wait();
+      if (live) p.bpart[(size_t)s_idx * p.cout + o] = nk ? __uint_as_float(r[0]) : 0.f;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tbase, ncols);
+  }
+}
+
+// gw[(o*C_in + c)*9 + tap] = sum over s of part[s][tap][c][o]. A block owns 32 consecutive o
+// (the lanes, so every read is one 128-byte row) of one input channel c and all 9 taps; warp w
+// sums the splits s = w, w + 8, ... in order and the eight warp sums are added in warp order,
+// so the result is fixed for a given number of splits.
+constexpr int kRwO = 32;
+__global__ void __launch_bounds__(256) k_reduce_wgrad_tc(const float* __restrict__ part, int S,
+                                                         int cin, int cout,
+                                                         float* __restrict__ gw, const int* skip) {
+  if (skip && *skip) return;
+  __shared__ float sh[8][9][kRwO + 1];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int otiles = (cout + kRwO - 1) / kRwO;
+  const int o0 = (blockIdx.x % otiles) * kRwO, c = blockIdx.x / otiles;
+  const int o = o0 + lane;
+  const size_t per = (size_t)9 * cout * cin, tstride = (size_t)cin * cout;
+  float acc[9];
+#pragma unroll
+  for (int t = 0; t < 9; ++t) acc[t] = 0.f;
+  if (o < cout) {
+    // splits w, w + 8, ... in order, four loads of each tap in flight (a, b, c, d hold the
+    // splits w + 32 i, w + 32 i + 8, ... and are added in that order)
+    const float* src = part + (size_t)c * cout + o;
+    int k = w;
+    for (; k + 24 < S; k += 32)
+#pragma unroll
+      for (int t = 0; t < 9; ++t) {
+        const float* q = src + (size_t)t * tstride;
+        const float a = q[k * per], b = q[(k + 8) * per], cc = q[(k + 16) * per],
+                    d = q[(k + 24) * per];
+        acc[t] = (((acc[t] + a) + b) + cc) + d;
+      }
+    for (; k < S; k += 8)
+#pragma unroll
+      for (int t = 0; t < 9; ++t) acc[t] += src[k * per + t * tstride];
+  }
+#pragma unroll
+  for (int t = 0; t < 9; ++t) sh[w][t][lane] = acc[t];
+  __syncthreads();
+  for (int i = threadIdx.x; i < kRwO * 9; i += 256) {
+    const int oo = i / 9, t = i % 9;
+    if (o0 + oo >= cout) continue;
+    float v = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v += sh[k][t][oo];
+    gw[((size_t)(o0 + oo) * cin + c) * 9 + t] = v;
+  }
+}
+
+}  // namespace
+
+// out[c] = sum_{r < R} part[r * C + c]: one block per column, each thread sums a fixed strided
+// subset of rows in order, then a fixed tree: deterministic for a given R.
+__global__ void k_reduce_cols(const float* __restrict__ part, int R, int C, float* __restrict__ out,
+                              const int* skip) {
+  if (skip && *skip) return;
+  __shared__ float sh[256];
+  const int c = blockIdx.x;
+  float s = 0.f;
+  for (int r = threadIdx.x; r < R; r += blockDim.x) s += part[(size_t)r * C + c];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[c] = sh[0];
+}
+
+cudaError_t launch_reduce_cols(const float* part, int R, int C, float* out, const int* skip,
+                               cudaStream_t st) {
+  k_reduce_cols<<<C, 256, 0, st>>>(part, R, C, out, skip);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// Sets the dynamic shared-memory limit of every weight-gradient kernel (the per-block opt-in total
+// minus its static shared memory), so that later launches (possibly inside a stream capture)
+// need no attribute calls.
+cudaError_t wgrad_tc_prepare() {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  auto set = [&](const void* f) {
+    if (e != cudaSuccess) return;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, f);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               optin - (int)fa.sharedSizeBytes);
+  };
+    set((const void*)k_wgrad_tc_bf16<0>);
+    set((const void*)k_wgrad_tc_bf16<1>);
+    set((const void*)k_wgrad_tc_f32<1, 0>);
+    set((const void*)k_wgrad_tc_f32<1, 1>);
+    set((const void*)k_wgrad_tc_f32<3, 1>);
+  return e;
+}
+
+bool tc_wgrad_supported(int cin, int cout, int bf16) {
+  (void)bf16;
+  return tc_supported(cin, cout);
+}
+
+// bf16 = 1: bf16 maps, k_wgrad_tc_bf16; bf16 = 0: float32 maps, k_wgrad_tc_f32 (three bf16 parts)
+static cudaError_t launch_wgrad_grouped(int bf16, const void* dout, const void* in, int cin,
+                                        int cout, int H, int W, float* part, size_t part_cap,
+                                        float* gw, float* gb, const int* skip, int* err,
+                                        cudaStream_t st) {
+  const TapGroups tg = tap_groups(cin);
+  const int KP = bf16 ? kWbKP : kW3KP, GE = bf16 ? 8 : 4;
+  // pixels per TMA unit: 128-byte box rows for bf16 (the halo grows by 14 pixels of 66),
+  // 64-byte rows for float32 (the raw tile of 16 pixels would grow too much with 8)
+  const int pu_max = bf16 ? 8 : 4;
+  int pu = 1;
+  while (pu < pu_max && W % (2 * pu) == 0) pu *= 2;
+  CUtensorMap md, mx;
+  cudaError_t e = make_map(&md, dout, bf16, cout, H, W, KP / pu, 1, 128 / GE, pu);
+  if (e == cudaSuccess) e = make_map(&mx, in, bf16, cin, H, W, KP / pu + 2, tg.R, tg.cn / GE, pu);
+  if (e != cudaSuccess) return e;
+  const int otiles = (cout + 127) / 128;
+  WgBf16Params p;
+  p.cin = cin;
+  p.cout = cout;
+  p.H = H;
+  p.W = W;
+  p.chunks_x = (W + KP - 1) / KP;
+  p.total_chunks = p.chunks_x * H;
+  p.tg = tg;
+  p.pu = pu;
+  const size_t per_split_elems = (size_t)9 * cout * cin;
+  int maxcols = 0;  // group 0 also holds the 16 bias columns
+  for (int g = 0; g < tg.n; ++g) {
+    const int cols = tg.count[g] * tg.cn + (g == 0 ? 16 : 0);
+    maxcols = cols > maxcols ? cols : maxcols;
+  }
+  const int max_res = 512 / (int)tmem_cols(maxcols);  // CTAs per SM that TMEM allows
+  // as many stages as fit beside the CTAs that TMEM allows on one SM
+  // tap-expanded x operand when a tap alone would give MMAs of small N: float32 form for
+  // C_in <= 64, bf16 form for C_in = 32 (its expansion is a copy pass)
+  const bool exp = bf16 ? tg.cn <= 32 : tg.cn <= 64;
+  const uint32_t sb = bf16 ? (exp ? wb_stage_exp(tg.cn, tg.R, pu, tg.count[0]) : wb_stage(tg.cn, tg.R, pu))
+                           : w3_layout(tg.cn, tg.R, pu, exp, tg.count[0]).stage;
+  const int max_stages = bf16 ? kWbMaxStages : kW3MaxStages;
+  p.stages = (int)((227u * 1024u / (uint32_t)max_res - 2048u) / sb);
+  if (p.stages > max_stages) p.stages = max_stages;
+  if (p.stages < 2) p.stages = 2;
+  uint32_t smem = (uint32_t)p.stages * sb;
+  // a CTA holding more than half of TMEM keeps the SM to itself
+  if (max_res == 1 && smem < 116u * 1024u) smem = 116u * 1024u;
+  const int per_sm = (int)((227u * 1024u) / (smem + 2048u));
+  const int ctas = otiles * tg.n;
+  // one wave of equal CTAs (every group carries the same work), unless it leaves more than a
+  // tenth of the slots idle; each extra wave costs a pipeline fill and a partial-sum epilogue
+  const int slots = 152 * (per_sm > 0 ? per_sm : 1);
+  int S = slots / ctas;
+  if (S * ctas * 10 < slots * 9) S = 2 * slots / ctas;
+  if (S > p.total_chunks / 16) S = p.total_chunks / 16;  // at least 16 pixel chunks per split
+  if (S < 1) S = 1;
+  while (S > 1 && (size_t)S * (per_split_elems + cout) + 64 > part_cap) --S;
+  if ((size_t)S * (per_split_elems + cout) + 64 > part_cap) return cudaErrorInvalidValue;
+  p.per_split = (p.total_chunks + S - 1) / S;
+  S = (p.total_chunks + p.per_split - 1) / p.per_split;
+  p.part = part;
+  p.bpart = part + ((size_t)S * per_split_elems + 63) / 64 * 64;
+  p.skip = skip;
+  p.err = err;
+  const dim3 grid((unsigned)otiles, (unsigned)tg.n, (unsigned)S);
+  if (bf16 && exp)
+    k_wgrad_tc_bf16<1><<<grid, 192, smem, st>>>(md, mx, p);
+  else if (bf16)
+    k_wgrad_tc_bf16<0><<<grid, 192, smem, st>>>(md, mx, p);
+  else if (tg.R == 3)
+    k_wgrad_tc_f32<3, 1><<<grid, kW3Threads, smem, st>>>(md, mx, p);
+  else if (exp)
+    k_wgrad_tc_f32<1, 1><<<grid, kW3Threads, smem, st>>>(md, mx, p);
+  else
+    k_wgrad_tc_f32<1, 0><<<grid, kW3Threads, smem, st>>>(md, mx, p);
+  count_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_reduce_wgrad_tc<<<(unsigned)(((cout + kRwO - 1) / kRwO) * cin), 256, 0, st>>>(part, S, cin,
+                                                                                 cout, gw, skip);
+  count_launch();
+  // bias: the S per-split sums of tap group 0, added in split order
+  return launch_reduce_cols(p.bpart, S, cout, gb, skip, st);
+}
+
+cudaError_t launch_wgrad_tc(int bf16, const void* dout, const void* in, int cin, int cout, int H,
+                            int W, float* part, size_t part_cap, float* gw, float* gb,
+                            const int* skip, int* err, cudaStream_t st) {
+  if (!tc_wgrad_supported(cin, cout, bf16)) return cudaErrorNotSupported;
+  if (const cudaError_t pe = tc_prepare()) return pe;
+  return launch_wgrad_grouped(bf16, dout, in, cin, cout, H, W, part, part_cap, gw, gb, skip, err,
+                              st);
+}
+
+}  // namespace n2f
