@@ -184,12 +184,10 @@ def roofline(stats, kclass: int, precision: int, engine_tc: bool, workload: str)
     if kclass in (1, 2, 3, 7) and engine_tc:
         if precision == 1:
             peak, note = pk["bf16_tflops_sustained"], f"bf16 dense sustained, {src}"
-        elif kclass == 3:
-            peak = pk["bf16_tflops_sustained"] / 6.0
-            note = f"float32 as three bf16 parts, six bf16 products: bf16 sustained / 6, {src}"
         else:
-            peak = pk["bf16_tflops_sustained"] * (1.1 / 2.25) / 3.0
-            note = f"3xTF32: TF32 = bf16 sustained x 1.1/2.25 (nominal ratio), /3 products, {src}"
+            peak = pk["bf16_tflops_sustained"] / 3.0
+            note = ("float32 as two scaled fp16 parts, three fp16 products at the bf16 dense "
+                    f"rate: bf16 sustained / 3, {src}")
         rl = {"bound": "tensor", "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s"}
     elif kclass in (1, 2, 3, 7):
         clk = pk.get("sm_max_mhz", 2070.0)

@@ -342,40 +342,43 @@ extern "C" int n2f_conv3x3(int mode, int engine, int precision, const void* in, 
   if (eng < 0) return N2F_ENOTSUP;
   cudaStream_t st = (cudaStream_t)stream;
   const size_t nw = (size_t)cin * cout * 9;
-  const size_t es = bf16 ? 2 : 4;
   char* buf = nullptr;
-  const size_t bytes = 2 * nw * sizeof(float) + 4 * nw * es + 4096 + 256;
+  const size_t bytes = 2 * nw * sizeof(float) + 4 * nw * 2 + 4096 + 256;
   CKR(cudaMallocAsync((void**)&buf, bytes, st));
   float* fwd = (float*)buf;
   float* dgr = fwd + nw;
   char* tc0 = (char*)(dgr + nw);
-  void *tcf = nullptr, *tcd = nullptr;
-  float *tcf_lo = nullptr, *tcd_lo = nullptr;
-  if (eng == N2F_ENGINE_TC) {
+  void *tcf = nullptr, *tcd = nullptr, *tcf_lo = nullptr, *tcd_lo = nullptr;
+  const bool tc = eng == N2F_ENGINE_TC;
+  if (tc) {  // 16-bit copies: bf16, or the float32 form's fp16 hi and lo parts
     tcf = tc0;
-    tcd = tc0 + nw * es;
+    tcd = tc0 + nw * 2;
     if (!bf16) {
-      tcf_lo = (float*)(tc0 + 2 * nw * es);
-      tcd_lo = (float*)(tc0 + 3 * nw * es);
+      tcf_lo = tc0 + 2 * nw * 2;
+      tcd_lo = tc0 + 3 * nw * 2;
     }
   }
-  int* err = (int*)(tc0 + 4 * nw * es);
-  cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), st);
+  int* err = (int*)(tc0 + 4 * nw * 2);
+  // float32 form: the largest weight and the largest input value set the operand scales
+  unsigned* wmax = (unsigned*)(err + 1);
+  unsigned* imax = wmax + 1;
+  const ConvScales sc{imax, wmax, nullptr};
+  const size_t n_in = (size_t)(mode == 0 ? cin : cout) * H * W;
+  cudaError_t e = cudaMemsetAsync(err, 0, 4 * sizeof(int), st);
   if (e == cudaSuccess)
-    e = launch_pack_layer(w, cin, cout, fwd, dgr, tcf, tcd, tcf_lo, tcd_lo, bf16, st);
+    e = launch_pack_layer(w, cin, cout, fwd, dgr, tcf, tcd, tcf_lo, tcd_lo, bf16, wmax, st);
+  if (e == cudaSuccess && tc && !bf16) e = launch_absmax(in, n_in, 0, imax, nullptr, st);
   if (e == cudaSuccess) {
     if (mode == 0) {
-      e = eng == N2F_ENGINE_TC
-              ? launch_conv_tc(0, bf16, in, cin, cout, H, W, tcf, tcf_lo, b, nullptr, out, nullptr,
-                               err, st)
-              : launch_conv_simt(0, bf16, in, cin, cout, H, W, fwd, b, nullptr, out, nullptr, st);
+      e = tc ? launch_conv_tc(0, bf16, in, cin, cout, H, W, tcf, tcf_lo, b, nullptr, out, sc,
+                              nullptr, err, st)
+             : launch_conv_simt(0, bf16, in, cin, cout, H, W, fwd, b, nullptr, out, nullptr, st);
     } else {
       // dgrad: `in` has C_out channels, `out` and `mask` have C_in
-      e = eng == N2F_ENGINE_TC
-              ? launch_conv_tc(1, bf16, in, cout, cin, H, W, tcd, tcd_lo, nullptr, mask, out,
-                               nullptr, err, st)
-              : launch_conv_simt(1, bf16, in, cout, cin, H, W, dgr, nullptr, mask, out, nullptr,
-                                 st);
+      e = tc ? launch_conv_tc(1, bf16, in, cout, cin, H, W, tcd, tcd_lo, nullptr, mask, out, sc,
+                              nullptr, err, st)
+             : launch_conv_simt(1, bf16, in, cout, cin, H, W, dgr, nullptr, mask, out, nullptr,
+                                st);
     }
   }
   int herr = 0;
@@ -401,11 +404,17 @@ extern "C" int n2f_conv3x3_wgrad(int engine, int precision, const void* dout, co
   float* part = nullptr;
   CKR(cudaMallocAsync((void**)&part, cap * sizeof(float) + 256, st));
   int* err = (int*)(part + cap);
-  cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), st);
+  unsigned* dmax = (unsigned*)(err + 1);  // float32 form: operand scales
+  unsigned* xmax = dmax + 1;
+  const bool tc = eng == N2F_ENGINE_TC;
+  cudaError_t e = cudaMemsetAsync(err, 0, 4 * sizeof(int), st);
+  if (e == cudaSuccess && tc && !bf16)
+    e = launch_absmax(dout, (size_t)cout * H * W, 0, dmax, nullptr, st);
+  if (e == cudaSuccess && tc && !bf16) e = launch_absmax(in, (size_t)cin * H * W, 0, xmax, nullptr, st);
   if (e == cudaSuccess)
-    e = eng == N2F_ENGINE_TC
-            ? launch_wgrad_tc(bf16, dout, in, cin, cout, H, W, part, cap, dw, db, nullptr, err, st)
-            : launch_wgrad_simt(bf16, dout, in, cin, cout, H, W, part, cap, dw, db, nullptr, st);
+    e = tc ? launch_wgrad_tc(bf16, dout, in, cin, cout, H, W, dmax, xmax, part, cap, dw, db,
+                             nullptr, err, st)
+           : launch_wgrad_simt(bf16, dout, in, cin, cout, H, W, part, cap, dw, db, nullptr, st);
   int herr = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);

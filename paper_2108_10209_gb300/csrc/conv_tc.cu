@@ -7,8 +7,9 @@
 // addressed at a shifted start: in the K-major no-swizzle layout each pixel row is 16 bytes, so
 // a shift of dx pixels is a 16*dx byte offset of the descriptor. One warp issues TMA copies,
 // one thread issues the MMAs into TMEM accumulators, the epilogue warps read TMEM back for the
-// fused bias + ReLU (forward) or ReLU mask (dgrad), and in the 3xTF32 form a warpgroup splits
-// the activations into TF32 hi/lo parts in shared memory first.
+// fused bias + ReLU (forward) or ReLU mask (dgrad), and in the float32 form a warpgroup splits
+// the activations into scaled fp16 hi/lo parts in shared memory first (f16_split.cuh; the
+// weights arrive as packed fp16 parts), so each K step is three f16-kind MMAs.
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -29,11 +30,12 @@ namespace {
 
 // ---- forward / dgrad ----------------------------------------------------------------------
 struct ConvTcParams {
-  const uint8_t* w_hi;  // packed weight stage images (bf16, or the TF32 hi parts)
-  const uint8_t* w_lo;  // TF32 residual images (3xTF32 form)
+  const uint8_t* w_hi;  // packed weight stage images (bf16, or the fp16 hi parts)
+  const uint8_t* w_lo;  // fp16 residual images (float32 form)
   const float* bias;    // forward
   const void* mask;     // dgrad: the layer's input activation (ReLU mask)
   void* out;
+  ConvScales sc;        // float32 form: largest magnitudes of A, of the weights, of the output
   int cin, cout, H, W, tiles_x;
   int stages;  // pipeline stages, 2 .. kConvMaxStages (a tuning choice; no effect on results)
   const int* skip;
@@ -51,6 +53,7 @@ struct alignas(128) ConvJob {
   const void* mask;
   void* out;
   const int* skip;  // the job's stop flag: its tiles are skipped once set
+  ConvScales sc;
   int H, W, tiles_x, tile0;
 };
 
@@ -63,16 +66,18 @@ constexpr int kConvMaxStages = 4;
 
 template <int BF16, int ROWS = kRowsM>
 struct ConvCfg {
-  static constexpr int GE = BF16 ? 8 : 4;     // channels per 16-byte group
-  static constexpr int KC = BF16 ? 16 : 8;    // channels per stage (= one K step of 32 bytes)
-  static constexpr int NSLAB = KC / GE;       // 16-byte K slabs per stage (2)
+  static constexpr int GE = BF16 ? 8 : 4;  // channels per 16-byte group of the activation map
+  static constexpr int KC = 16;            // channels per stage (one 16-element K step)
+  static constexpr int NSLAB = 2;          // 16-byte K slabs of a 16-bit operand per stage
+  static constexpr int NRAW = KC / GE;     // map groups per pixel and stage (2 bf16, 4 fp32)
   static constexpr int HALO_Y = ROWS + 2;
-  static constexpr uint32_t A_BYTES = NSLAB * HALO_Y * kHaloX * 16;
   static constexpr uint32_t A_SLAB = HALO_Y * kHaloX * 16;  // K distance between halo slabs
+  static constexpr uint32_t A_BYTES = NRAW * A_SLAB;         // the TMA halo tile
+  // float32 form: the split leaves the hi parts in slabs 0-1 and the lo parts in slabs 2-3
+  static constexpr uint32_t A_LO = 2 * A_SLAB;
   static __host__ __device__ uint32_t b_bytes(int NT) { return 9u * NSLAB * NT * 16; }
-  // stage layout: A | A_lo (tf32) | B | B_lo (tf32)
-  static __host__ __device__ uint32_t a_lo_off() { return align_up(A_BYTES, 1024); }
-  static __host__ __device__ uint32_t b_off() { return BF16 ? align_up(A_BYTES, 1024) : 2 * align_up(A_BYTES, 1024); }
+  // stage layout: A (raw, split in place) | B | B_lo (float32 form)
+  static __host__ __device__ uint32_t b_off() { return align_up(A_BYTES, 1024); }
   static __host__ __device__ uint32_t b_lo_off(int NT) { return b_off() + align_up(b_bytes(NT), 1024); }
   static __host__ __device__ uint32_t stage_bytes(int NT) {
     return BF16 ? b_off() + align_up(b_bytes(NT), 1024) : b_lo_off(NT) + align_up(b_bytes(NT), 1024);
@@ -84,7 +89,7 @@ struct ConvCfg {
 // successive tiles without a break; the accumulators are double-buffered in TMEM when two sets
 // fit (2 x kRowsM x N <= 512 columns), so a tile's epilogue overlaps the next tile's MMAs.
 // Warp roles: 0 TMA producer, 1 MMA issuer; bf16: 2-9 epilogue (two warps per TMEM lane
-// quarter, alternate 16-column blocks); 3xTF32: 2-5 epilogue, 6-9 operand split.
+// quarter, alternate 16-column blocks); float32: 2-5 epilogue, 6-9 operand split.
 template <int BF16>
 struct ConvWarps {
   static constexpr int kThreads = 320;
@@ -99,6 +104,7 @@ struct TileJob {
   const float* bias;
   const void* mask;
   void* out;
+  ConvScales sc;
   int H, W, tiles_x, local;
   bool skip;
 };
@@ -131,12 +137,14 @@ __global__ void __launch_bounds__(ConvWarps<BF16>::kThreads, 1)
     if constexpr (!GROUPED) {
       t.map = &tmA;
       t.w_hi = p.w_hi; t.w_lo = p.w_lo; t.bias = p.bias; t.mask = p.mask; t.out = p.out;
+      t.sc = p.sc;
       t.H = p.H; t.W = p.W; t.tiles_x = p.tiles_x; t.local = tile; t.skip = false;
     } else {
       while (cur + 1 < njobs && tile >= jobs[cur + 1].tile0) ++cur;
       const ConvJob& J = jobs[cur];
       t.map = &J.map;
       t.w_hi = J.w_hi; t.w_lo = J.w_lo; t.bias = J.bias; t.mask = J.mask; t.out = J.out;
+      t.sc = J.sc;
       t.H = J.H; t.W = J.W; t.tiles_x = J.tiles_x; t.local = tile - J.tile0;
       t.skip = J.skip && *J.skip;
     }
@@ -188,7 +196,7 @@ __global__ void __launch_bounds__(ConvWarps<BF16>::kThreads, 1)
             break;
           uint8_t* st = smem + s * SB;
           mbar_expect_tx(&full[s], C::A_BYTES + B_BYTES * (BF16 ? 1 : 2));
-          tma_load_4d(st, tj.map, &full[s], 0, x0 - 1, ty - 1, i * C::NSLAB);
+          tma_load_4d(st, tj.map, &full[s], 0, x0 - 1, ty - 1, i * C::NRAW);
           const size_t stage = (size_t)nt * nk + i;
           bulk_load(st + C::b_off(), tj.w_hi + stage * B_BYTES, B_BYTES, &full[s]);
           if (!BF16) bulk_load(st + C::b_lo_off(NT), tj.w_lo + stage * B_BYTES, B_BYTES, &full[s]);
@@ -201,7 +209,7 @@ __global__ void __launch_bounds__(ConvWarps<BF16>::kThreads, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {  // MMA issuer
-      const uint32_t id = idesc(BF16 ? 1 : 2, kTileM, NT, 0, 0);
+      const uint32_t id = idesc(BF16 ? 1 : 0, kTileM, NT, 0, 0);  // bf16 / fp16 operands
       uint32_t it = 0, lt = 0;
       bool ok = true;
       int cur = 0;
@@ -220,7 +228,7 @@ __global__ void __launch_bounds__(ConvWarps<BF16>::kThreads, 1)
           }
           tc_fence_after();
           const uint32_t sa = smem_u32(smem + s * SB);
-          const uint32_t sal = sa + C::a_lo_off();
+          const uint32_t sal = sa + C::A_LO;
           const uint32_t sb = sa + C::b_off(), sbl = sa + C::b_lo_off(NT);
 #pragma unroll
           for (int tap = 0; tap < 9; ++tap) {
@@ -232,12 +240,10 @@ __global__ void __launch_bounds__(ConvWarps<BF16>::kThreads, 1)
               const uint32_t ao = (uint32_t)((r + tap / 3) * kHaloX + (tap % 3)) * 16u;
               const uint64_t da = sdesc(sa + ao, C::A_SLAB, 128);
               const uint32_t d = dbase + (uint32_t)(r * NT);
-              if (BF16) {
-                mma_f16(d, da, db, id, acc);
-              } else {
-                mma_tf32(d, da, db, id, acc);
-                mma_tf32(d, da, sdesc(sbl + bo, NT * 16, 128), id, 1u);
-                mma_tf32(d, sdesc(sal + ao, C::A_SLAB, 128), db, id, 1u);
+              mma_f16(d, da, db, id, acc);
+              if (!BF16) {  // hi*lo and lo*hi
+                mma_f16(d, da, sdesc(sbl + bo, NT * 16, 128), id, 1u);
+                mma_f16(d, sdesc(sal + ao, C::A_SLAB, 128), db, id, 1u);
               }
             }
           }
@@ -248,22 +254,31 @@ __global__ void __launch_bounds__(ConvWarps<BF16>::kThreads, 1)
       }
     }
   } else if (!BF16 && warp >= 6) {
-    // 3xTF32: split each fp32 halo stage into TF32 hi and lo parts, ahead of the MMAs
+    // float32 form: each halo pixel's 16 fp32 channels (four map groups) -> the scaled fp16 hi
+    // parts (slabs 0-1) and lo parts (slabs 2-3), in place: a thread owns one pixel in all four
+    // slabs. The scale comes from the A tensor's largest magnitude.
     const int et = threadIdx.x - 192;
+    constexpr int QS = (int)(C::A_SLAB / 16);  // halo pixels
     uint32_t it = 0;
     int cur = 0;
     for (int tile = blockIdx.x; tile < ntiles && !*abort; tile += gridDim.x) {
-      if (locate(tile, cur).skip) continue;
+      const TileJob tj = locate(tile, cur);
+      if (tj.skip) continue;
+      const float sc = f16_scale(tj.sc.in);
       for (int i = 0; i < nk; ++i, ++it) {
         const int s = it % NS;
         if (!mbar_wait(&full[s], (it / NS) & 1, abort, p.err)) break;
         float4* A = reinterpret_cast<float4*>(smem + s * SB);
-        float4* Al = reinterpret_cast<float4*>(smem + s * SB + C::a_lo_off());
-        for (int q = et; q < (int)(C::A_BYTES / 16); q += 128) {
-          float4 h, l;
-          split4(A[q], h, l);
-          A[q] = h;
-          Al[q] = l;
+        uint4* U = reinterpret_cast<uint4*>(smem + s * SB);
+        for (int q = et; q < QS; q += 128) {
+          const float4 r0 = A[q], r1 = A[QS + q], r2 = A[2 * QS + q], r3 = A[3 * QS + q];
+          uint4 h0, l0, h1, l1;
+          split_f16_group(r0, r1, sc, h0, l0);
+          split_f16_group(r2, r3, sc, h1, l1);
+          U[q] = h0;
+          U[QS + q] = h1;
+          U[2 * QS + q] = l0;
+          U[3 * QS + q] = l1;
         }
         fence_proxy_async();
         mbar_arrive(&split[s]);
@@ -312,6 +327,9 @@ __global__ void __launch_bounds__(ConvWarps<BF16>::kThreads, 1)
       int nt, ty, x0;
       decode(tj, nt, ty, x0);
       const int x = x0 + row;
+      // float32 form: undo the operand scales (exact powers of two, applied one at a time)
+      const float ua = BF16 ? 1.f : f16_unscale(tj.sc.in), uw = BF16 ? 1.f : f16_unscale(tj.sc.w);
+      float mx = 0.f;  // largest |output| of this thread's tile part
       const size_t npx = (size_t)tj.H * tj.W;
       const uint4* mask = reinterpret_cast<const uint4*>(tj.mask);
       const uint32_t cbase = tbase + ((uint32_t)(wq * 32) << 16) + (uint32_t)(buf * acc_cols);
@@ -340,7 +358,7 @@ __global__ void __launch_bounds__(ConvWarps<BF16>::kThreads, 1)
         const int o0 = nt * NT + (c0 % NT);
         float v[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+        for (int j = 0; j < 16; ++j) v[j] = BF16 ? __uint_as_float(r[j]) : __uint_as_float(r[j]) * ua * uw;
 #pragma unroll
         for (int q = 0; q < NG; ++q) {
           float* vv = v + q * GE;
@@ -356,9 +374,13 @@ __global__ void __launch_bounds__(ConvWarps<BF16>::kThreads, 1)
 #pragma unroll
             for (int j = 0; j < GE; ++j) vv[j] = mk[j] > 0.f ? vv[j] : 0.f;
           }
+          if (!BF16)
+#pragma unroll
+            for (int j = 0; j < GE; ++j) mx = fmaxf(mx, fabsf(vv[j]));
           store_group<T>((T*)tj.out, gidx(c0, q), vv);
         }
       }
+      if (!BF16 && tj.sc.out) warp_absmax_to(mx, tj.sc.out);
       tc_fence_before();
       mbar_arrive(&acce[buf]);
       ++lt;
@@ -496,17 +518,18 @@ static cudaError_t conv_tc_dispatch(int mode, int bf16, const CUtensorMap& m, Co
 
 static cudaError_t conv_params(int bf16, const void* in, int cin, int cout, int H, int W,
                                const void* w_hi, const void* w_lo, const float* b,
-                               const void* mask, void* out, const int* skip, int* err, int rows,
-                               CUtensorMap* m, ConvTcParams* p) {
-  const int KC = bf16 ? ConvCfg<1>::KC : ConvCfg<0>::KC;
-  const int GE = bf16 ? 8 : 4;
-  cudaError_t e = make_map(m, in, bf16, cin, H, W, kHaloX, rows + 2, KC / GE);
+                               const void* mask, void* out, ConvScales sc, const int* skip,
+                               int* err, int rows, CUtensorMap* m, ConvTcParams* p) {
+  if (!bf16 && (!sc.in || !sc.w || !w_lo)) return cudaErrorInvalidValue;
+  const int NRAW = bf16 ? ConvCfg<1>::NRAW : ConvCfg<0>::NRAW;
+  cudaError_t e = make_map(m, in, bf16, cin, H, W, kHaloX, rows + 2, NRAW);
   if (e != cudaSuccess) return e;
   p->w_hi = (const uint8_t*)w_hi;
   p->w_lo = (const uint8_t*)w_lo;
   p->bias = b;
   p->mask = mask;
   p->out = out;
+  p->sc = sc;
   p->cin = cin;
   p->cout = cout;
   p->H = H;
@@ -520,7 +543,8 @@ static cudaError_t conv_params(int bf16, const void* in, int cin, int cout, int 
 
 cudaError_t conv_tc_autotune(int mode, int bf16, const void* in, int cin, int cout, int H, int W,
                              const void* w_hi, const void* w_lo, const float* b, const void* mask,
-                             void* out, int* err, cudaStream_t st) {
+                             void* out, ConvScales sc, int* err, cudaStream_t st) {
+  sc.out = nullptr;  // trial launches leave the tensors' magnitude words alone
   if (!tc_supported(cin, cout)) return cudaErrorNotSupported;
   if (const cudaError_t pe = tc_prepare()) return pe;
   const ConvKey key{mode, bf16, cin, cout, H, W};
@@ -537,7 +561,8 @@ cudaError_t conv_tc_autotune(int mode, int bf16, const void* in, int cin, int co
   for (int rows = 1; rows <= 2 && e == cudaSuccess; ++rows) {
     CUtensorMap m;
     ConvTcParams p;
-    e = conv_params(bf16, in, cin, cout, H, W, w_hi, w_lo, b, mask, out, nullptr, err, rows, &m, &p);
+    e = conv_params(bf16, in, cin, cout, H, W, w_hi, w_lo, b, mask, out, sc, nullptr, err, rows,
+                    &m, &p);
     if (e != cudaSuccess) break;
     const long ntiles = (long)p.tiles_x * ((H + rows - 1) / rows) * (cout / f.NT);
     const uint32_t sb = conv_stage_bytes(bf16, f.NT, rows);
@@ -571,14 +596,14 @@ cudaError_t conv_tc_autotune(int mode, int bf16, const void* in, int cin, int co
 
 cudaError_t launch_conv_tc(int mode, int bf16, const void* in, int cin, int cout, int H, int W,
                            const void* w_hi, const void* w_lo, const float* b, const void* mask,
-                           void* out, const int* skip, int* err, cudaStream_t st) {
+                           void* out, ConvScales sc, const int* skip, int* err, cudaStream_t st) {
   if (!tc_supported(cin, cout)) return cudaErrorNotSupported;
   if (const cudaError_t pe = tc_prepare()) return pe;
   const TcCfg f = tc_cfg(cin, cout, bf16);
   const ConvTune t = conv_tune_for(ConvKey{mode, bf16, cin, cout, H, W});
   CUtensorMap m;
   ConvTcParams p;
-  cudaError_t e = conv_params(bf16, in, cin, cout, H, W, w_hi, w_lo, b, mask, out, skip, err,
+  cudaError_t e = conv_params(bf16, in, cin, cout, H, W, w_hi, w_lo, b, mask, out, sc, skip, err,
                               t.rows, &m, &p);
   if (e != cudaSuccess) return e;
   const long ntiles = (long)p.tiles_x * ((H + t.rows - 1) / t.rows) * (cout / f.NT);
@@ -594,15 +619,16 @@ cudaError_t conv_group_table(int mode, int bf16, int cin, int cout, const ConvGr
   (void)mode;
   if (!tc_supported(cin, cout)) return cudaErrorNotSupported;
   const TcCfg f = tc_cfg(cin, cout, bf16);
-  const int KC = bf16 ? ConvCfg<1>::KC : ConvCfg<0>::KC;
-  const int GE = bf16 ? 8 : 4;
+  const int NRAW = bf16 ? ConvCfg<1>::NRAW : ConvCfg<0>::NRAW;
   ConvJob* t = static_cast<ConvJob*>(table);
   long tiles = 0;
   for (int k = 0; k < n; ++k) {
     memset(&t[k], 0, sizeof(ConvJob));
+    if (!bf16 && (!e[k].sc.in || !e[k].sc.w || !e[k].w_lo)) return cudaErrorInvalidValue;
     cudaError_t r = make_map(&t[k].map, e[k].in, bf16, cin, e[k].H, e[k].W, kHaloX, kRowsM + 2,
-                             KC / GE);
+                             NRAW);
     if (r != cudaSuccess) return r;
+    t[k].sc = e[k].sc;
     t[k].w_hi = (const uint8_t*)e[k].w_hi;
     t[k].w_lo = (const uint8_t*)e[k].w_lo;
     t[k].bias = e[k].bias;

@@ -4,6 +4,7 @@
 #include <math.h>
 
 #include "cg_util.cuh"
+#include "f16_split.cuh"
 #include "n2f_internal.h"
 #include "tc_layout.cuh"
 
@@ -205,10 +206,12 @@ cudaError_t launch_init_params(float* theta, const NetShape& net, uint64_t seed,
 //   SIMT forward  [C_in/8][tap][8][C_out]   (first layer: canonical [C_out][C_0][9])
 //   SIMT dgrad    [C_out/8][8 - tap][8][C_in]
 //   tensor core   tc_layout.cuh order, forward (rows o, k = tap*C_in + c) and dgrad
-//                 (rows c, k = (8 - tap)*C_out + o); bf16, or a TF32 hi part + residual.
+//                 (rows c, k = (8 - tap)*C_out + o); bf16, or (float32 form) the fp16 hi and lo
+//                 parts of th * s, s the layer's power-of-two weight scale.
 __device__ __forceinline__ void pack_one(float* fwd, float* dgr, void* tcf, void* tcd,
-                                         float* tcf_lo, float* tcd_lo, int tc_bf16, int first,
-                                         int cin, int cout, int o, int c, int tap, float th) {
+                                         void* tcf_lo, void* tcd_lo, int tc_bf16, int first,
+                                         int cin, int cout, int o, int c, int tap, float th,
+                                         float s) {
   if (first) {
     if (fwd) fwd[((size_t)o * cin + c) * 9 + tap] = th;
     return;
@@ -222,72 +225,173 @@ __device__ __forceinline__ void pack_one(float* fwd, float* dgr, void* tcf, void
       ((__nv_bfloat16*)tcf)[fi] = __float2bfloat16_rn(th);
       ((__nv_bfloat16*)tcd)[di] = __float2bfloat16_rn(th);
     } else {
-      // 3xTF32 split th = hi + lo, both parts rounded to the nearest TF32 value
-      const float hi = __uint_as_float((__float_as_uint(th) + 0x1000u) & 0xFFFFE000u);
-      const float lo = __uint_as_float((__float_as_uint(th - hi) + 0x1000u) & 0xFFFFE000u);
-      ((float*)tcf)[fi] = hi;
-      tcf_lo[fi] = lo;
-      ((float*)tcd)[di] = hi;
-      tcd_lo[di] = lo;
+      const float x = th * s;
+      const __half hi = __float2half_rn(x);
+      const __half lo = __float2half_rn(x - __half2float(hi));
+      ((__half*)tcf)[fi] = hi;
+      ((__half*)tcf_lo)[fi] = lo;
+      ((__half*)tcd)[di] = hi;
+      ((__half*)tcd_lo)[di] = lo;
     }
   }
 }
 
+// Layer of parameter i and whether it is a 3x3 weight (not a bias or the head).
+__device__ __forceinline__ int weight_layer(const PackArgs& pa, unsigned long long i) {
+  int l = 0;
+  while (l < kLayers && i >= pa.w_off[l + 1]) ++l;
+  return (l == kLayers || i >= pa.b_off[l]) ? -1 : l;
+}
+
+// Weight i (of layer l) into its SIMT copies and / or its tensor-core copies.
+__device__ __forceinline__ void pack_param(const PackArgs& pa, int l, unsigned long long i,
+                                           float th, bool simt, bool tc, float s) {
+  const int cin = l == 0 ? pa.c0 : pa.widths[l - 1], cout = pa.widths[l];
+  const size_t j = i - pa.w_off[l];
+  const int o = (int)(j / ((size_t)cin * 9));
+  const int rem = (int)(j % ((size_t)cin * 9));
+  pack_one(simt ? pa.fwd[l] : nullptr, simt ? pa.dgr[l] : nullptr, tc ? pa.tcf[l] : nullptr,
+           pa.tcd[l], pa.tcf_lo[l], pa.tcd_lo[l], pa.tc_bf16, l == 0, cin, cout, o, rem / 9,
+           rem % 9, th, s);
+}
+
 // Adam (Kingma & Ba, Algorithm 1; Methods: lr 0.001), fused with writing the packed weight
-// copies the convolution kernels read. update = 0 only packs (after init / set_theta).
+// copies the convolution kernels read. update = 0 only packs (after init / set_theta). In the
+// float32 form the tensor-core copies need each layer's largest weight first: this kernel
+// collects it (pa.sw->wnew, by step parity) and k_pack_f16 writes those copies; it also clears
+// the activation and delta words for the next pass and the other parity's weight words.
 __global__ void k_adam(PackArgs pa, const float* __restrict__ grad, float* __restrict__ m,
                        float* __restrict__ v, float lr, float b1, float b2, float eps,
                        const DevState* __restrict__ state, int update) {
   if (update && state->stopped) return;
+  __shared__ unsigned smax[kLayers];
+  ScaleWords* sw = pa.sw;
+  if (threadIdx.x < kLayers) smax[threadIdx.x] = 0u;
+  __syncthreads();
   float bc1 = 1.f, bc2 = 1.f;
   if (update) {
     bc1 = state->bc1;
     bc2 = state->bc2;
   }
-  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
-       i < pa.count; i += (unsigned long long)gridDim.x * blockDim.x) {
-    float th = pa.theta[i];
-    if (update) {
-      const float g = grad[i];
-      const float mi = b1 * m[i] + (1.f - b1) * g;
-      const float vi = b2 * v[i] + (1.f - b2) * g * g;
-      m[i] = mi;
-      v[i] = vi;
-      th -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
-      pa.theta[i] = th;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long i0 = blockIdx.x * (unsigned long long)blockDim.x; i0 < pa.count;
+       i0 += stride) {
+    const unsigned long long i = i0 + threadIdx.x;
+    int lw = -1;  // tensor-core layer of a float32-form weight
+    float aw = 0.f;
+    if (i < pa.count) {
+      float th = pa.theta[i];
+      if (update) {
+        const float g = grad[i];
+        const float mi = b1 * m[i] + (1.f - b1) * g;
+        const float vi = b2 * v[i] + (1.f - b2) * g * g;
+        m[i] = mi;
+        v[i] = vi;
+        th -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+        pa.theta[i] = th;
+      }
+      const int l = weight_layer(pa, i);
+      if (l >= 0) {
+        pack_param(pa, l, i, th, true, pa.tc_bf16 != 0, 1.f);
+        if (pa.tcf[l] && sw) {
+          lw = l;
+          aw = fabsf(th);
+        }
+      }
     }
-    int l = 0;
-    while (l < kLayers && i >= pa.w_off[l + 1]) ++l;
-    if (l == kLayers || i >= pa.b_off[l]) continue;  // head or a bias: read from theta
-    const int cin = l == 0 ? pa.c0 : pa.widths[l - 1], cout = pa.widths[l];
-    const size_t j = i - pa.w_off[l];
-    const int o = (int)(j / ((size_t)cin * 9));
-    const int rem = (int)(j % ((size_t)cin * 9));
-    pack_one(pa.fwd[l], pa.dgr[l], pa.tcf[l], pa.tcd[l], pa.tcf_lo[l], pa.tcd_lo[l], pa.tc_bf16,
-             l == 0, cin, cout, o, rem / 9, rem % 9, th);
+    if (sw) {  // one shared-memory atomic per warp when its lanes share a layer
+      const unsigned b = __float_as_uint(aw);
+      const int l0 = __shfl_sync(0xffffffffu, lw, 0);
+      if (__all_sync(0xffffffffu, lw == l0)) {
+        const unsigned mx = __reduce_max_sync(0xffffffffu, b);
+        if ((threadIdx.x & 31) == 0 && l0 >= 0) atomicMax(&smax[l0], mx);
+      } else if (lw >= 0) {
+        atomicMax(&smax[lw], b);
+      }
+    }
+  }
+  if (!sw) return;
+  __syncthreads();
+  const int slot = state->t & 1;
+  if (threadIdx.x < kLayers && smax[threadIdx.x]) atomicMax(&sw->wnew[slot][threadIdx.x], smax[threadIdx.x]);
+  if (blockIdx.x == 0 && threadIdx.x < kLayers) {
+    sw->wnew[slot ^ 1][threadIdx.x] = 0u;
+    sw->act[threadIdx.x] = 0u;
+    sw->delta[threadIdx.x] = 0u;
   }
 }
 
-// Packs one canonical [C_out][C_in][3][3] weight tensor into the kernels' operand copies.
+// Float32 form: the fp16 hi / lo tensor-core copies of every tensor-core layer, scaled by the
+// power of two that the layer's largest weight (collected by k_adam) gives; records that
+// largest weight in sw->w for the convolution kernels.
+__global__ void k_pack_f16(PackArgs pa, const DevState* __restrict__ state, int update) {
+  if (update && state->stopped) return;
+  __shared__ float ss[kLayers];
+  ScaleWords* sw = pa.sw;
+  const int slot = state->t & 1;
+  if (threadIdx.x < kLayers) {
+    const unsigned mw = sw->wnew[slot][threadIdx.x];
+    ss[threadIdx.x] = pow2f(f16_scale_exp(mw));
+    if (blockIdx.x == 0) sw->w[threadIdx.x] = mw;
+  }
+  __syncthreads();
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+       i < pa.count; i += (unsigned long long)gridDim.x * blockDim.x) {
+    const int l = weight_layer(pa, i);
+    if (l >= 0 && pa.tcf[l]) pack_param(pa, l, i, pa.theta[i], false, true, ss[l]);
+  }
+}
+
+// Packs one canonical [C_out][C_in][3][3] weight tensor into the kernels' operand copies
+// (float32 form: scaled by the largest weight, *wmax).
 __global__ void k_pack_layer(const float* __restrict__ w, int cin, int cout, float* fwd,
-                             float* dgr, void* tcf, void* tcd, float* tcf_lo, float* tcd_lo,
-                             int tc_bf16) {
+                             float* dgr, void* tcf, void* tcd, void* tcf_lo, void* tcd_lo,
+                             int tc_bf16, const unsigned* wmax) {
   const size_t n = (size_t)cout * cin * 9;
+  const float s = (tc_bf16 || !wmax) ? 1.f : f16_scale(wmax);
   for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < n;
        j += (size_t)gridDim.x * blockDim.x) {
     const int o = (int)(j / ((size_t)cin * 9));
     const int rem = (int)(j % ((size_t)cin * 9));
     pack_one(fwd, dgr, tcf, tcd, tcf_lo, tcd_lo, tc_bf16, cin == 1, cin, cout, o, rem / 9,
-             rem % 9, w[j]);
+             rem % 9, w[j], s);
   }
 }
 
+template <typename T>
+__global__ void k_absmax(const T* __restrict__ x, size_t n, unsigned* out, const int* skip) {
+  if (skip && *skip) return;
+  float mx = 0.f;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    mx = fmaxf(mx, fabsf((float)x[i]));
+  warp_absmax_to(mx, out);
+}
+
+cudaError_t launch_absmax(const void* x, size_t n, int bf16, unsigned* out, const int* skip,
+                          cudaStream_t st) {
+  unsigned g = nblocks(n, 256);
+  if (g > 152u * 4) g = 152u * 4;
+  if (g == 0) g = 1;
+  if (bf16)
+    k_absmax<__nv_bfloat16><<<g, 256, 0, st>>>((const __nv_bfloat16*)x, n, out, skip);
+  else
+    k_absmax<float><<<g, 256, 0, st>>>((const float*)x, n, out, skip);
+  N2F_LAUNCH_CHECK();
+}
+
 cudaError_t launch_pack_layer(const float* w, int cin, int cout, float* fwd, float* dgr, void* tcf,
-                              void* tcd, float* tcf_lo, float* tcd_lo, int tc_bf16,
+                              void* tcd, void* tcf_lo, void* tcd_lo, int tc_bf16, unsigned* wmax,
                               cudaStream_t st) {
-  unsigned g = nblocks((size_t)cout * cin * 9, 256);
+  const size_t n = (size_t)cout * cin * 9;
+  if (tcf && !tc_bf16) {
+    if (!wmax) return cudaErrorInvalidValue;
+    const cudaError_t e = launch_absmax(w, n, 0, wmax, nullptr, st);
+    if (e != cudaSuccess) return e;
+  }
+  unsigned g = nblocks(n, 256);
   if (g > 152u * 8) g = 152u * 8;
-  k_pack_layer<<<g, 256, 0, st>>>(w, cin, cout, fwd, dgr, tcf, tcd, tcf_lo, tcd_lo, tc_bf16);
+  k_pack_layer<<<g, 256, 0, st>>>(w, cin, cout, fwd, dgr, tcf, tcd, tcf_lo, tcd_lo, tc_bf16, wmax);
   N2F_LAUNCH_CHECK();
 }
 
@@ -297,6 +401,10 @@ cudaError_t launch_adam(const PackArgs& pa, const float* grad, float* m, float* 
   unsigned g = nblocks(pa.count, 256);
   if (g > 152u * 8) g = 152u * 8;
   k_adam<<<g, 256, 0, st>>>(pa, grad, m, v, lr, b1, b2, eps, state, update);
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !pa.sw) return e;
+  k_pack_f16<<<g, 256, 0, st>>>(pa, state, update);
   N2F_LAUNCH_CHECK();
 }
 
@@ -367,19 +475,11 @@ cudaError_t launch_unpack_cg_f64(const void* cg, int C, int H, int W, int bf16, 
 // 2a caption: the input may be multi-channel). One thread per pixel: 9 C_0 taps from the
 // planes (zero outside), C outputs + bias, ReLU.
 template <typename T, int C0>
-__global__ void __launch_bounds__(256) k_conv1_fwd(const float* __restrict__ img, int H, int W,
-                                                   const float* __restrict__ w,
-                                                   const float* __restrict__ b, int C,
-                                                   T* __restrict__ out, const int* skip) {
-  if (skip && *skip) return;
+__device__ __forceinline__ void conv1_pixel(const float* __restrict__ img, int H, int W,
+                                            const float* sw, const float* sb, int C,
+                                            T* __restrict__ out, size_t p, float& mx) {
   constexpr int G = CGTraits<T>::G;
-  __shared__ float sw[64 * C0 * 9], sb[64];
-  for (int i = threadIdx.x; i < C * C0 * 9; i += blockDim.x) sw[i] = w[i];
-  for (int i = threadIdx.x; i < C; i += blockDim.x) sb[i] = b[i];
-  __syncthreads();
   const size_t npx = (size_t)H * W;
-  const size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (p >= npx) return;
   const int y = (int)(p / W), x = (int)(p % W);
   float t[C0][9];
 #pragma unroll
@@ -404,32 +504,52 @@ __global__ void __launch_bounds__(256) k_conv1_fwd(const float* __restrict__ img
 #pragma unroll
         for (int q = 0; q < 9; ++q) s += sw[(o * C0 + c) * 9 + q] * t[c][q];
       v[k] = s > 0.f ? s : 0.f;
+      mx = fmaxf(mx, v[k]);
     }
     store_group<T>(out, (size_t)g * npx + p, v);
   }
 }
 
+template <typename T, int C0>
+__global__ void __launch_bounds__(256) k_conv1_fwd(const float* __restrict__ img, int H, int W,
+                                                   const float* __restrict__ w,
+                                                   const float* __restrict__ b, int C,
+                                                   T* __restrict__ out, unsigned* amax,
+                                                   const int* skip) {
+  if (skip && *skip) return;
+  __shared__ float sw[64 * C0 * 9], sb[64];
+  for (int i = threadIdx.x; i < C * C0 * 9; i += blockDim.x) sw[i] = w[i];
+  for (int i = threadIdx.x; i < C; i += blockDim.x) sb[i] = b[i];
+  __syncthreads();
+  const size_t npx = (size_t)H * W;
+  const size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  float mx = 0.f;  // largest output of this thread (ReLU outputs are >= 0)
+  if (p < npx) conv1_pixel<T, C0>(img, H, W, sw, sb, C, out, p, mx);
+  if (amax) block_absmax_to(mx, amax);
+}
+
 template <typename T>
 static void conv1_fwd_c0(int C0, unsigned g, const float* img, int H, int W, const float* w,
-                         const float* b, int C, T* out, const int* skip, cudaStream_t st) {
+                         const float* b, int C, T* out, unsigned* amax, const int* skip,
+                         cudaStream_t st) {
   switch (C0) {
-    case 1: k_conv1_fwd<T, 1><<<g, 256, 0, st>>>(img, H, W, w, b, C, out, skip); break;
-    case 2: k_conv1_fwd<T, 2><<<g, 256, 0, st>>>(img, H, W, w, b, C, out, skip); break;
-    case 3: k_conv1_fwd<T, 3><<<g, 256, 0, st>>>(img, H, W, w, b, C, out, skip); break;
-    default: k_conv1_fwd<T, 4><<<g, 256, 0, st>>>(img, H, W, w, b, C, out, skip); break;
+    case 1: k_conv1_fwd<T, 1><<<g, 256, 0, st>>>(img, H, W, w, b, C, out, amax, skip); break;
+    case 2: k_conv1_fwd<T, 2><<<g, 256, 0, st>>>(img, H, W, w, b, C, out, amax, skip); break;
+    case 3: k_conv1_fwd<T, 3><<<g, 256, 0, st>>>(img, H, W, w, b, C, out, amax, skip); break;
+    default: k_conv1_fwd<T, 4><<<g, 256, 0, st>>>(img, H, W, w, b, C, out, amax, skip); break;
   }
 }
 
 cudaError_t launch_conv1_fwd(const float* img, int C0, int H, int W, const float* w,
-                             const float* b, int C, int bf16, void* out, const int* skip,
-                             cudaStream_t st) {
+                             const float* b, int C, int bf16, void* out, unsigned* amax,
+                             const int* skip, cudaStream_t st) {
   if (C > 64 || C0 < 1 || C0 > kMaxC0) return cudaErrorInvalidValue;
   const size_t npx = (size_t)H * W;
   if (bf16)
     conv1_fwd_c0<__nv_bfloat16>(C0, nblocks(npx, 256), img, H, W, w, b, C, (__nv_bfloat16*)out,
-                                skip, st);
+                                nullptr, skip, st);
   else
-    conv1_fwd_c0<float>(C0, nblocks(npx, 256), img, H, W, w, b, C, (float*)out, skip, st);
+    conv1_fwd_c0<float>(C0, nblocks(npx, 256), img, H, W, w, b, C, (float*)out, amax, skip, st);
   N2F_LAUNCH_CHECK();
 }
 
@@ -566,7 +686,7 @@ __global__ void __launch_bounds__(256) k_head_train(const T* __restrict__ a8, in
                                                     const float* __restrict__ b9,
                                                     const float* __restrict__ tgt, int loss_kind,
                                                     float* __restrict__ dzbuf, T* __restrict__ d8,
-                                                    double* __restrict__ loss_part,
+                                                    unsigned* dmax, double* __restrict__ loss_part,
                                                     float* __restrict__ hpart, const int* skip) {
   if (skip && *skip) return;
   constexpr int G = CGTraits<T>::G;
@@ -605,13 +725,17 @@ __global__ void __launch_bounds__(256) k_head_train(const T* __restrict__ a8, in
     }
     dzbuf[p] = dz;
   }
+  float dmx = 0.f;  // largest |delta_8| of this pixel
   for (int g = 0; g < C / G; ++g) {
     float v[G];
     if (live) {
       load_group<T>(a8, (size_t)g * npx + p, v);
       float d[G];
 #pragma unroll
-      for (int k = 0; k < G; ++k) d[k] = v[k] > 0.f ? dz * sw[g * G + k] : 0.f;
+      for (int k = 0; k < G; ++k) {
+        d[k] = v[k] > 0.f ? dz * sw[g * G + k] : 0.f;
+        dmx = fmaxf(dmx, fabsf(d[k]));
+      }
       store_group<T>(d8, (size_t)g * npx + p, d);
     } else {
 #pragma unroll
@@ -647,22 +771,23 @@ __global__ void __launch_bounds__(256) k_head_train(const T* __restrict__ a8, in
     for (int k = 0; k < nw; ++k) s += sl[k];
     loss_part[blockIdx.x] = s;
   }
+  if (dmax) block_absmax_to(dmx, dmax);
 }
 
 cudaError_t launch_head_train(const void* a8, int C, int npx, const float* w9, const float* b9,
                               const float* tgt, int loss_kind, int bf16, float* dz, void* d8,
-                              double* loss_part, float* hpart, int* nblk_out, const int* skip,
-                              cudaStream_t st) {
+                              unsigned* dmax, double* loss_part, float* hpart, int* nblk_out,
+                              const int* skip, cudaStream_t st) {
   if (C > 256) return cudaErrorInvalidValue;
   const unsigned nb = nblocks(npx, 256);
   *nblk_out = (int)nb;
   if (bf16)
     k_head_train<__nv_bfloat16><<<nb, 256, 0, st>>>((const __nv_bfloat16*)a8, C, npx, w9, b9, tgt,
-                                                    loss_kind, dz, (__nv_bfloat16*)d8, loss_part,
-                                                    hpart, skip);
+                                                    loss_kind, dz, (__nv_bfloat16*)d8, nullptr,
+                                                    loss_part, hpart, skip);
   else
     k_head_train<float><<<nb, 256, 0, st>>>((const float*)a8, C, npx, w9, b9, tgt, loss_kind, dz,
-                                            (float*)d8, loss_part, hpart, skip);
+                                            (float*)d8, dmax, loss_part, hpart, skip);
   N2F_LAUNCH_CHECK();
 }
 

@@ -49,19 +49,33 @@ struct DevState {
   int pad;
 };
 
+// Largest magnitudes (float bits of |v|, raised by atomicMax in the kernels that write the
+// tensor) of the tensors that the float32 form's tensor-core kernels split into two fp16 parts;
+// each consumer derives its power-of-two operand scale from them (tc_common.cuh, f16_scale).
+// The Adam kernel clears `act` and `delta` after every step, so a word bounds the tensor's
+// current contents (it may also cover an earlier pass: still a bound, never too small).
+struct ScaleWords {
+  unsigned act[kLayers];       // act[m]: output of layer m (training or validation forward)
+  unsigned delta[kLayers];     // delta[m]: masked gradient at layer m's pre-activation
+  unsigned wnew[2][kLayers];   // weights after an Adam step, by the step's parity
+  unsigned w[kLayers];         // the weights that the packed tensor-core copies were made from
+};
+
 // Packed weight copies written by the init/Adam kernels, one per layer l = 0..7:
 //   fwd : [C_in/8][9][8][C_out] f32 (tap = 3*ky + kx; layer 1: [C_out][9]) -- SIMT forward
 //   dgr : [C_out/8][9][8][C_in] f32, tap rotated to 8 - tap                -- SIMT dgrad
 //   tcf/tcd : the same two matrices in the tensor-core operand order (tc_layout.cuh), bf16,
-//             or float32 TF32-hi parts with the residuals in tcf_lo/tcd_lo (3xTF32 form)
+//             or in the float32 form fp16 hi parts of the scaled weights with the fp16
+//             residuals in tcf_lo/tcd_lo (written by k_pack_f16 after the Adam kernel)
 struct PackArgs {
   float* theta;
   float* fwd[kLayers];
   float* dgr[kLayers];
   void* tcf[kLayers];
   void* tcd[kLayers];
-  float* tcf_lo[kLayers];
-  float* tcd_lo[kLayers];
+  void* tcf_lo[kLayers];
+  void* tcd_lo[kLayers];
+  ScaleWords* sw;  // float32 form with tensor-core layers; nullptr otherwise
   int widths[kLayers];
   int c0;       // input channels of the first layer
   unsigned long long w_off[kLayers + 1], b_off[kLayers + 1];
@@ -79,12 +93,19 @@ cudaError_t launch_gather(const float* x, int H, int W, float* ue, float* uo, fl
                           cudaStream_t st);
 cudaError_t launch_u16_to_f32(const uint16_t* in, float* out, size_t n, cudaStream_t st);
 cudaError_t launch_init_params(float* theta, const NetShape& net, uint64_t seed, cudaStream_t st);
+// Adam step (update = 1) or a plain repack (update = 0), then, in the float32 form, the fp16
+// tensor-core copies (k_pack_f16). With update = 0 the caller clears pa.sw->wnew first.
 cudaError_t launch_adam(const PackArgs& pa, const float* grad, float* m, float* v, float lr,
                         float b1, float b2, float eps, const DevState* state, int update,
                         cudaStream_t st);
+// One canonical weight tensor into its operand copies. Float32 form: wmax (device word, zeroed
+// by the caller) receives the tensor's largest magnitude and the fp16 parts are scaled by it.
 cudaError_t launch_pack_layer(const float* w, int cin, int cout, float* fwd, float* dgr, void* tcf,
-                              void* tcd, float* tcf_lo, float* tcd_lo, int tc_bf16,
+                              void* tcd, void* tcf_lo, void* tcd_lo, int tc_bf16, unsigned* wmax,
                               cudaStream_t st);
+// *out = max(*out, largest |x[i]|) as float bits, x float32 (bf16 = 0) or bf16.
+cudaError_t launch_absmax(const void* x, size_t n, int bf16, unsigned* out, const int* skip,
+                          cudaStream_t st);
 cudaError_t launch_pack_cg(const float* nchw, int C, int H, int W, int bf16, void* cg,
                            cudaStream_t st);
 cudaError_t launch_unpack_cg(const void* cg, int C, int H, int W, int bf16, float* nchw,
@@ -94,9 +115,10 @@ cudaError_t launch_unpack_cg_f64(const void* cg, int C, int H, int W, int bf16, 
 
 // First layer (C_in = 1): image plane -> CG map with bias + ReLU.
 constexpr int kMaxC0 = 4;  // input channels the first-layer kernels take
+// amax (may be null): receives the output's largest magnitude (float32 form).
 cudaError_t launch_conv1_fwd(const float* img /*[C0][H][W]*/, int C0, int H, int W,
                              const float* w /*[C][C0][9]*/, const float* b, int C, int bf16,
-                             void* out, const int* skip, cudaStream_t st);
+                             void* out, unsigned* amax, const int* skip, cudaStream_t st);
 // First layer weight gradient: partials then ordered reduce into grad (canonical order).
 cudaError_t launch_conv1_wgrad(const void* dout, const float* img, int C0, int H, int W, int C,
                                int bf16, float* part, size_t part_cap, float* gw, float* gb,
@@ -120,13 +142,22 @@ cudaError_t wgrad_tc_prepare();  // the weight-gradient kernels' part
 bool tc_supported(int cin, int cout);
 bool tc_wgrad_supported(int cin, int cout, int bf16);
 // mode 0 forward (bias + ReLU), 1 dgrad (ReLU mask); w_hi/w_lo: packed operand copies
-// (tc_layout.cuh), w_lo only in the float32 (3xTF32) form. err: device error word.
+// (tc_layout.cuh), w_lo only in the float32 form. err: device error word.
+// Float32 form: the operands are split into two fp16 parts scaled by powers of two derived from
+// the largest magnitudes `sc.in` (the A operand tensor) and `sc.w` (the weights the packed copies
+// were made from); `sc.out`, if not null, receives the output's largest magnitude. The bf16 form
+// ignores all three.
+struct ConvScales {
+  const unsigned* in = nullptr;
+  const unsigned* w = nullptr;
+  unsigned* out = nullptr;
+};
 // Times the launch choices that leave results unchanged (pipeline stages, CTAs per SM) for one
 // conv shape on the given buffers (their contents are overwritten) and caches the fastest for
 // every later launch of that (mode, precision, C_in, C_out, H, W) in this process.
 cudaError_t conv_tc_autotune(int mode, int bf16, const void* in, int cin, int cout, int H, int W,
                              const void* w_hi, const void* w_lo, const float* b, const void* mask,
-                             void* out, int* err, cudaStream_t st);
+                             void* out, ConvScales sc, int* err, cudaStream_t st);
 // Grouped forward / dgrad: one persistent launch over the tiles of n images of the same layer
 // shape, each with its own input, weights, bias or mask and output. The table (conv_job_size()
 // bytes per image, 128-byte aligned) is filled on the host by conv_group_table and copied to
@@ -140,6 +171,7 @@ struct ConvGroupEntry {
   const void* mask;
   void* out;
   const int* skip;
+  ConvScales sc;
 };
 size_t conv_job_size();
 cudaError_t conv_group_table(int mode, int bf16, int cin, int cout, const ConvGroupEntry* e,
@@ -148,17 +180,20 @@ cudaError_t launch_conv_tc_grouped(int mode, int bf16, int cin, int cout, const 
                                    int n, long ntiles, int* err, cudaStream_t st);
 cudaError_t launch_conv_tc(int mode, int bf16, const void* in, int cin, int cout, int H, int W,
                            const void* w_hi, const void* w_lo, const float* b, const void* mask,
-                           void* out, const int* skip, int* err, cudaStream_t st);
+                           void* out, ConvScales sc, const int* skip, int* err, cudaStream_t st);
+// dmax / xmax: largest magnitudes of dout and in (float32 form; ignored by the bf16 form).
 cudaError_t launch_wgrad_tc(int bf16, const void* dout, const void* in, int cin, int cout, int H,
-                            int W, float* part, size_t part_cap, float* gw, float* gb,
-                            const int* skip, int* err, cudaStream_t st);
+                            int W, const unsigned* dmax, const unsigned* xmax, float* part,
+                            size_t part_cap, float* gw, float* gb, const int* skip, int* err,
+                            cudaStream_t st);
 size_t tc_weight_elems(int cin, int cout);  // elements of one packed tensor-core weight copy
 
-// Head (1x1 conv + sigmoid), training: z, loss partials, dL/dz, delta_8, head-grad partials.
+// Head (1x1 conv + sigmoid), training: z, loss partials, dL/dz, delta_8, head-grad partials;
+// dmax (may be null) receives delta_8's largest magnitude.
 cudaError_t launch_head_train(const void* a8, int C, int npx, const float* w9, const float* b9,
                               const float* tgt, int loss_kind, int bf16, float* dz, void* d8,
-                              double* loss_part, float* hpart, int* nblk_out, const int* skip,
-                              cudaStream_t st);
+                              unsigned* dmax, double* loss_part, float* hpart, int* nblk_out,
+                              const int* skip, cudaStream_t st);
 // out[c] = sum over R rows of part[r][c] (C columns), fixed order (one block per column).
 cudaError_t launch_reduce_cols(const float* part, int R, int C, float* out, const int* skip,
                                cudaStream_t st);

@@ -67,12 +67,20 @@ extern "C" int n2f_conv3x3_wgrad_noalloc(int engine, int precision, const void* 
   cudaStream_t st = (cudaStream_t)stream;
   const size_t cap = kScratchFloats - kErrFloats;
   int* err = reinterpret_cast<int*>(scratch + cap);
-  // the partial sums are overwritten in full by every call; only the error word starts at zero
-  cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), st);
+  // float32 form: the operands' largest magnitudes (their fp16 scales), beside the error word
+  unsigned* dmax = reinterpret_cast<unsigned*>(err + 1);
+  unsigned* xmax = dmax + 1;
+  const bool tc = eng == N2F_ENGINE_TC;
+  // the partial sums are overwritten in full by every call; the error and magnitude words start
+  // at zero
+  cudaError_t e = cudaMemsetAsync(err, 0, 4 * sizeof(int), st);
+  if (e == cudaSuccess && tc && !bf16)
+    e = launch_absmax(dout, (size_t)cout * H * W, 0, dmax, nullptr, st);
+  if (e == cudaSuccess && tc && !bf16) e = launch_absmax(in, (size_t)cin * H * W, 0, xmax, nullptr, st);
   if (e == cudaSuccess)
-    e = eng == N2F_ENGINE_TC
-            ? launch_wgrad_tc(bf16, dout, in, cin, cout, H, W, scratch, cap, dw, db, nullptr, err, st)
-            : launch_wgrad_simt(bf16, dout, in, cin, cout, H, W, scratch, cap, dw, db, nullptr, st);
+    e = tc ? launch_wgrad_tc(bf16, dout, in, cin, cout, H, W, dmax, xmax, scratch, cap, dw, db,
+                             nullptr, err, st)
+           : launch_wgrad_simt(bf16, dout, in, cin, cout, H, W, scratch, cap, dw, db, nullptr, st);
   int herr = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);

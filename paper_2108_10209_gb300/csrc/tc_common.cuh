@@ -1,26 +1,17 @@
-// Helpers shared by the tcgen05 kernel files: TF32 rounding, alignment and the channel-grouped
-// TMA tensor maps (cuTensorMapEncodeTiled resolved from the driver once per process).
+// Helpers shared by the tcgen05 kernel files: the float32 form's scaled fp16 split, alignment
+// and the channel-grouped TMA tensor maps (cuTensorMapEncodeTiled resolved from the driver once
+// per process).
 #pragma once
 #include <cuda.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <stdint.h>
 #include <mutex>
+
+#include "f16_split.cuh"
 
 namespace n2f {
 namespace {
-
-// Round to the nearest TF32 value (10 explicit mantissa bits; ties away from zero) by adding
-// half a unit of the 13 dropped bits before clearing them. The 3xTF32 split x = hi + lo uses
-// it for both parts, so hi and lo are exact TF32 numbers and the dropped lo*lo term and the
-// rounding of lo are unbiased, about 2^-22 of x.
-__device__ __forceinline__ float tf32_round(float x) {
-  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
-}
-
-__device__ __forceinline__ void split4(float4 v, float4& h, float4& l) {
-  h = make_float4(tf32_round(v.x), tf32_round(v.y), tf32_round(v.z), tf32_round(v.w));
-  l = make_float4(tf32_round(v.x - h.x), tf32_round(v.y - h.y), tf32_round(v.z - h.z),
-                  tf32_round(v.w - h.w));
-}
 
 __host__ __device__ constexpr uint32_t align_up(uint32_t v, uint32_t a) { return (v + a - 1) / a * a; }
 

@@ -6,7 +6,8 @@
 // channels, laid out exactly as the K-major, no-swizzle shared-memory operand expects:
 //   [tap][k-slab of 16 bytes][row (NT)][16 bytes]
 // so that 8 rows x 16 bytes form one contiguous 128-byte core matrix. Stages are ordered
-// (n-tile, channel chunk). The float32 (3xTF32) form keeps two such arrays, hi and lo.
+// (n-tile, channel chunk). Elements are 16-bit: bf16, or in the float32 form the fp16 hi and lo
+// parts of the scaled weights, kept in two such arrays.
 #pragma once
 #include <stddef.h>
 
@@ -14,15 +15,16 @@ namespace n2f {
 
 struct TcCfg {
   int NT;  // output rows (N) per CTA
-  int KC;  // input channels per pipeline stage
+  int KC;  // input channels per pipeline stage (one 16-element K step)
   int GE;  // elements per 16 bytes
 };
 
+// N = 256 in the bf16 form; 128 in the float32 form, whose stage holds two weight parts
 __host__ __device__ __forceinline__ TcCfg tc_cfg(int cin, int cout, int bf16) {
   TcCfg c;
-  c.GE = bf16 ? 8 : 4;
+  c.GE = 8;
   c.NT = bf16 ? (cout < 256 ? cout : 256) : (cout < 128 ? cout : 128);
-  c.KC = bf16 ? 16 : 8;
+  c.KC = 16;
   (void)cin;
   return c;
 }

@@ -179,19 +179,24 @@ static size_t layout(Trainer* t, char* base) {
   t->m = c.take<float>(net.count);
   t->v = c.take<float>(net.count);
   memset(&t->pa, 0, sizeof(t->pa));
+  bool any_tc = false;
   for (int l = 0; l < kLayers; ++l) {
     const size_t nw = (size_t)net.widths[l] * net.cin(l) * 9;
     t->pa.fwd[l] = c.take<float>(nw);
     t->pa.dgr[l] = l > 0 ? c.take<float>(nw) : nullptr;
     if (l > 0 && t->engine[l] == N2F_ENGINE_TC) {
-      t->pa.tcf[l] = c.take<char>(nw * es);
-      t->pa.tcd[l] = c.take<char>(nw * es);
+      any_tc = true;
+      // 16-bit elements: bf16, or the float32 form's fp16 hi and lo parts
+      t->pa.tcf[l] = c.take<uint16_t>(nw);
+      t->pa.tcd[l] = c.take<uint16_t>(nw);
       if (!t->bf16) {
-        t->pa.tcf_lo[l] = c.take<float>(nw);
-        t->pa.tcd_lo[l] = c.take<float>(nw);
+        t->pa.tcf_lo[l] = c.take<uint16_t>(nw);
+        t->pa.tcd_lo[l] = c.take<uint16_t>(nw);
       }
     }
   }
+  t->sw = !t->bf16 && any_tc ? c.take<ScaleWords>(1) : nullptr;
+  t->pa.sw = t->sw;
   // activations / deltas (training) alias the validation ping-pong buffers
   const size_t Cmax = net.cmax(), Csum = net.csum();
   const size_t train_elems = Csum * t->maxP + (t->keep_deltas ? Csum : 2 * Cmax) * t->maxP;
@@ -366,14 +371,39 @@ int trainer_start(Trainer* t, int from_u16) {
   s.decision = -1;
   t->hstate_init = s;
   CK(cudaMemcpyAsync(t->state, &t->hstate_init, sizeof(DevState), cudaMemcpyHostToDevice, st));
+  if (t->sw) CK(cudaMemsetAsync(t->sw, 0, sizeof(ScaleWords), st));
   CK(launch_adam(t->pa, t->grad, t->m, t->v, 0.f, 0.f, 0.f, 0.f, t->state, 0, st));
   return N2F_OK;
 }
 
 int trainer_repack(Trainer* t) {
   LaunchScope ls(&t->launches);
+  // the largest weights are collected afresh for the new parameters
+  if (t->sw) CK(cudaMemsetAsync(t->sw->wnew, 0, sizeof(t->sw->wnew), t->st));
   CK(launch_adam(t->pa, t->grad, t->m, t->v, 0.f, 0.f, 0.f, 0.f, t->state, 0, t->st));
   return N2F_OK;
+}
+
+// Magnitude words of the float32 form (all null in the bf16 form): the forward of layer l reads
+// act[l - 1] and the weights, raises act[l]; the dgrad of layer l reads delta[l] and the
+// weights, raises delta[l - 1].
+static ConvScales fwd_scales(const Trainer* t, int l) {
+  ConvScales s;
+  if (t->sw) {
+    s.in = &t->sw->act[l - 1];
+    s.w = &t->sw->w[l];
+    s.out = &t->sw->act[l];
+  }
+  return s;
+}
+static ConvScales dgrad_scales(const Trainer* t, int l) {
+  ConvScales s;
+  if (t->sw) {
+    s.in = &t->sw->delta[l];
+    s.w = &t->sw->w[l];
+    s.out = &t->sw->delta[l - 1];
+  }
+  return s;
 }
 
 static int conv_layer(Trainer* t, int l, const void* in, void* out, int H, int W,
@@ -384,14 +414,15 @@ static int conv_layer(Trainer* t, int l, const void* in, void* out, int H, int W
   Timed tm(t, l == 0 ? N2F_K_FIRST : N2F_K_CONV_FWD, 2.0 * P * 9 * cin * cout,
            l == 0 ? P * 4.0 + P * cout * es : P * (cin + cout) * es, val);
   if (l == 0) {
-    CK(launch_conv1_fwd((const float*)in, cin, H, W, t->pa.fwd[0], b, cout, t->bf16, out, skip,
-                        t->st));
+    CK(launch_conv1_fwd((const float*)in, cin, H, W, t->pa.fwd[0], b, cout, t->bf16, out,
+                        t->sw ? &t->sw->act[0] : nullptr, skip, t->st));
   } else if (t->engine[l] == N2F_ENGINE_TC) {
     CK(launch_conv_tc(0, t->bf16, in, cin, cout, H, W, t->pa.tcf[l], t->pa.tcf_lo[l], b, nullptr,
-                      out, skip, &t->state->kerr, t->st));
+                      out, fwd_scales(t, l), skip, &t->state->kerr, t->st));
   } else {
     CK(launch_conv_simt(0, t->bf16, in, cin, cout, H, W, t->pa.fwd[l], b, nullptr, out, skip,
                         t->st));
+    if (t->sw) CK(launch_absmax(out, (size_t)cout * H * W, 0, &t->sw->act[l], skip, t->st));
   }
   return N2F_OK;
 }
@@ -429,7 +460,8 @@ static int step_head(Trainer* t, int pair) {
     Timed tm(t, N2F_K_HEAD, 2.0 * npx * C8, (double)npx * C8 * 2 * es + npx * 8.0, 0);
     CK(launch_head_train(t->act[kLayers - 1], C8, npx, t->theta + net.w_off[kLayers],
                          t->theta + net.b_off[kLayers], tgt, t->prm.loss, t->bf16, t->dz,
-                         delta_of(t, kLayers - 1), t->lpart, t->hpart, &nblk, skip, t->st));
+                         delta_of(t, kLayers - 1), t->sw ? &t->sw->delta[kLayers - 1] : nullptr,
+                         t->lpart, t->hpart, &nblk, skip, t->st));
   }
   CK(launch_step_finish(t->hpart, t->lpart, nblk, C8, npx, t->grad + net.w_off[kLayers],
                         t->grad + net.b_off[kLayers], t->state, t->prm.beta1, t->prm.beta2,
@@ -454,8 +486,9 @@ static int step_wgrad(Trainer* t, int pair, int l) {
   const double es = t->bf16 ? 2.0 : 4.0;
   Timed tm(t, N2F_K_CONV_WGRAD, 2.0 * npx * 9 * cin * cout, (double)npx * (cin + cout) * es, 0);
   if (t->wg_engine[l] == N2F_ENGINE_TC)
-    CK(launch_wgrad_tc(t->bf16, dcur, t->act[l - 1], cin, cout, h, w, t->wpart, t->wpart_cap, gw,
-                       gb, skip, &t->state->kerr, t->st));
+    CK(launch_wgrad_tc(t->bf16, dcur, t->act[l - 1], cin, cout, h, w,
+                       t->sw ? &t->sw->delta[l] : nullptr, t->sw ? &t->sw->act[l - 1] : nullptr,
+                       t->wpart, t->wpart_cap, gw, gb, skip, &t->state->kerr, t->st));
   else
     CK(launch_wgrad_simt(t->bf16, dcur, t->act[l - 1], cin, cout, h, w, t->wpart, t->wpart_cap,
                          gw, gb, skip, t->st));
@@ -471,11 +504,15 @@ static int step_dgrad(Trainer* t, int pair, int l) {
            0);
   if (t->engine[l] == N2F_ENGINE_TC)
     CK(launch_conv_tc(1, t->bf16, delta_of(t, l), cout, cin, h, w, t->pa.tcd[l], t->pa.tcd_lo[l],
-                      nullptr, t->act[l - 1], delta_of(t, l - 1), step_skip(t), &t->state->kerr,
-                      t->st));
-  else
+                      nullptr, t->act[l - 1], delta_of(t, l - 1), dgrad_scales(t, l), step_skip(t),
+                      &t->state->kerr, t->st));
+  else {
     CK(launch_conv_simt(1, t->bf16, delta_of(t, l), cout, cin, h, w, t->pa.dgr[l], nullptr,
                         t->act[l - 1], delta_of(t, l - 1), step_skip(t), t->st));
+    if (t->sw)
+      CK(launch_absmax(delta_of(t, l - 1), (size_t)cin * h * w, 0, &t->sw->delta[l - 1],
+                       step_skip(t), t->st));
+  }
   return N2F_OK;
 }
 
@@ -582,6 +619,7 @@ int group_init(TrainerGroup* g, const Allocator& al, cudaStream_t st) {
             q.w_lo = t->pa.tcf_lo[l];
             q.bias = t->theta + t->net.b_off[l];
             q.mask = nullptr;
+            q.sc = fwd_scales(t, l);
           } else {
             q.in = delta_of(t, l);
             q.out = delta_of(t, l - 1);
@@ -589,6 +627,7 @@ int group_init(TrainerGroup* g, const Allocator& al, cudaStream_t st) {
             q.w_lo = t->pa.tcd_lo[l];
             q.bias = nullptr;
             q.mask = t->act[l - 1];
+            q.sc = dgrad_scales(t, l);
           }
         }
         long nt = 0;
@@ -774,11 +813,11 @@ int trainer_autotune(Trainer* t) {
       const void* in = k == 2 ? t->vb[(l - 1) & 1] : t->act[l - 1];
       void* out = k == 2 ? t->vb[l & 1] : t->act[l];
       CK(conv_tc_autotune(0, t->bf16, in, cin, cout, h, w, t->pa.tcf[l], t->pa.tcf_lo[l], b,
-                          nullptr, out, &t->state->kerr, t->st));
+                          nullptr, out, fwd_scales(t, l), &t->state->kerr, t->st));
       if (k == 2) continue;
       CK(conv_tc_autotune(1, t->bf16, delta_of(t, l), cout, cin, h, w, t->pa.tcd[l],
                           t->pa.tcd_lo[l], nullptr, t->act[l - 1], delta_of(t, l - 1),
-                          &t->state->kerr, t->st));
+                          dgrad_scales(t, l), &t->state->kerr, t->st));
     }
   }
   return N2F_OK;

@@ -57,14 +57,16 @@ TapGroups tap_groups(int cin) {
 }
 
 // The bias gradient db[o] = sum_px delta[px][o] comes out of the same GEMM: in the CTAs of tap
-// group 0 the B operand of the group's last tap carries two more 8-channel groups, constant bf16
-// ones (zeros in the float32 form's second and third parts), so that tap's MMAs (N = C + 16)
-// also accumulate sum_px delta into 16 more TMEM columns, at no extra instruction.
+// group 0 the B operand of the group's last tap carries two more 8-channel groups, constant
+// ones (bf16, or fp16 in the float32 form's hi part and zeros in its lo part), so that tap's
+// MMAs (N = C + 16) also accumulate sum_px delta into 16 more TMEM columns, at no extra
+// instruction.
 __device__ __forceinline__ void fill_ext(uint8_t* ext, uint32_t bytes, uint32_t value) {
   for (uint32_t i = threadIdx.x; i < bytes / 4; i += blockDim.x)
     reinterpret_cast<uint32_t*>(ext)[i] = value;
 }
 constexpr uint32_t kBf16PairOne = 0x3F803F80u;  // two bf16 1.0
+constexpr uint32_t kF16PairOne = 0x3C003C00u;   // two fp16 1.0
 
 struct WgBf16Params {
   float* part;  // [S][9][C_in][C_out]
@@ -73,6 +75,8 @@ struct WgBf16Params {
   int pu;      // pixels per TMA unit of both maps
   float* bpart;  // [S][C_out] bias-gradient partials, written by the tap group 0 CTAs
   TapGroups tg;
+  const unsigned* dmax;  // float32 form: largest |delta| and |x| (operand scales)
+  const unsigned* xmax;
   const int* skip;
   int* err;
 };
@@ -266,19 +270,18 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc_bf16(const __grid_constant_
   }
 }
 
-// ---- float32 weight gradient as three bf16 parts per operand --------------------------------
-// Each fp32 value x is split into x = b0 + b1 + b2 (bf16, each the rounded remainder of the
-// previous) and D = sum of the six products b_i c_j with i + j <= 2; the three dropped products
-// are below 2^-25 of the true one. bf16 operands can be read MN-major, so the tap-grouped halo
-// scheme of the bf16 kernel applies unchanged: TMA brings the fp32 tiles, eight split warps
-// write the three bf16 images of each, one MMA warp issues six MMAs per tap and K step.
-constexpr int kW3KP = 16;  // pixels per stage (one bf16 K step)
+// ---- float32 weight gradient as two scaled fp16 parts per operand ---------------------------
+// Float32 form: delta and x are split into scaled fp16 hi and lo parts (f16_split.cuh) and
+// D = hi*hi + hi*lo + lo*hi. fp16 operands can be read MN-major, so the tap-grouped halo scheme
+// of the bf16 kernel applies unchanged: TMA brings the fp32 tiles, eight split warps write the
+// two fp16 images of each, one MMA warp issues three MMAs per tap and K step.
+constexpr int kW3KP = 16;  // pixels per stage (one 16-element K step)
 constexpr int kW3MaxStages = 4;
 constexpr int kW3SplitWarps = 8;
 constexpr int kW3Threads = 64 + 32 * kW3SplitWarps;
 
 struct W3Layout {
-  uint32_t rawA, rawB, a[3], b[3], stage;
+  uint32_t rawA, rawB, a[2], b[2], stage;
 };
 
 // raw x tile pitch: the 16 chunk pixels plus one TMA unit of pu pixels on each side
@@ -299,39 +302,20 @@ __host__ __device__ inline W3Layout w3_layout(int cin, int R, int pu, bool exp =
   uint32_t o = 0;
   L.rawA = o; o += align_up(ra, 1024);
   L.rawB = o; o += align_up(rb, 1024);
-  for (int k = 0; k < 3; ++k) { L.a[k] = o; o += align_up(pa, 1024); }
-  for (int k = 0; k < 3; ++k) { L.b[k] = o; o += align_up(pb, 1024); }
+  for (int k = 0; k < 2; ++k) { L.a[k] = o; o += align_up(pa, 1024); }
+  for (int k = 0; k < 2; ++k) { L.b[k] = o; o += align_up(pb, 1024); }
   L.stage = o;
   return L;
 }
 
-// Two fp32 values -> their three bf16 parts, packed in pairs (value a in the low half). The
-// remainders v - b0 and (v - b0) - b1 are exact in fp32.
-__device__ __forceinline__ void split3_pair(float a, float b, uint32_t& w0, uint32_t& w1,
-                                            uint32_t& w2) {
-  const __nv_bfloat162 p0 = __floats2bfloat162_rn(a, b);
-  const float2 f0 = __bfloat1622float2(p0);
-  const float ra = a - f0.x, rb = b - f0.y;
-  const __nv_bfloat162 p1 = __floats2bfloat162_rn(ra, rb);
-  const float2 f1 = __bfloat1622float2(p1);
-  const __nv_bfloat162 p2 = __floats2bfloat162_rn(ra - f1.x, rb - f1.y);
-  w0 = *reinterpret_cast<const uint32_t*>(&p0);
-  w1 = *reinterpret_cast<const uint32_t*>(&p1);
-  w2 = *reinterpret_cast<const uint32_t*>(&p2);
-}
-
-// One 16-byte group of 8 channels: the fp32 groups lo (channels 0-3) and hi (4-7) -> the three
-// bf16 images at element index u.
-__device__ __forceinline__ void split3_group(const float4 lo, const float4 hi, uint4* b0, uint4* b1,
-                                             uint4* b2, int u) {
-  uint4 o0, o1, o2;
-  split3_pair(lo.x, lo.y, o0.x, o1.x, o2.x);
-  split3_pair(lo.z, lo.w, o0.y, o1.y, o2.y);
-  split3_pair(hi.x, hi.y, o0.z, o1.z, o2.z);
-  split3_pair(hi.z, hi.w, o0.w, o1.w, o2.w);
-  b0[u] = o0;
-  b1[u] = o1;
-  b2[u] = o2;
+// One 16-byte group of 8 channels: the fp32 groups lo (channels 0-3) and hi (4-7) -> the hi and
+// lo fp16 images at element index u.
+__device__ __forceinline__ void split2_group(const float4 c03, const float4 c47, float s,
+                                             uint4* p0, uint4* p1, int u) {
+  uint4 h, l;
+  split_f16_group(c03, c47, s, h, l);
+  p0[u] = h;
+  p1[u] = l;
 }
 
 // Splits one stage. Delta tile: raw [32 g4][16 px], parts [16 g8][16 px]. x tile: raw
@@ -339,8 +323,9 @@ __device__ __forceinline__ void split3_group(const float4 lo, const float4 hi, u
 // quarter-warp takes 8 consecutive pixels of one row, so its eight 16-byte reads fall in
 // distinct bank groups; the 2 halo pixels of each row follow in a short second pass.
 template <int R, int EXP>
-__device__ __forceinline__ void split3_stage(const uint8_t* st, uint8_t* stw, const W3Layout& L,
-                                             int g8n, int pu, int et, int nt, int t0, int r0) {
+__device__ __forceinline__ void split2_stage(const uint8_t* st, uint8_t* stw, const W3Layout& L,
+                                             int g8n, int pu, int et, int nt, int t0, int r0,
+                                             float sd, float sx) {
   constexpr int kThr = 32 * kW3SplitWarps;
   constexpr int PP = kW3KP + 2;  // part pitch
   const int PR = w3_raw_pitch(pu);
@@ -348,15 +333,14 @@ __device__ __forceinline__ void split3_stage(const uint8_t* st, uint8_t* stw, co
     const float4* raw = reinterpret_cast<const float4*>(st + L.rawA);
     for (int u = et; u < 16 * kW3KP; u += kThr) {
       const int g8 = u / kW3KP, px = u % kW3KP;
-      split3_group(raw[(2 * g8) * kW3KP + px], raw[(2 * g8 + 1) * kW3KP + px],
+      split2_group(raw[(2 * g8) * kW3KP + px], raw[(2 * g8 + 1) * kW3KP + px], sd,
                    reinterpret_cast<uint4*>(stw + L.a[0]), reinterpret_cast<uint4*>(stw + L.a[1]),
-                   reinterpret_cast<uint4*>(stw + L.a[2]), u);
+                   u);
     }
   }
   const float4* raw = reinterpret_cast<const float4*>(st + L.rawB);
   uint4* b0 = reinterpret_cast<uint4*>(stw + L.b[0]);
   uint4* b1 = reinterpret_cast<uint4*>(stw + L.b[1]);
-  uint4* b2 = reinterpret_cast<uint4*>(stw + L.b[2]);
   if constexpr (EXP) {
     // group gq = j * g8n + g8 holds tap j's view of channel group g8: pixel px of the chunk at
     // raw row (tap / 3 - r0), raw column pu - 1 + px + tap % 3
@@ -364,8 +348,8 @@ __device__ __forceinline__ void split3_stage(const uint8_t* st, uint8_t* stw, co
       const int gq = u / kW3KP, px = u % kW3KP;
       const int j = gq / g8n, g8 = gq - j * g8n, tap = t0 + j;
       const int r = tap / 3 - r0, col = pu - 1 + px + tap % 3;
-      split3_group(raw[((2 * g8) * R + r) * PR + col], raw[((2 * g8 + 1) * R + r) * PR + col], b0,
-                   b1, b2, u);
+      split2_group(raw[((2 * g8) * R + r) * PR + col], raw[((2 * g8 + 1) * R + r) * PR + col], sx,
+                   b0, b1, u);
     }
     return;
   }
@@ -373,14 +357,14 @@ __device__ __forceinline__ void split3_stage(const uint8_t* st, uint8_t* stw, co
   for (int u = et; u < nmain; u += kThr) {
     const int q = u / kW3KP, i = 1 + u % kW3KP;  // q = g8 * R + r, part column i
     const int g8 = q / R, r = q - g8 * R, px = pu - 1 + i;
-    split3_group(raw[((2 * g8) * R + r) * PR + px], raw[((2 * g8 + 1) * R + r) * PR + px], b0, b1,
-                 b2, q * PP + i);
+    split2_group(raw[((2 * g8) * R + r) * PR + px], raw[((2 * g8 + 1) * R + r) * PR + px], sx, b0,
+                 b1, q * PP + i);
   }
   for (int u = et; u < g8n * R * 2; u += kThr) {
     const int q = u >> 1, i = (u & 1) ? PP - 1 : 0;
     const int g8 = q / R, r = q - g8 * R, px = pu - 1 + i;
-    split3_group(raw[((2 * g8) * R + r) * PR + px], raw[((2 * g8 + 1) * R + r) * PR + px], b0, b1,
-                 b2, q * PP + i);
+    split2_group(raw[((2 * g8) * R + r) * PR + px], raw[((2 * g8 + 1) * R + r) * PR + px], sx, b0,
+                 b1, q * PP + i);
   }
 }
 
@@ -418,12 +402,12 @@ __global__ void __launch_bounds__(kW3Threads, 2) k_wgrad_tc_f32(const __grid_con
     mbar_fence_init();
   }
   if (warp == 1) tmem_alloc(&tslot, ncols);
-  if (bias) {  // part 0: ones, parts 1 and 2: zeros, so the bias columns sum a0 + a1 + a2
+  if (bias) {  // hi part: ones, lo part: zeros, so the bias columns sum a_hi + a_lo
     const uint32_t eo = EXP ? (uint32_t)nt * cn / 8 * kW3KP * 16 : (uint32_t)cn * R * (kW3KP + 2) * 2;
     const uint32_t eb = EXP ? 2u * kW3KP * 16 : 2u * R * (kW3KP + 2) * 16;
     for (int s = 0; s < ns; ++s)
-      for (int q = 0; q < 3; ++q)
-        fill_ext(smem + s * L.stage + L.b[q] + eo, eb, q == 0 ? kBf16PairOne : 0u);
+      for (int q = 0; q < 2; ++q)
+        fill_ext(smem + s * L.stage + L.b[q] + eo, eb, q == 0 ? kF16PairOne : 0u);
     fence_proxy_async();
   }
   tc_fence_before();
@@ -451,7 +435,7 @@ __global__ void __launch_bounds__(kW3Threads, 2) k_wgrad_tc_f32(const __grid_con
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t idn = idesc(1, 128, cn, 1, 1), idx = idesc(1, 128, cn + 16, 1, 1);
+      const uint32_t idn = idesc(0, 128, cn, 1, 1), idx = idesc(0, 128, cn + 16, 1, 1);
       const uint32_t a_sbo = kW3KP * 16;                     // next 8-channel group of delta
       const uint32_t b_sbo = (uint32_t)R * (kW3KP + 2) * 16;  // next 8-channel group of x
       for (int i = 0; i < nk; ++i) {
@@ -459,42 +443,36 @@ __global__ void __launch_bounds__(kW3Threads, 2) k_wgrad_tc_f32(const __grid_con
         if (!mbar_wait(&split[s], (i / ns) & 1, abort, p.err)) break;
         tc_fence_after();
         const uint32_t st = smem_u32(smem + s * L.stage);
-        uint64_t da[3];
+        uint64_t da[2];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) da[k] = sdesc(st + L.a[k], 128, a_sbo);
+        for (int k = 0; k < 2; ++k) da[k] = sdesc(st + L.a[k], 128, a_sbo);
         if constexpr (EXP) {
           // the taps side by side along N, in chunks of at most 256 columns (multiples of 16)
           const int ntot = nt * cn, nch = (ntot + 255) / 256;
           const int csz = (ntot / nch + 15) / 16 * 16;
           for (int c0 = 0; c0 < ntot; c0 += csz) {
             const int n = min(csz, ntot - c0) + ((bias && c0 + csz >= ntot) ? 16 : 0);
-            const uint32_t id = idesc(1, 128, n, 1, 1);
-            uint64_t db[3];
+            const uint32_t id = idesc(0, 128, n, 1, 1);
+            uint64_t db[2];
 #pragma unroll
-            for (int q = 0; q < 3; ++q) db[q] = sdesc(st + L.b[q] + (uint32_t)(c0 / 8) * kW3KP * 16u, 128, kW3KP * 16);
+            for (int q = 0; q < 2; ++q) db[q] = sdesc(st + L.b[q] + (uint32_t)(c0 / 8) * kW3KP * 16u, 128, kW3KP * 16);
             const uint32_t d = tbase + (uint32_t)c0;
             mma_f16(d, da[0], db[0], id, i > 0 ? 1u : 0u);
             mma_f16(d, da[0], db[1], id, 1u);
             mma_f16(d, da[1], db[0], id, 1u);
-            mma_f16(d, da[0], db[2], id, 1u);
-            mma_f16(d, da[1], db[1], id, 1u);
-            mma_f16(d, da[2], db[0], id, 1u);
           }
         } else {
         for (int j = 0; j < nt; ++j) {
             const int tap = t0 + j;
             const uint32_t boff = (uint32_t)(((tap / 3) - r0) * (kW3KP + 2) + (tap % 3)) * 16u;
-            uint64_t db[3];
+            uint64_t db[2];
 #pragma unroll
-            for (int k = 0; k < 3; ++k) db[k] = sdesc(st + L.b[k] + boff, 128, b_sbo);
+            for (int k = 0; k < 2; ++k) db[k] = sdesc(st + L.b[k] + boff, 128, b_sbo);
             const uint32_t d = tbase + (uint32_t)(j * cn);
             const uint32_t id = (bias && j == nt - 1) ? idx : idn;
             mma_f16(d, da[0], db[0], id, i > 0 ? 1u : 0u);
             mma_f16(d, da[0], db[1], id, 1u);
             mma_f16(d, da[1], db[0], id, 1u);
-            mma_f16(d, da[0], db[2], id, 1u);
-            mma_f16(d, da[1], db[1], id, 1u);
-            mma_f16(d, da[2], db[0], id, 1u);
           }
         }
         mma_commit(&empty[s]);
@@ -503,11 +481,12 @@ __global__ void __launch_bounds__(kW3Threads, 2) k_wgrad_tc_f32(const __grid_con
     }
   } else {
     const int et = threadIdx.x - 64;
+    const float sd = f16_scale(p.dmax), sx = f16_scale(p.xmax);
     for (int i = 0; i < nk; ++i) {
       const int s = i % ns;
       if (!mbar_wait(&full[s], (i / ns) & 1, abort, p.err)) break;
       uint8_t* st = smem + s * L.stage;
-      split3_stage<R, EXP>(st, st, L, cn / 8, pu, et, nt, t0, r0);
+      split2_stage<R, EXP>(st, st, L, cn / 8, pu, et, nt, t0, r0, sd, sx);
       fence_proxy_async();
       __syncwarp();
       if (lane == 0) mbar_arrive(&split[s]);
@@ -519,6 +498,8 @@ __global__ void __launch_bounds__(kW3Threads, 2) k_wgrad_tc_f32(const __grid_con
     const int wq = warp & 3, half = (warp - 2) >> 2;
     const int o = o0 + wq * 32 + lane;
     const bool live = o < p.cout && !*abort;
+    // undo the operand scales (exact powers of two, applied one at a time)
+    const float ud = f16_unscale(p.dmax), ux = f16_unscale(p.xmax);
     for (int j = 0; j < nt; ++j) {
       const int tap = t0 + j;
       // part[s][tap][c][o]: the warp's 32 lanes are 32 consecutive o, one 128-byte row per c
@@ -529,14 +510,15 @@ __global__ void __launch_bounds__(kW3Threads, 2) k_wgrad_tc_f32(const __grid_con
         tmem_ld_wait();
         if (!live) continue;
 #pragma unroll
-        for (int q = 0; q < 16; ++q) dst[(size_t)(c0 + q) * p.cout] = nk ? __uint_as_float(r[q]) : 0.f;
+        for (int q = 0; q < 16; ++q)
+          dst[(size_t)(c0 + q) * p.cout] = nk ? __uint_as_float(r[q]) * ud * ux : 0.f;
       }
     }
     if (bias && half == 0) {
       uint32_t r[16];
       tmem_ld16(tbase + ((uint32_t)(wq * 32) << 16) + (uint32_t)(nt * cn), r);
       tmem_ld_wait();
-      if (live) p.bpart[(size_t)s_idx * p.cout + o] = nk ? __uint_as_float(r[0]) : 0.f;
+      if (live) p.bpart[(size_t)s_idx * p.cout + o] = nk ? __uint_as_float(r[0]) * ud : 0.f;
     }
   }
   tc_fence_before();
@@ -650,11 +632,13 @@ bool tc_wgrad_supported(int cin, int cout, int bf16) {
   return tc_supported(cin, cout);
 }
 
-// bf16 = 1: bf16 maps, k_wgrad_tc_bf16; bf16 = 0: float32 maps, k_wgrad_tc_f32 (three bf16 parts)
+// bf16 = 1: bf16 maps, k_wgrad_tc_bf16; bf16 = 0: float32 maps, k_wgrad_tc_f32 (two fp16 parts)
 static cudaError_t launch_wgrad_grouped(int bf16, const void* dout, const void* in, int cin,
-                                        int cout, int H, int W, float* part, size_t part_cap,
+                                        int cout, int H, int W, const unsigned* dmax,
+                                        const unsigned* xmax, float* part, size_t part_cap,
                                         float* gw, float* gb, const int* skip, int* err,
                                         cudaStream_t st) {
+  if (!bf16 && (!dmax || !xmax)) return cudaErrorInvalidValue;
   const TapGroups tg = tap_groups(cin);
   const int KP = bf16 ? kWbKP : kW3KP, GE = bf16 ? 8 : 4;
   // pixels per TMA unit: 128-byte box rows for bf16 (the halo grows by 14 pixels of 66),
@@ -676,6 +660,8 @@ static cudaError_t launch_wgrad_grouped(int bf16, const void* dout, const void* 
   p.total_chunks = p.chunks_x * H;
   p.tg = tg;
   p.pu = pu;
+  p.dmax = dmax;
+  p.xmax = xmax;
   const size_t per_split_elems = (size_t)9 * cout * cin;
   int maxcols = 0;  // group 0 also holds the 16 bias columns
   for (int g = 0; g < tg.n; ++g) {
@@ -734,12 +720,13 @@ static cudaError_t launch_wgrad_grouped(int bf16, const void* dout, const void* 
 }
 
 cudaError_t launch_wgrad_tc(int bf16, const void* dout, const void* in, int cin, int cout, int H,
-                            int W, float* part, size_t part_cap, float* gw, float* gb,
-                            const int* skip, int* err, cudaStream_t st) {
+                            int W, const unsigned* dmax, const unsigned* xmax, float* part,
+                            size_t part_cap, float* gw, float* gb, const int* skip, int* err,
+                            cudaStream_t st) {
   if (!tc_wgrad_supported(cin, cout, bf16)) return cudaErrorNotSupported;
   if (const cudaError_t pe = tc_prepare()) return pe;
-  return launch_wgrad_grouped(bf16, dout, in, cin, cout, H, W, part, part_cap, gw, gb, skip, err,
-                              st);
+  return launch_wgrad_grouped(bf16, dout, in, cin, cout, H, W, dmax, xmax, part, part_cap, gw, gb,
+                              skip, err, st);
 }
 
 }  // namespace n2f
