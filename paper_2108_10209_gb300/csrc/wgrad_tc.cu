@@ -277,8 +277,14 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc_bf16(const __grid_constant_
 // two fp16 images of each, one MMA warp issues three MMAs per tap and K step.
 constexpr int kW3KP = 16;  // pixels per stage (one 16-element K step)
 constexpr int kW3MaxStages = 4;
-constexpr int kW3SplitWarps = 8;
-constexpr int kW3Threads = 64 + 32 * kW3SplitWarps;
+// split warps (then epilogue warps): 16 for the one-row layers, whose CTA holds its SM alone
+// (TMEM), 8 for the tap-expanded small layers, which run two CTAs per SM
+template <int EXP>
+struct W3Warps {
+  static constexpr int kSplit = EXP ? 8 : 16;
+  static constexpr int kThreads = 64 + 32 * kSplit;
+  static constexpr int kPerSm = EXP ? 2 : 1;
+};
 
 struct W3Layout {
   uint32_t rawA, rawB, a[2], b[2], stage;
@@ -326,7 +332,7 @@ template <int R, int EXP>
 __device__ __forceinline__ void split2_stage(const uint8_t* st, uint8_t* stw, const W3Layout& L,
                                              int g8n, int pu, int et, int nt, int t0, int r0,
                                              float sd, float sx) {
-  constexpr int kThr = 32 * kW3SplitWarps;
+  constexpr int kThr = 32 * W3Warps<EXP>::kSplit;
   constexpr int PP = kW3KP + 2;  // part pitch
   const int PR = w3_raw_pitch(pu);
   {
@@ -369,7 +375,7 @@ __device__ __forceinline__ void split2_stage(const uint8_t* st, uint8_t* stw, co
 }
 
 template <int R, int EXP>
-__global__ void __launch_bounds__(kW3Threads, 2) k_wgrad_tc_f32(const __grid_constant__ CUtensorMap tmD,
+__global__ void __launch_bounds__(W3Warps<EXP>::kThreads, W3Warps<EXP>::kPerSm) k_wgrad_tc_f32(const __grid_constant__ CUtensorMap tmD,
                                                                const __grid_constant__ CUtensorMap tmX,
                                                                WgBf16Params p) {
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -395,7 +401,7 @@ __global__ void __launch_bounds__(kW3Threads, 2) k_wgrad_tc_f32(const __grid_con
     for (int s = 0; s < ns; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
-      mbar_init(&split[s], kW3SplitWarps);
+      mbar_init(&split[s], W3Warps<EXP>::kSplit);
     }
     mbar_init(&accf, 1);
     abort_flag = 0;
@@ -493,8 +499,9 @@ __global__ void __launch_bounds__(kW3Threads, 2) k_wgrad_tc_f32(const __grid_con
     }
     if (!mbar_wait(&accf, 0, abort, p.err)) mbar_drain(&accf, 0);
     tc_fence_after();
-    // warps 2..9: TMEM lane quarter warp % 4, column half (warp - 2) / 4 (16-column blocks
-    // alternate between the two halves)
+    // warps 2..: TMEM lane quarter warp % 4, column set (warp - 2) / 4 (16-column blocks are
+    // dealt round the sets)
+    constexpr int kSets = W3Warps<EXP>::kSplit / 4;
     const int wq = warp & 3, half = (warp - 2) >> 2;
     const int o = o0 + wq * 32 + lane;
     const bool live = o < p.cout && !*abort;
@@ -504,7 +511,7 @@ __global__ void __launch_bounds__(kW3Threads, 2) k_wgrad_tc_f32(const __grid_con
       const int tap = t0 + j;
       // part[s][tap][c][o]: the warp's 32 lanes are 32 consecutive o, one 128-byte row per c
       float* dst = p.part + ((size_t)s_idx * 9 + tap) * p.cin * p.cout + (size_t)c0g * p.cout + o;
-      for (int c0 = 16 * half; c0 < cn; c0 += 32) {
+      for (int c0 = 16 * half; c0 < cn; c0 += 16 * kSets) {
         uint32_t r[16];
         tmem_ld16(tbase + ((uint32_t)(wq * 32) << 16) + (uint32_t)(j * cn + c0), r);
         tmem_ld_wait();
@@ -705,11 +712,11 @@ static cudaError_t launch_wgrad_grouped(int bf16, const void* dout, const void* 
   else if (bf16)
     k_wgrad_tc_bf16<0><<<grid, 192, smem, st>>>(md, mx, p);
   else if (tg.R == 3)
-    k_wgrad_tc_f32<3, 1><<<grid, kW3Threads, smem, st>>>(md, mx, p);
+    k_wgrad_tc_f32<3, 1><<<grid, W3Warps<1>::kThreads, smem, st>>>(md, mx, p);
   else if (exp)
-    k_wgrad_tc_f32<1, 1><<<grid, kW3Threads, smem, st>>>(md, mx, p);
+    k_wgrad_tc_f32<1, 1><<<grid, W3Warps<1>::kThreads, smem, st>>>(md, mx, p);
   else
-    k_wgrad_tc_f32<1, 0><<<grid, kW3Threads, smem, st>>>(md, mx, p);
+    k_wgrad_tc_f32<1, 0><<<grid, W3Warps<0>::kThreads, smem, st>>>(md, mx, p);
   count_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_reduce_wgrad_tc<<<(unsigned)(((cout + kRwO - 1) / kRwO) * cin), 256, 0, st>>>(part, S, cin,
