@@ -182,7 +182,8 @@ def test_single_step_activations_and_gradients(n2f, widths, engine):
     units. The per-kernel test above holds every kernel to 1e-4 on identical inputs.
 
     Engines: the CUDA-core kernels compute in float32 and hold every tensor to 1e-4. The
-    tensor-core float32 form multiplies in 3xTF32 (about 2^-22 per product instead of 2^-24);
+    tensor-core float32 form multiplies two scaled fp16 parts per operand (about 2^-22 per
+    product instead of 2^-24);
     activations and deltas stay within 1e-4, but a weight gradient is a sum over every pixel
     with strong sign cancellation, which magnifies that difference relative to its largest
     element, so weight gradients on that engine are held to 1e-3."""
