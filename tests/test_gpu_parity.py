@@ -108,6 +108,51 @@ def test_conv_kernels_match_oracle(n2f, torch_mod, precision, engine, cin, cout,
     assert rel_err(db, db_ref) < (2e-5 if precision == 0 else 2e-3)
 
 
+# (activation scale, weight scale, delta scale, channels scaled down by 1e-6 in x): the float32
+# form's tensor-core GEMMs scale every operand tensor by a power of two from its largest
+# magnitude before splitting it into fp16 parts, so results must not depend on where the values
+# sit in the float32 range, on a tensor that is all zeros, or on values far below the tensor's
+# largest one
+SCALE_CASES = [(1e-30, 1e10, 1e-5, 0), (1e20, 1e-25, 1e10, 0), (1.0, 1.0, 1.0, 16),
+               (3e-12, 7e8, 2e-30, 8), (0.0, 1.0, 0.0, 0)]
+
+
+@pytest.mark.parametrize("sx,sw,sg,nsmall", SCALE_CASES)
+def test_float32_form_operand_scales(n2f, torch_mod, sx, sw, sg, nsmall):
+    T = torch_mod
+    cin, cout, H, W = 64, 128, 20, 136
+    x, w, b, g = _conv_inputs(cin, cout, H, W, 99)
+    x = x * sx
+    x[:nsmall] *= 1e-6
+    w, g = w * sw, g * sg
+    b = b * (sx * sw)
+    x, g = x.astype(np.float32).astype(np.float64), g.astype(np.float32).astype(np.float64)
+    wq = w.astype(np.float32).astype(np.float64)
+    bq = b.astype(np.float32).astype(np.float64)
+    dev = lambda a: T.tensor(np.ascontiguousarray(a, np.float32), device="cuda")
+    xc, gc = n2f.pack_cg(dev(x), 0), n2f.pack_cg(dev(g), 0)
+    wd, bd = dev(w), dev(b)
+    y = n2f.unpack_cg(n2f.conv3x3(0, xc, cin, cout, H, W, wd, bd, precision=0, engine=2),
+                      cout, H, W, 0).cpu().numpy()
+    d = n2f.unpack_cg(n2f.conv3x3(1, gc, cin, cout, H, W, wd, mask_cg=xc, precision=0,
+                                  engine=2), cin, H, W, 0).cpu().numpy()
+    dw, db = n2f.conv3x3_wgrad(gc, xc, cin, cout, H, W, precision=0, engine=2)
+    dw, db = dw.cpu().numpy(), db.cpu().numpy()
+    y_ref = oracle.conv3x3_fwd(x, wq, bq, relu=True)
+    d_ref = oracle.conv3x3_dgrad(g, wq) * (x > 0)
+    dw_ref, db_ref = oracle.conv3x3_wgrad(g, x)
+    for got, ref in ((y, y_ref), (d, d_ref), (dw, dw_ref), (db, db_ref)):
+        assert np.all(np.isfinite(got))
+        if not np.any(ref):
+            assert not np.any(got)
+        else:
+            assert rel_err(got, ref) < 2e-5
+    # the small channels' own weight gradients, relative to their own size, where that size is a
+    # normal float32 number
+    if nsmall and np.max(np.abs(dw_ref[:, :nsmall])) > 1e-30:
+        assert rel_err(dw[:, :nsmall], dw_ref[:, :nsmall]) < 1e-3
+
+
 # ------------------------------------------------------------------- one training step -----
 
 def _small_case():
