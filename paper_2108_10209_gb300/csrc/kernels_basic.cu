@@ -793,9 +793,27 @@ cudaError_t launch_head_train(const void* a8, int C, int npx, const float* w9, c
 
 // Loss sum (fixed tree over the per-block partials) and Adam's step counter and bias
 // corrections; the head-gradient partials are summed by the column reducer.
-__global__ void k_step_finish(const double* __restrict__ lpart, int nblk, int npx, DevState* state,
+// Blocks 0..C: head-gradient column c = sum over the R = nblk partial rows (each thread a fixed
+// strided subset in order, then a fixed tree). Block C + 1: the loss (fixed tree over the
+// per-block loss partials) and Adam's step counter and bias corrections.
+__global__ void k_step_finish(const float* __restrict__ hpart, const double* __restrict__ lpart,
+                              int nblk, int C, int npx, float* __restrict__ gw9, DevState* state,
                               float b1, float b2) {
   if (state->stopped) return;
+  if ((int)blockIdx.x <= C) {
+    __shared__ float shf[256];
+    const int c = blockIdx.x;
+    float s = 0.f;
+    for (int r = threadIdx.x; r < nblk; r += blockDim.x) s += hpart[(size_t)r * (C + 1) + c];
+    shf[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+      if (threadIdx.x < w) shf[threadIdx.x] += shf[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) gw9[c] = shf[0];
+    return;
+  }
   __shared__ double sh[256];
   double s = 0.0;
   for (int k = threadIdx.x; k < nblk; k += blockDim.x) s += lpart[k];
@@ -820,9 +838,7 @@ cudaError_t launch_step_finish(const float* hpart, const double* loss_part, int 
                                float b2, cudaStream_t st) {
   // gw9[0..C) and gb9 (= gw9 + C in the flat vector) are the columns of hpart
   if (gb9 != gw9 + C) return cudaErrorInvalidValue;
-  cudaError_t e = launch_reduce_cols(hpart, nblk, C + 1, gw9, &state->stopped, st);
-  if (e != cudaSuccess) return e;
-  k_step_finish<<<1, 256, 0, st>>>(loss_part, nblk, npx, state, b1, b2);
+  k_step_finish<<<C + 2, 256, 0, st>>>(hpart, loss_part, nblk, C, npx, gw9, state, b1, b2);
   N2F_LAUNCH_CHECK();
 }
 

@@ -194,10 +194,7 @@ cudaError_t launch_head_train(const void* a8, int C, int npx, const float* w9, c
                               const float* tgt, int loss_kind, int bf16, float* dz, void* d8,
                               unsigned* dmax, double* loss_part, float* hpart, int* nblk_out,
                               const int* skip, cudaStream_t st);
-// out[c] = sum over R rows of part[r][c] (C columns), fixed order (one block per column).
-cudaError_t launch_reduce_cols(const float* part, int R, int C, float* out, const int* skip,
-                               cudaStream_t st);
-// Sums head-grad and loss partials in a fixed order, advances the Adam step counter.
+// Sums head-grad and loss partials in a fixed order, advances the Adam step counter (one launch).
 cudaError_t launch_step_finish(const float* hpart, const double* loss_part, int nblk, int C,
                                int npx, float* gw9, float* gb9, DevState* state, float b1,
                                float b2, cudaStream_t st);

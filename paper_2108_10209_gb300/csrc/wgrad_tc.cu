@@ -541,13 +541,31 @@ __global__ void __launch_bounds__(W3Warps<EXP>::kThreads, W3Warps<EXP>::kPerSm) 
 // sums the splits s = w, w + 8, ... in order and the eight warp sums are added in warp order,
 // so the result is fixed for a given number of splits.
 constexpr int kRwO = 32;
+// The last C_out blocks sum the bias partials bpart[s][o], one column each: every thread a fixed
+// strided subset of the splits in order, then a fixed tree.
 __global__ void __launch_bounds__(256) k_reduce_wgrad_tc(const float* __restrict__ part, int S,
                                                          int cin, int cout,
-                                                         float* __restrict__ gw, const int* skip) {
+                                                         float* __restrict__ gw,
+                                                         const float* __restrict__ bpart,
+                                                         float* __restrict__ gb, const int* skip) {
   if (skip && *skip) return;
   __shared__ float sh[8][9][kRwO + 1];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int otiles = (cout + kRwO - 1) / kRwO;
+  if (blockIdx.x >= otiles * cin) {
+    float* tr = &sh[0][0][0];  // 256 floats
+    const int o = blockIdx.x - otiles * cin;
+    float a = 0.f;
+    for (int k = threadIdx.x; k < S; k += blockDim.x) a += bpart[(size_t)k * cout + o];
+    tr[threadIdx.x] = a;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+      if (threadIdx.x < h) tr[threadIdx.x] += tr[threadIdx.x + h];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) gb[o] = tr[0];
+    return;
+  }
   const int o0 = (blockIdx.x % otiles) * kRwO, c = blockIdx.x / otiles;
   const int o = o0 + lane;
   const size_t per = (size_t)9 * cout * cin, tstride = (size_t)cin * cout;
@@ -586,30 +604,6 @@ __global__ void __launch_bounds__(256) k_reduce_wgrad_tc(const float* __restrict
 
 }  // namespace
 
-// out[c] = sum_{r < R} part[r * C + c]: one block per column, each thread sums a fixed strided
-// subset of rows in order, then a fixed tree: deterministic for a given R.
-__global__ void k_reduce_cols(const float* __restrict__ part, int R, int C, float* __restrict__ out,
-                              const int* skip) {
-  if (skip && *skip) return;
-  __shared__ float sh[256];
-  const int c = blockIdx.x;
-  float s = 0.f;
-  for (int r = threadIdx.x; r < R; r += blockDim.x) s += part[(size_t)r * C + c];
-  sh[threadIdx.x] = s;
-  __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) out[c] = sh[0];
-}
-
-cudaError_t launch_reduce_cols(const float* part, int R, int C, float* out, const int* skip,
-                               cudaStream_t st) {
-  k_reduce_cols<<<C, 256, 0, st>>>(part, R, C, out, skip);
-  count_launch();
-  return cudaGetLastError();
-}
 
 // Sets the dynamic shared-memory limit of every weight-gradient kernel (the per-block opt-in total
 // minus its static shared memory), so that later launches (possibly inside a stream capture)
@@ -719,11 +713,12 @@ static cudaError_t launch_wgrad_grouped(int bf16, const void* dout, const void* 
     k_wgrad_tc_f32<1, 0><<<grid, W3Warps<0>::kThreads, smem, st>>>(md, mx, p);
   count_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_reduce_wgrad_tc<<<(unsigned)(((cout + kRwO - 1) / kRwO) * cin), 256, 0, st>>>(part, S, cin,
-                                                                                 cout, gw, skip);
+  // weights, and (last C_out blocks) the bias from the S per-split sums of tap group 0
+  const int rot = (cout + kRwO - 1) / kRwO;
+  k_reduce_wgrad_tc<<<(unsigned)(rot * cin + cout), 256, 0, st>>>(part, S, cin, cout, gw, p.bpart,
+                                                                  gb, skip);
   count_launch();
-  // bias: the S per-split sums of tap group 0, added in split order
-  return launch_reduce_cols(p.bpart, S, cout, gb, skip, st);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_wgrad_tc(int bf16, const void* dout, const void* in, int cin, int cout, int H,
