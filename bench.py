@@ -148,7 +148,8 @@ def peaks():
 
 
 # the sources of the conv kernel whose DRAM traffic profiles/traffic.json records
-CONV_SOURCES = ("conv_tc.cu", "tc_common.cuh", "tc_ptx.cuh", "tc_layout.cuh", "cg_util.cuh")
+CONV_SOURCES = ("conv_tc.cu", "tc_common.cuh", "f16_split.cuh", "tc_ptx.cuh", "tc_layout.cuh",
+                "cg_util.cuh")
 
 
 def kernel_source_hash(files=CONV_SOURCES):
