@@ -50,7 +50,9 @@ extern "C" {
 
 /* ---- enumerations ----------------------------------------------------------------------- */
 enum n2f_precision {
-  N2F_FP32 = 0, /* activations, weights and GEMM operands in float32 (plain form) */
+  N2F_FP32 = 0, /* activations, weights, gradients and results in float32 (plain form); the
+                   tensor-core GEMMs multiply two power-of-two-scaled fp16 parts of every
+                   float32 operand (about 22 significant bits per product) */
   N2F_BF16 = 1  /* GEMM operands and stored activations in bfloat16, FP32 accumulation,
                    FP32 master weights, Adam and loss; FP64 validation-MSE reduction */
 };

@@ -68,9 +68,9 @@ CASES = [
     ("tf32 K-major padded", 1, 64, 32, 0, 0, 128 * 16 + 48, 128, 8 * 256 + 16, 256),
     ("bf16 MN-major padded", 0, 128, 32, 1, 1, 160, 4 * 160 + 32, 144, 4 * 160 + 32),
 ]
-# TF32 operands are used K-major only: an MN-major TF32 image in the same convention did not
-# give the product on the GB300, so the float32-form weight gradient transposes its operands
-# to K-major while splitting them into TF32 hi and lo parts.
+# TF32 operands would have to be K-major: an MN-major TF32 image in the same convention did not
+# give the product on the GB300. The float32 form therefore multiplies fp16 parts, which the
+# weight gradient reads MN-major like the bf16 form's operands.
 
 
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
