@@ -158,18 +158,18 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc_bf16(const __grid_constant_
 
   if (warp == 0) {
     if (lane == 0) {
-      int issued = 0;
+      int issued = 0, s = 0, y = cbeg / p.chunks_x, cx = cbeg - y * p.chunks_x;
+      uint32_t ph = 0;
       for (int i = 0; i < nk; ++i) {
-        const int s = i % ns;
-        if (i >= ns && !mbar_wait(&empty[s], ((i / ns) - 1) & 1, abort, p.err))
-          break;
-        const int ch = cbeg + i;
-        const int y = ch / p.chunks_x, x0 = (ch % p.chunks_x) * kWbKP;
+        if (i >= ns && !mbar_wait(&empty[s], ph ^ 1u, abort, p.err)) break;
+        const int x0 = cx * kWbKP;
         uint8_t* st = smem + s * SB;
         mbar_expect_tx(&full[s], kWbA + BB);
         tma_load_4d(st, &tmD, &full[s], 0, x0 / pu, y, o0 / 8);
         tma_load_4d(st + b_off, &tmX, &full[s], 0, x0 / pu - 1, y + r0 - 1, c0g / 8);
         issued = i + 1;
+        if (++cx == p.chunks_x) { cx = 0; ++y; }
+        if (++s == ns) { s = 0; ph ^= 1u; }
       }
       if (*abort)
         for (int i = issued > ns ? issued - ns : 0; i < issued; ++i)
@@ -177,43 +177,53 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc_bf16(const __grid_constant_
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t id = idesc(1, 128, cn, 1, 1), idx = idesc(1, 128, cn + 16, 1, 1);
-      const uint32_t a_sbo = kWbKP * 16;                    // next 8-channel group of delta
+      // descriptors and instruction words fixed up front for stage 0 (stage s adds
+      // s x SB / 16 to the start-address field): per chunk, the MMA groups (taps of the group, or
+      // tap-expanded column chunks of at most 256) x the four 16-pixel K steps
+      constexpr int kWbMma = EXP ? 2 : 3, kKs = kWbKP / 16;
+      const uint32_t a_sbo = kWbKP * 16;             // next 8-channel group of delta
       const uint32_t b_sbo = (uint32_t)R * HX * 16;  // next 8-channel group of x
+      const uint32_t s0 = smem_u32(smem);
+      uint64_t da[kKs], db[kWbMma];
+      uint32_t dcol[kWbMma], idw[kWbMma];
+      int ngrp = 0;
+#pragma unroll
+      for (int k = 0; k < kKs; ++k) da[k] = sdesc(s0 + (uint32_t)k * 256u, 128, a_sbo);
+      if constexpr (EXP) {
+        const int ntot = nt * cn, nch = (ntot + 255) / 256;
+        const int csz = (ntot / nch + 15) / 16 * 16;
+        for (int c0 = 0; c0 < ntot && ngrp < kWbMma; c0 += csz, ++ngrp) {
+          const int n = min(csz, ntot - c0) + ((bias && c0 + csz >= ntot) ? 16 : 0);
+          idw[ngrp] = idesc(1, 128, n, 1, 1);
+          dcol[ngrp] = tbase + (uint32_t)c0;
+          db[ngrp] = sdesc(s0 + e_off + (uint32_t)(c0 / 8) * kWbKP * 16u, 128, kWbKP * 16);
+        }
+      } else {
+        for (int j = 0; j < nt && j < kWbMma; ++j, ++ngrp) {
+          const int tap = t0 + j;
+          // pixel p of the chunk, tap column dx, sits at halo column p + dx - 1 + pu
+          const uint32_t boff = (uint32_t)(((tap / 3) - r0) * HX + (tap % 3) + pu - 1) * 16u;
+          db[j] = sdesc(s0 + b_off + boff, 128, b_sbo);
+          dcol[j] = tbase + (uint32_t)(j * cn);
+          idw[j] = idesc(1, 128, cn + ((bias && j == nt - 1) ? 16 : 0), 1, 1);
+        }
+      }
+      int s = 0;
+      uint32_t ph = 0;
       for (int i = 0; i < nk; ++i) {
-        const int s = i % ns;
-        if (!mbar_wait(EXP ? &split[s] : &full[s], (i / ns) & 1, abort, p.err)) break;
+        if (!mbar_wait(EXP ? &split[s] : &full[s], ph, abort, p.err)) break;
         tc_fence_after();
-        const uint32_t sa = smem_u32(smem + s * SB), sb = sa + b_off;
-        if constexpr (EXP) {
-          // taps side by side along N, in chunks of at most 256 columns (multiples of 16)
-          const int ntot = nt * cn, nch = (ntot + 255) / 256;
-          const int csz = (ntot / nch + 15) / 16 * 16;
-          for (int c0 = 0; c0 < ntot; c0 += csz) {
-            const int n = min(csz, ntot - c0) + ((bias && c0 + csz >= ntot) ? 16 : 0);
-            const uint32_t idc = idesc(1, 128, n, 1, 1);
-            const uint32_t eb = sa + e_off + (uint32_t)(c0 / 8) * kWbKP * 16u;
+        const uint64_t so = (uint64_t)((uint32_t)s * SB >> 4);
 #pragma unroll
-            for (int k = 0; k < kWbKP / 16; ++k)
-              mma_f16(tbase + (uint32_t)c0, sdesc(sa + (uint32_t)k * 256u, 128, a_sbo),
-                      sdesc(eb + (uint32_t)k * 256u, 128, kWbKP * 16), idc,
-                      (i > 0 || k > 0) ? 1u : 0u);
-          }
-        } else {
-          for (int j = 0; j < nt; ++j) {
-            const int tap = t0 + j;
-            // pixel p of the chunk, tap column dx, sits at halo column p + dx - 1 + pu
-            const uint32_t boff = (uint32_t)(((tap / 3) - r0) * HX + (tap % 3) + pu - 1) * 16u;
+        for (int g = 0; g < kWbMma; ++g) {
+          if (g >= ngrp) break;
 #pragma unroll
-            for (int k = 0; k < kWbKP / 16; ++k) {
-              const uint32_t ko = (uint32_t)k * 16u * 16u;
-              mma_f16(tbase + (uint32_t)(j * cn), sdesc(sa + ko, 128, a_sbo),
-                      sdesc(sb + boff + ko, 128, b_sbo), (bias && j == nt - 1) ? idx : id,
-                      (i > 0 || k > 0) ? 1u : 0u);
-            }
-          }
+          for (int k = 0; k < kKs; ++k)  // K step k: 16 pixels = 256 bytes further
+            mma_f16(dcol[g], da[k] + so, db[g] + so + (uint64_t)(16 * k), idw[g],
+                    (i > 0 || k > 0) ? 1u : 0u);
         }
         mma_commit(&empty[s]);
+        if (++s == ns) { s = 0; ph ^= 1u; }
       }
       mma_commit(&accf);
     }
@@ -276,7 +286,7 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc_bf16(const __grid_constant_
 // of the bf16 kernel applies unchanged: TMA brings the fp32 tiles, eight split warps write the
 // two fp16 images of each, one MMA warp issues three MMAs per tap and K step.
 constexpr int kW3KP = 16;  // pixels per stage (one 16-element K step)
-constexpr int kW3MaxStages = 4;
+constexpr int kW3MaxStages = 6;
 // split warps (then epilogue warps): 16 for the one-row layers, whose CTA holds its SM alone
 // (TMEM), 8 for the tap-expanded small layers, which run two CTAs per SM
 template <int EXP>
@@ -423,17 +433,18 @@ __global__ void __launch_bounds__(W3Warps<EXP>::kThreads, W3Warps<EXP>::kPerSm) 
 
   if (warp == 0) {
     if (lane == 0) {
-      int issued = 0;
+      int issued = 0, s = 0, y = cbeg / p.chunks_x, cx = cbeg - y * p.chunks_x;
+      uint32_t ph = 0;
       for (int i = 0; i < nk; ++i) {
-        const int s = i % ns;
-        if (i >= ns && !mbar_wait(&empty[s], ((i / ns) - 1) & 1, abort, p.err)) break;
-        const int ch = cbeg + i;
-        const int y = ch / p.chunks_x, x0 = (ch % p.chunks_x) * kW3KP;
+        if (i >= ns && !mbar_wait(&empty[s], ph ^ 1u, abort, p.err)) break;
+        const int x0 = cx * kW3KP;
         uint8_t* st = smem + s * L.stage;
         mbar_expect_tx(&full[s], 128u * kW3KP * 4 + RB);
         tma_load_4d(st + L.rawA, &tmD, &full[s], 0, x0 / pu, y, o0 / 4);
         tma_load_4d(st + L.rawB, &tmX, &full[s], 0, x0 / pu - 1, y + r0 - 1, c0g / 4);
         issued = i + 1;
+        if (++cx == p.chunks_x) { cx = 0; ++y; }
+        if (++s == ns) { s = 0; ph ^= 1u; }
       }
       if (*abort)
         for (int i = issued > ns ? issued - ns : 0; i < issued; ++i)
@@ -441,61 +452,70 @@ __global__ void __launch_bounds__(W3Warps<EXP>::kThreads, W3Warps<EXP>::kPerSm) 
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t idn = idesc(0, 128, cn, 1, 1), idx = idesc(0, 128, cn + 16, 1, 1);
+      // Every MMA's descriptors and instruction word are fixed up front for stage 0; stage s
+      // adds (s x stage bytes) / 16 to the start-address field (addresses stay below 2^18, so
+      // the 14-bit field never carries). Up to kW3Mma MMA groups per chunk: the taps of the
+      // group (one row) or, tap-expanded, the column chunks of at most 256.
+      constexpr int kW3Mma = EXP ? 2 : 3;
       const uint32_t a_sbo = kW3KP * 16;                     // next 8-channel group of delta
       const uint32_t b_sbo = (uint32_t)R * (kW3KP + 2) * 16;  // next 8-channel group of x
+      const uint32_t s0 = smem_u32(smem);
+      uint64_t da[2], db[kW3Mma][2];
+      uint32_t dcol[kW3Mma], idw[kW3Mma];
+      int ngrp = 0;
+#pragma unroll
+      for (int k = 0; k < 2; ++k) da[k] = sdesc(s0 + L.a[k], 128, a_sbo);
+      if constexpr (EXP) {
+        const int ntot = nt * cn, nch = (ntot + 255) / 256;
+        const int csz = (ntot / nch + 15) / 16 * 16;
+        for (int c0 = 0; c0 < ntot && ngrp < kW3Mma; c0 += csz, ++ngrp) {
+          const int n = min(csz, ntot - c0) + ((bias && c0 + csz >= ntot) ? 16 : 0);
+          idw[ngrp] = idesc(0, 128, n, 1, 1);
+          dcol[ngrp] = tbase + (uint32_t)c0;
+          for (int q = 0; q < 2; ++q)
+            db[ngrp][q] = sdesc(s0 + L.b[q] + (uint32_t)(c0 / 8) * kW3KP * 16u, 128, kW3KP * 16);
+        }
+      } else {
+        for (int j = 0; j < nt && j < kW3Mma; ++j, ++ngrp) {
+          const int tap = t0 + j;
+          const uint32_t boff = (uint32_t)(((tap / 3) - r0) * (kW3KP + 2) + (tap % 3)) * 16u;
+          for (int k = 0; k < 2; ++k) db[j][k] = sdesc(s0 + L.b[k] + boff, 128, b_sbo);
+          dcol[j] = tbase + (uint32_t)(j * cn);
+          idw[j] = idesc(0, 128, cn + ((bias && j == nt - 1) ? 16 : 0), 1, 1);
+        }
+      }
+      int s = 0;
+      uint32_t ph = 0;
       for (int i = 0; i < nk; ++i) {
-        const int s = i % ns;
-        if (!mbar_wait(&split[s], (i / ns) & 1, abort, p.err)) break;
+        if (!mbar_wait(&split[s], ph, abort, p.err)) break;
         tc_fence_after();
-        const uint32_t st = smem_u32(smem + s * L.stage);
-        uint64_t da[2];
+        const uint64_t so = (uint64_t)((uint32_t)s * L.stage >> 4);
+        const uint32_t acc0 = i > 0 ? 1u : 0u;
 #pragma unroll
-        for (int k = 0; k < 2; ++k) da[k] = sdesc(st + L.a[k], 128, a_sbo);
-        if constexpr (EXP) {
-          // the taps side by side along N, in chunks of at most 256 columns (multiples of 16)
-          const int ntot = nt * cn, nch = (ntot + 255) / 256;
-          const int csz = (ntot / nch + 15) / 16 * 16;
-          for (int c0 = 0; c0 < ntot; c0 += csz) {
-            const int n = min(csz, ntot - c0) + ((bias && c0 + csz >= ntot) ? 16 : 0);
-            const uint32_t id = idesc(0, 128, n, 1, 1);
-            uint64_t db[2];
-#pragma unroll
-            for (int q = 0; q < 2; ++q) db[q] = sdesc(st + L.b[q] + (uint32_t)(c0 / 8) * kW3KP * 16u, 128, kW3KP * 16);
-            const uint32_t d = tbase + (uint32_t)c0;
-            mma_f16(d, da[0], db[0], id, i > 0 ? 1u : 0u);
-            mma_f16(d, da[0], db[1], id, 1u);
-            mma_f16(d, da[1], db[0], id, 1u);
-          }
-        } else {
-        for (int j = 0; j < nt; ++j) {
-            const int tap = t0 + j;
-            const uint32_t boff = (uint32_t)(((tap / 3) - r0) * (kW3KP + 2) + (tap % 3)) * 16u;
-            uint64_t db[2];
-#pragma unroll
-            for (int k = 0; k < 2; ++k) db[k] = sdesc(st + L.b[k] + boff, 128, b_sbo);
-            const uint32_t d = tbase + (uint32_t)(j * cn);
-            const uint32_t id = (bias && j == nt - 1) ? idx : idn;
-            mma_f16(d, da[0], db[0], id, i > 0 ? 1u : 0u);
-            mma_f16(d, da[0], db[1], id, 1u);
-            mma_f16(d, da[1], db[0], id, 1u);
-          }
+        for (int g = 0; g < kW3Mma; ++g) {
+          if (g >= ngrp) break;
+          mma_f16(dcol[g], da[0] + so, db[g][0] + so, idw[g], acc0);
+          mma_f16(dcol[g], da[0] + so, db[g][1] + so, idw[g], 1u);
+          mma_f16(dcol[g], da[1] + so, db[g][0] + so, idw[g], 1u);
         }
         mma_commit(&empty[s]);
+        if (++s == ns) { s = 0; ph ^= 1u; }
       }
       mma_commit(&accf);
     }
   } else {
     const int et = threadIdx.x - 64;
     const float sd = f16_scale(p.dmax), sx = f16_scale(p.xmax);
+    int s = 0;
+    uint32_t ph = 0;
     for (int i = 0; i < nk; ++i) {
-      const int s = i % ns;
-      if (!mbar_wait(&full[s], (i / ns) & 1, abort, p.err)) break;
+      if (!mbar_wait(&full[s], ph, abort, p.err)) break;
       uint8_t* st = smem + s * L.stage;
       split2_stage<R, EXP>(st, st, L, cn / 8, pu, et, nt, t0, r0, sd, sx);
       fence_proxy_async();
       __syncwarp();
       if (lane == 0) mbar_arrive(&split[s]);
+      if (++s == ns) { s = 0; ph ^= 1u; }
     }
     if (!mbar_wait(&accf, 0, abort, p.err)) mbar_drain(&accf, 0);
     tc_fence_after();
