@@ -58,5 +58,25 @@ cudaError_t make_map(CUtensorMap* m, const void* base, int bf16, int C, int H, i
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// A float32 channel-grouped map act[g][y][x][4] seen as a 3-D tensor (4 W, H, C / 4): a box
+// row is a run of bx whole pixels of one group and image row (bx * 16 bytes, at most 256
+// floats), so a halo tile costs no extra units at its ends. The box is (4 bx, by rows, bg
+// groups); outside the tensor it reads zeros. The innermost start coordinate is 4 x (a whole
+// pixel, 16 bytes).
+cudaError_t make_map_rows(CUtensorMap* m, const void* base, int C, int H, int W, int bx, int by,
+                          int bg) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return cudaErrorNotSupported;
+  if (4 * bx > 256 || C % 4) return cudaErrorInvalidValue;
+  cuuint64_t dims[3] = {(cuuint64_t)(4 * W), (cuuint64_t)H, (cuuint64_t)(C / 4)};
+  cuuint64_t strides[2] = {(cuuint64_t)W * 16, (cuuint64_t)H * W * 16};
+  cuuint32_t box[3] = {(cuuint32_t)(4 * bx), (cuuint32_t)by, (cuuint32_t)bg};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides,
+                  box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 }  // namespace
 }  // namespace n2f

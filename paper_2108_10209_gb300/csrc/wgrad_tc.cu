@@ -300,7 +300,8 @@ struct W3Layout {
   uint32_t rawA, rawB, a[2], b[2], stage;
 };
 
-// raw x tile pitch: the 16 chunk pixels plus one TMA unit of pu pixels on each side
+// raw x tile pitch: the 16 chunk pixels plus pu halo pixels on each side (the kernel loads whole
+// pixels, pu = 1)
 __host__ __device__ inline int w3_raw_pitch(int pu) { return kW3KP + 2 * pu; }
 
 // exp: the x parts are written tap-expanded, [taps x C/8][16 px][16 B] + 2 bias groups, so one
@@ -401,9 +402,9 @@ __global__ void __launch_bounds__(W3Warps<EXP>::kThreads, W3Warps<EXP>::kPerSm) 
   const int cbeg = s_idx * p.per_split;
   const int cend = min(p.total_chunks, cbeg + p.per_split);
   const int nk = cend > cbeg ? cend - cbeg : 0;
-  const int pu = p.pu;
-  const W3Layout L = w3_layout(cn, R, pu, EXP, nt);
-  const uint32_t RB = (uint32_t)cn * R * w3_raw_pitch(pu) * 4;
+  // both tiles come by whole-pixel box rows (make_map_rows): x with one halo pixel each side
+  const W3Layout L = w3_layout(cn, R, 1, EXP, nt);
+  const uint32_t RB = (uint32_t)cn * R * w3_raw_pitch(1) * 4;
   const bool bias = grp == 0;
   const uint32_t ncols = tmem_cols(nt * cn + (bias ? 16 : 0));
   volatile int* abort = &abort_flag;
@@ -440,8 +441,8 @@ __global__ void __launch_bounds__(W3Warps<EXP>::kThreads, W3Warps<EXP>::kPerSm) 
         const int x0 = cx * kW3KP;
         uint8_t* st = smem + s * L.stage;
         mbar_expect_tx(&full[s], 128u * kW3KP * 4 + RB);
-        tma_load_4d(st + L.rawA, &tmD, &full[s], 0, x0 / pu, y, o0 / 4);
-        tma_load_4d(st + L.rawB, &tmX, &full[s], 0, x0 / pu - 1, y + r0 - 1, c0g / 4);
+        tma_load_3d(st + L.rawA, &tmD, &full[s], 4 * x0, y, o0 / 4);
+        tma_load_3d(st + L.rawB, &tmX, &full[s], 4 * (x0 - 1), y + r0 - 1, c0g / 4);
         issued = i + 1;
         if (++cx == p.chunks_x) { cx = 0; ++y; }
         if (++s == ns) { s = 0; ph ^= 1u; }
@@ -511,7 +512,7 @@ __global__ void __launch_bounds__(W3Warps<EXP>::kThreads, W3Warps<EXP>::kPerSm) 
     for (int i = 0; i < nk; ++i) {
       if (!mbar_wait(&full[s], ph, abort, p.err)) break;
       uint8_t* st = smem + s * L.stage;
-      split2_stage<R, EXP>(st, st, L, cn / 8, pu, et, nt, t0, r0, sd, sx);
+      split2_stage<R, EXP>(st, st, L, cn / 8, 1, et, nt, t0, r0, sd, sx);
       fence_proxy_async();
       __syncwarp();
       if (lane == 0) mbar_arrive(&split[s]);
@@ -668,8 +669,13 @@ static cudaError_t launch_wgrad_grouped(int bf16, const void* dout, const void* 
   int pu = 1;
   while (pu < pu_max && W % (2 * pu) == 0) pu *= 2;
   CUtensorMap md, mx;
-  cudaError_t e = make_map(&md, dout, bf16, cout, H, W, KP / pu, 1, 128 / GE, pu);
-  if (e == cudaSuccess) e = make_map(&mx, in, bf16, cin, H, W, KP / pu + 2, tg.R, tg.cn / GE, pu);
+  // bf16 tiles by pu-pixel units (128-byte box rows); float32 tiles by whole-pixel box rows (one
+  // row of 16 or 18 pixels per channel group and image row, no halo units)
+  cudaError_t e = bf16 ? make_map(&md, dout, bf16, cout, H, W, KP / pu, 1, 128 / GE, pu)
+                       : make_map_rows(&md, dout, cout, H, W, KP, 1, 128 / 4);
+  if (e == cudaSuccess)
+    e = bf16 ? make_map(&mx, in, bf16, cin, H, W, KP / pu + 2, tg.R, tg.cn / GE, pu)
+             : make_map_rows(&mx, in, cin, H, W, KP + 2, tg.R, tg.cn / 4);
   if (e != cudaSuccess) return e;
   const int otiles = (cout + 127) / 128;
   WgBf16Params p;
@@ -695,7 +701,7 @@ static cudaError_t launch_wgrad_grouped(int bf16, const void* dout, const void* 
   // C_in <= 64, bf16 form for C_in = 32 (its expansion is a copy pass)
   const bool exp = bf16 ? tg.cn <= 32 : tg.cn <= 64;
   const uint32_t sb = bf16 ? (exp ? wb_stage_exp(tg.cn, tg.R, pu, tg.count[0]) : wb_stage(tg.cn, tg.R, pu))
-                           : w3_layout(tg.cn, tg.R, pu, exp, tg.count[0]).stage;
+                           : w3_layout(tg.cn, tg.R, 1, exp, tg.count[0]).stage;
   const int max_stages = bf16 ? kWbMaxStages : kW3MaxStages;
   p.stages = (int)((227u * 1024u / (uint32_t)max_res - 2048u) / sb);
   if (p.stages > max_stages) p.stages = max_stages;
