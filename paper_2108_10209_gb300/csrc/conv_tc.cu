@@ -210,7 +210,16 @@ __global__ void __launch_bounds__(ConvWarps<BF16>::kThreads, 1)
   } else if (warp == 1) {
     if (lane == 0) {  // MMA issuer
       const uint32_t id = idesc(BF16 ? 1 : 0, kTileM, NT, 0, 0);  // bf16 / fp16 operands
-      uint32_t it = 0, lt = 0;
+      // descriptors of stage 0; a stage, a tap and a row only add their byte offset / 16 to the
+      // start-address field (every address is below 2^18, so the 14-bit field never carries)
+      const uint32_t s0 = smem_u32(smem);
+      const uint64_t dA0 = sdesc(s0, C::A_SLAB, 128), dAl0 = sdesc(s0 + C::A_LO, C::A_SLAB, 128);
+      const uint64_t dB0 = sdesc(s0 + C::b_off(), NT * 16, 128);
+      const uint64_t dBl0 = sdesc(s0 + C::b_lo_off(NT), NT * 16, 128);
+      const uint64_t btap = (uint64_t)(C::NSLAB * NT);  // one tap of B, in 16-byte units
+      uint32_t lt = 0;
+      int s = 0;  // stage and phase of the next K step (the producer's sequence)
+      uint32_t ph = 0;
       bool ok = true;
       int cur = 0;
       for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
@@ -219,35 +228,31 @@ __global__ void __launch_bounds__(ConvWarps<BF16>::kThreads, 1)
         if (lt >= (uint32_t)NB && !mbar_wait(&acce[buf], ((lt / NB) - 1) & 1, abort, p.err)) break;
         tc_fence_after();
         const uint32_t dbase = tbase + (uint32_t)(buf * acc_cols);
-        for (int i = 0; i < nk; ++i, ++it) {
-          const int s = it % NS;
-          const uint32_t ph = (it / NS) & 1;
+        for (int i = 0; i < nk; ++i) {
           if (!mbar_wait(BF16 ? &full[s] : &split[s], ph, abort, p.err)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t sa = smem_u32(smem + s * SB);
-          const uint32_t sal = sa + C::A_LO;
-          const uint32_t sb = sa + C::b_off(), sbl = sa + C::b_lo_off(NT);
+          const uint64_t so = (uint64_t)((uint32_t)s * SB >> 4);
+          const uint64_t dA = dA0 + so, dAl = dAl0 + so;
+          uint64_t db = dB0 + so, dbl = dBl0 + so;
 #pragma unroll
-          for (int tap = 0; tap < 9; ++tap) {
-            const uint32_t bo = (uint32_t)tap * C::NSLAB * NT * 16u;
-            const uint64_t db = sdesc(sb + bo, NT * 16, 128);
+          for (int tap = 0; tap < 9; ++tap, db += btap, dbl += btap) {
             const uint32_t acc = (i > 0 || tap > 0) ? 1u : 0u;
 #pragma unroll
             for (int r = 0; r < ROWS; ++r) {  // output row r reads halo rows r .. r + 2
-              const uint32_t ao = (uint32_t)((r + tap / 3) * kHaloX + (tap % 3)) * 16u;
-              const uint64_t da = sdesc(sa + ao, C::A_SLAB, 128);
+              const uint64_t ao = (uint64_t)((r + tap / 3) * kHaloX + (tap % 3));  // 16-byte units
               const uint32_t d = dbase + (uint32_t)(r * NT);
-              mma_f16(d, da, db, id, acc);
+              mma_f16(d, dA + ao, db, id, acc);
               if (!BF16) {  // hi*lo and lo*hi
-                mma_f16(d, da, sdesc(sbl + bo, NT * 16, 128), id, 1u);
-                mma_f16(d, sdesc(sal + ao, C::A_SLAB, 128), db, id, 1u);
+                mma_f16(d, dA + ao, dbl, id, 1u);
+                mma_f16(d, dAl + ao, db, id, 1u);
               }
             }
           }
           mma_commit(&empty[s]);
+          if (++s == NS) { s = 0; ph ^= 1u; }
         }
         mma_commit(&accf[buf]);
         ++lt;
