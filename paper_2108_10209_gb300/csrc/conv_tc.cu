@@ -3,9 +3,11 @@
 //
 // D[px][n] = sum_{tap, c} A[px + tap][c] B[n][tap, c]: M = 128 pixels of one image row, N =
 // output channels, K = 9 C_in. The A operand of every tap is the same TMA halo tile (rows + 2
-// rows x 130 pixels x a chunk of channels, zero outside the image = the "same" padding)
-// addressed at a shifted start: in the K-major no-swizzle layout each pixel row is 16 bytes, so
-// a shift of dx pixels is a 16*dx byte offset of the descriptor. One warp issues TMA copies,
+// rows x 132 pixels from two left of the tile x a chunk of channels, zero outside the image =
+// the "same" padding) addressed at a shifted start: in the K-major no-swizzle layout each pixel
+// row is 16 bytes, so a shift of dx pixels is a 16*dx byte offset of the descriptor. Starting
+// two pixels left lets TMA move the tile in two-pixel (32-byte) box rows when W is even: with
+// 16-byte rows it fetches every 32-byte L2 sector twice. One warp issues TMA copies,
 // one thread issues the MMAs into TMEM accumulators, the epilogue warps read TMEM back for the
 // fused bias + ReLU (forward) or ReLU mask (dgrad), and in the float32 form a warpgroup splits
 // the activations into scaled fp16 hi/lo parts in shared memory first (f16_split.cuh; the
@@ -37,6 +39,7 @@ struct ConvTcParams {
   void* out;
   ConvScales sc;        // float32 form: largest magnitudes of A, of the weights, of the output
   int cin, cout, H, W, tiles_x;
+  int pu;      // pixels per TMA box row of the halo map (2 when W is even, else 1)
   int stages;  // pipeline stages, 2 .. kConvMaxStages (a tuning choice; no effect on results)
   const int* skip;
   int* err;
@@ -54,14 +57,14 @@ struct alignas(128) ConvJob {
   void* out;
   const int* skip;  // the job's stop flag: its tiles are skipped once set
   ConvScales sc;
-  int H, W, tiles_x, tile0;
+  int H, W, tiles_x, tile0, pu;
 };
 
 constexpr int kTileM = 128;   // pixels per accumulator (one image row segment)
 constexpr int kRowsM = 2;     // image rows per tile by default: each weight stage feeds two
                               // accumulators (1 is a tuning choice: twice the tiles, half the
                               // accumulator columns, so TMEM double-buffers at N = 256)
-constexpr int kHaloX = kTileM + 2;
+constexpr int kHaloX = kTileM + 4;  // halo tile pixels: x0 - 2 .. x0 + 129
 constexpr int kConvMaxStages = 4;
 
 template <int BF16, int ROWS = kRowsM>
@@ -105,7 +108,7 @@ struct TileJob {
   const void* mask;
   void* out;
   ConvScales sc;
-  int H, W, tiles_x, local;
+  int H, W, tiles_x, local, pu;
   bool skip;
 };
 
@@ -138,14 +141,14 @@ __global__ void __launch_bounds__(ConvWarps<BF16>::kThreads, 1)
       t.map = &tmA;
       t.w_hi = p.w_hi; t.w_lo = p.w_lo; t.bias = p.bias; t.mask = p.mask; t.out = p.out;
       t.sc = p.sc;
-      t.H = p.H; t.W = p.W; t.tiles_x = p.tiles_x; t.local = tile; t.skip = false;
+      t.H = p.H; t.W = p.W; t.tiles_x = p.tiles_x; t.local = tile; t.skip = false; t.pu = p.pu;
     } else {
       while (cur + 1 < njobs && tile >= jobs[cur + 1].tile0) ++cur;
       const ConvJob& J = jobs[cur];
       t.map = &J.map;
       t.w_hi = J.w_hi; t.w_lo = J.w_lo; t.bias = J.bias; t.mask = J.mask; t.out = J.out;
       t.sc = J.sc;
-      t.H = J.H; t.W = J.W; t.tiles_x = J.tiles_x; t.local = tile - J.tile0;
+      t.H = J.H; t.W = J.W; t.tiles_x = J.tiles_x; t.local = tile - J.tile0; t.pu = J.pu;
       t.skip = J.skip && *J.skip;
     }
     return t;
@@ -196,7 +199,7 @@ __global__ void __launch_bounds__(ConvWarps<BF16>::kThreads, 1)
             break;
           uint8_t* st = smem + s * SB;
           mbar_expect_tx(&full[s], C::A_BYTES + B_BYTES * (BF16 ? 1 : 2));
-          tma_load_4d(st, tj.map, &full[s], 0, x0 - 1, ty - 1, i * C::NRAW);
+          tma_load_4d(st, tj.map, &full[s], 0, (x0 - 2) / tj.pu, ty - 1, i * C::NRAW);
           const size_t stage = (size_t)nt * nk + i;
           bulk_load(st + C::b_off(), tj.w_hi + stage * B_BYTES, B_BYTES, &full[s]);
           if (!BF16) bulk_load(st + C::b_lo_off(NT), tj.w_lo + stage * B_BYTES, B_BYTES, &full[s]);
@@ -242,7 +245,8 @@ __global__ void __launch_bounds__(ConvWarps<BF16>::kThreads, 1)
             const uint32_t acc = (i > 0 || tap > 0) ? 1u : 0u;
 #pragma unroll
             for (int r = 0; r < ROWS; ++r) {  // output row r reads halo rows r .. r + 2
-              const uint64_t ao = (uint64_t)((r + tap / 3) * kHaloX + (tap % 3));  // 16-byte units
+              // output pixel m, tap column dx in 0..2 reads halo column m + dx + 1
+              const uint64_t ao = (uint64_t)((r + tap / 3) * kHaloX + (tap % 3) + 1);  // 16 B units
               const uint32_t d = dbase + (uint32_t)(r * NT);
               mma_f16(d, dA + ao, db, id, acc);
               if (!BF16) {  // hi*lo and lo*hi
@@ -527,7 +531,8 @@ static cudaError_t conv_params(int bf16, const void* in, int cin, int cout, int 
                                int* err, int rows, CUtensorMap* m, ConvTcParams* p) {
   if (!bf16 && (!sc.in || !sc.w || !w_lo)) return cudaErrorInvalidValue;
   const int NRAW = bf16 ? ConvCfg<1>::NRAW : ConvCfg<0>::NRAW;
-  cudaError_t e = make_map(m, in, bf16, cin, H, W, kHaloX, rows + 2, NRAW);
+  const int pu = W % 2 == 0 ? 2 : 1;
+  cudaError_t e = make_map(m, in, bf16, cin, H, W, kHaloX / pu, rows + 2, NRAW, pu);
   if (e != cudaSuccess) return e;
   p->w_hi = (const uint8_t*)w_hi;
   p->w_lo = (const uint8_t*)w_lo;
@@ -540,6 +545,7 @@ static cudaError_t conv_params(int bf16, const void* in, int cin, int cout, int 
   p->H = H;
   p->W = W;
   p->tiles_x = (W + kTileM - 1) / kTileM;
+  p->pu = pu;
   p->stages = 2;
   p->skip = skip;
   p->err = err;
@@ -630,9 +636,11 @@ cudaError_t conv_group_table(int mode, int bf16, int cin, int cout, const ConvGr
   for (int k = 0; k < n; ++k) {
     memset(&t[k], 0, sizeof(ConvJob));
     if (!bf16 && (!e[k].sc.in || !e[k].sc.w || !e[k].w_lo)) return cudaErrorInvalidValue;
-    cudaError_t r = make_map(&t[k].map, e[k].in, bf16, cin, e[k].H, e[k].W, kHaloX, kRowsM + 2,
-                             NRAW);
+    const int pu = e[k].W % 2 == 0 ? 2 : 1;
+    cudaError_t r = make_map(&t[k].map, e[k].in, bf16, cin, e[k].H, e[k].W, kHaloX / pu,
+                             kRowsM + 2, NRAW, pu);
     if (r != cudaSuccess) return r;
+    t[k].pu = pu;
     t[k].sc = e[k].sc;
     t[k].w_hi = (const uint8_t*)e[k].w_hi;
     t[k].w_lo = (const uint8_t*)e[k].w_lo;
