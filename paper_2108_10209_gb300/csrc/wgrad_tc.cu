@@ -292,6 +292,10 @@ constexpr int kW3MaxStages = 6;
 template <int EXP>
 struct W3Warps {
   static constexpr int kSplit = EXP ? 8 : 16;
+  // one-row layers: two teams of eight warps split alternate chunks, so two chunks are split at
+  // once (a chunk gives each thread about one group: its latency, not its instructions, bounds it)
+  static constexpr int kTeams = EXP ? 1 : 2;
+  static constexpr int kTeamWarps = kSplit / kTeams;
   static constexpr int kThreads = 64 + 32 * kSplit;
   static constexpr int kPerSm = EXP ? 2 : 1;
 };
@@ -343,7 +347,7 @@ template <int R, int EXP>
 __device__ __forceinline__ void split2_stage(const uint8_t* st, uint8_t* stw, const W3Layout& L,
                                              int g8n, int pu, int et, int nt, int t0, int r0,
                                              float sd, float sx) {
-  constexpr int kThr = 32 * W3Warps<EXP>::kSplit;
+  constexpr int kThr = 32 * W3Warps<EXP>::kTeamWarps;
   constexpr int PP = kW3KP + 2;  // part pitch
   const int PR = w3_raw_pitch(pu);
   {
@@ -412,7 +416,7 @@ __global__ void __launch_bounds__(W3Warps<EXP>::kThreads, W3Warps<EXP>::kPerSm) 
     for (int s = 0; s < ns; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
-      mbar_init(&split[s], W3Warps<EXP>::kSplit);
+      mbar_init(&split[s], W3Warps<EXP>::kTeamWarps);
     }
     mbar_init(&accf, 1);
     abort_flag = 0;
@@ -505,17 +509,20 @@ __global__ void __launch_bounds__(W3Warps<EXP>::kThreads, W3Warps<EXP>::kPerSm) 
       mma_commit(&accf);
     }
   } else {
-    const int et = threadIdx.x - 64;
+    constexpr int kTT = 32 * W3Warps<EXP>::kTeamWarps;  // threads per team
+    const int team = (threadIdx.x - 64) / kTT, et = (threadIdx.x - 64) % kTT;
     const float sd = f16_scale(p.dmax), sx = f16_scale(p.xmax);
     int s = 0;
     uint32_t ph = 0;
     for (int i = 0; i < nk; ++i) {
-      if (!mbar_wait(&full[s], ph, abort, p.err)) break;
-      uint8_t* st = smem + s * L.stage;
-      split2_stage<R, EXP>(st, st, L, cn / 8, 1, et, nt, t0, r0, sd, sx);
-      fence_proxy_async();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&split[s]);
+      if (i % W3Warps<EXP>::kTeams == team) {  // this team's chunk
+        if (!mbar_wait(&full[s], ph, abort, p.err)) break;
+        uint8_t* st = smem + s * L.stage;
+        split2_stage<R, EXP>(st, st, L, cn / 8, 1, et, nt, t0, r0, sd, sx);
+        fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&split[s]);
+      }
       if (++s == ns) { s = 0; ph ^= 1u; }
     }
     if (!mbar_wait(&accf, 0, abort, p.err)) mbar_drain(&accf, 0);
