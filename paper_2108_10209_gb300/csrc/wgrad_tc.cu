@@ -299,6 +299,8 @@ struct W3Warps {
   static constexpr int kThreads = 64 + 32 * kSplit;
   static constexpr int kPerSm = EXP ? 2 : 1;
 };
+static_assert(kW3MaxStages % W3Warps<0>::kTeams == 0 && 2 % W3Warps<0>::kTeams == 0,
+              "float32 stage counts must stay multiples of the split team count");
 
 struct W3Layout {
   uint32_t rawA, rawB, a[2], b[2], stage;
@@ -712,6 +714,10 @@ static cudaError_t launch_wgrad_grouped(int bf16, const void* dout, const void* 
   const int max_stages = bf16 ? kWbMaxStages : kW3MaxStages;
   p.stages = (int)((227u * 1024u / (uint32_t)max_res - 2048u) / sb);
   if (p.stages > max_stages) p.stages = max_stages;
+  // float32 one-row layers: split teams take chunks i = team (mod teams); a team's next chunk
+  // reuses the stage of chunk (next - stages), which must be one of its own (already waited for)
+  // or its parity wait could see that older load's phase: stages a multiple of the team count
+  if (!bf16 && !exp) p.stages -= p.stages % W3Warps<0>::kTeams;
   if (p.stages < 2) p.stages = 2;
   uint32_t smem = (uint32_t)p.stages * sb;
   // a CTA holding more than half of TMEM keeps the SM to itself
