@@ -634,7 +634,7 @@ cudaError_t conv_group_table(int mode, int bf16, int cin, int cout, const ConvGr
   ConvJob* t = static_cast<ConvJob*>(table);
   long tiles = 0;
   for (int k = 0; k < n; ++k) {
-    memset(&t[k], 0, sizeof(ConvJob));
+    memset(static_cast<void*>(&t[k]), 0, sizeof(ConvJob));  // the table is host bytes
     if (!bf16 && (!e[k].sc.in || !e[k].sc.w || !e[k].w_lo)) return cudaErrorInvalidValue;
     const int pu = e[k].W % 2 == 0 ? 2 : 1;
     cudaError_t r = make_map(&t[k].map, e[k].in, bf16, cin, e[k].H, e[k].W, kHaloX / pu,
@@ -664,7 +664,7 @@ cudaError_t launch_conv_tc_grouped(int mode, int bf16, int cin, int cout, const 
   if (const cudaError_t pe = tc_prepare()) return pe;
   if (ntiles > 0x7fffffffL) return cudaErrorInvalidValue;
   ConvTcParams p;
-  memset(&p, 0, sizeof(p));
+  memset(static_cast<void*>(&p), 0, sizeof(p));
   p.cin = cin;
   p.cout = cout;
   p.tiles_x = (int)ntiles;  // the grouped kernel's total tile count
