@@ -276,12 +276,19 @@ int n2f_unpack_cg(const void* cg, int C, int H, int W, int precision, float* nch
  *   dgrad   (mode 1):  out = conv^T(in, w) * [mask > 0]   (in = dL/d pre-activation of this
  *                      layer, mask = the layer's input activation, out has C_in channels)
  * in/out/mask in CG layout of `precision`; w: float32 [C_out][C_in][3][3] (device), b: C_out.
- * C_in, C_out in {32, 64, 128, 256} for the tensor-core engine; multiples of G for SIMT. */
+ * C_in, C_out in {32, 64, 128, 256} for the tensor-core engine; multiples of G for SIMT.
+ * Tensor-core engine, N2F_FP32: the call first finds the largest |w| and |in| (the power-of-two
+ * scales of their two fp16 parts); accuracy about 2^-22 per product at any float32 magnitude.
+ * Allocates a small workspace (cudaMallocAsync), synchronises the stream; N2F_ETIMEDOUT if a
+ * kernel wait ran out. */
 int n2f_conv3x3(int mode, int engine, int precision, const void* in, int cin, int cout, int H,
                 int W, const float* w, const float* b, const void* mask, void* out,
                 void* stream);
 /* Weight/bias gradient of one 3x3 layer: dw[C_out][C_in][3][3] and db[C_out] (float32,
- * overwritten) from dout (CG, C_out channels) and in (CG, C_in channels). */
+ * overwritten) from dout (CG, C_out channels) and in (CG, C_in channels). Tensor-core engine,
+ * N2F_FP32: scales from the largest |dout| and |in|, as for n2f_conv3x3. Allocates its
+ * partial-sum workspace (cudaMallocAsync), synchronises the stream; N2F_ETIMEDOUT if a kernel
+ * wait ran out. */
 int n2f_conv3x3_wgrad(int engine, int precision, const void* dout, const void* in, int cin,
                       int cout, int H, int W, float* dw, float* db, void* stream);
 
