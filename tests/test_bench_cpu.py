@@ -1,0 +1,64 @@
+"""bench.py's host logic on the CPU: the reference arm's JSON line (the FP64 oracle timed on the
+host cores) and the roofline arithmetic of our arm's line."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def test_reference_arm_prints_one_contract_line():
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.strip().startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference"
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["value"] > 0 and d["unit"] == "images/s" and d["higher_is_better"] is True
+    assert d["dtype"] == "f64" and d["steps"] == 1
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"]
+    e = d["e2e"]
+    assert e["value"] == d["value"] and e["unit"] == d["unit"]
+    assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_conv_roofline_uses_the_form_ceiling(precision):
+    # 10 launches of 48.7 GFLOP in 1.0 ms: 487 TFLOP/s achieved
+    stats = {"prof_launches": 10, "prof_ms": 1.0, "prof_flops": 10 * 48.7e9, "prof_bytes": 0.0}
+    rl = bench.roofline(stats, 7, precision, True, "none")
+    pk, _ = bench.peaks()
+    ceiling = pk["bf16_tflops_sustained"] / (3.0 if precision == 0 else 1.0)
+    assert rl["bound"] == "tensor" and rl["unit"] == "TFLOP/s"
+    assert rl["achieved"] == pytest.approx(487.0)
+    assert rl["peak"] == pytest.approx(ceiling)
+    assert rl["frac"] == pytest.approx(487.0 / ceiling)
+    assert rl["traffic"] is None  # no record for this workload name
+
+
+def test_memory_bound_roofline_is_against_hbm():
+    stats = {"prof_launches": 4, "prof_ms": 2.0, "prof_flops": 0.0, "prof_bytes": 4 * 1e9}
+    rl = bench.roofline(stats, 5, 0, True, "none")  # the head: 1 GB per launch in 0.5 ms
+    pk, _ = bench.peaks()
+    assert rl["bound"] == "hbm" and rl["unit"] == "GB/s"
+    assert rl["achieved"] == pytest.approx(2000.0)
+    assert rl["frac"] == pytest.approx(2000.0 / pk["hbm_gbs"])
+
+
+def test_traffic_record_is_keyed_on_the_conv_sources():
+    recs = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    for key, r in recs.items():
+        kclass, workload = key.split("|", 1)
+        expected = r["dram_bytes_per_launch"] if r["source_hash"] == bench.kernel_source_hash() \
+            else None
+        assert bench.traffic_record(kclass, workload) == expected
