@@ -321,6 +321,13 @@ int n2f_umma_gemm(int tf32, int N, int K, int a_mn, int b_mn, const void* A, siz
                   uint32_t a_lbo, uint32_t a_sbo, uint32_t a_kstep, const void* B, size_t b_bytes,
                   uint32_t b_lbo, uint32_t b_sbo, uint32_t b_kstep, float* D, void* stream);
 
+/* Failure-detection check: one kernel waits on a barrier that nothing ever completes, with the
+ * bounded wait every tensor-core kernel uses (here limit_ms, 1..10000). The wait gives up after
+ * the limit, the kernel records the time-out and returns, and the context stays usable: the
+ * call returns N2F_ETIMEDOUT (the expected result) after about limit_ms, N2F_OK never.
+ * N2F_EINVAL for a limit out of range. Synchronises the stream. */
+int n2f_wait_probe(uint32_t limit_ms, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

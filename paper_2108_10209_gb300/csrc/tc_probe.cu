@@ -80,6 +80,22 @@ __global__ void __launch_bounds__(128, 1) k_umma_probe(ProbeArgs a) {
   }
 }
 
+// ---- bounded-wait check --------------------------------------------------------------------
+// One warp waits on an mbarrier that nothing ever arrives on, with the same bounded wait as
+// the tensor-core kernels (here with a caller-given limit): the wait must give up, record the
+// time-out in the error word and let the kernel return.
+__global__ void k_wait_probe(uint64_t limit_ns, int* err) {
+  __shared__ uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    abort_flag = 0;
+    mbar_fence_init();
+  }
+  __syncthreads();
+  mbar_wait_for(&bar, 0, &abort_flag, err, limit_ns);
+}
+
 }  // namespace
 
 // Resolves the tensor-map encoder and sets the shared-memory limits of every tensor-core kernel
@@ -144,5 +160,24 @@ extern "C" int n2f_umma_gemm(int tf32, int N, int K, int a_mn, int b_mn, const v
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cudaFreeAsync(err, st);
   if (e != cudaSuccess) return set_cuda_error(e, "n2f_umma_gemm");
+  return herr ? N2F_ETIMEDOUT : N2F_OK;
+}
+
+// ---- diagnostic entry point: the bounded wait gives up (declared in n2f.h) -----------------
+extern "C" int n2f_wait_probe(uint32_t limit_ms, void* stream) {
+  using namespace n2f;
+  if (limit_ms < 1 || limit_ms > 10000) return N2F_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  int* err = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&err, sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), st);
+  if (e != cudaSuccess) return set_cuda_error(e, "n2f_wait_probe");
+  k_wait_probe<<<1, 32, 0, st>>>((uint64_t)limit_ms * 1000000ull, err);
+  e = cudaGetLastError();
+  int herr = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFreeAsync(err, st);
+  if (e != cudaSuccess) return set_cuda_error(e, "n2f_wait_probe");
   return herr ? N2F_ETIMEDOUT : N2F_OK;
 }

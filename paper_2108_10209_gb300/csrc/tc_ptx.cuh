@@ -56,21 +56,26 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
 
 // Waits for the phase with the given parity. Returns false when *abort becomes non-zero or
 // the time limit passes (then it also sets *abort and the kernel's error word).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort,
-                                          int* err) {
+__device__ __forceinline__ bool mbar_wait_for(uint64_t* bar, uint32_t parity, volatile int* abort,
+                                              int* err, uint64_t limit_ns) {
   if (mbar_try(bar, parity)) return true;
   const uint64_t t0 = gtimer();
   for (uint32_t it = 1;; ++it) {
     if (mbar_try(bar, parity)) return true;
     if ((it & 63) == 0) {
       if (abort && *abort) return false;
-      if (gtimer() - t0 > kWaitLimitNs) {
+      if (gtimer() - t0 > limit_ns) {
         if (abort) *abort = 1;
         if (err) atomicCAS(err, kErrNone, kErrTimeout);
         return false;
       }
     }
   }
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort,
+                                          int* err) {
+  return mbar_wait_for(bar, parity, abort, err, kWaitLimitNs);
 }
 
 // Same, ignoring the abort flag (used to drain copies that are already in flight).

@@ -107,6 +107,7 @@ SIGNATURES = {
     "n2f_conv3x3_wgrad_noalloc": (_I, [_I, _I, _P, _P, _I, _I, _I, _I, _P, _P, _P]),
     "n2f_umma_gemm": (_I, [_I, _I, _I, _I, _I, _P, _Z, C.c_uint32, C.c_uint32, C.c_uint32, _P, _Z,
                            C.c_uint32, C.c_uint32, C.c_uint32, _P, _P]),
+    "n2f_wait_probe": (_I, [C.c_uint32, _P]),
 }
 
 _lib = None
@@ -481,6 +482,12 @@ def umma_gemm(A_img, a_lbo, a_sbo, a_kstep, B_img, b_lbo, b_sbo, b_kstep, N, K, 
                               a_sbo, a_kstep, _ptr(B_img), B_img.numel(), b_lbo, b_sbo, b_kstep,
                               _ptr(D), _stream_ptr(stream)), "n2f_umma_gemm")
     return D
+
+
+def wait_probe(limit_ms: int, stream=None) -> int:
+    """Failure-detection check: a kernel waits on a barrier nothing completes; returns the
+    library's code (N2F_ETIMEDOUT when the bounded wait gave up, as it must)."""
+    return int(lib().n2f_wait_probe(int(limit_ms), _stream_ptr(stream)))
 
 
 def conv3x3_wgrad_noalloc(dout_cg, in_cg, cin, cout, H, W, dw, db, precision=N2F_FP32,
