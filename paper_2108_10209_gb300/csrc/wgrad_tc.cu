@@ -72,7 +72,7 @@ struct WgBf16Params {
   float* part;  // [S][9][C_in][C_out]
   int cin, cout, H, W, chunks_x, total_chunks, per_split;
   int stages;  // pipeline stages
-  int pu;      // pixels per TMA unit of both maps
+  int pu;      // bf16 kernel: pixels per TMA unit of both maps
   float* bpart;  // [S][C_out] bias-gradient partials, written by the tap group 0 CTAs
   TapGroups tg;
   const unsigned* dmax;  // float32 form: largest |delta| and |x| (operand scales)
@@ -672,11 +672,9 @@ static cudaError_t launch_wgrad_grouped(int bf16, const void* dout, const void* 
   if (!bf16 && (!dmax || !xmax)) return cudaErrorInvalidValue;
   const TapGroups tg = tap_groups(cin);
   const int KP = bf16 ? kWbKP : kW3KP, GE = bf16 ? 8 : 4;
-  // pixels per TMA unit: 128-byte box rows for bf16 (the halo grows by 14 pixels of 66),
-  // 64-byte rows for float32 (the raw tile of 16 pixels would grow too much with 8)
-  const int pu_max = bf16 ? 8 : 4;
+  // bf16: pixels per TMA unit, up to 8 (128-byte box rows; the halo grows by 14 pixels of 66)
   int pu = 1;
-  while (pu < pu_max && W % (2 * pu) == 0) pu *= 2;
+  while (bf16 && pu < 8 && W % (2 * pu) == 0) pu *= 2;
   CUtensorMap md, mx;
   // bf16 tiles by pu-pixel units (128-byte box rows); float32 tiles by whole-pixel box rows (one
   // row of 16 or 18 pixels per channel group and image row, no halo units)
