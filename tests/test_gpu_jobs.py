@@ -210,3 +210,25 @@ def test_admission_by_hbm_budget(n2f):
     assert seen_queued
     for o in outs:
         assert np.array_equal(o, ref)
+
+
+@pytest.mark.parametrize("case", ["smallest 2x2", "constant", "all zeros"])
+def test_degenerate_images_against_oracle(n2f, case):
+    # The smallest image the method accepts (sub-images 2x1 and 1x2), a constant image (the four
+    # sub-images and every target identical) and an all-zero one (BCE targets 0, the first
+    # layer's output its bias alone), through the job API with the literal widths on the
+    # tensor-core engine, 4 fixed steps, against the oracle's run.
+    if case == "smallest 2x2":
+        x = np.array([[0.2, 0.7], [0.9, 0.1]], np.float32)
+    elif case == "constant":
+        x = np.full((16, 24), 0.5, np.float32)
+    else:
+        x = np.zeros((16, 24), np.float32)
+    p = n2f.params(seed=3, fixed_steps=4)
+    with n2f.Context() as ctx:
+        j = ctx.submit(x, p)
+        assert ctx.wait(j, 120000) == n2f.N2F_OK
+        out = ctx.result(j, x.shape)
+    ref, _ = oracle.denoise(x.astype(np.float64), oracle.Params(seed=3, fixed_steps=4))
+    assert np.all(np.isfinite(out))
+    assert float(np.max(np.abs(out - ref))) < 2e-3
