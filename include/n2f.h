@@ -268,7 +268,12 @@ int n2f_checker_gather(const float* x, int H, int W, float* up_e, float* up_o, f
  * returns without waiting. N2F_EINVAL for a NULL pointer or Z, H or W < 1; N2F_EDEVICE if the
  * launch fails. */
 int n2f_max_project(const float* vol, int Z, int H, int W, float* out, void* stream);
-/* NCHW float32 <-> CG layout of the given precision (C a multiple of G). */
+/* NCHW float32 <-> CG layout of the given precision (C a multiple of G); device pointers, runs on
+ * `stream` without waiting. N2F_EINVAL for a NULL pointer, a precision other than N2F_FP32 or
+ * N2F_BF16, C not a positive multiple of G, or H or W < 1.
+ * The convolution entry points below return N2F_EINVAL in the same cases (C_in and C_out
+ * positive multiples of 8, an engine outside enum n2f_engine, a mode other than 0 or 1) and
+ * N2F_ENOTSUP when N2F_ENGINE_TC is asked for channel counts it is not built for. */
 int n2f_pack_cg(const float* nchw, int C, int H, int W, int precision, void* cg, void* stream);
 int n2f_unpack_cg(const void* cg, int C, int H, int W, int precision, float* nchw, void* stream);
 /* One 3x3 convolution layer with zero "same" padding (Methods; Fig. 2a):

@@ -308,10 +308,17 @@ extern "C" int n2f_max_project(const float* vol, int Z, int H, int W, float* out
   return N2F_OK;
 }
 
+// the op-level entry points take one of the two precision forms and one of the engines by value
+static bool valid_form(int precision) { return precision == N2F_FP32 || precision == N2F_BF16; }
+static bool valid_engine(int engine) {
+  return engine >= N2F_ENGINE_AUTO && engine <= N2F_ENGINE_TC;
+}
+
 extern "C" int n2f_pack_cg(const float* nchw, int C, int H, int W, int precision, void* cg,
                            void* stream) {
   const int G = precision == N2F_BF16 ? 8 : 4;
-  if (!nchw || !cg || C < G || C % G || H < 1 || W < 1) return N2F_EINVAL;
+  if (!valid_form(precision) || !nchw || !cg || C < G || C % G || H < 1 || W < 1)
+    return N2F_EINVAL;
   CKR(launch_pack_cg(nchw, C, H, W, precision == N2F_BF16, cg, (cudaStream_t)stream));
   return N2F_OK;
 }
@@ -319,7 +326,8 @@ extern "C" int n2f_pack_cg(const float* nchw, int C, int H, int W, int precision
 extern "C" int n2f_unpack_cg(const void* cg, int C, int H, int W, int precision, float* nchw,
                              void* stream) {
   const int G = precision == N2F_BF16 ? 8 : 4;
-  if (!nchw || !cg || C < G || C % G || H < 1 || W < 1) return N2F_EINVAL;
+  if (!valid_form(precision) || !nchw || !cg || C < G || C % G || H < 1 || W < 1)
+    return N2F_EINVAL;
   CKR(launch_unpack_cg(cg, C, H, W, precision == N2F_BF16, nchw, (cudaStream_t)stream));
   return N2F_OK;
 }
@@ -335,7 +343,8 @@ extern "C" int n2f_conv3x3(int mode, int engine, int precision, const void* in, 
                            int H, int W, const float* w, const float* b, const void* mask,
                            void* out, void* stream) {
   if (!in || !out || !w || (mode == 0 && !b) || (mode == 1 && !mask) || H < 1 || W < 1 ||
-      cin % 8 || cout % 8 || cin < 8 || cout < 8 || (mode != 0 && mode != 1))
+      cin % 8 || cout % 8 || cin < 8 || cout < 8 || (mode != 0 && mode != 1) ||
+      !valid_form(precision) || !valid_engine(engine))
     return N2F_EINVAL;
   const int bf16 = precision == N2F_BF16;
   const int eng = resolve_engine(engine, cin, cout);
@@ -392,7 +401,8 @@ extern "C" int n2f_conv3x3(int mode, int engine, int precision, const void* in, 
 extern "C" int n2f_conv3x3_wgrad(int engine, int precision, const void* dout, const void* in,
                                  int cin, int cout, int H, int W, float* dw, float* db,
                                  void* stream) {
-  if (!dout || !in || !dw || !db || H < 1 || W < 1 || cin % 8 || cout % 8 || cin < 8 || cout < 8)
+  if (!dout || !in || !dw || !db || H < 1 || W < 1 || cin % 8 || cout % 8 || cin < 8 ||
+      cout < 8 || !valid_form(precision) || !valid_engine(engine))
     return N2F_EINVAL;
   const int bf16 = precision == N2F_BF16;
   int eng = resolve_engine(engine, cin, cout);

@@ -51,6 +51,7 @@ extern "C" int n2f_conv3x3_wgrad_noalloc(int engine, int precision, const void* 
   if (!dout || !in || !dw || !db || H < 1 || W < 1 || cin % 8 || cout % 8 || cin < 8 || cout < 8)
     return N2F_EINVAL;
   if (engine < N2F_ENGINE_AUTO || engine > N2F_ENGINE_TC) return N2F_EINVAL;
+  if (precision != N2F_FP32 && precision != N2F_BF16) return N2F_EINVAL;
   // at least one split of the pixel sum plus the bias partials must fit the array
   const size_t need = (size_t)9 * cin * cout + (size_t)cout + (size_t)1024 * cout + 64;
   if (need > kScratchFloats - kErrFloats) {

@@ -80,3 +80,37 @@ def test_error_strings(n2f):
     L = n2f.lib()
     for code in range(0, -11, -1):
         assert L.n2f_strerror(code)
+
+
+def _no_gpu():
+    import torch
+    return not torch.cuda.is_available()
+
+
+# The argument checks return before any CUDA call. The pointers below are placeholders that no
+# call may dereference, so the test runs only where there is no GPU: a missing check then ends in
+# a failed CUDA call (another error code), never in a device access.
+@pytest.mark.skipif(not _no_gpu(), reason="placeholder pointers: run without a GPU only")
+def test_op_level_argument_checks(n2f):
+    L = n2f.lib()
+    P = C.c_void_p(256)  # placeholder, never dereferenced
+    E = n2f.N2F_EINVAL
+    F32, TC = n2f.N2F_FP32, n2f.N2F_ENGINE_TC
+    # precision outside the two forms
+    assert L.n2f_pack_cg(P, 8, 4, 4, 7, P, None) == E
+    assert L.n2f_unpack_cg(P, 8, 4, 4, -1, P, None) == E
+    assert L.n2f_conv3x3(0, TC, 2, P, 32, 32, 8, 8, P, P, None, P, None) == E
+    assert L.n2f_conv3x3_wgrad(TC, 5, P, P, 32, 32, 8, 8, P, P, None) == E
+    assert L.n2f_conv3x3_wgrad_noalloc(TC, 5, P, P, 32, 32, 8, 8, P, P, None) == E
+    # engine outside enum n2f_engine, mode other than 0 / 1, channel counts, sizes
+    assert L.n2f_conv3x3(0, 3, F32, P, 32, 32, 8, 8, P, P, None, P, None) == E
+    assert L.n2f_conv3x3(2, TC, F32, P, 32, 32, 8, 8, P, P, P, P, None) == E
+    assert L.n2f_conv3x3(1, TC, F32, P, 32, 32, 8, 8, P, None, None, P, None) == E  # no mask
+    assert L.n2f_conv3x3(0, TC, F32, P, 12, 32, 8, 8, P, P, None, P, None) == E
+    assert L.n2f_conv3x3_wgrad(-1, F32, P, P, 32, 32, 8, 8, P, P, None) == E
+    assert L.n2f_conv3x3_wgrad(TC, F32, P, P, 32, 32, 0, 8, P, P, None) == E
+    assert L.n2f_pack_cg(P, 6, 4, 4, F32, P, None) == E      # C not a multiple of G = 4
+    assert L.n2f_pack_cg(P, 12, 4, 4, n2f.N2F_BF16, P, None) == E  # G = 8 for bf16
+    assert L.n2f_checker_gather(P, 1, 8, P, P, P, P, None) == E
+    assert L.n2f_max_project(P, 0, 4, 4, P, None) == E
+    assert L.n2f_wait_probe(0, None) == E and L.n2f_wait_probe(10001, None) == E
