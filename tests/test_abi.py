@@ -6,6 +6,7 @@ import re
 import subprocess
 import tempfile
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -114,3 +115,29 @@ def test_op_level_argument_checks(n2f):
     assert L.n2f_checker_gather(P, 1, 8, P, P, P, P, None) == E
     assert L.n2f_max_project(P, 0, 4, 4, P, None) == E
     assert L.n2f_wait_probe(0, None) == E and L.n2f_wait_probe(10001, None) == E
+
+
+@pytest.mark.parametrize("bad", [
+    dict(precision=2), dict(loss=5), dict(widths=3), dict(engine=4), dict(engine=-1),
+    dict(lr=0.0), dict(lr=float("nan")), dict(beta1=1.0), dict(beta2=-0.5), dict(eps=0.0),
+    dict(patience=0), dict(incl_best=1, patience=1), dict(channels=5), dict(channels=-1),
+    dict(channels=3, target_channel=3), dict(target_channel=1), dict(downsample=9),
+    dict(exact=2), dict(struct_size=8)])
+def test_trainer_rejects_parameters_before_touching_the_device(n2f, bad):
+    # a valid host image (room for every plane any of these parameter sets could ask for): the
+    # parameter check runs before the first CUDA call, so this runs with or without a GPU
+    img = np.random.default_rng(0).random(6 * 8 * 8).astype(np.float32)
+    tr = C.c_void_p()
+    p = n2f.params(**bad)
+    rc = n2f.lib().n2f_trainer_create(C.byref(tr), img.ctypes.data, 8, 8, C.byref(p), None)
+    assert rc == n2f.N2F_EINVAL and not tr.value
+
+
+@pytest.mark.parametrize("H,W,poison", [(1, 8, None), (8, 1, None), (0, 0, None), (8, 8, 17)])
+def test_trainer_rejects_images_before_touching_the_device(n2f, H, W, poison):
+    img = np.zeros(64, np.float32)
+    if poison is not None:
+        img[poison] = np.inf
+    tr = C.c_void_p()
+    rc = n2f.lib().n2f_trainer_create(C.byref(tr), img.ctypes.data, H, W, None, None)
+    assert rc == n2f.N2F_EINVAL and not tr.value
