@@ -62,3 +62,44 @@ def test_traffic_record_is_keyed_on_the_conv_sources():
         expected = r["dram_bytes_per_launch"] if r["source_hash"] == bench.kernel_source_hash() \
             else None
         assert bench.traffic_record(kclass, workload) == expected
+
+
+class _DoneProc:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+    def kill(self):
+        pass
+
+
+def test_clock_samples_give_median_max_and_active_reasons(tmp_path):
+    # nvidia-smi --format=csv,noheader,nounits rows of ClockSampler.FIELDS
+    rows = ["0, 2070, 2070, 900.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+            "0, 1995, 2070, 1390.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+            "0, 2032, 2070, 1200.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+            "garbled line",
+            "0, [N/A], 2070, 0, 0x0, Not Active, Not Active, Not Active, Not Active"]
+    f = tmp_path / "clocks.csv"
+    f.write_text("\n".join(rows) + "\n")
+    cs = bench.ClockSampler(0)
+    cs.proc, cs.path = _DoneProc(), str(f)
+    clk = cs.stop()
+    assert clk["samples"] == 3 and clk["sm_mhz"] == 2032.0 and clk["sm_max_mhz"] == 2070.0
+    assert clk["reasons"] == ["sw_power_cap"]
+    assert not f.exists()
+
+
+def test_clock_samples_report_a_thermal_slowdown(tmp_path):
+    f = tmp_path / "clocks.csv"
+    f.write_text("0, 1500, 2070, 1400, 0x40, Not Active, Active, Not Active, Not Active\n")
+    cs = bench.ClockSampler(0)
+    cs.proc, cs.path = _DoneProc(), str(f)
+    assert cs.stop()["reasons"] == ["hw_thermal_slowdown"]
+
+
+def test_missing_sampler_is_reported():
+    cs = bench.ClockSampler(0)
+    assert cs.stop()["reasons"] == ["nvidia-smi unavailable"]
