@@ -221,7 +221,15 @@ int n2f_stats(n2f_ctx* ctx, n2f_ctx_stats* st);
 /* ---- trainer API: one job's device state, stepped by the caller (parity tests) ----------
  * A trainer runs on the caller's stream; calls enqueue work and return. Exports synchronise
  * the stream and return values converted to float64 in the layouts of the CPU oracle:
- * NCHW maps, weights [C_out][C_in][3][3], the flat parameter order of n2f_param_count. */
+ * NCHW maps, weights [C_out][C_in][3][3], the flat parameter order of n2f_param_count.
+ * Errors: n2f_trainer_create returns EINVAL for a NULL out or image, bad params, H or W < 2 or
+ * a non-finite pixel, all checked before any device work, and ENOMEM / EDEVICE when the device
+ * state cannot be made; every call returns EINVAL for a NULL trainer and EDEVICE for a failed
+ * CUDA call. n2f_trainer_run (max_epochs <= 0: no limit) runs epochs in blocks of four and
+ * reads the device state after each block: it stops once the rule has fired or at least
+ * max_epochs epochs ran (params.max_epochs is the exact cap on the device), and returns
+ * ETIMEDOUT if a kernel's bounded wait ran out; n2f_trainer_status then reports FAILED with
+ * that error (ENONFINITE for a non-finite validation score). */
 typedef struct n2f_trainer n2f_trainer;
 int n2f_trainer_create(n2f_trainer** out, const float* image, int H, int W, const n2f_params* p,
                        void* stream);          /* image: host memory, p->channels planes */
@@ -231,6 +239,8 @@ int n2f_trainer_validate(n2f_trainer* tr);       /* full-image forward + MSE + s
 int n2f_trainer_epoch(n2f_trainer* tr);          /* four steps + validate */
 int n2f_trainer_run(n2f_trainer* tr, int max_epochs); /* epochs until the rule fires or cap */
 int n2f_trainer_finish(n2f_trainer* tr);         /* computes the output image on the device */
+/* Sets the parameters (the flat order of n2f_param_count, rounded to float32) and repacks the
+ * kernels' weight copies; EINVAL unless n equals n2f_param_count. Synchronises the stream. */
 int n2f_trainer_set_theta(n2f_trainer* tr, const double* theta, size_t n);
 enum n2f_export {
   N2F_X_THETA = 0, N2F_X_GRAD = 1, N2F_X_ADAM_M = 2, N2F_X_ADAM_V = 3, /* flat */
@@ -242,7 +252,8 @@ enum n2f_export {
   N2F_X_SUM = 10,   /* running output sum, H*W */
   N2F_X_OUT = 11    /* output image (after n2f_trainer_finish), H*W */
 };
-/* Returns the number of values through *n_out; out may be NULL to query the size. */
+/* Returns the number of values through *n_out; out may be NULL to query the size. EINVAL for an
+ * unknown `what`, a layer index outside 1..8 or a pair outside 0..3, or cap below the size. */
 int n2f_trainer_export(n2f_trainer* tr, int what, int index, double* out, size_t cap,
                        size_t* n_out);
 int n2f_trainer_status(n2f_trainer* tr, n2f_status* st);

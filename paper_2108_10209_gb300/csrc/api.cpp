@@ -200,6 +200,10 @@ extern "C" int n2f_trainer_run(n2f_trainer* tr, int max_epochs) {
     }
     int rc = trainer_read_state(t, &s);
     if (rc) return rc;
+    if (s.kerr) {
+      tl_error = "a device wait ran out of time";
+      return N2F_ETIMEDOUT;
+    }
     if (s.stopped) break;
   }
   return trainer_finish(t);
@@ -286,8 +290,8 @@ extern "C" int n2f_trainer_status(n2f_trainer* tr, n2f_status* st) {
   if (rc) return rc;
   fill_status(&tr->t, s, st);
   st->state = s.stopped ? N2F_DONE : N2F_RUNNING;
-  st->error = s.stopped == 3 ? N2F_ENONFINITE : N2F_OK;
-  if (s.stopped == 3) st->state = N2F_FAILED;
+  st->error = s.kerr ? N2F_ETIMEDOUT : (s.stopped == 3 ? N2F_ENONFINITE : N2F_OK);
+  if (s.stopped == 3 || s.kerr) st->state = N2F_FAILED;
   return N2F_OK;
 }
 
