@@ -402,6 +402,51 @@ def test_output_is_mean_of_last_patience_validations():
     np.testing.assert_allclose(out, np.mean(outs[-P:], axis=0), rtol=1e-13, atol=1e-15)
 
 
+def _replay(x, p, epochs):
+    """Validation scores and outputs of the first `epochs` epochs, stepped by hand."""
+    j = oracle.Job(x, p)
+    scores, outs = [], []
+    for _ in range(epochs):
+        for k in range(4):
+            j.step(k)
+        sc, v = j.validate()
+        scores.append(sc)
+        outs.append(v)
+    return scores, outs
+
+
+def test_window_including_the_best_epoch():
+    # incl_best: the averaging window is the best epoch and the patience - 1 epochs after it;
+    # the output is still the mean of the last `patience` validations when the rule fires
+    r = _rng(21)
+    x = r.uniform(0, 1, size=(6, 6))
+    P = 3
+    p = oracle.Params(widths=(2,) * 8, seed=4, patience=P, lr=3e-2, incl_best=True)
+    out, info = oracle.denoise(x, p)
+    assert info["stopped"]
+    scores, outs = _replay(x, p, info["epoch"])
+    best = int(np.argmin(scores))  # strict improvement: the first of equal minima
+    assert best == info["epoch"] - P
+    np.testing.assert_allclose(out, np.mean(outs[best:], axis=0), rtol=1e-13, atol=1e-15)
+
+
+@pytest.mark.parametrize("cap", [1, 2, 3, 5, 8])
+def test_epoch_cap_averages_the_window_so_far(cap):
+    # a cap reached before the rule fires: the mean of the validations after the best epoch,
+    # or the best epoch's own output when none came after it (the first epoch always sets the
+    # best, so a cap of one takes that branch)
+    r = _rng(22)
+    x = r.uniform(0, 1, size=(6, 6))
+    p = oracle.Params(widths=(2,) * 8, seed=4, patience=100, lr=3e-2, max_epochs=cap)
+    out, info = oracle.denoise(x, p)
+    assert info["epoch"] == cap and not info["stopped"]
+    scores, outs = _replay(x, p, cap)
+    best = min(range(cap), key=lambda e: (scores[e], e))
+    assert (best + 1 < cap) == (cap == 8)  # both branches are exercised on this image
+    expect = np.mean(outs[best + 1:], axis=0) if best + 1 < cap else outs[best]
+    np.testing.assert_allclose(out, expect, rtol=1e-13, atol=1e-15)
+
+
 def test_max_projection():
     # The projection of a Z-stack (Methods, fluorescence microscopy) against numpy's max along
     # Z, plus its defining properties: never below a slice, equal to some slice at every pixel,
