@@ -110,9 +110,23 @@ class ClockSampler:
 
 # ---------------------------------------------------------------------------- CPU oracle -----
 
+def host_cores() -> int:
+    """Cores this process may run on (its affinity set)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count() or 1
+
+
+def oracle_threads() -> int:
+    """Threads the oracle's parallel loops actually use."""
+    import oracle
+    return oracle.threads()
+
+
 def oracle_epoch_seconds(noisy, widths: int, crop: int = 128):
     """Wall time of one oracle epoch (4 steps + validation) on the top-left crop x crop."""
-    os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
+    os.environ.setdefault("OMP_NUM_THREADS", str(host_cores()))
     import oracle
     ow = oracle.WIDTHS_PLIT if widths == 0 else oracle.WIDTHS_W64
     job = oracle.Job(noisy[:crop, :crop], oracle.Params(widths=ow, seed=0))
@@ -126,7 +140,7 @@ def cpu_baseline(noisy, size: int, widths: int, crop: int = 128, reps: int = 1):
     t = min(ts)
     scale = (size * size) / float(crop * crop)
     ips = 1.0 / (MIN_EPOCHS * scale * t)
-    return {"value": ips, "unit": UNIT, "cores": int(os.environ.get("OMP_NUM_THREADS", "1")),
+    return {"value": ips, "unit": UNIT, "cores": oracle_threads(),
             "kind": "oracle",
             "sample": (f"one epoch (4 training steps + validation) of the FP64 oracle on a "
                        f"{crop}x{crop} crop: {t:.2f} s; scaled by pixel count x{scale:.0f} to the "
@@ -556,7 +570,7 @@ def run_reference(args, ws, rank):
     scale = (size * size) / (128.0 * 128.0)
     per_img = [MIN_EPOCHS * scale * t for t in ts]
     value = len(per_img) / sum(per_img)
-    cores = int(os.environ.get("OMP_NUM_THREADS", "1"))
+    cores = oracle_threads()
     sample = (f"each step: one epoch of the FP64 oracle on a 128x128 crop, scaled by pixel "
               f"count x{scale:.0f} and by {MIN_EPOCHS} epochs (the shortest stopping-rule run)")
     q = sorted(per_img)
@@ -608,7 +622,7 @@ def main():
                     help="batched / zstack: lockstep group size (n2f_config.group_size), 0 = off")
     ap.add_argument("--stack-side", type=int, default=1024, help="zstack: slice side")
     args = ap.parse_args()
-    os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
+    os.environ.setdefault("OMP_NUM_THREADS", str(host_cores()))
     ws, rank, local = dist_env()
     if args.impl == "reference":
         line = run_reference(args, ws, rank)

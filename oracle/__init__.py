@@ -56,6 +56,8 @@ def lib():
         L.orc_adam.argtypes = [_dp, _dp, _dp, _dp, C.c_size_t, C.c_long, C.c_double, C.c_double,
                                C.c_double, C.c_double]
         L.orc_stop_init.argtypes = [C.c_void_p]
+        L.orc_threads.restype = C.c_int
+        L.orc_threads.argtypes = []
         L.orc_stop_update.restype = C.c_int
         L.orc_stop_update.argtypes = [C.c_void_p, C.c_double, C.c_int, C.c_int]
         L.orc_job_new.restype = C.c_void_p
@@ -341,6 +343,11 @@ def denoise(x, params: Params = Params()):
     j = Job(x, params)
     out = j.run()
     return out, j.info()
+
+
+def threads() -> int:
+    """Threads the oracle's parallel loops use (OMP_NUM_THREADS as read when it was loaded)."""
+    return int(lib().orc_threads())
 
 
 def max_project(vol):

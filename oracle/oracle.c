@@ -12,6 +12,18 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads the parallel loops use (OpenMP over independent outputs only), for reporting. */
+int orc_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
 
 /* ------------------------------------------------------------------------------------------ */
 /* SplitMix64 (Steele, Lea & Flood, OOPSLA 2014), counter form.                                */

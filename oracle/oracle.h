@@ -95,6 +95,8 @@ typedef struct {
   int stopped;   /* 1 once the rule fired */
 } orc_stop_state;
 void orc_stop_init(orc_stop_state* s);
+/* Threads the oracle's parallel loops use (1 without OpenMP). */
+int orc_threads(void);
 /* Feed one validation score. Returns 1 when it is a new best (the running output sum restarts),
  * 0 otherwise (the output of this epoch joins the sum). Sets ->stopped when `since` reaches
  * `patience` (or patience-1 when incl_best, the reading whose window contains the best epoch). */
