@@ -13,7 +13,7 @@
 #include <stdlib.h>
 #include <string.h>
 #ifdef _OPENMP
-#include <omp.h>
+int omp_get_max_threads(void); /* OpenMP runtime library routine */
 #endif
 
 /* Threads the parallel loops use (OpenMP over independent outputs only), for reporting. */
