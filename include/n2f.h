@@ -37,7 +37,8 @@ extern "C" {
 
 /* ---- error codes ------------------------------------------------------------------------ */
 #define N2F_OK 0
-#define N2F_EINVAL (-1)     /* NULL pointer, H or W < 2, non-finite pixel, bad struct_size/enum */
+#define N2F_EINVAL (-1)     /* NULL pointer, H or W < 2 or H*W >= 2^31, non-finite pixel, bad
+                               struct_size/enum */
 #define N2F_ETOOBIG (-2)    /* the job can never fit the context's HBM budget */
 #define N2F_EAGAIN (-3)     /* result not ready yet */
 #define N2F_ENOENT (-4)     /* unknown or already collected job */
@@ -182,7 +183,7 @@ int n2f_create(n2f_ctx** out, const n2f_config* cfg);
 void n2f_destroy(n2f_ctx* ctx);
 /* Queues one H x W image (host memory, copied before return); with p->channels = C_0 > 1, C_0
  * planes of H x W. p may be NULL (defaults).
- * Errors: EINVAL (NULL, H or W < 2, non-finite pixel, bad params), ETOOBIG. */
+ * Errors: EINVAL (NULL, H or W < 2, H*W >= 2^31, non-finite pixel, bad params), ETOOBIG. */
 int n2f_submit(n2f_ctx* ctx, const float* image, int H, int W, const n2f_params* p, n2f_job* out);
 /* Same, for an image already in device memory (copied on the device before the job runs;
  * the caller must keep it valid until n2f_poll reports RUNNING or later). */
@@ -222,8 +223,8 @@ int n2f_stats(n2f_ctx* ctx, n2f_ctx_stats* st);
  * A trainer runs on the caller's stream; calls enqueue work and return. Exports synchronise
  * the stream and return values converted to float64 in the layouts of the CPU oracle:
  * NCHW maps, weights [C_out][C_in][3][3], the flat parameter order of n2f_param_count.
- * Errors: n2f_trainer_create returns EINVAL for a NULL out or image, bad params, H or W < 2 or
- * a non-finite pixel, all checked before any device work, and ENOMEM / EDEVICE when the device
+ * Errors: n2f_trainer_create returns EINVAL for a NULL out or image, bad params, H or W < 2,
+ * H*W >= 2^31 or a non-finite pixel, all checked before any device work, and ENOMEM / EDEVICE when the device
  * state cannot be made; every call returns EINVAL for a NULL trainer and EDEVICE for a failed
  * CUDA call. n2f_trainer_run (max_epochs <= 0: no limit) runs epochs in blocks of four and
  * reads the device state after each block: it stops once the rule has fired or at least

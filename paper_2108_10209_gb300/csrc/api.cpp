@@ -109,7 +109,7 @@ static size_t planes(const n2f_params* p) {
 
 static int check_image(int H, int W) {
   if (H < 2 || W < 2) return N2F_EINVAL;
-  if ((size_t)H * W > ((size_t)1 << 31)) return N2F_EINVAL;
+  if ((size_t)H * W >= ((size_t)1 << 31)) return N2F_EINVAL;  // pixel indices are 32-bit ints
   return N2F_OK;
 }
 

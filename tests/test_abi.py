@@ -133,7 +133,8 @@ def test_trainer_rejects_parameters_before_touching_the_device(n2f, bad):
     assert rc == n2f.N2F_EINVAL and not tr.value
 
 
-@pytest.mark.parametrize("H,W,poison", [(1, 8, None), (8, 1, None), (0, 0, None), (8, 8, 17)])
+@pytest.mark.parametrize("H,W,poison", [(1, 8, None), (8, 1, None), (0, 0, None), (8, 8, 17),
+                                         (1 << 16, 1 << 15, None)])
 def test_trainer_rejects_images_before_touching_the_device(n2f, H, W, poison):
     img = np.zeros(64, np.float32)
     if poison is not None:
