@@ -106,3 +106,23 @@ def test_clock_samples_report_a_thermal_slowdown(tmp_path):
 def test_missing_sampler_is_reported():
     cs = bench.ClockSampler(0)
     assert cs.stop()["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_reference_arm_under_torchrun_prints_once_from_rank_0():
+    # two ranks on one node: rank 0 times the oracle and prints; rank 1 exits 0 without work
+    import socket
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    env = dict(os.environ, OMP_NUM_THREADS="4")
+    r = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1",
+                        "--nproc-per-node", "2", "--master-addr", "127.0.0.1", "--master-port",
+                        str(port), "bench.py", "--impl", "reference", "--gpus", "2", "--steps",
+                        "1", "--warmup", "0"], cwd=ROOT, capture_output=True, text=True,
+                       timeout=600, env=env)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.strip().startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
