@@ -185,8 +185,11 @@ void n2f_destroy(n2f_ctx* ctx);
  * planes of H x W. p may be NULL (defaults).
  * Errors: EINVAL (NULL, H or W < 2, H*W >= 2^31, non-finite pixel, bad params), ETOOBIG. */
 int n2f_submit(n2f_ctx* ctx, const float* image, int H, int W, const n2f_params* p, n2f_job* out);
-/* Same, for an image already in device memory (copied on the device before the job runs;
- * the caller must keep it valid until n2f_poll reports RUNNING or later). */
+/* Same, for an image already in device memory (this context's device). The library copies it
+ * on the job's own stream when the job is admitted, which can be any time after the call, with
+ * no ordering against the caller's streams: the work that wrote the image must be finished
+ * before the call (its stream synchronised), and the image must stay valid and unchanged until
+ * the job is DONE, FAILED or CANCELED. Pixels are not checked for finiteness here. */
 int n2f_submit_device(n2f_ctx* ctx, const float* dimage, int H, int W, const n2f_params* p,
                       n2f_job* out);
 /* Same, for a 16-bit microscope image, normalised on the device as value / 65535 (one plane:

@@ -191,6 +191,7 @@ class Context:
         cfg.autotune = int(autotune)
         self.device = device
         self._keep = []
+        self._dev_inputs = {}  # job -> device image tensor, held until the job is collected
         if torch_alloc:
             import torch
 
@@ -213,6 +214,7 @@ class Context:
         if getattr(self, "h", None):
             lib().n2f_destroy(self.h)
             self.h = None
+            self._dev_inputs.clear()
 
     def __del__(self):
         try:
@@ -245,11 +247,18 @@ class Context:
         return job.value
 
     def submit_device(self, dimage, p: Params | None = None) -> int:
-        """dimage: a contiguous float32 CUDA tensor (H, W) that stays valid until RUNNING."""
-        H, W = dimage.shape
+        """dimage: a contiguous float32 CUDA tensor (H, W), or (planes, H, W). The library copies
+        it on the job's own stream once the job is admitted, with no ordering against torch's
+        streams: torch's current stream on that device is synchronised here (a tensor written on
+        another stream needs that stream synchronised first), and the tensor is held, and must
+        not be written, until the job's result is collected."""
+        import torch
+        H, W = dimage.shape[-2:]
+        torch.cuda.current_stream(dimage.device).synchronize()
         job = C.c_uint64()
         check(lib().n2f_submit_device(self.h, _ptr(dimage), H, W, C.byref(p) if p else None,
                                       C.byref(job)), "n2f_submit_device")
+        self._dev_inputs[job.value] = dimage
         return job.value
 
     def poll(self, job: int) -> Status:
@@ -261,14 +270,21 @@ class Context:
     def wait(self, job: int, timeout_ms: int = -1) -> int:
         return lib().n2f_wait(self.h, job, timeout_ms)
 
+    def _collected(self, job: int, rc: int) -> int:
+        # any other outcome means the job reached a final state (its copy of the input is done)
+        if rc not in (N2F_EAGAIN, N2F_EINVAL):
+            self._dev_inputs.pop(job, None)
+        return rc
+
     def result(self, job: int, shape) -> np.ndarray:
         out = np.empty(shape, np.float32)
-        check(lib().n2f_result(self.h, job, out.ctypes.data_as(C.c_void_p), out.size),
-              "n2f_result")
+        rc = lib().n2f_result(self.h, job, out.ctypes.data_as(C.c_void_p), out.size)
+        check(self._collected(job, rc), "n2f_result")
         return out
 
     def result_device(self, job: int, dout) -> None:
-        check(lib().n2f_result_device(self.h, job, _ptr(dout), dout.numel()), "n2f_result_device")
+        rc = lib().n2f_result_device(self.h, job, _ptr(dout), dout.numel())
+        check(self._collected(job, rc), "n2f_result_device")
 
     def cancel(self, job: int) -> int:
         return lib().n2f_cancel(self.h, job)
