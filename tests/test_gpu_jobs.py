@@ -68,6 +68,24 @@ def test_odd_sizes_and_u16_input(n2f):
     assert float(np.max(np.abs(oa - ref))) < 2e-3
 
 
+def test_device_input_and_device_result(n2f):
+    # n2f_submit_device / n2f_result_device: the job fed from device memory gives the host
+    # path's result bit for bit; the binding holds the input tensor until the job is collected
+    import torch
+    _, x = _img(40, 36, 7)
+    p = n2f.params(seed=3, fixed_steps=4, widths=1)
+    with n2f.Context() as ctx:
+        a = ctx.submit(x, p)
+        b = ctx.submit_device(torch.from_numpy(x).cuda(), p)
+        assert b in ctx._dev_inputs
+        assert ctx.wait(a, 120000) == 0 and ctx.wait(b, 120000) == 0
+        oa = ctx.result(a, x.shape)
+        ob = torch.empty(x.shape, dtype=torch.float32, device="cuda")
+        ctx.result_device(b, ob)
+        assert b not in ctx._dev_inputs
+    assert np.array_equal(oa, ob.cpu().numpy())
+
+
 def test_results_do_not_depend_on_the_job_mix(n2f):
     # Each job runs on its own device state and stream with deterministic kernels (fixed
     # reduction orders, no atomics), so a job's output is bit-identical alone and in a mix.
