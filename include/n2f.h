@@ -181,8 +181,9 @@ const char* n2f_strerror(int code);
 int n2f_create(n2f_ctx** out, const n2f_config* cfg);
 /* Stops the scheduler, cancels unfinished jobs and frees everything. */
 void n2f_destroy(n2f_ctx* ctx);
-/* Queues one H x W image (host memory, copied before return); with p->channels = C_0 > 1, C_0
- * planes of H x W. p may be NULL (defaults).
+/* Queues one H x W image (host memory, copied before return) for the whole method (Methods,
+ * "Noise2Fast Implementation Details"); with p->channels = C_0 > 1, C_0 planes of H x W. p may
+ * be NULL (defaults).
  * Errors: EINVAL (NULL, H or W < 2, H*W >= 2^31, non-finite pixel, bad params), ETOOBIG. */
 int n2f_submit(n2f_ctx* ctx, const float* image, int H, int W, const n2f_params* p, n2f_job* out);
 /* Same, for an image already in device memory (this context's device). The library copies it
@@ -200,7 +201,8 @@ int n2f_submit_u16(n2f_ctx* ctx, const uint16_t* image, int H, int W, const n2f_
 int n2f_poll(n2f_ctx* ctx, n2f_job job, n2f_status* st);
 /* Blocks until the job is DONE/FAILED/CANCELED or timeout_ms passes (< 0: no limit). */
 int n2f_wait(n2f_ctx* ctx, n2f_job job, int timeout_ms);
-/* Copies the H*W denoised floats to host memory and releases the job.
+/* Copies the H*W denoised floats (the averaged output of the stopping rule, Methods) to host
+ * memory and releases the job.
  * EAGAIN while queued or running. A FAILED or CANCELED job is released too and its error
  * code (ENONFINITE, EDEVICE, ECANCELED, ...) is returned instead of an image. */
 int n2f_result(n2f_ctx* ctx, n2f_job job, float* out, size_t out_elems);
@@ -239,10 +241,14 @@ int n2f_trainer_create(n2f_trainer** out, const float* image, int H, int W, cons
                        void* stream);          /* image: host memory, p->channels planes */
 void n2f_trainer_destroy(n2f_trainer* tr);
 int n2f_trainer_step(n2f_trainer* tr, int pair); /* one Adam step on pair 0..3 (Methods table) */
-int n2f_trainer_validate(n2f_trainer* tr);       /* full-image forward + MSE + stop rule */
-int n2f_trainer_epoch(n2f_trainer* tr);          /* four steps + validate */
+int n2f_trainer_validate(n2f_trainer* tr); /* full-image forward + MSE + stop rule (Methods,
+                                              validation paragraph) */
+int n2f_trainer_epoch(n2f_trainer* tr);    /* four steps in table order + validate (Methods) */
 int n2f_trainer_run(n2f_trainer* tr, int max_epochs); /* epochs until the rule fires or cap */
-int n2f_trainer_finish(n2f_trainer* tr);         /* computes the output image on the device */
+int n2f_trainer_finish(n2f_trainer* tr); /* the output image on the device: the mean of the
+                                            averaging window (Methods, last sentence of the
+                                            validation paragraph), or the fixed-step run's
+                                            validation output */
 /* Sets the parameters (the flat order of n2f_param_count, rounded to float32) and repacks the
  * kernels' weight copies; EINVAL unless n equals n2f_param_count. Synchronises the stream. */
 int n2f_trainer_set_theta(n2f_trainer* tr, const double* theta, size_t n);
