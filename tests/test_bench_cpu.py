@@ -126,3 +126,14 @@ def test_reference_arm_under_torchrun_prints_once_from_rank_0():
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+
+
+def test_cpu_baseline_scales_one_crop_epoch_to_a_whole_run(monkeypatch):
+    # one epoch on a 128x128 crop taking t seconds stands for (512/128)^2 = 16 times the pixels
+    # and MIN_EPOCHS = 101 epochs (one best epoch + 100 without improvement)
+    monkeypatch.setattr(bench, "oracle_epoch_seconds", lambda noisy, widths, crop=128: 0.5)
+    cb = bench.cpu_baseline(None, 512, 0)
+    assert bench.MIN_EPOCHS == 101
+    assert cb["value"] == pytest.approx(1.0 / (101 * 16 * 0.5))
+    assert cb["unit"] == "images/s" and cb["kind"] == "oracle" and cb["cores"] >= 1
+    assert "128x128" in cb["sample"]
