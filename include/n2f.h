@@ -119,9 +119,12 @@ enum n2f_downsample { N2F_DOWN_CHECKER = 0, N2F_DOWN_QUAD = 1 };
  * moments and epsilon are Kingma & Ba's defaults (the paper cites Adam without them). */
 typedef struct {
   uint32_t struct_size; /* sizeof(n2f_params) */
-  float lr;             /* 1e-3 */
-  float beta1, beta2;   /* 0.9, 0.999 */
-  float eps;            /* 1e-8 */
+  /* Adam's step size and constants, held in double like the method's own values: the kernels
+   * take beta, 1 - beta (formed in double), lr and eps rounded once to float32, and the bias
+   * corrections 1 - beta^t come from powers of the double beta. */
+  double lr;            /* 1e-3 */
+  double beta1, beta2;  /* 0.9, 0.999 */
+  double eps;           /* 1e-8 */
   uint32_t patience;    /* 100 */
   uint32_t max_epochs;  /* safety cap, 0 = none */
   int32_t fixed_steps;  /* -1: stopping rule; k >= 0: k steps (pairs cycled), one validation */
@@ -197,6 +200,12 @@ int n2f_submit_device(n2f_ctx* ctx, const float* dimage, int H, int W, const n2f
  * EINVAL when p->channels > 1). */
 int n2f_submit_u16(n2f_ctx* ctx, const uint16_t* image, int H, int W, const n2f_params* p,
                    n2f_job* out);
+/* Device bytes a job of this size and parameters holds while it is admitted: the amount the
+ * scheduler counts against n2f_config.hbm_budget_bytes (weights, Adam moments, the training
+ * activations of the larger sub-image, the validation buffers, the output sum and history).
+ * Touches no device. EINVAL for a NULL bytes pointer, bad params or image size; ENOTSUP for a
+ * combination this build does not provide. */
+int n2f_job_bytes(int H, int W, const n2f_params* p, uint64_t* bytes);
 /* Status snapshot; never blocks. */
 int n2f_poll(n2f_ctx* ctx, n2f_job job, n2f_status* st);
 /* Blocks until the job is DONE/FAILED/CANCELED or timeout_ms passes (< 0: no limit). */
@@ -210,6 +219,16 @@ int n2f_result(n2f_ctx* ctx, n2f_job job, float* out, size_t out_elems);
 int n2f_result_device(n2f_ctx* ctx, n2f_job job, float* dout, size_t out_elems);
 /* Cancels a queued or running job; its resources are freed by the scheduler. */
 int n2f_cancel(n2f_ctx* ctx, n2f_job job);
+/* The job's validation history (Methods, validation paragraph: one full-image MSE per epoch,
+ * the scores the stopping rule decides on), kept on the device while the job runs and copied
+ * out with its result: the scores of epochs first..epoch, oldest first, at most N2F_HIST_CAP
+ * (the latest ones). *n_out receives the count and *first_epoch (may be NULL) the 1-based
+ * epoch of out[0]; out may be NULL to query the count. Available once the job is DONE and
+ * until its result is collected; EAGAIN while it is queued or running, ENOENT for an unknown
+ * or collected job, EINVAL if cap is below the count or the job did not finish (FAILED,
+ * CANCELED). A fixed-step job takes no scores under the rule: count 0. */
+int n2f_history(n2f_ctx* ctx, n2f_job job, double* out, size_t cap, size_t* n_out,
+                uint32_t* first_epoch);
 
 typedef struct {
   uint32_t struct_size;
@@ -260,13 +279,35 @@ enum n2f_export {
   N2F_X_PAIR = 8,   /* sub-image 0..3 = up_e, up_o, lf_e, lf_o (all input planes) */
   N2F_X_VAL = 9,    /* last validation output, H*W */
   N2F_X_SUM = 10,   /* running output sum, H*W */
-  N2F_X_OUT = 11    /* output image (after n2f_trainer_finish), H*W */
+  N2F_X_OUT = 11,   /* output image (after n2f_trainer_finish), H*W */
+  N2F_X_HIST = 12,  /* validation scores (FP64 MSE, Methods' validation paragraph) of the last
+                       min(epoch, N2F_HIST_CAP) epochs under the stopping rule, oldest first */
+  N2F_X_VBEST = 13  /* validation output of the best epoch, H*W */
 };
+/* Epochs of validation scores each job keeps on the device (a ring; older epochs are
+ * overwritten). */
+#define N2F_HIST_CAP 4096
 /* Returns the number of values through *n_out; out may be NULL to query the size. EINVAL for an
  * unknown `what`, a layer index outside 1..8 or a pair outside 0..3, or cap below the size. */
 int n2f_trainer_export(n2f_trainer* tr, int what, int index, double* out, size_t cap,
                        size_t* n_out);
 int n2f_trainer_status(n2f_trainer* tr, n2f_status* st);
+/* Loads one part of the job's state from host doubles (rounded to float32), the inverse of
+ * n2f_trainer_export for: N2F_X_THETA (then the kernels' weight copies are repacked, as by
+ * n2f_trainer_set_theta), N2F_X_ADAM_M, N2F_X_ADAM_V (flat, n2f_param_count values),
+ * N2F_X_SUM and N2F_X_VBEST (H*W). With n2f_trainer_set_progress it puts a trainer in any
+ * state the method passes through (Methods: Adam moments, the stopping rule's best score and
+ * count, the running output sum), so that an epoch can be compared with another
+ * implementation's epoch from the same state. index is unused (0). EINVAL for another `what`
+ * or n not equal to the size. Synchronises the stream. */
+int n2f_trainer_import(n2f_trainer* tr, int what, int index, const double* in, size_t n);
+/* Sets the step and stopping-rule counters: t Adam steps taken (bias corrections 1 - beta^t),
+ * `epoch` epochs validated, `since` epochs since the best, `best` the best validation score
+ * (+inf: none yet); the job is marked running. Validation scores recorded before keep their
+ * places in the N2F_X_HIST ring. EINVAL in fixed-step mode or for since > epoch.
+ * Synchronises the stream. */
+int n2f_trainer_set_progress(n2f_trainer* tr, uint32_t t, uint32_t epoch, uint32_t since,
+                             double best);
 uint64_t n2f_trainer_launches(const n2f_trainer* tr);
 
 /* Number of parameters of the network (n2f_widths). */
@@ -330,8 +371,13 @@ int n2f_conv3x3_wgrad(int engine, int precision, const void* dout, const void* i
  *    that device current; make that first call before any stream capture on that device.
  *  - All calls share the one array and it keeps the last call's contents: calls that can overlap
  *    on the GPU (different streams, or several host threads) race and must be serialised.
- *  - A layer needs 9*C_in*C_out + 1025*C_out + 64 floats of the 4 Mi-float array; larger layers
- *    return N2F_ETOOBIG. Synchronises the stream; N2F_ETIMEDOUT if a kernel wait ran out. */
+ *  - The address is looked up once per device and kept: after cudaDeviceReset on a device the
+ *    cached address is stale, so a process that resets a device must not call this entry point
+ *    on that device again.
+ *  - A layer needs 9*C_in*C_out + C_out + 64 floats (one split of the pixel sum) of the
+ *    4 Mi-float array, less 64 floats the library keeps for its error and magnitude words;
+ *    larger layers return N2F_ETOOBIG. Layers that leave room use several splits.
+ *    Synchronises the stream; N2F_ETIMEDOUT if a kernel wait ran out. */
 int n2f_conv3x3_wgrad_noalloc(int engine, int precision, const void* dout, const void* in, int cin,
                               int cout, int H, int W, float* dw, float* db, void* stream);
 

@@ -39,10 +39,10 @@ void n2f_config_default(n2f_config* c) {
 void n2f_params_default(n2f_params* p) {
   memset(p, 0, sizeof(*p));
   p->struct_size = sizeof(n2f_params);
-  p->lr = 1e-3f;
-  p->beta1 = 0.9f;
-  p->beta2 = 0.999f;
-  p->eps = 1e-8f;
+  p->lr = 1e-3;
+  p->beta1 = 0.9;
+  p->beta2 = 0.999;
+  p->eps = 1e-8;
   p->patience = 100;
   p->max_epochs = 0;
   p->fixed_steps = -1;
@@ -89,8 +89,8 @@ static int check_params(const n2f_params* p) {
   if (p->loss != N2F_LOSS_BCE && p->loss != N2F_LOSS_MSE) return N2F_EINVAL;
   if (p->widths != N2F_WIDTHS_PLIT && p->widths != N2F_WIDTHS_W64) return N2F_EINVAL;
   if (p->engine < N2F_ENGINE_AUTO || p->engine > N2F_ENGINE_TC) return N2F_EINVAL;
-  if (!(p->lr > 0.f) || !(p->beta1 >= 0.f && p->beta1 < 1.f) ||
-      !(p->beta2 >= 0.f && p->beta2 < 1.f) || !(p->eps > 0.f))
+  if (!(p->lr > 0.0 && p->lr < 1e30) || !(p->beta1 >= 0.0 && p->beta1 < 1.0) ||
+      !(p->beta2 >= 0.0 && p->beta2 < 1.0) || !(p->eps > 0.0 && p->eps < 1e30))
     return N2F_EINVAL;
   if (p->fixed_steps < 0 && p->patience < 1) return N2F_EINVAL;
   if (p->incl_best && p->patience < 2) return N2F_EINVAL;
@@ -244,9 +244,20 @@ static int export_cg(Trainer* t, const void* cg, int C, int h, int w, double* ou
   return rc;
 }
 
+// The ring holds the score of epoch e at (e - 1) % kHistCap: writes the last min(end, kHistCap)
+// of epochs 1..end oldest first.
+static void hist_unroll(const double* ring, int end, double* out) {
+  const int n = std::min(end, kHistCap);
+  for (int k = 0; k < n; ++k) {
+    const int e = end - n + 1 + k;  // 1-based epoch
+    out[k] = ring[(e - 1) % kHistCap];
+  }
+}
+
 extern "C" int n2f_trainer_export(n2f_trainer* tr, int what, int index, double* out, size_t cap,
                                   size_t* n_out) {
   if (!tr) return N2F_EINVAL;
+  int hist_end = 0;
   Trainer* t = &tr->t;
   const int h = t->ph[t->last_pair], w = t->pw[t->last_pair];
   size_t n = 0;
@@ -261,7 +272,15 @@ extern "C" int n2f_trainer_export(n2f_trainer* tr, int what, int index, double* 
       if (index < 0 || index > 3) return N2F_EINVAL;
       n = (size_t)t->net.c0 * t->ph[index] * t->pw[index];
       break;
-    case N2F_X_VAL: case N2F_X_SUM: case N2F_X_OUT: n = t->N; break;
+    case N2F_X_VAL: case N2F_X_SUM: case N2F_X_OUT: case N2F_X_VBEST: n = t->N; break;
+    case N2F_X_HIST: {
+      DevState s;
+      const int rc = trainer_read_state(t, &s);
+      if (rc) return rc;
+      n = (size_t)std::min(s.epoch, kHistCap);
+      hist_end = s.epoch;
+      break;
+    }
     default: return N2F_EINVAL;
   }
   if (n_out) *n_out = n;
@@ -279,8 +298,71 @@ extern "C" int n2f_trainer_export(n2f_trainer* tr, int what, int index, double* 
     case N2F_X_VAL: return export_floats(t->st, t->V, n, out);
     case N2F_X_SUM: return export_floats(t->st, t->S, n, out);
     case N2F_X_OUT: return export_floats(t->st, t->out, n, out);
+    case N2F_X_VBEST: return export_floats(t->st, t->Vbest, n, out);
+    case N2F_X_HIST: {
+      std::vector<double> ring(kHistCap);
+      CKR(cudaMemcpyAsync(ring.data(), t->hist, kHistCap * sizeof(double), cudaMemcpyDeviceToHost,
+                          t->st));
+      CKR(cudaStreamSynchronize(t->st));
+      hist_unroll(ring.data(), hist_end, out);
+      return N2F_OK;
+    }
   }
   return N2F_EINVAL;
+}
+
+static int import_floats(cudaStream_t st, float* d, const double* in, size_t n) {
+  std::vector<float> f(n);
+  for (size_t i = 0; i < n; ++i) f[i] = (float)in[i];
+  CKR(cudaMemcpyAsync(d, f.data(), n * sizeof(float), cudaMemcpyHostToDevice, st));
+  CKR(cudaStreamSynchronize(st));
+  return N2F_OK;
+}
+
+extern "C" int n2f_trainer_import(n2f_trainer* tr, int what, int index, const double* in,
+                                  size_t n) {
+  (void)index;
+  if (!tr || !in) return N2F_EINVAL;
+  Trainer* t = &tr->t;
+  switch (what) {
+    case N2F_X_THETA: return n2f_trainer_set_theta(tr, in, n);
+    case N2F_X_ADAM_M: case N2F_X_ADAM_V:
+      if (n != t->net.count) return N2F_EINVAL;
+      return import_floats(t->st, what == N2F_X_ADAM_M ? t->m : t->v, in, n);
+    case N2F_X_SUM: case N2F_X_VBEST:
+      if (n != t->N) return N2F_EINVAL;
+      return import_floats(t->st, what == N2F_X_SUM ? t->S : t->Vbest, in, n);
+  }
+  return N2F_EINVAL;
+}
+
+extern "C" int n2f_trainer_set_progress(n2f_trainer* tr, uint32_t steps, uint32_t epoch,
+                                        uint32_t since, double best) {
+  if (!tr) return N2F_EINVAL;
+  Trainer* t = &tr->t;
+  if (t->fixed_mode || since > epoch || epoch > (uint32_t)INT32_MAX || steps > (uint32_t)INT32_MAX)
+    return N2F_EINVAL;
+  DevState s;
+  int rc = trainer_read_state(t, &s);
+  if (rc) return rc;
+  s.t = (int)steps;
+  // beta^t by repeated products, as the step kernel forms it one step at a time
+  s.b1t = 1.0;
+  s.b2t = 1.0;
+  for (uint32_t k = 0; k < steps; ++k) {
+    s.b1t *= t->prm.beta1;
+    s.b2t *= t->prm.beta2;
+  }
+  s.bc1 = (float)(1.0 - s.b1t);
+  s.bc2 = (float)(1.0 - s.b2t);
+  s.epoch = (int)epoch;
+  s.since = (int)since;
+  s.best = best;
+  s.stopped = 0;
+  s.decision = -1;
+  CKR(cudaMemcpyAsync(t->state, &s, sizeof(DevState), cudaMemcpyHostToDevice, t->st));
+  CKR(cudaStreamSynchronize(t->st));
+  return N2F_OK;
 }
 
 extern "C" int n2f_trainer_status(n2f_trainer* tr, n2f_status* st) {
@@ -455,6 +537,7 @@ struct Job {
   uint16_t* pin_u16 = nullptr;
   const float* dev_in = nullptr;
   float* pin_out = nullptr;
+  double* pin_hist = nullptr;  // the device history ring, copied out with the result
   std::atomic<int> state{N2F_QUEUED};
   int error = 0;
   bool cancel = false;
@@ -532,6 +615,8 @@ static void free_job_host(Job* j) {
   if (j->pin_u16) cudaFreeHost(j->pin_u16);
   if (j->pin_out) cudaFreeHost(j->pin_out);
   if (j->hst) cudaFreeHost(j->hst);
+  if (j->pin_hist) cudaFreeHost(j->pin_hist);
+  j->pin_hist = nullptr;
   j->pin_in = nullptr;
   j->pin_u16 = nullptr;
   j->pin_out = nullptr;
@@ -586,6 +671,7 @@ static int admit(n2f_ctx* c, Job* j) {
   for (int k = 0; k < j->ring; ++k) CKR(cudaEventCreateWithFlags(&j->ev_ep[k], cudaEventDisableTiming));
   CKR(cudaMallocHost((void**)&j->hst, sizeof(DevState) * j->ring));
   CKR(cudaMallocHost((void**)&j->pin_out, sizeof(float) * (size_t)j->H * j->W));
+  CKR(cudaMallocHost((void**)&j->pin_hist, sizeof(double) * kHistCap));
   int rc = trainer_init(&j->tr, c->al, j->st, j->src_kind == 2);
   if (rc) return rc;
   CKR(cudaEventRecord(j->ev_start, j->st));
@@ -753,6 +839,8 @@ static bool progress(n2f_ctx* c, Job* j) {
       if (e == cudaSuccess) e = cudaMemcpyAsync(j->pin_out, j->tr.out, sizeof(float) * j->tr.N, cudaMemcpyDeviceToHost,
                           j->st);
       if (e == cudaSuccess) e = cudaMemcpyAsync(&j->hst[0], j->tr.state, sizeof(DevState),
+                                                cudaMemcpyDeviceToHost, j->st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(j->pin_hist, j->tr.hist, sizeof(double) * kHistCap,
                                                 cudaMemcpyDeviceToHost, j->st);
       if (e == cudaSuccess) e = cudaEventRecord(j->ev_done, j->st);
       if (e != cudaSuccess) rc = set_cuda_error(e, "result enqueue");
@@ -1022,6 +1110,20 @@ extern "C" int n2f_submit_u16(n2f_ctx* c, const uint16_t* image, int H, int W,
   return submit_common(c, 2, image, H, W, p, out);
 }
 
+extern "C" int n2f_job_bytes(int H, int W, const n2f_params* p, uint64_t* bytes) {
+  if (!bytes) return N2F_EINVAL;
+  n2f_params def;
+  n2f_params_default(&def);
+  if (!p) p = &def;
+  int rc = check_params(p);
+  if (rc) return rc;
+  if ((rc = check_image(H, W))) return rc;
+  Trainer t;
+  if ((rc = trainer_configure(&t, H, W, p, 0))) return rc;
+  *bytes = trainer_bytes(H, W, p, 0);
+  return N2F_OK;
+}
+
 static Job* find(n2f_ctx* c, n2f_job id) {
   auto it = c->jobs.find(id);
   return it == c->jobs.end() ? nullptr : it->second;
@@ -1098,6 +1200,25 @@ extern "C" int n2f_result(n2f_ctx* c, n2f_job id, float* out, size_t out_elems) 
 }
 extern "C" int n2f_result_device(n2f_ctx* c, n2f_job id, float* dout, size_t out_elems) {
   return take_result(c, id, dout, out_elems, true);
+}
+
+extern "C" int n2f_history(n2f_ctx* c, n2f_job id, double* out, size_t cap, size_t* n_out,
+                           uint32_t* first_epoch) {
+  if (!c || !n_out) return N2F_EINVAL;
+  std::lock_guard<std::mutex> g(c->mu);
+  Job* j = find(c, id);
+  if (!j) return N2F_ENOENT;
+  const int s = j->state.load();
+  if (s < N2F_DONE) return N2F_EAGAIN;
+  if (s != N2F_DONE || !j->pin_hist) return N2F_EINVAL;
+  const int end = j->prm.fixed_steps >= 0 ? 0 : j->last.epoch;
+  const size_t n = (size_t)std::min(end, kHistCap);
+  *n_out = n;
+  if (first_epoch) *first_epoch = (uint32_t)(end - (int)n + 1);
+  if (!out) return N2F_OK;
+  if (cap < n) return N2F_EINVAL;
+  hist_unroll(j->pin_hist, end, out);
+  return N2F_OK;
 }
 
 extern "C" int n2f_cancel(n2f_ctx* c, n2f_job id) {

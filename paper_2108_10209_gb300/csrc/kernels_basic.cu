@@ -261,8 +261,8 @@ __device__ __forceinline__ void pack_param(const PackArgs& pa, int l, unsigned l
 // collects it (pa.sw->wnew, by step parity) and k_pack_f16 writes those copies; it also clears
 // the activation and delta words for the next pass and the other parity's weight words.
 __global__ void k_adam(PackArgs pa, const float* __restrict__ grad, float* __restrict__ m,
-                       float* __restrict__ v, float lr, float b1, float b2, float eps,
-                       const DevState* __restrict__ state, int update) {
+                       float* __restrict__ v, AdamConsts k, const DevState* __restrict__ state,
+                       int update) {
   if (update && state->stopped) return;
   __shared__ unsigned smax[kLayers];
   ScaleWords* sw = pa.sw;
@@ -283,11 +283,11 @@ __global__ void k_adam(PackArgs pa, const float* __restrict__ grad, float* __res
       float th = pa.theta[i];
       if (update) {
         const float g = grad[i];
-        const float mi = b1 * m[i] + (1.f - b1) * g;
-        const float vi = b2 * v[i] + (1.f - b2) * g * g;
+        const float mi = k.b1 * m[i] + k.omb1 * g;
+        const float vi = k.b2 * v[i] + k.omb2 * g * g;
         m[i] = mi;
         v[i] = vi;
-        th -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+        th -= k.lr * (mi / bc1) / (sqrtf(vi / bc2) + k.eps);
         pa.theta[i] = th;
       }
       const int l = weight_layer(pa, i);
@@ -395,12 +395,22 @@ cudaError_t launch_pack_layer(const float* w, int cin, int cout, float* fwd, flo
   N2F_LAUNCH_CHECK();
 }
 
-cudaError_t launch_adam(const PackArgs& pa, const float* grad, float* m, float* v, float lr,
-                        float b1, float b2, float eps, const DevState* state, int update,
-                        cudaStream_t st) {
+AdamConsts adam_consts(double lr, double b1, double b2, double eps) {
+  AdamConsts k;
+  k.lr = (float)lr;
+  k.b1 = (float)b1;
+  k.omb1 = (float)(1.0 - b1);  // formed in double: 1 - float(b) would round b first
+  k.b2 = (float)b2;
+  k.omb2 = (float)(1.0 - b2);
+  k.eps = (float)eps;
+  return k;
+}
+
+cudaError_t launch_adam(const PackArgs& pa, const float* grad, float* m, float* v,
+                        const AdamConsts& k, const DevState* state, int update, cudaStream_t st) {
   unsigned g = nblocks(pa.count, 256);
   if (g > 152u * 8) g = 152u * 8;
-  k_adam<<<g, 256, 0, st>>>(pa, grad, m, v, lr, b1, b2, eps, state, update);
+  k_adam<<<g, 256, 0, st>>>(pa, grad, m, v, k, state, update);
   count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !pa.sw) return e;
@@ -695,8 +705,9 @@ __global__ void __launch_bounds__(256) k_head_train(const T* __restrict__ a8, in
   __shared__ double sl[8];
   for (int i = threadIdx.x; i < C; i += blockDim.x) sw[i] = w9[i];
   __syncthreads();
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool live = p < npx;
+  // unsigned: the last block may reach past 2^31 - 1 when npx is close to it
+  const unsigned p = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = p < (unsigned)npx;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float z = b9[0];
   if (live)
@@ -798,7 +809,7 @@ cudaError_t launch_head_train(const void* a8, int C, int npx, const float* w9, c
 // per-block loss partials) and Adam's step counter and bias corrections.
 __global__ void k_step_finish(const float* __restrict__ hpart, const double* __restrict__ lpart,
                               int nblk, int C, int npx, float* __restrict__ gw9, DevState* state,
-                              float b1, float b2) {
+                              double b1, double b2) {
   if (state->stopped) return;
   if ((int)blockIdx.x <= C) {
     __shared__ float shf[256];
@@ -826,16 +837,16 @@ __global__ void k_step_finish(const float* __restrict__ hpart, const double* __r
   if (threadIdx.x == 0) {
     state->loss = sh[0] / (double)npx;
     state->t += 1;
-    state->b1t *= (double)b1;
-    state->b2t *= (double)b2;
+    state->b1t *= b1;
+    state->b2t *= b2;
     state->bc1 = (float)(1.0 - state->b1t);
     state->bc2 = (float)(1.0 - state->b2t);
   }
 }
 
 cudaError_t launch_step_finish(const float* hpart, const double* loss_part, int nblk, int C,
-                               int npx, float* gw9, float* gb9, DevState* state, float b1,
-                               float b2, cudaStream_t st) {
+                               int npx, float* gw9, float* gb9, DevState* state, double b1,
+                               double b2, cudaStream_t st) {
   // gw9[0..C) and gb9 (= gw9 + C in the flat vector) are the columns of hpart
   if (gb9 != gw9 + C) return cudaErrorInvalidValue;
   k_step_finish<<<C + 2, 256, 0, st>>>(hpart, loss_part, nblk, C, npx, gw9, state, b1, b2);
@@ -858,9 +869,9 @@ __global__ void __launch_bounds__(256) k_head_val(const T* __restrict__ a8, int 
   __shared__ double sl[8];
   for (int i = threadIdx.x; i < C; i += blockDim.x) sw[i] = w9[i];
   __syncthreads();
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned p = blockIdx.x * blockDim.x + threadIdx.x;  // see k_head_train
   double e2 = 0.0;
-  if (p < npx) {
+  if (p < (unsigned)npx) {
     float z = b9[0];
     for (int g = 0; g < C / G; ++g) {
       float v[G];
@@ -901,7 +912,7 @@ cudaError_t launch_head_val(const void* a8, int C, int npx, const float* w9, con
 // Stop rule (Methods: terminate once one hundred epochs pass without improving the best
 // validation score). Strict improvement; the first epoch always sets the best.
 __global__ void k_val_decide(const double* __restrict__ part, int nblk, double npx,
-                             DevState* state, int fixed_mode) {
+                             DevState* state, int fixed_mode, double* __restrict__ hist) {
   __shared__ double sp[256];
   double s = 0.0;
   for (int k = threadIdx.x; k < nblk; k += blockDim.x) s += part[k];
@@ -926,6 +937,7 @@ __global__ void k_val_decide(const double* __restrict__ part, int nblk, double n
     return;
   }
   state->epoch += 1;
+  if (hist) hist[(state->epoch - 1) % kHistCap] = mse;  // the job's validation history
   if (mse < state->best) {
     state->best = mse;
     state->since = 0;
@@ -941,8 +953,8 @@ __global__ void k_val_decide(const double* __restrict__ part, int nblk, double n
 }
 
 cudaError_t launch_val_decide(const double* mse_part, int nblk, size_t npx, DevState* state,
-                              int fixed_mode, cudaStream_t st) {
-  k_val_decide<<<1, 256, 0, st>>>(mse_part, nblk, (double)npx, state, fixed_mode);
+                              int fixed_mode, double* hist, cudaStream_t st) {
+  k_val_decide<<<1, 256, 0, st>>>(mse_part, nblk, (double)npx, state, fixed_mode, hist);
   N2F_LAUNCH_CHECK();
 }
 

@@ -93,11 +93,15 @@ cudaError_t launch_gather(const float* x, int H, int W, float* ue, float* uo, fl
                           cudaStream_t st);
 cudaError_t launch_u16_to_f32(const uint16_t* in, float* out, size_t n, cudaStream_t st);
 cudaError_t launch_init_params(float* theta, const NetShape& net, uint64_t seed, cudaStream_t st);
+// Adam's constants as the float32 kernel uses them: beta, 1 - beta formed in double, lr, eps.
+struct AdamConsts {
+  float lr, b1, omb1, b2, omb2, eps;
+};
+AdamConsts adam_consts(double lr, double b1, double b2, double eps);
 // Adam step (update = 1) or a plain repack (update = 0), then, in the float32 form, the fp16
 // tensor-core copies (k_pack_f16). With update = 0 the caller clears pa.sw->wnew first.
-cudaError_t launch_adam(const PackArgs& pa, const float* grad, float* m, float* v, float lr,
-                        float b1, float b2, float eps, const DevState* state, int update,
-                        cudaStream_t st);
+cudaError_t launch_adam(const PackArgs& pa, const float* grad, float* m, float* v,
+                        const AdamConsts& k, const DevState* state, int update, cudaStream_t st);
 // One canonical weight tensor into its operand copies. Float32 form: wmax (device word, zeroed
 // by the caller) receives the tensor's largest magnitude and the fp16 parts are scaled by it.
 cudaError_t launch_pack_layer(const float* w, int cin, int cout, float* fwd, float* dgr, void* tcf,
@@ -196,15 +200,17 @@ cudaError_t launch_head_train(const void* a8, int C, int npx, const float* w9, c
                               const int* skip, cudaStream_t st);
 // Sums head-grad and loss partials in a fixed order, advances the Adam step counter (one launch).
 cudaError_t launch_step_finish(const float* hpart, const double* loss_part, int nblk, int C,
-                               int npx, float* gw9, float* gb9, DevState* state, float b1,
-                               float b2, cudaStream_t st);
+                               int npx, float* gw9, float* gb9, DevState* state, double b1,
+                               double b2, cudaStream_t st);
 // Head, validation: V = sigmoid(z), FP64 partial sums of (V - x)^2.
 cudaError_t launch_head_val(const void* a8, int C, int npx, const float* w9, const float* b9,
                             const float* x, int bf16, float* V, double* mse_part, int* nblk_out,
                             const int* skip, cudaStream_t st);
-// Stop rule: reduce the MSE partials (fixed order), update best/since/epoch/stopped.
+// Stop rule: reduce the MSE partials (fixed order), update best/since/epoch/stopped, and
+// record the score in the history ring (kHistCap doubles; may be null) at (epoch - 1) % kHistCap.
+constexpr int kHistCap = N2F_HIST_CAP;
 cudaError_t launch_val_decide(const double* mse_part, int nblk, size_t npx, DevState* state,
-                              int fixed_mode, cudaStream_t st);
+                              int fixed_mode, double* hist, cudaStream_t st);
 // Output averaging: S = 0 / V (new best) or S += V; Vbest = V on a new best.
 cudaError_t launch_val_accum(const float* V, float* S, float* Vbest, size_t n,
                              const DevState* state, cudaStream_t st);

@@ -20,6 +20,10 @@ constexpr size_t kScratchFloats = (size_t)4 << 20;
 constexpr size_t kErrFloats = 64;
 static __device__ __align__(256) float g_wgrad_scratch[kScratchFloats];
 
+// The address is cached per device ordinal for the life of the process. cudaDeviceReset on a
+// device destroys its context and with it the array's old address: a process that resets a
+// device and then calls this entry point again on it would pass a stale pointer, so such
+// processes must not use this entry point after the reset.
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 float* g_addr[kMaxDevices] = {};
@@ -52,8 +56,10 @@ extern "C" int n2f_conv3x3_wgrad_noalloc(int engine, int precision, const void* 
     return N2F_EINVAL;
   if (engine < N2F_ENGINE_AUTO || engine > N2F_ENGINE_TC) return N2F_EINVAL;
   if (precision != N2F_FP32 && precision != N2F_BF16) return N2F_EINVAL;
-  // at least one split of the pixel sum plus the bias partials must fit the array
-  const size_t need = (size_t)9 * cin * cout + (size_t)cout + (size_t)1024 * cout + 64;
+  // one split of the pixel sum (its weight and bias partials) must fit the array; the
+  // tensor-core launcher also keeps up to 63 floats of alignment padding before the bias
+  // partials, which the 64 covers; more splits are used when they fit
+  const size_t need = (size_t)9 * cin * cout + (size_t)cout + 64;
   if (need > kScratchFloats - kErrFloats) {
     tl_error = "n2f_conv3x3_wgrad_noalloc: layer too large for the fixed 16 MiB workspace";
     return N2F_ETOOBIG;

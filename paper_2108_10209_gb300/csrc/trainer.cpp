@@ -233,6 +233,7 @@ static size_t layout(Trainer* t, char* base) {
   t->wpart_cap = (size_t)16 << 20;
   t->wpart = c.take<float>(t->wpart_cap);
   t->state = c.take<DevState>(1);
+  t->hist = c.take<double>(kHistCap);
   t->in_u16 = c.take<uint16_t>(t->want_u16 ? t->N : 0);
   return align_up(c.off, 256);
 }
@@ -359,6 +360,8 @@ int trainer_start(Trainer* t, int from_u16) {
   CK(cudaMemsetAsync(t->S, 0, t->N * sizeof(float), st));
   CK(cudaMemsetAsync(t->Vbest, 0, t->N * sizeof(float), st));
   CK(cudaMemsetAsync(t->V, 0, t->N * sizeof(float), st));
+  // all-ones bytes: the history ring starts as NaN (no score recorded)
+  CK(cudaMemsetAsync(t->hist, 0xff, kHistCap * sizeof(double), st));
   DevState s;
   memset(&s, 0, sizeof(s));
   s.best = INFINITY;
@@ -372,7 +375,7 @@ int trainer_start(Trainer* t, int from_u16) {
   t->hstate_init = s;
   CK(cudaMemcpyAsync(t->state, &t->hstate_init, sizeof(DevState), cudaMemcpyHostToDevice, st));
   if (t->sw) CK(cudaMemsetAsync(t->sw, 0, sizeof(ScaleWords), st));
-  CK(launch_adam(t->pa, t->grad, t->m, t->v, 0.f, 0.f, 0.f, 0.f, t->state, 0, st));
+  CK(launch_adam(t->pa, t->grad, t->m, t->v, AdamConsts{}, t->state, 0, st));
   return N2F_OK;
 }
 
@@ -380,7 +383,7 @@ int trainer_repack(Trainer* t) {
   LaunchScope ls(&t->launches);
   // the largest weights are collected afresh for the new parameters
   if (t->sw) CK(cudaMemsetAsync(t->sw->wnew, 0, sizeof(t->sw->wnew), t->st));
-  CK(launch_adam(t->pa, t->grad, t->m, t->v, 0.f, 0.f, 0.f, 0.f, t->state, 0, t->st));
+  CK(launch_adam(t->pa, t->grad, t->m, t->v, AdamConsts{}, t->state, 0, t->st));
   return N2F_OK;
 }
 
@@ -518,8 +521,9 @@ static int step_dgrad(Trainer* t, int pair, int l) {
 
 static int step_adam(Trainer* t) {
   Timed tm(t, N2F_K_ADAM, 0.0, (double)t->net.count * 4.0 * 9, 0);
-  CK(launch_adam(t->pa, t->grad, t->m, t->v, t->prm.lr, t->prm.beta1, t->prm.beta2, t->prm.eps,
-                 t->state, 1, t->st));
+  CK(launch_adam(t->pa, t->grad, t->m, t->v,
+                 adam_consts(t->prm.lr, t->prm.beta1, t->prm.beta2, t->prm.eps), t->state, 1,
+                 t->st));
   return N2F_OK;
 }
 
@@ -556,7 +560,7 @@ static int val_finish(Trainer* t) {
                        t->x + (size_t)t->prm.target_channel * t->N, t->bf16, t->V, t->mpart,
                        &nblk, skip, t->st));
   }
-  CK(launch_val_decide(t->mpart, nblk, t->N, t->state, t->fixed_mode, t->st));
+  CK(launch_val_decide(t->mpart, nblk, t->N, t->state, t->fixed_mode, t->hist, t->st));
   if (!t->fixed_mode) CK(launch_val_accum(t->V, t->S, t->Vbest, t->N, t->state, t->st));
   t->vals_enqueued += 1;
   return N2F_OK;

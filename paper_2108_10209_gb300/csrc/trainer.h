@@ -86,6 +86,7 @@ struct Trainer {
   size_t wpart_cap = 0;
   int nblk_max = 0;
   DevState* state = nullptr;
+  double* hist = nullptr;    // validation scores by epoch, a ring of kHistCap
   ScaleWords* sw = nullptr;  // float32 form: tensor magnitudes for the fp16 operand scales
   uint16_t* in_u16 = nullptr;
   DevState hstate_init;

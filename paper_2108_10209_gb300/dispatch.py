@@ -52,3 +52,118 @@ class LeastLoaded:
         self.load[g] -= work
         heapq.heappush(self.heap, (self.load[g], g))
         return g
+
+
+class MultiContext:
+    """Serving front end over several GPUs in one process: one library context per device (each
+    with its own scheduler, HBM budget and slots), every arriving image assigned on arrival to
+    the device with the least outstanding work (LeastLoaded; work = pixels x planes, the
+    per-epoch cost; the epochs a job will take are not known in advance), its status, history
+    and result fetched from that device. A job's work is returned to its device once a final
+    state is seen (poll, wait or result). Images are independent, so no data crosses devices.
+
+    make_context(device) builds a context object with the methods of n2f.Context (submit,
+    submit_u16, poll, wait, result, history, cancel, close); the default builds n2f.Context
+    with **ctx_kw."""
+
+    FINAL = (2, 3, 4)  # N2F_DONE, N2F_FAILED, N2F_CANCELED
+
+    def __init__(self, devices, make_context=None, **ctx_kw):
+        if not devices:
+            raise ValueError("at least one device")
+        if make_context is None:
+            from . import n2f
+
+            def make_context(dev):
+                return n2f.Context(device=dev, **ctx_kw)
+        self.devices = list(devices)
+        self.ctxs = [make_context(d) for d in self.devices]
+        self.sched = LeastLoaded(len(self.devices))
+        self.jobs = {}  # front-end id -> (context index, the context's job id)
+        self.next_id = 1
+
+    def _add(self, work, submit):
+        jid = self.next_id
+        g = self.sched.assign(jid, float(work))
+        try:
+            cid = submit(self.ctxs[g])
+        except Exception:
+            self.sched.done(jid)
+            raise
+        self.next_id += 1
+        self.jobs[jid] = (g, cid)
+        return jid
+
+    @staticmethod
+    def _work(shape):
+        n = 1
+        for s in shape:
+            n *= int(s)
+        return n
+
+    def submit(self, image, p=None) -> int:
+        return self._add(self._work(image.shape), lambda c: c.submit(image, p))
+
+    def submit_u16(self, image, p=None) -> int:
+        return self._add(self._work(image.shape), lambda c: c.submit_u16(image, p))
+
+    def device_of(self, jid) -> int:
+        return self.devices[self.jobs[jid][0]]
+
+    def _release(self, jid):
+        if jid in self.sched.where:
+            self.sched.done(jid)
+
+    def poll(self, jid):
+        g, cid = self.jobs[jid]
+        st = self.ctxs[g].poll(cid)
+        if st.state in self.FINAL:
+            self._release(jid)
+        return st
+
+    def wait(self, jid, timeout_ms: int = -1) -> int:
+        g, cid = self.jobs[jid]
+        rc = self.ctxs[g].wait(cid, timeout_ms)
+        if rc == 0:
+            self._release(jid)
+        return rc
+
+    def result(self, jid, shape):
+        """The job's output; the job is released from its device and this front end unless the
+        call failed with EAGAIN (still running) or EINVAL (a wrong size: nothing released)."""
+        g, cid = self.jobs[jid]
+        try:
+            out = self.ctxs[g].result(cid, shape)
+        except Exception as e:
+            if getattr(e, "code", None) not in (-3, -1):  # N2F_EAGAIN, N2F_EINVAL
+                self._forget(jid)
+            raise
+        self._forget(jid)
+        return out
+
+    def _forget(self, jid):
+        self._release(jid)
+        self.jobs.pop(jid, None)
+
+    def history(self, jid):
+        g, cid = self.jobs[jid]
+        return self.ctxs[g].history(cid)
+
+    def cancel(self, jid) -> int:
+        g, cid = self.jobs[jid]
+        return self.ctxs[g].cancel(cid)
+
+    def load(self):
+        """Outstanding work per device, in the order of `devices`."""
+        return list(self.sched.load)
+
+    def close(self):
+        for c in self.ctxs:
+            c.close()
+        self.ctxs = []
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -25,7 +25,9 @@ N2F_ENGINE_AUTO, N2F_ENGINE_SIMT, N2F_ENGINE_TC = 0, 1, 2
 N2F_DOWN_CHECKER, N2F_DOWN_QUAD = 0, 1
 N2F_QUEUED, N2F_RUNNING, N2F_DONE, N2F_FAILED, N2F_CANCELED = range(5)
 (N2F_X_THETA, N2F_X_GRAD, N2F_X_ADAM_M, N2F_X_ADAM_V, N2F_X_ACT, N2F_X_DELTA) = range(6)
-N2F_X_DZ, N2F_X_PAIR, N2F_X_VAL, N2F_X_SUM, N2F_X_OUT = 7, 8, 9, 10, 11
+N2F_X_DZ, N2F_X_PAIR, N2F_X_VAL, N2F_X_SUM, N2F_X_OUT, N2F_X_HIST, N2F_X_VBEST = (
+    7, 8, 9, 10, 11, 12, 13)
+N2F_HIST_CAP = 4096
 (N2F_K_NONE, N2F_K_CONV_FWD, N2F_K_CONV_DGRAD, N2F_K_CONV_WGRAD, N2F_K_FIRST, N2F_K_HEAD,
  N2F_K_ADAM, N2F_K_CONV) = range(8)
 
@@ -41,8 +43,8 @@ class Config(C.Structure):
 
 
 class Params(C.Structure):
-    _fields_ = [("struct_size", C.c_uint32), ("lr", C.c_float), ("beta1", C.c_float),
-                ("beta2", C.c_float), ("eps", C.c_float), ("patience", C.c_uint32),
+    _fields_ = [("struct_size", C.c_uint32), ("lr", C.c_double), ("beta1", C.c_double),
+                ("beta2", C.c_double), ("eps", C.c_double), ("patience", C.c_uint32),
                 ("max_epochs", C.c_uint32), ("fixed_steps", C.c_int32), ("seed", C.c_uint64),
                 ("precision", C.c_int32), ("loss", C.c_int32), ("widths", C.c_int32),
                 ("incl_best", C.c_int32), ("engine", C.c_int32), ("channels", C.c_int32),
@@ -80,11 +82,13 @@ SIGNATURES = {
     "n2f_submit": (_I, [_P, _P, _I, _I, C.POINTER(Params), C.POINTER(_U64)]),
     "n2f_submit_device": (_I, [_P, _P, _I, _I, C.POINTER(Params), C.POINTER(_U64)]),
     "n2f_submit_u16": (_I, [_P, _P, _I, _I, C.POINTER(Params), C.POINTER(_U64)]),
+    "n2f_job_bytes": (_I, [_I, _I, C.POINTER(Params), C.POINTER(_U64)]),
     "n2f_poll": (_I, [_P, _U64, C.POINTER(Status)]),
     "n2f_wait": (_I, [_P, _U64, _I]),
     "n2f_result": (_I, [_P, _U64, _P, _Z]),
     "n2f_result_device": (_I, [_P, _U64, _P, _Z]),
     "n2f_cancel": (_I, [_P, _U64]),
+    "n2f_history": (_I, [_P, _U64, _P, _Z, C.POINTER(_Z), C.POINTER(C.c_uint32)]),
     "n2f_stats": (_I, [_P, C.POINTER(CtxStats)]),
     "n2f_trainer_create": (_I, [C.POINTER(_P), _P, _I, _I, C.POINTER(Params), _P]),
     "n2f_trainer_destroy": (None, [_P]),
@@ -97,6 +101,8 @@ SIGNATURES = {
     "n2f_trainer_export": (_I, [_P, _I, _I, _P, _Z, C.POINTER(_Z)]),
     "n2f_trainer_status": (_I, [_P, C.POINTER(Status)]),
     "n2f_trainer_launches": (_U64, [_P]),
+    "n2f_trainer_import": (_I, [_P, _I, _I, _P, _Z]),
+    "n2f_trainer_set_progress": (_I, [_P, C.c_uint32, C.c_uint32, C.c_uint32, _D]),
     "n2f_param_count": (_Z, [_I]),
     "n2f_checker_gather": (_I, [_P, _I, _I, _P, _P, _P, _P, _P]),
     "n2f_max_project": (_I, [_P, _I, _I, _I, _P, _P]),
@@ -152,6 +158,14 @@ def params(**kw) -> Params:
     return p
 
 
+def job_bytes(H: int, W: int, p: Params | None = None) -> int:
+    """Device bytes a job holds while admitted (``n2f_job_bytes``): what the context counts
+    against its HBM budget."""
+    n = C.c_uint64()
+    check(lib().n2f_job_bytes(H, W, C.byref(p) if p else None, C.byref(n)), "n2f_job_bytes")
+    return int(n.value)
+
+
 def param_count(widths=N2F_WIDTHS_PLIT) -> int:
     return int(lib().n2f_param_count(widths))
 
@@ -168,6 +182,36 @@ def _ptr(t):
 
 
 # ---- job API ---------------------------------------------------------------------------------
+
+def image_planes(p: Params | None) -> int:
+    """Planes of H x W floats a submitted image holds: the input channels (0 means 1), plus the
+    clean plane of the Exact ablation."""
+    if p is None:
+        return 1
+    return max(1, int(p.channels)) + (1 if p.exact else 0)
+
+
+def _check_device_image(dimage, p: Params | None, device: int):
+    """n2f_submit_device takes no element count: the library copies image_planes(p) * H * W
+    floats from the pointer. Raises ValueError unless dimage is a contiguous float32 tensor of
+    exactly that many elements (shape (H, W) or (planes, H, W)) on the context's device."""
+    import torch
+    if not isinstance(dimage, torch.Tensor):
+        raise ValueError("dimage: a torch tensor is required")
+    if dimage.dtype != torch.float32:
+        raise ValueError(f"dimage: dtype {dimage.dtype}, torch.float32 required")
+    if dimage.dim() not in (2, 3):
+        raise ValueError(f"dimage: shape {tuple(dimage.shape)}, (H, W) or (planes, H, W) required")
+    H, W = dimage.shape[-2:]
+    need = image_planes(p) * H * W
+    if dimage.numel() != need:
+        raise ValueError(f"dimage: {dimage.numel()} elements, {need} required "
+                         f"({image_planes(p)} planes of {H} x {W})")
+    if not dimage.is_contiguous():
+        raise ValueError("dimage: must be contiguous")
+    if dimage.device.type != "cuda" or dimage.device.index != device:
+        raise ValueError(f"dimage: on {dimage.device}, cuda:{device} required")
+
 
 class Context:
     """A scheduler context (``n2f_create``); device memory comes from torch's caching allocator
@@ -254,6 +298,7 @@ class Context:
         not be written, until the job's result is collected."""
         import torch
         H, W = dimage.shape[-2:]
+        _check_device_image(dimage, p, self.device)
         torch.cuda.current_stream(dimage.device).synchronize()
         job = C.c_uint64()
         check(lib().n2f_submit_device(self.h, _ptr(dimage), H, W, C.byref(p) if p else None,
@@ -265,10 +310,16 @@ class Context:
         st = Status()
         st.struct_size = C.sizeof(Status)
         check(lib().n2f_poll(self.h, job, C.byref(st)), "n2f_poll")
+        if st.state >= N2F_DONE:
+            # a final state: the library no longer reads a device input of this job
+            self._dev_inputs.pop(job, None)
         return st
 
     def wait(self, job: int, timeout_ms: int = -1) -> int:
-        return lib().n2f_wait(self.h, job, timeout_ms)
+        rc = lib().n2f_wait(self.h, job, timeout_ms)
+        if rc == N2F_OK:
+            self._dev_inputs.pop(job, None)
+        return rc
 
     def _collected(self, job: int, rc: int) -> int:
         # any other outcome means the job reached a final state (its copy of the input is done)
@@ -286,7 +337,20 @@ class Context:
         rc = lib().n2f_result_device(self.h, job, _ptr(dout), dout.numel())
         check(self._collected(job, rc), "n2f_result_device")
 
+    def history(self, job: int):
+        """The job's validation scores, one per epoch (``n2f_history``): returns (scores as a
+        float64 array, 1-based epoch of the first score). Available once the job is DONE and
+        until its result is collected."""
+        n, first = C.c_size_t(), C.c_uint32()
+        check(lib().n2f_history(self.h, job, None, 0, C.byref(n), C.byref(first)), "n2f_history")
+        out = np.empty(n.value, np.float64)
+        check(lib().n2f_history(self.h, job, out.ctypes.data_as(C.c_void_p), out.size,
+                                C.byref(n), C.byref(first)), "n2f_history")
+        return out, int(first.value)
+
     def cancel(self, job: int) -> int:
+        """Cancels the job; its device input (submit_device) is released by the next poll or
+        wait that sees it final, or when the context closes."""
         return lib().n2f_cancel(self.h, job)
 
     def stats(self) -> dict:
@@ -393,6 +457,17 @@ class Trainer:
         st.struct_size = C.sizeof(Status)
         check(lib().n2f_trainer_status(self.h, C.byref(st)), "n2f_trainer_status")
         return st
+
+    def import_(self, what: int, values: np.ndarray):
+        """Loads THETA, ADAM_M, ADAM_V, SUM or VBEST from host values (``n2f_trainer_import``)."""
+        a = np.ascontiguousarray(values, dtype=np.float64).ravel()
+        check(lib().n2f_trainer_import(self.h, what, 0, a.ctypes.data_as(C.c_void_p), a.size),
+              "n2f_trainer_import")
+
+    def set_progress(self, steps: int, epoch: int, since: int, best: float):
+        """Adam step count and stopping-rule counters (``n2f_trainer_set_progress``)."""
+        check(lib().n2f_trainer_set_progress(self.h, steps, epoch, since, float(best)),
+              "n2f_trainer_set_progress")
 
     def launches(self) -> int:
         return int(lib().n2f_trainer_launches(self.h))
@@ -506,10 +581,43 @@ def wait_probe(limit_ms: int, stream=None) -> int:
     return int(lib().n2f_wait_probe(int(limit_ms), _stream_ptr(stream)))
 
 
+def _need_layout(name, t, dtype=None, shape=None, nbytes=None):
+    """Raises ValueError unless t is a contiguous tensor of the given dtype and shape (or of at
+    least nbytes bytes), naming the first mismatch."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{name}: a torch tensor is required")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name}: dtype {t.dtype}, {dtype} required")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name}: shape {tuple(t.shape)}, {tuple(shape)} required")
+    if nbytes is not None and t.numel() * t.element_size() < nbytes:
+        raise ValueError(f"{name}: {t.numel() * t.element_size()} bytes, {nbytes} required")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: must be contiguous")
+
+
+def _need_current_device(name, t):
+    import torch
+    if t.device.type != "cuda" or t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name}: on {t.device}, the current CUDA device is required")
+
+
 def conv3x3_wgrad_noalloc(dout_cg, in_cg, cin, cout, H, W, dw, db, precision=N2F_FP32,
                           engine=N2F_ENGINE_AUTO, stream=None):
     """n2f_conv3x3_wgrad_noalloc into caller-provided dw [C_out][C_in][3][3] and db [C_out]
-    (float32 CUDA tensors); the library allocates nothing for the call."""
+    (contiguous float32 tensors on the current CUDA device, where the kernels run); the library
+    allocates nothing for the call. dout_cg and in_cg are CG maps of C_out and C_in channels
+    (at least C * H * W elements of the precision). Raises ValueError before the call when a
+    tensor does not fit, since the kernels write dw and db without knowing their size."""
+    import torch
+    es = 2 if precision == N2F_BF16 else 4
+    _need_layout("dw", dw, torch.float32, (cout, cin, 3, 3))
+    _need_layout("db", db, torch.float32, (cout,))
+    _need_layout("dout_cg", dout_cg, nbytes=cout * H * W * es)
+    _need_layout("in_cg", in_cg, nbytes=cin * H * W * es)
+    for name, t in (("dw", dw), ("db", db), ("dout_cg", dout_cg), ("in_cg", in_cg)):
+        _need_current_device(name, t)
     check(lib().n2f_conv3x3_wgrad_noalloc(engine, precision, _ptr(dout_cg), _ptr(in_cg), cin, cout,
                                           H, W, _ptr(dw), _ptr(db), _stream_ptr(stream)),
           "n2f_conv3x3_wgrad_noalloc")

@@ -47,8 +47,9 @@ def test_struct_layouts_match_the_header(n2f):
 int main(void) {
   printf("%zu %zu %zu %zu\n", sizeof(n2f_config), sizeof(n2f_params), sizeof(n2f_status),
          sizeof(n2f_ctx_stats));
-  printf("%zu %zu %zu\n", offsetof(n2f_params, seed), offsetof(n2f_params, engine),
-         offsetof(n2f_status, t_done_ms));
+  printf("%zu %zu %zu %zu %zu\n", offsetof(n2f_params, seed), offsetof(n2f_params, engine),
+         offsetof(n2f_status, t_done_ms), offsetof(n2f_params, eps),
+         offsetof(n2f_params, patience));
   return 0;
 }'''
     with tempfile.TemporaryDirectory() as d:
@@ -61,14 +62,16 @@ int main(void) {
     assert sizes[:4] == [C.sizeof(n2f.Config), C.sizeof(n2f.Params), C.sizeof(n2f.Status),
                          C.sizeof(n2f.CtxStats)]
     assert sizes[4:] == [n2f.Params.seed.offset, n2f.Params.engine.offset,
-                         n2f.Status.t_done_ms.offset]
+                         n2f.Status.t_done_ms.offset, n2f.Params.eps.offset,
+                         n2f.Params.patience.offset]
 
 
 def test_defaults_follow_the_methods_section(n2f):
     p = n2f.params()
-    assert abs(p.lr - 1e-3) < 1e-9 and p.patience == 100 and p.fixed_steps == -1
+    # Adam's constants are held in double, exactly as the oracle's (Kingma & Ba's defaults)
+    assert p.lr == 1e-3 and p.patience == 100 and p.fixed_steps == -1
     assert p.precision == n2f.N2F_FP32 and p.loss == n2f.N2F_LOSS_BCE
-    assert abs(p.beta1 - 0.9) < 1e-7 and abs(p.beta2 - 0.999) < 1e-7
+    assert p.beta1 == 0.9 and p.beta2 == 0.999 and p.eps == 1e-8
 
 
 def test_param_counts_agree_with_the_oracle(n2f):

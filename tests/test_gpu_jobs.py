@@ -121,6 +121,45 @@ def test_cancel(n2f):
         assert e.value.code == n2f.N2F_ECANCELED
 
 
+def test_budget_admission_of_the_largest_serving_size(n2f):
+    """Admission against the HBM budget with 2048x2048 literal-width jobs (the largest side of
+    the serving stream): under a budget of one and a half jobs' bytes the second of two jobs
+    waits in the queue while the first holds the device, is admitted once the first retires,
+    and both results are bit-identical to the same jobs run alone; the resident bytes never
+    exceed the budget; a budget below one job's bytes refuses the job at submission."""
+    import time
+    from paper_2108_10209_gb300 import synth
+    p = n2f.params(seed=0, fixed_steps=2)  # short runs: admission does not depend on the mode
+    nb = n2f.job_bytes(2048, 2048, p)
+    assert nb > (8 << 30)  # the literal-width float32 job holds more than 8 GiB
+    _, noisy = synth.image_cells(2048, 2048, seed=21)
+    x = noisy.astype(np.float32)
+    y = np.ascontiguousarray(x[::-1])
+    budget = nb + nb // 2
+    with n2f.Context(hbm_budget_bytes=budget) as ctx:
+        a, b = ctx.submit(x, p), ctx.submit(y, p)
+        polls = 0
+        while True:
+            sb = ctx.poll(b).state          # b first: if a still runs afterwards, it ran here too
+            sa = ctx.poll(a).state
+            assert ctx.stats()["bytes_resident"] <= budget
+            if sa >= n2f.N2F_DONE:
+                break
+            if sa == n2f.N2F_RUNNING:
+                assert sb == n2f.N2F_QUEUED
+                polls += 1
+            time.sleep(0.0005)
+        assert polls > 0
+        assert ctx.wait(b, 120000) == n2f.N2F_OK and ctx.poll(b).state == n2f.N2F_DONE
+        out_a, out_b = ctx.result(a, x.shape), ctx.result(b, y.shape)
+    for img, out in ((x, out_a), (y, out_b)):
+        assert np.array_equal(out, n2f.denoise(img, p))
+    with n2f.Context(hbm_budget_bytes=nb - 1) as ctx:
+        with pytest.raises(n2f.N2FError) as e:
+            ctx.submit(x, p)
+        assert e.value.code == n2f.N2F_ETOOBIG
+
+
 def test_trained_network_gains_over_the_untrained_path(n2f):
     # The learned part: the network trained by the library's own forward/backward kernels on
     # the four checkerboard pairs denoises the full image; without training (zero steps) the
@@ -143,6 +182,8 @@ def test_trained_network_gains_over_the_untrained_path(n2f):
     assert st.stopped == 1 and st.epoch >= 101
     assert p_out > p_noisy + 3.0
     assert p_out > p_out0 + 5.0
+    # and it beats the non-learned 3x3 mean filter on the same image
+    assert p_out > p_mean
 
 
 def test_graph_replay_matches_launch_by_launch(n2f):

@@ -226,18 +226,21 @@ def test_single_step_activations_and_gradients(n2f, widths, engine):
     (1e-4) wherever no mask above them differs, and at least one step must be free of such
     units. The per-kernel test above holds every kernel to 1e-4 on identical inputs.
 
-    Engines: the CUDA-core kernels compute in float32 and hold every tensor to 1e-4. The
-    tensor-core float32 form multiplies two scaled fp16 parts per operand (about 2^-22 per
-    product instead of 2^-24);
-    activations and deltas stay within 1e-4, but a weight gradient is a sum over every pixel
-    with strong sign cancellation, which magnifies that difference relative to its largest
-    element, so weight gradients on that engine are held to 1e-3."""
+    Engines: the CUDA-core kernels compute in float32 and hold every tensor to 1e-4 of its
+    largest element. The tensor-core float32 form multiplies two scaled fp16 parts per operand
+    (about 2^-22 per product instead of float32's exact products) and compounds that through
+    eight layers forward and back: activations and deltas stay within 1e-4, but a weight
+    gradient is a pixel sum whose terms cancel (the largest sum of |delta| |x| over the pixels
+    is up to 12 times the largest gradient on this image), and the error of such a sum scales
+    with the sum of the magnitudes, not with the result. So tensor-core weight gradients are held
+    to 1e-4 of that cancellation-free magnitude, max over entries of sum_px |delta| |x|, and to
+    1e-3 of the largest gradient. Measured: 1.4e-5 and 1.8e-4 at worst (layer 8 of the literal
+    widths, the fourth pair); the CUDA-core engine 3e-7 and 1.4e-6 on the same step."""
     clean, noisy = _small_case()
     ow = oracle.WIDTHS_PLIT if widths == 0 else oracle.WIDTHS_W64
     tr = n2f.Trainer(noisy, n2f.params(seed=0, widths=widths, engine=engine))
     job = oracle.Job(noisy, oracle.Params(widths=ow, seed=0))
     sl = layer_slices(ow)
-    gtol = REL_STEP if engine == 1 else 10 * REL_STEP
     clean_steps = 0
     for pair in (0, 2, 1, 3):
         job.set_theta(tr.export(n2f.N2F_X_THETA))
@@ -261,11 +264,54 @@ def test_single_step_activations_and_gradients(n2f, widths, engine):
             d, do = tr.export(n2f.N2F_X_DELTA, l), job.get(oracle.DELTA, l)
             assert rel_err(d, do) < REL_STEP, (pair, l, flips)
             ws, bs = sl[l - 1]
-            assert rel_err(g[ws], go[ws]) < gtol and rel_err(g[bs], go[bs]) < gtol, (pair, l)
+            if engine == 1:
+                assert rel_err(g[ws], go[ws]) < REL_STEP and rel_err(g[bs], go[bs]) < REL_STEP
+            else:
+                h, w = (32, 16) if pair < 2 else (16, 32)
+                cin = 1 if l == 1 else ow[l - 2]
+                x_o = (job.get(oracle.PAIR_IN, pair) if l == 1 else job.get(oracle.ACT, l - 1))
+                mag_w, mag_b = oracle.conv3x3_wgrad(np.abs(do.reshape(ow[l - 1], h, w)),
+                                                    np.abs(x_o.reshape(cin, h, w)))
+                for got, ref, mag in ((g[ws], go[ws], mag_w), (g[bs], go[bs], mag_b)):
+                    assert np.max(np.abs(got - ref)) <= REL_STEP * np.max(mag), (pair, l)
+                    assert rel_err(got, ref) < 10 * REL_STEP, (pair, l)
             compared += 1
         clean_steps += compared == 8
         print(f"pair {pair}: ReLU decisions differing per layer {flips}, layers compared {compared}")
     assert clean_steps >= 1
+
+
+@pytest.mark.parametrize("engine", [1, 2])
+def test_mse_training_loss(n2f, engine):
+    """The MSE training loss the Methods section compares BCE with (loss flag N2F_LOSS_MSE):
+    dL/dz = 2 (s - y) s (1 - s) / P on the GPU's own head inputs within 1e-4 for every pair,
+    then a fixed 10-step run within the fixed-run bar (0.05 dB, 2e-3)."""
+    from paper_2108_10209_gb300 import synth
+    clean, noisy = _small_case()
+    ow = oracle.WIDTHS_PLIT
+    tr = n2f.Trainer(noisy, n2f.params(seed=0, engine=engine, loss=n2f.N2F_LOSS_MSE))
+    for pair in (0, 2, 1, 3):
+        theta = tr.export(n2f.N2F_X_THETA)
+        tr.step(pair)
+        h, w = (32, 16) if pair < 2 else (16, 32)
+        parts = oracle.unpack(ow, theta)
+        a8 = tr.export(n2f.N2F_X_ACT, 8).reshape(ow[7], h, w)
+        tgt = tr.export(n2f.N2F_X_PAIR, pair ^ 1).reshape(h, w)
+        z = oracle.head_fwd(a8, parts[8][0], parts[8][1][0])
+        _, dz_ref = oracle.loss(z, tgt, 1)
+        _, dz_bce = oracle.loss(z, tgt, 0)
+        dz = tr.export(n2f.N2F_X_DZ).reshape(h, w)
+        assert rel_err(dz, dz_ref) < REL_STEP, pair
+        assert rel_err(dz_bce, dz_ref) > 1e-2  # the flag changes the gradient
+        d8 = dz[None] * parts[8][0][:, None, None] * (a8 > 0)
+        assert rel_err(tr.export(n2f.N2F_X_DELTA, 8), d8) < REL_STEP, pair
+    p = n2f.params(seed=0, fixed_steps=10, engine=engine, loss=n2f.N2F_LOSS_MSE)
+    out = n2f.denoise(noisy, p).astype(np.float64)
+    ref, _ = oracle.denoise(noisy, oracle.Params(seed=0, fixed_steps=10, loss_kind=1))
+    dpsnr = abs(synth.psnr(out, clean) - synth.psnr(ref, clean))
+    maxabs = float(np.max(np.abs(out - ref)))
+    print(f"MSE loss, engine {engine}: 10 steps dPSNR {dpsnr:.5f} dB, max-abs {maxabs:.2e}")
+    assert dpsnr <= PSNR_TOL and maxabs <= MAXABS_TOL
 
 
 def test_zero_steps_equals_one_forward_pass(n2f):
@@ -288,31 +334,6 @@ def test_fixed_ten_step_run(n2f, widths):
     dpsnr = abs(synth.psnr(out, clean) - synth.psnr(ref, clean))
     assert dpsnr <= PSNR_TOL, dpsnr
     assert float(np.max(np.abs(out - ref))) <= MAXABS_TOL
-
-
-def test_stop_rule_run_matches_oracle(n2f):
-    from paper_2108_10209_gb300 import synth
-    clean = synth.blobs(16, 16, seed=3)
-    noisy = (clean + synth.rng(4).normal(0, 0.1, clean.shape)).astype(np.float32).astype(np.float64)
-    P = 6
-    ref, info = oracle.denoise(noisy, oracle.Params(widths=oracle.WIDTHS_W64, seed=1, patience=P,
-                                                    max_epochs=200))
-    p = n2f.params(seed=1, patience=P, widths=1, max_epochs=200)
-    tr = n2f.Trainer(noisy, p)
-    tr.run()
-    st = tr.status()
-    out = tr.export(n2f.N2F_X_OUT)
-    if st.epoch == info["epoch"]:
-        assert st.stopped == (1 if info["stopped"] else 2)
-        assert float(np.max(np.abs(out - ref.ravel()))) <= MAXABS_TOL
-    else:
-        # a near-tie of two validation scores may flip a decision between FP32 and FP64;
-        # then the run is compared at the oracle's stop epoch
-        assert abs(st.epoch - info["epoch"]) <= P
-        tr2 = n2f.Trainer(noisy, n2f.params(seed=1, patience=P, widths=1,
-                                            max_epochs=info["epoch"]))
-        tr2.run()
-        assert tr2.status().epoch == info["epoch"]
 
 
 # ------------------------------------------------------------------- bf16 form --------------

@@ -624,3 +624,28 @@ def test_exact_targets(downsample):
     for k in range(4):
         g = order[k]
         np.testing.assert_array_equal(j.get(oracle.PAIR_TGT, k), (xs[g] - (ss[g] - ss[k])).ravel())
+
+
+def test_stop_rule_golden_is_the_oracle_run():
+    """tests/golden/stop_rule_plit_48.npz (written by make_stop_rule_golden.py from the oracle
+    alone) is self-consistent and still the oracle's run: the image is the seeded generator's,
+    the stopping rule replayed on the stored scores fires at the stored stop epoch, the output
+    is the window sum over the patience, and the oracle recomputes the first two epochs' scores
+    bit for bit."""
+    from paper_2108_10209_gb300 import synth
+    g = np.load(os.path.join(os.path.dirname(__file__), "golden", "stop_rule_plit_48.npz"))
+    clean, noisy = synth.image_cells(48, 48, sigma=25.0 / 255.0, seed=int(g["image_seed"]))
+    assert np.array_equal(noisy, g["noisy"]) and np.array_equal(clean, g["clean"])
+    scores, P = g["scores"], int(g["patience"])
+    rule = oracle.StopRule(patience=P)
+    fired = []
+    for s in scores:
+        rule.update(float(s))
+        fired.append(rule.stopped)
+    assert fired[-1] and not any(fired[:-1]) and len(scores) == int(g["stop_epoch"])
+    assert int(g["best_epoch"]) == int(np.argmin(scores)) + 1 == len(scores) - P
+    assert rule.best == float(g["best"])
+    assert np.array_equal(g["out"], g["window_sum"] / P)
+    job = oracle.Job(g["noisy"], oracle.Params(widths=oracle.WIDTHS_PLIT,
+                                               seed=int(g["init_seed"]), patience=P))
+    assert [job.epoch(), job.epoch()] == list(scores[:2])

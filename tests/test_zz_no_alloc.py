@@ -55,8 +55,10 @@ def test_noalloc_wgrad_matches_allocating_entry_point(env, precision, engine):
 
 def test_noalloc_rejects_layers_beyond_the_workspace(env):
     n2f, torch = env
-    big = 1024  # 9 * 1024 * 1024 floats exceed the 4 Mi-float array
-    t = torch.zeros(16, dtype=torch.float32, device="cuda")
+    big = 1024  # one split needs 9 * 1024 * 1024 floats: more than the 4 Mi-float array
+    t = torch.zeros(big * 2 * 2, dtype=torch.float32, device="cuda")
+    dw = torch.zeros((big, big, 3, 3), dtype=torch.float32, device="cuda")
+    db = torch.zeros((big,), dtype=torch.float32, device="cuda")
     with pytest.raises(n2f.N2FError) as e:
-        n2f.conv3x3_wgrad_noalloc(t, t, big, big, 2, 2, t, t, engine=n2f.N2F_ENGINE_SIMT)
+        n2f.conv3x3_wgrad_noalloc(t, t, big, big, 2, 2, dw, db, engine=n2f.N2F_ENGINE_SIMT)
     assert e.value.code == n2f.N2F_ETOOBIG
