@@ -135,18 +135,38 @@ def oracle_epoch_seconds(noisy, widths: int, crop: int = 128):
     return time.perf_counter() - t0
 
 
-def cpu_baseline(noisy, size: int, widths: int, crop: int = 128, reps: int = 1):
+def oracle_whole_run(widths: int, side: int = 24):
+    """One whole stopping-rule run (patience 100) of the FP64 oracle on a side x side cell
+    image, timed on the host cores: the measured counterpart of the extrapolation."""
+    os.environ.setdefault("OMP_NUM_THREADS", str(host_cores()))
+    import oracle
+    from paper_2108_10209_gb300 import synth
+    ow = oracle.WIDTHS_PLIT if widths == 0 else oracle.WIDTHS_W64
+    _, noisy = synth.image_cells(side, side, seed=5)
+    t0 = time.perf_counter()
+    _, info = oracle.denoise(noisy, oracle.Params(widths=ow, seed=0))
+    secs = time.perf_counter() - t0
+    return {"image": [side, side], "epochs": info["epoch"], "seconds": secs,
+            "images_per_s": 1.0 / secs,
+            "us_per_pixel_epoch": secs / (info["epoch"] * side * side) * 1e6}
+
+
+def cpu_baseline(noisy, size: int, widths: int, crop: int = 128, reps: int = 1,
+                 whole_run: bool = True):
     ts = [oracle_epoch_seconds(noisy, widths, crop) for _ in range(reps)]
     t = min(ts)
     scale = (size * size) / float(crop * crop)
     ips = 1.0 / (MIN_EPOCHS * scale * t)
-    return {"value": ips, "unit": UNIT, "cores": oracle_threads(),
-            "kind": "oracle",
-            "sample": (f"one epoch (4 training steps + validation) of the FP64 oracle on a "
-                       f"{crop}x{crop} crop: {t:.2f} s; scaled by pixel count x{scale:.0f} to the "
-                       f"{size}x{size} image and by {MIN_EPOCHS} epochs, the shortest run the "
-                       f"stopping rule allows (real runs are longer, so this overstates the "
-                       f"oracle)")}
+    out = {"value": ips, "unit": UNIT, "cores": oracle_threads(),
+           "kind": "oracle",
+           "sample": (f"one epoch (4 training steps + validation) of the FP64 oracle on a "
+                      f"{crop}x{crop} crop: {t:.2f} s; scaled by pixel count x{scale:.0f} to the "
+                      f"{size}x{size} image and by {MIN_EPOCHS} epochs, the shortest run the "
+                      f"stopping rule allows (real runs are longer, so this overstates the "
+                      f"oracle)")}
+    if whole_run:
+        out["whole_run_measured"] = oracle_whole_run(widths)
+    return out
 
 
 # ---------------------------------------------------------------------------- peaks ----------
@@ -309,9 +329,12 @@ def run_ours(args, ws, rank, local):
     from paper_2108_10209_gb300 import synth
     line["psnr_db"] = [round(synth.psnr(o, work[args.warmup + k][0]), 3)
                        for k, o in enumerate(outs)]
+    line["mpx_per_s"] = args.steps * size * size / 1e6 / tot_dev_s
     if args.compare_batch > 0 and args.precision == 0:
-        line["bf16_batched"] = bf16_batched_compare(
-            n2f, work[args.warmup:args.warmup + args.steps], outs, args.widths, args.compare_batch)
+        line["bf16_batched"] = c3_batched(n2f, args.widths, args.c3_jobs)
+        line["bf16_vs_fp32"] = bf16_vs_fp32(
+            n2f, work[args.warmup:args.warmup + args.steps], outs, epochs, args.widths,
+            args.compare_batch)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(work[args.warmup][1], size, args.widths)
     return line
@@ -319,13 +342,12 @@ def run_ours(args, ws, rank, local):
 
 # ---------------------------------------------------------------------------- batched / serving
 
-def run_jobs(ctx, n2f, jobs, p_of, submit_times=None):
-    """Submits jobs (list of (noisy float32 array)), optionally at host times (seconds from
-    start), waits for all, returns per-job dicts and the host/device makespans."""
-    import numpy as np
+def run_jobs(ctx, n2f, jobs, p_of, submit_times=None, u16=False):
+    """Submits jobs (list of noisy float32 arrays, or uint16 arrays with u16=True, submitted
+    through n2f_submit_u16), optionally at host times (seconds from start), waits for all,
+    returns per-job dicts and the host/device makespans."""
     t0 = time.perf_counter()
-    ids, t_sub = [], []
-    pending = list(range(len(jobs)))
+    ids = []
     results = [None] * len(jobs)
     next_i = 0
     while next_i < len(jobs):
@@ -335,8 +357,7 @@ def run_jobs(ctx, n2f, jobs, p_of, submit_times=None):
                 time.sleep(min(wait, 0.002))
                 continue
         x = jobs[next_i]
-        t_sub.append(time.perf_counter())
-        ids.append(ctx.submit(x, p_of(next_i)))
+        ids.append(ctx.submit_u16(x, p_of(next_i)) if u16 else ctx.submit(x, p_of(next_i)))
         next_i += 1
     for i, j in enumerate(ids):
         ctx.wait(j)
@@ -356,27 +377,68 @@ def pct(v, q):
     return v[min(len(v) - 1, int(q * len(v)))]
 
 
-def bf16_batched_compare(n2f, noisy_clean, fp32_outs, widths, batch):
-    """The same images (plus more, up to `batch`) through the bf16 form, submitted together."""
+def c3_batched(n2f, widths, n_jobs):
+    """The batching form's workload: n_jobs independent jobs, sizes uniform over 256x256,
+    512x512, 768x512 and 1024x768, sigma U[15, 50]/255, each with its own weights and the
+    stopping rule, all submitted at once in the bf16 form (one stream and one epoch graph per
+    job, autotuned launches). value: jobs / device makespan (first upload to last result)."""
     from paper_2108_10209_gb300 import synth
-    imgs = [nc for nc in noisy_clean]
-    k = len(imgs)
-    i = 0
-    while len(imgs) < batch:
-        imgs.append(image_for(100 + i, 0, imgs[0][1].shape[0]))
-        i += 1
+    jobs = synth.batch_jobs(n_jobs)
+    imgs = [synth.image_cells(j["h"], j["w"], sigma=j["sigma"], seed=j["seed"]) for j in jobs]
     p = n2f.params(seed=0, precision=1, widths=widths)
-    with n2f.Context(max_slots=batch, autotune=True) as ctx:
-        res, host_s, dev_s = run_jobs(ctx, n2f, [nc[1].astype("float32") for nc in imgs],
+    with n2f.Context(max_slots=n_jobs, autotune=True) as ctx:
+        # warm-up: one job of every size (tunes each conv shape once, outside the timed region)
+        seen = {}
+        for j, im in zip(jobs, imgs):
+            seen.setdefault((j["h"], j["w"]), im[1].astype("float32"))
+        run_jobs(ctx, n2f, list(seen.values()), lambda _: n2f.params(seed=0, precision=1,
+                                                                     widths=widths,
+                                                                     fixed_steps=4))
+        st0 = ctx.stats()
+        res, host_s, dev_s = run_jobs(ctx, n2f, [im[1].astype("float32") for im in imgs],
                                       lambda _: p)
-    dps = [synth.psnr(res[j]["out"], imgs[j][0]) - synth.psnr(fp32_outs[j], imgs[j][0])
-           for j in range(k)]
+        st1 = ctx.stats()
     lat = [r["latency_ms"] for r in res]
-    return {"value": len(res) / dev_s, "unit": UNIT, "jobs": len(res), "jobs_in_flight": batch,
-            "precision": "bf16", "e2e": len(res) / host_s,
-            "latency_ms": {"p50": pct(lat, 0.5), "p99": pct(lat, 0.99)},
-            "psnr_bf16_minus_fp32_db": [round(d, 4) for d in dps],
-            "epochs": [r["epoch"] for r in res]}
+    mpx = sum(r["H"] * r["W"] for r in res) / 1e6
+    return {"value": len(res) / dev_s, "unit": UNIT, "precision": "bf16",
+            "workload": f"{n_jobs} jobs, sizes uniform over 256x256, 512x512, 768x512, 1024x768, "
+                        "sigma U[15,50]/255, stopping rule, all in flight",
+            "jobs": len(res), "jobs_in_flight": n_jobs, "megapixels": round(mpx, 3),
+            "mpx_per_s": mpx / dev_s,
+            "e2e": {"value": len(res) / host_s, "unit": UNIT,
+                    "h2d_bytes_per_step": int(mpx * 4e6), "d2h_bytes_per_step": int(mpx * 4e6)},
+            "latency_ms": {"p50": pct(lat, 0.5), "p99": pct(lat, 0.99), "max": max(lat)},
+            "gpu_launches": int(st1["kernel_launches"] - st0["kernel_launches"]),
+            "epochs": [r["epoch"] for r in res],
+            "psnr_db": [round(synth.psnr(r["out"], imgs[k][0]), 3) for k, r in enumerate(res)]}
+
+
+def bf16_vs_fp32(n2f, noisy_clean, fp32_outs, fp32_epochs, widths, batch):
+    """The plain form's images again in the bf16 form (submitted together): PSNR per image
+    against the float32 plain output, from free runs (each form stops where its own rule
+    fires) and at the float32 run's stop epoch (the bf16 job capped there, its patience raised
+    so that only the cap ends it: its output is then the mean of its validation outputs since
+    its own best epoch, or that epoch's output)."""
+    from paper_2108_10209_gb300 import synth
+    imgs = [nc[1].astype("float32") for nc in noisy_clean]
+    p_free = n2f.params(seed=0, precision=1, widths=widths)
+    with n2f.Context(max_slots=batch, autotune=True) as ctx:
+        free, host_s, dev_s = run_jobs(ctx, n2f, imgs, lambda _: p_free)
+        forced, _, _ = run_jobs(ctx, n2f, imgs, lambda k: n2f.params(
+            seed=0, precision=1, widths=widths, max_epochs=fp32_epochs[k],
+            patience=fp32_epochs[k] + 1))
+    ref = [synth.psnr(o, nc[0]) for o, nc in zip(fp32_outs, noisy_clean)]
+    d_free = [synth.psnr(r["out"], nc[0]) - p for r, nc, p in zip(free, noisy_clean, ref)]
+    d_forced = [synth.psnr(r["out"], nc[0]) - p for r, nc, p in zip(forced, noisy_clean, ref)]
+    return {"images": len(imgs), "jobs_in_flight": batch,
+            "value_free_runs": len(free) / dev_s, "unit": UNIT,
+            "psnr_bf16_minus_fp32_db": [round(d, 4) for d in d_free],
+            "epochs_bf16": [r["epoch"] for r in free], "epochs_fp32": list(fp32_epochs),
+            "psnr_bf16_minus_fp32_at_fp32_stop_epoch_db": [round(d, 4) for d in d_forced],
+            "max_abs_delta_db": {"free": max(abs(d) for d in d_free),
+                                 "at_fp32_stop_epoch": max(abs(d) for d in d_forced)},
+            "mean_delta_db": {"free": sum(d_free) / len(d_free),
+                              "at_fp32_stop_epoch": sum(d_forced) / len(d_forced)}}
 
 
 def run_batched(args, n2f):
@@ -423,28 +485,67 @@ def run_batched(args, n2f):
 
 
 def run_serving(args, n2f):
-    """Poisson arrivals of u16-quantised images, sides log-uniform in [256, 2048] (square),
-    Gaussian or Poisson-Gaussian noise; latency = submit to result ready (host clock)."""
+    """Poisson arrivals of 16-bit images (n2f_submit_u16: normalised on the device as
+    value / 65535), square sides log-uniform in [256, max_side], Gaussian (sigma U[10, 50]/255)
+    or Poisson-Gaussian (photon peak U(10, 100)) noise, admitted against the HBM budget as slots
+    and memory free up. For every rate in --rates a stream of --jobs requests (the first
+    --jobs of one seeded 1000-request stream, arrival times rescaled to the rate); latency =
+    submit to DONE (host clock). Reported per rate: delivered images/s (completed / time from
+    the first arrival to the last result) and p50 / p99 latency."""
     import numpy as np
     from paper_2108_10209_gb300 import synth
-    reqs = synth.serving_stream(args.jobs, rate=args.rate, smin=256, smax=args.max_side)
-    imgs = [synth.make_serving_image(r)[0].astype(np.float32) for r in reqs]
-    t_arr = [r["t"] for r in reqs]
+    rates = [float(r) for r in args.rates.split(",")]
+    full = synth.serving_stream(1000, rate=1.0, smin=256, smax=args.max_side)
+    base = full[:args.jobs]
+    # the two largest images of the whole 1000-request stream join the shorter stream (at a
+    # third and two thirds of it), so that every rate admits the largest sides
+    big = sorted(full[args.jobs:], key=lambda r: -r["side"])[:2]
+    for k, r in enumerate(big):
+        base.insert((k + 1) * len(base) // 3, dict(r))
+    t_unit = [r["t"] for r in full[:len(base)]]  # arrival times at 1 request/s
+    imgs = [synth.to_u16(synth.make_serving_image(r)[0]) for r in base]
+    clean = [synth.make_serving_image(r)[1] for r in base]
     p = n2f.params(seed=0, precision=args.precision, widths=args.widths, engine=args.engine)
-    with n2f.Context(max_slots=args.slots, autotune=bool(args.autotune)) as ctx:
-        res, host_s, dev_s = run_jobs(ctx, n2f, imgs, lambda _: p, submit_times=t_arr)
-    lat = [r["latency_ms"] for r in res]
+    rows = []
+    budget = int(args.budget_gb * (1 << 30))
+    with n2f.Context(max_slots=args.slots, autotune=bool(args.autotune),
+                     hbm_budget_bytes=budget) as ctx:
+        warm = synth.to_u16(synth.image_cells(256, 256, seed=7)[1])
+        run_jobs(ctx, n2f, [warm], lambda _: n2f.params(seed=0, precision=args.precision,
+                                                        widths=args.widths, fixed_steps=4),
+                 u16=True)
+        for rate in rates:
+            res, host_s, dev_s = run_jobs(ctx, n2f, imgs, lambda _: p,
+                                          submit_times=[t / rate for t in t_unit], u16=True)
+            lat = [r["latency_ms"] for r in res]
+            rows.append({
+                "rate_per_s": rate, "completed": len(res), "images_per_s": len(res) / host_s,
+                "device_images_per_s": len(res) / dev_s,
+                "latency_ms": {"p50": pct(lat, 0.5), "p99": pct(lat, 0.99), "max": max(lat)},
+                "mpx": sum(r["H"] * r["W"] for r in res) / 1e6,
+                "psnr_db_mean": float(np.mean([synth.psnr(r["out"], c)
+                                               for r, c in zip(res, clean)]))})
+            print(json.dumps({"rate": rate, **{k: v for k, v in rows[-1].items()
+                                               if k != "rate_per_s"}}), file=sys.stderr,
+                  flush=True)
+    sides = [r["side"] for r in base]
+    best = max(rows, key=lambda r: r["images_per_s"])
     return {
-        "metric": METRIC, "value": len(res) / host_s, "unit": UNIT, "n_gpus": 1,
-        "steps": 1, "warmup": 0, "ms_per_step": host_s * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
+        "metric": METRIC, "value": best["images_per_s"], "unit": UNIT, "n_gpus": 1,
+        "steps": len(rates), "warmup": 1, "ms_per_step": 1e3 / best["images_per_s"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "bf16 (f32 accumulate)" if args.precision else "f32",
-        "data": "synthetic (ellipse cells, Gaussian or Poisson-Gaussian, u16-quantised)",
-        "config": {"workload": f"{args.jobs} requests, Poisson arrivals at {args.rate}/s, square "
-                               f"sides log-uniform 256..{args.max_side}, stopping rule",
-                   "slots": args.slots, "widths": WIDTH_NAMES[args.widths]},
-        "latency_ms": {"p50": pct(lat, 0.5), "p99": pct(lat, 0.99), "max": max(lat)},
-        "offered_rate": args.rate, "completed": len(res),
+        "data": "synthetic (ellipse cells, Gaussian or Poisson-Gaussian, 16-bit)",
+        "config": {"workload": f"{len(base)} requests per rate (the first {args.jobs} of a "
+                               "seeded 1000-request stream and its two largest), Poisson "
+                               "arrivals at "
+                               f"{args.rates} /s, square sides log-uniform 256..{args.max_side}, "
+                               "16-bit input, stopping rule",
+                   "slots": args.slots, "hbm_budget_gb": args.budget_gb,
+                   "widths": WIDTH_NAMES[args.widths],
+                   "sides": {"min": min(sides), "max": max(sides),
+                             "n_2048": sum(1 for x in sides if x >= 2000)}},
+        "per_rate": rows,
     }
 
 
@@ -607,9 +708,14 @@ def main():
     ap.add_argument("--form", default="plain",
                     choices=["plain", "batched", "serving", "zstack", "variants"])
     ap.add_argument("--compare-batch", type=int, default=16,
-                    help="plain form: also run this many images in the bf16 form together (0 = off)")
+                    help="plain form: also run the timed images in the bf16 form, this many in "
+                         "flight, and the batching form's job mix (0 = off)")
+    ap.add_argument("--c3-jobs", type=int, default=64,
+                    help="plain form: jobs of the batching form's size mix run in bf16")
     ap.add_argument("--jobs", type=int, default=64, help="batched / serving: number of images")
-    ap.add_argument("--rate", type=float, default=5.0, help="serving: arrivals per second")
+    ap.add_argument("--rates", default="1,2,5,10,20,50,100,200",
+                    help="serving: arrival rates per second, one stream each")
+    ap.add_argument("--budget-gb", type=float, default=150.0, help="serving: HBM admission budget")
     ap.add_argument("--slots", type=int, default=64, help="serving: jobs resident at once")
     ap.add_argument("--max-side", type=int, default=2048, help="serving: largest image side")
     ap.add_argument("--z", type=int, default=41, help="zstack: slices")

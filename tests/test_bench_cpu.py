@@ -132,8 +132,18 @@ def test_cpu_baseline_scales_one_crop_epoch_to_a_whole_run(monkeypatch):
     # one epoch on a 128x128 crop taking t seconds stands for (512/128)^2 = 16 times the pixels
     # and MIN_EPOCHS = 101 epochs (one best epoch + 100 without improvement)
     monkeypatch.setattr(bench, "oracle_epoch_seconds", lambda noisy, widths, crop=128: 0.5)
+    monkeypatch.setattr(bench, "oracle_whole_run", lambda widths: {"seconds": 1.0})
     cb = bench.cpu_baseline(None, 512, 0)
+    assert cb["whole_run_measured"] == {"seconds": 1.0}
     assert bench.MIN_EPOCHS == 101
     assert cb["value"] == pytest.approx(1.0 / (101 * 16 * 0.5))
     assert cb["unit"] == "images/s" and cb["kind"] == "oracle" and cb["cores"] >= 1
     assert "128x128" in cb["sample"]
+
+
+def test_oracle_whole_run_is_a_stopping_rule_run():
+    # a whole run on a tiny image: the rule fires after at least 101 epochs, and the rate per
+    # pixel-epoch follows from the measured seconds
+    w = bench.oracle_whole_run(1, side=8)
+    assert w["image"] == [8, 8] and w["epochs"] >= bench.MIN_EPOCHS and w["seconds"] > 0
+    assert w["us_per_pixel_epoch"] == pytest.approx(w["seconds"] / (w["epochs"] * 64) * 1e6)
