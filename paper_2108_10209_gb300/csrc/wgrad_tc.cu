@@ -566,70 +566,90 @@ __global__ void __launch_bounds__(W3Warps<EXP>::kThreads, W3Warps<EXP>::kPerSm) 
   }
 }
 
-// gw[(o*C_in + c)*9 + tap] = sum over s of part[s][tap][c][o]. A block owns 32 consecutive o
-// (the lanes, so every read is one 128-byte row) of one input channel c and all 9 taps; warp w
-// sums the splits s = w, w + 8, ... in order and the eight warp sums are added in warp order,
-// so the result is fixed for a given number of splits.
-constexpr int kRwO = 32;
-// The last C_out blocks sum the bias partials bpart[s][o], one column each: every thread a fixed
-// strided subset of the splits in order, then a fixed tree.
+// gw[(o*C_in + c)*9 + tap] = sum over s of part[s][tap][c][o], and gb[o] = sum over s of
+// bpart[s][o]. Work unit: four consecutive o of one (tap, c) row (a float4 of every split's
+// slab). A block's eight warps form kRwGroups(S) split ranges x (8 / that) unit groups of 32
+// units; each thread sums its unit over its contiguous range of splits in split order (four
+// loads in flight), and the ranges' sums are then added in range order, so the result is fixed
+// for a given number of splits. The S loads of a unit are spread over up to eight warps so that
+// the many-split layers (small C) do not wait on one long chain of loads. The last blocks do the
+// bias partials the same way.
+__host__ __device__ inline int kRwGroups(int S) { return S >= 32 ? 8 : S >= 16 ? 4 : S >= 8 ? 2 : 1; }
+
 __global__ void __launch_bounds__(256) k_reduce_wgrad_tc(const float* __restrict__ part, int S,
                                                          int cin, int cout,
                                                          float* __restrict__ gw,
                                                          const float* __restrict__ bpart,
-                                                         float* __restrict__ gb, const int* skip) {
+                                                         float* __restrict__ gb, int wblocks,
+                                                         const int* skip) {
   if (skip && *skip) return;
-  __shared__ float sh[8][9][kRwO + 1];
+  __shared__ float4 red[8][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int otiles = (cout + kRwO - 1) / kRwO;
-  if (blockIdx.x >= otiles * cin) {
-    float* tr = &sh[0][0][0];  // 256 floats
-    const int o = blockIdx.x - otiles * cin;
-    float a = 0.f;
-    for (int k = threadIdx.x; k < S; k += blockDim.x) a += bpart[(size_t)k * cout + o];
-    tr[threadIdx.x] = a;
-    __syncthreads();
-    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-      if (threadIdx.x < h) tr[threadIdx.x] += tr[threadIdx.x + h];
-      __syncthreads();
+  const int R = kRwGroups(S), UG = 8 / R;  // split ranges, unit groups per block
+  const int r = w % R, ug = w / R;
+  const bool bias = (int)blockIdx.x >= wblocks;
+  const int blk = bias ? (int)blockIdx.x - wblocks : (int)blockIdx.x;
+  const size_t per4 = bias ? (size_t)cout / 4 : (size_t)9 * cin * cout / 4;  // units per split
+  const float4* src = reinterpret_cast<const float4*>(bias ? bpart : part);
+  const size_t u = ((size_t)blk * UG + ug) * 32 + lane;
+  const int s0 = (int)((long)S * r / R), s1 = (int)((long)S * (r + 1) / R);
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (u < per4) {
+    const float4* q = src + u;
+    int k = s0;
+    for (; k + 4 <= s1; k += 4) {
+      const float4 a = q[(size_t)k * per4], b = q[(size_t)(k + 1) * per4],
+                   c = q[(size_t)(k + 2) * per4], d = q[(size_t)(k + 3) * per4];
+      acc.x = (((acc.x + a.x) + b.x) + c.x) + d.x;
+      acc.y = (((acc.y + a.y) + b.y) + c.y) + d.y;
+      acc.z = (((acc.z + a.z) + b.z) + c.z) + d.z;
+      acc.w = (((acc.w + a.w) + b.w) + c.w) + d.w;
     }
-    if (threadIdx.x == 0) gb[o] = tr[0];
+    for (; k < s1; ++k) {
+      const float4 a = q[(size_t)k * per4];
+      acc.x += a.x;
+      acc.y += a.y;
+      acc.z += a.z;
+      acc.w += a.w;
+    }
+  }
+  red[w][lane] = acc;
+  __syncthreads();
+  if (r != 0 || u >= per4) return;
+  float4 v = red[ug * R][lane];
+  for (int k = 1; k < R; ++k) {
+    const float4 a = red[ug * R + k][lane];
+    v.x += a.x;
+    v.y += a.y;
+    v.z += a.z;
+    v.w += a.w;
+  }
+  if (bias) {  // gb comes from the caller at the op-level entry points: align before a float4 store
+    if ((reinterpret_cast<uintptr_t>(gb) & 15u) == 0) {
+      reinterpret_cast<float4*>(gb)[u] = v;
+    } else {
+      gb[4 * u] = v.x;
+      gb[4 * u + 1] = v.y;
+      gb[4 * u + 2] = v.z;
+      gb[4 * u + 3] = v.w;
+    }
     return;
   }
-  const int o0 = (blockIdx.x % otiles) * kRwO, c = blockIdx.x / otiles;
-  const int o = o0 + lane;
-  const size_t per = (size_t)9 * cout * cin, tstride = (size_t)cin * cout;
-  float acc[9];
+  // unit u = (tap * C_in + c) * (C_out / 4) + o / 4
+  const size_t row = u / ((size_t)cout / 4);
+  const int o = (int)(u - row * ((size_t)cout / 4)) * 4;
+  const int tap = (int)(row / cin), c = (int)(row - (size_t)tap * cin);
+  const float vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-  for (int t = 0; t < 9; ++t) acc[t] = 0.f;
-  if (o < cout) {
-    // splits w, w + 8, ... in order, four loads of each tap in flight (a, b, c, d hold the
-    // splits w + 32 i, w + 32 i + 8, ... and are added in that order)
-    const float* src = part + (size_t)c * cout + o;
-    int k = w;
-    for (; k + 24 < S; k += 32)
-#pragma unroll
-      for (int t = 0; t < 9; ++t) {
-        const float* q = src + (size_t)t * tstride;
-        const float a = q[k * per], b = q[(k + 8) * per], cc = q[(k + 16) * per],
-                    d = q[(k + 24) * per];
-        acc[t] = (((acc[t] + a) + b) + cc) + d;
-      }
-    for (; k < S; k += 8)
-#pragma unroll
-      for (int t = 0; t < 9; ++t) acc[t] += src[k * per + t * tstride];
-  }
-#pragma unroll
-  for (int t = 0; t < 9; ++t) sh[w][t][lane] = acc[t];
-  __syncthreads();
-  for (int i = threadIdx.x; i < kRwO * 9; i += 256) {
-    const int oo = i / 9, t = i % 9;
-    if (o0 + oo >= cout) continue;
-    float v = 0.f;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) v += sh[k][t][oo];
-    gw[((size_t)(o0 + oo) * cin + c) * 9 + t] = v;
-  }
+  for (int j = 0; j < 4; ++j) gw[((size_t)(o + j) * cin + c) * 9 + tap] = vv[j];
+}
+
+// Grid of k_reduce_wgrad_tc: weight blocks, then bias blocks.
+inline void reduce_grid(int S, int cin, int cout, int* wblocks, int* total) {
+  const int per_block = 32 * (8 / kRwGroups(S));  // units per block
+  const size_t uw = (size_t)9 * cin * cout / 4, ub = (size_t)cout / 4;
+  *wblocks = (int)((uw + per_block - 1) / per_block);
+  *total = *wblocks + (int)((ub + per_block - 1) / per_block);
 }
 
 }  // namespace
@@ -750,10 +770,11 @@ static cudaError_t launch_wgrad_grouped(int bf16, const void* dout, const void* 
     k_wgrad_tc_f32<1, 0><<<grid, W3Warps<0>::kThreads, smem, st>>>(md, mx, p);
   count_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  // weights, and (last C_out blocks) the bias from the S per-split sums of tap group 0
-  const int rot = (cout + kRwO - 1) / kRwO;
-  k_reduce_wgrad_tc<<<(unsigned)(rot * cin + cout), 256, 0, st>>>(part, S, cin, cout, gw, p.bpart,
-                                                                  gb, skip);
+  // weights, and (last blocks) the bias from the S per-split sums of tap group 0
+  int wblocks = 0, rblocks = 0;
+  reduce_grid(S, cin, cout, &wblocks, &rblocks);
+  k_reduce_wgrad_tc<<<(unsigned)rblocks, 256, 0, st>>>(part, S, cin, cout, gw, p.bpart, gb,
+                                                       wblocks, skip);
   count_launch();
   return cudaGetLastError();
 }

@@ -21,8 +21,8 @@ epoch:
     is within the fixed-run bar: max-abs 2e-3 and 0.05 dB PSNR.
 The free-running job is checked for what is unique to it: its history ring holds its own scores,
 the oracle's stopping rule replayed on them fires where the GPU's fired, the first epoch (before
-the trajectories separate) matches the oracle's golden run, and the final quality stays within
-the spread that float32 trajectories show.
+the trajectories separate) matches the oracle's golden run, and the final quality lies within
+the oracle's own spread over initial seeds.
 """
 import os
 
@@ -185,7 +185,7 @@ def test_forced_run_short_patience_both_windows(n2f, incl_best):
 def test_free_run_against_the_oracle_golden(n2f):
     """A free-running job through the job API on the 48x48 golden image (literal widths,
     patience 100): its validation history, its own decisions, its first epoch against the
-    oracle's, and its output quality against the spread of float32 trajectories."""
+    oracle's, and its output quality against the oracle's own spread over initial seeds."""
     g = np.load(GOLDEN)
     noisy, clean = g["noisy"], g["clean"]
     p = n2f.params(seed=int(g["init_seed"]), patience=int(g["patience"]))
@@ -209,11 +209,14 @@ def test_free_run_against_the_oracle_golden(n2f):
     assert st.last_mse == hist[-1]
     # epoch 1 starts from bit-identical weights: its score is within the one-epoch bar
     assert abs(hist[0] - g["scores"][0]) <= SCORE_REL[0]["max"] * g["scores"][0]
-    # the run's quality: the spread of whole float32 runs around the oracle's (measured up to
-    # 0.9 dB on 32x32 and 48x48 images between the engines and the oracle) bounds the output
-    p_gpu, p_orc, p_noisy = _psnr(out, clean), _psnr(g["out"], clean), _psnr(noisy, clean)
-    print(f"free run: GPU stop {st.epoch} (oracle {int(g['stop_epoch'])}), PSNR GPU {p_gpu:.3f}, "
-          f"oracle {p_orc:.3f}, noisy {p_noisy:.3f} dB; first-epoch score rel "
+    # the run's quality: a free run's trajectory is one sample of the method's run-to-run
+    # variation, so its PSNR must lie within the oracle's own spread over initial seeds (the
+    # golden run and SPREAD_SEEDS more, each FP64 to its stop) around their mean
+    orc = np.concatenate([[_psnr(g["out"], clean)], g["spread_psnr"]])
+    p_gpu, p_noisy = _psnr(out, clean), _psnr(noisy, clean)
+    print(f"free run: GPU stop {st.epoch} (oracle {int(g['stop_epoch'])}, other seeds "
+          f"{list(g['spread_stop_epochs'])}), PSNR GPU {p_gpu:.3f}, oracle seeds "
+          f"{np.round(orc, 3).tolist()}, noisy {p_noisy:.3f} dB; first-epoch score rel "
           f"{abs(hist[0] - g['scores'][0]) / g['scores'][0]:.2e}")
-    assert abs(p_gpu - p_orc) <= 1.0
+    assert abs(p_gpu - orc.mean()) <= orc.max() - orc.min()
     assert p_gpu > p_noisy + 3.0
