@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc_bf16(const __grid_constant_
 // of the bf16 kernel applies unchanged: TMA brings the fp32 tiles, eight split warps write the
 // two fp16 images of each, one MMA warp issues three MMAs per tap and K step.
 constexpr int kW3KP = 16;  // pixels per stage (one 16-element K step)
-constexpr int kW3MaxStages = 6;
+constexpr int kW3MaxStages = 12;
 // split warps (then epilogue warps): 16 for the one-row layers, whose CTA holds its SM alone
 // (TMEM), 8 for the tap-expanded small layers, which run two CTAs per SM
 template <int EXP>
@@ -302,8 +302,14 @@ struct W3Warps {
 static_assert(kW3MaxStages % W3Warps<0>::kTeams == 0 && 2 % W3Warps<0>::kTeams == 0,
               "float32 stage counts must stay multiples of the split team count");
 
+// One-row layers (not tap-expanded) split in place: the fp16 hi and lo images of each pair of
+// fp32 4-channel groups take that pair's two slots (hi in the first, lo in the second), so a
+// stage is its raw tiles alone (about half the bytes) and twice as many stages fit; the MMA
+// descriptors step two slots per 8-channel group. Tap-expanded layers write separate images.
 struct W3Layout {
   uint32_t rawA, rawB, a[2], b[2], stage;
+  uint32_t a_sbo, b_sbo;  // bytes between the operand images' 8-channel groups
+  uint32_t ext;           // offset of the two bias groups' images (B operand, tap group 0)
 };
 
 // raw x tile pitch: the 16 chunk pixels plus pu halo pixels on each side (the kernel loads whole
@@ -324,9 +330,26 @@ __host__ __device__ inline W3Layout w3_layout(int cin, int R, int pu, bool exp =
                                 + 2u * R * (kW3KP + 2) * 16;     // + 2 bias groups
   uint32_t o = 0;
   L.rawA = o; o += align_up(ra, 1024);
-  L.rawB = o; o += align_up(rb, 1024);
+  L.rawB = o;
+  if (!exp) {  // in place: a[k] / b[k] are the first hi / lo slots
+    const uint32_t slot = (uint32_t)R * w3_raw_pitch(pu) * 16;  // one 4-channel group of x
+    o += align_up(rb + 4u * slot, 1024);  // + the two bias groups' hi and lo slots
+    L.a[0] = L.rawA;
+    L.a[1] = L.rawA + kW3KP * 16;
+    L.b[0] = L.rawB;
+    L.b[1] = L.rawB + slot;
+    L.a_sbo = 2u * kW3KP * 16;
+    L.b_sbo = 2u * slot;
+    L.ext = L.rawB + (uint32_t)cin / 4 * slot;
+    L.stage = o;
+    return L;
+  }
+  o += align_up(rb, 1024);
   for (int k = 0; k < 2; ++k) { L.a[k] = o; o += align_up(pa, 1024); }
   for (int k = 0; k < 2; ++k) { L.b[k] = o; o += align_up(pb, 1024); }
+  L.a_sbo = kW3KP * 16;
+  L.b_sbo = (uint32_t)R * (kW3KP + 2) * 16;
+  L.ext = 0;
   L.stage = o;
   return L;
 }
@@ -342,9 +365,12 @@ __device__ __forceinline__ void split2_group(const float4 c03, const float4 c47,
 }
 
 // Splits one stage. Delta tile: raw [32 g4][16 px], parts [16 g8][16 px]. x tile: raw
-// [C/4][R][16 + 2 pu px], parts [C/8][R][18 px] (raw column pu - 1 + i -> part column i). Each
-// quarter-warp takes 8 consecutive pixels of one row, so its eight 16-byte reads fall in
-// distinct bank groups; the 2 halo pixels of each row follow in a short second pass.
+// [C/4][R][16 + 2 pu px], parts [C/8][R][18 px] (raw column pu - 1 + i -> part column i). The
+// parts' 8-channel groups lie L.a_sbo / L.b_sbo bytes apart: in the in-place layout (pu = 1,
+// one-row layers) group g8's hi and lo images take raw slots 2 g8 and 2 g8 + 1, the very slots
+// the thread read them from. Each quarter-warp takes 8 consecutive pixels of one row, so its
+// eight 16-byte reads fall in distinct bank groups; the 2 halo pixels of each row follow in a
+// short second pass.
 template <int R, int EXP>
 __device__ __forceinline__ void split2_stage(const uint8_t* st, uint8_t* stw, const W3Layout& L,
                                              int g8n, int pu, int et, int nt, int t0, int r0,
@@ -354,11 +380,12 @@ __device__ __forceinline__ void split2_stage(const uint8_t* st, uint8_t* stw, co
   const int PR = w3_raw_pitch(pu);
   {
     const float4* raw = reinterpret_cast<const float4*>(st + L.rawA);
+    const int ga = (int)(L.a_sbo / 16);  // 16-byte units between the parts' groups
     for (int u = et; u < 16 * kW3KP; u += kThr) {
       const int g8 = u / kW3KP, px = u % kW3KP;
       split2_group(raw[(2 * g8) * kW3KP + px], raw[(2 * g8 + 1) * kW3KP + px], sd,
                    reinterpret_cast<uint4*>(stw + L.a[0]), reinterpret_cast<uint4*>(stw + L.a[1]),
-                   u);
+                   g8 * ga + px);
     }
   }
   const float4* raw = reinterpret_cast<const float4*>(st + L.rawB);
@@ -376,18 +403,19 @@ __device__ __forceinline__ void split2_stage(const uint8_t* st, uint8_t* stw, co
     }
     return;
   }
+  const int gb = (int)(L.b_sbo / 16);  // 16-byte units between the parts' groups
   const int nmain = g8n * R * kW3KP;
   for (int u = et; u < nmain; u += kThr) {
     const int q = u / kW3KP, i = 1 + u % kW3KP;  // q = g8 * R + r, part column i
     const int g8 = q / R, r = q - g8 * R, px = pu - 1 + i;
     split2_group(raw[((2 * g8) * R + r) * PR + px], raw[((2 * g8 + 1) * R + r) * PR + px], sx, b0,
-                 b1, q * PP + i);
+                 b1, g8 * gb + r * PP + i);
   }
   for (int u = et; u < g8n * R * 2; u += kThr) {
     const int q = u >> 1, i = (u & 1) ? PP - 1 : 0;
     const int g8 = q / R, r = q - g8 * R, px = pu - 1 + i;
     split2_group(raw[((2 * g8) * R + r) * PR + px], raw[((2 * g8 + 1) * R + r) * PR + px], sx, b0,
-                 b1, q * PP + i);
+                 b1, g8 * gb + r * PP + i);
   }
 }
 
@@ -426,11 +454,17 @@ __global__ void __launch_bounds__(W3Warps<EXP>::kThreads, W3Warps<EXP>::kPerSm) 
   }
   if (warp == 1) tmem_alloc(&tslot, ncols);
   if (bias) {  // hi part: ones, lo part: zeros, so the bias columns sum a_hi + a_lo
-    const uint32_t eo = EXP ? (uint32_t)nt * cn / 8 * kW3KP * 16 : (uint32_t)cn * R * (kW3KP + 2) * 2;
-    const uint32_t eb = EXP ? 2u * kW3KP * 16 : 2u * R * (kW3KP + 2) * 16;
-    for (int s = 0; s < ns; ++s)
-      for (int q = 0; q < 2; ++q)
-        fill_ext(smem + s * L.stage + L.b[q] + eo, eb, q == 0 ? kF16PairOne : 0u);
+    if (EXP) {
+      const uint32_t eo = (uint32_t)nt * cn / 8 * kW3KP * 16, eb = 2u * kW3KP * 16;
+      for (int s = 0; s < ns; ++s)
+        for (int q = 0; q < 2; ++q)
+          fill_ext(smem + s * L.stage + L.b[q] + eo, eb, q == 0 ? kF16PairOne : 0u);
+    } else {  // in place: the two bias groups' hi, lo, hi, lo slots after the raw x tile
+      const uint32_t slot = L.b_sbo / 2;
+      for (int s = 0; s < ns; ++s)
+        for (int k = 0; k < 4; ++k)
+          fill_ext(smem + s * L.stage + L.ext + k * slot, slot, (k & 1) ? 0u : kF16PairOne);
+    }
     fence_proxy_async();
   }
   tc_fence_before();
@@ -464,8 +498,8 @@ __global__ void __launch_bounds__(W3Warps<EXP>::kThreads, W3Warps<EXP>::kPerSm) 
       // the 14-bit field never carries). Up to kW3Mma MMA groups per chunk: the taps of the
       // group (one row) or, tap-expanded, the column chunks of at most 256.
       constexpr int kW3Mma = EXP ? 2 : 3;
-      const uint32_t a_sbo = kW3KP * 16;                     // next 8-channel group of delta
-      const uint32_t b_sbo = (uint32_t)R * (kW3KP + 2) * 16;  // next 8-channel group of x
+      const uint32_t a_sbo = L.a_sbo;  // next 8-channel group of delta
+      const uint32_t b_sbo = L.b_sbo;  // next 8-channel group of x
       const uint32_t s0 = smem_u32(smem);
       uint64_t da[2], db[kW3Mma][2];
       uint32_t dcol[kW3Mma], idw[kW3Mma];
