@@ -381,6 +381,18 @@ int n2f_conv3x3_wgrad(int engine, int precision, const void* dout, const void* i
 int n2f_conv3x3_wgrad_noalloc(int engine, int precision, const void* dout, const void* in, int cin,
                               int cout, int H, int W, float* dw, float* db, void* stream);
 
+/* ---- checked build ----------------------------------------------------------------------
+ * libn2f_checked.so (paper_2108_10209_gb300/build.py --checked: the same sources compiled with
+ * N2F_CHECKED) tests the global-memory indexes its kernels compute against the extent of the
+ * tensor each one addresses, known from the launch shapes and the workspace sizes: an index out
+ * of range is counted and that access skipped, so nothing traps and the context stays usable.
+ * n2f_check_status reports the count since the last clear on the current device and the first
+ * failing site as file * 100000 + line (file 1 kernels_basic.cu, 2 kernels_simt.cu,
+ * 3 conv_tc.cu, 4 wgrad_tc.cu; 0: none); clear != 0 zeroes the counts afterwards. Synchronises
+ * the device. N2F_ENOTSUP in the normal build (libn2f.so), whose kernels carry no checks;
+ * N2F_EINVAL for a NULL pointer; N2F_EDEVICE if the counts cannot be read. */
+int n2f_check_status(uint64_t* failures, int* first_site, int clear);
+
 /* ---- diagnostics ------------------------------------------------------------------------
  * One 128 x N tile of D = A * B^T (K-step by K-step) through the tcgen05 tensor cores, with the
  * operands given as ready shared-memory images (no swizzle) and the descriptor strides the

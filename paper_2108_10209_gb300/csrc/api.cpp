@@ -519,6 +519,30 @@ extern "C" int n2f_conv3x3_wgrad(int engine, int precision, const void* dout, co
   return herr ? N2F_ETIMEDOUT : N2F_OK;
 }
 
+extern "C" int n2f_check_status(uint64_t* failures, int* first_site, int clear) {
+  if (!failures || !first_site) return N2F_EINVAL;
+#ifndef N2F_CHECKED
+  (void)clear;
+  return N2F_ENOTSUP;
+#else
+  CKR(cudaDeviceSynchronize());
+  int (*const readers[4])(unsigned long long*, int*, int) = {check_read_basic, check_read_simt,
+                                                            check_read_conv, check_read_wgrad};
+  uint64_t total = 0;
+  int site = 0;
+  for (int k = 0; k < 4; ++k) {
+    unsigned long long f = 0;
+    int line = 0;
+    if (readers[k](&f, &line, clear)) return set_cuda_error(cudaGetLastError(), "n2f_check_status");
+    total += f;
+    if (f && !site) site = (k + 1) * 100000 + line;
+  }
+  *failures = total;
+  *first_site = site;
+  return N2F_OK;
+#endif
+}
+
 // ------------------------------------------------------------------------------------------
 // Job scheduler
 namespace {

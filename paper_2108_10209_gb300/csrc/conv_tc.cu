@@ -18,6 +18,7 @@
 #include <type_traits>
 
 #include "cg_util.cuh"
+#include "checked.cuh"
 #include "n2f_internal.h"
 #include "tc_common.cuh"
 #include "tc_layout.cuh"
@@ -348,10 +349,12 @@ __global__ void __launch_bounds__(ConvWarps<BF16>::kThreads, 1)
         return (size_t)((nt * NT + (c0 % NT) + q * GE) / GE) * npx + pix;
       };
       auto live = [&](int c0) { return x < tj.W && ty + c0 / NT < tj.H; };
+      const size_t ngroups = (size_t)(ntn * NT / GE) * npx;  // groups of the output (and mask)
       uint4 mnext[NG];
       if (MODE == 1 && live(cfirst))
 #pragma unroll
-        for (int q = 0; q < NG; ++q) mnext[q] = __ldg(mask + gidx(cfirst, q));
+        for (int q = 0; q < NG; ++q)
+          if (N2F_IN(gidx(cfirst, q), ngroups)) mnext[q] = __ldg(mask + gidx(cfirst, q));
       for (int c0 = cfirst; c0 < acc_cols; c0 += CSTEP) {
         uint4 mcur[NG];
 #pragma unroll
@@ -359,7 +362,8 @@ __global__ void __launch_bounds__(ConvWarps<BF16>::kThreads, 1)
         const int c1 = c0 + CSTEP;
         if (MODE == 1 && c1 < acc_cols && live(c1))
 #pragma unroll
-          for (int q = 0; q < NG; ++q) mnext[q] = __ldg(mask + gidx(c1, q));
+          for (int q = 0; q < NG; ++q)
+            if (N2F_IN(gidx(c1, q), ngroups)) mnext[q] = __ldg(mask + gidx(c1, q));
         uint32_t r[16];
         tmem_ld16(cbase + c0, r);
         tmem_ld_wait();
@@ -386,7 +390,7 @@ __global__ void __launch_bounds__(ConvWarps<BF16>::kThreads, 1)
           if (!BF16)
 #pragma unroll
             for (int j = 0; j < GE; ++j) mx = fmaxf(mx, fabsf(vv[j]));
-          store_group<T>((T*)tj.out, gidx(c0, q), vv);
+          if (N2F_IN(gidx(c0, q), ngroups)) store_group<T>((T*)tj.out, gidx(c0, q), vv);
         }
       }
       if (!BF16 && tj.sc.out) warp_absmax_to(mx, tj.sc.out);
@@ -677,5 +681,7 @@ cudaError_t launch_conv_tc_grouped(int mode, int bf16, int cin, int cout, const 
   count_launch();
   return e;
 }
+
+N2F_CHECK_READER(check_read_conv)
 
 }  // namespace n2f

@@ -4,6 +4,7 @@
 #include <math.h>
 
 #include "cg_util.cuh"
+#include "checked.cuh"
 #include "f16_split.cuh"
 #include "n2f_internal.h"
 #include "tc_layout.cuh"
@@ -32,13 +33,19 @@ __global__ void k_gather(const float* __restrict__ x, int H, int W, float* __res
     if (t < nup) {
       const int i = (int)(t / hw), j = (int)(t % hw);
       const float* row = x + (size_t)i * W;
-      ue[t] = row[2 * j + (i & 1)];
-      uo[t] = row[2 * j + 1 - (i & 1)];
+      const int je = 2 * j + (i & 1), jo = 2 * j + 1 - (i & 1);
+      if (N2F_IN(je, W) && N2F_IN(jo, W)) {
+        ue[t] = row[je];
+        uo[t] = row[jo];
+      }
     } else {
       const size_t u = t - nup;
       const int i = (int)(u / W), j = (int)(u % W);
-      le[u] = x[(size_t)(2 * i + (j & 1)) * W + j];
-      lo[u] = x[(size_t)(2 * i + 1 - (j & 1)) * W + j];
+      const int ie = 2 * i + (j & 1), io = 2 * i + 1 - (j & 1);
+      if (N2F_IN(ie, H) && N2F_IN(io, H)) {
+        le[u] = x[(size_t)ie * W + j];
+        lo[u] = x[(size_t)io * W + j];
+      }
     }
   }
 }
@@ -221,6 +228,8 @@ __device__ __forceinline__ void pack_one(float* fwd, float* dgr, void* tcf, void
   if (tcf) {
     const size_t fi = tc_index_cfg(tc_cfg(cin, cout, tc_bf16), cin, o, tap, c);
     const size_t di = tc_index_cfg(tc_cfg(cout, cin, tc_bf16), cout, c, 8 - tap, o);
+    const size_t nw = (size_t)cin * cout * 9;
+    if (!N2F_IN(fi, nw) || !N2F_IN(di, nw)) return;
     if (tc_bf16) {
       ((__nv_bfloat16*)tcf)[fi] = __float2bfloat16_rn(th);
       ((__nv_bfloat16*)tcd)[di] = __float2bfloat16_rn(th);
@@ -428,7 +437,8 @@ __global__ void k_pack_cg(const float* __restrict__ src, int C, size_t npx, T* _
        i += (size_t)gridDim.x * blockDim.x) {
     const int c = (int)(i / npx);
     const size_t p = i % npx;
-    dst[((size_t)(c / G) * npx + p) * G + (c % G)] = CGTraits<T>::from_float(src[i]);
+    const size_t di = ((size_t)(c / G) * npx + p) * G + (c % G);
+    if (N2F_IN(di, n)) dst[di] = CGTraits<T>::from_float(src[i]);
   }
 }
 
@@ -440,7 +450,8 @@ __global__ void k_unpack_cg(const T* __restrict__ src, int C, size_t npx, D* __r
        i += (size_t)gridDim.x * blockDim.x) {
     const int c = (int)(i / npx);
     const size_t p = i % npx;
-    dst[i] = (D)CGTraits<T>::to_float(src[((size_t)(c / G) * npx + p) * G + (c % G)]);
+    const size_t si = ((size_t)(c / G) * npx + p) * G + (c % G);
+    if (N2F_IN(si, n)) dst[i] = (D)CGTraits<T>::to_float(src[si]);
   }
 }
 
@@ -516,7 +527,7 @@ __device__ __forceinline__ void conv1_pixel(const float* __restrict__ img, int H
       v[k] = s > 0.f ? s : 0.f;
       mx = fmaxf(mx, v[k]);
     }
-    store_group<T>(out, (size_t)g * npx + p, v);
+    if (N2F_IN((size_t)g * npx + p, (size_t)(C / G) * npx)) store_group<T>(out, (size_t)g * npx + p, v);
   }
 }
 
@@ -570,7 +581,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_conv1_wgrad(const T* __restrict__ dout,
                                                      const float* __restrict__ img, int C0, int H,
                                                      int W, int C, float* __restrict__ part,
-                                                     const int* skip) {
+                                                     size_t part_cap, const int* skip) {
   if (skip && *skip) return;
   constexpr int G = CGTraits<T>::G;
   constexpr int TP = 64;
@@ -628,7 +639,8 @@ __global__ void __launch_bounds__(256) k_conv1_wgrad(const T* __restrict__ dout,
 #pragma unroll
   for (int r = 0; r < kConv1Acc; ++r) {
     const int qi = threadIdx.x + r * 256;
-    if (qi < Q) part[(size_t)blockIdx.x * Q + qi] = acc[r];
+    if (qi < Q && N2F_IN((size_t)blockIdx.x * Q + qi, part_cap))
+      part[(size_t)blockIdx.x * Q + qi] = acc[r];
   }
 }
 
@@ -671,9 +683,10 @@ cudaError_t launch_conv1_wgrad(const void* dout, const float* img, int C0, int H
   if (S < 1) return cudaErrorInvalidValue;
   if (bf16)
     k_conv1_wgrad<__nv_bfloat16><<<S, 256, 0, st>>>((const __nv_bfloat16*)dout, img, C0, H, W,
-                                                    C, part, skip);
+                                                    C, part, part_cap, skip);
   else
-    k_conv1_wgrad<float><<<S, 256, 0, st>>>((const float*)dout, img, C0, H, W, C, part, skip);
+    k_conv1_wgrad<float><<<S, 256, 0, st>>>((const float*)dout, img, C0, H, W, C, part, part_cap,
+                                            skip);
   count_launch();
   k_reduce_conv1<<<nblocks(Q, 32), 256, 0, st>>>(part, S, C, K, gw, gb, skip);
   N2F_LAUNCH_CHECK();
@@ -747,7 +760,8 @@ __global__ void __launch_bounds__(256) k_head_train(const T* __restrict__ a8, in
         d[k] = v[k] > 0.f ? dz * sw[g * G + k] : 0.f;
         dmx = fmaxf(dmx, fabsf(d[k]));
       }
-      store_group<T>(d8, (size_t)g * npx + p, d);
+      if (N2F_IN((size_t)g * npx + p, (size_t)(C / G) * npx))
+        store_group<T>(d8, (size_t)g * npx + p, d);
     } else {
 #pragma unroll
       for (int k = 0; k < G; ++k) v[k] = 0.f;
@@ -1013,5 +1027,7 @@ cudaError_t launch_result(const float* V, const float* S, const float* Vbest, fl
   k_result<<<g, 256, 0, st>>>(V, S, Vbest, out, n, state, fixed_mode);
   N2F_LAUNCH_CHECK();
 }
+
+N2F_CHECK_READER(check_read_basic)
 
 }  // namespace n2f

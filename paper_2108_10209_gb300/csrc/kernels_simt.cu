@@ -4,6 +4,7 @@
 //   dgrad:   out(p, c) = [mask(p, c) > 0] * sum_{tap', o} W[o][c][8 - tap'] in(p + tap', o)
 // (the dgrad weight copy already holds the rotated transpose, so both run the same loop).
 #include "cg_util.cuh"
+#include "checked.cuh"
 #include "n2f_internal.h"
 
 namespace n2f {
@@ -39,7 +40,8 @@ __global__ void __launch_bounds__(256) k_conv_simt(const T* __restrict__ in, int
       const int px = i % (TX + 2), r = (i / (TX + 2)) % 3, gg = i / ((TX + 2) * 3);
       const int yy = y + r - 1, xx = x0 + px - 1;
       float v[G];
-      if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
+      if (yy >= 0 && yy < H && xx >= 0 && xx < W &&
+          N2F_IN((size_t)(c0 / G + gg) * npx + (size_t)yy * W + xx, (size_t)(cin / G) * npx)) {
         load_group<T>(in, (size_t)(c0 / G + gg) * npx + (size_t)yy * W + xx, v);
       } else {
 #pragma unroll
@@ -81,6 +83,7 @@ __global__ void __launch_bounds__(256) k_conv_simt(const T* __restrict__ in, int
     const int x = x0 + tx + 16 * i;
     if (x >= W) continue;
     const size_t p = (size_t)y * W + x;
+    if (!N2F_IN((size_t)g * npx + p, (size_t)(cout / G) * npx)) continue;
     float mk[G];
     if (MODE == 1) load_group<T>(mask, (size_t)g * npx + p, mk);
     float v[4];
@@ -108,7 +111,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_wgrad_simt(const T* __restrict__ dout,
                                                     const T* __restrict__ in, int cin, int cout,
                                                     int H, int W, int rows, float* __restrict__ part,
-                                                    const int* skip) {
+                                                    size_t part_cap, const int* skip) {
   if (skip && *skip) return;
   constexpr int G = CGTraits<T>::G;
   __shared__ __align__(16) float sD[WTX][36];
@@ -178,8 +181,11 @@ __global__ void __launch_bounds__(256) k_wgrad_simt(const T* __restrict__ dout,
     if (o >= cout) continue;
     if (c < cin)
 #pragma unroll
-      for (int t = 0; t < 9; ++t) pp[((size_t)o * cin + c) * 9 + t] = acc[j][t];
-    if (blockIdx.y == 0 && ic == 0) pp[(size_t)cout * cin * 9 + o] = bacc[j];
+      for (int t = 0; t < 9; ++t)
+        if (N2F_IN(pp + ((size_t)o * cin + c) * 9 + t - part, part_cap))
+          pp[((size_t)o * cin + c) * 9 + t] = acc[j][t];
+    if (blockIdx.y == 0 && ic == 0 && N2F_IN(pp + (size_t)cout * cin * 9 + o - part, part_cap))
+      pp[(size_t)cout * cin * 9 + o] = bacc[j];
   }
 }
 
@@ -241,10 +247,10 @@ cudaError_t launch_wgrad_simt(int bf16, const void* dout, const void* in, int ci
   if (bf16)
     k_wgrad_simt<__nv_bfloat16><<<grid, 256, 0, st>>>((const __nv_bfloat16*)dout,
                                                       (const __nv_bfloat16*)in, cin, cout, H, W,
-                                                      rows, part, skip);
+                                                      rows, part, part_cap, skip);
   else
     k_wgrad_simt<float><<<grid, 256, 0, st>>>((const float*)dout, (const float*)in, cin, cout, H,
-                                              W, rows, part, skip);
+                                              W, rows, part, part_cap, skip);
   count_launch();
   unsigned g = (unsigned)((Q + 255) / 256);
   if (g > 152u * 8) g = 152u * 8;
@@ -252,5 +258,7 @@ cudaError_t launch_wgrad_simt(int bf16, const void* dout, const void* in, int ci
   count_launch();
   return cudaGetLastError();
 }
+
+N2F_CHECK_READER(check_read_simt)
 
 }  // namespace n2f

@@ -218,6 +218,14 @@ cudaError_t launch_val_accum(const float* V, float* S, float* Vbest, size_t n,
 cudaError_t launch_result(const float* V, const float* S, const float* Vbest, float* out, size_t n,
                           const DevState* state, int fixed_mode, cudaStream_t st);
 
+// Checked builds (N2F_CHECKED, checked.cuh): each kernel file's count of indexes found outside
+// their tensor and the first such source line, on the current device (clear != 0: zero them
+// afterwards); the normal build reports zeros.
+int check_read_basic(unsigned long long* fails, int* line, int clear);
+int check_read_simt(unsigned long long* fails, int* line, int clear);
+int check_read_conv(unsigned long long* fails, int* line, int clear);
+int check_read_wgrad(unsigned long long* fails, int* line, int clear);
+
 // Count of kernel launches made by this thread's current owner (see LaunchCounter).
 extern thread_local uint64_t* tl_launch_counter;
 inline void count_launch(int n = 1) {

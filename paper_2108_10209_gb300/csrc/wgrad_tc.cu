@@ -12,6 +12,7 @@
 #include <type_traits>
 
 #include "cg_util.cuh"
+#include "checked.cuh"
 #include "n2f_internal.h"
 #include "tc_common.cuh"
 #include "tc_layout.cuh"
@@ -70,6 +71,7 @@ constexpr uint32_t kF16PairOne = 0x3C003C00u;   // two fp16 1.0
 
 struct WgBf16Params {
   float* part;  // [S][9][C_in][C_out]
+  size_t part_cap;  // floats of the workspace at part (partials, then the bias partials)
   int cin, cout, H, W, chunks_x, total_chunks, per_split;
   int stages;  // pipeline stages
   int pu;      // bf16 kernel: pixels per TMA unit of both maps
@@ -262,14 +264,17 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc_bf16(const __grid_constant_
         tmem_ld_wait();
         if (!live) continue;
 #pragma unroll
-        for (int q = 0; q < 16; ++q) dst[(size_t)(c0 + q) * p.cout] = nk ? __uint_as_float(r[q]) : 0.f;
+        for (int q = 0; q < 16; ++q)
+          if (N2F_IN(dst + (size_t)(c0 + q) * p.cout - p.part, p.part_cap))
+            dst[(size_t)(c0 + q) * p.cout] = nk ? __uint_as_float(r[q]) : 0.f;
       }
     }
     if (bias) {
       uint32_t r[16];
       tmem_ld16(tbase + ((uint32_t)(wq * 32) << 16) + (uint32_t)(nt * cn), r);
       tmem_ld_wait();
-      if (live) p.bpart[(size_t)s_idx * p.cout + o] = nk ? __uint_as_float(r[0]) : 0.f;
+      if (live && N2F_IN(p.bpart + (size_t)s_idx * p.cout + o - p.part, p.part_cap))
+        p.bpart[(size_t)s_idx * p.cout + o] = nk ? __uint_as_float(r[0]) : 0.f;
     }
   }
   tc_fence_before();
@@ -582,14 +587,16 @@ __global__ void __launch_bounds__(W3Warps<EXP>::kThreads, W3Warps<EXP>::kPerSm) 
         if (!live) continue;
 #pragma unroll
         for (int q = 0; q < 16; ++q)
-          dst[(size_t)(c0 + q) * p.cout] = nk ? __uint_as_float(r[q]) * ud * ux : 0.f;
+          if (N2F_IN(dst + (size_t)(c0 + q) * p.cout - p.part, p.part_cap))
+            dst[(size_t)(c0 + q) * p.cout] = nk ? __uint_as_float(r[q]) * ud * ux : 0.f;
       }
     }
     if (bias && half == 0) {
       uint32_t r[16];
       tmem_ld16(tbase + ((uint32_t)(wq * 32) << 16) + (uint32_t)(nt * cn), r);
       tmem_ld_wait();
-      if (live) p.bpart[(size_t)s_idx * p.cout + o] = nk ? __uint_as_float(r[0]) * ud : 0.f;
+      if (live && N2F_IN(p.bpart + (size_t)s_idx * p.cout + o - p.part, p.part_cap))
+        p.bpart[(size_t)s_idx * p.cout + o] = nk ? __uint_as_float(r[0]) * ud : 0.f;
     }
   }
   tc_fence_before();
@@ -615,7 +622,7 @@ __global__ void __launch_bounds__(256) k_reduce_wgrad_tc(const float* __restrict
                                                          float* __restrict__ gw,
                                                          const float* __restrict__ bpart,
                                                          float* __restrict__ gb, int wblocks,
-                                                         const int* skip) {
+                                                         size_t part_cap, const int* skip) {
   if (skip && *skip) return;
   __shared__ float4 red[8][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -628,7 +635,9 @@ __global__ void __launch_bounds__(256) k_reduce_wgrad_tc(const float* __restrict
   const size_t u = ((size_t)blk * UG + ug) * 32 + lane;
   const int s0 = (int)((long)S * r / R), s1 = (int)((long)S * (r + 1) / R);
   float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (u < per4) {
+  // float4 units of the workspace from src on
+  const size_t cap4 = (part_cap - (size_t)((bias ? bpart : part) - part)) / 4;
+  if (u < per4 && N2F_IN((size_t)(s1 > 0 ? s1 - 1 : 0) * per4 + u, cap4)) {
     const float4* q = src + u;
     int k = s0;
     for (; k + 4 <= s1; k += 4) {
@@ -675,7 +684,9 @@ __global__ void __launch_bounds__(256) k_reduce_wgrad_tc(const float* __restrict
   const int tap = (int)(row / cin), c = (int)(row - (size_t)tap * cin);
   const float vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-  for (int j = 0; j < 4; ++j) gw[((size_t)(o + j) * cin + c) * 9 + tap] = vv[j];
+  for (int j = 0; j < 4; ++j)
+    if (N2F_IN(((size_t)(o + j) * cin + c) * 9 + tap, (size_t)9 * cin * cout))
+      gw[((size_t)(o + j) * cin + c) * 9 + tap] = vv[j];
 }
 
 // Grid of k_reduce_wgrad_tc: weight blocks, then bias blocks.
@@ -788,6 +799,7 @@ static cudaError_t launch_wgrad_grouped(int bf16, const void* dout, const void* 
   p.per_split = (p.total_chunks + S - 1) / S;
   S = (p.total_chunks + p.per_split - 1) / p.per_split;
   p.part = part;
+  p.part_cap = part_cap;
   p.bpart = part + ((size_t)S * per_split_elems + 63) / 64 * 64;
   p.skip = skip;
   p.err = err;
@@ -808,7 +820,7 @@ static cudaError_t launch_wgrad_grouped(int bf16, const void* dout, const void* 
   int wblocks = 0, rblocks = 0;
   reduce_grid(S, cin, cout, &wblocks, &rblocks);
   k_reduce_wgrad_tc<<<(unsigned)rblocks, 256, 0, st>>>(part, S, cin, cout, gw, p.bpart, gb,
-                                                       wblocks, skip);
+                                                       wblocks, part_cap, skip);
   count_launch();
   return cudaGetLastError();
 }
@@ -822,5 +834,7 @@ cudaError_t launch_wgrad_tc(int bf16, const void* dout, const void* in, int cin,
   return launch_wgrad_grouped(bf16, dout, in, cin, cout, H, W, dmax, xmax, part, part_cap, gw, gb,
                               skip, err, st);
 }
+
+N2F_CHECK_READER(check_read_wgrad)
 
 }  // namespace n2f

@@ -13,7 +13,10 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libn2f.so")
+# N2F_LIBRARY=checked loads the checked build (libn2f_checked.so: bounds-checked kernel indexes,
+# see n2f_check_status); anything else, or unset, the normal library
+LIB_PATH = os.path.join(_HERE, "libn2f_checked.so" if os.environ.get("N2F_LIBRARY") == "checked"
+                        else "libn2f.so")
 
 N2F_OK, N2F_EINVAL, N2F_ETOOBIG, N2F_EAGAIN, N2F_ENOENT = 0, -1, -2, -3, -4
 N2F_ETIMEDOUT, N2F_ENONFINITE, N2F_EDEVICE, N2F_ENOMEM, N2F_ECANCELED, N2F_ENOTSUP = (
@@ -114,6 +117,7 @@ SIGNATURES = {
     "n2f_umma_gemm": (_I, [_I, _I, _I, _I, _I, _P, _Z, C.c_uint32, C.c_uint32, C.c_uint32, _P, _Z,
                            C.c_uint32, C.c_uint32, C.c_uint32, _P, _P]),
     "n2f_wait_probe": (_I, [C.c_uint32, _P]),
+    "n2f_check_status": (_I, [C.POINTER(_U64), C.POINTER(_I), _I]),
 }
 
 _lib = None
@@ -573,6 +577,14 @@ def umma_gemm(A_img, a_lbo, a_sbo, a_kstep, B_img, b_lbo, b_sbo, b_kstep, N, K, 
                               a_sbo, a_kstep, _ptr(B_img), B_img.numel(), b_lbo, b_sbo, b_kstep,
                               _ptr(D), _stream_ptr(stream)), "n2f_umma_gemm")
     return D
+
+
+def check_status(clear: bool = True):
+    """Checked build only: (indexes found out of range since the last clear, first failing site
+    as file * 100000 + line); raises N2FError(N2F_ENOTSUP) with the normal library."""
+    n, site = C.c_uint64(), C.c_int()
+    check(lib().n2f_check_status(C.byref(n), C.byref(site), int(clear)), "n2f_check_status")
+    return int(n.value), int(site.value)
 
 
 def wait_probe(limit_ms: int, stream=None) -> int:

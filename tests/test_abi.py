@@ -145,3 +145,10 @@ def test_trainer_rejects_images_before_touching_the_device(n2f, H, W, poison):
     tr = C.c_void_p()
     rc = n2f.lib().n2f_trainer_create(C.byref(tr), img.ctypes.data, H, W, None, None)
     assert rc == n2f.N2F_EINVAL and not tr.value
+
+
+def test_normal_build_has_no_checks(n2f):
+    # n2f_check_status answers N2F_ENOTSUP in libn2f.so before touching any device
+    n, site = C.c_uint64(7), C.c_int(7)
+    assert n2f.lib().n2f_check_status(C.byref(n), C.byref(site), 0) == n2f.N2F_ENOTSUP
+    assert n2f.lib().n2f_check_status(None, C.byref(site), 0) == n2f.N2F_EINVAL
