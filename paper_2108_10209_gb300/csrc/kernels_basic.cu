@@ -615,7 +615,9 @@ __global__ void __launch_bounds__(256) k_conv1_wgrad(const T* __restrict__ dout,
       const size_t p = p0 + pp;
       float v = 0.f;
       if (p < npx) {
-        const int y = (int)(p / W) + q / 3 - 1, x = (int)(p % W) + q % 3 - 1;
+        // 32-bit division: images hold fewer than 2^31 pixels
+        const unsigned p32 = (unsigned)p, yq = p32 / (unsigned)W;
+        const int y = (int)yq + q / 3 - 1, x = (int)(p32 - yq * (unsigned)W) + q % 3 - 1;
         if (y >= 0 && y < H && x >= 0 && x < W) v = img[(size_t)c * npx + (size_t)y * W + x];
       }
       sX[pp][cq] = v;
@@ -656,8 +658,15 @@ __global__ void __launch_bounds__(256) k_reduce_conv1(const float* __restrict__ 
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int q = blockIdx.x * 32 + lane;
   float s = 0.f;
-  if (q < Q)
-    for (int k = w; k < S; k += 8) s += part[(size_t)k * Q + q];
+  if (q < Q) {
+    int k = w;
+    for (; k + 24 < S; k += 32) {  // four loads in flight, added in split order
+      const float a = part[(size_t)k * Q + q], b = part[(size_t)(k + 8) * Q + q];
+      const float c = part[(size_t)(k + 16) * Q + q], d = part[(size_t)(k + 24) * Q + q];
+      s = (((s + a) + b) + c) + d;
+    }
+    for (; k < S; k += 8) s += part[(size_t)k * Q + q];
+  }
   sh[w][lane] = s;
   __syncthreads();
   if (w == 0 && q < Q) {
@@ -678,7 +687,7 @@ cudaError_t launch_conv1_wgrad(const void* dout, const float* img, int C0, int H
   const size_t npx = (size_t)H * W;
   const int K = C0 * 9, Q = C * (K + 1);
   int S = (int)((npx + 127) / 128);
-  if (S > 304) S = 304;
+  if (S > 608) S = 608;  // four blocks per SM: more loads in flight than two
   if ((size_t)S * Q > part_cap) S = (int)(part_cap / Q);
   if (S < 1) return cudaErrorInvalidValue;
   if (bf16)
