@@ -605,10 +605,13 @@ void group_unref(Group* g) {
   delete g;
 }
 
-// Jobs that may share a group: everything that shapes the kernels and the schedule is equal.
+// Jobs that may share a group: everything that shapes the kernels and the schedule is equal,
+// the image size included -- members of different sizes run their per-member kernels for
+// different times, and the group's epoch waits for the largest at every join.
 bool same_group_key(const Job* a, const Job* b) {
   const n2f_params &p = a->prm, &q = b->prm;
-  return p.precision == q.precision && p.widths == q.widths && p.engine == q.engine &&
+  return a->H == b->H && a->W == b->W &&
+         p.precision == q.precision && p.widths == q.widths && p.engine == q.engine &&
          p.loss == q.loss && p.channels == q.channels && p.downsample == q.downsample &&
          p.exact == q.exact && p.fixed_steps < 0 && q.fixed_steps < 0 &&
          a->src_kind != 2 && b->src_kind != 2;

@@ -38,13 +38,16 @@ def _run(n2f, imgs, p, **ctx_kw):
 
 @pytest.mark.parametrize("precision,widths", [(0, 0), (1, 0), (1, 1)])
 def test_group_members_equal_solo_runs(n2f, precision, widths):
-    imgs = [_img(40, 36, 1), _img(64, 64, 2), _img(33, 47, 3), _img(24, 80, 4)]
+    # groups form among jobs of the same size: two groups of two here, plus one job alone
+    imgs = [_img(40, 36, 1), _img(64, 64, 2), _img(40, 36, 3), _img(64, 64, 4), _img(33, 47, 5)]
     p = n2f.params(seed=5, patience=4, precision=precision, widths=widths)
-    solo, _ = _run(n2f, imgs, p)
+    solo, st_solo = _run(n2f, imgs, p)
     grp, st = _run(n2f, imgs, p, group_size=8)
     for (a, ea, sa), (b, eb, sb) in zip(solo, grp):
         assert ea == eb and sa == sb
         assert np.array_equal(a, b)
+    # the grouped forward / dgrad launches replaced the members' own: fewer kernels launched
+    assert st["kernel_launches"] < st_solo["kernel_launches"]
 
 
 def test_groups_split_by_parameters(n2f):
