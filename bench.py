@@ -253,7 +253,8 @@ def run_ours(args, ws, rank, local):
     from paper_2108_10209_gb300 import n2f
 
     size = args.size
-    p = n2f.params(seed=0, precision=args.precision, widths=args.widths, engine=args.engine)
+    p = n2f.params(seed=0, precision=args.precision, widths=args.widths, engine=args.engine,
+                   overlap=args.overlap)
     work = [image_for(i, rank, size) for i in range(args.warmup + args.steps)]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
     ctx = n2f.Context(device=local, max_slots=1, profile_kernel=args.profile_kernel,
@@ -289,6 +290,31 @@ def run_ours(args, ws, rank, local):
         torch.distributed.barrier()
     clk = clocks.stop()
     st1 = ctx.stats()
+    overlap = None
+    if not args.overlap:
+        # the same images again, each epoch's validation beside the next epoch's training
+        po = n2f.params(seed=0, precision=args.precision, widths=args.widths, engine=args.engine,
+                        overlap=1)
+        o_ms, same = [], True
+        for k, i in enumerate(range(args.warmup, args.warmup + args.steps)):
+            flush.zero_()
+            torch.cuda.synchronize()
+            x = work[i][1].astype(np.float32)
+            j = ctx.submit(x, po)
+            ctx.wait(j)
+            st = ctx.poll(j)
+            out = ctx.result(j, x.shape)
+            assert st.state == n2f.N2F_DONE, st.as_dict()
+            o_ms.append(st.compute_ms)
+            same = same and st.epoch == epochs[k] and bool(np.array_equal(out, outs[k]))
+        from paper_2108_10209_gb300 import dispatch
+        o_dev_s, o_img = dispatch.aggregate(sum(o_ms) / 1e3, args.steps)
+        overlap = {"value": o_img / o_dev_s, "unit": UNIT,
+                   "epochs_per_s_mpx": sum(epochs) * size * size / 1e6 / (sum(o_ms) / 1e3),
+                   "results_identical": same,
+                   "note": "n2f_params.overlap = 1: each epoch's validation on a second stream "
+                           "beside the next epoch's training (weights snapshot at the boundary); "
+                           "same images, same stop epochs"}
     ctx.close()
     from paper_2108_10209_gb300 import dispatch
     tot_dev_s, n_img = dispatch.aggregate(sum(comp_ms) / 1e3, args.steps)
@@ -330,6 +356,8 @@ def run_ours(args, ws, rank, local):
     line["psnr_db"] = [round(synth.psnr(o, work[args.warmup + k][0]), 3)
                        for k, o in enumerate(outs)]
     line["mpx_per_s"] = args.steps * size * size / 1e6 / tot_dev_s
+    if overlap is not None:
+        line["overlap_validation"] = overlap
     if args.compare_batch > 0 and args.precision == 0:
         line["bf16_batched"] = c3_batched(n2f, args.widths, args.c3_jobs)
         line["bf16_vs_fp32"] = bf16_vs_fp32(
@@ -704,6 +732,11 @@ def main():
     ap.add_argument("--profile-kernel", type=int, default=7,
                     help="kernel class timed for the roofline (7 conv forward+dgrad, 1 forward, "
                          "2 dgrad, 3 wgrad)")
+    ap.add_argument("--overlap", type=int, default=0,
+                    help="plain form: 1 validates each epoch beside the next epoch's training "
+                         "(n2f_params.overlap; results identical), 0 in line (the default: "
+                         "the roofline's per-launch times are then the kernels' own); with 0 the "
+                         "timed images are also run once with 1 and reported beside")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--form", default="plain",
                     choices=["plain", "batched", "serving", "zstack", "variants"])

@@ -151,6 +151,15 @@ typedef struct {
    * x_tgt - (s_tgt - s_in), removing the signal-difference term of the Theoretical Background. */
   int32_t downsample;   /* enum n2f_downsample */
   int32_t exact;
+  /* overlap = 1: a job that runs alone (not in a lockstep group, stopping rule) validates each
+   * epoch's weights on a second stream while the next epoch trains: the weights and packed
+   * copies are snapshot at the epoch boundary (one device copy) and the validation reads the
+   * snapshot, so the validation scores, the stop epoch and the result are bit-identical to
+   * overlap = 0. The epoch after the stop has then already run; its steps are discarded (Adam
+   * state counters restored, the weights not used again). Costs one more set of validation
+   * activations (2 x 256 x H x W elements) and the snapshot (about 3 x the weight count in
+   * floats). 0: each validation runs in line after its epoch (default). */
+  int32_t overlap;
 } n2f_params;
 
 typedef struct {

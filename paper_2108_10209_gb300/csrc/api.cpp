@@ -56,6 +56,7 @@ void n2f_params_default(n2f_params* p) {
   p->target_channel = 0;
   p->downsample = N2F_DOWN_CHECKER;
   p->exact = 0;
+  p->overlap = 0;
 }
 
 const char* n2f_strerror(int code) {
@@ -99,6 +100,7 @@ static int check_params(const n2f_params* p) {
     return N2F_EINVAL;
   if (p->downsample != N2F_DOWN_CHECKER && p->downsample != N2F_DOWN_QUAD) return N2F_EINVAL;
   if (p->exact != 0 && p->exact != 1) return N2F_EINVAL;
+  if (p->overlap != 0 && p->overlap != 1) return N2F_EINVAL;
   return N2F_OK;
 }
 
@@ -840,7 +842,7 @@ static bool progress(n2f_ctx* c, Job* j) {
     const uint32_t la = std::max<uint32_t>(1, c->cfg.lookahead);
     while (!j->finishing && j->ep_enq - j->ep_seen < la) {
       // epochs replay a captured graph (timed launches keep event-record nodes in it)
-      if ((rc = !c->cfg.use_graphs ? trainer_epoch(&j->tr) : trainer_epoch_graph(&j->tr)))
+      if ((rc = !c->cfg.use_graphs ? trainer_epoch_job(&j->tr) : trainer_epoch_graph(&j->tr)))
         break;
       const int slot = (int)(j->ep_enq % j->ring);
       cudaError_t e = cudaMemcpyAsync(&j->hst[slot], j->tr.state, sizeof(DevState),

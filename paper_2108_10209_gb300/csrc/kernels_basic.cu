@@ -1037,6 +1037,25 @@ cudaError_t launch_result(const float* V, const float* S, const float* Vbest, fl
   N2F_LAUNCH_CHECK();
 }
 
+// Overlapped validation: when the validation that ran beside an epoch stopped the job, that
+// epoch is discarded -- the step counters return to their values at the epoch boundary (the
+// weights it changed are not read again: the result comes from the validation outputs), so
+// the job ends in the state it would have had with the validation in line.
+__global__ void k_step_restore(DevState* __restrict__ state, const DevState* __restrict__ saved) {
+  if (threadIdx.x != 0 || !state->stopped) return;
+  state->t = saved->t;
+  state->b1t = saved->b1t;
+  state->b2t = saved->b2t;
+  state->bc1 = saved->bc1;
+  state->bc2 = saved->bc2;
+  state->loss = saved->loss;
+}
+
+cudaError_t launch_step_restore(DevState* state, const DevState* saved, cudaStream_t st) {
+  k_step_restore<<<1, 32, 0, st>>>(state, saved);
+  N2F_LAUNCH_CHECK();
+}
+
 N2F_CHECK_READER(check_read_basic)
 
 }  // namespace n2f

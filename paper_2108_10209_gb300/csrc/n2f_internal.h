@@ -55,10 +55,14 @@ struct DevState {
 // The Adam kernel clears `act` and `delta` after every step, so a word bounds the tensor's
 // current contents (it may also cover an earlier pass: still a bound, never too small).
 struct ScaleWords {
-  unsigned act[kLayers];       // act[m]: output of layer m (training or validation forward)
+  unsigned act[kLayers];       // act[m]: output of layer m in the training forward
   unsigned delta[kLayers];     // delta[m]: masked gradient at layer m's pre-activation
   unsigned wnew[2][kLayers];   // weights after an Adam step, by the step's parity
   unsigned w[kLayers];         // the weights that the packed tensor-core copies were made from
+  // the validation forward's own words (cleared when a validation starts), so that training
+  // and validation scales never mix and the two may run at the same time
+  unsigned vact[kLayers];      // vact[m]: output of layer m in the validation forward
+  unsigned vw[kLayers];        // w[] as of the weight snapshot a concurrent validation reads
 };
 
 // Packed weight copies written by the init/Adam kernels, one per layer l = 0..7:
@@ -217,6 +221,9 @@ cudaError_t launch_val_accum(const float* V, float* S, float* Vbest, size_t n,
 // Result: S / patience, S / count, Vbest or V (fixed-step mode).
 cudaError_t launch_result(const float* V, const float* S, const float* Vbest, float* out, size_t n,
                           const DevState* state, int fixed_mode, cudaStream_t st);
+// Puts DevState's step counters back from `saved` if the job has stopped (overlapped
+// validation: the epoch that ran beside the deciding validation is discarded).
+cudaError_t launch_step_restore(DevState* state, const DevState* saved, cudaStream_t st);
 
 // Checked builds (N2F_CHECKED, checked.cuh): each kernel file's count of indexes found outside
 // their tensor and the first such source line, on the current device (clear != 0: zero them

@@ -164,6 +164,9 @@ static int layer_engine(const Trainer* t, int l) {
   return tc ? N2F_ENGINE_TC : N2F_ENGINE_SIMT;
 }
 
+// The job validates beside the next epoch's training (stopping-rule jobs only).
+static bool overlapped(const Trainer* t) { return t->prm.overlap && !t->fixed_mode; }
+
 // Carves every buffer out of one slab; with base == nullptr it only measures.
 static size_t layout(Trainer* t, char* base) {
   Carver c;
@@ -174,34 +177,65 @@ static size_t layout(Trainer* t, char* base) {
   t->x = c.take<float>(np * t->N);
   for (int k = 0; k < 4; ++k) t->sub[k] = c.take<float>(np * t->ph[k] * t->pw[k]);
   for (int k = 0; k < 4; ++k) t->tx[k] = c.take<float>(t->prm.exact ? (size_t)t->ph[k] * t->pw[k] : 0);
-  t->theta = c.take<float>(net.count);
-  t->grad = c.take<float>(net.count);
-  t->m = c.take<float>(net.count);
-  t->v = c.take<float>(net.count);
+  // theta and every weight copy a forward pass reads form one contiguous range: the snapshot
+  // that an overlapped validation reads
   memset(&t->pa, 0, sizeof(t->pa));
+  t->snap_off = align_up(c.off, 256);
+  t->theta = c.take<float>(net.count);
   bool any_tc = false;
   for (int l = 0; l < kLayers; ++l) {
     const size_t nw = (size_t)net.widths[l] * net.cin(l) * 9;
     t->pa.fwd[l] = c.take<float>(nw);
-    t->pa.dgr[l] = l > 0 ? c.take<float>(nw) : nullptr;
     if (l > 0 && t->engine[l] == N2F_ENGINE_TC) {
       any_tc = true;
       // 16-bit elements: bf16, or the float32 form's fp16 hi and lo parts
       t->pa.tcf[l] = c.take<uint16_t>(nw);
-      t->pa.tcd[l] = c.take<uint16_t>(nw);
-      if (!t->bf16) {
-        t->pa.tcf_lo[l] = c.take<uint16_t>(nw);
-        t->pa.tcd_lo[l] = c.take<uint16_t>(nw);
-      }
+      if (!t->bf16) t->pa.tcf_lo[l] = c.take<uint16_t>(nw);
     }
   }
+  t->snap_bytes = c.off - t->snap_off;
+  for (int l = 1; l < kLayers; ++l) {
+    const size_t nw = (size_t)net.widths[l] * net.cin(l) * 9;
+    t->pa.dgr[l] = c.take<float>(nw);
+    if (t->engine[l] == N2F_ENGINE_TC) {
+      t->pa.tcd[l] = c.take<uint16_t>(nw);
+      if (!t->bf16) t->pa.tcd_lo[l] = c.take<uint16_t>(nw);
+    }
+  }
+  t->grad = c.take<float>(net.count);
+  t->m = c.take<float>(net.count);
+  t->v = c.take<float>(net.count);
   t->sw = !t->bf16 && any_tc ? c.take<ScaleWords>(1) : nullptr;
   t->pa.sw = t->sw;
-  // activations / deltas (training) alias the validation ping-pong buffers
+  // activations / deltas (training) alias the validation ping-pong buffers, unless the two run
+  // at the same time (overlap)
+  const bool ovl = overlapped(t);
   const size_t Cmax = net.cmax(), Csum = net.csum();
   const size_t train_elems = Csum * t->maxP + (t->keep_deltas ? Csum : 2 * Cmax) * t->maxP;
   const size_t val_elems = 2 * Cmax * t->N;
-  char* region = c.take<char>(std::max(train_elems, val_elems) * es);
+  char* region = c.take<char>((ovl ? train_elems : std::max(train_elems, val_elems)) * es);
+  char* vregion = ovl ? c.take<char>(val_elems * es) : region;
+  char* vsnap = c.take<char>(ovl ? t->snap_bytes : 0);
+  DevState* ssave = c.take<DevState>(ovl ? 1 : 0);
+  if (base && ovl) {
+    t->vsnap = vsnap;
+    t->state_save = ssave;
+    // the snapshot's copies sit at the same offsets from vsnap as the live ones from snap_off
+    auto rebase = [&](auto* p) -> decltype(p) {
+      return p ? reinterpret_cast<decltype(p)>(vsnap + (reinterpret_cast<char*>(p) -
+                                                        (base + t->snap_off)))
+               : nullptr;
+    };
+    t->vpa = t->pa;
+    t->vpa.theta = rebase(t->theta);
+    for (int l = 0; l < kLayers; ++l) {
+      t->vpa.fwd[l] = rebase(t->pa.fwd[l]);
+      t->vpa.tcf[l] = rebase(t->pa.tcf[l]);
+      t->vpa.tcf_lo[l] = rebase(t->pa.tcf_lo[l]);
+      t->vpa.dgr[l] = nullptr;
+      t->vpa.tcd[l] = t->vpa.tcd_lo[l] = nullptr;
+    }
+  }
   if (base) {
     size_t o = 0;
     for (int l = 0; l < kLayers; ++l) {
@@ -218,8 +252,8 @@ static size_t layout(Trainer* t, char* base) {
       t->dl[0] = region + o * es;
       t->dl[1] = region + (o + Cmax * t->maxP) * es;
     }
-    t->vb[0] = region;
-    t->vb[1] = region + Cmax * t->N * es;
+    t->vb[0] = vregion;
+    t->vb[1] = vregion + Cmax * t->N * es;
   }
   t->dz = c.take<float>(t->maxP);
   t->V = c.take<float>(t->N);
@@ -301,6 +335,22 @@ int trainer_init(Trainer* t, const Allocator& al, cudaStream_t st, int want_u16)
   }
   pa.count = t->net.count;
   pa.tc_bf16 = t->bf16;
+  if (overlapped(t)) {
+    PackArgs v = pa;  // the shape fields; the pointers into the snapshot come from layout
+    v.theta = t->vpa.theta;
+    for (int l = 0; l < kLayers; ++l) {
+      v.fwd[l] = t->vpa.fwd[l];
+      v.tcf[l] = t->vpa.tcf[l];
+      v.tcf_lo[l] = t->vpa.tcf_lo[l];
+      v.dgr[l] = nullptr;
+      v.tcd[l] = v.tcd_lo[l] = nullptr;
+    }
+    t->vpa = v;
+    cudaError_t e = cudaStreamCreateWithFlags(&t->vst, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t->ev_vfork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t->ev_vjoin, cudaEventDisableTiming);
+    if (e != cudaSuccess) return set_cuda_error(e, "validation stream");
+  }
   return N2F_OK;
 }
 
@@ -316,6 +366,11 @@ void trainer_release(Trainer* t) {
     }
   }
   t->tnodes.clear();
+  if (t->vst) cudaStreamSynchronize(t->vst), cudaStreamDestroy(t->vst);
+  if (t->ev_vfork) cudaEventDestroy(t->ev_vfork);
+  if (t->ev_vjoin) cudaEventDestroy(t->ev_vjoin);
+  t->vst = nullptr;
+  t->ev_vfork = t->ev_vjoin = nullptr;
   if (t->slab) dev_free(t->al, t->slab, t->slab_bytes);
   t->slab = nullptr;
 }
@@ -387,15 +442,36 @@ int trainer_repack(Trainer* t) {
   return N2F_OK;
 }
 
-// Magnitude words of the float32 form (all null in the bf16 form): the forward of layer l reads
-// act[l - 1] and the weights, raises act[l]; the dgrad of layer l reads delta[l] and the
-// weights, raises delta[l - 1].
-static ConvScales fwd_scales(const Trainer* t, int l) {
-  ConvScales s;
+// Magnitude words of the float32 form (all null in the bf16 form). One forward pass uses one
+// set: the training step's act[] with w[], or the validation's vact[] with w[] (in line) or
+// vw[] (reading the weight snapshot). The forward of layer l reads act[l - 1] and the weights,
+// raises act[l]; the dgrad of layer l reads delta[l] and the weights, raises delta[l - 1].
+struct FwdWords {
+  unsigned* act = nullptr;
+  const unsigned* w = nullptr;
+};
+static FwdWords train_words(const Trainer* t) {
+  FwdWords f;
   if (t->sw) {
-    s.in = &t->sw->act[l - 1];
-    s.w = &t->sw->w[l];
-    s.out = &t->sw->act[l];
+    f.act = t->sw->act;
+    f.w = t->sw->w;
+  }
+  return f;
+}
+static FwdWords val_words(const Trainer* t, bool snap) {
+  FwdWords f;
+  if (t->sw) {
+    f.act = t->sw->vact;
+    f.w = snap ? t->sw->vw : t->sw->w;
+  }
+  return f;
+}
+static ConvScales fwd_scales(FwdWords f, int l) {
+  ConvScales s;
+  if (f.act) {
+    s.in = &f.act[l - 1];
+    s.w = &f.w[l];
+    s.out = &f.act[l];
   }
   return s;
 }
@@ -409,23 +485,24 @@ static ConvScales dgrad_scales(const Trainer* t, int l) {
   return s;
 }
 
+// Forward of layer l with the weights of `wp` (the live ones, or the validation's snapshot).
 static int conv_layer(Trainer* t, int l, const void* in, void* out, int H, int W,
-                      const int* skip, int val) {
+                      const int* skip, int val, const PackArgs& wp, FwdWords fw) {
   const int cin = t->net.cin(l), cout = t->net.widths[l];
-  const float* b = t->theta + t->net.b_off[l];
+  const float* b = wp.theta + t->net.b_off[l];
   const double P = (double)H * W, es = t->bf16 ? 2.0 : 4.0;
   Timed tm(t, l == 0 ? N2F_K_FIRST : N2F_K_CONV_FWD, 2.0 * P * 9 * cin * cout,
            l == 0 ? P * 4.0 + P * cout * es : P * (cin + cout) * es, val);
   if (l == 0) {
-    CK(launch_conv1_fwd((const float*)in, cin, H, W, t->pa.fwd[0], b, cout, t->bf16, out,
-                        t->sw ? &t->sw->act[0] : nullptr, skip, t->st));
+    CK(launch_conv1_fwd((const float*)in, cin, H, W, wp.fwd[0], b, cout, t->bf16, out,
+                        fw.act ? &fw.act[0] : nullptr, skip, t->st));
   } else if (t->engine[l] == N2F_ENGINE_TC) {
-    CK(launch_conv_tc(0, t->bf16, in, cin, cout, H, W, t->pa.tcf[l], t->pa.tcf_lo[l], b, nullptr,
-                      out, fwd_scales(t, l), skip, &t->state->kerr, t->st));
+    CK(launch_conv_tc(0, t->bf16, in, cin, cout, H, W, wp.tcf[l], wp.tcf_lo[l], b, nullptr, out,
+                      fwd_scales(fw, l), skip, &t->state->kerr, t->st));
   } else {
-    CK(launch_conv_simt(0, t->bf16, in, cin, cout, H, W, t->pa.fwd[l], b, nullptr, out, skip,
+    CK(launch_conv_simt(0, t->bf16, in, cin, cout, H, W, wp.fwd[l], b, nullptr, out, skip,
                         t->st));
-    if (t->sw) CK(launch_absmax(out, (size_t)cout * H * W, 0, &t->sw->act[l], skip, t->st));
+    if (fw.act) CK(launch_absmax(out, (size_t)cout * H * W, 0, &fw.act[l], skip, t->st));
   }
   return N2F_OK;
 }
@@ -442,7 +519,8 @@ static void* delta_of(const Trainer* t, int m) {
 
 static int step_forward(Trainer* t, int pair, int l) {
   const void* in = l == 0 ? (const void*)t->sub[pair] : t->act[l - 1];
-  return conv_layer(t, l, in, t->act[l], t->ph[pair], t->pw[pair], step_skip(t), 0);
+  return conv_layer(t, l, in, t->act[l], t->ph[pair], t->pw[pair], step_skip(t), 0, t->pa,
+                    train_words(t));
 }
 
 static int step_head(Trainer* t, int pair) {
@@ -542,21 +620,29 @@ int trainer_step(Trainer* t, int pair) {
   return N2F_OK;
 }
 
-// validation forward of layer l: x -> vb[0] -> vb[1] -> ...
-static int val_forward(Trainer* t, int l) {
+// validation forward of layer l: x -> vb[0] -> vb[1] -> ...; snap: with the weight snapshot
+static int val_forward(Trainer* t, int l, bool snap) {
   const void* in = l == 0 ? (const void*)t->x : t->vb[(l - 1) & 1];
-  return conv_layer(t, l, in, t->vb[l & 1], t->H, t->W, step_skip(t), 1);
+  return conv_layer(t, l, in, t->vb[l & 1], t->H, t->W, step_skip(t), 1, snap ? t->vpa : t->pa,
+                    val_words(t, snap));
 }
 
-static int val_finish(Trainer* t) {
+// the validation's magnitude words start afresh
+static int val_begin(Trainer* t) {
+  if (t->sw) CK(cudaMemsetAsync(t->sw->vact, 0, sizeof(t->sw->vact), t->st));
+  return N2F_OK;
+}
+
+static int val_finish(Trainer* t, bool snap) {
   const NetShape& net = t->net;
+  const float* th = snap ? t->vpa.theta : t->theta;
   const int* skip = step_skip(t);
   int nblk = 0;
   {
     const double es = t->bf16 ? 2.0 : 4.0, C8 = net.widths[kLayers - 1];
     Timed tm(t, N2F_K_HEAD, 2.0 * t->N * C8, (double)t->N * (C8 * es + 8.0), 1);
     CK(launch_head_val(t->vb[(kLayers - 1) & 1], net.widths[kLayers - 1], (int)t->N,
-                       t->theta + net.w_off[kLayers], t->theta + net.b_off[kLayers],
+                       th + net.w_off[kLayers], th + net.b_off[kLayers],
                        t->x + (size_t)t->prm.target_channel * t->N, t->bf16, t->V, t->mpart,
                        &nblk, skip, t->st));
   }
@@ -566,13 +652,16 @@ static int val_finish(Trainer* t) {
   return N2F_OK;
 }
 
-int trainer_validate(Trainer* t) {
+static int validate(Trainer* t, bool snap) {
   LaunchScope ls(&t->launches);
   int rc;
+  if ((rc = val_begin(t))) return rc;
   for (int l = 0; l < kLayers; ++l)
-    if ((rc = val_forward(t, l))) return rc;
-  return val_finish(t);
+    if ((rc = val_forward(t, l, snap))) return rc;
+  return val_finish(t, snap);
 }
+
+int trainer_validate(Trainer* t) { return validate(t, false); }
 
 // ---- lockstep group -----------------------------------------------------------------------
 
@@ -623,7 +712,7 @@ int group_init(TrainerGroup* g, const Allocator& al, cudaStream_t st) {
             q.w_lo = t->pa.tcf_lo[l];
             q.bias = t->theta + t->net.b_off[l];
             q.mask = nullptr;
-            q.sc = fwd_scales(t, l);
+            q.sc = fwd_scales(k == 2 ? val_words(t, false) : train_words(t), l);
           } else {
             q.in = delta_of(t, l);
             q.out = delta_of(t, l - 1);
@@ -741,19 +830,21 @@ int group_step(TrainerGroup* g, int pair) {
 int group_validate(TrainerGroup* g) {
   LaunchScope ls(&g->launches);
   int rc;
+  for (Trainer* t : g->ts)
+    if (t->sw) CK(cudaMemsetAsync(t->sw->vact, 0, sizeof(t->sw->vact), g->st));
   for (int l = 0; l < kLayers; ++l) {
     if (g->grouped[l]) {
       if ((rc = group_conv(g, l, 2, 0))) return rc;
     } else {
       if ((rc = fork(g))) return rc;
       for (Trainer* t : g->ts)
-        if ((rc = val_forward(t, l))) return rc;
+        if ((rc = val_forward(t, l, false))) return rc;
       if ((rc = join(g))) return rc;
     }
   }
   if ((rc = fork(g))) return rc;
   for (Trainer* t : g->ts)
-    if ((rc = val_finish(t))) return rc;
+    if ((rc = val_finish(t, false))) return rc;
   return join(g);
 }
 
@@ -817,7 +908,8 @@ int trainer_autotune(Trainer* t) {
       const void* in = k == 2 ? t->vb[(l - 1) & 1] : t->act[l - 1];
       void* out = k == 2 ? t->vb[l & 1] : t->act[l];
       CK(conv_tc_autotune(0, t->bf16, in, cin, cout, h, w, t->pa.tcf[l], t->pa.tcf_lo[l], b,
-                          nullptr, out, fwd_scales(t, l), &t->state->kerr, t->st));
+                          nullptr, out, fwd_scales(k == 2 ? val_words(t, false) : train_words(t), l),
+                          &t->state->kerr, t->st));
       if (k == 2) continue;
       CK(conv_tc_autotune(1, t->bf16, delta_of(t, l), cout, cin, h, w, t->pa.tcd[l],
                           t->pa.tcd_lo[l], nullptr, t->act[l - 1], delta_of(t, l - 1),
@@ -833,6 +925,48 @@ int trainer_epoch(Trainer* t) {
     if (rc) return rc;
   }
   return trainer_validate(t);
+}
+
+// Overlapped epoch: the previous epoch's validation runs on vst, reading a snapshot of the
+// weights that epoch left, beside this epoch's four steps on st; the streams join before the
+// epoch ends. The validation's buffers, magnitude words and weight copies are its own, so the
+// two share only the job state, in which they write different fields (the steps: t, the bias
+// corrections and the loss; the validation: the stop-rule fields). If the validation stops the
+// job the steps beside it are discarded (k_step_restore) and the job's final state equals the
+// in-line schedule's.
+static int epoch_overlapped(Trainer* t) {
+  int rc;
+  const bool val = t->val_pending;
+  if (val) {
+    LaunchScope ls(&t->launches);
+    CK(cudaMemcpyAsync(t->vsnap, t->slab + t->snap_off, t->snap_bytes, cudaMemcpyDeviceToDevice,
+                       t->st));
+    if (t->sw)
+      CK(cudaMemcpyAsync(t->sw->vw, t->sw->w, sizeof(t->sw->w), cudaMemcpyDeviceToDevice, t->st));
+    CK(cudaMemcpyAsync(t->state_save, t->state, sizeof(DevState), cudaMemcpyDeviceToDevice,
+                       t->st));
+    CK(cudaEventRecord(t->ev_vfork, t->st));
+    CK(cudaStreamWaitEvent(t->vst, t->ev_vfork, 0));
+    cudaStream_t main = t->st;
+    t->st = t->vst;  // every launch of the validation goes to vst
+    rc = validate(t, true);
+    t->st = main;
+    if (rc) return rc;
+    CK(cudaEventRecord(t->ev_vjoin, t->vst));
+  }
+  for (int k = 0; k < 4; ++k)
+    if ((rc = trainer_step(t, k))) return rc;
+  t->val_pending = true;
+  if (val) {
+    LaunchScope ls(&t->launches);
+    CK(cudaStreamWaitEvent(t->st, t->ev_vjoin, 0));
+    CK(launch_step_restore(t->state, t->state_save, t->st));
+  }
+  return N2F_OK;
+}
+
+int trainer_epoch_job(Trainer* t) {
+  return overlapped(t) ? epoch_overlapped(t) : trainer_epoch(t);
 }
 
 namespace {
@@ -863,6 +997,8 @@ int bind_timed_nodes(Trainer* t, cudaGraph_t g) {
 }  // namespace
 
 int trainer_epoch_graph(Trainer* t) {
+  // an overlapped job's first epoch has no validation beside it: it runs as it is
+  if (overlapped(t) && !t->val_pending) return epoch_overlapped(t);
   if (!t->epoch_exec) {
     uint64_t counted = 0;
     cudaGraph_t g = nullptr;
@@ -877,7 +1013,7 @@ int trainer_epoch_graph(Trainer* t) {
         t->capturing = false;
         return set_cuda_error(e, "epoch graph capture");
       }
-      const int rc = trainer_epoch(t);
+      const int rc = trainer_epoch_job(t);
       e = cudaStreamEndCapture(t->st, &g);
       t->capturing = false;
       if (rc) {

@@ -109,6 +109,18 @@ struct Trainer {
   bool capturing = false;
   uint64_t cap_steps0 = 0, cap_vals0 = 0;
   std::vector<TimedNode> tnodes;
+  // Overlapped validation (prm.overlap): the validation buffers do not alias the training
+  // ones; at each epoch boundary theta and the forward weight copies (one contiguous range of
+  // the slab, snap_off / snap_bytes) are copied to vsnap, and the previous epoch's validation
+  // runs on vst from that copy (vpa) while the epoch trains on st. DevState's step counters
+  // are saved in state_save at the boundary and put back if that validation stopped the job.
+  cudaStream_t vst = nullptr;
+  cudaEvent_t ev_vfork = nullptr, ev_vjoin = nullptr;
+  char* vsnap = nullptr;
+  size_t snap_off = 0, snap_bytes = 0;
+  PackArgs vpa;
+  DevState* state_save = nullptr;
+  bool val_pending = false;  // an epoch has trained whose validation has not been enqueued
 };
 
 int trainer_configure(Trainer* t, int H, int W, const n2f_params* p, int keep_deltas);
@@ -122,7 +134,10 @@ int trainer_validate(Trainer* t);
 int trainer_epoch(Trainer* t);
 // Tunes the job's conv launch choices (see conv_tc_autotune) before its first epoch.
 int trainer_autotune(Trainer* t);
-// Same as trainer_epoch, replaying a CUDA graph of the epoch captured on first use.
+// A job's epoch: trainer_epoch, or with prm.overlap the previous epoch's validation on a
+// second stream beside this epoch's four steps (the first epoch trains only).
+int trainer_epoch_job(Trainer* t);
+// Same as trainer_epoch_job, replaying a CUDA graph of the epoch captured on first use.
 int trainer_epoch_graph(Trainer* t);
 int trainer_finish(Trainer* t);
 

@@ -51,7 +51,8 @@ class Params(C.Structure):
                 ("max_epochs", C.c_uint32), ("fixed_steps", C.c_int32), ("seed", C.c_uint64),
                 ("precision", C.c_int32), ("loss", C.c_int32), ("widths", C.c_int32),
                 ("incl_best", C.c_int32), ("engine", C.c_int32), ("channels", C.c_int32),
-                ("target_channel", C.c_int32), ("downsample", C.c_int32), ("exact", C.c_int32)]
+                ("target_channel", C.c_int32), ("downsample", C.c_int32), ("exact", C.c_int32),
+                ("overlap", C.c_int32)]
 
 
 class Status(C.Structure):

@@ -152,3 +152,25 @@ def test_normal_build_has_no_checks(n2f):
     n, site = C.c_uint64(7), C.c_int(7)
     assert n2f.lib().n2f_check_status(C.byref(n), C.byref(site), 0) == n2f.N2F_ENOTSUP
     assert n2f.lib().n2f_check_status(None, C.byref(site), 0) == n2f.N2F_EINVAL
+
+
+def test_overlap_holds_its_own_validation_buffers(n2f):
+    """n2f_job_bytes (what admission counts) includes what overlapped validation adds: the
+    validation ping-pong pair (2 x 256 channels x H x W), no longer aliasing the training
+    activations, and the weight snapshot (theta and the forward weight copies); fixed-step jobs
+    never overlap and hold nothing more."""
+    H, W = 64, 96
+    count = n2f.param_count()
+    for precision, es in ((n2f.N2F_FP32, 4), (n2f.N2F_BF16, 2)):
+        a = n2f.job_bytes(H, W, n2f.params(precision=precision))
+        b = n2f.job_bytes(H, W, n2f.params(precision=precision, overlap=1))
+        vb = 2 * 256 * H * W * es
+        # snapshot: theta (4 B) + SIMT forward copies (4 B per weight, the biases and head
+        # excluded) + the tensor-core copies where the driver's tensor-map encoder is present
+        # (2 B per weight, float32 form also the 2-byte lo parts), alignment, a saved job state
+        assert vb + 7 * count <= b - a <= vb + 12 * count + 64 * 256, (precision, b - a)
+        fa = n2f.job_bytes(H, W, n2f.params(precision=precision, fixed_steps=5))
+        fb = n2f.job_bytes(H, W, n2f.params(precision=precision, fixed_steps=5, overlap=1))
+        assert fa == fb
+    with pytest.raises(n2f.N2FError):
+        n2f.job_bytes(H, W, n2f.params(overlap=2))
