@@ -132,6 +132,8 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc_bf16(const __grid_constant_
   const uint32_t b_off = align_up(kWbA, 1024);
   const bool bias = grp == 0;
   const uint32_t ncols = tmem_cols(nt * cn + (bias ? 16 : 0));
+  // delta's 8-channel groups that hold output channels (the rest of the M = 128 rows is zero)
+  const int dgroups = min(16, (p.cout - o0 + 7) / 8);
   volatile int* abort = &abort_flag;
   if (threadIdx.x == 0) {
     for (int s = 0; s < ns; ++s) {
@@ -292,19 +294,22 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc_bf16(const __grid_constant_
 // two fp16 images of each, one MMA warp issues three MMAs per tap and K step.
 constexpr int kW3KP = 16;  // pixels per stage (one 16-element K step)
 constexpr int kW3MaxStages = 12;
-// split warps (then epilogue warps): 16 for the one-row layers, whose CTA holds its SM alone
-// (TMEM), 8 for the tap-expanded small layers, which run two CTAs per SM
-template <int EXP>
+// split warps (then epilogue warps): 16 where the CTA holds its SM alone (TMEM: the one-row
+// layers and the nine-tap C_in = 32 layers), as two teams of eight that split alternate
+// chunks, so two chunks are split at once (a chunk gives each thread one to three groups: its
+// latency, not its instructions, bounds it); 8, one team, for the three-tap C_in = 64 layers,
+// which run two CTAs per SM
+template <int R, int EXP>
 struct W3Warps {
-  static constexpr int kSplit = EXP ? 8 : 16;
-  // one-row layers: two teams of eight warps split alternate chunks, so two chunks are split at
-  // once (a chunk gives each thread about one group: its latency, not its instructions, bounds it)
-  static constexpr int kTeams = EXP ? 1 : 2;
+  static constexpr bool kPair = EXP && R == 1;  // two CTAs per SM
+  static constexpr int kSplit = kPair ? 8 : 16;
+  static constexpr int kTeams = kPair ? 1 : 2;
   static constexpr int kTeamWarps = kSplit / kTeams;
   static constexpr int kThreads = 64 + 32 * kSplit;
-  static constexpr int kPerSm = EXP ? 2 : 1;
+  static constexpr int kPerSm = kPair ? 2 : 1;
 };
-static_assert(kW3MaxStages % W3Warps<0>::kTeams == 0 && 2 % W3Warps<0>::kTeams == 0,
+static_assert(kW3MaxStages % W3Warps<1, 0>::kTeams == 0 && 2 % W3Warps<1, 0>::kTeams == 0 &&
+                  kW3MaxStages % W3Warps<3, 1>::kTeams == 0 && 2 % W3Warps<3, 1>::kTeams == 0,
               "float32 stage counts must stay multiples of the split team count");
 
 // One-row layers (not tap-expanded) split in place: the fp16 hi and lo images of each pair of
@@ -369,63 +374,106 @@ __device__ __forceinline__ void split2_group(const float4 c03, const float4 c47,
   p1[u] = l;
 }
 
-// Splits one stage. Delta tile: raw [32 g4][16 px], parts [16 g8][16 px]. x tile: raw
-// [C/4][R][16 + 2 pu px], parts [C/8][R][18 px] (raw column pu - 1 + i -> part column i). The
-// parts' 8-channel groups lie L.a_sbo / L.b_sbo bytes apart: in the in-place layout (pu = 1,
-// one-row layers) group g8's hi and lo images take raw slots 2 g8 and 2 g8 + 1, the very slots
-// the thread read them from. Each quarter-warp takes 8 consecutive pixels of one row, so its
-// eight 16-byte reads fall in distinct bank groups; the 2 halo pixels of each row follow in a
-// short second pass.
+// The split of one stage, planned once per thread. Delta tile: raw [32 g4][16 px], parts
+// [16 g8][16 px]; only the 8-channel groups below C_out are split (the others stay zero). x
+// tile: raw [C/4][R][16 + 2 pu px], parts [C/8][R][18 px] (raw column pu - 1 + i -> part column
+// i), or tap-expanded [taps x C/8][16 px]. The parts' 8-channel groups lie L.a_sbo / L.b_sbo
+// bytes apart: in the in-place layout (pu = 1, one-row layers) group g8's hi and lo images take
+// raw slots 2 g8 and 2 g8 + 1, the very slots the thread read them from. The layout and the
+// chunk's taps are the same for every chunk, so each thread's groups -- the raw float4 index
+// of their channels 0-3 (channels 4-7 lie a fixed stride on) and the part index -- are worked
+// out once; a chunk's split is then loads, conversions and stores only. Consecutive threads
+// take consecutive pixels of one row, so a quarter-warp's eight 16-byte reads fall in distinct
+// bank groups.
 template <int R, int EXP>
-__device__ __forceinline__ void split2_stage(const uint8_t* st, uint8_t* stw, const W3Layout& L,
-                                             int g8n, int pu, int et, int nt, int t0, int r0,
-                                             float sd, float sx) {
-  constexpr int kThr = 32 * W3Warps<EXP>::kTeamWarps;
-  constexpr int PP = kW3KP + 2;  // part pitch
-  const int PR = w3_raw_pitch(pu);
-  {
-    const float4* raw = reinterpret_cast<const float4*>(st + L.rawA);
+struct SplitPlan {
+  static constexpr int kThr = 32 * W3Warps<R, EXP>::kTeamWarps;
+  static constexpr int kMaxA = (16 * kW3KP + kThr - 1) / kThr;
+  // x groups: tap-expanded at most 9 taps x 4 or 3 taps x 8 groups of 16 pixels; one-row at
+  // most 16 groups x (16 + 2 halo) pixels
+  static constexpr int kMaxB =
+      EXP ? (36 * kW3KP + kThr - 1) / kThr : (16 * (kW3KP + 2) + kThr - 1) / kThr;
+  int na = 0, nb = 0;
+  int as[kMaxA], ad[kMaxA];
+  int bs[kMaxB], bd[kMaxB];
+  int bstep;  // float4 units from a group's channels 0-3 to its channels 4-7 in the raw x tile
+
+  __device__ __forceinline__ SplitPlan(const W3Layout& L, int dgroups, int g8n, int pu, int et,
+                                       int nt, int t0, int r0) {
+    constexpr int PP = kW3KP + 2;  // part pitch
+    const int PR = w3_raw_pitch(pu);
+    bstep = R * PR;
     const int ga = (int)(L.a_sbo / 16);  // 16-byte units between the parts' groups
-    for (int u = et; u < 16 * kW3KP; u += kThr) {
-      const int g8 = u / kW3KP, px = u % kW3KP;
-      split2_group(raw[(2 * g8) * kW3KP + px], raw[(2 * g8 + 1) * kW3KP + px], sd,
-                   reinterpret_cast<uint4*>(stw + L.a[0]), reinterpret_cast<uint4*>(stw + L.a[1]),
-                   g8 * ga + px);
+#pragma unroll
+    for (int k = 0; k < kMaxA; ++k) {
+      const int u = et + k * kThr;
+      if (u < dgroups * kW3KP) {
+        const int g8 = u / kW3KP, px = u % kW3KP;
+        as[k] = (2 * g8) * kW3KP + px;
+        ad[k] = g8 * ga + px;
+        na = k + 1;  // u grows with k: the valid entries are a prefix
+      }
+    }
+    if constexpr (EXP) {
+      // group gq = j * g8n + g8 holds tap j's view of channel group g8: pixel px of the chunk
+      // at raw row (tap / 3 - r0), raw column pu - 1 + px + tap % 3
+      const int n = nt * g8n * kW3KP;
+#pragma unroll
+      for (int k = 0; k < kMaxB; ++k) {
+        const int u = et + k * kThr;
+        if (u < n) {
+          const int gq = u / kW3KP, px = u % kW3KP;
+          const int j = gq / g8n, g8 = gq - j * g8n, tap = t0 + j;
+          const int r = tap / 3 - r0, col = pu - 1 + px + tap % 3;
+          bs[k] = ((2 * g8) * R + r) * PR + col;
+          bd[k] = u;
+          nb = k + 1;
+        }
+      }
+    } else {
+      const int gb = (int)(L.b_sbo / 16);
+      const int nmain = g8n * R * kW3KP, n = nmain + g8n * R * 2;
+#pragma unroll
+      for (int k = 0; k < kMaxB; ++k) {
+        const int u = et + k * kThr;
+        if (u < n) {
+          int q, i;
+          if (u < nmain) {
+            q = u / kW3KP;
+            i = 1 + u % kW3KP;
+          } else {  // the 2 halo pixels of each row
+            q = (u - nmain) >> 1;
+            i = ((u - nmain) & 1) ? PP - 1 : 0;
+          }
+          const int g8 = q / R, r = q - g8 * R, px = pu - 1 + i;
+          bs[k] = ((2 * g8) * R + r) * PR + px;
+          bd[k] = g8 * gb + r * PP + i;
+          nb = k + 1;
+        }
+      }
     }
   }
-  const float4* raw = reinterpret_cast<const float4*>(st + L.rawB);
-  uint4* b0 = reinterpret_cast<uint4*>(stw + L.b[0]);
-  uint4* b1 = reinterpret_cast<uint4*>(stw + L.b[1]);
-  if constexpr (EXP) {
-    // group gq = j * g8n + g8 holds tap j's view of channel group g8: pixel px of the chunk at
-    // raw row (tap / 3 - r0), raw column pu - 1 + px + tap % 3
-    for (int u = et; u < nt * g8n * kW3KP; u += kThr) {
-      const int gq = u / kW3KP, px = u % kW3KP;
-      const int j = gq / g8n, g8 = gq - j * g8n, tap = t0 + j;
-      const int r = tap / 3 - r0, col = pu - 1 + px + tap % 3;
-      split2_group(raw[((2 * g8) * R + r) * PR + col], raw[((2 * g8 + 1) * R + r) * PR + col], sx,
-                   b0, b1, u);
-    }
-    return;
-  }
-  const int gb = (int)(L.b_sbo / 16);  // 16-byte units between the parts' groups
-  const int nmain = g8n * R * kW3KP;
-  for (int u = et; u < nmain; u += kThr) {
-    const int q = u / kW3KP, i = 1 + u % kW3KP;  // q = g8 * R + r, part column i
-    const int g8 = q / R, r = q - g8 * R, px = pu - 1 + i;
-    split2_group(raw[((2 * g8) * R + r) * PR + px], raw[((2 * g8 + 1) * R + r) * PR + px], sx, b0,
-                 b1, g8 * gb + r * PP + i);
-  }
-  for (int u = et; u < g8n * R * 2; u += kThr) {
-    const int q = u >> 1, i = (u & 1) ? PP - 1 : 0;
-    const int g8 = q / R, r = q - g8 * R, px = pu - 1 + i;
-    split2_group(raw[((2 * g8) * R + r) * PR + px], raw[((2 * g8 + 1) * R + r) * PR + px], sx, b0,
-                 b1, g8 * gb + r * PP + i);
-  }
+};
+
+template <int R, int EXP>
+__device__ __forceinline__ void split2_stage(uint8_t* st, const W3Layout& L,
+                                             const SplitPlan<R, EXP>& pl, float sd, float sx) {
+  const float4* rawA = reinterpret_cast<const float4*>(st + L.rawA);
+  uint4* a0 = reinterpret_cast<uint4*>(st + L.a[0]);
+  uint4* a1 = reinterpret_cast<uint4*>(st + L.a[1]);
+#pragma unroll
+  for (int k = 0; k < SplitPlan<R, EXP>::kMaxA; ++k)
+    if (k < pl.na) split2_group(rawA[pl.as[k]], rawA[pl.as[k] + kW3KP], sd, a0, a1, pl.ad[k]);
+  const float4* rawB = reinterpret_cast<const float4*>(st + L.rawB);
+  uint4* b0 = reinterpret_cast<uint4*>(st + L.b[0]);
+  uint4* b1 = reinterpret_cast<uint4*>(st + L.b[1]);
+#pragma unroll
+  for (int k = 0; k < SplitPlan<R, EXP>::kMaxB; ++k)
+    if (k < pl.nb) split2_group(rawB[pl.bs[k]], rawB[pl.bs[k] + pl.bstep], sx, b0, b1, pl.bd[k]);
 }
 
 template <int R, int EXP>
-__global__ void __launch_bounds__(W3Warps<EXP>::kThreads, W3Warps<EXP>::kPerSm) k_wgrad_tc_f32(const __grid_constant__ CUtensorMap tmD,
+__global__ void __launch_bounds__(W3Warps<R, EXP>::kThreads, W3Warps<R, EXP>::kPerSm) k_wgrad_tc_f32(const __grid_constant__ CUtensorMap tmD,
                                                                const __grid_constant__ CUtensorMap tmX,
                                                                WgBf16Params p) {
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -446,18 +494,29 @@ __global__ void __launch_bounds__(W3Warps<EXP>::kThreads, W3Warps<EXP>::kPerSm) 
   const uint32_t RB = (uint32_t)cn * R * w3_raw_pitch(1) * 4;
   const bool bias = grp == 0;
   const uint32_t ncols = tmem_cols(nt * cn + (bias ? 16 : 0));
+  // delta's 8-channel groups that hold output channels (the rest of the M = 128 rows is zero)
+  const int dgroups = min(16, (p.cout - o0 + 7) / 8);
   volatile int* abort = &abort_flag;
   if (threadIdx.x == 0) {
     for (int s = 0; s < ns; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
-      mbar_init(&split[s], W3Warps<EXP>::kTeamWarps);
+      mbar_init(&split[s], W3Warps<R, EXP>::kTeamWarps);
     }
     mbar_init(&accf, 1);
     abort_flag = 0;
     mbar_fence_init();
   }
   if (warp == 1) tmem_alloc(&tslot, ncols);
+  if (EXP && dgroups < 16) {
+    // separate delta part images: the groups never split are zeroed once (in place, the TMA
+    // box's zero fill beyond C_out leaves zero parts in those slots every chunk)
+    const uint32_t gbytes = kW3KP * 16, ga = L.a_sbo;
+    for (int s = 0; s < ns; ++s)
+      for (int q = 0; q < 2; ++q)
+        for (int g8 = dgroups; g8 < 16; ++g8)
+          fill_ext(smem + s * L.stage + L.a[q] + g8 * ga, gbytes, 0u);
+  }
   if (bias) {  // hi part: ones, lo part: zeros, so the bias columns sum a_hi + a_lo
     if (EXP) {
       const uint32_t eo = (uint32_t)nt * cn / 8 * kW3KP * 16, eb = 2u * kW3KP * 16;
@@ -470,8 +529,8 @@ __global__ void __launch_bounds__(W3Warps<EXP>::kThreads, W3Warps<EXP>::kPerSm) 
         for (int k = 0; k < 4; ++k)
           fill_ext(smem + s * L.stage + L.ext + k * slot, slot, (k & 1) ? 0u : kF16PairOne);
     }
-    fence_proxy_async();
   }
+  fence_proxy_async();  // the fills above are read by the MMAs (async proxy)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -550,16 +609,17 @@ __global__ void __launch_bounds__(W3Warps<EXP>::kThreads, W3Warps<EXP>::kPerSm) 
       mma_commit(&accf);
     }
   } else {
-    constexpr int kTT = 32 * W3Warps<EXP>::kTeamWarps;  // threads per team
+    constexpr int kTT = 32 * W3Warps<R, EXP>::kTeamWarps;  // threads per team
     const int team = (threadIdx.x - 64) / kTT, et = (threadIdx.x - 64) % kTT;
     const float sd = f16_scale(p.dmax), sx = f16_scale(p.xmax);
+    const SplitPlan<R, EXP> plan(L, dgroups, cn / 8, 1, et, nt, t0, r0);
     int s = 0;
     uint32_t ph = 0;
     for (int i = 0; i < nk; ++i) {
-      if (i % W3Warps<EXP>::kTeams == team) {  // this team's chunk
+      if (i % W3Warps<R, EXP>::kTeams == team) {  // this team's chunk
         if (!mbar_wait(&full[s], ph, abort, p.err)) break;
         uint8_t* st = smem + s * L.stage;
-        split2_stage<R, EXP>(st, st, L, cn / 8, 1, et, nt, t0, r0, sd, sx);
+        split2_stage<R, EXP>(st, L, plan, sd, sx);
         fence_proxy_async();
         __syncwarp();
         if (lane == 0) mbar_arrive(&split[s]);
@@ -570,7 +630,7 @@ __global__ void __launch_bounds__(W3Warps<EXP>::kThreads, W3Warps<EXP>::kPerSm) 
     tc_fence_after();
     // warps 2..: TMEM lane quarter warp % 4, column set (warp - 2) / 4 (16-column blocks are
     // dealt round the sets)
-    constexpr int kSets = W3Warps<EXP>::kSplit / 4;
+    constexpr int kSets = W3Warps<R, EXP>::kSplit / 4;
     const int wq = warp & 3, half = (warp - 2) >> 2;
     const int o = o0 + wq * 32 + lane;
     const bool live = o < p.cout && !*abort;
@@ -772,15 +832,22 @@ static cudaError_t launch_wgrad_grouped(int bf16, const void* dout, const void* 
   // tap-expanded x operand when a tap alone would give MMAs of small N: float32 form for
   // C_in <= 64, bf16 form for C_in = 32 (its expansion is a copy pass)
   const bool exp = bf16 ? tg.cn <= 32 : tg.cn <= 64;
+  // a float32 split thread's x groups must fit its plan (SplitPlan::kMaxB): at most 36
+  // tap-expanded 8-channel groups, or 16 groups of one row
+  if (!bf16 && (exp ? tg.count[0] * tg.cn / 8 > 36 : tg.cn / 8 * tg.R > 16))
+    return cudaErrorInvalidValue;
   const uint32_t sb = bf16 ? (exp ? wb_stage_exp(tg.cn, tg.R, pu, tg.count[0]) : wb_stage(tg.cn, tg.R, pu))
                            : w3_layout(tg.cn, tg.R, 1, exp, tg.count[0]).stage;
   const int max_stages = bf16 ? kWbMaxStages : kW3MaxStages;
   p.stages = (int)((227u * 1024u / (uint32_t)max_res - 2048u) / sb);
   if (p.stages > max_stages) p.stages = max_stages;
-  // float32 one-row layers: split teams take chunks i = team (mod teams); a team's next chunk
-  // reuses the stage of chunk (next - stages), which must be one of its own (already waited for)
-  // or its parity wait could see that older load's phase: stages a multiple of the team count
-  if (!bf16 && !exp) p.stages -= p.stages % W3Warps<0>::kTeams;
+  // float32 layers with two split teams: team k takes chunks i = k (mod teams); a team's next
+  // chunk reuses the stage of chunk (next - stages), which must be one of its own (already
+  // waited for) or its parity wait could see that older load's phase: stages a multiple of the
+  // team count
+  const int teams = bf16 ? 1 : tg.R == 3 ? W3Warps<3, 1>::kTeams
+                                         : exp ? W3Warps<1, 1>::kTeams : W3Warps<1, 0>::kTeams;
+  p.stages -= p.stages % teams;
   if (p.stages < 2) p.stages = 2;
   uint32_t smem = (uint32_t)p.stages * sb;
   // a CTA holding more than half of TMEM keeps the SM to itself
@@ -809,11 +876,11 @@ static cudaError_t launch_wgrad_grouped(int bf16, const void* dout, const void* 
   else if (bf16)
     k_wgrad_tc_bf16<0><<<grid, 192, smem, st>>>(md, mx, p);
   else if (tg.R == 3)
-    k_wgrad_tc_f32<3, 1><<<grid, W3Warps<1>::kThreads, smem, st>>>(md, mx, p);
+    k_wgrad_tc_f32<3, 1><<<grid, W3Warps<3, 1>::kThreads, smem, st>>>(md, mx, p);
   else if (exp)
-    k_wgrad_tc_f32<1, 1><<<grid, W3Warps<1>::kThreads, smem, st>>>(md, mx, p);
+    k_wgrad_tc_f32<1, 1><<<grid, W3Warps<1, 1>::kThreads, smem, st>>>(md, mx, p);
   else
-    k_wgrad_tc_f32<1, 0><<<grid, W3Warps<0>::kThreads, smem, st>>>(md, mx, p);
+    k_wgrad_tc_f32<1, 0><<<grid, W3Warps<1, 0>::kThreads, smem, st>>>(md, mx, p);
   count_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // weights, and (last blocks) the bias from the S per-split sums of tap group 0
