@@ -257,8 +257,10 @@ def run_ours(args, ws, rank, local):
                    overlap=args.overlap)
     work = [image_for(i, rank, size) for i in range(args.warmup + args.steps)]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
+    # the launches of every --profile-every-th epoch are timed for the roofline: timing every
+    # launch of a step puts two event records around each one and costs the step several percent
     ctx = n2f.Context(device=local, max_slots=1, profile_kernel=args.profile_kernel,
-                      autotune=bool(args.autotune))
+                      autotune=bool(args.autotune), profile_every=args.profile_every)
     for i in range(args.warmup):
         j = ctx.submit(work[i][1].astype(np.float32), p)
         ctx.wait(j)
@@ -325,6 +327,9 @@ def run_ours(args, ws, rank, local):
     workload = f"{size}x{size} cells fp{'32' if args.precision == 0 else 'bf16'} " \
                f"{WIDTH_NAMES[args.widths]} plain"
     rl = roofline(stats, args.profile_kernel, args.precision, args.engine != 1, workload)
+    if rl is not None:
+        rl["sample"] = (f"the class's launches in every {args.profile_every}th epoch of the timed "
+                        "images (epochs 0, k, 2k, ...), CUDA events on the launching stream")
     q = sorted(comp_ms)
     line = {
         "metric": METRIC, "value": n_img / tot_dev_s, "unit": UNIT, "n_gpus": ws,
@@ -737,6 +742,9 @@ def main():
                          "(n2f_params.overlap; results identical), 0 in line (the default: "
                          "the roofline's per-launch times are then the kernels' own); with 0 the "
                          "timed images are also run once with 1 and reported beside")
+    ap.add_argument("--profile-every", type=int, default=8,
+                    help="plain form: time the profiled class's launches in every k-th epoch "
+                         "(n2f_config.profile_every)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--form", default="plain",
                     choices=["plain", "batched", "serving", "zstack", "variants"])

@@ -111,6 +111,9 @@ typedef struct {
                                 results unchanged (pipeline stages, CTAs per SM) are timed for
                                 each of its conv shapes not seen before in this process and the
                                 fastest kept; 0: fixed choices (default). */
+  uint32_t profile_every;    /* with profile_kernel: the launches of every profile_every-th
+                                epoch of a job are timed (its epoch graph is captured twice,
+                                with and without the event records); 0 or 1: every epoch. */
 } n2f_config;
 
 enum n2f_downsample { N2F_DOWN_CHECKER = 0, N2F_DOWN_QUAD = 1 };

@@ -696,6 +696,7 @@ static int admit(n2f_ctx* c, Job* j) {
   CKR(cudaEventCreate(&j->ev_done));
   j->kt.kind = j->grp ? N2F_K_NONE : c->cfg.profile_kernel;
   if (j->kt.kind != N2F_K_NONE) j->tr.kt = &j->kt;
+  j->tr.profile_every = std::max<uint32_t>(1, c->cfg.profile_every);
   j->ring = (int)std::min<uint32_t>(8, std::max<uint32_t>(2, c->cfg.lookahead + 1));
   for (int k = 0; k < j->ring; ++k) CKR(cudaEventCreateWithFlags(&j->ev_ep[k], cudaEventDisableTiming));
   CKR(cudaMallocHost((void**)&j->hst, sizeof(DevState) * j->ring));

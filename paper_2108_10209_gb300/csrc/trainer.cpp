@@ -103,7 +103,7 @@ struct Timed {
   cudaStream_t st;
   KTimer::Pair p;
   Timed(Trainer* tr, int kind, double flops, double bytes, int val) : st(tr->st) {
-    if (!tr->kt) return;
+    if (!tr->kt || !tr->timing_on) return;
     const bool conv = tr->kt->kind == N2F_K_CONV && (kind == N2F_K_CONV_FWD || kind == N2F_K_CONV_DGRAD);
     if (tr->kt->kind != kind && !conv) return;
     t = tr;
@@ -359,6 +359,10 @@ void trainer_release(Trainer* t) {
   t->epoch_exec = nullptr;
   if (t->epoch_graph) cudaGraphDestroy(t->epoch_graph);
   t->epoch_graph = nullptr;
+  if (t->epoch_exec_plain) cudaGraphExecDestroy(t->epoch_exec_plain);
+  t->epoch_exec_plain = nullptr;
+  if (t->epoch_graph_plain) cudaGraphDestroy(t->epoch_graph_plain);
+  t->epoch_graph_plain = nullptr;
   for (Trainer::TimedNode& n : t->tnodes) {
     if (t->kt) {
       t->kt->pool.push_back(n.a);
@@ -965,8 +969,20 @@ static int epoch_overlapped(Trainer* t) {
   return N2F_OK;
 }
 
-int trainer_epoch_job(Trainer* t) {
+// Whether the launches of the next epoch are timed (kt set): every profile_every-th epoch.
+static bool timed_epoch(const Trainer* t) {
+  return t->profile_every <= 1 || (t->steps_enqueued / 4) % t->profile_every == 0;
+}
+
+static int epoch_job(Trainer* t) {
   return overlapped(t) ? epoch_overlapped(t) : trainer_epoch(t);
+}
+
+int trainer_epoch_job(Trainer* t) {
+  t->timing_on = !t->kt || timed_epoch(t);
+  const int rc = epoch_job(t);
+  t->timing_on = true;
+  return rc;
 }
 
 namespace {
@@ -996,62 +1012,80 @@ int bind_timed_nodes(Trainer* t, cudaGraph_t g) {
 
 }  // namespace
 
-int trainer_epoch_graph(Trainer* t) {
-  // an overlapped job's first epoch has no validation beside it: it runs as it is
-  if (overlapped(t) && !t->val_pending) return epoch_overlapped(t);
-  if (!t->epoch_exec) {
-    uint64_t counted = 0;
-    cudaGraph_t g = nullptr;
-    {
-      LaunchScope ls(&counted);
-      t->tnodes.clear();
-      t->cap_steps0 = t->steps_enqueued;
-      t->cap_vals0 = t->vals_enqueued;
-      t->capturing = true;
-      cudaError_t e = cudaStreamBeginCapture(t->st, cudaStreamCaptureModeThreadLocal);
-      if (e != cudaSuccess) {
-        t->capturing = false;
-        return set_cuda_error(e, "epoch graph capture");
-      }
-      const int rc = trainer_epoch_job(t);
-      e = cudaStreamEndCapture(t->st, &g);
+// Captures one epoch (with the timed launches' event records, or without any) and
+// instantiates it; the enqueue counters are left as they were.
+static int capture_epoch(Trainer* t, bool timed, cudaGraph_t* gout, cudaGraphExec_t* xout,
+                         uint64_t* kernels) {
+  uint64_t counted = 0;
+  cudaGraph_t g = nullptr;
+  {
+    LaunchScope ls(&counted);
+    if (timed) t->tnodes.clear();
+    t->cap_steps0 = t->steps_enqueued;
+    t->cap_vals0 = t->vals_enqueued;
+    t->capturing = true;
+    t->timing_on = timed;
+    cudaError_t e = cudaStreamBeginCapture(t->st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
       t->capturing = false;
-      if (rc) {
-        if (g) cudaGraphDestroy(g);
-        return rc;
-      }
-      if (e != cudaSuccess) return set_cuda_error(e, "epoch graph capture");
+      t->timing_on = true;
+      return set_cuda_error(e, "epoch graph capture");
     }
-    int rc = bind_timed_nodes(t, g);
+    const int rc = epoch_job(t);
+    e = cudaStreamEndCapture(t->st, &g);
+    t->capturing = false;
+    t->timing_on = true;
     if (rc) {
-      cudaGraphDestroy(g);
+      if (g) cudaGraphDestroy(g);
       return rc;
     }
-    const cudaError_t e = cudaGraphInstantiate(&t->epoch_exec, g, 0);
-    if (e != cudaSuccess) {
-      cudaGraphDestroy(g);
-      return set_cuda_error(e, "epoch graph instantiate");
+    if (e != cudaSuccess) return set_cuda_error(e, "epoch graph capture");
+  }
+  int rc = timed ? bind_timed_nodes(t, g) : N2F_OK;
+  if (rc) {
+    cudaGraphDestroy(g);
+    return rc;
+  }
+  const cudaError_t e = cudaGraphInstantiate(xout, g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return set_cuda_error(e, "epoch graph instantiate");
+  }
+  *gout = g;  // kept: the timed nodes are addressed through it
+  *kernels = counted;
+  // the captured calls advanced the enqueue counters once; the launch is the epoch
+  t->steps_enqueued -= 4;
+  t->vals_enqueued -= 1;
+  return N2F_OK;
+}
+
+int trainer_epoch_graph(Trainer* t) {
+  // an overlapped job's first epoch has no validation beside it: it runs as it is
+  if (overlapped(t) && !t->val_pending) return trainer_epoch_job(t);
+  // a profiled job replays the graph with event records on its timed epochs only
+  const bool timed = !t->kt || timed_epoch(t);
+  cudaGraph_t* g = timed ? &t->epoch_graph : &t->epoch_graph_plain;
+  cudaGraphExec_t* x = timed ? &t->epoch_exec : &t->epoch_exec_plain;
+  if (!*x) {
+    const int rc = capture_epoch(t, timed && t->kt, g, x, &t->epoch_kernels);
+    if (rc) return rc;
+  }
+  if (timed && t->kt) {
+    // every replay records into its own events, harvested when the job's steps are known
+    for (const Trainer::TimedNode& tn : t->tnodes) {
+      KTimer::Pair p;
+      p.a = t->kt->get();
+      p.b = t->kt->get();
+      p.flops = tn.flops;
+      p.bytes = tn.bytes;
+      p.val = tn.val;
+      p.seq = tn.val ? t->vals_enqueued + tn.k : t->steps_enqueued + tn.k;
+      CK(cudaGraphExecEventRecordNodeSetEvent(*x, tn.na, p.a));
+      CK(cudaGraphExecEventRecordNodeSetEvent(*x, tn.nb, p.b));
+      t->kt->pending.push_back(p);
     }
-    t->epoch_graph = g;  // kept: the timed nodes are addressed through it
-    t->epoch_kernels = counted;
-    // the captured calls advanced the enqueue counters once; the launch below is the epoch
-    t->steps_enqueued -= 4;
-    t->vals_enqueued -= 1;
   }
-  // every replay records into its own events, harvested when the job's steps are known
-  for (const Trainer::TimedNode& tn : t->tnodes) {
-    KTimer::Pair p;
-    p.a = t->kt->get();
-    p.b = t->kt->get();
-    p.flops = tn.flops;
-    p.bytes = tn.bytes;
-    p.val = tn.val;
-    p.seq = tn.val ? t->vals_enqueued + tn.k : t->steps_enqueued + tn.k;
-    CK(cudaGraphExecEventRecordNodeSetEvent(t->epoch_exec, tn.na, p.a));
-    CK(cudaGraphExecEventRecordNodeSetEvent(t->epoch_exec, tn.nb, p.b));
-    t->kt->pending.push_back(p);
-  }
-  CK(cudaGraphLaunch(t->epoch_exec, t->st));
+  CK(cudaGraphLaunch(*x, t->st));
   t->steps_enqueued += 4;
   t->vals_enqueued += 1;
   t->launches += t->epoch_kernels;

@@ -96,6 +96,12 @@ struct Trainer {
   // one epoch captured as a CUDA graph (everything it mutates lives in device memory)
   cudaGraph_t epoch_graph = nullptr;
   cudaGraphExec_t epoch_exec = nullptr;
+  // a profiled job (kt) with profile_every > 1 also replays an epoch captured without the
+  // timed launches' event records on its untimed epochs
+  cudaGraph_t epoch_graph_plain = nullptr;
+  cudaGraphExec_t epoch_exec_plain = nullptr;
+  uint32_t profile_every = 1;
+  bool timing_on = true;       // Timed brackets launches (cleared for untimed epochs)
   uint64_t epoch_kernels = 0;  // kernels in one captured epoch
   // Timed launches inside the captured epoch: their event-record nodes get fresh events before
   // every replay, so a profiled job still replays graphs. `k` is the step within the epoch

@@ -42,7 +42,8 @@ class Config(C.Structure):
     _fields_ = [("struct_size", C.c_uint32), ("device", C.c_int), ("hbm_budget_bytes", C.c_uint64),
                 ("max_slots", C.c_uint32), ("lookahead", C.c_uint32), ("alloc", ALLOC_FN),
                 ("free", FREE_FN), ("alloc_user", C.c_void_p), ("profile_kernel", C.c_int32),
-                ("use_graphs", C.c_int32), ("group_size", C.c_uint32), ("autotune", C.c_int32)]
+                ("use_graphs", C.c_int32), ("group_size", C.c_uint32), ("autotune", C.c_int32),
+                ("profile_every", C.c_uint32)]
 
 
 class Params(C.Structure):
@@ -224,7 +225,8 @@ class Context:
 
     def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, max_slots: int = 0,
                  lookahead: int = 0, torch_alloc: bool = True, profile_kernel: int = 0,
-                 use_graphs: bool = True, group_size: int = 0, autotune: bool = False):
+                 use_graphs: bool = True, group_size: int = 0, autotune: bool = False,
+                 profile_every: int = 0):
         cfg = Config()
         lib().n2f_config_default(C.byref(cfg))
         cfg.device = device
@@ -238,6 +240,7 @@ class Context:
         cfg.use_graphs = int(use_graphs)
         cfg.group_size = group_size
         cfg.autotune = int(autotune)
+        cfg.profile_every = profile_every
         self.device = device
         self._keep = []
         self._dev_inputs = {}  # job -> device image tensor, held until the job is collected

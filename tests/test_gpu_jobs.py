@@ -223,6 +223,31 @@ def test_profiled_graph_replay(n2f):
         assert got[(kind, False)] == got[(kind, True)]
 
 
+def test_profiling_every_nth_epoch(n2f):
+    # With profile_every = k only the launches of epochs 0, k, 2k, ... are timed (the epoch graph
+    # is also captured without its event records and replayed on the other epochs): results are
+    # unchanged, and the timed launch count is the per-epoch count times those epochs.
+    _, x = _img(48, 40, 34)
+    p = n2f.params(seed=4, patience=6)
+    ref = n2f.denoise(x, p)
+    got = {}
+    for every in (1, 3):
+        for graphs in (False, True):
+            with n2f.Context(profile_kernel=n2f.N2F_K_CONV, use_graphs=graphs,
+                             profile_every=every) as ctx:
+                j = ctx.submit(x, p)
+                ctx.wait(j)
+                ep = ctx.poll(j).epoch
+                out = ctx.result(j, x.shape)
+                st = ctx.stats()
+            assert np.array_equal(out, ref)
+            got[(every, graphs)] = (st["prof_launches"], ep)
+    full, epochs = got[(1, True)]
+    assert got[(1, False)] == (full, epochs) and full % epochs == 0 and epochs > 3
+    for graphs in (False, True):
+        assert got[(3, graphs)] == (full // epochs * ((epochs + 2) // 3), epochs)
+
+
 def test_autotuned_launches_give_identical_results(n2f):
     # The tuner only picks among launch choices that leave every result unchanged (pipeline
     # stages, CTAs per SM): tuned and untuned jobs agree bit for bit, in both forms.
