@@ -106,10 +106,20 @@ __host__ __device__ inline uint32_t wb_stage_exp(int cin, int R, int pu, int tap
   return wb_exp_off(cin, R, pu) + align_up(((uint32_t)taps * cin / 8 + 2) * kWbKP * 16, 1024);
 }
 
-// EXP = 1 (small C_in): warps 2-5 first copy each stage's x tile into the tap-expanded layout
-// (pure 16-byte copies), then serve as the epilogue.
+// Warps after the producer and the MMA warp: the epilogue, and for EXP = 1 (small C_in) first
+// the copy of each stage's x tile into the tap-expanded layout (pure 16-byte copies). The copy
+// of a 64-pixel chunk is 2304 groups for the nine taps of C_in = 32; four warps took ~3600
+// cycles a chunk for ~600 tensor cycles, so the tap-expanded kernel has sixteen.
 template <int EXP>
-__global__ void __launch_bounds__(192, 1) k_wgrad_tc_bf16(const __grid_constant__ CUtensorMap tmD,
+struct WbWarps {
+  static constexpr int kCopy = EXP ? 16 : 4;  // copy / epilogue warps
+  static constexpr int kThreads = 64 + 32 * kCopy;
+  // each copy thread's groups of one chunk (at most 36 8-channel groups x 64 pixels)
+  static constexpr int kMaxCopy = (36 * kWbKP + 32 * kCopy - 1) / (32 * kCopy);
+};
+
+template <int EXP>
+__global__ void __launch_bounds__(WbWarps<EXP>::kThreads, 1) k_wgrad_tc_bf16(const __grid_constant__ CUtensorMap tmD,
                                                          const __grid_constant__ CUtensorMap tmX,
                                                          WgBf16Params p) {
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -139,7 +149,7 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc_bf16(const __grid_constant_
     for (int s = 0; s < ns; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
-      mbar_init(&split[s], 4);
+      mbar_init(&split[s], WbWarps<EXP>::kCopy);
     }
     mbar_init(&accf, 1);
     abort_flag = 0;
@@ -234,18 +244,25 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc_bf16(const __grid_constant_
   } else {
     if constexpr (EXP) {
       // group gq = j * g8n + g8 holds tap j's view of channel group g8: pixel px of the chunk
-      // at raw row (tap / 3 - r0), raw column pu - 1 + px + tap % 3
-      const int g8n = cn / 8, et = threadIdx.x - 64;
+      // at raw row (tap / 3 - r0), raw column pu - 1 + px + tap % 3. A thread's groups are the
+      // same for every chunk: their raw offsets are worked out once.
+      constexpr int kThr = 32 * WbWarps<EXP>::kCopy, kMax = WbWarps<EXP>::kMaxCopy;
+      const int g8n = cn / 8, et = threadIdx.x - 64, n = nt * g8n * kWbKP;
+      int src[kMax];
+#pragma unroll
+      for (int k = 0; k < kMax; ++k) {
+        const int u = et + k * kThr, gq = u / kWbKP, px = u % kWbKP;
+        const int j = gq / g8n, g8 = gq - j * g8n, tap = t0 + j;
+        src[k] = (g8 * R + (tap / 3 - r0)) * HX + pu - 1 + px + tap % 3;
+      }
       for (int i = 0; i < nk; ++i) {
         const int s = i % ns;
         if (!mbar_wait(&full[s], (i / ns) & 1, abort, p.err)) break;
         const uint4* raw = reinterpret_cast<const uint4*>(smem + s * SB + b_off);
         uint4* ex = reinterpret_cast<uint4*>(smem + s * SB + e_off);
-        for (int u = et; u < nt * g8n * kWbKP; u += 128) {
-          const int gq = u / kWbKP, px = u % kWbKP;
-          const int j = gq / g8n, g8 = gq - j * g8n, tap = t0 + j;
-          ex[u] = raw[(g8 * R + (tap / 3 - r0)) * HX + pu - 1 + px + tap % 3];
-        }
+#pragma unroll
+        for (int k = 0; k < kMax; ++k)
+          if (et + k * kThr < n) ex[et + k * kThr] = raw[src[k]];
         fence_proxy_async();
         __syncwarp();
         if (lane == 0) mbar_arrive(&split[s]);
@@ -253,14 +270,17 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc_bf16(const __grid_constant_
     }
     if (!mbar_wait(&accf, 0, abort, p.err)) mbar_drain(&accf, 0);
     tc_fence_after();
-    const int wq = warp & 3;
+    // warps 2..: TMEM lane quarter warp % 4, column set (warp - 2) / 4 (16-column blocks dealt
+    // round the sets)
+    constexpr int kSets = WbWarps<EXP>::kCopy / 4;
+    const int wq = warp & 3, set = (warp - 2) >> 2;
     const int o = o0 + wq * 32 + lane;
     const bool live = o < p.cout && !*abort;
     for (int j = 0; j < nt; ++j) {
       const int tap = t0 + j;
       // part[s][tap][c][o]: the warp's 32 lanes are 32 consecutive o, one 128-byte row per c
       float* dst = p.part + ((size_t)s_idx * 9 + tap) * p.cin * p.cout + (size_t)c0g * p.cout + o;
-      for (int c0 = 0; c0 < cn; c0 += 16) {
+      for (int c0 = 16 * set; c0 < cn; c0 += 16 * kSets) {
         uint32_t r[16];
         tmem_ld16(tbase + ((uint32_t)(wq * 32) << 16) + (uint32_t)(j * cn + c0), r);
         tmem_ld_wait();
@@ -271,7 +291,7 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc_bf16(const __grid_constant_
             dst[(size_t)(c0 + q) * p.cout] = nk ? __uint_as_float(r[q]) : 0.f;
       }
     }
-    if (bias) {
+    if (bias && set == 0) {
       uint32_t r[16];
       tmem_ld16(tbase + ((uint32_t)(wq * 32) << 16) + (uint32_t)(nt * cn), r);
       tmem_ld_wait();
@@ -872,9 +892,9 @@ static cudaError_t launch_wgrad_grouped(int bf16, const void* dout, const void* 
   p.err = err;
   const dim3 grid((unsigned)otiles, (unsigned)tg.n, (unsigned)S);
   if (bf16 && exp)
-    k_wgrad_tc_bf16<1><<<grid, 192, smem, st>>>(md, mx, p);
+    k_wgrad_tc_bf16<1><<<grid, WbWarps<1>::kThreads, smem, st>>>(md, mx, p);
   else if (bf16)
-    k_wgrad_tc_bf16<0><<<grid, 192, smem, st>>>(md, mx, p);
+    k_wgrad_tc_bf16<0><<<grid, WbWarps<0>::kThreads, smem, st>>>(md, mx, p);
   else if (tg.R == 3)
     k_wgrad_tc_f32<3, 1><<<grid, W3Warps<3, 1>::kThreads, smem, st>>>(md, mx, p);
   else if (exp)
