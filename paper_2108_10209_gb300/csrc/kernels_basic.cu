@@ -703,17 +703,45 @@ cudaError_t launch_conv1_wgrad(const void* dout, const float* img, int C0, int H
 
 // ---------------------------------------------------------------------------------------------
 // Head, training step (Methods: 1x1 convolution, sigmoid, BCE loss against the target).
-// One thread per pixel: z = b + w . a8, dL/dz = (sigmoid(z) - y) / P away from the -100 clamps
-// of the BCE log terms (MSE alternative: 2 (s - y) s (1 - s) / P), delta_8 = dL/dz * w * [a8 > 0], and per-block
-// partial sums of dL/dz * a8 (head weight gradient), dL/dz (head bias) and the loss (FP64).
+// Per pixel z = b + w . a8, dL/dz = (sigmoid(z) - y) / P away from the -100 clamps of the BCE
+// log terms (MSE alternative: 2 (s - y) s (1 - s) / P), delta_8 = dL/dz * w * [a8 > 0]; per
+// block of 256 pixels the partial sums of dL/dz * a8 (head weight gradient), dL/dz (head bias)
+// and the loss (FP64).
 __device__ __forceinline__ float sigmoid_f(float z) {
   if (z >= 0.f) return 1.f / (1.f + expf(-z));
   const float e = expf(z);
   return e / (1.f + e);
 }
 
+// Unpacks a 16-byte group (G channels) held in a register.
 template <typename T>
-__global__ void __launch_bounds__(256) k_head_train(const T* __restrict__ a8, int C, int npx,
+__device__ __forceinline__ void unpack_group(const uint4 q, float* v);
+template <>
+__device__ __forceinline__ void unpack_group<float>(const uint4 q, float* v) {
+  v[0] = __uint_as_float(q.x); v[1] = __uint_as_float(q.y);
+  v[2] = __uint_as_float(q.z); v[3] = __uint_as_float(q.w);
+}
+template <>
+__device__ __forceinline__ void unpack_group<__nv_bfloat16>(const uint4 q, float* v) {
+  const unsigned w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    v[2 * i] = __uint_as_float(w[i] << 16);
+    v[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+  }
+}
+
+// One read of the layer-8 map: a block takes 256 pixels as eight sub-tiles of 32, each staged
+// in shared memory ([C/G][33] 16-byte groups, one pad group per row), from which it computes
+// z (eight threads per pixel, a fixed butterfly over their partial sums), dL/dz, the
+// head-gradient sums (thread c: channel c over the pixels in order) and delta_8 (stored group
+// by group, coalesced). Reading the map once instead of twice (z, then delta_8) halves its
+// traffic.
+constexpr int kHeadTP = 32;  // pixels per sub-tile
+constexpr int kHeadSub = 8;  // sub-tiles per block: 256 pixels, one row of head partials
+
+template <typename T>
+__global__ void __launch_bounds__(256, 4) k_head_train(const T* __restrict__ a8, int C, int npx,
                                                     const float* __restrict__ w9,
                                                     const float* __restrict__ b9,
                                                     const float* __restrict__ tgt, int loss_kind,
@@ -722,87 +750,126 @@ __global__ void __launch_bounds__(256) k_head_train(const T* __restrict__ a8, in
                                                     float* __restrict__ hpart, const int* skip) {
   if (skip && *skip) return;
   constexpr int G = CGTraits<T>::G;
+  constexpr int PITCH = kHeadTP + 1;
+  constexpr int kTpp = 256 / kHeadTP;  // threads per pixel for z
+  __shared__ uint4 tile[(256 / G) * PITCH];
   __shared__ float sw[256];
-  __shared__ float sred[8][257];
+  __shared__ float sdz[kHeadTP];
   __shared__ double sl[8];
-  for (int i = threadIdx.x; i < C; i += blockDim.x) sw[i] = w9[i];
-  __syncthreads();
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int ng = C / G;
+  for (int i = t; i < C; i += blockDim.x) sw[i] = w9[i];
+  const float bias = b9[0];
+  float acc = 0.f;     // thread c < C: sum of dL/dz * a8[c] over the block's pixels
+  float dzsum = 0.f;   // thread C (or 0 when C = 256, after its channel): sum of dL/dz
+  double lsum = 0.0;   // loss terms of the pixels this thread scored
+  float dmx = 0.f;     // largest |delta_8| this thread stored
   // unsigned: the last block may reach past 2^31 - 1 when npx is close to it
-  const unsigned p = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool live = p < (unsigned)npx;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float z = b9[0];
-  if (live)
-    for (int g = 0; g < C / G; ++g) {
-      float v[G];
-      load_group<T>(a8, (size_t)g * npx + p, v);
+  const unsigned pb = blockIdx.x * (unsigned)(kHeadTP * kHeadSub);
+  // a thread's groups of a sub-tile (units u = t + 256 i), loaded one sub-tile ahead
+  constexpr int kU = (256 / G) * kHeadTP / 256;
+  uint4 nxt[kU];
+  auto load_sub = [&](int sub) {
+    const unsigned p0 = pb + sub * kHeadTP;
 #pragma unroll
-      for (int k = 0; k < G; ++k) z += sw[g * G + k] * v[k];
+    for (int i = 0; i < kU; ++i) {
+      const int u = t + 256 * i, g = u / kHeadTP, px = u % kHeadTP;
+      nxt[i] = make_uint4(0u, 0u, 0u, 0u);
+      if (u < ng * kHeadTP && p0 + px < (unsigned)npx)
+        nxt[i] = reinterpret_cast<const uint4*>(a8)[(size_t)g * npx + p0 + px];
     }
-  float dz = 0.f;
-  double lterm = 0.0;
-  if (live) {
-    const float s = sigmoid_f(z), y = tgt[p];
-    if (loss_kind == 0) {
-      // BCE with each log term clamped at -100 (bounded for unclipped targets outside [0, 1]);
-      // log s = -softplus(-z), log(1 - s) = -softplus(z)
-      const float sp = log1pf(expf(-fabsf(z)));
-      const float lp = -(fmaxf(-z, 0.f) + sp), lq = -(fmaxf(z, 0.f) + sp);
-      const bool m1 = lp > -100.f, m2 = lq > -100.f;
-      const float g = (m1 && m2) ? s - y : (m1 ? -y * (1.f - s) : 0.f) + (m2 ? (1.f - y) * s : 0.f);
-      dz = g / (float)npx;
-      lterm = -(double)y * (m1 ? lp : -100.0) - (1.0 - (double)y) * (m2 ? lq : -100.0);
-    } else {
-      dz = 2.f * (s - y) * s * (1.f - s) / (float)npx;
-      lterm = (double)(s - y) * (double)(s - y);
+  };
+  load_sub(0);
+  for (int sub = 0; sub < kHeadSub; ++sub) {
+    const unsigned p0 = pb + sub * kHeadTP;
+#pragma unroll
+    for (int i = 0; i < kU; ++i) {
+      const int u = t + 256 * i;
+      if (u < ng * kHeadTP) tile[(u / kHeadTP) * PITCH + u % kHeadTP] = nxt[i];
     }
-    dzbuf[p] = dz;
-  }
-  float dmx = 0.f;  // largest |delta_8| of this pixel
-  for (int g = 0; g < C / G; ++g) {
-    float v[G];
-    if (live) {
-      load_group<T>(a8, (size_t)g * npx + p, v);
-      float d[G];
+    __syncthreads();
+    if (sub + 1 < kHeadSub) load_sub(sub + 1);  // in flight while this sub-tile is worked
+    {  // z = b + w . a8 and dL/dz for pixel px
+      const int px = t / kTpp, q = t % kTpp;
+      float z = 0.f;
+      for (int g = q; g < ng; g += kTpp) {
+        float v[G];
+        unpack_group<T>(tile[g * PITCH + px], v);
+#pragma unroll
+        for (int k = 0; k < G; ++k) z += sw[g * G + k] * v[k];
+      }
+#pragma unroll
+      for (int off = 1; off < kTpp; off <<= 1) z += __shfl_xor_sync(0xffffffffu, z, off);
+      z += bias;
+      const unsigned p = p0 + px;
+      if (q == 0) {
+        float dz = 0.f;
+        if (p < (unsigned)npx) {
+          const float s = sigmoid_f(z), y = tgt[p];
+          if (loss_kind == 0) {
+            // BCE with each log term clamped at -100 (bounded for unclipped targets outside
+            // [0, 1]); log s = -softplus(-z), log(1 - s) = -softplus(z)
+            const float sp = log1pf(expf(-fabsf(z)));
+            const float lp = -(fmaxf(-z, 0.f) + sp), lq = -(fmaxf(z, 0.f) + sp);
+            const bool m1 = lp > -100.f, m2 = lq > -100.f;
+            const float gr = (m1 && m2) ? s - y
+                                        : (m1 ? -y * (1.f - s) : 0.f) + (m2 ? (1.f - y) * s : 0.f);
+            dz = gr / (float)npx;
+            lsum += -(double)y * (m1 ? lp : -100.0) - (1.0 - (double)y) * (m2 ? lq : -100.0);
+          } else {
+            dz = 2.f * (s - y) * s * (1.f - s) / (float)npx;
+            lsum += (double)(s - y) * (double)(s - y);
+          }
+          dzbuf[p] = dz;
+        }
+        sdz[px] = dz;
+      }
+    }
+    __syncthreads();
+    if (t < C) {  // head-weight gradient: channel t, the sub-tile's pixels in order
+      // the 32-bit word of the group that holds channel t (bf16: two channels a word, the
+      // even one in the low half), read directly
+      const int g = t / G, k = t % G;
+      const uint32_t* tw =
+          reinterpret_cast<const uint32_t*>(tile) + g * PITCH * 4 + (G == 4 ? k : k >> 1);
+      const bool hi = G == 8 && (k & 1);
+#pragma unroll 8
+      for (int px = 0; px < kHeadTP; ++px) {
+        const uint32_t w = tw[px * 4];
+        const float v =
+            G == 4 ? __uint_as_float(w) : __uint_as_float(hi ? (w & 0xffff0000u) : (w << 16));
+        acc += sdz[px] * v;
+      }
+    }
+    if (t == (C < 256 ? C : 0))
+      for (int px = 0; px < kHeadTP; ++px) dzsum += sdz[px];
+    for (int u = t; u < ng * kHeadTP; u += 256) {  // delta_8 = dL/dz * w * [a8 > 0]
+      const int g = u / kHeadTP, px = u % kHeadTP;
+      const unsigned p = p0 + px;
+      if (p >= (unsigned)npx) continue;
+      float v[G], d[G];
+      unpack_group<T>(tile[g * PITCH + px], v);
+      const float dz = sdz[px];
 #pragma unroll
       for (int k = 0; k < G; ++k) {
         d[k] = v[k] > 0.f ? dz * sw[g * G + k] : 0.f;
         dmx = fmaxf(dmx, fabsf(d[k]));
       }
-      if (N2F_IN((size_t)g * npx + p, (size_t)(C / G) * npx))
-        store_group<T>(d8, (size_t)g * npx + p, d);
-    } else {
-#pragma unroll
-      for (int k = 0; k < G; ++k) v[k] = 0.f;
+      if (N2F_IN((size_t)g * npx + p, (size_t)ng * npx)) store_group<T>(d8, (size_t)g * npx + p, d);
     }
-#pragma unroll
-    for (int k = 0; k < G; ++k) {
-      float c = dz * v[k];
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
-      if (lane == 0) sred[warp][g * G + k] = c;
-    }
+    __syncthreads();  // the next sub-tile overwrites the tile and sdz
   }
-  {
-    float c = dz;
+  float* row = hpart + (size_t)blockIdx.x * (C + 1);
+  if (t < C) row[t] = acc;
+  if (t == (C < 256 ? C : 0)) row[C] = dzsum;
+  double l = lsum;
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
-    if (lane == 0) sred[warp][C] = c;
-    double l = lterm;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) l += __shfl_xor_sync(0xffffffffu, l, off);
-    if (lane == 0) sl[warp] = l;
-  }
+  for (int off = 16; off > 0; off >>= 1) l += __shfl_xor_sync(0xffffffffu, l, off);
+  if (lane == 0) sl[warp] = l;
   __syncthreads();
-  const int nw = blockDim.x >> 5;
-  for (int q = threadIdx.x; q <= C; q += blockDim.x) {
-    float s = 0.f;
-    for (int k = 0; k < nw; ++k) s += sred[k][q];
-    hpart[(size_t)blockIdx.x * (C + 1) + q] = s;
-  }
-  if (threadIdx.x == 0) {
+  if (t == 0) {
     double s = 0.0;
-    for (int k = 0; k < nw; ++k) s += sl[k];
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += sl[k];
     loss_part[blockIdx.x] = s;
   }
   if (dmax) block_absmax_to(dmx, dmax);
