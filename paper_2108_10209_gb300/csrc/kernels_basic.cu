@@ -256,19 +256,20 @@ __device__ __forceinline__ int weight_layer(const PackArgs& pa, unsigned long lo
 __device__ __forceinline__ void pack_param(const PackArgs& pa, int l, unsigned long long i,
                                            float th, bool simt, bool tc, float s) {
   const int cin = l == 0 ? pa.c0 : pa.widths[l - 1], cout = pa.widths[l];
-  const size_t j = i - pa.w_off[l];
-  const int o = (int)(j / ((size_t)cin * 9));
-  const int rem = (int)(j % ((size_t)cin * 9));
+  // 32-bit: a layer holds at most 256 x 256 x 9 weights
+  const unsigned j = (unsigned)(i - pa.w_off[l]), cin9 = (unsigned)cin * 9u;
+  const int o = (int)(j / cin9);
+  const int rem = (int)(j - (unsigned)o * cin9);
   pack_one(simt ? pa.fwd[l] : nullptr, simt ? pa.dgr[l] : nullptr, tc ? pa.tcf[l] : nullptr,
            pa.tcd[l], pa.tcf_lo[l], pa.tcd_lo[l], pa.tc_bf16, l == 0, cin, cout, o, rem / 9,
            rem % 9, th, s);
 }
 
-// Adam (Kingma & Ba, Algorithm 1; Methods: lr 0.001), fused with writing the packed weight
-// copies the convolution kernels read. update = 0 only packs (after init / set_theta). In the
-// float32 form the tensor-core copies need each layer's largest weight first: this kernel
-// collects it (pa.sw->wnew, by step parity) and k_pack_f16 writes those copies; it also clears
-// the activation and delta words for the next pass and the other parity's weight words.
+// Adam (Kingma & Ba, Algorithm 1; Methods: lr 0.001), fused with writing the CUDA-core weight
+// copies (the layers that have them). update = 0 only packs (after init / set_theta). The
+// tensor-core copies follow in k_pack_tc; in the float32 form they need each layer's largest
+// weight first: this kernel collects it (pa.sw->wnew, by step parity); it also clears the
+// activation and delta words for the next pass and the other parity's weight words.
 __global__ void k_adam(PackArgs pa, const float* __restrict__ grad, float* __restrict__ m,
                        float* __restrict__ v, AdamConsts k, const DevState* __restrict__ state,
                        int update) {
@@ -301,7 +302,7 @@ __global__ void k_adam(PackArgs pa, const float* __restrict__ grad, float* __res
       }
       const int l = weight_layer(pa, i);
       if (l >= 0) {
-        pack_param(pa, l, i, th, true, pa.tc_bf16 != 0, 1.f);
+        pack_param(pa, l, i, th, true, false, 1.f);  // tensor-core copies: k_pack_tc
         if (pa.tcf[l] && sw) {
           lw = l;
           aw = fabsf(th);
@@ -330,24 +331,81 @@ __global__ void k_adam(PackArgs pa, const float* __restrict__ grad, float* __res
   }
 }
 
-// Float32 form: the fp16 hi / lo tensor-core copies of every tensor-core layer, scaled by the
-// power of two that the layer's largest weight (collected by k_adam) gives; records that
-// largest weight in sw->w for the convolution kernels.
-__global__ void k_pack_f16(PackArgs pa, const DevState* __restrict__ state, int update) {
+// The tensor-core copies of every tensor-core layer (bf16; float32 form: fp16 hi / lo parts
+// scaled by the power of two that the layer's largest weight, collected by k_adam, gives), for
+// the forward (rows o, K = tap x C_in + c) and the dgrad (rows c, K = (8 - tap) x C_out + o).
+// A block packs one tile of 32 rows for one 16-channel K chunk: it reads the weights
+// those rows need, contiguous in theta ([o][c][tap]), into shared memory, then writes each
+// (tap, 8-channel slab) run of the packed stage, 8 x rows contiguous elements, in order, so
+// both its reads and its writes are coalesced (element by element in theta order the packed
+// positions scatter: one store per sector). Block 0 also records the largest weights in sw->w
+// for the convolution kernels.
+struct PackTcPlan {
+  int start[2 * kLayers + 1];  // first block of (layer l, direction d) at 2 l + d
+};
+
+constexpr int kPackRows = 32;  // rows per k_pack_tc block (every tensor-core layer has >= 32)
+
+__global__ void __launch_bounds__(256) k_pack_tc(PackArgs pa, PackTcPlan plan,
+                                                 const DevState* __restrict__ state, int update) {
   if (update && state->stopped) return;
-  __shared__ float ss[kLayers];
+  constexpr int TR = kPackRows, N = 16 * TR * 9, PER = N / 256;
+  __shared__ float buf[N];
   ScaleWords* sw = pa.sw;
   const int slot = state->t & 1;
-  if (threadIdx.x < kLayers) {
-    const unsigned mw = sw->wnew[slot][threadIdx.x];
-    ss[threadIdx.x] = pow2f(f16_scale_exp(mw));
-    if (blockIdx.x == 0) sw->w[threadIdx.x] = mw;
+  if (sw && blockIdx.x == 0 && threadIdx.x < kLayers) sw->w[threadIdx.x] = sw->wnew[slot][threadIdx.x];
+  int q = 0;
+  while (q < 2 * kLayers && (int)blockIdx.x >= plan.start[q + 1]) ++q;
+  const int l = q >> 1, dir = q & 1;
+  const int cin = l == 0 ? pa.c0 : pa.widths[l - 1], cout = pa.widths[l];
+  const int Kc = dir ? cout : cin;  // K-side channels
+  const int NT = dir ? tc_cfg(cout, cin, pa.tc_bf16).NT : tc_cfg(cin, cout, pa.tc_bf16).NT;
+  const int nchunks = Kc / 16;
+  const int b = (int)blockIdx.x - plan.start[q];
+  const int tile = b / nchunks, chunk = b - tile * nchunks;
+  const int r0 = tile * TR, nt = r0 / NT, rr0 = r0 % NT;
+  const float* th = pa.theta + pa.w_off[l];
+  float s = 1.f;
+  if (!pa.tc_bf16) s = pow2f(f16_scale_exp(sw->wnew[slot][l]));
+  // theta[o][c][tap]: forward, rows o = r0.., channels c = 16 chunk..: 144 floats per row;
+  // dgrad, rows c = r0.., channels o = 16 chunk..: TR x 9 floats per channel o
+  float v[PER];
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {  // all loads in flight before any store
+    const int u = threadIdx.x + 256 * k;
+    if (!dir) {
+      const int rl = u / 144, j = u - rl * 144;
+      v[k] = th[((size_t)(r0 + rl) * cin + chunk * 16) * 9 + j];
+    } else {
+      const int ol = u / (TR * 9), j = u - ol * (TR * 9);
+      v[k] = th[((size_t)(chunk * 16 + ol) * cin + r0) * 9 + j];
+    }
   }
+#pragma unroll
+  for (int k = 0; k < PER; ++k) buf[threadIdx.x + 256 * k] = v[k];
   __syncthreads();
-  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
-       i < pa.count; i += (unsigned long long)gridDim.x * blockDim.x) {
-    const int l = weight_layer(pa, i);
-    if (l >= 0 && pa.tcf[l]) pack_param(pa, l, i, pa.theta[i], false, true, ss[l]);
+  void* dhi = dir ? pa.tcd[l] : pa.tcf[l];
+  void* dlo = dir ? pa.tcd_lo[l] : pa.tcf_lo[l];
+  const size_t stage = (size_t)nt * nchunks + chunk;
+  const size_t nw = (size_t)cin * cout * 9;
+  (void)nw;  // the checked build's bound
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    // u = ((tap x 2 + slab) x TR + rl) x 8 + e: the stage's element order within this tile
+    const int u = threadIdx.x + 256 * k;
+    const int e = u & 7, rl = (u >> 3) % TR, ts = (u >> 3) / TR, slab = ts & 1, tap = ts >> 1;
+    const int kc = slab * 8 + e;  // K-side channel within the chunk
+    const float x0 = !dir ? buf[rl * 144 + kc * 9 + tap] : buf[kc * (TR * 9) + rl * 9 + (8 - tap)];
+    const size_t idx = (((stage * 9 + tap) * 2 + slab) * NT + rr0 + rl) * 8 + e;
+    if (!N2F_IN(idx, nw)) continue;
+    if (pa.tc_bf16) {
+      ((__nv_bfloat16*)dhi)[idx] = __float2bfloat16_rn(x0);
+    } else {
+      const float x = x0 * s;
+      const __half hi = __float2half_rn(x);
+      ((__half*)dhi)[idx] = hi;
+      ((__half*)dlo)[idx] = __float2half_rn(x - __half2float(hi));
+    }
   }
 }
 
@@ -422,8 +480,22 @@ cudaError_t launch_adam(const PackArgs& pa, const float* grad, float* m, float* 
   k_adam<<<g, 256, 0, st>>>(pa, grad, m, v, k, state, update);
   count_launch();
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess || !pa.sw) return e;
-  k_pack_f16<<<g, 256, 0, st>>>(pa, state, update);
+  if (e != cudaSuccess) return e;
+  // the tensor-core copies: blocks of (layer, direction) = row tiles of 32 x K chunks of 16
+  PackTcPlan plan;
+  int nb = 0;
+  for (int l = 0; l < kLayers; ++l)
+    for (int d = 0; d < 2; ++d) {
+      plan.start[2 * l + d] = nb;
+      if (!pa.tcf[l]) continue;
+      const int cin = l == 0 ? pa.c0 : pa.widths[l - 1], cout = pa.widths[l];
+      const int R = d ? cin : cout, Kc = d ? cout : cin;
+      if (R % kPackRows || Kc % 16) return cudaErrorInvalidValue;
+      nb += (R / kPackRows) * (Kc / 16);
+    }
+  plan.start[2 * kLayers] = nb;
+  if (nb == 0) return cudaSuccess;
+  k_pack_tc<<<nb, 256, 0, st>>>(pa, plan, state, update);
   N2F_LAUNCH_CHECK();
 }
 

@@ -70,7 +70,8 @@ struct ScaleWords {
 //   dgr : [C_out/8][9][8][C_in] f32, tap rotated to 8 - tap                -- SIMT dgrad
 //   tcf/tcd : the same two matrices in the tensor-core operand order (tc_layout.cuh), bf16,
 //             or in the float32 form fp16 hi parts of the scaled weights with the fp16
-//             residuals in tcf_lo/tcd_lo (written by k_pack_f16 after the Adam kernel)
+//             residuals in tcf_lo/tcd_lo (written by k_pack_tc after the Adam kernel; the
+//             CUDA-core copies fwd/dgr exist only for the layers that run on the CUDA cores)
 struct PackArgs {
   float* theta;
   float* fwd[kLayers];
@@ -102,8 +103,9 @@ struct AdamConsts {
   float lr, b1, omb1, b2, omb2, eps;
 };
 AdamConsts adam_consts(double lr, double b1, double b2, double eps);
-// Adam step (update = 1) or a plain repack (update = 0), then, in the float32 form, the fp16
-// tensor-core copies (k_pack_f16). With update = 0 the caller clears pa.sw->wnew first.
+// Adam step (update = 1) or a plain repack (update = 0), then the tensor-core copies
+// (k_pack_tc: bf16, or the float32 form's fp16 parts). With update = 0 the caller clears
+// pa.sw->wnew first.
 cudaError_t launch_adam(const PackArgs& pa, const float* grad, float* m, float* v,
                         const AdamConsts& k, const DevState* state, int update, cudaStream_t st);
 // One canonical weight tensor into its operand copies. Float32 form: wmax (device word, zeroed

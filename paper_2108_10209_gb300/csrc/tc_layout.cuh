@@ -29,12 +29,23 @@ __host__ __device__ __forceinline__ TcCfg tc_cfg(int cin, int cout, int bf16) {
   return c;
 }
 
-// Element offset of B[r][tap * cin + c] in the packed array.
+// log2 of a power of two
+__host__ __device__ __forceinline__ int log2_pow2(int v) {
+#ifdef __CUDA_ARCH__
+  return __ffs(v) - 1;
+#else
+  return __builtin_ctz((unsigned)v);
+#endif
+}
+
+// Element offset of B[r][tap * cin + c] in the packed array (NT, KC and GE are powers of two
+// for every supported shape: the row split is a shift and a mask).
 __host__ __device__ __forceinline__ size_t tc_index_cfg(const TcCfg& f, int cin, int r, int tap,
                                                          int c) {
   const int nchunks = cin / f.KC;
   const int nslab = f.KC / f.GE;
-  const int nt = r / f.NT, rr = r % f.NT;
+  const int lnt = log2_pow2(f.NT);
+  const int nt = r >> lnt, rr = r & (f.NT - 1);
   const int chunk = c / f.KC, cc = c % f.KC;
   const int slab = cc / f.GE, e = cc % f.GE;
   const size_t stage = (size_t)nt * nchunks + chunk;

@@ -185,8 +185,11 @@ static size_t layout(Trainer* t, char* base) {
   bool any_tc = false;
   for (int l = 0; l < kLayers; ++l) {
     const size_t nw = (size_t)net.widths[l] * net.cin(l) * 9;
-    t->pa.fwd[l] = c.take<float>(nw);
-    if (l > 0 && t->engine[l] == N2F_ENGINE_TC) {
+    // the CUDA-core copies only for the layers that run on the CUDA cores (the first layer
+    // always): the packing kernels skip a copy that is not there
+    const bool tc = l > 0 && t->engine[l] == N2F_ENGINE_TC;
+    t->pa.fwd[l] = tc ? nullptr : c.take<float>(nw);
+    if (tc) {
       any_tc = true;
       // 16-bit elements: bf16, or the float32 form's fp16 hi and lo parts
       t->pa.tcf[l] = c.take<uint16_t>(nw);
@@ -196,8 +199,9 @@ static size_t layout(Trainer* t, char* base) {
   t->snap_bytes = c.off - t->snap_off;
   for (int l = 1; l < kLayers; ++l) {
     const size_t nw = (size_t)net.widths[l] * net.cin(l) * 9;
-    t->pa.dgr[l] = c.take<float>(nw);
-    if (t->engine[l] == N2F_ENGINE_TC) {
+    const bool tc = t->engine[l] == N2F_ENGINE_TC;
+    t->pa.dgr[l] = tc ? nullptr : c.take<float>(nw);
+    if (tc) {
       t->pa.tcd[l] = c.take<uint16_t>(nw);
       if (!t->bf16) t->pa.tcd_lo[l] = c.take<uint16_t>(nw);
     }
