@@ -648,7 +648,13 @@ cudaError_t launch_conv1_fwd(const float* img, int C0, int H, int W, const float
 
 // First-layer weight gradient: dW[o][c][tap] = sum_p d(p,o) x_c(p + tap), db[o] = sum_p d(p,o).
 // Block s sums pixel tiles s, s+S, ... in order; the partials are reduced in block order.
-constexpr int kConv1Acc = (64 * (kMaxC0 * 9 + 1) + 255) / 256;  // (o, c, tap) + biases per thread
+// First-layer weight and bias gradients, per block over a strided set of 64-pixel tiles: the
+// tile's delta (C channels) and the K = C_0 x 9 shifted input values of each pixel are staged
+// in shared memory; each thread owns a register tile of 4 output channels x 3 of the K values
+// (or x the constant 1 for the biases) and runs over its share of the tile's pixels (pixel
+// groups pg, pg + npg, ...), so one 16-byte load of delta feeds up to twelve FMAs. At the end
+// the pixel groups' sums are added in group order and the block writes its partial row
+// part[blockIdx][q], q = o K + c x 9 + tap, then the C biases.
 template <typename T>
 __global__ void __launch_bounds__(256) k_conv1_wgrad(const T* __restrict__ dout,
                                                      const float* __restrict__ img, int C0, int H,
@@ -656,20 +662,27 @@ __global__ void __launch_bounds__(256) k_conv1_wgrad(const T* __restrict__ dout,
                                                      size_t part_cap, const int* skip) {
   if (skip && *skip) return;
   constexpr int G = CGTraits<T>::G;
-  constexpr int TP = 64;
-  __shared__ float sD[TP][64 + 1];
+  constexpr int TP = 64, DP = 68;  // pixels per tile; delta row pitch (16-byte aligned rows)
+  __shared__ __align__(16) float sD[TP * DP];
   __shared__ float sX[TP][kMaxC0 * 9 + 1];
   const size_t npx = (size_t)H * W;
   const int K = C0 * 9;
   const int Q = C * (K + 1);  // (o, c, tap) triples then the C biases
-  float acc[kConv1Acc];
+  const int ncg = K / 3 + 1, nslot = (C / 4) * ncg, npg = 256 / nslot;
+  const int t = threadIdx.x, slot = t % nslot, pg = t / nslot;
+  const bool act = pg < npg;
+  const int og = slot / ncg, cg = slot - og * ncg;
+  const bool bias = cg == ncg - 1;
+  float acc[4][3];
 #pragma unroll
-  for (int r = 0; r < kConv1Acc; ++r) acc[r] = 0.f;
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) acc[i][j] = 0.f;
   const size_t ntiles = (npx + TP - 1) / TP;
   for (size_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const size_t p0 = tile * TP;
     __syncthreads();
-    for (int i = threadIdx.x; i < TP * (C / G); i += blockDim.x) {
+    for (int i = t; i < TP * (C / G); i += blockDim.x) {
       const int pp = i % TP, g = i / TP;
       const size_t p = p0 + pp;
       float v[G];
@@ -680,9 +693,11 @@ __global__ void __launch_bounds__(256) k_conv1_wgrad(const T* __restrict__ dout,
         for (int k = 0; k < G; ++k) v[k] = 0.f;
       }
 #pragma unroll
-      for (int k = 0; k < G; ++k) sD[pp][g * G + k] = v[k];
+      for (int k = 0; k < G; k += 4)
+        *reinterpret_cast<float4*>(&sD[pp * DP + g * G + k]) =
+            make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
     }
-    for (int i = threadIdx.x; i < TP * K; i += blockDim.x) {
+    for (int i = t; i < TP * K; i += blockDim.x) {
       const int pp = i / K, cq = i % K, c = cq / 9, q = cq % 9;
       const size_t p = p0 + pp;
       float v = 0.f;
@@ -695,56 +710,72 @@ __global__ void __launch_bounds__(256) k_conv1_wgrad(const T* __restrict__ dout,
       sX[pp][cq] = v;
     }
     __syncthreads();
+    if (act) {
+      for (int pp = pg; pp < TP; pp += npg) {
+        const float4 d = *reinterpret_cast<const float4*>(&sD[pp * DP + og * 4]);
+        const float dv[4] = {d.x, d.y, d.z, d.w};
+        float xv[3];
 #pragma unroll
-    for (int r = 0; r < kConv1Acc; ++r) {
-      const int qi = threadIdx.x + r * 256;
-      if (qi >= Q) break;
-      float s = acc[r];
-      if (qi < C * K) {
-        const int o = qi / K, cq = qi % K;
-        for (int pp = 0; pp < TP; ++pp) s += sD[pp][o] * sX[pp][cq];
-      } else {
-        const int o = qi - C * K;
-        for (int pp = 0; pp < TP; ++pp) s += sD[pp][o];
+        for (int j = 0; j < 3; ++j) xv[j] = bias ? (j == 0 ? 1.f : 0.f) : sX[pp][cg * 3 + j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j) acc[i][j] += dv[i] * xv[j];
       }
-      acc[r] = s;
     }
   }
+  // the pixel groups' sums, added in group order (sD reused: npg x Q <= 2816 floats)
+  __syncthreads();
+  float* red = sD;
+  if (act) {
 #pragma unroll
-  for (int r = 0; r < kConv1Acc; ++r) {
-    const int qi = threadIdx.x + r * 256;
-    if (qi < Q && N2F_IN((size_t)blockIdx.x * Q + qi, part_cap))
-      part[(size_t)blockIdx.x * Q + qi] = acc[r];
+    for (int i = 0; i < 4; ++i) {
+      const int o = og * 4 + i;
+      if (bias) {
+        red[pg * Q + C * K + o] = acc[i][0];
+      } else {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) red[pg * Q + o * K + cg * 3 + j] = acc[i][j];
+      }
+    }
+  }
+  __syncthreads();
+  for (int q = t; q < Q; q += blockDim.x) {
+    float sum = 0.f;
+    for (int g2 = 0; g2 < npg; ++g2) sum += red[g2 * Q + q];
+    if (N2F_IN((size_t)blockIdx.x * Q + q, part_cap)) part[(size_t)blockIdx.x * Q + q] = sum;
   }
 }
 
 // out[q] = sum over s of part[s * Q + q], canonical placement of dW and db. A block owns 32
-// consecutive q (the lanes); warp w sums s = w, w + 8, ... in order and the eight warp sums
-// are added in warp order, so the result is fixed for a given S.
-__global__ void __launch_bounds__(256) k_reduce_conv1(const float* __restrict__ part, int S,
-                                                      int C, int K, float* __restrict__ gw,
-                                                      float* __restrict__ gb, const int* skip) {
+// consecutive q (the lanes); warp w sums s = w, w + 32, ... in order and the 32 warp sums are
+// added in warp order, so the result is fixed for a given S (Q is a few hundred: few blocks,
+// so each warp's chain of loads is kept short).
+__global__ void __launch_bounds__(1024) k_reduce_conv1(const float* __restrict__ part, int S,
+                                                       int C, int K, float* __restrict__ gw,
+                                                       float* __restrict__ gb, const int* skip) {
   if (skip && *skip) return;
-  __shared__ float sh[8][33];
+  constexpr int NW = 32;  // warps: a short chain of loads each (Q is small, few blocks)
+  __shared__ float sh[NW][33];
   const int Q = C * (K + 1);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int q = blockIdx.x * 32 + lane;
   float s = 0.f;
   if (q < Q) {
     int k = w;
-    for (; k + 24 < S; k += 32) {  // four loads in flight, added in split order
-      const float a = part[(size_t)k * Q + q], b = part[(size_t)(k + 8) * Q + q];
-      const float c = part[(size_t)(k + 16) * Q + q], d = part[(size_t)(k + 24) * Q + q];
+    for (; k + 3 * NW < S; k += 4 * NW) {  // four loads in flight, added in split order
+      const float a = part[(size_t)k * Q + q], b = part[(size_t)(k + NW) * Q + q];
+      const float c = part[(size_t)(k + 2 * NW) * Q + q], d = part[(size_t)(k + 3 * NW) * Q + q];
       s = (((s + a) + b) + c) + d;
     }
-    for (; k < S; k += 8) s += part[(size_t)k * Q + q];
+    for (; k < S; k += NW) s += part[(size_t)k * Q + q];
   }
   sh[w][lane] = s;
   __syncthreads();
   if (w == 0 && q < Q) {
     float t = 0.f;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) t += sh[k][lane];
+    for (int k = 0; k < NW; ++k) t += sh[k][lane];
     if (q < C * K)
       gw[q] = t;  // [o][c][ky][kx] == (o * C0 + c) * 9 + tap
     else
@@ -769,7 +800,7 @@ cudaError_t launch_conv1_wgrad(const void* dout, const float* img, int C0, int H
     k_conv1_wgrad<float><<<S, 256, 0, st>>>((const float*)dout, img, C0, H, W, C, part, part_cap,
                                             skip);
   count_launch();
-  k_reduce_conv1<<<nblocks(Q, 32), 256, 0, st>>>(part, S, C, K, gw, gb, skip);
+  k_reduce_conv1<<<nblocks(Q, 32), 1024, 0, st>>>(part, S, C, K, gw, gb, skip);
   N2F_LAUNCH_CHECK();
 }
 
