@@ -20,11 +20,11 @@ def _image(h, w, seed, sigma=25):
     return synth.image_cells(h, w, sigma=sigma / 255.0, seed=seed)[1].astype(np.float32)
 
 
-def _run(imgs, prm, use_graphs=True, lookahead=0, profile_kernel=0):
+def _run(imgs, prm, use_graphs=True, lookahead=0, profile_kernel=0, group_size=0):
     """Submits every image at once; returns per image (result, status dict, history)."""
     out = []
-    with n2f.Context(use_graphs=use_graphs, lookahead=lookahead,
-                     profile_kernel=profile_kernel) as ctx:
+    with n2f.Context(use_graphs=use_graphs, lookahead=lookahead, profile_kernel=profile_kernel,
+                     group_size=group_size) as ctx:
         ids = [ctx.submit(x, prm) for x in imgs]
         for j, x in zip(ids, imgs):
             assert ctx.wait(j, 600000) == n2f.N2F_OK
@@ -79,3 +79,11 @@ def test_overlap_is_ignored_by_fixed_step_jobs():
     imgs = [_image(32, 48, seed=16)]
     base = dict(seed=8, fixed_steps=9)
     _same(_run(imgs, n2f.params(**base)), _run(imgs, n2f.params(**base, overlap=1)))
+
+
+def test_overlap_jobs_in_a_lockstep_group():
+    # jobs that ask for overlap and join a lockstep group validate in line with their group; the
+    # numbers are the same, so each result equals its solo overlapped run
+    imgs = [_image(40, 48, seed=17), _image(40, 48, seed=18, sigma=50)]
+    p = n2f.params(seed=9, patience=10, widths=n2f.N2F_WIDTHS_W64, overlap=1)
+    _same(_run(imgs, p), _run(imgs, p, group_size=4))
