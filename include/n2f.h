@@ -160,8 +160,10 @@ typedef struct {
    * snapshot, so the validation scores, the stop epoch and the result are bit-identical to
    * overlap = 0. The epoch after the stop has then already run; its steps are discarded (Adam
    * state counters restored, the weights not used again). Costs one more set of validation
-   * activations (2 x 256 x H x W elements) and the snapshot (about 3 x the weight count in
-   * floats). 0: each validation runs in line after its epoch (default). */
+   * activations (2 x 256 x H x W elements) and the snapshot (theta and the forward weight
+   * copies: about twice the weight count in floats with the tensor-core engine). A job in a
+   * lockstep group validates in line with its group. 0: each validation runs in line after its
+   * epoch (default). */
   int32_t overlap;
 } n2f_params;
 
